@@ -1,0 +1,358 @@
+#!/usr/bin/env python
+"""Benchmark of the restricted additive Vanka (RAV) multigrid V-cycle on GB300.
+
+Workload (default): 2-D Stokes, Q2-Q1 on a uniform 512x512 grid of the unit
+square (2,101,250 velocity + 263,169 pressure DoFs), 7 levels (512 -> 8),
+manufactured solution u = curl(sin^2(pi x) sin^2(pi y)), p = cos(pi x) cos(pi y),
+viscosity 1, plain FP64 RAV smoother with damping 0.5, V(2,2).
+
+A step is one V(2,2) cycle on the finest level (smoothing, residuals,
+transfers, coarse solve on every level).  value = DoFs x steps / seconds.
+
+Reported with it:
+  roofline      the dominant kernel (the fine-level RAV subdomain apply),
+                timed live with CUDA events on its launching stream over the
+                timed region, against the FP64 arithmetic peak (it is bound by
+                fp64 FMA throughput on GB300) -- see the design doc for the counts;
+  e2e           the same metric with host buffers, host<->device copies inside;
+  cpu_baseline  the FP64 oracle (one host core) on a bounded sample;
+  time_to_tol   wall time of a full solve to a 1e-8 residual reduction.
+
+--impl reference times the oracle itself as the reference arm.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+# FP64 peak derived from unit counts and clocks: 152 SMs x 2 FP64 FMA/clk/SM x
+# 2 flop x 2.07 GHz (the nominal 1.25 TFLOP/s of GB300).
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+L2_BYTES = 129 * 2 ** 20
+
+WORKLOADS = {
+    "2d512": dict(dim=2, N=512, nlev=7, bc=1, forcing=1, kind=0, prec=0, omega=0.5, nu=2,
+                  desc="2D Stokes Q2-Q1 512x512 unit square, 7 levels, manufactured psi solution, "
+                       "viscosity 1, RAV V(2,2) omega 0.5, FP64"),
+    "2d512-f32": dict(dim=2, N=512, nlev=7, bc=1, forcing=1, kind=0, prec=1, omega=0.5, nu=2,
+                      desc="as 2d512 with FP32-stored patch inverses (FP32 accumulation)"),
+}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=300)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="2d512", choices=sorted(WORKLOADS))
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-tol", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+# ---------------------------------------------------------------------------
+def patch_work(dim, N):
+    """(sum over subdomains of owned rows x subdomain size, total DoFs written)
+    counting only DoFs in the subdomains (compact sizes, Sec. 4.3)."""
+    import numpy as np
+    per_n, per_o = [], []
+    for v in range(N + 1):
+        per_n.append(sum(1 for a in range(5) if 1 <= 2 * v - 2 + a <= 2 * N - 1))
+        per_o.append(sum(1 for a in (2, 3) if 1 <= 2 * v + a - 2 <= 2 * N - 1))
+    pn, po = np.array(per_n, float), np.array(per_o, float)
+    if dim == 2:
+        nodes = np.outer(pn, pn)
+        own = np.outer(po, po)
+    else:
+        nodes = np.einsum("i,j,k->ijk", pn, pn, pn)
+        own = np.einsum("i,j,k->ijk", po, po, po)
+    ni = dim * nodes + 1
+    nown = dim * own + 1
+    return float((ni * nown).sum()), float(nown.sum())
+
+
+def clocks_start():
+    f = tempfile.NamedTemporaryFile(prefix="clocks", suffix=".csv", delete=False)
+    q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+    try:
+        p = subprocess.Popen(["nvidia-smi", f"--query-gpu={q}", "--format=csv,noheader,nounits", "-lms", "100"],
+                             stdout=f, stderr=subprocess.DEVNULL)
+    except OSError:
+        p = None
+    return p, f.name
+
+
+def clocks_stop(handle, gpu_index):
+    p, path = handle
+    if p is None:
+        return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+    p.terminate()
+    try:
+        p.wait(timeout=5)
+    except subprocess.TimeoutExpired:
+        p.kill()
+    sm, mx, reasons = [], [], set()
+    names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+    for line in open(path):
+        f = [x.strip() for x in line.split(",")]
+        if len(f) < 9 or not f[0].isdigit() or int(f[0]) != gpu_index:
+            continue
+        try:
+            sm.append(float(f[1]))
+            mx.append(float(f[2]))
+        except ValueError:
+            continue
+        for nm, v in zip(names, f[5:9]):
+            if v.lower().startswith("active"):
+                reasons.add(nm)
+    os.unlink(path)
+    sm.sort()
+    return {"sm_mhz": sm[len(sm) // 2] if sm else None, "sm_max_mhz": max(mx) if mx else None,
+            "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def measured_traffic(kernel_key):
+    """dram bytes per launch from the committed ncu summary, if it was taken on
+    the current kernel source (else None)."""
+    src = os.path.join(ROOT, "paper_2103_10127_gb300", "csrc", "smoother.cu")
+    digest = hashlib.sha1(open(src, "rb").read()).hexdigest()[:12]
+    path = os.path.join(ROOT, "profiles", f"{kernel_key}.txt")
+    if not os.path.exists(path):
+        return None
+    vals = {}
+    for line in open(path):
+        if ":" in line:
+            k, v = line.split(":", 1)
+            vals[k.strip()] = v.strip()
+    if vals.get("source_sha1") != digest:
+        return None
+    try:
+        return float(vals["dram_bytes_per_launch"])
+    except (KeyError, ValueError):
+        return None
+
+
+# ---------------------------------------------------------------------------
+def cpu_baseline(W, cycles=1):
+    """The oracle, as it stands, on the same workload: untimed set-up, then
+    `cycles` timed V-cycles on one host core."""
+    import oracle as O
+    import numpy as np
+    orc = O.Oracle(W["dim"], W["N"], W["nlev"], bc=W["bc"])
+    orc.setup_smoother(O.RAV, W["omega"], W["prec"])
+    b = orc.rhs(W["forcing"])
+    x = orc.initial_guess()
+    n = orc.sizes(W["nlev"] - 1)["n"]
+    t0 = time.perf_counter()
+    for _ in range(cycles):
+        x = orc.vcycle(x, b, W["nu"], W["nu"])
+    dt = time.perf_counter() - t0
+    del orc
+    return n * cycles / dt, dt, n
+
+
+def run_reference(args, W):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    import oracle as O
+    orc = O.Oracle(W["dim"], W["N"], W["nlev"], bc=W["bc"])
+    orc.setup_smoother(O.RAV, W["omega"], W["prec"])
+    b = orc.rhs(W["forcing"])
+    x = orc.initial_guess()
+    n = orc.sizes(W["nlev"] - 1)["n"]
+    for _ in range(args.warmup):
+        x = orc.vcycle(x, b, W["nu"], W["nu"])
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        x = orc.vcycle(x, b, W["nu"], W["nu"])
+    dt = time.perf_counter() - t0
+    v = n * args.steps / dt
+    out = {"impl": "reference", "metric": "V-cycle DoFs/s", "value": v, "unit": "DoF/s", "n_gpus": args.gpus,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": W["desc"], "dofs": n, "levels": W["nlev"]},
+           "cpu_baseline": {"value": v, "unit": "DoF/s", "cores": 1, "kind": "oracle",
+                            "sample": f"{args.steps} V(2,2) cycles of the full workload after untimed set-up"},
+           "e2e": {"value": v, "unit": "DoF/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def run_ours(args, W):
+    import numpy as np
+    import torch
+    import paper_2103_10127_gb300 as R
+    from paper_2103_10127_gb300 import _capi
+
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    lib = _capi.load()
+    stream = torch.cuda.current_stream()
+
+    mg = R.Multigrid(W["dim"], W["N"], W["nlev"], bc=W["bc"])
+    sm = R.Smoother(mg, W["kind"], W["prec"], W["omega"])
+    fine = W["nlev"] - 1
+    n = mg.n()
+    b = mg.rhs(W["forcing"])
+    x0 = mg.initial_guess()
+    x = x0.clone()
+    nu = W["nu"]
+
+    def step():
+        mg.vcycle(sm, x, b, nu, nu)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    # ---- timed region (device) ----
+    lib.rav_profile_enable(sm.h, 1)
+    cnt = ctypes_i64()
+    tot = ctypes_f64()
+    lib.rav_profile_read(sm.h, fine, cnt, tot)  # clear
+    launches0 = lib.rav_kernel_launches()
+    clk = clocks_start()
+    time.sleep(0.3)
+    barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+    e1.record(stream)
+    barrier()
+    ms = e0.elapsed_time(e1)
+    clocks = clocks_stop(clk, local)
+    launches = lib.rav_kernel_launches() - launches0
+    lib.rav_profile_read(sm.h, fine, cnt, tot)
+    lib.rav_profile_enable(sm.h, 0)
+    apply_ms = tot.value / max(cnt.value, 1)
+    if dist is not None:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = ws * n * args.steps / (ms / 1e3)
+
+    # ---- roofline of the dominant kernel: fine-level subdomain apply ----
+    rows_x_cols, owned = patch_work(W["dim"], W["N"])
+    esz = {0: 8, 1: 4, 2: 2, 3: 1}[W["prec"]]
+    flops = 2.0 * rows_x_cols
+    bytes_alg = rows_x_cols * esz + 8.0 * n + 16.0 * owned
+    if W["prec"] == 0:
+        roof = {"bound": "alu", "achieved": flops / (apply_ms / 1e3) / 1e12, "peak": FP64_PEAK_TFLOPS,
+                "unit": "TFLOP/s"}
+    else:
+        peak = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"] if os.path.exists(
+            os.path.join(ROOT, "MEASURED_PEAKS.json")) else 6800.0
+        roof = {"bound": "hbm", "achieved": bytes_alg / (apply_ms / 1e3) / 1e9, "peak": peak, "unit": "GB/s"}
+    roof["frac"] = roof["achieved"] / roof["peak"]
+    traffic = measured_traffic(f"rav_apply_{args.workload}")
+    roof["traffic"] = traffic
+    roof["kernel"] = "k_rav_apply (fine level)"
+    roof["launch_ms"] = apply_ms
+    roof["launches_timed"] = cnt.value
+    roof["algorithmic_bytes"] = bytes_alg
+    roof["algorithmic_flops"] = flops
+    roof["hbm_gbs_equiv"] = bytes_alg / (apply_ms / 1e3) / 1e9
+
+    out = {"metric": "V-cycle DoFs/s", "value": value, "unit": "DoF/s", "n_gpus": ws, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": W["desc"], "dofs": n, "levels": W["nlev"], "nu": [nu, nu],
+                      "smoother": "RAV", "inverse_storage": ["f64", "f32", "bf16", "fp8"][W["prec"]],
+                      "l2": "inputs larger than L2: each fine-level pass streams the operator "
+                            f"({mg.counts(fine)['nnz'] * 12 / 1e9:.2f} GB) and the patch inverse rows "
+                            f"({rows_x_cols * esz / 1e9:.2f} GB) > 129 MB L2",
+                      "parallelism": "replicas" if ws > 1 else "single GPU"},
+           "roofline": roof, "gpu_launches": int(launches), "clocks": clocks}
+
+    # ---- end to end through the public API with host buffers ----
+    if not args.no_e2e:
+        xh = x0.cpu().pin_memory()
+        bh = b.cpu().pin_memory()
+        xo = torch.empty_like(xh).pin_memory()
+        xd, bd = torch.empty_like(x), torch.empty_like(b)
+        K = max(10, args.steps // 10)
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(K):
+            xd.copy_(xh, non_blocking=True)
+            bd.copy_(bh, non_blocking=True)
+            mg.vcycle(sm, xd, bd, nu, nu)
+            xo.copy_(xd, non_blocking=True)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        out["e2e"] = {"value": ws * n * K / dt, "unit": "DoF/s", "h2d_bytes_per_step": 2 * n * 8,
+                      "d2h_bytes_per_step": n * 8, "steps": K}
+
+    # ---- time to a 1e-8 residual reduction (host-driven stationary solve) ----
+    if not args.no_tol:
+        xs = x0.clone()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        it, hist, rc = mg.solve(sm, xs, b, tol=1e-8, maxit=200, nu_pre=nu, nu_post=nu, raise_on_error=False)
+        dt = time.perf_counter() - t0
+        out["time_to_tol"] = {"seconds": dt, "cycles": it, "tol": 1e-8, "status": rc,
+                              "rho": float(hist[-1] ** (1.0 / max(it, 1)))}
+
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        v, dt, nn = cpu_baseline(W)
+        out["cpu_baseline"] = {"value": v, "unit": "DoF/s", "cores": 1, "kind": "oracle",
+                               "sample": "1 V(2,2) cycle of the full workload on one host core after untimed "
+                                         f"set-up ({dt:.2f} s)"}
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+
+
+def ctypes_i64():
+    import ctypes
+    return ctypes.c_int64(0)
+
+
+def ctypes_f64():
+    import ctypes
+    return ctypes.c_double(0.0)
+
+
+def main():
+    args = parse()
+    W = WORKLOADS[args.workload]
+    if args.impl == "reference":
+        run_reference(args, W)
+    else:
+        run_ours(args, W)
+
+
+if __name__ == "__main__":
+    main()

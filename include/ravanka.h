@@ -1,0 +1,225 @@
+/*
+ * ravanka.h -- C ABI of the GB300 restricted additive Vanka multigrid library.
+ *
+ * Method: Saberi, Meschke, Vogel, "A restricted additive Vanka smoother for
+ * geometric multigrid".  The library solves the Stokes saddle-point system
+ * L x = b, L = [A B; B^T 0] (Sec. 2, Eqs. 5-7 and 9) discretised with
+ * inf-sup-stable Q2-Q1 (Taylor-Hood) elements (C = 0, Sec. 2 after Eq. 7) on
+ * tensor-product box grids, by a geometric multigrid V-cycle (Sec. 2, Fig. 1)
+ * whose smoother is one of
+ *   RAV  restricted additive Vanka, Eq. 13 (the method of the paper),
+ *   AV   additive Vanka, Eq. 12,
+ *   MV   multiplicative Vanka, Eq. 11, run in a 4^d-coloured patch order,
+ * each applied as x <- x + S (b - L x) (Eq. 10).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  * Numbering (all DoFs, Dirichlet ones included, live in x):
+ *      Q2 node I in [0,2N]^d, node id = I0 + (2N+1)(I1 + (2N+1) I2),
+ *      velocity DoF = d*id + c (components interleaved per node),
+ *      pressure vertex v in [0,N]^d, id = v0 + (N+1)(v1 + (N+1) v2),
+ *      pressure DoF = n_u + id, n_u = d (2N+1)^d, n = n_u + (N+1)^d.
+ *  * Every boundary Q2 node is a Dirichlet node for all components.  Its row
+ *    of L is the identity row; the residual is defined as 0 there; the
+ *    Dirichlet value lives in x (no lifting).
+ *  * Level 0 is the coarsest, level n_levels-1 the finest (N cells per axis);
+ *    level l has N / 2^(n_levels-1-l) cells per axis.
+ *  * Pointers named *_dev are CUDA device pointers owned by the caller;
+ *    pointers named *_host are host pointers owned by the caller.  The
+ *    library never frees caller memory.  Library objects (matrices, patch
+ *    inverses, work vectors, the coarse inverse) are owned by the handle and
+ *    released by mg_destroy / vanka_destroy.
+ *  * stream is a cudaStream_t (NULL = legacy default stream).  Calls enqueue
+ *    work on it and return without synchronising, except where stated.
+ *  * Every call returns RAV_OK (0) or a negative RAV_ERR_* code; nothing
+ *    aborts and no device code traps.  rav_strerror() names a code.
+ */
+#ifndef RAVANKA_H
+#define RAVANKA_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct rav_mg rav_mg;             /* grid hierarchy + assembled operators */
+typedef struct rav_smoother rav_smoother; /* Vanka subdomains + stored inverses   */
+typedef void* rav_stream;                 /* cudaStream_t                         */
+
+enum {
+  RAV_OK = 0,
+  RAV_ERR_ARG = -1,             /* invalid argument or size                    */
+  RAV_ERR_CUDA = -2,            /* a CUDA runtime call failed                  */
+  RAV_ERR_SINGULAR_PATCH = -3,  /* a local system L_i could not be factorised  */
+  RAV_ERR_SINGULAR_COARSE = -4, /* the bordered coarse system is singular      */
+  RAV_ERR_NOT_CONVERGED = -5,   /* maxit reached before the tolerance          */
+  RAV_ERR_DIVERGED = -6,        /* residual grew beyond the divergence guard   */
+  RAV_ERR_NAN = -7,             /* non-finite residual                         */
+  RAV_ERR_TIMEOUT = -8          /* a bounded device wait gave up               */
+};
+
+enum rav_bc { RAV_BC_CAVITY = 0, RAV_BC_NOSLIP = 1, RAV_BC_QUADRATIC = 2 };
+enum rav_forcing { RAV_F_NONE = 0, RAV_F_PSI = 1, RAV_F_SINKER = 2, RAV_F_QUADRATIC = 3 };
+enum rav_smoother_kind { RAV_RAV = 0, RAV_AV = 1, RAV_MV_COLOURED = 3 };
+enum rav_precision { RAV_F64 = 0, RAV_F32 = 1, RAV_BF16 = 2, RAV_FP8 = 3 };
+
+/* Problem on the unit square (dim 2) or cube (dim 3).
+ *  coords_host: dim*(N+1) finest-level vertex coordinates, axis-major, strictly
+ *               increasing, or NULL for a uniform grid.  Coarser levels use
+ *               every 2nd, 4th, ... vertex.
+ *  viscosity:   eta(x) = eta0 * 10^(max_k s_k exp(-|x - c_k|^2 / (2 rho_k^2)))
+ *               with blobs_host = nblobs * (cx, cy, cz, rho, s); eta0 if nblobs = 0.
+ *  bc:          RAV_BC_CAVITY (u = e_0 on the face x_{d-1} = 1, edges and corners
+ *               of that face included, 0 elsewhere), RAV_BC_NOSLIP (u = 0),
+ *               RAV_BC_QUADRATIC (u = (y^2, x^2) in 2-D, (y^2, z^2, x^2) in 3-D). */
+typedef struct rav_problem {
+  int dim;
+  int N;
+  const double* coords_host;
+  double eta0;
+  int nblobs;
+  const double* blobs_host;
+  int bc;
+} rav_problem;
+
+/* Builds the hierarchy: per level the Q2-Q1 operator of Eq. 7 assembled from
+ * 3^d-point Gauss quadrature (the paper assembles on every grid, Sec. 4), the
+ * interpolation tables of the nested Q2/Q1 spaces, and on level 0 the explicit
+ * inverse of the bordered system [L e_p; e_p^T 0] for the LU coarse solve of
+ * Sec. 2.  Requires N divisible by 2^(n_levels-1) and a coarsest grid of at
+ * least 2 cells per axis.  Synchronises the stream before returning.
+ * Errors: RAV_ERR_ARG, RAV_ERR_CUDA, RAV_ERR_SINGULAR_COARSE. */
+int mg_setup(const rav_problem* p, int n_levels, rav_stream stream, rav_mg** out);
+void mg_destroy(rav_mg* mg);
+
+/* Sizes of level l: out[0] = n_u, out[1] = n_p, out[2] = n, out[3] = nnz of L,
+ * out[4] = N (cells per axis). */
+int rav_get_counts(const rav_mg* mg, int level, int64_t out[5]);
+
+/* Copies the CSR form of level l's operator into caller device buffers:
+ * rowptr_dev[n+1] (int64), col_dev[nnz] (int32, ascending per row),
+ * val_dev[nnz] (fp64).  Structural entries that cancel are kept. */
+int rav_get_csr(const rav_mg* mg, int level, int64_t* rowptr_dev, int32_t* col_dev, double* val_dev,
+                rav_stream stream);
+
+/* Finest-level right-hand side: b_u = int v . f over 3^d Gauss points of every
+ * cell, b_p = 0 (Eq. 6), b = Dirichlet value on Dirichlet rows.  forcing is one
+ * of rav_forcing (PSI: manufactured curl of sin^2(pi x) sin^2(pi y) with
+ * p = cos(pi x) cos(pi y); SINKER: f = (0,..,0,-max_k exp(-|x-c_k|^2/(2 rho_k^2)));
+ * QUADRATIC: the body force of the quadratic exact solution). b_dev has n entries. */
+int rav_assemble_rhs(rav_mg* mg, int forcing, double* b_dev, rav_stream stream);
+
+/* x_dev[n] = Dirichlet values on Dirichlet DoFs, 0 elsewhere (the initial guess). */
+int rav_initial_guess(rav_mg* mg, double* x_dev, rav_stream stream);
+
+/* r = b - L x on free rows, r = 0 on Dirichlet rows (the residual of Eq. 10), on
+ * level l; all three vectors have that level's n entries.  If norm_host is not
+ * NULL the call synchronises and stores ||r||_2 there. */
+int rav_residual(rav_mg* mg, int level, const double* x_dev, const double* b_dev, double* r_dev,
+                 double* norm_host, rav_stream stream);
+
+/* Grid transfers between level l-1 (coarse) and l (fine), canonical nested
+ * interpolation P of the Q2 velocity and Q1 pressure spaces (the paper builds
+ * its transfers from the grid hierarchy, Sec. 2):
+ *   rav_restrict:   bc = P^T rf, then 0 on coarse Dirichlet rows;
+ *   rav_prolong_add: xf += P xc on free fine DoFs (fine Dirichlet DoFs untouched). */
+int rav_restrict(rav_mg* mg, int level, const double* rf_dev, double* bc_dev, rav_stream stream);
+int rav_prolong_add(rav_mg* mg, int level, const double* xc_dev, double* xf_dev, rav_stream stream);
+
+/* Coarse solve on level 0 (Sec. 2, LU to machine accuracy): x = first n_0
+ * entries of [L e_p; e_p^T 0]^{-1} [b masked to free rows; 0]; the pressure of
+ * x has zero sum. */
+int rav_coarse_solve(rav_mg* mg, const double* b_dev, double* x_dev, rav_stream stream);
+
+/* Builds the Vanka subdomains of every level above the coarsest (Sec. 3):
+ * subdomain i = pressure DoF p_i plus every free velocity DoF of the cells
+ * around vertex i.  Factorises each local system L_i = R_i L R_i^T in fp64 and
+ * stores
+ *   RAV: the rows of L_i^{-1} of the DoFs owned by i (Sec. 4.3), ownership =
+ *        vertex floor(I/2) for a velocity DoF at Q2 node I, own vertex for p_i;
+ *   AV, MV: all rows of L_i^{-1}.
+ * precision selects the stored format of those rows (fp64, fp32, bf16, or fp8
+ * e4m3 with an fp32 scale per row); reduced formats are applied with fp32
+ * accumulation (RAV only).  omega is the damping of every subdomain (Eq. 11).
+ * Synchronises the stream.  Errors: RAV_ERR_ARG, RAV_ERR_CUDA,
+ * RAV_ERR_SINGULAR_PATCH. */
+int vanka_setup(rav_mg* mg, int kind, int precision, double omega, rav_stream stream, rav_smoother** out);
+void vanka_destroy(rav_smoother* sm);
+
+/* Replaces the damping of level l's subdomains by w_dev[n_p(l)] (fp32, device),
+ * e.g. the per-subdomain weights of a learned model. */
+int rav_set_patch_omega(rav_smoother* sm, int level, const float* w_dev, rav_stream stream);
+
+/* Subdomain structure of level l for inspection: counts_out[0] = number of
+ * subdomains, counts_out[1] = total DoFs over all subdomains. */
+int rav_get_patch_counts(const rav_smoother* sm, int level, int64_t counts_out[2]);
+/* offsets_dev[np+1], dofs_dev[total] (each list ascending), owner_dev[n]
+ * (owning subdomain per DoF, -1 for Dirichlet DoFs); int32, device. */
+int rav_get_patches(const rav_smoother* sm, int level, int32_t* offsets_dev, int32_t* dofs_dev,
+                    int32_t* owner_dev, rav_stream stream);
+/* Stored inverse rows of subdomains [first, first+count) of level l, expanded
+ * to fp64 (scale applied) in the sorted DoF order of each subdomain, into
+ * out_dev[count][rows_max][cols_max] (zero padded); rows_max/cols_max are
+ * 2^d d + 1 and 5^d d + 1 for RAV, 5^d d + 1 for both otherwise. */
+int rav_get_inverse_rows(const rav_smoother* sm, int level, int64_t first, int64_t count, double* out_dev,
+                         rav_stream stream);
+
+/* steps smoothing steps x <- x + S (b - L x) on level l (Eq. 10 with S from
+ * Eq. 13, 12 or 11).  x_dev, b_dev have n(l) entries. */
+int vanka_smooth(rav_smoother* sm, int level, double* x_dev, const double* b_dev, int steps, rav_stream stream);
+
+/* The subdomain part of one RAV or AV step on level l (Eq. 13 or 12 applied to a
+ * given residual): x += S r, with r_dev the residual of that level (zero on
+ * Dirichlet rows, e.g. from rav_residual).  vanka_smooth = rav_residual +
+ * vanka_apply.  RAV_ERR_ARG for MV, whose residual changes inside the sweep. */
+int vanka_apply(rav_smoother* sm, int level, const double* r_dev, double* x_dev, rav_stream stream);
+
+/* One V(nu_pre, nu_post) cycle on the finest level (Sec. 2, Fig. 1): smoothing,
+ * residual restriction, recursive coarse correction with x_c = 0, the coarse
+ * solve on level 0, prolongation, smoothing.  x_dev is updated in place. */
+int vcycle(rav_mg* mg, rav_smoother* sm, double* x_dev, const double* b_dev, int nu_pre, int nu_post,
+           rav_stream stream);
+
+typedef struct rav_solve_opts {
+  double tol;      /* stop when ||r_k||_2 / ||r_0||_2 <= tol (Sec. 4 uses 1e-8) */
+  int maxit;       /* V-cycles (stationary) or inner iterations (FGMRES)         */
+  int nu_pre, nu_post;
+  int outer;       /* 0 stationary multigrid, 1 FGMRES(restart) with one V-cycle as
+                      right preconditioner                                         */
+  int restart;     /* FGMRES restart length (30)                                */
+  double diverge;  /* stop with RAV_ERR_DIVERGED when the ratio exceeds this     */
+} rav_solve_opts;
+
+typedef struct rav_solve_info {
+  int iterations;         /* V-cycles or FGMRES inner iterations done           */
+  int status;             /* RAV_OK or the error returned                       */
+  double final_ratio;     /* ||r||/||r_0|| at exit                              */
+  double* history_host;   /* optional, maxit+1 entries: ratio after each step  */
+} rav_solve_info;
+
+/* Solves L x = b from the given x (usually rav_initial_guess).  Host-driven:
+ * synchronises once per V-cycle (stationary) or inner iteration (FGMRES) to
+ * read the residual norm.  info may be NULL. */
+int solve(rav_mg* mg, rav_smoother* sm, double* x_dev, const double* b_dev, const rav_solve_opts* opts,
+          rav_solve_info* info, rav_stream stream);
+
+/* Timing hook.  While enabled, every subdomain kernel launch of the smoother
+ * (vanka_apply, and the subdomain part of each smoothing step) is bracketed by
+ * a pair of CUDA events recorded on its launching stream.  rav_profile_read
+ * waits for the recorded events of level l and returns how many launches they
+ * bracket and their summed duration in ms, then forgets them. */
+int rav_profile_enable(rav_smoother* sm, int enable);
+int rav_profile_read(rav_smoother* sm, int level, int64_t* launches, double* total_ms);
+
+/* Number of kernels the solve path of this library (residuals, subdomain
+ * applies, transfers, coarse solves, Krylov vector updates) has launched in
+ * this process so far; set-up kernels are not counted. */
+int64_t rav_kernel_launches(void);
+
+const char* rav_strerror(int code);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* RAVANKA_H */

@@ -1,0 +1,186 @@
+"""GB300 restricted additive Vanka (RAV) multigrid for Q2-Q1 Stokes.
+
+Python binding of the C ABI in include/ravanka.h.  Every numerical step runs
+in the CUDA library (libravanka.so); this module only marshals torch device
+tensors (memory) and the current torch stream into the C calls.  There is no
+CPU path: without a CUDA device or the library, the calls raise.
+
+Method: Saberi, Meschke, Vogel, "A restricted additive Vanka smoother for
+geometric multigrid" (Sec. 3, Eq. 13).
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+
+from . import _capi
+from ._capi import RavError, check
+
+RAV, AV, MV_COLOURED = 0, 1, 3
+F64, F32, BF16, FP8 = 0, 1, 2, 3
+BC_CAVITY, BC_NOSLIP, BC_QUADRATIC = 0, 1, 2
+F_NONE, F_PSI, F_SINKER, F_QUADRATIC = 0, 1, 2, 3
+
+__all__ = ["Multigrid", "Smoother", "RavError", "RAV", "AV", "MV_COLOURED", "F64", "F32", "BF16", "FP8",
+           "BC_CAVITY", "BC_NOSLIP", "BC_QUADRATIC", "F_NONE", "F_PSI", "F_SINKER", "F_QUADRATIC"]
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _stream(stream=None):
+    torch = _torch()
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if not t.is_cuda or not t.is_contiguous():
+        raise ValueError("expected a contiguous CUDA tensor")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+class Multigrid:
+    """Grid hierarchy and assembled operators (mg_setup)."""
+
+    def __init__(self, dim, N, n_levels, coords=None, eta0=1.0, blobs=None, bc=BC_CAVITY, stream=None):
+        lib = _capi.load()
+        self._coords = None if coords is None else np.ascontiguousarray(coords, np.float64).reshape(-1)
+        self._blobs = np.zeros((0, 5)) if blobs is None else np.ascontiguousarray(blobs, np.float64).reshape(-1, 5)
+        prob = _capi.RavProblem(dim, N, None if self._coords is None else self._coords.ctypes.data, float(eta0),
+                                self._blobs.shape[0], self._blobs.ctypes.data if self._blobs.size else None, bc)
+        h = ctypes.c_void_p()
+        check(lib.mg_setup(ctypes.byref(prob), n_levels, _stream(stream), ctypes.byref(h)), "mg_setup")
+        self.h = h
+        self.dim, self.N, self.nlev = dim, N, n_levels
+
+    def __del__(self):
+        if getattr(self, "h", None) is not None and _capi._lib is not None:
+            _capi._lib.mg_destroy(self.h)
+            self.h = None
+
+    def counts(self, level):
+        out = (ctypes.c_int64 * 5)()
+        check(_capi.load().rav_get_counts(self.h, level, out), "rav_get_counts")
+        return dict(n_u=out[0], n_p=out[1], n=out[2], nnz=out[3], N=out[4])
+
+    def n(self, level=None):
+        return self.counts(self.nlev - 1 if level is None else level)["n"]
+
+    def csr(self, level, stream=None):
+        torch = _torch()
+        c = self.counts(level)
+        rp = torch.empty(c["n"] + 1, dtype=torch.int64, device="cuda")
+        ci = torch.empty(c["nnz"], dtype=torch.int32, device="cuda")
+        va = torch.empty(c["nnz"], dtype=torch.float64, device="cuda")
+        check(_capi.load().rav_get_csr(self.h, level, _ptr(rp), _ptr(ci), _ptr(va), _stream(stream)), "rav_get_csr")
+        return rp, ci, va
+
+    def vector(self, level=None):
+        return _torch().zeros(self.n(level), dtype=_torch().float64, device="cuda")
+
+    def rhs(self, forcing, out=None, stream=None):
+        b = self.vector() if out is None else out
+        check(_capi.load().rav_assemble_rhs(self.h, forcing, _ptr(b), _stream(stream)), "rav_assemble_rhs")
+        return b
+
+    def initial_guess(self, out=None, stream=None):
+        x = self.vector() if out is None else out
+        check(_capi.load().rav_initial_guess(self.h, _ptr(x), _stream(stream)), "rav_initial_guess")
+        return x
+
+    def residual(self, level, x, b, r=None, norm=False, stream=None):
+        r = _torch().empty_like(x) if r is None else r
+        nrm = ctypes.c_double(0.0)
+        check(_capi.load().rav_residual(self.h, level, _ptr(x), _ptr(b), _ptr(r),
+                                        ctypes.byref(nrm) if norm else None, _stream(stream)), "rav_residual")
+        return (r, nrm.value) if norm else r
+
+    def restrict(self, level, rf, out=None, stream=None):
+        bc = self.vector(level - 1) if out is None else out
+        check(_capi.load().rav_restrict(self.h, level, _ptr(rf), _ptr(bc), _stream(stream)), "rav_restrict")
+        return bc
+
+    def prolong_add(self, level, xc, xf, stream=None):
+        check(_capi.load().rav_prolong_add(self.h, level, _ptr(xc), _ptr(xf), _stream(stream)), "rav_prolong_add")
+        return xf
+
+    def coarse_solve(self, b, out=None, stream=None):
+        x = self.vector(0) if out is None else out
+        check(_capi.load().rav_coarse_solve(self.h, _ptr(b), _ptr(x), _stream(stream)), "rav_coarse_solve")
+        return x
+
+    def vcycle(self, sm, x, b, nu_pre=2, nu_post=2, stream=None):
+        check(_capi.load().vcycle(self.h, sm.h, _ptr(x), _ptr(b), nu_pre, nu_post, _stream(stream)), "vcycle")
+        return x
+
+    def solve(self, sm, x, b, tol=1e-8, maxit=100, nu_pre=2, nu_post=2, outer=0, restart=30, diverge=1e6,
+              stream=None, raise_on_error=True):
+        """Returns (iterations, history ||r_k||/||r_0||, status)."""
+        opts = _capi.RavSolveOpts(tol, maxit, nu_pre, nu_post, outer, restart, diverge)
+        hist = np.zeros(maxit + 1)
+        info = _capi.RavSolveInfo(0, 0, 0.0, hist.ctypes.data)
+        rc = _capi.load().solve(self.h, sm.h, _ptr(x), _ptr(b), ctypes.byref(opts), ctypes.byref(info),
+                                _stream(stream))
+        if raise_on_error and rc != 0:
+            raise RavError(rc, "solve")
+        return info.iterations, hist[: info.iterations + 1].copy(), rc
+
+
+class Smoother:
+    """Vanka subdomains and stored inverses (vanka_setup)."""
+
+    def __init__(self, mg: Multigrid, kind=RAV, precision=F64, omega=0.5, stream=None):
+        h = ctypes.c_void_p()
+        check(_capi.load().vanka_setup(mg.h, kind, precision, float(omega), _stream(stream), ctypes.byref(h)),
+              "vanka_setup")
+        self.h = h
+        self.mg, self.kind, self.precision = mg, kind, precision
+
+    def __del__(self):
+        if getattr(self, "h", None) is not None and _capi._lib is not None:
+            _capi._lib.vanka_destroy(self.h)
+            self.h = None
+
+    def smooth(self, level, x, b, steps=1, stream=None):
+        check(_capi.load().vanka_smooth(self.h, level, _ptr(x), _ptr(b), steps, _stream(stream)), "vanka_smooth")
+        return x
+
+    def apply(self, level, r, x, stream=None):
+        """x += S r (the subdomain part of one RAV/AV step for a given residual r)."""
+        check(_capi.load().vanka_apply(self.h, level, _ptr(r), _ptr(x), _stream(stream)), "vanka_apply")
+        return x
+
+    def set_omega(self, level, w, stream=None):
+        w = w.to(dtype=_torch().float32).contiguous()
+        check(_capi.load().rav_set_patch_omega(self.h, level, _ptr(w), _stream(stream)), "rav_set_patch_omega")
+
+    def patch_counts(self, level):
+        out = (ctypes.c_int64 * 2)()
+        check(_capi.load().rav_get_patch_counts(self.h, level, out), "rav_get_patch_counts")
+        return out[0], out[1]
+
+    def patches(self, level, stream=None):
+        torch = _torch()
+        np_, tot = self.patch_counts(level)
+        n = self.mg.n(level)
+        off = torch.empty(np_ + 1, dtype=torch.int32, device="cuda")
+        dofs = torch.empty(tot, dtype=torch.int32, device="cuda")
+        own = torch.empty(n, dtype=torch.int32, device="cuda")
+        check(_capi.load().rav_get_patches(self.h, level, _ptr(off), _ptr(dofs), _ptr(own), _stream(stream)),
+              "rav_get_patches")
+        return off, dofs, own
+
+    def inverse_rows(self, level, first, count, stream=None):
+        d = self.mg.dim
+        nc = 5 ** d * d + 1
+        nr = (2 ** d * d + 1) if self.kind == RAV else nc
+        out = _torch().empty((count, nr, nc), dtype=_torch().float64, device="cuda")
+        check(_capi.load().rav_get_inverse_rows(self.h, level, first, count, _ptr(out), _stream(stream)),
+              "rav_get_inverse_rows")
+        return out

@@ -1,0 +1,202 @@
+// Internal declarations shared by the translation units of libravanka.
+// Q2-Q1 Stokes on tensor box grids; numbering and conventions as in ravanka.h.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <vector>
+
+#include "../../include/ravanka.h"
+
+#define RAV_TRY(call)                           \
+  do {                                          \
+    int rc_ = (call);                           \
+    if (rc_ != RAV_OK) return rc_;              \
+  } while (0)
+
+#define RAV_CUDA(call)                          \
+  do {                                          \
+    cudaError_t e_ = (call);                    \
+    if (e_ != cudaSuccess) {                    \
+      rav::note_cuda_error(e_);                 \
+      return RAV_ERR_CUDA;                      \
+    }                                           \
+  } while (0)
+
+namespace rav {
+
+void note_cuda_error(cudaError_t e);
+inline cudaStream_t S(rav_stream s) { return reinterpret_cast<cudaStream_t>(s); }
+
+constexpr int kMaxLevels = 16;
+
+// Geometry of one level, passed by value to kernels.
+struct Geo {
+  int dim;
+  int N;
+  int64_t M;      // Q2 nodes per axis, 2N + 1
+  int64_t nnode;  // M^dim
+  int64_t n_u, n_p, n;
+  const double* xv[3];  // device vertex coordinates per axis (N + 1)
+};
+
+// Per-axis interpolation tables from level l-1 into level l.  For fine Q2 node
+// index I on an axis: coarse cell k2[I] and the values of the three quadratic
+// Lagrange functions of that cell at the node (w2[3I..3I+2]); for fine vertex
+// v: coarse cell k1[v] and the two linear Lagrange values (w1[2v..2v+1]).
+struct XferTab {
+  const int* k2[3];
+  const double* w2[3];
+  const int* k1[3];
+  const double* w1[3];
+};
+
+struct Level {
+  Geo g;
+  double* xv_dev[3] = {nullptr, nullptr, nullptr};
+  std::vector<double> xv_host[3];
+  int64_t nnz = 0;
+  int64_t* rp = nullptr;   // CSR row pointer (n + 1)
+  int32_t* ci = nullptr;   // CSR columns, ascending per row
+  double* va = nullptr;    // CSR values
+  double* x = nullptr;     // level work vectors (coarse levels' iterate and rhs)
+  double* b = nullptr;
+  double* r = nullptr;     // residual
+  // interpolation tables into this level (unused on level 0)
+  int* k2[3] = {nullptr, nullptr, nullptr};
+  double* w2[3] = {nullptr, nullptr, nullptr};
+  int* k1[3] = {nullptr, nullptr, nullptr};
+  double* w1[3] = {nullptr, nullptr, nullptr};
+  XferTab tab() const {
+    XferTab t;
+    for (int a = 0; a < 3; ++a) { t.k2[a] = k2[a]; t.w2[a] = w2[a]; t.k1[a] = k1[a]; t.w1[a] = w1[a]; }
+    return t;
+  }
+};
+
+}  // namespace rav
+
+struct rav_mg {
+  int dim = 2, N = 0, nlev = 0;
+  double eta0 = 1.0;
+  int bc = 0;
+  std::vector<double> blobs;   // host copy
+  double* blobs_dev = nullptr;
+  int nblobs = 0;
+  rav::Level lev[rav::kMaxLevels];
+  double* cinv = nullptr;      // (n0 + 1)^2 row-major inverse of the bordered coarse system
+  double* norm_part = nullptr; // partial sums for norms and dot products
+  double* scalar_dev = nullptr;
+  double* scalar_host = nullptr;  // pinned
+  int part_cap = 0;
+};
+
+// Smoother data of one level: stored inverse rows and damping per subdomain.
+struct SmLevel {
+  int64_t np = 0, units = 0;
+  void* inv = nullptr;       // RAV: packed owned rows; AV/MV: full inverses (fp64, column-major)
+  float* scale = nullptr;    // fp8 row scales
+  double* omega = nullptr;   // damping per subdomain
+  double* corr = nullptr;    // AV corrections, n_p x n_box
+};
+
+struct rav_smoother {
+  rav_mg* mg = nullptr;
+  int kind = RAV_RAV, prec = RAV_F64;
+  double omega = 0.5;
+  SmLevel lev[rav::kMaxLevels];
+  // timing hook: event pairs around each subdomain kernel, per level
+  bool prof = false;
+  std::vector<cudaEvent_t> ev_free;
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_used[rav::kMaxLevels];
+};
+
+namespace rav {
+// Process-wide count of the kernels the solve path (residual, subdomain
+// apply, transfers, coarse solve, vector updates) has launched.
+void note_launch(int k = 1);
+}
+
+// ---- device helpers -------------------------------------------------------
+namespace rav {
+
+__host__ __device__ inline int64_t ipow(int64_t b, int e) {
+  int64_t r = 1;
+  for (int i = 0; i < e; ++i) r *= b;
+  return r;
+}
+
+// Q2 node tuple of velocity DoF i (i < n_u) and its component.
+__device__ inline void vel_node(const Geo& g, int64_t i, int64_t* I, int& c) {
+  int64_t id = i / g.dim;
+  c = (int)(i - id * g.dim);
+  for (int a = 0; a < g.dim; ++a) { I[a] = id % g.M; id /= g.M; }
+}
+__device__ inline bool node_on_boundary(const Geo& g, const int64_t* I) {
+  bool b = false;
+  for (int a = 0; a < g.dim; ++a) b |= (I[a] == 0) | (I[a] == 2 * g.N);
+  return b;
+}
+__device__ inline bool is_dirichlet(const Geo& g, int64_t i) {
+  if (i >= g.n_u) return false;
+  int64_t I[3];
+  int c;
+  vel_node(g, i, I, c);
+  return node_on_boundary(g, I);
+}
+__device__ inline int64_t node_id(const Geo& g, const int64_t* I) {
+  int64_t id = 0;
+  for (int a = g.dim - 1; a >= 0; --a) id = id * g.M + I[a];
+  return id;
+}
+__device__ inline int64_t vert_id(const Geo& g, const int64_t* v) {
+  int64_t id = 0;
+  for (int a = g.dim - 1; a >= 0; --a) id = id * (g.N + 1) + v[a];
+  return id;
+}
+__device__ inline double node_coord(const Geo& g, int a, int64_t I) {
+  return (I & 1) ? 0.5 * (g.xv[a][(I - 1) >> 1] + g.xv[a][(I + 1) >> 1]) : g.xv[a][I >> 1];
+}
+
+// Block-wide sum of one double per thread (blockDim.x a multiple of 32, <= 1024).
+__device__ inline double block_sum(double v) {
+  __shared__ double wsum[32];
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  __syncthreads();
+  if (l == 0) wsum[w] = v;
+  __syncthreads();
+  v = 0.0;
+  if (w == 0) {
+    const int nw = blockDim.x >> 5;
+    v = l < nw ? wsum[l] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  }
+  return v;
+}
+
+inline int grid_for(int64_t n, int threads, int cap = 152 * 64) {
+  int64_t b = (n + threads - 1) / threads;
+  if (b > cap) b = cap;
+  if (b < 1) b = 1;
+  return (int)b;
+}
+
+// Shared host routines (defined in cycle.cu).
+int residual_impl(rav_mg* mg, int level, const double* x, const double* b, double* r, double* norm2_dev,
+                  cudaStream_t s);
+int restrict_impl(rav_mg* mg, int level, const double* rf, double* bc, cudaStream_t s);
+int prolong_impl(rav_mg* mg, int level, const double* xc, double* xf, cudaStream_t s);
+int coarse_impl(rav_mg* mg, const double* b, double* x, cudaStream_t s);
+// Deterministic sum of squares / dot product into *out_dev (two kernels).
+int dot_impl(rav_mg* mg, const double* a, const double* b, int64_t n, double* out_dev, cudaStream_t s);
+
+}  // namespace rav
+
+// Smoother entry used by the cycle (defined in smoother.cu) and the V-cycle (cycle.cu).
+int rav_smooth_impl(rav_smoother* sm, int level, double* x, const double* b, int steps, cudaStream_t s);
+namespace rav {
+int vcycle_impl(rav_mg* mg, rav_smoother* sm, double* x, const double* b, int nu1, int nu2, bool x_is_zero,
+                cudaStream_t s);
+}

@@ -1,0 +1,509 @@
+// Residual (Eq. 10), grid transfers, coarse solve, V-cycle (Sec. 2, Fig. 1)
+// and the outer iterations (stationary multigrid and FGMRES, Sec. 4).
+#include <cmath>
+#include <vector>
+
+#include "common.cuh"
+
+namespace rav {
+
+// ---------------------------------------------------------------------------
+// r = b - L x on free rows, 0 on Dirichlet rows (the identity rows, the only
+// rows of L with a single entry).  G lanes per row; optional per-block partial
+// sums of r^2 into part[blockIdx.x].
+template <int G>
+__global__ void __launch_bounds__(256) k_residual(int64_t n, const int64_t* __restrict__ rp,
+                                                  const int32_t* __restrict__ ci, const double* __restrict__ va,
+                                                  const double* __restrict__ x, const double* __restrict__ b,
+                                                  double* __restrict__ r, double* __restrict__ part) {
+  const int lane = threadIdx.x & (G - 1);
+  const int64_t rows_per_block = blockDim.x / G;
+  double acc2 = 0.0;
+  // the loop bound is block-uniform so every lane reaches the shuffles
+  for (int64_t base = blockIdx.x * rows_per_block; base < n; base += (int64_t)gridDim.x * rows_per_block) {
+    const int64_t row = base + threadIdx.x / G;
+    double t = 0.0;
+    int64_t s = 0, e = 0;
+    if (row < n) {
+      s = rp[row];
+      e = rp[row + 1];
+      for (int64_t k = s + lane; k < e; k += G) t += va[k] * x[ci[k]];
+    }
+#pragma unroll
+    for (int o = G / 2; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o, G);
+    if (lane == 0 && row < n) {
+      const double v = (e - s == 1) ? 0.0 : b[row] - t;
+      r[row] = v;
+      acc2 += v * v;
+    }
+  }
+  if (part) {
+    const double bs = block_sum(acc2);
+    if (threadIdx.x == 0) part[blockIdx.x] = bs;
+  }
+}
+
+__global__ void k_sum_parts(const double* __restrict__ part, int np, double* __restrict__ out, int take_sqrt) {
+  double v = 0.0;
+  for (int i = threadIdx.x; i < np; i += blockDim.x) v += part[i];
+  v = block_sum(v);
+  if (threadIdx.x == 0) *out = take_sqrt ? sqrt(v) : v;
+}
+
+__global__ void k_dot_parts(const double* __restrict__ a, const double* __restrict__ b, int64_t n,
+                            double* __restrict__ part) {
+  double v = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    v += a[i] * b[i];
+  v = block_sum(v);
+  if (threadIdx.x == 0) part[blockIdx.x] = v;
+}
+
+// ---------------------------------------------------------------------------
+// Transfers with the per-axis tables (see common.cuh, XferTab).
+template <int D>
+__global__ void k_prolong(Geo gf, Geo gc, XferTab T, const double* __restrict__ xc, double* __restrict__ xf) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t < gf.nnode) {
+    int64_t I[3] = {0, 0, 0}, id = t;
+    for (int a = 0; a < D; ++a) { I[a] = id % gf.M; id /= gf.M; }
+    if (node_on_boundary(gf, I)) return;
+    int k[3] = {0, 0, 0};
+    double w[3][3];
+    for (int a = 0; a < D; ++a) {
+      k[a] = T.k2[a][I[a]];
+      for (int j = 0; j < 3; ++j) w[a][j] = T.w2[a][3 * I[a] + j];
+    }
+    double acc[3] = {0, 0, 0};
+    for (int t2 = 0; t2 < (D == 3 ? 3 : 1); ++t2)
+      for (int t1 = 0; t1 < 3; ++t1)
+        for (int t0 = 0; t0 < 3; ++t0) {
+          double ww = w[0][t0] * w[1][t1];
+          int64_t K[3] = {2 * k[0] + t0, 2 * k[1] + t1, 0};
+          if (D == 3) { ww *= w[2][t2]; K[2] = 2 * k[2] + t2; }
+          if (ww == 0.0) continue;
+          const int64_t base = D * node_id(gc, K);
+          for (int c = 0; c < D; ++c) acc[c] += ww * xc[base + c];
+        }
+    for (int c = 0; c < D; ++c) xf[D * t + c] += acc[c];
+  } else if (t < gf.nnode + gf.n_p) {
+    int64_t v = t - gf.nnode, vv[3] = {0, 0, 0};
+    for (int a = 0; a < D; ++a) { vv[a] = v % (gf.N + 1); v /= (gf.N + 1); }
+    int k[3] = {0, 0, 0};
+    double w[3][2];
+    for (int a = 0; a < D; ++a) {
+      k[a] = T.k1[a][vv[a]];
+      w[a][0] = T.w1[a][2 * vv[a]];
+      w[a][1] = T.w1[a][2 * vv[a] + 1];
+    }
+    double acc = 0.0;
+    for (int t2 = 0; t2 < (D == 3 ? 2 : 1); ++t2)
+      for (int t1 = 0; t1 < 2; ++t1)
+        for (int t0 = 0; t0 < 2; ++t0) {
+          double ww = w[0][t0] * w[1][t1];
+          int64_t K[3] = {k[0] + t0, k[1] + t1, 0};
+          if (D == 3) { ww *= w[2][t2]; K[2] = k[2] + t2; }
+          if (ww == 0.0) continue;
+          acc += ww * xc[gc.n_u + vert_id(gc, K)];
+        }
+    xf[gf.n_u + (t - gf.nnode)] += acc;
+  }
+}
+
+// bc = P^T rf (gather over the fine nodes whose interpolation uses the coarse
+// node), 0 on coarse Dirichlet rows.
+template <int D>
+__global__ void k_restrict(Geo gf, Geo gc, XferTab T, const double* __restrict__ rf, double* __restrict__ bc) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t < gc.nnode) {
+    int64_t K[3] = {0, 0, 0}, id = t;
+    for (int a = 0; a < D; ++a) { K[a] = id % gc.M; id /= gc.M; }
+    if (node_on_boundary(gc, K)) {
+      for (int c = 0; c < D; ++c) bc[D * t + c] = 0.0;
+      return;
+    }
+    // per axis: candidate fine nodes [2K-4, 2K+4] with their weights
+    int64_t Ilo[3] = {0, 0, 0};
+    double w[3][9];
+    int cnt[3] = {1, 1, 1};
+    for (int a = 0; a < D; ++a) {
+      Ilo[a] = 2 * K[a] - 4;
+      cnt[a] = 9;
+      for (int j = 0; j < 9; ++j) {
+        const int64_t I = Ilo[a] + j;
+        double ww = 0.0;
+        if (I >= 0 && I <= 2 * gf.N) {
+          const int64_t loc = K[a] - 2 * (int64_t)T.k2[a][I];
+          if (loc >= 0 && loc <= 2) ww = T.w2[a][3 * I + loc];
+        }
+        w[a][j] = ww;
+      }
+    }
+    double acc[3] = {0, 0, 0};
+    for (int j2 = 0; j2 < (D == 3 ? 9 : 1); ++j2)
+      for (int j1 = 0; j1 < 9; ++j1)
+        for (int j0 = 0; j0 < 9; ++j0) {
+          double ww = w[0][j0] * w[1][j1];
+          int64_t I[3] = {Ilo[0] + j0, Ilo[1] + j1, 0};
+          if (D == 3) { ww *= w[2][j2]; I[2] = Ilo[2] + j2; }
+          if (ww == 0.0) continue;
+          if (node_on_boundary(gf, I)) continue;
+          const int64_t base = D * node_id(gf, I);
+          for (int c = 0; c < D; ++c) acc[c] += ww * rf[base + c];
+        }
+    for (int c = 0; c < D; ++c) bc[D * t + c] = acc[c];
+  } else if (t < gc.nnode + gc.n_p) {
+    int64_t v = t - gc.nnode, K[3] = {0, 0, 0};
+    for (int a = 0; a < D; ++a) { K[a] = v % (gc.N + 1); v /= (gc.N + 1); }
+    int64_t Vlo[3] = {0, 0, 0};
+    double w[3][5];
+    for (int a = 0; a < D; ++a) {
+      Vlo[a] = 2 * K[a] - 2;
+      for (int j = 0; j < 5; ++j) {
+        const int64_t V = Vlo[a] + j;
+        double ww = 0.0;
+        if (V >= 0 && V <= gf.N) {
+          const int64_t loc = K[a] - (int64_t)T.k1[a][V];
+          if (loc >= 0 && loc <= 1) ww = T.w1[a][2 * V + loc];
+        }
+        w[a][j] = ww;
+      }
+    }
+    double acc = 0.0;
+    for (int j2 = 0; j2 < (D == 3 ? 5 : 1); ++j2)
+      for (int j1 = 0; j1 < 5; ++j1)
+        for (int j0 = 0; j0 < 5; ++j0) {
+          double ww = w[0][j0] * w[1][j1];
+          int64_t V[3] = {Vlo[0] + j0, Vlo[1] + j1, 0};
+          if (D == 3) { ww *= w[2][j2]; V[2] = Vlo[2] + j2; }
+          if (ww == 0.0) continue;
+          acc += ww * rf[gf.n_u + vert_id(gf, V)];
+        }
+    bc[gc.n_u + (t - gc.nnode)] = acc;
+  }
+}
+
+// Coarse solve x = C[:, :n] (b masked to free rows): one warp per row.
+__global__ void k_mask_free(Geo g, const double* __restrict__ b, double* __restrict__ bm) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < g.n) bm[i] = is_dirichlet(g, i) ? 0.0 : b[i];
+}
+__global__ void k_coarse_gemv(int64_t n, const double* __restrict__ C, const double* __restrict__ bm,
+                              double* __restrict__ x, int accumulate) {
+  const int64_t m = n + 1;
+  const int lane = threadIdx.x & 31;
+  const int64_t row = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (row >= n) return;
+  double s = 0.0;
+  for (int64_t j = lane; j < n; j += 32) s += C[row * m + j] * bm[j];
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if (lane == 0) x[row] = accumulate ? x[row] + s : s;
+}
+
+__global__ void k_axpy(int64_t n, double a, const double* __restrict__ xv, double* __restrict__ y) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    y[i] += a * xv[i];
+}
+__global__ void k_scale_copy(int64_t n, double a, const double* __restrict__ xv, double* __restrict__ y) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    y[i] = a * xv[i];
+}
+// y = a * x scaled by the device scalar 1/(*den)
+__global__ void k_scale_by_inv(int64_t n, const double* __restrict__ den, const double* __restrict__ xv,
+                               double* __restrict__ y) {
+  const double s = *den > 0.0 ? 1.0 / *den : 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    y[i] = s * xv[i];
+}
+// y -= (*h) x  (Gram-Schmidt step with a device coefficient)
+__global__ void k_axpy_dev(int64_t n, const double* __restrict__ h, const double* __restrict__ xv,
+                           double* __restrict__ y) {
+  const double a = -*h;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    y[i] += a * xv[i];
+}
+
+// ---------------------------------------------------------------------------
+int residual_impl(rav_mg* mg, int level, const double* x, const double* b, double* r, double* norm2_dev,
+                  cudaStream_t s) {
+  const Level& L = mg->lev[level];
+  const int64_t n = L.g.n;
+  const int G = L.g.dim == 2 ? 8 : 16;
+  const int rpb = 256 / G;
+  int blocks = (int)std::min<int64_t>((n + rpb - 1) / rpb, (int64_t)mg->part_cap);
+  double* part = norm2_dev ? mg->norm_part : nullptr;
+  if (G == 8) k_residual<8><<<blocks, 256, 0, s>>>(n, L.rp, L.ci, L.va, x, b, r, part);
+  else k_residual<16><<<blocks, 256, 0, s>>>(n, L.rp, L.ci, L.va, x, b, r, part);
+  if (norm2_dev) k_sum_parts<<<1, 256, 0, s>>>(mg->norm_part, blocks, norm2_dev, 1);
+  note_launch(norm2_dev ? 2 : 1);
+  RAV_CUDA(cudaGetLastError());
+  return RAV_OK;
+}
+
+int dot_impl(rav_mg* mg, const double* a, const double* b, int64_t n, double* out_dev, cudaStream_t s) {
+  const int blocks = (int)std::min<int64_t>((n + 255) / 256, (int64_t)mg->part_cap);
+  k_dot_parts<<<blocks, 256, 0, s>>>(a, b, n, mg->norm_part);
+  k_sum_parts<<<1, 256, 0, s>>>(mg->norm_part, blocks, out_dev, 0);
+  note_launch(2);
+  RAV_CUDA(cudaGetLastError());
+  return RAV_OK;
+}
+
+int restrict_impl(rav_mg* mg, int level, const double* rf, double* bc, cudaStream_t s) {
+  const Level &F = mg->lev[level], &C = mg->lev[level - 1];
+  const int64_t tot = C.g.nnode + C.g.n_p;
+  const int blocks = (int)((tot + 127) / 128);
+  if (F.g.dim == 2) k_restrict<2><<<blocks, 128, 0, s>>>(F.g, C.g, F.tab(), rf, bc);
+  else k_restrict<3><<<blocks, 128, 0, s>>>(F.g, C.g, F.tab(), rf, bc);
+  note_launch();
+  RAV_CUDA(cudaGetLastError());
+  return RAV_OK;
+}
+
+int prolong_impl(rav_mg* mg, int level, const double* xc, double* xf, cudaStream_t s) {
+  const Level &F = mg->lev[level], &C = mg->lev[level - 1];
+  const int64_t tot = F.g.nnode + F.g.n_p;
+  const int blocks = (int)((tot + 127) / 128);
+  if (F.g.dim == 2) k_prolong<2><<<blocks, 128, 0, s>>>(F.g, C.g, F.tab(), xc, xf);
+  else k_prolong<3><<<blocks, 128, 0, s>>>(F.g, C.g, F.tab(), xc, xf);
+  note_launch();
+  RAV_CUDA(cudaGetLastError());
+  return RAV_OK;
+}
+
+// x = C b (overwrite) or x += C b, with b masked to free rows.
+static int coarse_apply(rav_mg* mg, const double* b, double* x, int accumulate, cudaStream_t s) {
+  Level& L = mg->lev[0];
+  const int64_t n = L.g.n;
+  double* bm = L.b == b ? L.r : L.b;  // masked copy in whichever work vector is not the input
+  if (bm == b) return RAV_ERR_ARG;
+  k_mask_free<<<(int)((n + 255) / 256), 256, 0, s>>>(L.g, b, bm);
+  k_coarse_gemv<<<(int)((n + 7) / 8), 256, 0, s>>>(n, mg->cinv, bm, x, accumulate);
+  note_launch(2);
+  RAV_CUDA(cudaGetLastError());
+  return RAV_OK;
+}
+
+int coarse_impl(rav_mg* mg, const double* b, double* x, cudaStream_t s) { return coarse_apply(mg, b, x, 0, s); }
+
+// V(nu1, nu2) on level l with iterate x and right-hand side b.  When
+// x_is_zero the first residual equals b and the coarse correction simply
+// overwrites x.
+static int vcycle_rec(rav_mg* mg, rav_smoother* sm, int l, double* x, const double* b, int nu1, int nu2,
+                      bool x_is_zero, cudaStream_t s) {
+  Level& L = mg->lev[l];
+  if (l == 0) {
+    if (x_is_zero) return coarse_apply(mg, b, x, 0, s);
+    RAV_TRY(residual_impl(mg, 0, x, b, L.r, nullptr, s));
+    // masked copy of r goes to L.b; L.r is the input here
+    k_mask_free<<<(int)((L.g.n + 255) / 256), 256, 0, s>>>(L.g, L.r, L.b);
+    k_coarse_gemv<<<(int)((L.g.n + 7) / 8), 256, 0, s>>>(L.g.n, mg->cinv, L.b, x, 1);
+    note_launch(2);
+    RAV_CUDA(cudaGetLastError());
+    return RAV_OK;
+  }
+  RAV_TRY(rav_smooth_impl(sm, l, x, b, nu1, s));
+  Level& C = mg->lev[l - 1];
+  RAV_TRY(residual_impl(mg, l, x, b, L.r, nullptr, s));
+  RAV_TRY(restrict_impl(mg, l, L.r, C.b, s));
+  RAV_CUDA(cudaMemsetAsync(C.x, 0, sizeof(double) * C.g.n, s));
+  RAV_TRY(vcycle_rec(mg, sm, l - 1, C.x, C.b, nu1, nu2, true, s));
+  RAV_TRY(prolong_impl(mg, l, C.x, x, s));
+  RAV_TRY(rav_smooth_impl(sm, l, x, b, nu2, s));
+  return RAV_OK;
+}
+
+int vcycle_impl(rav_mg* mg, rav_smoother* sm, double* x, const double* b, int nu1, int nu2, bool x_is_zero,
+                cudaStream_t s) {
+  return vcycle_rec(mg, sm, mg->nlev - 1, x, b, nu1, nu2, x_is_zero, s);
+}
+
+static int read_scalar(rav_mg* mg, const double* dev, double* host, cudaStream_t s) {
+  RAV_CUDA(cudaMemcpyAsync(mg->scalar_host, dev, sizeof(double), cudaMemcpyDeviceToHost, s));
+  RAV_CUDA(cudaStreamSynchronize(s));
+  *host = mg->scalar_host[0];
+  return RAV_OK;
+}
+
+}  // namespace rav
+
+using namespace rav;
+
+extern "C" int rav_residual(rav_mg* mg, int level, const double* x, const double* b, double* r, double* norm_host,
+                            rav_stream stream) {
+  if (!mg || !x || !b || !r || level < 0 || level >= mg->nlev) return RAV_ERR_ARG;
+  cudaStream_t s = S(stream);
+  RAV_TRY(residual_impl(mg, level, x, b, r, norm_host ? mg->scalar_dev : nullptr, s));
+  if (norm_host) RAV_TRY(read_scalar(mg, mg->scalar_dev, norm_host, s));
+  return RAV_OK;
+}
+
+extern "C" int rav_restrict(rav_mg* mg, int level, const double* rf, double* bc, rav_stream stream) {
+  if (!mg || !rf || !bc || level < 1 || level >= mg->nlev) return RAV_ERR_ARG;
+  return restrict_impl(mg, level, rf, bc, S(stream));
+}
+
+extern "C" int rav_prolong_add(rav_mg* mg, int level, const double* xc, double* xf, rav_stream stream) {
+  if (!mg || !xc || !xf || level < 1 || level >= mg->nlev) return RAV_ERR_ARG;
+  return prolong_impl(mg, level, xc, xf, S(stream));
+}
+
+extern "C" int rav_coarse_solve(rav_mg* mg, const double* b, double* x, rav_stream stream) {
+  if (!mg || !b || !x) return RAV_ERR_ARG;
+  Level& L = mg->lev[0];
+  if (b == L.r || b == L.b) return RAV_ERR_ARG;
+  return coarse_impl(mg, b, x, S(stream));
+}
+
+extern "C" int vcycle(rav_mg* mg, rav_smoother* sm, double* x, const double* b, int nu1, int nu2,
+                      rav_stream stream) {
+  if (!mg || !sm || sm->mg != mg || !x || !b || nu1 < 0 || nu2 < 0) return RAV_ERR_ARG;
+  return vcycle_impl(mg, sm, x, b, nu1, nu2, false, S(stream));
+}
+
+// ---------------------------------------------------------------------------
+static int solve_stationary(rav_mg* mg, rav_smoother* sm, double* x, const double* b, const rav_solve_opts& o,
+                            rav_solve_info* info, cudaStream_t s) {
+  Level& L = mg->lev[mg->nlev - 1];
+  double r0 = 0.0, rk = 0.0;
+  RAV_TRY(residual_impl(mg, mg->nlev - 1, x, b, L.r, mg->scalar_dev, s));
+  RAV_TRY(read_scalar(mg, mg->scalar_dev, &r0, s));
+  if (info && info->history_host) info->history_host[0] = 1.0;
+  if (r0 == 0.0) {
+    if (info) { info->iterations = 0; info->final_ratio = 0.0; info->status = RAV_OK; }
+    return RAV_OK;
+  }
+  int rc = RAV_ERR_NOT_CONVERGED, k = 0;
+  double ratio = 1.0;
+  for (k = 1; k <= o.maxit; ++k) {
+    RAV_TRY(vcycle_impl(mg, sm, x, b, o.nu_pre, o.nu_post, false, s));
+    RAV_TRY(residual_impl(mg, mg->nlev - 1, x, b, L.r, mg->scalar_dev, s));
+    RAV_TRY(read_scalar(mg, mg->scalar_dev, &rk, s));
+    ratio = rk / r0;
+    if (info && info->history_host) info->history_host[k] = ratio;
+    if (!std::isfinite(ratio)) { rc = RAV_ERR_NAN; break; }
+    if (ratio <= o.tol) { rc = RAV_OK; break; }
+    if (o.diverge > 0 && ratio > o.diverge) { rc = RAV_ERR_DIVERGED; break; }
+  }
+  if (info) {
+    info->iterations = k > o.maxit ? o.maxit : k;
+    info->final_ratio = ratio;
+    info->status = rc;
+  }
+  return rc;
+}
+
+// FGMRES(m), right-preconditioned by one V-cycle from a zero guess, modified
+// Gram-Schmidt with device dot products, Givens rotations on the host.
+static int solve_fgmres(rav_mg* mg, rav_smoother* sm, double* x, const double* b, const rav_solve_opts& o,
+                        rav_solve_info* info, cudaStream_t s) {
+  const int fine = mg->nlev - 1;
+  Level& L = mg->lev[fine];
+  const int64_t n = L.g.n;
+  const int m = o.restart > 0 ? o.restart : 30;
+  double *V = nullptr, *Z = nullptr, *w = nullptr, *zero = nullptr, *hdev = nullptr;
+  RAV_CUDA(cudaMallocAsync(&V, sizeof(double) * n * (m + 1), s));
+  RAV_CUDA(cudaMallocAsync(&Z, sizeof(double) * n * m, s));
+  RAV_CUDA(cudaMallocAsync(&w, sizeof(double) * n, s));
+  RAV_CUDA(cudaMallocAsync(&zero, sizeof(double) * n, s));
+  RAV_CUDA(cudaMallocAsync(&hdev, sizeof(double) * (m + 2), s));
+  RAV_CUDA(cudaMemsetAsync(zero, 0, sizeof(double) * n, s));
+  std::vector<double> H((m + 1) * m), cs(m), sn(m), gam(m + 1), y(m);
+  const int gb = grid_for(n, 256, 152 * 16);
+  double r0 = 0.0, beta = 0.0, ratio = 1.0;
+  int it = 0, rc = RAV_ERR_NOT_CONVERGED;
+  RAV_TRY(residual_impl(mg, fine, x, b, L.r, mg->scalar_dev, s));
+  RAV_TRY(read_scalar(mg, mg->scalar_dev, &r0, s));
+  if (info && info->history_host) info->history_host[0] = 1.0;
+  if (r0 == 0.0) rc = RAV_OK;
+  while (rc == RAV_ERR_NOT_CONVERGED && it < o.maxit) {
+    RAV_TRY(residual_impl(mg, fine, x, b, L.r, mg->scalar_dev, s));
+    RAV_TRY(read_scalar(mg, mg->scalar_dev, &beta, s));
+    if (beta / r0 <= o.tol) { rc = RAV_OK; ratio = beta / r0; break; }
+    k_scale_copy<<<gb, 256, 0, s>>>(n, 1.0 / beta, L.r, V);
+    note_launch();
+    std::fill(gam.begin(), gam.end(), 0.0);
+    gam[0] = beta;
+    int j = 0;
+    bool done = false;
+    for (; j < m && it < o.maxit; ++j) {
+      double* vj = V + (int64_t)j * n;
+      double* zj = Z + (int64_t)j * n;
+      RAV_CUDA(cudaMemsetAsync(zj, 0, sizeof(double) * n, s));
+      RAV_TRY(vcycle_impl(mg, sm, zj, vj, o.nu_pre, o.nu_post, true, s));
+      // w = L z: the residual of z against a zero right-hand side is -L z
+      RAV_TRY(residual_impl(mg, fine, zj, zero, w, nullptr, s));
+      k_scale_copy<<<gb, 256, 0, s>>>(n, -1.0, w, w);
+      note_launch();
+      for (int i = 0; i <= j; ++i) {
+        RAV_TRY(dot_impl(mg, w, V + (int64_t)i * n, n, hdev + i, s));
+        k_axpy_dev<<<gb, 256, 0, s>>>(n, hdev + i, V + (int64_t)i * n, w);
+        note_launch();
+      }
+      RAV_TRY(dot_impl(mg, w, w, n, hdev + j + 1, s));
+      RAV_CUDA(cudaMemcpyAsync(mg->scalar_host, hdev, sizeof(double) * (j + 2), cudaMemcpyDeviceToHost, s));
+      RAV_CUDA(cudaStreamSynchronize(s));
+      for (int i = 0; i <= j; ++i) H[i * m + j] = mg->scalar_host[i];
+      const double hn = std::sqrt(mg->scalar_host[j + 1]);
+      H[(j + 1) * m + j] = hn;
+      k_scale_copy<<<gb, 256, 0, s>>>(n, hn > 0 ? 1.0 / hn : 0.0, w, V + (int64_t)(j + 1) * n);
+      note_launch();
+      for (int i = 0; i < j; ++i) {
+        const double a = H[i * m + j], bb = H[(i + 1) * m + j];
+        H[i * m + j] = cs[i] * a + sn[i] * bb;
+        H[(i + 1) * m + j] = -sn[i] * a + cs[i] * bb;
+      }
+      const double a = H[j * m + j], bb = H[(j + 1) * m + j];
+      const double den = std::sqrt(a * a + bb * bb);
+      cs[j] = a / den;
+      sn[j] = bb / den;
+      H[j * m + j] = den;
+      H[(j + 1) * m + j] = 0.0;
+      gam[j + 1] = -sn[j] * gam[j];
+      gam[j] = cs[j] * gam[j];
+      ++it;
+      ratio = std::fabs(gam[j + 1]) / r0;
+      if (info && info->history_host) info->history_host[it] = ratio;
+      if (!std::isfinite(ratio)) { rc = RAV_ERR_NAN; done = true; ++j; break; }
+      if (ratio <= o.tol) { done = true; ++j; break; }
+    }
+    for (int i = j - 1; i >= 0; --i) {
+      double sum = gam[i];
+      for (int k = i + 1; k < j; ++k) sum -= H[i * m + k] * y[k];
+      y[i] = sum / H[i * m + i];
+    }
+    for (int i = 0; i < j; ++i) k_axpy<<<gb, 256, 0, s>>>(n, y[i], Z + (int64_t)i * n, x);
+    note_launch(j);
+    RAV_CUDA(cudaGetLastError());
+    if (rc == RAV_ERR_NAN) break;
+    if (done) {
+      RAV_TRY(residual_impl(mg, fine, x, b, L.r, mg->scalar_dev, s));
+      double rt;
+      RAV_TRY(read_scalar(mg, mg->scalar_dev, &rt, s));
+      ratio = rt / r0;
+      if (info && info->history_host) info->history_host[it] = ratio;
+      if (ratio <= o.tol) rc = RAV_OK;
+    }
+  }
+  cudaFreeAsync(V, s);
+  cudaFreeAsync(Z, s);
+  cudaFreeAsync(w, s);
+  cudaFreeAsync(zero, s);
+  cudaFreeAsync(hdev, s);
+  if (info) {
+    info->iterations = it;
+    info->final_ratio = ratio;
+    info->status = rc;
+  }
+  return rc;
+}
+
+extern "C" int solve(rav_mg* mg, rav_smoother* sm, double* x, const double* b, const rav_solve_opts* opts,
+                     rav_solve_info* info, rav_stream stream) {
+  if (!mg || !sm || sm->mg != mg || !x || !b || !opts || opts->maxit < 0 || !(opts->tol > 0)) return RAV_ERR_ARG;
+  if (opts->outer == 1) {
+    if (opts->restart > 62) return RAV_ERR_ARG;
+    return solve_fgmres(mg, sm, x, b, *opts, info, S(stream));
+  }
+  return solve_stationary(mg, sm, x, b, *opts, info, S(stream));
+}

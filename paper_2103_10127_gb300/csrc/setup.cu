@@ -1,0 +1,862 @@
+// Hierarchy set-up: geometry, Q2-Q1 element matrices (Sec. 2, Eq. 7), row-wise
+// CSR assembly on every level (the paper assembles on all grids, Sec. 4),
+// right-hand side, interpolation tables of the nested spaces and the explicit
+// inverse of the bordered coarse system (LU coarse solve of Sec. 2).
+#include <cmath>
+#include <cstdio>
+#include <atomic>
+#include <cstring>
+
+#include "common.cuh"
+
+namespace rav {
+
+static thread_local cudaError_t g_last_cuda = cudaSuccess;
+void note_cuda_error(cudaError_t e) { g_last_cuda = e; }
+static std::atomic<int64_t> g_launches{0};
+void note_launch(int k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
+
+// ---------------------------------------------------------------------------
+// 1-D reference quantities on [0,1]: three-point Gauss rule, quadratic
+// Lagrange functions with nodes 0, 1/2, 1 and linear ones with nodes 0, 1.
+__device__ __forceinline__ double gauss_x(int q) {
+  const double d = 0.38729833462074168852;  // sqrt(3/5) / 2
+  return q == 0 ? 0.5 - d : (q == 1 ? 0.5 : 0.5 + d);
+}
+__device__ __forceinline__ double gauss_w(int q) { return q == 1 ? 8.0 / 18.0 : 5.0 / 18.0; }
+__host__ __device__ __forceinline__ double lag2(int a, double t) {
+  return a == 0 ? 2.0 * (t - 0.5) * (t - 1.0) : (a == 1 ? 4.0 * t * (1.0 - t) : 2.0 * t * (t - 0.5));
+}
+__device__ __forceinline__ double dlag2(int a, double t) {
+  return a == 0 ? 4.0 * t - 3.0 : (a == 1 ? 4.0 - 8.0 * t : 4.0 * t - 1.0);
+}
+__device__ __forceinline__ double lag1(int b, double t) { return b == 0 ? 1.0 - t : t; }
+
+struct Coef {
+  double eta0;
+  int nblobs;
+  const double* blobs;  // device, nblobs * 5
+};
+
+__device__ double viscosity_at(const Coef& C, int dim, const double* x) {
+  if (C.nblobs == 0) return C.eta0;
+  double m = 0.0;
+  for (int k = 0; k < C.nblobs; ++k) {
+    const double* b = C.blobs + 5 * k;
+    double d2 = 0.0;
+    for (int a = 0; a < dim; ++a) d2 += (x[a] - b[a]) * (x[a] - b[a]);
+    const double v = b[4] * exp(-d2 / (2.0 * b[3] * b[3]));
+    m = v > m ? v : m;
+  }
+  return C.eta0 * exp(m * 2.302585092994045684);  // 10^m
+}
+
+__device__ void body_force(const Coef& C, int kind, int dim, const double* x, double* f) {
+  for (int c = 0; c < dim; ++c) f[c] = 0.0;
+  const double pi = 3.14159265358979323846;
+  if (kind == RAV_F_PSI) {
+    // u = curl psi, psi = sin^2(pi x) sin^2(pi y); p = cos(pi x) cos(pi y); f = -eta0 lap u + grad p
+    const double X = x[0], Y = x[1], p3 = pi * pi * pi;
+    const double lu0 = 2.0 * p3 * sin(2.0 * pi * Y) * (2.0 * cos(2.0 * pi * X) - 1.0);
+    const double lu1 = -2.0 * p3 * sin(2.0 * pi * X) * (2.0 * cos(2.0 * pi * Y) - 1.0);
+    f[0] = -C.eta0 * lu0 - pi * sin(pi * X) * cos(pi * Y);
+    f[1] = -C.eta0 * lu1 - pi * cos(pi * X) * sin(pi * Y);
+  } else if (kind == RAV_F_SINKER) {
+    double m = 0.0;
+    for (int k = 0; k < C.nblobs; ++k) {
+      const double* b = C.blobs + 5 * k;
+      double d2 = 0.0;
+      for (int a = 0; a < dim; ++a) d2 += (x[a] - b[a]) * (x[a] - b[a]);
+      const double v = exp(-d2 / (2.0 * b[3] * b[3]));
+      m = v > m ? v : m;
+    }
+    f[dim - 1] = -m;
+  } else if (kind == RAV_F_QUADRATIC) {
+    for (int c = 0; c < dim; ++c) f[c] = 1.0 - 2.0 * C.eta0;
+  }
+}
+
+__device__ double boundary_value(int bc, int dim, const double* x, bool top, int c) {
+  if (bc == RAV_BC_CAVITY) return (top && c == 0) ? 1.0 : 0.0;
+  if (bc == RAV_BC_QUADRATIC) {
+    if (dim == 2) return c == 0 ? x[1] * x[1] : x[0] * x[0];
+    return c == 0 ? x[1] * x[1] : (c == 1 ? x[2] * x[2] : x[0] * x[0]);
+  }
+  return 0.0;
+}
+
+// ---------------------------------------------------------------------------
+// Element matrices, one block per cell.  Local Q2 node A = a0 + 3 a1 + 9 a2,
+// local vertex b = b0 + 2 b1 + 4 b2, quadrature point q = q0 + 3 q1 + 9 q2.
+//   Ke[e][A][A2]   = sum_q W_q eta_q grad phi_A . grad phi_A2
+//   Be[e][c][A][b] = -sum_q W_q psi_b d_c phi_A
+template <int D>
+__global__ void k_cell_matrices(Geo g, Coef C, double* __restrict__ Ke, double* __restrict__ Be) {
+  constexpr int NL = D == 2 ? 9 : 27, NV = D == 2 ? 4 : 8, NQ = NL;
+  __shared__ double grad[NL][NQ][D];
+  __shared__ double psi[NV][NQ];
+  __shared__ double W[NQ], eW[NQ];
+  const int64_t e = blockIdx.x;
+  int64_t c[3] = {0, 0, 0};
+  {
+    int64_t t = e;
+    for (int a = 0; a < D; ++a) { c[a] = t % g.N; t /= g.N; }
+  }
+  double lo[3], h[3];
+  for (int a = 0; a < D; ++a) {
+    lo[a] = g.xv[a][c[a]];
+    h[a] = g.xv[a][c[a] + 1] - lo[a];
+  }
+  const int t = threadIdx.x;
+  if (t < NQ) {
+    int qt[3] = {t % 3, (t / 3) % 3, t / 9};
+    double x[3] = {0, 0, 0}, w = 1.0;
+    for (int a = 0; a < D; ++a) {
+      x[a] = lo[a] + h[a] * gauss_x(qt[a]);
+      w *= gauss_w(qt[a]) * h[a];
+    }
+    W[t] = w;
+    eW[t] = w * viscosity_at(C, D, x);
+  }
+  if (t < NL) {
+    int at[3] = {t % 3, (t / 3) % 3, t / 9};
+    for (int q = 0; q < NQ; ++q) {
+      int qt[3] = {q % 3, (q / 3) % 3, q / 9};
+      for (int k = 0; k < D; ++k) {
+        double v = dlag2(at[k], gauss_x(qt[k])) / h[k];
+        for (int m = 0; m < D; ++m)
+          if (m != k) v *= lag2(at[m], gauss_x(qt[m]));
+        grad[t][q][k] = v;
+      }
+    }
+  }
+  if (t < NV) {
+    int bt[3] = {t & 1, (t >> 1) & 1, t >> 2};
+    for (int q = 0; q < NQ; ++q) {
+      int qt[3] = {q % 3, (q / 3) % 3, q / 9};
+      double v = 1.0;
+      for (int a = 0; a < D; ++a) v *= lag1(bt[a], gauss_x(qt[a]));
+      psi[t][q] = v;
+    }
+  }
+  __syncthreads();
+  if (t < NL) {
+    double* K = Ke + (e * NL + t) * NL;
+    for (int A2 = 0; A2 < NL; ++A2) {
+      double s = 0.0;
+      for (int q = 0; q < NQ; ++q) {
+        double dd = 0.0;
+        for (int k = 0; k < D; ++k) dd += grad[t][q][k] * grad[A2][q][k];
+        s += eW[q] * dd;
+      }
+      K[A2] = s;
+    }
+    for (int cc = 0; cc < D; ++cc)
+      for (int b = 0; b < NV; ++b) {
+        double s = 0.0;
+        for (int q = 0; q < NQ; ++q) s += -W[q] * psi[b][q] * grad[t][q][cc];
+        Be[((e * D + cc) * NL + t) * NV + b] = s;
+      }
+  }
+}
+
+// Element load vectors Fe[e][A][c] = sum_q W_q f_c(x_q) phi_A(x_q).
+template <int D>
+__global__ void k_cell_load(Geo g, Coef C, int kind, double* __restrict__ Fe) {
+  constexpr int NL = D == 2 ? 9 : 27, NQ = NL;
+  __shared__ double fW[NQ][D];
+  const int64_t e = blockIdx.x;
+  int64_t c[3] = {0, 0, 0};
+  {
+    int64_t t = e;
+    for (int a = 0; a < D; ++a) { c[a] = t % g.N; t /= g.N; }
+  }
+  double lo[3], h[3];
+  for (int a = 0; a < D; ++a) {
+    lo[a] = g.xv[a][c[a]];
+    h[a] = g.xv[a][c[a] + 1] - lo[a];
+  }
+  const int t = threadIdx.x;
+  if (t < NQ) {
+    int qt[3] = {t % 3, (t / 3) % 3, t / 9};
+    double x[3] = {0, 0, 0}, w = 1.0, f[3];
+    for (int a = 0; a < D; ++a) {
+      x[a] = lo[a] + h[a] * gauss_x(qt[a]);
+      w *= gauss_w(qt[a]) * h[a];
+    }
+    body_force(C, kind, D, x, f);
+    for (int cc = 0; cc < D; ++cc) fW[t][cc] = w * f[cc];
+  }
+  __syncthreads();
+  if (t < NL) {
+    int at[3] = {t % 3, (t / 3) % 3, t / 9};
+    for (int cc = 0; cc < D; ++cc) {
+      double s = 0.0;
+      for (int q = 0; q < NQ; ++q) {
+        int qt[3] = {q % 3, (q / 3) % 3, q / 9};
+        double phi = 1.0;
+        for (int a = 0; a < D; ++a) phi *= lag2(at[a], gauss_x(qt[a]));
+        s += fW[q][cc] * phi;
+      }
+      Fe[(e * NL + t) * D + cc] = s;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Row structure.  A free velocity row at node I couples to the nodes of the
+// cells containing I (per axis [I-1, I+1] for odd I, [I-2, I+2] clipped for
+// even I) and to their vertices; a pressure row at vertex v couples to every
+// component at the nodes [2v-2, 2v+2] (clipped); a Dirichlet row is the
+// identity row.
+__device__ __forceinline__ void node_range(const Geo& g, int64_t I, int64_t& lo, int64_t& hi) {
+  if (I & 1) { lo = I - 1; hi = I + 1; }
+  else { lo = I - 2 < 0 ? 0 : I - 2; hi = I + 2 > 2 * g.N ? 2 * g.N : I + 2; }
+}
+__device__ __forceinline__ void vert_range(const Geo& g, int64_t I, int64_t& lo, int64_t& hi) {
+  if (I & 1) { lo = (I - 1) >> 1; hi = (I + 1) >> 1; }
+  else { lo = (I >> 1) - 1 < 0 ? 0 : (I >> 1) - 1; hi = (I >> 1) + 1 > g.N ? g.N : (I >> 1) + 1; }
+}
+__device__ __forceinline__ void pnode_range(const Geo& g, int64_t v, int64_t& lo, int64_t& hi) {
+  lo = 2 * v - 2 < 0 ? 0 : 2 * v - 2;
+  hi = 2 * v + 2 > 2 * g.N ? 2 * g.N : 2 * v + 2;
+}
+
+__global__ void k_row_len(Geo g, int64_t* __restrict__ len) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= g.n) return;
+  int64_t L = 1;
+  if (i < g.n_u) {
+    int64_t I[3];
+    int c;
+    vel_node(g, i, I, c);
+    if (!node_on_boundary(g, I)) {
+      int64_t a1 = 1, a2 = 1;
+      for (int a = 0; a < g.dim; ++a) {
+        int64_t lo, hi;
+        node_range(g, I[a], lo, hi);
+        a1 *= hi - lo + 1;
+        vert_range(g, I[a], lo, hi);
+        a2 *= hi - lo + 1;
+      }
+      L = a1 + a2;
+    }
+  } else {
+    int64_t v = i - g.n_u;
+    L = g.dim;
+    for (int a = 0; a < g.dim; ++a) {
+      int64_t va = v % (g.N + 1);
+      v /= (g.N + 1);
+      int64_t lo, hi;
+      pnode_range(g, va, lo, hi);
+      L *= hi - lo + 1;
+    }
+  }
+  len[i] = L;
+}
+
+// Exclusive scan of n int64 values in place, writes the total to out[n].
+__global__ void k_scan_blocks(int64_t* __restrict__ a, int64_t n, int64_t* __restrict__ bsum) {
+  __shared__ int64_t s[1024];
+  const int64_t i = blockIdx.x * 1024ll + threadIdx.x;
+  int64_t v = i < n ? a[i] : 0;
+  s[threadIdx.x] = v;
+  __syncthreads();
+  for (int o = 1; o < 1024; o <<= 1) {
+    int64_t t = threadIdx.x >= o ? s[threadIdx.x - o] : 0;
+    __syncthreads();
+    s[threadIdx.x] += t;
+    __syncthreads();
+  }
+  if (i < n) a[i] = s[threadIdx.x] - v;
+  if (threadIdx.x == 1023) bsum[blockIdx.x] = s[1023];
+}
+__global__ void k_scan_sums(int64_t* __restrict__ bsum, int nb) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    int64_t acc = 0;
+    for (int k = 0; k < nb; ++k) {
+      int64_t v = bsum[k];
+      bsum[k] = acc;
+      acc += v;
+    }
+    bsum[nb] = acc;
+  }
+}
+__global__ void k_scan_add(int64_t* __restrict__ a, int64_t n, const int64_t* __restrict__ bsum) {
+  const int64_t i = blockIdx.x * 1024ll + threadIdx.x;
+  if (i < n) a[i] += bsum[blockIdx.x];
+  if (i == 0) a[n] = bsum[gridDim.x];
+}
+
+// Cells (per axis) containing both node indices I and J.
+__device__ __forceinline__ void shared_cells(const Geo& g, int64_t I, int64_t J, int64_t& lo, int64_t& hi) {
+  const int64_t mx = I > J ? I : J, mn = I < J ? I : J;
+  lo = (mx - 1) >> 1;  // smallest e with 2e + 2 >= mx
+  if (lo < 0) lo = 0;
+  hi = mn >> 1;        // largest e with 2e <= mn
+  if (hi > g.N - 1) hi = g.N - 1;
+}
+
+template <int D>
+__global__ void k_assemble(Geo g, const double* __restrict__ Ke, const double* __restrict__ Be,
+                           const int64_t* __restrict__ rp, int32_t* __restrict__ ci, double* __restrict__ va) {
+  constexpr int NL = D == 2 ? 9 : 27, NV = D == 2 ? 4 : 8;
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= g.n) return;
+  int64_t pos = rp[i];
+  if (i < g.n_u) {
+    int64_t I[3] = {0, 0, 0};
+    int c;
+    vel_node(g, i, I, c);
+    if (node_on_boundary(g, I)) {
+      ci[pos] = (int32_t)i;
+      va[pos] = 1.0;
+      return;
+    }
+    int64_t nlo[3] = {0, 0, 0}, nhi[3] = {0, 0, 0}, vlo[3] = {0, 0, 0}, vhi[3] = {0, 0, 0};
+    for (int a = 0; a < D; ++a) {
+      node_range(g, I[a], nlo[a], nhi[a]);
+      vert_range(g, I[a], vlo[a], vhi[a]);
+    }
+    // velocity columns (J, c)
+    for (int64_t J2 = (D == 3 ? nlo[2] : 0); J2 <= (D == 3 ? nhi[2] : 0); ++J2)
+      for (int64_t J1 = nlo[1]; J1 <= nhi[1]; ++J1)
+        for (int64_t J0 = nlo[0]; J0 <= nhi[0]; ++J0) {
+          const int64_t J[3] = {J0, J1, J2};
+          int64_t elo[3] = {0, 0, 0}, ehi[3] = {0, 0, 0};
+          for (int a = 0; a < D; ++a) shared_cells(g, I[a], J[a], elo[a], ehi[a]);
+          double s = 0.0;
+          for (int64_t e2 = elo[2]; e2 <= ehi[2]; ++e2)
+            for (int64_t e1 = elo[1]; e1 <= ehi[1]; ++e1)
+              for (int64_t e0 = elo[0]; e0 <= ehi[0]; ++e0) {
+                const int64_t ec[3] = {e0, e1, e2};
+                int64_t e = 0;
+                int A = 0, A2 = 0;
+                for (int a = D - 1; a >= 0; --a) {
+                  e = e * g.N + ec[a];
+                  A = A * 3 + (int)(I[a] - 2 * ec[a]);
+                  A2 = A2 * 3 + (int)(J[a] - 2 * ec[a]);
+                }
+                s += Ke[(e * NL + A) * NL + A2];
+              }
+          ci[pos] = (int32_t)(D * node_id(g, J) + c);
+          va[pos] = s;
+          ++pos;
+        }
+    // pressure columns p_V
+    for (int64_t V2 = (D == 3 ? vlo[2] : 0); V2 <= (D == 3 ? vhi[2] : 0); ++V2)
+      for (int64_t V1 = vlo[1]; V1 <= vhi[1]; ++V1)
+        for (int64_t V0 = vlo[0]; V0 <= vhi[0]; ++V0) {
+          const int64_t V[3] = {V0, V1, V2};
+          int64_t elo[3] = {0, 0, 0}, ehi[3] = {0, 0, 0};
+          for (int a = 0; a < D; ++a) {
+            // cells containing vertex V (V-1, V) and node I (2e <= I <= 2e+2)
+            int64_t lo = V[a] - 1, hi = V[a];
+            const int64_t ilo = (I[a] - 1) >> 1, ihi = I[a] >> 1;
+            lo = lo > ilo ? lo : ilo;
+            hi = hi < ihi ? hi : ihi;
+            lo = lo < 0 ? 0 : lo;
+            hi = hi > g.N - 1 ? g.N - 1 : hi;
+            elo[a] = lo;
+            ehi[a] = hi;
+          }
+          double s = 0.0;
+          for (int64_t e2 = elo[2]; e2 <= ehi[2]; ++e2)
+            for (int64_t e1 = elo[1]; e1 <= ehi[1]; ++e1)
+              for (int64_t e0 = elo[0]; e0 <= ehi[0]; ++e0) {
+                const int64_t ec[3] = {e0, e1, e2};
+                int64_t e = 0;
+                int A = 0, b = 0;
+                for (int a = D - 1; a >= 0; --a) {
+                  e = e * g.N + ec[a];
+                  A = A * 3 + (int)(I[a] - 2 * ec[a]);
+                  b = b * 2 + (int)(V[a] - ec[a]);
+                }
+                s += Be[((e * D + c) * NL + A) * NV + b];
+              }
+          ci[pos] = (int32_t)(g.n_u + vert_id(g, V));
+          va[pos] = s;
+          ++pos;
+        }
+  } else {
+    int64_t v[3] = {0, 0, 0};
+    {
+      int64_t t = i - g.n_u;
+      for (int a = 0; a < D; ++a) { v[a] = t % (g.N + 1); t /= (g.N + 1); }
+    }
+    int64_t nlo[3] = {0, 0, 0}, nhi[3] = {0, 0, 0};
+    for (int a = 0; a < D; ++a) pnode_range(g, v[a], nlo[a], nhi[a]);
+    for (int64_t J2 = (D == 3 ? nlo[2] : 0); J2 <= (D == 3 ? nhi[2] : 0); ++J2)
+      for (int64_t J1 = nlo[1]; J1 <= nhi[1]; ++J1)
+        for (int64_t J0 = nlo[0]; J0 <= nhi[0]; ++J0) {
+          const int64_t J[3] = {J0, J1, J2};
+          int64_t elo[3] = {0, 0, 0}, ehi[3] = {0, 0, 0};
+          for (int a = 0; a < D; ++a) {
+            int64_t lo = v[a] - 1, hi = v[a];
+            const int64_t jlo = (J[a] - 1) >> 1, jhi = J[a] >> 1;
+            lo = lo > jlo ? lo : jlo;
+            hi = hi < jhi ? hi : jhi;
+            lo = lo < 0 ? 0 : lo;
+            hi = hi > g.N - 1 ? g.N - 1 : hi;
+            elo[a] = lo;
+            ehi[a] = hi;
+          }
+          const int64_t jid = node_id(g, J);
+          for (int cc = 0; cc < D; ++cc) {
+            double s = 0.0;
+            for (int64_t e2 = elo[2]; e2 <= ehi[2]; ++e2)
+              for (int64_t e1 = elo[1]; e1 <= ehi[1]; ++e1)
+                for (int64_t e0 = elo[0]; e0 <= ehi[0]; ++e0) {
+                  const int64_t ec[3] = {e0, e1, e2};
+                  int64_t e = 0;
+                  int A = 0, b = 0;
+                  for (int a = D - 1; a >= 0; --a) {
+                    e = e * g.N + ec[a];
+                    A = A * 3 + (int)(J[a] - 2 * ec[a]);
+                    b = b * 2 + (int)(v[a] - ec[a]);
+                  }
+                  s += Be[((e * D + cc) * NL + A) * NV + b];
+                }
+            ci[pos] = (int32_t)(D * jid + cc);
+            va[pos] = s;
+            ++pos;
+          }
+        }
+  }
+}
+
+// Right-hand side: free velocity rows sum the element loads of the cells
+// containing the node (ascending cell order), Dirichlet rows get g, pressure rows 0.
+template <int D>
+__global__ void k_rhs(Geo g, int bc, const double* __restrict__ Fe, double* __restrict__ b) {
+  constexpr int NL = D == 2 ? 9 : 27;
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= g.n) return;
+  if (i >= g.n_u) { b[i] = 0.0; return; }
+  int64_t I[3] = {0, 0, 0};
+  int c;
+  vel_node(g, i, I, c);
+  if (node_on_boundary(g, I)) {
+    double x[3] = {0, 0, 0};
+    for (int a = 0; a < D; ++a) x[a] = node_coord(g, a, I[a]);
+    b[i] = boundary_value(bc, D, x, I[D - 1] == 2 * g.N, c);
+    return;
+  }
+  int64_t elo[3] = {0, 0, 0}, ehi[3] = {0, 0, 0};
+  for (int a = 0; a < D; ++a) shared_cells(g, I[a], I[a], elo[a], ehi[a]);
+  double s = 0.0;
+  for (int64_t e2 = elo[2]; e2 <= ehi[2]; ++e2)
+    for (int64_t e1 = elo[1]; e1 <= ehi[1]; ++e1)
+      for (int64_t e0 = elo[0]; e0 <= ehi[0]; ++e0) {
+        const int64_t ec[3] = {e0, e1, e2};
+        int64_t e = 0;
+        int A = 0;
+        for (int a = D - 1; a >= 0; --a) {
+          e = e * g.N + ec[a];
+          A = A * 3 + (int)(I[a] - 2 * ec[a]);
+        }
+        s += Fe[(e * NL + A) * D + c];
+      }
+  b[i] = s;
+}
+
+template <int D>
+__global__ void k_initial_guess(Geo g, int bc, double* __restrict__ x) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= g.n) return;
+  double v = 0.0;
+  if (i < g.n_u) {
+    int64_t I[3] = {0, 0, 0};
+    int c;
+    vel_node(g, i, I, c);
+    if (node_on_boundary(g, I)) {
+      double xx[3] = {0, 0, 0};
+      for (int a = 0; a < D; ++a) xx[a] = node_coord(g, a, I[a]);
+      v = boundary_value(bc, D, xx, I[D - 1] == 2 * g.N, c);
+    }
+  }
+  x[i] = v;
+}
+
+// ---------------------------------------------------------------------------
+// Bordered coarse system and its Gauss-Jordan inverse (partial pivoting).
+__global__ void k_fill_bordered(Geo g, const int64_t* __restrict__ rp, const int32_t* __restrict__ ci,
+                                const double* __restrict__ va, double* __restrict__ Mb, double* __restrict__ Id) {
+  const int64_t m = g.n + 1;
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= m) return;
+  double* row = Mb + i * m;
+  double* irow = Id + i * m;
+  for (int64_t j = 0; j < m; ++j) { row[j] = 0.0; irow[j] = 0.0; }
+  irow[i] = 1.0;
+  if (i < g.n) {
+    for (int64_t k = rp[i]; k < rp[i + 1]; ++k) row[ci[k]] = va[k];
+    if (i >= g.n_u) row[g.n] = 1.0;
+  } else {
+    for (int64_t j = g.n_u; j < g.n; ++j) row[j] = 1.0;
+  }
+}
+
+__global__ void k_absmax(const double* __restrict__ a, int64_t n, double* __restrict__ out) {
+  double m = 0.0;
+  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) m = fmax(m, fabs(a[i]));
+  __shared__ double s[1024];
+  s[threadIdx.x] = m;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) s[threadIdx.x] = fmax(s[threadIdx.x], s[threadIdx.x + o]);
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *out = s[0];
+}
+
+// State: st[0] = max|M| (set once), st[1] = pivot value, st[2] = singular flag; piv = pivot row.
+__global__ void k_gj_pivot(const double* __restrict__ A, int64_t m, int64_t k, double* st, int64_t* piv) {
+  __shared__ double sv[1024];
+  __shared__ int64_t si[1024];
+  double best = -1.0;
+  int64_t bi = k;
+  for (int64_t i = k + threadIdx.x; i < m; i += blockDim.x) {
+    const double v = fabs(A[i * m + k]);
+    if (v > best) { best = v; bi = i; }
+  }
+  sv[threadIdx.x] = best;
+  si[threadIdx.x] = bi;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) {
+      const double v2 = sv[threadIdx.x + o];
+      const int64_t i2 = si[threadIdx.x + o];
+      if (v2 > sv[threadIdx.x] || (v2 == sv[threadIdx.x] && i2 < si[threadIdx.x])) {
+        sv[threadIdx.x] = v2;
+        si[threadIdx.x] = i2;
+      }
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    *piv = si[0];
+    st[1] = A[si[0] * m + k];
+    if (!(sv[0] > 1e-14 * st[0])) { st[2] = 1.0; st[1] = 1.0; }
+  }
+}
+__global__ void k_gj_swap_scale(double* __restrict__ A, double* __restrict__ Inv, int64_t m, int64_t k,
+                                const double* __restrict__ st, const int64_t* __restrict__ piv) {
+  const int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (j >= 2 * m) return;
+  double* X = j < m ? A : Inv;
+  const int64_t col = j < m ? j : j - m;
+  const int64_t p = *piv;
+  const double pv = st[1];
+  const double ak = X[k * m + col], ap = X[p * m + col];
+  X[k * m + col] = ap / pv;
+  if (p != k) X[p * m + col] = ak;
+}
+__global__ void k_gj_colsave(const double* __restrict__ A, int64_t m, int64_t k, double* __restrict__ f) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < m) f[i] = i == k ? 0.0 : A[i * m + k];
+}
+__global__ void k_gj_eliminate(double* __restrict__ A, double* __restrict__ Inv, int64_t m, int64_t k,
+                               const double* __restrict__ f) {
+  const int64_t i = blockIdx.y;
+  if (i == k) return;
+  const double fi = f[i];
+  if (fi == 0.0) return;
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < 2 * m; j += (int64_t)gridDim.x * blockDim.x) {
+    if (j < m) {
+      if (j >= k) A[i * m + j] -= fi * A[k * m + j];
+    } else {
+      Inv[i * m + (j - m)] -= fi * Inv[k * m + (j - m)];
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+static int level_geometry(rav_mg* mg, Level& L, int N, const double* fine_coords, int stride) {
+  L.g.dim = mg->dim;
+  L.g.N = N;
+  L.g.M = 2 * (int64_t)N + 1;
+  L.g.nnode = ipow(L.g.M, mg->dim);
+  L.g.n_u = mg->dim * L.g.nnode;
+  L.g.n_p = ipow(N + 1, mg->dim);
+  L.g.n = L.g.n_u + L.g.n_p;
+  const int Nf = N * stride;
+  for (int a = 0; a < 3; ++a) {
+    L.g.xv[a] = nullptr;
+    if (a >= mg->dim) continue;
+    L.xv_host[a].resize(N + 1);
+    for (int k = 0; k <= N; ++k)
+      L.xv_host[a][k] = fine_coords ? fine_coords[a * (Nf + 1) + k * stride] : (double)(k * stride) / Nf;
+    RAV_CUDA(cudaMalloc(&L.xv_dev[a], sizeof(double) * (N + 1)));
+    RAV_CUDA(cudaMemcpy(L.xv_dev[a], L.xv_host[a].data(), sizeof(double) * (N + 1), cudaMemcpyHostToDevice));
+    L.g.xv[a] = L.xv_dev[a];
+  }
+  return RAV_OK;
+}
+
+static int assemble_level(rav_mg* mg, Level& L, cudaStream_t s) {
+  const Geo& g = L.g;
+  const int D = g.dim;
+  const int NL = D == 2 ? 9 : 27, NV = D == 2 ? 4 : 8;
+  const int64_t ncell = ipow(g.N, D);
+  double *Ke = nullptr, *Be = nullptr;
+  RAV_CUDA(cudaMallocAsync(&Ke, sizeof(double) * ncell * NL * NL, s));
+  RAV_CUDA(cudaMallocAsync(&Be, sizeof(double) * ncell * D * NL * NV, s));
+  Coef C{mg->eta0, mg->nblobs, mg->blobs_dev};
+  if (D == 2) k_cell_matrices<2><<<(unsigned)ncell, 32, 0, s>>>(g, C, Ke, Be);
+  else k_cell_matrices<3><<<(unsigned)ncell, 32, 0, s>>>(g, C, Ke, Be);
+  RAV_CUDA(cudaGetLastError());
+  // row lengths -> exclusive scan -> row pointer
+  RAV_CUDA(cudaMalloc(&L.rp, sizeof(int64_t) * (g.n + 1)));
+  const int nb = (int)((g.n + 1023) / 1024);
+  int64_t* bsum = nullptr;
+  RAV_CUDA(cudaMallocAsync(&bsum, sizeof(int64_t) * (nb + 1), s));
+  k_row_len<<<nb * 4, 256, 0, s>>>(g, L.rp);
+  k_scan_blocks<<<nb, 1024, 0, s>>>(L.rp, g.n, bsum);
+  k_scan_sums<<<1, 32, 0, s>>>(bsum, nb);
+  k_scan_add<<<nb, 1024, 0, s>>>(L.rp, g.n, bsum);
+  RAV_CUDA(cudaGetLastError());
+  RAV_CUDA(cudaMemcpyAsync(&L.nnz, L.rp + g.n, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+  RAV_CUDA(cudaStreamSynchronize(s));
+  if (L.nnz >= (int64_t)1 << 31 || g.n >= (int64_t)1 << 31) return RAV_ERR_ARG;
+  RAV_CUDA(cudaMalloc(&L.ci, sizeof(int32_t) * L.nnz));
+  RAV_CUDA(cudaMalloc(&L.va, sizeof(double) * L.nnz));
+  const int blocks = (int)((g.n + 127) / 128);
+  if (D == 2) k_assemble<2><<<blocks, 128, 0, s>>>(g, Ke, Be, L.rp, L.ci, L.va);
+  else k_assemble<3><<<blocks, 128, 0, s>>>(g, Ke, Be, L.rp, L.ci, L.va);
+  RAV_CUDA(cudaGetLastError());
+  RAV_CUDA(cudaFreeAsync(Ke, s));
+  RAV_CUDA(cudaFreeAsync(Be, s));
+  RAV_CUDA(cudaFreeAsync(bsum, s));
+  RAV_CUDA(cudaMalloc(&L.r, sizeof(double) * g.n));
+  RAV_CUDA(cudaMalloc(&L.x, sizeof(double) * g.n));
+  RAV_CUDA(cudaMalloc(&L.b, sizeof(double) * g.n));
+  return RAV_OK;
+}
+
+// Interpolation tables of fine level F from coarse level C (host, O(N) per axis):
+// a fine Q2 node at position x in coarse cell k (k = min(I/4, Nc-1)) takes the
+// three quadratic Lagrange values at t = (x - xc_k)/(xc_{k+1} - xc_k); a fine
+// vertex takes the two linear ones.
+static int transfer_tables(rav_mg* mg, const Level& C, Level& F) {
+  for (int a = 0; a < mg->dim; ++a) {
+    const int Nf = F.g.N, Nc = C.g.N;
+    std::vector<int> k2(2 * Nf + 1), k1(Nf + 1);
+    std::vector<double> w2(3 * (2 * Nf + 1)), w1(2 * (Nf + 1));
+    const std::vector<double>& xf = F.xv_host[a];
+    const std::vector<double>& xc = C.xv_host[a];
+    for (int I = 0; I <= 2 * Nf; ++I) {
+      const double x = (I & 1) ? 0.5 * (xf[(I - 1) / 2] + xf[(I + 1) / 2]) : xf[I / 2];
+      int k = I / 4;
+      if (k > Nc - 1) k = Nc - 1;
+      const double t = (x - xc[k]) / (xc[k + 1] - xc[k]);
+      k2[I] = k;
+      for (int j = 0; j < 3; ++j) w2[3 * I + j] = lag2(j, t);
+    }
+    for (int v = 0; v <= Nf; ++v) {
+      int k = v / 2;
+      if (k > Nc - 1) k = Nc - 1;
+      const double t = (xf[v] - xc[k]) / (xc[k + 1] - xc[k]);
+      k1[v] = k;
+      w1[2 * v] = 1.0 - t;
+      w1[2 * v + 1] = t;
+    }
+    RAV_CUDA(cudaMalloc(&F.k2[a], sizeof(int) * k2.size()));
+    RAV_CUDA(cudaMalloc(&F.w2[a], sizeof(double) * w2.size()));
+    RAV_CUDA(cudaMalloc(&F.k1[a], sizeof(int) * k1.size()));
+    RAV_CUDA(cudaMalloc(&F.w1[a], sizeof(double) * w1.size()));
+    RAV_CUDA(cudaMemcpy(F.k2[a], k2.data(), sizeof(int) * k2.size(), cudaMemcpyHostToDevice));
+    RAV_CUDA(cudaMemcpy(F.w2[a], w2.data(), sizeof(double) * w2.size(), cudaMemcpyHostToDevice));
+    RAV_CUDA(cudaMemcpy(F.k1[a], k1.data(), sizeof(int) * k1.size(), cudaMemcpyHostToDevice));
+    RAV_CUDA(cudaMemcpy(F.w1[a], w1.data(), sizeof(double) * w1.size(), cudaMemcpyHostToDevice));
+  }
+  return RAV_OK;
+}
+
+static int coarse_inverse(rav_mg* mg, cudaStream_t s) {
+  const Level& L = mg->lev[0];
+  const int64_t m = L.g.n + 1;
+  double *A = nullptr, *f = nullptr, *st = nullptr;
+  int64_t* piv = nullptr;
+  RAV_CUDA(cudaMalloc(&mg->cinv, sizeof(double) * m * m));
+  RAV_CUDA(cudaMallocAsync(&A, sizeof(double) * m * m, s));
+  RAV_CUDA(cudaMallocAsync(&f, sizeof(double) * m, s));
+  RAV_CUDA(cudaMallocAsync(&st, sizeof(double) * 4, s));
+  RAV_CUDA(cudaMallocAsync(&piv, sizeof(int64_t), s));
+  RAV_CUDA(cudaMemsetAsync(st, 0, sizeof(double) * 4, s));
+  k_fill_bordered<<<grid_for(m, 128, 1 << 30), 128, 0, s>>>(L.g, L.rp, L.ci, L.va, A, mg->cinv);
+  k_absmax<<<1, 1024, 0, s>>>(A, m * m, st);
+  const int gb = grid_for(2 * m, 256, 1 << 30);
+  const unsigned gx = (unsigned)((2 * m + 255) / 256 < 8 ? (2 * m + 255) / 256 : 8);
+  for (int64_t k = 0; k < m; ++k) {
+    k_gj_pivot<<<1, 1024, 0, s>>>(A, m, k, st, piv);
+    k_gj_swap_scale<<<gb, 256, 0, s>>>(A, mg->cinv, m, k, st, piv);
+    k_gj_colsave<<<grid_for(m, 256, 1 << 30), 256, 0, s>>>(A, m, k, f);
+    k_gj_eliminate<<<dim3(gx, (unsigned)m), 256, 0, s>>>(A, mg->cinv, m, k, f);
+  }
+  RAV_CUDA(cudaGetLastError());
+  double h[4];
+  RAV_CUDA(cudaMemcpyAsync(h, st, sizeof(double) * 4, cudaMemcpyDeviceToHost, s));
+  RAV_CUDA(cudaStreamSynchronize(s));
+  RAV_CUDA(cudaFreeAsync(A, s));
+  RAV_CUDA(cudaFreeAsync(f, s));
+  RAV_CUDA(cudaFreeAsync(st, s));
+  RAV_CUDA(cudaFreeAsync(piv, s));
+  if (h[2] != 0.0) return RAV_ERR_SINGULAR_COARSE;
+  return RAV_OK;
+}
+
+}  // namespace rav
+
+using namespace rav;
+
+extern "C" int mg_setup(const rav_problem* p, int n_levels, rav_stream stream, rav_mg** out) {
+  if (!p || !out || (p->dim != 2 && p->dim != 3) || p->N < 2 || n_levels < 1 || n_levels > kMaxLevels)
+    return RAV_ERR_ARG;
+  if (p->N % (1 << (n_levels - 1)) != 0 || p->N / (1 << (n_levels - 1)) < 2) return RAV_ERR_ARG;
+  if (p->nblobs < 0 || (p->nblobs > 0 && !p->blobs_host)) return RAV_ERR_ARG;
+  {
+    // the explicit coarse inverse is formed with one grid row per matrix row
+    const int64_t N0 = p->N >> (n_levels - 1);
+    const int64_t n0 = p->dim * ipow(2 * N0 + 1, p->dim) + ipow(N0 + 1, p->dim);
+    if (n0 + 1 > 65535) return RAV_ERR_ARG;
+  }
+  if (p->coords_host) {
+    for (int a = 0; a < p->dim; ++a)
+      for (int k = 0; k < p->N; ++k)
+        if (!(p->coords_host[a * (p->N + 1) + k + 1] > p->coords_host[a * (p->N + 1) + k])) return RAV_ERR_ARG;
+  }
+  cudaStream_t s = S(stream);
+  rav_mg* mg = new rav_mg();
+  *out = nullptr;
+  mg->dim = p->dim;
+  mg->N = p->N;
+  mg->nlev = n_levels;
+  mg->eta0 = p->eta0;
+  mg->bc = p->bc;
+  mg->nblobs = p->nblobs;
+  int rc = RAV_OK;
+  auto fail = [&](int code) {
+    mg_destroy(mg);
+    return code;
+  };
+  if (p->nblobs > 0) {
+    mg->blobs.assign(p->blobs_host, p->blobs_host + 5 * p->nblobs);
+    if (cudaMalloc(&mg->blobs_dev, sizeof(double) * 5 * p->nblobs) != cudaSuccess) return fail(RAV_ERR_CUDA);
+    cudaMemcpy(mg->blobs_dev, mg->blobs.data(), sizeof(double) * 5 * p->nblobs, cudaMemcpyHostToDevice);
+  }
+  for (int l = n_levels - 1; l >= 0; --l) {
+    const int stride = 1 << (n_levels - 1 - l);
+    if ((rc = level_geometry(mg, mg->lev[l], p->N / stride, p->coords_host, stride)) != RAV_OK) return fail(rc);
+    if ((rc = assemble_level(mg, mg->lev[l], s)) != RAV_OK) return fail(rc);
+  }
+  for (int l = 1; l < n_levels; ++l)
+    if ((rc = transfer_tables(mg, mg->lev[l - 1], mg->lev[l])) != RAV_OK) return fail(rc);
+  if ((rc = coarse_inverse(mg, s)) != RAV_OK) return fail(rc);
+  mg->part_cap = 152 * 8;
+  if (cudaMalloc(&mg->norm_part, sizeof(double) * (mg->part_cap + 8)) != cudaSuccess) return fail(RAV_ERR_CUDA);
+  if (cudaMalloc(&mg->scalar_dev, sizeof(double) * 64) != cudaSuccess) return fail(RAV_ERR_CUDA);
+  if (cudaMallocHost(&mg->scalar_host, sizeof(double) * 64) != cudaSuccess) return fail(RAV_ERR_CUDA);
+  if (cudaStreamSynchronize(s) != cudaSuccess) return fail(RAV_ERR_CUDA);
+  *out = mg;
+  return RAV_OK;
+}
+
+extern "C" void mg_destroy(rav_mg* mg) {
+  if (!mg) return;
+  cudaDeviceSynchronize();
+  for (int l = 0; l < kMaxLevels; ++l) {
+    Level& L = mg->lev[l];
+    for (int a = 0; a < 3; ++a) {
+      cudaFree(L.xv_dev[a]);
+      cudaFree(L.k2[a]);
+      cudaFree(L.w2[a]);
+      cudaFree(L.k1[a]);
+      cudaFree(L.w1[a]);
+    }
+    cudaFree(L.rp);
+    cudaFree(L.ci);
+    cudaFree(L.va);
+    cudaFree(L.x);
+    cudaFree(L.b);
+    cudaFree(L.r);
+  }
+  cudaFree(mg->cinv);
+  cudaFree(mg->blobs_dev);
+  cudaFree(mg->norm_part);
+  cudaFree(mg->scalar_dev);
+  if (mg->scalar_host) cudaFreeHost(mg->scalar_host);
+  delete mg;
+}
+
+extern "C" int rav_get_counts(const rav_mg* mg, int level, int64_t out[5]) {
+  if (!mg || !out || level < 0 || level >= mg->nlev) return RAV_ERR_ARG;
+  const Level& L = mg->lev[level];
+  out[0] = L.g.n_u;
+  out[1] = L.g.n_p;
+  out[2] = L.g.n;
+  out[3] = L.nnz;
+  out[4] = L.g.N;
+  return RAV_OK;
+}
+
+extern "C" int rav_get_csr(const rav_mg* mg, int level, int64_t* rp, int32_t* ci, double* va, rav_stream stream) {
+  if (!mg || level < 0 || level >= mg->nlev || !rp || !ci || !va) return RAV_ERR_ARG;
+  const Level& L = mg->lev[level];
+  cudaStream_t s = S(stream);
+  RAV_CUDA(cudaMemcpyAsync(rp, L.rp, sizeof(int64_t) * (L.g.n + 1), cudaMemcpyDeviceToDevice, s));
+  RAV_CUDA(cudaMemcpyAsync(ci, L.ci, sizeof(int32_t) * L.nnz, cudaMemcpyDeviceToDevice, s));
+  RAV_CUDA(cudaMemcpyAsync(va, L.va, sizeof(double) * L.nnz, cudaMemcpyDeviceToDevice, s));
+  return RAV_OK;
+}
+
+extern "C" int rav_assemble_rhs(rav_mg* mg, int forcing, double* b, rav_stream stream) {
+  if (!mg || !b || forcing < 0 || forcing > 3) return RAV_ERR_ARG;
+  if (forcing == RAV_F_PSI && mg->dim != 2) return RAV_ERR_ARG;
+  Level& L = mg->lev[mg->nlev - 1];
+  const Geo& g = L.g;
+  cudaStream_t s = S(stream);
+  const int D = g.dim, NL = D == 2 ? 9 : 27;
+  const int64_t ncell = ipow(g.N, D);
+  double* Fe = nullptr;
+  RAV_CUDA(cudaMallocAsync(&Fe, sizeof(double) * ncell * NL * D, s));
+  Coef C{mg->eta0, mg->nblobs, mg->blobs_dev};
+  const int blocks = (int)((g.n + 255) / 256);
+  if (D == 2) {
+    k_cell_load<2><<<(unsigned)ncell, 32, 0, s>>>(g, C, forcing, Fe);
+    k_rhs<2><<<blocks, 256, 0, s>>>(g, mg->bc, Fe, b);
+  } else {
+    k_cell_load<3><<<(unsigned)ncell, 32, 0, s>>>(g, C, forcing, Fe);
+    k_rhs<3><<<blocks, 256, 0, s>>>(g, mg->bc, Fe, b);
+  }
+  RAV_CUDA(cudaGetLastError());
+  RAV_CUDA(cudaFreeAsync(Fe, s));
+  return RAV_OK;
+}
+
+extern "C" int rav_initial_guess(rav_mg* mg, double* x, rav_stream stream) {
+  if (!mg || !x) return RAV_ERR_ARG;
+  const Geo& g = mg->lev[mg->nlev - 1].g;
+  const int blocks = (int)((g.n + 255) / 256);
+  if (g.dim == 2) k_initial_guess<2><<<blocks, 256, 0, S(stream)>>>(g, mg->bc, x);
+  else k_initial_guess<3><<<blocks, 256, 0, S(stream)>>>(g, mg->bc, x);
+  RAV_CUDA(cudaGetLastError());
+  return RAV_OK;
+}
+
+extern "C" int64_t rav_kernel_launches(void) { return g_launches.load(); }
+
+extern "C" const char* rav_strerror(int code) {
+  switch (code) {
+    case RAV_OK: return "ok";
+    case RAV_ERR_ARG: return "invalid argument";
+    case RAV_ERR_CUDA: return cudaGetErrorString(g_last_cuda);
+    case RAV_ERR_SINGULAR_PATCH: return "singular subdomain system";
+    case RAV_ERR_SINGULAR_COARSE: return "singular coarse system";
+    case RAV_ERR_NOT_CONVERGED: return "not converged within maxit";
+    case RAV_ERR_DIVERGED: return "diverged";
+    case RAV_ERR_NAN: return "non-finite residual";
+    case RAV_ERR_TIMEOUT: return "device wait timed out";
+  }
+  return "unknown error";
+}

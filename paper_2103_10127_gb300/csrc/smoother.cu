@@ -1,0 +1,1039 @@
+// Vanka smoothers (Sec. 3): subdomain set-up and application.
+//
+// Subdomain i = pressure DoF p_i + the free velocity DoFs of the cells around
+// vertex i.  On a tensor grid its DoFs are the positions of a fixed "box":
+// Q2 nodes J = 2i - 2 + a, a in [0,5)^d, all components, then p_i; box
+// position k = d (a0 + 5 a1 + 25 a2) + c, pressure last (n_box = 5^d d + 1).
+// A position whose node lies outside the domain or on the boundary is not in
+// the subdomain; it keeps a zero row and column, so every subdomain is handled
+// with the same padded shape.  Ascending box position = ascending DoF index,
+// so the compact subdomain list of the paper is the box filtered by validity.
+//
+// Local inverse.  The operator is L_i = [A_i b; b^T 0] with one pressure and
+// A_i = I_d (x) K_i (the gradient form of Eq. 7 does not couple velocity
+// components).  With w = A_i^{-1} b and the scalar Schur complement
+// s = -b^T w the block inverse is
+//     L_i^{-1} = [A_i^{-1} + w w^T / s,  -w / s;  -w^T / s,  1 / s],
+// so one fp64 Cholesky factorisation of K_i (5^d nodes) replaces the LU of the
+// full (5^d d + 1)-square system: the paper's L_i^{-1} (Eq. 11) computed
+// exactly, at 1/d^3 of the cost.  RAV keeps the rows of the owned DoFs only
+// (Sec. 4.3): owned = box nodes a in {2,3}^d (J = 2i + delta) and p_i.
+#include <cuda_bf16.h>
+#include <cuda_fp8.h>
+
+#include <cmath>
+#include <type_traits>
+#include <vector>
+
+#include "common.cuh"
+
+namespace rav {
+
+template <int D>
+struct BoxT {
+  static constexpr int NV = D == 2 ? 25 : 125;   // box nodes
+  static constexpr int NC = D * NV + 1;          // box positions
+  static constexpr int NON = 1 << D;             // owned nodes
+  static constexpr int NR = D * NON + 1;         // owned rows
+  static constexpr int RB = D == 2 ? 9 : 5;      // owned rows per thread in the RAV apply
+  static constexpr int NCH = NR / RB;            // threads per subdomain in the RAV apply
+};
+
+// Vertex tuple of subdomain p.
+__device__ __forceinline__ void vertex_of(const Geo& g, int64_t p, int* v) {
+  for (int a = 0; a < g.dim; ++a) { v[a] = (int)(p % (g.N + 1)); p /= (g.N + 1); }
+}
+// Box node a (per-axis offsets) of subdomain at vertex v is valid iff
+// 1 <= 2v - 2 + a <= 2N - 1 on every axis (inside, not on the boundary).
+__device__ __forceinline__ bool box_node_valid(const Geo& g, const int* v, const int* a) {
+  bool ok = true;
+  for (int d = 0; d < g.dim; ++d) {
+    const int J = 2 * v[d] - 2 + a[d];
+    ok &= (J >= 1) & (J <= 2 * g.N - 1);
+  }
+  return ok;
+}
+__device__ __forceinline__ void box_tuple(int D, int m, int* a) {
+  a[0] = m % 5;
+  a[1] = (m / 5) % 5;
+  a[2] = D == 3 ? m / 25 : 0;
+}
+
+// ---------------------------------------------------------------------------
+// Factorisation: one block per subdomain.  Writes the requested fp64 rows in
+// box coordinates, row-major: RAV rows = owned rows (NR), all rows otherwise (NC).
+template <int D, bool ALL>
+__global__ void __launch_bounds__(256) k_factor(Geo g, const int64_t* __restrict__ rp, const double* __restrict__ va,
+                                                int64_t first, int64_t count, double* __restrict__ out,
+                                                int* __restrict__ err) {
+  using B = BoxT<D>;
+  constexpr int NV = B::NV, NC = B::NC;
+  constexpr int NROW = ALL ? NC : B::NR;
+  constexpr int NRHS = 32;  // right-hand sides solved per batch
+  extern __shared__ double sm[];
+  double* K = sm;                  // NV x NV, lower triangle -> Cholesky factor
+  double* bv = K + NV * NV;        // NV x D  (B column of p_i, node-major)
+  double* w = bv + NV * D;         // NV x D  (A^{-1} b)
+  double* Z = w + NV * D;          // NRHS x NV solutions
+  __shared__ int valid[NV];
+  __shared__ double s_inv;
+  __shared__ int bad;
+  const int64_t pl = blockIdx.x;
+  if (pl >= count) return;
+  const int64_t p = first + pl;
+  int v[3] = {0, 0, 0};
+  vertex_of(g, p, v);
+  const int tid = threadIdx.x, nt = blockDim.x;
+  if (tid == 0) bad = 0;
+  for (int m = tid; m < NV; m += nt) {
+    int a[3];
+    box_tuple(D, m, a);
+    valid[m] = box_node_valid(g, v, a);
+  }
+  __syncthreads();
+  // K entries from velocity rows (component 0).  A free velocity row at node
+  // J lists its velocity columns over the tensor range of the nodes of its cells.
+  for (int e = tid; e < NV * NV; e += nt) {
+    const int m = e / NV, n = e % NV;
+    double val = (m == n) ? 1.0 : 0.0;
+    if (valid[m] && valid[n]) {
+      int am[3], an[3];
+      box_tuple(D, m, am);
+      box_tuple(D, n, an);
+      int64_t Jm[3] = {0, 0, 0}, Jn[3] = {0, 0, 0};
+      int64_t pos = 0, len = 1;
+      bool in = true;
+      for (int d = 0; d < D; ++d) {
+        Jm[d] = 2 * v[d] - 2 + am[d];
+        Jn[d] = 2 * v[d] - 2 + an[d];
+      }
+      for (int d = D - 1; d >= 0; --d) {
+        int64_t lo, hi;
+        if (Jm[d] & 1) { lo = Jm[d] - 1; hi = Jm[d] + 1; }
+        else { lo = Jm[d] - 2 < 0 ? 0 : Jm[d] - 2; hi = Jm[d] + 2 > 2 * g.N ? 2 * g.N : Jm[d] + 2; }
+        in &= (Jn[d] >= lo) & (Jn[d] <= hi);
+        pos = pos * (hi - lo + 1) + (Jn[d] - lo);
+        len *= hi - lo + 1;
+      }
+      val = 0.0;
+      if (in) {
+        const int64_t row = D * node_id(g, Jm);
+        val = va[rp[row] + pos];
+      }
+    }
+    K[m * NV + n] = val;
+  }
+  // b from the pressure row of p_i: columns = nodes [2v-2, 2v+2] (clipped) x components.
+  {
+    const int64_t prow = g.n_u + p;
+    for (int e = tid; e < NV * D; e += nt) {
+      const int m = e / D, c = e % D;
+      double val = 0.0;
+      if (valid[m]) {
+        int a[3];
+        box_tuple(D, m, a);
+        int64_t pos = 0;
+        for (int d = D - 1; d >= 0; --d) {
+          const int64_t lo = 2 * v[d] - 2 < 0 ? 0 : 2 * v[d] - 2;
+          const int64_t hi = 2 * v[d] + 2 > 2 * g.N ? 2 * g.N : 2 * v[d] + 2;
+          pos = pos * (hi - lo + 1) + (2 * v[d] - 2 + a[d] - lo);
+        }
+        val = va[rp[prow] + pos * D + c];
+      }
+      bv[m * D + c] = val;
+    }
+  }
+  __syncthreads();
+  // Cholesky K = L L^T (lower triangle, right-looking).
+  double dmax = 0.0;
+  for (int m = 0; m < NV; ++m) dmax = fmax(dmax, fabs(K[m * NV + m]));
+  for (int k = 0; k < NV; ++k) {
+    if (tid == 0) {
+      const double dkk = K[k * NV + k];
+      if (!(dkk > 1e-14 * dmax)) { bad = 1; K[k * NV + k] = 1.0; }
+      else K[k * NV + k] = sqrt(dkk);
+    }
+    __syncthreads();
+    const double lkk = K[k * NV + k];
+    for (int j = k + 1 + tid; j < NV; j += nt) K[j * NV + k] /= lkk;
+    __syncthreads();
+    const int rem = NV - k - 1;
+    for (int e = tid; e < rem * rem; e += nt) {
+      const int i = k + 1 + e / rem, j = k + 1 + e % rem;
+      if (j <= i) K[i * NV + j] -= K[i * NV + k] * K[j * NV + k];
+    }
+    __syncthreads();
+  }
+  // Solves with the factor: warp r handles right-hand side r of the batch.
+  const int warp = tid >> 5, lane = tid & 31, nwarp = nt >> 5;
+  auto solve_rhs = [&](double* z) {
+    for (int k = 0; k < NV; ++k) {  // L y = z
+      const double yk = z[k] / K[k * NV + k];
+      __syncwarp();
+      if (lane == 0) z[k] = yk;
+      for (int j = k + 1 + lane; j < NV; j += 32) z[j] -= K[j * NV + k] * yk;
+      __syncwarp();
+    }
+    for (int k = NV - 1; k >= 0; --k) {  // L^T x = y
+      const double xk = z[k] / K[k * NV + k];
+      __syncwarp();
+      if (lane == 0) z[k] = xk;
+      for (int j = lane; j < k; j += 32) z[j] -= K[k * NV + j] * xk;
+      __syncwarp();
+    }
+  };
+  // w = K^{-1} b, one component per warp.
+  for (int c = warp; c < D; c += nwarp) {
+    double* z = Z + c * NV;
+    for (int m = lane; m < NV; m += 32) z[m] = bv[m * D + c];
+    __syncwarp();
+    solve_rhs(z);
+    for (int m = lane; m < NV; m += 32) w[m * D + c] = z[m];
+  }
+  __syncthreads();
+  if (tid < 32) {
+    double s = 0.0;
+    for (int e = lane; e < NV * D; e += 32) s += bv[e] * w[e];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if (lane == 0) {
+      const double sch = -s;
+      double bmax = 0.0;
+      for (int e = 0; e < NV * D; ++e) bmax = fmax(bmax, fabs(bv[e]));
+      if (!(fabs(sch) > 1e-300) || bmax == 0.0) { bad = 1; s_inv = 0.0; }
+      else s_inv = 1.0 / sch;
+    }
+  }
+  __syncthreads();
+  const double si = s_inv;
+  double* orow = out + pl * (int64_t)NROW * NC;
+  // Pressure row (last row in both layouts): (n,c') -> -w[n,c'] / s, (p,p) -> 1/s.
+  for (int k = tid; k < NC; k += nt) orow[(int64_t)(NROW - 1) * NC + k] = k < NC - 1 ? -w[k] * si : si;
+  // Velocity rows: row (m,c) = [delta_cc' Kinv[m,n] + w[m,c] w[n,c'] / s ; -w[m,c] / s].
+  const int nnodes = ALL ? NV : B::NON;
+  for (int r0 = 0; r0 < nnodes; r0 += NRHS) {
+    const int nb = nnodes - r0 < NRHS ? nnodes - r0 : NRHS;
+    __syncthreads();
+    for (int r = warp; r < nb; r += nwarp) {
+      const int q = r0 + r;  // row node index (ALL: box node; RAV: owned node)
+      int m;
+      if (ALL) m = q;
+      else m = (2 + (q & 1)) + 5 * (2 + ((q >> 1) & 1)) + (D == 3 ? 25 * (2 + ((q >> 2) & 1)) : 0);
+      double* z = Z + r * NV;
+      for (int n = lane; n < NV; n += 32) z[n] = (n == m) ? 1.0 : 0.0;
+      __syncwarp();
+      if (valid[m]) solve_rhs(z);
+      __syncwarp();
+      for (int c = 0; c < D; ++c) {
+        const int orw = ALL ? m * D + c : q * D + c;
+        double* o = orow + (int64_t)orw * NC;
+        const bool vm = valid[m];
+        const double wm = w[m * D + c];
+        for (int k = lane; k < NC; k += 32) {
+          double val = 0.0;
+          if (vm) {
+            if (k < NC - 1) {
+              const int n = k / D, c2 = k % D;
+              val = (c2 == c ? z[n] : 0.0) + wm * w[k] * si;
+              if (!valid[n]) val = 0.0;
+            } else {
+              val = -wm * si;
+            }
+          }
+          o[k] = val;
+        }
+      }
+    }
+  }
+  __syncthreads();
+  if (tid == 0 && bad) atomicOr(err, 1);
+}
+
+// ---------------------------------------------------------------------------
+// Reduced-precision storage: round-to-nearest-even to a binary format with p
+// significand bits, minimum normal exponent emin, saturating at vmax.
+__device__ double round_fmt(double v, int p, int emin, double vmax) {
+  if (v == 0.0 || !isfinite(v)) return v;
+  int E;
+  frexp(v, &E);
+  int e = E - 1;
+  if (e < emin) e = emin;
+  const double quantum = ldexp(1.0, e - (p - 1));
+  double q = rint(v / quantum) * quantum;
+  q = q > vmax ? vmax : (q < -vmax ? -vmax : q);
+  return q;
+}
+
+template <typename T>
+struct Fmt;
+template <>
+struct Fmt<double> {
+  static __device__ double enc(double v) { return v; }
+  static __device__ double dec(double v, const float*) { return v; }
+  static constexpr bool scaled = false;
+};
+template <>
+struct Fmt<float> {
+  static __device__ float enc(double v) { return (float)round_fmt(v, 24, -126, 3.4028234663852886e38); }
+  static __device__ float dec(float v, const float*) { return v; }
+  static constexpr bool scaled = false;
+};
+template <>
+struct Fmt<__nv_bfloat16> {
+  static __device__ __nv_bfloat16 enc(double v) {
+    return __float2bfloat16_rn((float)round_fmt(v, 8, -126, 3.3895313892515355e38));
+  }
+  static __device__ float dec(__nv_bfloat16 v, const float*) { return __bfloat162float(v); }
+  static constexpr bool scaled = false;
+};
+struct fp8_t {
+  uint8_t bits;
+};
+template <>
+struct Fmt<fp8_t> {
+  static __device__ fp8_t enc(double v) {
+    const float q = (float)round_fmt(v, 4, -6, 448.0);
+    fp8_t r;
+    r.bits = (uint8_t)__nv_cvt_float_to_fp8(q, __NV_SATFINITE, __NV_E4M3);
+    return r;
+  }
+  static __device__ float dec(fp8_t v, const float* lut) { return lut[v.bits]; }
+  static constexpr bool scaled = true;
+};
+
+// Pack fp64 staging rows (box coordinates, row-major) into the RAV apply layout:
+// unit u = subdomain * NCH + chunk (RB consecutive owned rows); units grouped
+// by 32; element (u, jl, k) at ((u/32 * NC + k) * RB + jl) * 32 + u%32, so a
+// warp reads 32 consecutive elements per (k, jl).  fp8 rows carry an fp32 scale
+// max|row| / 448 (scale index (u/32 * RB + jl) * 32 + u%32).
+template <int D, typename T>
+__global__ void k_pack_rav(const double* __restrict__ stage, int64_t first, int64_t count, T* __restrict__ inv,
+                           float* __restrict__ scale) {
+  using B = BoxT<D>;
+  constexpr int NC = B::NC, NR = B::NR, RB = B::RB, NCH = B::NCH;
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;  // (local unit, jl)
+  if (t >= count * NR) return;
+  const int64_t ul = t / RB;
+  const int jl = (int)(t % RB);
+  const int64_t pl = ul / NCH;
+  const int h = (int)(ul % NCH);
+  const int j = h * RB + jl;
+  const int64_t u = first * NCH + ul;
+  const int64_t G = u >> 5;
+  const int lane = (int)(u & 31);
+  const double* row = stage + (pl * NR + j) * (int64_t)NC;
+  double s = 1.0;
+  if (Fmt<T>::scaled) {
+    double m = 0.0;
+    for (int k = 0; k < NC; ++k) m = fmax(m, fabs(row[k]));
+    s = m == 0.0 ? 1.0 : (double)(float)(m / 448.0);
+    scale[(G * RB + jl) * 32 + lane] = (float)s;
+  }
+  for (int k = 0; k < NC; ++k) inv[((G * NC + k) * RB + jl) * 32 + lane] = Fmt<T>::enc(row[k] / s);
+}
+
+// Full inverses (AV, MV): per subdomain column-major NC x NC (element (j,k) at k*NC + j).
+template <int D>
+__global__ void k_pack_full(const double* __restrict__ stage, int64_t first, int64_t count, double* __restrict__ inv) {
+  constexpr int NC = BoxT<D>::NC;
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= count * NC * NC) return;
+  const int64_t pl = t / (NC * NC);
+  const int e = (int)(t % (NC * NC));
+  const int j = e / NC, k = e % NC;
+  inv[(first + pl) * (int64_t)NC * NC + (int64_t)k * NC + j] = stage[t];
+}
+
+// ---------------------------------------------------------------------------
+// RAV apply (Eq. 13): one thread per unit; gathers the NC residual entries of
+// its subdomain, forms RB owned rows of L_i^{-1} r_i and adds omega_i times
+// them to the owned DoFs of x.  Owned DoFs of different subdomains are
+// disjoint, so the writes need no atomics.
+template <int D, typename T>
+__global__ void __launch_bounds__(128) k_rav_apply(Geo g, const T* __restrict__ inv, const float* __restrict__ scale,
+                                                   const double* __restrict__ omega, const double* __restrict__ r,
+                                                   double* __restrict__ x, int64_t units) {
+  using B = BoxT<D>;
+  constexpr int NC = B::NC, RB = B::RB, NCH = B::NCH;
+  using Acc = typename std::conditional<std::is_same<T, double>::value, double, float>::type;
+  __shared__ float lut[256];
+  if (Fmt<T>::scaled) {
+    for (int i = threadIdx.x; i < 256; i += blockDim.x) {
+      __half_raw h = __nv_cvt_fp8_to_halfraw((__nv_fp8_storage_t)i, __NV_E4M3);
+      lut[i] = __half2float(__half(h));
+    }
+    __syncthreads();
+  }
+  const int64_t u = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (u >= units) return;
+  const int64_t p = u / NCH;
+  const int h = (int)(u % NCH);
+  int v[3] = {0, 0, 0};
+  vertex_of(g, p, v);
+  const int M = (int)g.M;
+  int alo[3] = {0, 0, 0}, ahi[3] = {0, 0, 0};
+  for (int d = 0; d < 3; ++d) {
+    if (d < D) {
+      alo[d] = 2 - 2 * v[d] > 0 ? 2 - 2 * v[d] : 0;
+      ahi[d] = 2 * g.N - 2 * v[d] + 2 < 4 ? 2 * g.N - 2 * v[d] + 2 : 4;
+    }
+  }
+  int64_t base = 0;
+  for (int d = D - 1; d >= 0; --d) base = base * M + (2 * v[d] - 2);
+  base *= D;
+  const T* ip = inv + ((u >> 5) * NC * RB) * 32 + (u & 31);
+  Acc acc[RB];
+#pragma unroll
+  for (int j = 0; j < RB; ++j) acc[j] = 0;
+  int k = 0;
+  for (int a2 = 0; a2 < (D == 3 ? 5 : 1); ++a2) {
+    const bool v2 = D == 2 || (a2 >= alo[2] && a2 <= ahi[2]);
+    for (int a1 = 0; a1 < 5; ++a1) {
+      const bool v1 = v2 && a1 >= alo[1] && a1 <= ahi[1];
+      const int64_t rowoff = base + (int64_t)D * M * (a1 + (int64_t)M * a2);
+#pragma unroll
+      for (int a0 = 0; a0 < 5; ++a0) {
+        const bool vv = v1 && a0 >= alo[0] && a0 <= ahi[0];
+#pragma unroll
+        for (int c = 0; c < D; ++c) {
+          const double rv = vv ? r[rowoff + D * a0 + c] : 0.0;
+          const Acc ra = (Acc)rv;
+#pragma unroll
+          for (int j = 0; j < RB; ++j) acc[j] += (Acc)Fmt<T>::dec(ip[(k * RB + j) * 32], lut) * ra;
+          ++k;
+        }
+      }
+    }
+  }
+  {
+    const Acc ra = (Acc)r[g.n_u + p];
+#pragma unroll
+    for (int j = 0; j < RB; ++j) acc[j] += (Acc)Fmt<T>::dec(ip[(k * RB + j) * 32], lut) * ra;
+  }
+  const double om = omega[p];
+#pragma unroll
+  for (int jl = 0; jl < RB; ++jl) {
+    const int j = h * RB + jl;
+    Acc y = acc[jl];
+    if (Fmt<T>::scaled) y *= scale[((u >> 5) * RB + jl) * 32 + (u & 31)];
+    if (j < B::NR - 1) {
+      const int q = j / D, c = j % D;
+      int64_t J[3] = {0, 0, 0};
+      bool ok = true;
+      for (int d = 0; d < D; ++d) {
+        J[d] = 2 * v[d] + ((q >> d) & 1);
+        ok &= (J[d] >= 1) & (J[d] <= 2 * g.N - 1);
+      }
+      if (ok) x[D * node_id(g, J) + c] += om * (double)y;
+    } else {
+      x[g.n_u + p] += om * (double)y;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Full-inverse subdomain solve shared by AV and MV: one warp per subdomain,
+// rloc in shared memory, y = L_i^{-1} rloc with the column-major inverse.
+template <int D>
+__device__ void warp_full_solve(const double* __restrict__ Inv, const double* rloc, double* y) {
+  constexpr int NC = BoxT<D>::NC;
+  const int lane = threadIdx.x & 31;
+  for (int j = lane; j < NC; j += 32) {
+    double s = 0.0;
+    for (int k = 0; k < NC; ++k) s += Inv[(int64_t)k * NC + j] * rloc[k];
+    y[j] = s;
+  }
+  __syncwarp();
+}
+
+// Global DoF of box position k of the subdomain at vertex v (-1 if not in it).
+template <int D>
+__device__ __forceinline__ int64_t box_dof(const Geo& g, const int* v, int64_t p, int k) {
+  constexpr int NC = BoxT<D>::NC;
+  if (k == NC - 1) return g.n_u + p;
+  int a[3];
+  box_tuple(D, k / D, a);
+  if (!box_node_valid(g, v, a)) return -1;
+  int64_t J[3] = {0, 0, 0};
+  for (int d = 0; d < D; ++d) J[d] = 2 * v[d] - 2 + a[d];
+  return D * node_id(g, J) + k % D;
+}
+
+// AV (Eq. 12), step 1: corr[p][k] = omega_p (L_p^{-1} r_p)_k for every box position.
+template <int D>
+__global__ void k_av_corr(Geo g, const double* __restrict__ inv, const double* __restrict__ omega,
+                          const double* __restrict__ r, double* __restrict__ corr) {
+  constexpr int NC = BoxT<D>::NC;
+  constexpr int WPB = 4;
+  __shared__ double rl[WPB][NC], yl[WPB][NC];
+  const int wi = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t p = blockIdx.x * (int64_t)WPB + wi;
+  if (p >= g.n_p) return;
+  int v[3] = {0, 0, 0};
+  vertex_of(g, p, v);
+  for (int k = lane; k < NC; k += 32) {
+    const int64_t dof = box_dof<D>(g, v, p, k);
+    rl[wi][k] = dof >= 0 ? r[dof] : 0.0;
+  }
+  __syncwarp();
+  warp_full_solve<D>(inv + p * (int64_t)NC * NC, rl[wi], yl[wi]);
+  const double om = omega[p];
+  for (int k = lane; k < NC; k += 32) corr[p * NC + k] = om * yl[wi][k];
+}
+
+// AV, step 2: x[dof] += sum over the subdomains containing dof (ascending) of corr.
+template <int D>
+__global__ void k_av_gather(Geo g, const double* __restrict__ corr, double* __restrict__ x) {
+  constexpr int NC = BoxT<D>::NC;
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= g.n) return;
+  if (i >= g.n_u) {
+    x[i] += corr[(i - g.n_u) * NC + NC - 1];
+    return;
+  }
+  int64_t I[3] = {0, 0, 0};
+  int c;
+  vel_node(g, i, I, c);
+  if (node_on_boundary(g, I)) return;
+  int lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0};
+  for (int d = 0; d < D; ++d) {
+    lo[d] = (int)((I[d] - 1) >> 1);  // vertices v with 2v-2 <= I <= 2v+2
+    hi[d] = (int)((I[d] + 2) >> 1);
+    lo[d] = lo[d] < 0 ? 0 : lo[d];
+    hi[d] = hi[d] > g.N ? g.N : hi[d];
+  }
+  double s = 0.0;
+  for (int v2 = (D == 3 ? lo[2] : 0); v2 <= (D == 3 ? hi[2] : 0); ++v2)
+    for (int v1 = lo[1]; v1 <= hi[1]; ++v1)
+      for (int v0 = lo[0]; v0 <= hi[0]; ++v0) {
+        const int vv[3] = {v0, v1, v2};
+        int64_t p = 0;
+        int m = 0;
+        for (int d = D - 1; d >= 0; --d) {
+          p = p * (g.N + 1) + vv[d];
+          m = m * 5 + (int)(I[d] - (2 * vv[d] - 2));
+        }
+        s += corr[p * NC + m * D + c];
+      }
+  x[i] += s;
+}
+
+// MV (Eq. 11 with the residual refresh of Eq. 15) over one colour class:
+// subdomains whose vertices agree mod 4 on every axis touch disjoint DoFs and
+// read no DoF another one of the class writes, so the class is processed in
+// parallel and equals the sequential sweep over it.
+template <int D>
+__global__ void k_mv_colour(Geo g, const int64_t* __restrict__ rp, const int32_t* __restrict__ ci,
+                            const double* __restrict__ va, const double* __restrict__ inv,
+                            const double* __restrict__ omega, const double* __restrict__ b, double* __restrict__ x,
+                            int colour) {
+  constexpr int NC = BoxT<D>::NC;
+  constexpr int WPB = 4;
+  __shared__ double rl[WPB][NC], yl[WPB][NC];
+  __shared__ int64_t dl[WPB][NC];
+  const int wi = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  // enumerate the vertices of this colour: v_a = col_a + 4 t_a
+  int col[3] = {colour & 3, (colour >> 2) & 3, (colour >> 4) & 3};
+  int cnt[3] = {1, 1, 1};
+  int64_t tot = 1;
+  for (int d = 0; d < D; ++d) {
+    cnt[d] = col[d] <= g.N ? (g.N - col[d]) / 4 + 1 : 0;
+    tot *= cnt[d];
+  }
+  const int64_t t = blockIdx.x * (int64_t)WPB + wi;
+  if (t >= tot) return;
+  int v[3] = {0, 0, 0};
+  {
+    int64_t tt = t;
+    for (int d = 0; d < D; ++d) { v[d] = col[d] + 4 * (int)(tt % cnt[d]); tt /= cnt[d]; }
+  }
+  int64_t p = 0;
+  for (int d = D - 1; d >= 0; --d) p = p * (g.N + 1) + v[d];
+  for (int k = lane; k < NC; k += 32) {
+    const int64_t dof = box_dof<D>(g, v, p, k);
+    dl[wi][k] = dof;
+    double s = 0.0;
+    if (dof >= 0) {
+      s = b[dof];
+      for (int64_t q = rp[dof]; q < rp[dof + 1]; ++q) s -= va[q] * x[ci[q]];
+    }
+    rl[wi][k] = s;
+  }
+  __syncwarp();
+  warp_full_solve<D>(inv + p * (int64_t)NC * NC, rl[wi], yl[wi]);
+  const double om = omega[p];
+  for (int k = lane; k < NC; k += 32)
+    if (dl[wi][k] >= 0) x[dl[wi][k]] += om * yl[wi][k];
+}
+
+// ---------------------------------------------------------------------------
+// Inspection: compact (sorted) subdomain lists and the stored rows expanded.
+template <int D>
+__global__ void k_patch_count(Geo g, int32_t* __restrict__ cnt) {
+  constexpr int NC = BoxT<D>::NC;
+  const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (p >= g.n_p) return;
+  int v[3] = {0, 0, 0};
+  vertex_of(g, p, v);
+  int c = 0;
+  for (int k = 0; k < NC; k += D) {
+    if (k == NC - 1) { ++c; break; }
+    int a[3];
+    box_tuple(D, k / D, a);
+    if (box_node_valid(g, v, a)) c += D;
+  }
+  cnt[p] = c;
+}
+template <int D>
+__global__ void k_patch_list(Geo g, const int32_t* __restrict__ off, int32_t* __restrict__ dofs) {
+  constexpr int NC = BoxT<D>::NC;
+  const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (p >= g.n_p) return;
+  int v[3] = {0, 0, 0};
+  vertex_of(g, p, v);
+  int32_t pos = off[p];
+  for (int k = 0; k < NC; ++k) {
+    const int64_t dof = box_dof<D>(g, v, p, k);
+    if (dof >= 0) dofs[pos++] = (int32_t)dof;
+  }
+}
+// owner(velocity DoF at node I) = vertex floor(I/2); owner(p_i) = i; Dirichlet -1.
+__global__ void k_owner(Geo g, int32_t* __restrict__ owner) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= g.n) return;
+  if (i >= g.n_u) { owner[i] = (int32_t)(i - g.n_u); return; }
+  int64_t I[3] = {0, 0, 0};
+  int c;
+  vel_node(g, i, I, c);
+  if (node_on_boundary(g, I)) { owner[i] = -1; return; }
+  int64_t v[3];
+  for (int d = 0; d < g.dim; ++d) v[d] = I[d] >> 1;
+  owner[i] = (int32_t)vert_id(g, v);
+}
+__global__ void k_scan_i32(const int32_t* __restrict__ cnt, int64_t n, int32_t* __restrict__ off) {
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    int32_t a = 0;
+    for (int64_t i = 0; i < n; ++i) { off[i] = a; a += cnt[i]; }
+    off[n] = a;
+  }
+}
+
+// Expanded stored rows for subdomains [first, first+count): out[p][j][k] in
+// compact sorted order, padded to rows_max x cols_max.
+template <int D, typename T>
+__global__ void k_export_rav(Geo g, const T* __restrict__ inv, const float* __restrict__ scale, int64_t first,
+                             int64_t count, double* __restrict__ out) {
+  using B = BoxT<D>;
+  constexpr int NC = B::NC, NR = B::NR, RB = B::RB, NCH = B::NCH;
+  __shared__ float lut[256];
+  __shared__ int colmap[NC], rowmap[NR];
+  __shared__ int ncol, nrow;
+  if (Fmt<T>::scaled) {
+    for (int i = threadIdx.x; i < 256; i += blockDim.x) {
+      __half_raw h = __nv_cvt_fp8_to_halfraw((__nv_fp8_storage_t)i, __NV_E4M3);
+      lut[i] = __half2float(__half(h));
+    }
+  }
+  const int64_t p = first + blockIdx.x;
+  int v[3] = {0, 0, 0};
+  vertex_of(g, p, v);
+  if (threadIdx.x == 0) {
+    int c = 0;
+    for (int k = 0; k < NC; ++k)
+      if (box_dof<D>(g, v, p, k) >= 0) colmap[c++] = k;
+    ncol = c;
+    int rr = 0;
+    for (int j = 0; j < NR; ++j) {
+      int k;
+      if (j == NR - 1) k = NC - 1;
+      else {
+        const int q = j / D;
+        const int m = (2 + (q & 1)) + 5 * (2 + ((q >> 1) & 1)) + (D == 3 ? 25 * (2 + ((q >> 2) & 1)) : 0);
+        k = m * D + j % D;
+      }
+      if (box_dof<D>(g, v, p, k) >= 0) rowmap[rr++] = j;
+    }
+    nrow = rr;
+  }
+  __syncthreads();
+  double* o = out + blockIdx.x * (int64_t)NR * NC;
+  for (int e = threadIdx.x; e < NR * NC; e += blockDim.x) {
+    const int jr = e / NC, kc = e % NC;
+    double val = 0.0;
+    if (jr < nrow && kc < ncol) {
+      const int j = rowmap[jr], k = colmap[kc];
+      const int64_t u = p * NCH + j / RB;
+      const int jl = j % RB;
+      val = (double)Fmt<T>::dec(inv[(((u >> 5) * NC + k) * RB + jl) * 32 + (u & 31)], lut);
+      if (Fmt<T>::scaled) val *= (double)scale[((u >> 5) * RB + jl) * 32 + (u & 31)];
+    }
+    o[e] = val;
+  }
+}
+template <int D>
+__global__ void k_export_full(Geo g, const double* __restrict__ inv, int64_t first, int64_t count,
+                              double* __restrict__ out) {
+  constexpr int NC = BoxT<D>::NC;
+  __shared__ int colmap[NC];
+  __shared__ int ncol;
+  const int64_t p = first + blockIdx.x;
+  int v[3] = {0, 0, 0};
+  vertex_of(g, p, v);
+  if (threadIdx.x == 0) {
+    int c = 0;
+    for (int k = 0; k < NC; ++k)
+      if (box_dof<D>(g, v, p, k) >= 0) colmap[c++] = k;
+    ncol = c;
+  }
+  __syncthreads();
+  double* o = out + blockIdx.x * (int64_t)NC * NC;
+  for (int e = threadIdx.x; e < NC * NC; e += blockDim.x) {
+    const int jr = e / NC, kc = e % NC;
+    double val = 0.0;
+    if (jr < ncol && kc < ncol) val = inv[p * (int64_t)NC * NC + (int64_t)colmap[kc] * NC + colmap[jr]];
+    o[e] = val;
+  }
+}
+
+__global__ void k_fill(double* __restrict__ a, int64_t n, double v) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    a[i] = v;
+}
+__global__ void k_f32_to_f64(const float* __restrict__ a, int64_t n, double* __restrict__ b) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    b[i] = (double)a[i];
+}
+
+}  // namespace rav
+
+using namespace rav;
+
+static size_t elem_size(int prec) {
+  return prec == RAV_F64 ? 8 : prec == RAV_F32 ? 4 : prec == RAV_BF16 ? 2 : 1;
+}
+
+template <int D>
+static int setup_level(rav_smoother* sm, int l, cudaStream_t s, int* err_dev) {
+  using B = BoxT<D>;
+  rav_mg* mg = sm->mg;
+  const Level& L = mg->lev[l];
+  SmLevel& S_ = sm->lev[l];
+  const Geo& g = L.g;
+  S_.np = g.n_p;
+  const bool all = sm->kind != RAV_RAV;
+  const int NROW = all ? B::NC : B::NR;
+  RAV_CUDA(cudaMalloc(&S_.omega, sizeof(double) * S_.np));
+  k_fill<<<grid_for(S_.np, 256), 256, 0, s>>>(S_.omega, S_.np, sm->omega);
+  if (all) {
+    RAV_CUDA(cudaMalloc(&S_.inv, sizeof(double) * S_.np * B::NC * B::NC));
+    if (sm->kind == RAV_AV) RAV_CUDA(cudaMalloc(&S_.corr, sizeof(double) * S_.np * B::NC));
+  } else {
+    S_.units = S_.np * B::NCH;
+    const int64_t groups = (S_.units + 31) / 32;
+    RAV_CUDA(cudaMalloc(&S_.inv, elem_size(sm->prec) * groups * 32 * B::NC * B::RB));
+    RAV_CUDA(cudaMemsetAsync(S_.inv, 0, elem_size(sm->prec) * groups * 32 * B::NC * B::RB, s));
+    if (sm->prec == RAV_FP8) RAV_CUDA(cudaMalloc(&S_.scale, sizeof(float) * groups * 32 * B::RB));
+  }
+  // factorise in batches; staging rows in fp64
+  const int64_t batch = std::min<int64_t>(S_.np, all ? 8192 : 32768);
+  double* stage = nullptr;
+  RAV_CUDA(cudaMallocAsync(&stage, sizeof(double) * batch * NROW * B::NC, s));
+  const size_t smem = sizeof(double) * (B::NV * B::NV + 2 * B::NV * D + 32 * B::NV);
+  auto kf = all ? k_factor<D, true> : k_factor<D, false>;
+  RAV_CUDA(cudaFuncSetAttribute(kf, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  const int threads = D == 2 ? 128 : 256;
+  for (int64_t f = 0; f < S_.np; f += batch) {
+    const int64_t cnt = std::min<int64_t>(batch, S_.np - f);
+    kf<<<(unsigned)cnt, threads, smem, s>>>(g, L.rp, L.va, f, cnt, stage, err_dev);
+    if (all) {
+      const int64_t tot = cnt * B::NC * B::NC;
+      k_pack_full<D><<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(stage, f, cnt, (double*)S_.inv);
+    } else {
+      const int64_t tot = cnt * B::NR;
+      const unsigned gb = (unsigned)((tot + 127) / 128);
+      switch (sm->prec) {
+        case RAV_F64: k_pack_rav<D, double><<<gb, 128, 0, s>>>(stage, f, cnt, (double*)S_.inv, S_.scale); break;
+        case RAV_F32: k_pack_rav<D, float><<<gb, 128, 0, s>>>(stage, f, cnt, (float*)S_.inv, S_.scale); break;
+        case RAV_BF16:
+          k_pack_rav<D, __nv_bfloat16><<<gb, 128, 0, s>>>(stage, f, cnt, (__nv_bfloat16*)S_.inv, S_.scale);
+          break;
+        default: k_pack_rav<D, fp8_t><<<gb, 128, 0, s>>>(stage, f, cnt, (fp8_t*)S_.inv, S_.scale); break;
+      }
+    }
+    RAV_CUDA(cudaGetLastError());
+  }
+  RAV_CUDA(cudaFreeAsync(stage, s));
+  return RAV_OK;
+}
+
+extern "C" int vanka_setup(rav_mg* mg, int kind, int precision, double omega, rav_stream stream,
+                           rav_smoother** out) {
+  if (!mg || !out || (kind != RAV_RAV && kind != RAV_AV && kind != RAV_MV_COLOURED)) return RAV_ERR_ARG;
+  if (precision < RAV_F64 || precision > RAV_FP8) return RAV_ERR_ARG;
+  if (kind != RAV_RAV && precision != RAV_F64) return RAV_ERR_ARG;
+  cudaStream_t s = S(stream);
+  *out = nullptr;
+  rav_smoother* sm = new rav_smoother();
+  sm->mg = mg;
+  sm->kind = kind;
+  sm->prec = precision;
+  sm->omega = omega;
+  int* err_dev = nullptr;
+  int rc = RAV_OK;
+  if (cudaMalloc(&err_dev, sizeof(int)) != cudaSuccess) { delete sm; return RAV_ERR_CUDA; }
+  cudaMemsetAsync(err_dev, 0, sizeof(int), s);
+  for (int l = 1; l < mg->nlev && rc == RAV_OK; ++l)
+    rc = mg->dim == 2 ? setup_level<2>(sm, l, s, err_dev) : setup_level<3>(sm, l, s, err_dev);
+  int err = 0;
+  if (rc == RAV_OK) {
+    if (cudaMemcpyAsync(&err, err_dev, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+      rc = RAV_ERR_CUDA;
+    else if (err)
+      rc = RAV_ERR_SINGULAR_PATCH;
+  }
+  cudaFree(err_dev);
+  if (rc != RAV_OK) {
+    vanka_destroy(sm);
+    return rc;
+  }
+  *out = sm;
+  return RAV_OK;
+}
+
+extern "C" void vanka_destroy(rav_smoother* sm) {
+  if (!sm) return;
+  cudaDeviceSynchronize();
+  for (cudaEvent_t e : sm->ev_free) cudaEventDestroy(e);
+  for (int l = 0; l < kMaxLevels; ++l)
+    for (auto& pr : sm->ev_used[l]) {
+      cudaEventDestroy(pr.first);
+      cudaEventDestroy(pr.second);
+    }
+  for (int l = 0; l < kMaxLevels; ++l) {
+    cudaFree(sm->lev[l].inv);
+    cudaFree(sm->lev[l].scale);
+    cudaFree(sm->lev[l].omega);
+    cudaFree(sm->lev[l].corr);
+  }
+  delete sm;
+}
+
+extern "C" int rav_set_patch_omega(rav_smoother* sm, int level, const float* w, rav_stream stream) {
+  if (!sm || !w || level < 1 || level >= sm->mg->nlev) return RAV_ERR_ARG;
+  const int64_t n = sm->lev[level].np;
+  k_f32_to_f64<<<grid_for(n, 256), 256, 0, S(stream)>>>(w, n, sm->lev[level].omega);
+  RAV_CUDA(cudaGetLastError());
+  return RAV_OK;
+}
+
+static cudaEvent_t take_event(rav_smoother* sm) {
+  if (sm->ev_free.empty()) {
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+    return e;
+  }
+  cudaEvent_t e = sm->ev_free.back();
+  sm->ev_free.pop_back();
+  return e;
+}
+
+static int apply_impl(rav_smoother* sm, int level, const double* r, double* x, cudaStream_t s) {
+  rav_mg* mg = sm->mg;
+  Level& L = mg->lev[level];
+  SmLevel& SL = sm->lev[level];
+  const Geo& g = L.g;
+  const int D = g.dim;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (sm->prof) {
+    e0 = take_event(sm);
+    e1 = take_event(sm);
+    if (!e0 || !e1) return RAV_ERR_CUDA;
+    RAV_CUDA(cudaEventRecord(e0, s));
+  }
+  if (sm->kind == RAV_AV) {
+    const unsigned gb = (unsigned)((g.n_p + 3) / 4);
+    const int gg = (int)((g.n + 255) / 256);
+    if (D == 2) {
+      k_av_corr<2><<<gb, 128, 0, s>>>(g, (double*)SL.inv, SL.omega, r, SL.corr);
+      k_av_gather<2><<<gg, 256, 0, s>>>(g, SL.corr, x);
+    } else {
+      k_av_corr<3><<<gb, 128, 0, s>>>(g, (double*)SL.inv, SL.omega, r, SL.corr);
+      k_av_gather<3><<<gg, 256, 0, s>>>(g, SL.corr, x);
+    }
+    note_launch(2);
+  } else {
+    const unsigned gb = (unsigned)((SL.units + 127) / 128);
+#define RAV_APPLY(DD, T) \
+  k_rav_apply<DD, T><<<gb, 128, 0, s>>>(g, (const T*)SL.inv, SL.scale, SL.omega, r, x, SL.units)
+    if (D == 2) {
+      switch (sm->prec) {
+        case RAV_F64: RAV_APPLY(2, double); break;
+        case RAV_F32: RAV_APPLY(2, float); break;
+        case RAV_BF16: RAV_APPLY(2, __nv_bfloat16); break;
+        default: RAV_APPLY(2, fp8_t); break;
+      }
+    } else {
+      switch (sm->prec) {
+        case RAV_F64: RAV_APPLY(3, double); break;
+        case RAV_F32: RAV_APPLY(3, float); break;
+        case RAV_BF16: RAV_APPLY(3, __nv_bfloat16); break;
+        default: RAV_APPLY(3, fp8_t); break;
+      }
+    }
+#undef RAV_APPLY
+    note_launch();
+  }
+  RAV_CUDA(cudaGetLastError());
+  if (sm->prof) {
+    RAV_CUDA(cudaEventRecord(e1, s));
+    sm->ev_used[level].push_back({e0, e1});
+  }
+  return RAV_OK;
+}
+
+int rav_smooth_impl(rav_smoother* sm, int level, double* x, const double* b, int steps, cudaStream_t s) {
+  rav_mg* mg = sm->mg;
+  Level& L = mg->lev[level];
+  SmLevel& SL = sm->lev[level];
+  const Geo& g = L.g;
+  const int D = g.dim;
+  for (int it = 0; it < steps; ++it) {
+    if (sm->kind == RAV_MV_COLOURED) {
+      const int ncol = D == 2 ? 16 : 64;
+      for (int c = 0; c < ncol; ++c) {
+        int cnt = 1;
+        for (int d = 0; d < D; ++d) {
+          const int cd = (c >> (2 * d)) & 3;
+          cnt *= cd <= g.N ? (g.N - cd) / 4 + 1 : 0;
+        }
+        if (cnt == 0) continue;
+        const unsigned gb = (unsigned)((cnt + 3) / 4);
+        if (D == 2) k_mv_colour<2><<<gb, 128, 0, s>>>(g, L.rp, L.ci, L.va, (double*)SL.inv, SL.omega, b, x, c);
+        else k_mv_colour<3><<<gb, 128, 0, s>>>(g, L.rp, L.ci, L.va, (double*)SL.inv, SL.omega, b, x, c);
+        note_launch();
+      }
+      RAV_CUDA(cudaGetLastError());
+      continue;
+    }
+    RAV_TRY(residual_impl(mg, level, x, b, L.r, nullptr, s));
+    RAV_TRY(apply_impl(sm, level, L.r, x, s));
+    RAV_CUDA(cudaGetLastError());
+  }
+  return RAV_OK;
+}
+
+extern "C" int vanka_apply(rav_smoother* sm, int level, const double* r, double* x, rav_stream stream) {
+  if (!sm || !x || !r || level < 1 || level >= sm->mg->nlev || sm->kind == RAV_MV_COLOURED) return RAV_ERR_ARG;
+  return apply_impl(sm, level, r, x, S(stream));
+}
+
+extern "C" int vanka_smooth(rav_smoother* sm, int level, double* x, const double* b, int steps, rav_stream stream) {
+  if (!sm || !x || !b || level < 1 || level >= sm->mg->nlev || steps < 0) return RAV_ERR_ARG;
+  return rav_smooth_impl(sm, level, x, b, steps, S(stream));
+}
+
+extern "C" int rav_get_patch_counts(const rav_smoother* sm, int level, int64_t out[2]) {
+  if (!sm || !out || level < 1 || level >= sm->mg->nlev) return RAV_ERR_ARG;
+  const Geo& g = sm->mg->lev[level].g;
+  // closed form: per axis the box positions inside the domain interior
+  int64_t tot = 0;
+  std::vector<int64_t> per(g.N + 1);
+  for (int v = 0; v <= g.N; ++v) {
+    int c = 0;
+    for (int a = 0; a < 5; ++a) {
+      const int J = 2 * v - 2 + a;
+      c += (J >= 1 && J <= 2 * g.N - 1);
+    }
+    per[v] = c;
+  }
+  if (g.dim == 2) {
+    for (int v1 = 0; v1 <= g.N; ++v1)
+      for (int v0 = 0; v0 <= g.N; ++v0) tot += 2 * per[v0] * per[v1] + 1;
+  } else {
+    for (int v2 = 0; v2 <= g.N; ++v2)
+      for (int v1 = 0; v1 <= g.N; ++v1)
+        for (int v0 = 0; v0 <= g.N; ++v0) tot += 3 * per[v0] * per[v1] * per[v2] + 1;
+  }
+  out[0] = g.n_p;
+  out[1] = tot;
+  return RAV_OK;
+}
+
+extern "C" int rav_get_patches(const rav_smoother* sm, int level, int32_t* off, int32_t* dofs, int32_t* owner,
+                               rav_stream stream) {
+  if (!sm || level < 1 || level >= sm->mg->nlev || !off || !dofs || !owner) return RAV_ERR_ARG;
+  const Geo& g = sm->mg->lev[level].g;
+  cudaStream_t s = S(stream);
+  int32_t* cnt = nullptr;
+  RAV_CUDA(cudaMallocAsync(&cnt, sizeof(int32_t) * g.n_p, s));
+  const int gb = (int)((g.n_p + 127) / 128);
+  if (g.dim == 2) k_patch_count<2><<<gb, 128, 0, s>>>(g, cnt);
+  else k_patch_count<3><<<gb, 128, 0, s>>>(g, cnt);
+  k_scan_i32<<<1, 32, 0, s>>>(cnt, g.n_p, off);
+  if (g.dim == 2) k_patch_list<2><<<gb, 128, 0, s>>>(g, off, dofs);
+  else k_patch_list<3><<<gb, 128, 0, s>>>(g, off, dofs);
+  k_owner<<<(int)((g.n + 255) / 256), 256, 0, s>>>(g, owner);
+  RAV_CUDA(cudaGetLastError());
+  RAV_CUDA(cudaFreeAsync(cnt, s));
+  return RAV_OK;
+}
+
+extern "C" int rav_get_inverse_rows(const rav_smoother* sm, int level, int64_t first, int64_t count, double* out,
+                                    rav_stream stream) {
+  if (!sm || !out || level < 1 || level >= sm->mg->nlev) return RAV_ERR_ARG;
+  const SmLevel& SL = sm->lev[level];
+  const Geo& g = sm->mg->lev[level].g;
+  if (first < 0 || count < 0 || first + count > SL.np) return RAV_ERR_ARG;
+  if (count == 0) return RAV_OK;
+  cudaStream_t s = S(stream);
+  const unsigned gb = (unsigned)count;
+  if (sm->kind != RAV_RAV) {
+    if (g.dim == 2) k_export_full<2><<<gb, 256, 0, s>>>(g, (const double*)SL.inv, first, count, out);
+    else k_export_full<3><<<gb, 256, 0, s>>>(g, (const double*)SL.inv, first, count, out);
+  } else {
+#define RAV_EXP(DD, T) k_export_rav<DD, T><<<gb, 256, 0, s>>>(g, (const T*)SL.inv, SL.scale, first, count, out)
+    if (g.dim == 2) {
+      switch (sm->prec) {
+        case RAV_F64: RAV_EXP(2, double); break;
+        case RAV_F32: RAV_EXP(2, float); break;
+        case RAV_BF16: RAV_EXP(2, __nv_bfloat16); break;
+        default: RAV_EXP(2, fp8_t); break;
+      }
+    } else {
+      switch (sm->prec) {
+        case RAV_F64: RAV_EXP(3, double); break;
+        case RAV_F32: RAV_EXP(3, float); break;
+        case RAV_BF16: RAV_EXP(3, __nv_bfloat16); break;
+        default: RAV_EXP(3, fp8_t); break;
+      }
+    }
+#undef RAV_EXP
+  }
+  RAV_CUDA(cudaGetLastError());
+  return RAV_OK;
+}
+
+extern "C" int rav_profile_enable(rav_smoother* sm, int enable) {
+  if (!sm) return RAV_ERR_ARG;
+  sm->prof = enable != 0;
+  return RAV_OK;
+}
+
+extern "C" int rav_profile_read(rav_smoother* sm, int level, int64_t* launches, double* total_ms) {
+  if (!sm || !launches || !total_ms || level < 1 || level >= sm->mg->nlev) return RAV_ERR_ARG;
+  double tot = 0.0;
+  int64_t cnt = 0;
+  for (auto& pr : sm->ev_used[level]) {
+    RAV_CUDA(cudaEventSynchronize(pr.second));
+    float ms = 0.0f;
+    RAV_CUDA(cudaEventElapsedTime(&ms, pr.first, pr.second));
+    tot += ms;
+    ++cnt;
+    sm->ev_free.push_back(pr.first);
+    sm->ev_free.push_back(pr.second);
+  }
+  sm->ev_used[level].clear();
+  *launches = cnt;
+  *total_ms = tot;
+  return RAV_OK;
+}

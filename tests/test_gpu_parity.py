@@ -1,0 +1,307 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Bars: indices and patch/owner lists bit-exact; assembled values and
+transfers to 1e-13 relative; one FP64 smoothing step (RAV, AV, MV) to 1e-12
+relative; per-cycle convergence factors within 2 %; reduced-precision codes
+bit-exact for the same fp64 input; reduced-precision steps within the error
+the format allows.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2103_10127_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA device", allow_module_level=True)
+
+import paper_2103_10127_gb300 as R  # noqa: E402
+
+
+def make_pair(dim, N, nlev, graded=False, nblobs=0, bc=O.BC_CAVITY, eta0=1.0, seed=21, s_max=2.0):
+    coords = inputs.graded_coordinates(N, 4.0, dim) if graded else None
+    blobs = inputs.viscosity_blobs(seed, k=nblobs, s_max=s_max) if nblobs else None
+    mg = R.Multigrid(dim, N, nlev, coords=coords, eta0=eta0, blobs=blobs, bc=bc)
+    orc = O.Oracle(dim, N, nlev, coords=coords, eta0=eta0, blobs=blobs, bc=bc)
+    return mg, orc
+
+
+CASES = [
+    dict(dim=2, N=8, nlev=3),
+    dict(dim=2, N=12, nlev=2, graded=True, nblobs=6, bc=O.BC_NOSLIP),
+    dict(dim=3, N=4, nlev=2, nblobs=4),
+    dict(dim=3, N=6, nlev=2, graded=True, nblobs=5, bc=O.BC_NOSLIP),
+]
+IDS = ["2d-8-cavity", "2d-12-graded-blobs", "3d-4-blobs", "3d-6-graded-blobs"]
+
+
+def cpu(t):
+    return t.detach().cpu().numpy()
+
+
+def gpu(a):
+    return torch.from_numpy(np.ascontiguousarray(a, np.float64)).cuda()
+
+
+def rel(a, b):
+    return np.abs(a - b).max() / max(np.abs(b).max(), 1e-300)
+
+
+@pytest.mark.parametrize("case", CASES, ids=IDS)
+def test_assembled_operators_match(case):
+    mg, orc = make_pair(**case)
+    for lev in range(case["nlev"]):
+        rp, ci, va = (cpu(t) for t in mg.csr(lev))
+        orp, oci, ova = orc.csr(lev)
+        assert np.array_equal(rp, orp)
+        assert np.array_equal(ci.astype(np.int64), oci)
+        assert np.abs(va - ova).max() <= 1e-13 * np.abs(ova).max()
+
+
+@pytest.mark.parametrize("case", CASES, ids=IDS)
+def test_rhs_and_initial_guess_match(case):
+    mg, orc = make_pair(**case)
+    forcings = [O.F_NONE, O.F_QUADRATIC] + ([O.F_PSI] if case["dim"] == 2 else [O.F_SINKER])
+    for f in forcings:
+        b = cpu(mg.rhs(f))
+        ob = orc.rhs(f)
+        assert np.abs(b - ob).max() <= 1e-13 * max(np.abs(ob).max(), 1.0), f
+    assert np.array_equal(cpu(mg.initial_guess()), orc.initial_guess())
+
+
+@pytest.mark.parametrize("case", CASES, ids=IDS)
+def test_patch_lists_and_owners_bit_exact(case):
+    mg, orc = make_pair(**case)
+    sm = R.Smoother(mg, R.RAV, R.F64, 0.5)
+    for lev in range(1, case["nlev"]):
+        orc.build_patches(lev)
+        off, dofs, own = (cpu(t).astype(np.int64) for t in sm.patches(lev))
+        ooff, odofs, oown = orc.patches(lev)
+        assert np.array_equal(off, ooff)
+        assert np.array_equal(dofs, odofs)
+        assert np.array_equal(own, oown)
+
+
+@pytest.mark.parametrize("case", CASES, ids=IDS)
+@pytest.mark.parametrize("kind", [R.RAV, R.AV])
+def test_stored_inverse_rows_match(case, kind):
+    if kind == R.AV and case["dim"] == 3 and case["N"] > 4:
+        pytest.skip("full 3-D inverses checked on the 4^3 case")
+    mg, orc = make_pair(**case)
+    sm = R.Smoother(mg, kind, R.F64, 0.5)
+    orc.setup_smoother(O.RAV if kind == R.RAV else O.AV, 0.5)
+    lev = case["nlev"] - 1
+    npatch = mg.counts(lev)["n_p"]
+    got = cpu(sm.inverse_rows(lev, 0, npatch))
+    for p in range(npatch):
+        want = orc.inverse(lev, p)
+        g = got[p, : want.shape[0], : want.shape[1]]
+        assert np.abs(g - want).max() <= 1e-11 * np.abs(want).max(), p
+        assert not got[p, want.shape[0]:, :].any() and not got[p, :, want.shape[1]:].any()
+
+
+@pytest.mark.parametrize("case", CASES, ids=IDS)
+@pytest.mark.parametrize("kind,omega", [(R.RAV, 0.5), (R.AV, 0.1), (R.MV_COLOURED, 0.66)])
+def test_one_fp64_smoothing_step_matches(case, kind, omega):
+    if kind != R.RAV and case["dim"] == 3 and case["N"] > 4:
+        pytest.skip("3-D AV/MV checked on the 4^3 case")
+    mg, orc = make_pair(**case)
+    sm = R.Smoother(mg, kind, R.F64, omega)
+    okind = {R.RAV: O.RAV, R.AV: O.AV, R.MV_COLOURED: O.MV_COLOURED}[kind]
+    orc.setup_smoother(okind, omega)
+    rng = np.random.default_rng(3)
+    for lev in range(1, case["nlev"]):
+        n = mg.n(lev)
+        x, b = rng.standard_normal(n), rng.standard_normal(n)
+        want = orc.smooth(lev, x, b, 2)
+        xg = gpu(x)
+        sm.smooth(lev, xg, gpu(b), 2)
+        got = cpu(xg)
+        assert rel(got, want) <= 1e-12
+        assert np.linalg.norm(got - want) <= 1e-12 * np.linalg.norm(want - x) * 10
+
+
+@pytest.mark.parametrize("case", CASES, ids=IDS)
+def test_per_patch_damping_is_applied(case):
+    mg, orc = make_pair(**case)
+    sm = R.Smoother(mg, R.RAV, R.F64, 0.5)
+    orc.setup_smoother(O.RAV, 0.5)
+    lev = case["nlev"] - 1
+    w = (0.2 + 0.9 * inputs.uniform(8, mg.counts(lev)["n_p"])).astype(np.float32)
+    sm.set_omega(lev, torch.from_numpy(w).cuda())
+    orc.set_omega(lev, w.astype(np.float64))
+    rng = np.random.default_rng(4)
+    n = mg.n(lev)
+    x, b = rng.standard_normal(n), rng.standard_normal(n)
+    xg = gpu(x)
+    sm.smooth(lev, xg, gpu(b), 1)
+    assert rel(cpu(xg), orc.smooth(lev, x, b, 1)) <= 1e-12
+
+
+@pytest.mark.parametrize("case", CASES, ids=IDS)
+def test_residual_transfers_and_coarse_solve_match(case):
+    mg, orc = make_pair(**case)
+    rng = np.random.default_rng(5)
+    for lev in range(case["nlev"]):
+        n = mg.n(lev)
+        x, b = rng.standard_normal(n), rng.standard_normal(n)
+        r, nrm = mg.residual(lev, gpu(x), gpu(b), norm=True)
+        want = orc.residual(lev, x, b)
+        assert rel(cpu(r), want) <= 1e-13
+        assert abs(nrm - np.linalg.norm(want)) <= 1e-13 * np.linalg.norm(want)
+        if lev > 0:
+            rf = want
+            bc = cpu(mg.restrict(lev, gpu(rf)))
+            assert rel(bc, orc.restrict(lev, rf)) <= 1e-14
+            xc = rng.standard_normal(mg.n(lev - 1))
+            xf = rng.standard_normal(n)
+            got = cpu(mg.prolong_add(lev, gpu(xc), gpu(xf)))
+            assert rel(got, orc.prolong_add(lev, xc, xf)) <= 1e-14
+    m0, _ = orc.dirichlet(0)
+    b0 = rng.standard_normal(mg.n(0))
+    got = cpu(mg.coarse_solve(gpu(b0)))
+    want = orc.coarse_solve(b0)
+    assert rel(got, want) <= 1e-11
+
+
+@pytest.mark.parametrize("case", CASES[:3], ids=IDS[:3])
+def test_vcycle_matches(case):
+    mg, orc = make_pair(**case)
+    sm = R.Smoother(mg, R.RAV, R.F64, 0.5)
+    orc.setup_smoother(O.RAV, 0.5)
+    rng = np.random.default_rng(6)
+    n = mg.n()
+    x, b = rng.standard_normal(n), rng.standard_normal(n)
+    want = orc.vcycle(x, b, 2, 2)
+    xg = gpu(x)
+    mg.vcycle(sm, xg, gpu(b), 2, 2)
+    assert rel(cpu(xg), want) <= 1e-11
+
+
+def test_cavity_convergence_factors_within_two_percent():
+    """16x16 Q2-Q1 lid-driven cavity, 3 levels, RAV(0.5), V(2,2), to 1e-8."""
+    mg, orc = make_pair(2, 16, 3)
+    sm = R.Smoother(mg, R.RAV, R.F64, 0.5)
+    orc.setup_smoother(O.RAV, 0.5)
+    b = mg.rhs(R.F_NONE)
+    x = mg.initial_guess()
+    it, hist, rc = mg.solve(sm, x, b, tol=1e-8, maxit=100)
+    ox, oit, ohist = orc.solve(orc.initial_guess(), orc.rhs(O.F_NONE), tol=1e-8, maxit=100)
+    assert rc == 0 and it == oit
+    fac, ofac = hist[1:] / hist[:-1], ohist[1:] / ohist[:-1]
+    assert np.all(np.abs(fac / ofac - 1.0) <= 0.02)
+    rho, orho = hist[-1] ** (1.0 / it), ohist[-1] ** (1.0 / oit)
+    assert abs(rho / orho - 1.0) <= 0.02
+    assert rel(cpu(x), ox) <= 1e-6
+
+
+@pytest.mark.parametrize("kind,omega", [(R.AV, 0.1), (R.MV_COLOURED, 0.66)])
+def test_comparator_solves_match(kind, omega):
+    mg, orc = make_pair(2, 8, 2)
+    sm = R.Smoother(mg, kind, R.F64, omega)
+    orc.setup_smoother(O.AV if kind == R.AV else O.MV_COLOURED, omega)
+    it, hist, rc = mg.solve(sm, mg.initial_guess(), mg.rhs(R.F_NONE), tol=1e-8, maxit=300)
+    _, oit, ohist = orc.solve(orc.initial_guess(), orc.rhs(O.F_NONE), tol=1e-8, maxit=300)
+    assert rc == 0 and it == oit
+    assert np.all(np.abs(hist[1:] / ohist[1:] - 1.0) <= 1e-6)
+
+
+def test_fgmres_matches():
+    mg, orc = make_pair(2, 16, 3, nblobs=8, s_max=3.0)
+    sm = R.Smoother(mg, R.RAV, R.F64, 0.5)
+    orc.setup_smoother(O.RAV, 0.5)
+    x = mg.initial_guess()
+    it, hist, rc = mg.solve(sm, x, mg.rhs(R.F_NONE), tol=1e-10, maxit=100, outer=1)
+    ox, oit, ohist = orc.fgmres(orc.initial_guess(), orc.rhs(O.F_NONE), tol=1e-10, maxit=100)
+    assert rc == 0 and abs(it - oit) <= 1
+    k = min(it, oit)
+    assert np.all(np.abs(hist[1:k] / ohist[1:k] - 1.0) <= 1e-4)
+    nu = mg.counts(2)["n_u"]
+    assert np.abs(cpu(x)[:nu] - ox[:nu]).max() <= 1e-8
+
+
+@pytest.mark.parametrize("prec", [R.F32, R.BF16, R.FP8])
+@pytest.mark.parametrize("case", [CASES[1], CASES[2]], ids=[IDS[1], IDS[2]])
+def test_reduced_precision_codes_and_step(case, prec):
+    mg, orc = make_pair(**case)
+    lev = case["nlev"] - 1
+    npatch = mg.counts(lev)["n_p"]
+    s64 = R.Smoother(mg, R.RAV, R.F64, 0.5)
+    sq = R.Smoother(mg, R.RAV, prec, 0.5)
+    rows64 = cpu(s64.inverse_rows(lev, 0, npatch))
+    rowsq = cpu(sq.inverse_rows(lev, 0, npatch))
+    # same fp64 input -> same codes: quantise the GPU fp64 rows with the oracle's rounding
+    if prec == R.FP8:
+        m = np.abs(rows64).max(axis=2, keepdims=True)
+        s = np.where(m == 0, 1.0, (m / 448.0).astype(np.float32).astype(np.float64))
+    else:
+        s = np.ones_like(rows64[..., :1])
+    want = O.round_format(prec, rows64 / s) * s
+    assert np.array_equal(rowsq, want)
+    # one step against the oracle's emulation of the same format
+    orc.setup_smoother(O.RAV, 0.5, prec)
+    rng = np.random.default_rng(7)
+    n = mg.n(lev)
+    x, b = rng.standard_normal(n), rng.standard_normal(n)
+    xg = gpu(x)
+    sq.smooth(lev, xg, gpu(b), 1)
+    got = cpu(xg) - x
+    want_q = orc.smooth(lev, x, b, 1) - x
+    orc64 = O.Oracle(case["dim"], case["N"], case["nlev"],
+                     coords=inputs.graded_coordinates(case["N"], 4.0, case["dim"]) if case.get("graded") else None,
+                     blobs=inputs.viscosity_blobs(21, k=case.get("nblobs", 0), s_max=2.0) if case.get("nblobs") else None,
+                     bc=case.get("bc", O.BC_CAVITY))
+    orc64.setup_smoother(O.RAV, 0.5)
+    d64 = orc64.smooth(lev, x, b, 1) - x
+    fmt_err = np.linalg.norm(want_q - d64) / np.linalg.norm(d64)
+    assert np.linalg.norm(got - want_q) <= 1e-5 * np.linalg.norm(d64) + 0.05 * fmt_err * np.linalg.norm(d64)
+    assert fmt_err <= {R.F32: 1e-6, R.BF16: 2e-2, R.FP8: 2e-1}[prec]
+
+
+@pytest.mark.parametrize("prec", [R.F32, R.BF16])
+def test_reduced_precision_fgmres_reaches_fp64_tolerance(prec):
+    """The fp64 outer loop absorbs the error of the stored inverses (spec form 1)."""
+    mg, _ = make_pair(3, 8, 2, nblobs=10, s_max=3.0, bc=O.BC_NOSLIP)
+    sm = R.Smoother(mg, R.RAV, prec, 0.5)
+    x = mg.initial_guess()
+    b = mg.rhs(R.F_SINKER)
+    it, hist, rc = mg.solve(sm, x, b, tol=1e-8, maxit=200, outer=1)
+    assert rc == 0 and hist[-1] <= 1e-8
+    _, nrm = mg.residual(1, x, b, norm=True)
+    _, nrm0 = mg.residual(1, mg.initial_guess(), b, norm=True)
+    assert nrm <= 1.01e-8 * nrm0
+
+
+@pytest.mark.slow
+def test_full_size_512_sampled_parity():
+    """512^2 Q2-Q1 (2,364,419 DoFs), the benchmark's launch configuration:
+    the whole assembled fine operator, and one RAV step at sampled subdomains."""
+    N, nlev = 512, 7
+    mg = R.Multigrid(2, N, nlev, bc=R.BC_NOSLIP)
+    orc = O.Oracle(2, N, 1, bc=O.BC_NOSLIP)
+    rp, ci, va = (cpu(t) for t in mg.csr(nlev - 1))
+    orp, oci, ova = orc.csr(0)
+    assert np.array_equal(rp, orp) and np.array_equal(ci.astype(np.int64), oci)
+    assert np.abs(va - ova).max() <= 1e-13 * np.abs(ova).max()
+    del oci, ova
+    sm = R.Smoother(mg, R.RAV, R.F64, 0.5)
+    rng = np.random.default_rng(8)
+    n = mg.n()
+    x, b = rng.standard_normal(n), rng.standard_normal(n)
+    xg = gpu(x)
+    sm.smooth(nlev - 1, xg, gpu(b), 1)
+    got = cpu(xg)
+    r = orc.residual(0, x, b)
+    orc.build_patches(0)
+    off, dofs, own = orc.patches(0)
+    samples = np.concatenate([[0, N, N * (N + 1), (N + 1) ** 2 - 1],
+                              (inputs.uniform(9, 60) * (N + 1) ** 2).astype(np.int64)])
+    for p in samples:
+        s = dofs[off[p]:off[p + 1]]
+        mine = s[own[s] == p]
+        rows = orc.patch_rows(0, int(p))[: len(mine) * len(s)].reshape(len(mine), len(s))
+        want = x[mine] + 0.5 * rows @ r[s]
+        assert np.abs(got[mine] - want).max() <= 1e-12 * max(np.abs(want).max(), 1.0), p
