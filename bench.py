@@ -51,13 +51,15 @@ WORKLOADS = {
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=300)
+    ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="2d512", choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-tol", action="store_true")
+    ap.add_argument("--N", type=int, default=None, help="override the grid size (profiling runs)")
+    ap.add_argument("--levels", type=int, default=None)
     return ap.parse_args()
 
 
@@ -347,7 +349,11 @@ def ctypes_f64():
 
 def main():
     args = parse()
-    W = WORKLOADS[args.workload]
+    W = dict(WORKLOADS[args.workload])
+    if args.N:
+        W["N"] = args.N
+        W["nlev"] = args.levels or W["nlev"]
+        W["desc"] += f" [size override: {args.N}x{args.N}, {W['nlev']} levels]"
     if args.impl == "reference":
         run_reference(args, W)
     else:
