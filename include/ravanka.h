@@ -62,7 +62,14 @@ enum {
 enum rav_bc { RAV_BC_CAVITY = 0, RAV_BC_NOSLIP = 1, RAV_BC_QUADRATIC = 2 };
 enum rav_forcing { RAV_F_NONE = 0, RAV_F_PSI = 1, RAV_F_SINKER = 2, RAV_F_QUADRATIC = 3 };
 enum rav_smoother_kind { RAV_RAV = 0, RAV_AV = 1, RAV_MV_COLOURED = 3 };
-enum rav_precision { RAV_F64 = 0, RAV_F32 = 1, RAV_BF16 = 2, RAV_FP8 = 3 };
+/* Storage of the RAV inverse rows.  RAV_F64: fp64, factored through the block
+ * form of L_i^{-1} (rows of K_i^{-1} of the owned nodes, w = A_i^{-1} b and
+ * 1/s; see vanka_setup).  RAV_F64_ROWS: the owned rows of L_i^{-1} themselves
+ * in fp64 (the storage of Sec. 4.3 as written).  RAV_F32 / RAV_BF16 / RAV_FP8:
+ * the owned rows rounded to nearest-even into that format (fp8 e4m3 with an
+ * fp32 scale max|row|/448 per row), applied with fp32 accumulation.  AV and MV
+ * store all rows in fp64 (RAV_F64 or RAV_F64_ROWS). */
+enum rav_precision { RAV_F64 = 0, RAV_F32 = 1, RAV_BF16 = 2, RAV_FP8 = 3, RAV_F64_ROWS = 4 };
 
 /* Problem on the unit square (dim 2) or cube (dim 3).
  *  coords_host: dim*(N+1) finest-level vertex coordinates, axis-major, strictly

@@ -18,11 +18,11 @@ from . import _capi
 from ._capi import RavError, check
 
 RAV, AV, MV_COLOURED = 0, 1, 3
-F64, F32, BF16, FP8 = 0, 1, 2, 3
+F64, F32, BF16, FP8, F64_ROWS = 0, 1, 2, 3, 4
 BC_CAVITY, BC_NOSLIP, BC_QUADRATIC = 0, 1, 2
 F_NONE, F_PSI, F_SINKER, F_QUADRATIC = 0, 1, 2, 3
 
-__all__ = ["Multigrid", "Smoother", "RavError", "RAV", "AV", "MV_COLOURED", "F64", "F32", "BF16", "FP8",
+__all__ = ["Multigrid", "Smoother", "RavError", "RAV", "AV", "MV_COLOURED", "F64", "F32", "BF16", "FP8", "F64_ROWS",
            "BC_CAVITY", "BC_NOSLIP", "BC_QUADRATIC", "F_NONE", "F_PSI", "F_SINKER", "F_QUADRATIC"]
 
 

@@ -41,15 +41,26 @@ struct Geo {
   const double* xv[3];  // device vertex coordinates per axis (N + 1)
 };
 
-// Per-axis interpolation tables from level l-1 into level l.  For fine Q2 node
-// index I on an axis: coarse cell k2[I] and the values of the three quadratic
-// Lagrange functions of that cell at the node (w2[3I..3I+2]); for fine vertex
-// v: coarse cell k1[v] and the two linear Lagrange values (w1[2v..2v+1]).
+// Per-axis interpolation tables from level l-1 into level l, nonzero weights
+// only.  Prolongation: fine Q2 node index I takes pc2[I] coarse nodes
+// pk2[3I+j] with weights pw2[3I+j]; fine vertex v takes pc1[v] coarse vertices
+// (pk1, pw1, stride 2).  Restriction (the transpose): coarse Q2 node K gathers
+// rc2[K] fine nodes rk2[7K+j] with weights rw2[7K+j], fine boundary nodes left
+// out (up to 7 per axis on graded grids); coarse vertex K gathers rc1[K] fine
+// vertices (rk1, rw1, stride 3).
 struct XferTab {
-  const int* k2[3];
-  const double* w2[3];
-  const int* k1[3];
-  const double* w1[3];
+  const int* pc2[3];
+  const int* pk2[3];
+  const double* pw2[3];
+  const int* pc1[3];
+  const int* pk1[3];
+  const double* pw1[3];
+  const int* rc2[3];
+  const int* rk2[3];
+  const double* rw2[3];
+  const int* rc1[3];
+  const int* rk1[3];
+  const double* rw1[3];
 };
 
 struct Level {
@@ -60,19 +71,22 @@ struct Level {
   int64_t* rp = nullptr;   // CSR row pointer (n + 1)
   int32_t* ci = nullptr;   // CSR columns, ascending per row
   double* va = nullptr;    // CSR values
+  // sliced-ELL copy of the operator for the residual: slices of 32 rows of one
+  // common length (rows grouped by length), column-major inside a slice
+  int64_t nslice = 0;
+  int32_t* sperm = nullptr;  // row of slot t = 32 s + lane, -1 for padding
+  int64_t* sptr = nullptr;   // offset of slice s in sval/scol
+  int32_t* slen = nullptr;   // row length of slice s (1 = Dirichlet identity rows)
+  int32_t* scol = nullptr;
+  double* sval = nullptr;
   double* x = nullptr;     // level work vectors (coarse levels' iterate and rhs)
   double* b = nullptr;
   double* r = nullptr;     // residual
-  // interpolation tables into this level (unused on level 0)
-  int* k2[3] = {nullptr, nullptr, nullptr};
-  double* w2[3] = {nullptr, nullptr, nullptr};
-  int* k1[3] = {nullptr, nullptr, nullptr};
-  double* w1[3] = {nullptr, nullptr, nullptr};
-  XferTab tab() const {
-    XferTab t;
-    for (int a = 0; a < 3; ++a) { t.k2[a] = k2[a]; t.w2[a] = w2[a]; t.k1[a] = k1[a]; t.w1[a] = w1[a]; }
-    return t;
-  }
+  // interpolation tables into this level (unused on level 0); one device
+  // allocation per axis holding the twelve arrays of XferTab
+  void* xfer[3] = {nullptr, nullptr, nullptr};
+  XferTab tabs{};
+  XferTab tab() const { return tabs; }
 };
 
 }  // namespace rav
@@ -95,6 +109,8 @@ struct rav_mg {
 // Smoother data of one level: stored inverse rows and damping per subdomain.
 struct SmLevel {
   int64_t np = 0, units = 0;
+  bool factored = false;     // RAV fp64: rows of K^{-1} in inv, w and 1/s in ws
+  double* ws = nullptr;
   void* inv = nullptr;       // RAV: packed owned rows; AV/MV: full inverses (fp64, column-major)
   float* scale = nullptr;    // fp8 row scales
   double* omega = nullptr;   // damping per subdomain

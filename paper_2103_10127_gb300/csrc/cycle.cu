@@ -8,33 +8,36 @@
 namespace rav {
 
 // ---------------------------------------------------------------------------
-// r = b - L x on free rows, 0 on Dirichlet rows (the identity rows, the only
-// rows of L with a single entry).  G lanes per row; optional per-block partial
-// sums of r^2 into part[blockIdx.x].
-template <int G>
-__global__ void __launch_bounds__(256) k_residual(int64_t n, const int64_t* __restrict__ rp,
-                                                  const int32_t* __restrict__ ci, const double* __restrict__ va,
-                                                  const double* __restrict__ x, const double* __restrict__ b,
-                                                  double* __restrict__ r, double* __restrict__ part) {
-  const int lane = threadIdx.x & (G - 1);
-  const int64_t rows_per_block = blockDim.x / G;
+// r = b - L x on free rows, 0 on Dirichlet rows (Eq. 10), on the sliced-ELL
+// copy of L: one thread per row, every lane of a
+// slice runs the same trip count, so each fp64 FMA instruction is fully used
+// (on GB300 an fp64 warp instruction occupies the pipe whatever its active
+// lanes).  Slices of length 1 hold the Dirichlet identity rows: r = 0.
+__global__ void __launch_bounds__(256) k_residual_sell(int64_t nslots, const int32_t* __restrict__ sperm,
+                                                       const int64_t* __restrict__ sptr,
+                                                       const int32_t* __restrict__ slen,
+                                                       const int32_t* __restrict__ scol,
+                                                       const double* __restrict__ sval,
+                                                       const double* __restrict__ x, const double* __restrict__ b,
+                                                       double* __restrict__ r, double* __restrict__ part) {
   double acc2 = 0.0;
-  // the loop bound is block-uniform so every lane reaches the shuffles
-  for (int64_t base = blockIdx.x * rows_per_block; base < n; base += (int64_t)gridDim.x * rows_per_block) {
-    const int64_t row = base + threadIdx.x / G;
-    double t = 0.0;
-    int64_t s = 0, e = 0;
-    if (row < n) {
-      s = rp[row];
-      e = rp[row + 1];
-      for (int64_t k = s + lane; k < e; k += G) t += va[k] * x[ci[k]];
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < nslots;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t s = t >> 5;
+    const int32_t row = sperm[t];
+    const int len = slen[s];
+    const int64_t base = sptr[s] + (t & 31);
+    double acc = 0.0;
+    if (len > 1) {
+      const int32_t* c = scol + base;
+      const double* v = sval + base;
+#pragma unroll 4
+      for (int k = 0; k < len; ++k) acc += v[32 * k] * x[c[32 * k]];
     }
-#pragma unroll
-    for (int o = G / 2; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o, G);
-    if (lane == 0 && row < n) {
-      const double v = (e - s == 1) ? 0.0 : b[row] - t;
-      r[row] = v;
-      acc2 += v * v;
+    if (row >= 0) {
+      const double rv = len > 1 ? b[row] - acc : 0.0;
+      r[row] = rv;
+      acc2 += rv * rv;
     }
   }
   if (part) {
@@ -60,126 +63,116 @@ __global__ void k_dot_parts(const double* __restrict__ a, const double* __restri
 }
 
 // ---------------------------------------------------------------------------
-// Transfers with the per-axis tables (see common.cuh, XferTab).
+// Transfers with the per-axis tables (see common.cuh, XferTab): a tensor
+// product of per-axis lists of nonzero weights, 32-bit indices.
 template <int D>
 __global__ void k_prolong(Geo gf, Geo gc, XferTab T, const double* __restrict__ xc, double* __restrict__ xf) {
-  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (t < gf.nnode) {
-    int64_t I[3] = {0, 0, 0}, id = t;
-    for (int a = 0; a < D; ++a) { I[a] = id % gf.M; id /= gf.M; }
-    if (node_on_boundary(gf, I)) return;
-    int k[3] = {0, 0, 0};
-    double w[3][3];
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  const int Mf = (int)gf.M, Mc = (int)gc.M, nnf = (int)gf.nnode;
+  if (t < nnf) {
+    int I[3] = {0, 0, 0}, id = t;
+    bool bnd = false;
     for (int a = 0; a < D; ++a) {
-      k[a] = T.k2[a][I[a]];
-      for (int j = 0; j < 3; ++j) w[a][j] = T.w2[a][3 * I[a] + j];
+      I[a] = id % Mf;
+      id /= Mf;
+      bnd |= (I[a] == 0) | (I[a] == Mf - 1);
     }
-    double acc[3] = {0, 0, 0};
-    for (int t2 = 0; t2 < (D == 3 ? 3 : 1); ++t2)
-      for (int t1 = 0; t1 < 3; ++t1)
-        for (int t0 = 0; t0 < 3; ++t0) {
-          double ww = w[0][t0] * w[1][t1];
-          int64_t K[3] = {2 * k[0] + t0, 2 * k[1] + t1, 0};
-          if (D == 3) { ww *= w[2][t2]; K[2] = 2 * k[2] + t2; }
-          if (ww == 0.0) continue;
-          const int64_t base = D * node_id(gc, K);
+    if (bnd) return;
+    const int c0 = T.pc2[0][I[0]], c1 = T.pc2[1][I[1]], c2 = D == 3 ? T.pc2[2][I[2]] : 1;
+    double acc[D];
+#pragma unroll
+    for (int c = 0; c < D; ++c) acc[c] = 0.0;
+    for (int j2 = 0; j2 < c2; ++j2) {
+      const int K2 = D == 3 ? T.pk2[2][3 * I[2] + j2] : 0;
+      const double w2 = D == 3 ? T.pw2[2][3 * I[2] + j2] : 1.0;
+      for (int j1 = 0; j1 < c1; ++j1) {
+        const int K1 = T.pk2[1][3 * I[1] + j1];
+        const double w12 = D == 3 ? w2 * T.pw2[1][3 * I[1] + j1] : T.pw2[1][3 * I[1] + j1];
+        const int rowbase = D * Mc * (K1 + Mc * K2);
+        for (int j0 = 0; j0 < c0; ++j0) {
+          const double ww = w12 * T.pw2[0][3 * I[0] + j0];
+          const int base = rowbase + D * T.pk2[0][3 * I[0] + j0];
+#pragma unroll
           for (int c = 0; c < D; ++c) acc[c] += ww * xc[base + c];
         }
-    for (int c = 0; c < D; ++c) xf[D * t + c] += acc[c];
-  } else if (t < gf.nnode + gf.n_p) {
-    int64_t v = t - gf.nnode, vv[3] = {0, 0, 0};
-    for (int a = 0; a < D; ++a) { vv[a] = v % (gf.N + 1); v /= (gf.N + 1); }
-    int k[3] = {0, 0, 0};
-    double w[3][2];
-    for (int a = 0; a < D; ++a) {
-      k[a] = T.k1[a][vv[a]];
-      w[a][0] = T.w1[a][2 * vv[a]];
-      w[a][1] = T.w1[a][2 * vv[a] + 1];
+      }
     }
+#pragma unroll
+    for (int c = 0; c < D; ++c) xf[(int64_t)D * t + c] += acc[c];
+  } else if (t < nnf + (int)gf.n_p) {
+    const int Nf1 = gf.N + 1, Nc1 = gc.N + 1;
+    int v[3] = {0, 0, 0}, id = t - nnf;
+    for (int a = 0; a < D; ++a) { v[a] = id % Nf1; id /= Nf1; }
+    const int c0 = T.pc1[0][v[0]], c1 = T.pc1[1][v[1]], c2 = D == 3 ? T.pc1[2][v[2]] : 1;
     double acc = 0.0;
-    for (int t2 = 0; t2 < (D == 3 ? 2 : 1); ++t2)
-      for (int t1 = 0; t1 < 2; ++t1)
-        for (int t0 = 0; t0 < 2; ++t0) {
-          double ww = w[0][t0] * w[1][t1];
-          int64_t K[3] = {k[0] + t0, k[1] + t1, 0};
-          if (D == 3) { ww *= w[2][t2]; K[2] = k[2] + t2; }
-          if (ww == 0.0) continue;
-          acc += ww * xc[gc.n_u + vert_id(gc, K)];
-        }
-    xf[gf.n_u + (t - gf.nnode)] += acc;
+    for (int j2 = 0; j2 < c2; ++j2) {
+      const int K2 = D == 3 ? T.pk1[2][2 * v[2] + j2] : 0;
+      const double w2 = D == 3 ? T.pw1[2][2 * v[2] + j2] : 1.0;
+      for (int j1 = 0; j1 < c1; ++j1) {
+        const int K1 = T.pk1[1][2 * v[1] + j1];
+        const double w12 = D == 3 ? w2 * T.pw1[1][2 * v[1] + j1] : T.pw1[1][2 * v[1] + j1];
+        for (int j0 = 0; j0 < c0; ++j0)
+          acc += w12 * T.pw1[0][2 * v[0] + j0] * xc[gc.n_u + T.pk1[0][2 * v[0] + j0] + Nc1 * (K1 + Nc1 * K2)];
+      }
+    }
+    xf[gf.n_u + (t - nnf)] += acc;
   }
 }
 
-// bc = P^T rf (gather over the fine nodes whose interpolation uses the coarse
-// node), 0 on coarse Dirichlet rows.
+// bc = P^T rf: each coarse DoF gathers the fine DoFs whose interpolation
+// uses it (fine boundary nodes are not in the lists); 0 on coarse Dirichlet rows.
 template <int D>
-__global__ void k_restrict(Geo gf, Geo gc, XferTab T, const double* __restrict__ rf, double* __restrict__ bc) {
-  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (t < gc.nnode) {
-    int64_t K[3] = {0, 0, 0}, id = t;
-    for (int a = 0; a < D; ++a) { K[a] = id % gc.M; id /= gc.M; }
-    if (node_on_boundary(gc, K)) {
-      for (int c = 0; c < D; ++c) bc[D * t + c] = 0.0;
-      return;
-    }
-    // per axis: candidate fine nodes [2K-4, 2K+4] with their weights
-    int64_t Ilo[3] = {0, 0, 0};
-    double w[3][9];
-    int cnt[3] = {1, 1, 1};
+__global__ void k_restrict_c(Geo gf, Geo gc, XferTab T, const double* __restrict__ rf, double* __restrict__ bc) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  const int Mf = (int)gf.M, Mc = (int)gc.M, nnc = (int)gc.nnode;
+  if (t < nnc) {
+    int K[3] = {0, 0, 0}, id = t;
+    bool bnd = false;
     for (int a = 0; a < D; ++a) {
-      Ilo[a] = 2 * K[a] - 4;
-      cnt[a] = 9;
-      for (int j = 0; j < 9; ++j) {
-        const int64_t I = Ilo[a] + j;
-        double ww = 0.0;
-        if (I >= 0 && I <= 2 * gf.N) {
-          const int64_t loc = K[a] - 2 * (int64_t)T.k2[a][I];
-          if (loc >= 0 && loc <= 2) ww = T.w2[a][3 * I + loc];
+      K[a] = id % Mc;
+      id /= Mc;
+      bnd |= (K[a] == 0) | (K[a] == Mc - 1);
+    }
+    double acc[D];
+#pragma unroll
+    for (int c = 0; c < D; ++c) acc[c] = 0.0;
+    if (!bnd) {
+      const int c0 = T.rc2[0][K[0]], c1 = T.rc2[1][K[1]], c2 = D == 3 ? T.rc2[2][K[2]] : 1;
+      for (int j2 = 0; j2 < c2; ++j2) {
+        const int I2 = D == 3 ? T.rk2[2][7 * K[2] + j2] : 0;
+        const double w2 = D == 3 ? T.rw2[2][7 * K[2] + j2] : 1.0;
+        for (int j1 = 0; j1 < c1; ++j1) {
+          const int I1 = T.rk2[1][7 * K[1] + j1];
+          const double w12 = D == 3 ? w2 * T.rw2[1][7 * K[1] + j1] : T.rw2[1][7 * K[1] + j1];
+          const int64_t rowbase = (int64_t)D * Mf * (I1 + (int64_t)Mf * I2);
+          for (int j0 = 0; j0 < c0; ++j0) {
+            const double ww = w12 * T.rw2[0][7 * K[0] + j0];
+            const int64_t base = rowbase + D * T.rk2[0][7 * K[0] + j0];
+#pragma unroll
+            for (int c = 0; c < D; ++c) acc[c] += ww * rf[base + c];
+          }
         }
-        w[a][j] = ww;
       }
     }
-    double acc[3] = {0, 0, 0};
-    for (int j2 = 0; j2 < (D == 3 ? 9 : 1); ++j2)
-      for (int j1 = 0; j1 < 9; ++j1)
-        for (int j0 = 0; j0 < 9; ++j0) {
-          double ww = w[0][j0] * w[1][j1];
-          int64_t I[3] = {Ilo[0] + j0, Ilo[1] + j1, 0};
-          if (D == 3) { ww *= w[2][j2]; I[2] = Ilo[2] + j2; }
-          if (ww == 0.0) continue;
-          if (node_on_boundary(gf, I)) continue;
-          const int64_t base = D * node_id(gf, I);
-          for (int c = 0; c < D; ++c) acc[c] += ww * rf[base + c];
-        }
-    for (int c = 0; c < D; ++c) bc[D * t + c] = acc[c];
-  } else if (t < gc.nnode + gc.n_p) {
-    int64_t v = t - gc.nnode, K[3] = {0, 0, 0};
-    for (int a = 0; a < D; ++a) { K[a] = v % (gc.N + 1); v /= (gc.N + 1); }
-    int64_t Vlo[3] = {0, 0, 0};
-    double w[3][5];
-    for (int a = 0; a < D; ++a) {
-      Vlo[a] = 2 * K[a] - 2;
-      for (int j = 0; j < 5; ++j) {
-        const int64_t V = Vlo[a] + j;
-        double ww = 0.0;
-        if (V >= 0 && V <= gf.N) {
-          const int64_t loc = K[a] - (int64_t)T.k1[a][V];
-          if (loc >= 0 && loc <= 1) ww = T.w1[a][2 * V + loc];
-        }
-        w[a][j] = ww;
-      }
-    }
+#pragma unroll
+    for (int c = 0; c < D; ++c) bc[(int64_t)D * t + c] = acc[c];
+  } else if (t < nnc + (int)gc.n_p) {
+    const int Nf1 = gf.N + 1, Nc1 = gc.N + 1;
+    int K[3] = {0, 0, 0}, id = t - nnc;
+    for (int a = 0; a < D; ++a) { K[a] = id % Nc1; id /= Nc1; }
+    const int c0 = T.rc1[0][K[0]], c1 = T.rc1[1][K[1]], c2 = D == 3 ? T.rc1[2][K[2]] : 1;
     double acc = 0.0;
-    for (int j2 = 0; j2 < (D == 3 ? 5 : 1); ++j2)
-      for (int j1 = 0; j1 < 5; ++j1)
-        for (int j0 = 0; j0 < 5; ++j0) {
-          double ww = w[0][j0] * w[1][j1];
-          int64_t V[3] = {Vlo[0] + j0, Vlo[1] + j1, 0};
-          if (D == 3) { ww *= w[2][j2]; V[2] = Vlo[2] + j2; }
-          if (ww == 0.0) continue;
-          acc += ww * rf[gf.n_u + vert_id(gf, V)];
-        }
-    bc[gc.n_u + (t - gc.nnode)] = acc;
+    for (int j2 = 0; j2 < c2; ++j2) {
+      const int V2 = D == 3 ? T.rk1[2][3 * K[2] + j2] : 0;
+      const double w2 = D == 3 ? T.rw1[2][3 * K[2] + j2] : 1.0;
+      for (int j1 = 0; j1 < c1; ++j1) {
+        const int V1 = T.rk1[1][3 * K[1] + j1];
+        const double w12 = D == 3 ? w2 * T.rw1[1][3 * K[1] + j1] : T.rw1[1][3 * K[1] + j1];
+        for (int j0 = 0; j0 < c0; ++j0)
+          acc += w12 * T.rw1[0][3 * K[0] + j0] * rf[gf.n_u + T.rk1[0][3 * K[0] + j0] + Nf1 * (V1 + (int64_t)Nf1 * V2)];
+      }
+    }
+    bc[gc.n_u + (t - nnc)] = acc;
   }
 }
 
@@ -227,13 +220,10 @@ __global__ void k_axpy_dev(int64_t n, const double* __restrict__ h, const double
 int residual_impl(rav_mg* mg, int level, const double* x, const double* b, double* r, double* norm2_dev,
                   cudaStream_t s) {
   const Level& L = mg->lev[level];
-  const int64_t n = L.g.n;
-  const int G = L.g.dim == 2 ? 8 : 16;
-  const int rpb = 256 / G;
-  int blocks = (int)std::min<int64_t>((n + rpb - 1) / rpb, (int64_t)mg->part_cap);
+  const int64_t nslots = L.nslice * 32;
+  int blocks = (int)std::min<int64_t>((nslots + 255) / 256, (int64_t)mg->part_cap);
   double* part = norm2_dev ? mg->norm_part : nullptr;
-  if (G == 8) k_residual<8><<<blocks, 256, 0, s>>>(n, L.rp, L.ci, L.va, x, b, r, part);
-  else k_residual<16><<<blocks, 256, 0, s>>>(n, L.rp, L.ci, L.va, x, b, r, part);
+  k_residual_sell<<<blocks, 256, 0, s>>>(nslots, L.sperm, L.sptr, L.slen, L.scol, L.sval, x, b, r, part);
   if (norm2_dev) k_sum_parts<<<1, 256, 0, s>>>(mg->norm_part, blocks, norm2_dev, 1);
   note_launch(norm2_dev ? 2 : 1);
   RAV_CUDA(cudaGetLastError());
@@ -253,8 +243,8 @@ int restrict_impl(rav_mg* mg, int level, const double* rf, double* bc, cudaStrea
   const Level &F = mg->lev[level], &C = mg->lev[level - 1];
   const int64_t tot = C.g.nnode + C.g.n_p;
   const int blocks = (int)((tot + 127) / 128);
-  if (F.g.dim == 2) k_restrict<2><<<blocks, 128, 0, s>>>(F.g, C.g, F.tab(), rf, bc);
-  else k_restrict<3><<<blocks, 128, 0, s>>>(F.g, C.g, F.tab(), rf, bc);
+  if (F.g.dim == 2) k_restrict_c<2><<<blocks, 128, 0, s>>>(F.g, C.g, F.tab(), rf, bc);
+  else k_restrict_c<3><<<blocks, 128, 0, s>>>(F.g, C.g, F.tab(), rf, bc);
   note_launch();
   RAV_CUDA(cudaGetLastError());
   return RAV_OK;

@@ -425,6 +425,34 @@ __global__ void k_assemble(Geo g, const double* __restrict__ Ke, const double* _
   }
 }
 
+__global__ void k_row_lengths(int64_t n, const int64_t* __restrict__ rp, int32_t* __restrict__ len) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n) len[i] = (int32_t)(rp[i + 1] - rp[i]);
+}
+// Sliced-ELL fill: slot t = 32 s + lane holds row sperm[t]; entry k of the
+// slice at sptr[s] + 32 k + lane.
+__global__ void k_sell_fill(int64_t nslice, const int32_t* __restrict__ sperm, const int64_t* __restrict__ sptr,
+                            const int32_t* __restrict__ slen, const int64_t* __restrict__ rp,
+                            const int32_t* __restrict__ ci, const double* __restrict__ va, int32_t* __restrict__ scol,
+                            double* __restrict__ sval) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= nslice * 32) return;
+  const int64_t s = t >> 5;
+  const int lane = (int)(t & 31);
+  const int32_t row = sperm[t];
+  const int len = slen[s];
+  for (int k = 0; k < len; ++k) {
+    const int64_t o = sptr[s] + 32 * (int64_t)k + lane;
+    if (row >= 0) {
+      scol[o] = ci[rp[row] + k];
+      sval[o] = va[rp[row] + k];
+    } else {
+      scol[o] = 0;
+      sval[o] = 0.0;
+    }
+  }
+}
+
 // Right-hand side: free velocity rows sum the element loads of the cells
 // containing the node (ascending cell order), Dirichlet rows get g, pressure rows 0.
 template <int D>
@@ -594,6 +622,52 @@ static int level_geometry(rav_mg* mg, Level& L, int N, const double* fine_coords
   return RAV_OK;
 }
 
+// Sliced-ELL copy of level L's CSR operator.  Rows are grouped by length
+// (longest first, ascending row index inside a group; a counting sort on the
+// host) and cut into slices of 32 rows of one length, a new slice starting at
+// every change of length, so every lane of a slice runs the same trip count.
+static int build_sell(Level& L, cudaStream_t s) {
+  const int64_t n = L.g.n;
+  int32_t* len_d = nullptr;
+  RAV_CUDA(cudaMallocAsync(&len_d, sizeof(int32_t) * n, s));
+  k_row_lengths<<<(int)((n + 255) / 256), 256, 0, s>>>(n, L.rp, len_d);
+  std::vector<int32_t> len(n);
+  RAV_CUDA(cudaMemcpyAsync(len.data(), len_d, sizeof(int32_t) * n, cudaMemcpyDeviceToHost, s));
+  RAV_CUDA(cudaStreamSynchronize(s));
+  RAV_CUDA(cudaFreeAsync(len_d, s));
+  int32_t maxlen = 0;
+  for (int32_t v : len) maxlen = v > maxlen ? v : maxlen;
+  std::vector<int64_t> cnt(maxlen + 1, 0);
+  for (int32_t v : len) ++cnt[v];
+  std::vector<int32_t> perm;
+  std::vector<int64_t> sptr(1, 0);
+  std::vector<int32_t> slen;
+  std::vector<std::vector<int32_t>> bucket(maxlen + 1);
+  for (int32_t k = 0; k <= maxlen; ++k) bucket[k].reserve(cnt[k]);
+  for (int64_t i = 0; i < n; ++i) bucket[len[i]].push_back((int32_t)i);
+  for (int32_t k = maxlen; k >= 0; --k) {
+    const std::vector<int32_t>& b = bucket[k];
+    for (size_t j = 0; j < b.size(); j += 32) {
+      for (size_t q = 0; q < 32; ++q) perm.push_back(j + q < b.size() ? b[j + q] : -1);
+      slen.push_back(k);
+      sptr.push_back(sptr.back() + 32 * (int64_t)k);
+    }
+  }
+  L.nslice = (int64_t)slen.size();
+  RAV_CUDA(cudaMalloc(&L.sperm, sizeof(int32_t) * perm.size()));
+  RAV_CUDA(cudaMalloc(&L.sptr, sizeof(int64_t) * sptr.size()));
+  RAV_CUDA(cudaMalloc(&L.slen, sizeof(int32_t) * slen.size()));
+  RAV_CUDA(cudaMalloc(&L.scol, sizeof(int32_t) * sptr.back()));
+  RAV_CUDA(cudaMalloc(&L.sval, sizeof(double) * sptr.back()));
+  RAV_CUDA(cudaMemcpy(L.sperm, perm.data(), sizeof(int32_t) * perm.size(), cudaMemcpyHostToDevice));
+  RAV_CUDA(cudaMemcpy(L.sptr, sptr.data(), sizeof(int64_t) * sptr.size(), cudaMemcpyHostToDevice));
+  RAV_CUDA(cudaMemcpy(L.slen, slen.data(), sizeof(int32_t) * slen.size(), cudaMemcpyHostToDevice));
+  k_sell_fill<<<(int)((L.nslice * 32 + 255) / 256), 256, 0, s>>>(L.nslice, L.sperm, L.sptr, L.slen, L.rp, L.ci,
+                                                                  L.va, L.scol, L.sval);
+  RAV_CUDA(cudaGetLastError());
+  return RAV_OK;
+}
+
 static int assemble_level(rav_mg* mg, Level& L, cudaStream_t s) {
   const Geo& g = L.g;
   const int D = g.dim;
@@ -631,44 +705,96 @@ static int assemble_level(rav_mg* mg, Level& L, cudaStream_t s) {
   RAV_CUDA(cudaMalloc(&L.r, sizeof(double) * g.n));
   RAV_CUDA(cudaMalloc(&L.x, sizeof(double) * g.n));
   RAV_CUDA(cudaMalloc(&L.b, sizeof(double) * g.n));
-  return RAV_OK;
+  return build_sell(L, s);
 }
 
 // Interpolation tables of fine level F from coarse level C (host, O(N) per axis):
 // a fine Q2 node at position x in coarse cell k (k = min(I/4, Nc-1)) takes the
 // three quadratic Lagrange values at t = (x - xc_k)/(xc_{k+1} - xc_k); a fine
 // vertex takes the two linear ones.
+// Only nonzero weights are kept; the restriction lists are the transposes of
+// the prolongation lists with fine boundary nodes (any axis index 0 or 2N)
+// left out, which on a tensor grid is a per-axis condition.
 static int transfer_tables(rav_mg* mg, const Level& C, Level& F) {
   for (int a = 0; a < mg->dim; ++a) {
     const int Nf = F.g.N, Nc = C.g.N;
-    std::vector<int> k2(2 * Nf + 1), k1(Nf + 1);
-    std::vector<double> w2(3 * (2 * Nf + 1)), w1(2 * (Nf + 1));
+    const int mf = 2 * Nf + 1, mc = 2 * Nc + 1;
+    std::vector<int> pc2(mf, 0), pk2(3 * mf, 0), pc1(Nf + 1, 0), pk1(2 * (Nf + 1), 0);
+    std::vector<double> pw2(3 * mf, 0.0), pw1(2 * (Nf + 1), 0.0);
+    std::vector<int> rc2(mc, 0), rk2(7 * mc, 0), rc1(Nc + 1, 0), rk1(3 * (Nc + 1), 0);
+    std::vector<double> rw2(7 * mc, 0.0), rw1(3 * (Nc + 1), 0.0);
     const std::vector<double>& xf = F.xv_host[a];
     const std::vector<double>& xc = C.xv_host[a];
-    for (int I = 0; I <= 2 * Nf; ++I) {
+    for (int I = 0; I < mf; ++I) {
       const double x = (I & 1) ? 0.5 * (xf[(I - 1) / 2] + xf[(I + 1) / 2]) : xf[I / 2];
       int k = I / 4;
       if (k > Nc - 1) k = Nc - 1;
       const double t = (x - xc[k]) / (xc[k + 1] - xc[k]);
-      k2[I] = k;
-      for (int j = 0; j < 3; ++j) w2[3 * I + j] = lag2(j, t);
+      for (int j = 0; j < 3; ++j) {
+        const double w = lag2(j, t);
+        if (w == 0.0) continue;
+        const int K = 2 * k + j;
+        pk2[3 * I + pc2[I]] = K;
+        pw2[3 * I + pc2[I]] = w;
+        ++pc2[I];
+        if (I == 0 || I == mf - 1) continue;
+        if (rc2[K] >= 7) return RAV_ERR_ARG;
+        rk2[7 * K + rc2[K]] = I;
+        rw2[7 * K + rc2[K]] = w;
+        ++rc2[K];
+      }
     }
     for (int v = 0; v <= Nf; ++v) {
       int k = v / 2;
       if (k > Nc - 1) k = Nc - 1;
       const double t = (xf[v] - xc[k]) / (xc[k + 1] - xc[k]);
-      k1[v] = k;
-      w1[2 * v] = 1.0 - t;
-      w1[2 * v + 1] = t;
+      for (int j = 0; j < 2; ++j) {
+        const double w = j == 0 ? 1.0 - t : t;
+        if (w == 0.0) continue;
+        const int K = k + j;
+        pk1[2 * v + pc1[v]] = K;
+        pw1[2 * v + pc1[v]] = w;
+        ++pc1[v];
+        if (rc1[K] >= 3) return RAV_ERR_ARG;
+        rk1[3 * K + rc1[K]] = v;
+        rw1[3 * K + rc1[K]] = w;
+        ++rc1[K];
+      }
     }
-    RAV_CUDA(cudaMalloc(&F.k2[a], sizeof(int) * k2.size()));
-    RAV_CUDA(cudaMalloc(&F.w2[a], sizeof(double) * w2.size()));
-    RAV_CUDA(cudaMalloc(&F.k1[a], sizeof(int) * k1.size()));
-    RAV_CUDA(cudaMalloc(&F.w1[a], sizeof(double) * w1.size()));
-    RAV_CUDA(cudaMemcpy(F.k2[a], k2.data(), sizeof(int) * k2.size(), cudaMemcpyHostToDevice));
-    RAV_CUDA(cudaMemcpy(F.w2[a], w2.data(), sizeof(double) * w2.size(), cudaMemcpyHostToDevice));
-    RAV_CUDA(cudaMemcpy(F.k1[a], k1.data(), sizeof(int) * k1.size(), cudaMemcpyHostToDevice));
-    RAV_CUDA(cudaMemcpy(F.w1[a], w1.data(), sizeof(double) * w1.size(), cudaMemcpyHostToDevice));
+    // one allocation per axis: doubles first (8-byte aligned), then ints
+    const size_t nd = pw2.size() + pw1.size() + rw2.size() + rw1.size();
+    const size_t ni = pc2.size() + pk2.size() + pc1.size() + pk1.size() + rc2.size() + rk2.size() + rc1.size() +
+                      rk1.size();
+    std::vector<char> blob(8 * nd + 4 * ni);
+    size_t off = 0;
+    char* dev = nullptr;
+    RAV_CUDA(cudaMalloc(&dev, blob.size()));
+    F.xfer[a] = dev;
+    auto put_d = [&](const std::vector<double>& v) {
+      std::memcpy(blob.data() + off, v.data(), 8 * v.size());
+      const double* p = reinterpret_cast<const double*>(dev + off);
+      off += 8 * v.size();
+      return p;
+    };
+    auto put_i = [&](const std::vector<int>& v) {
+      std::memcpy(blob.data() + off, v.data(), 4 * v.size());
+      const int* p = reinterpret_cast<const int*>(dev + off);
+      off += 4 * v.size();
+      return p;
+    };
+    F.tabs.pw2[a] = put_d(pw2);
+    F.tabs.pw1[a] = put_d(pw1);
+    F.tabs.rw2[a] = put_d(rw2);
+    F.tabs.rw1[a] = put_d(rw1);
+    F.tabs.pc2[a] = put_i(pc2);
+    F.tabs.pk2[a] = put_i(pk2);
+    F.tabs.pc1[a] = put_i(pc1);
+    F.tabs.pk1[a] = put_i(pk1);
+    F.tabs.rc2[a] = put_i(rc2);
+    F.tabs.rk2[a] = put_i(rk2);
+    F.tabs.rc1[a] = put_i(rc1);
+    F.tabs.rk1[a] = put_i(rk1);
+    RAV_CUDA(cudaMemcpy(dev, blob.data(), blob.size(), cudaMemcpyHostToDevice));
   }
   return RAV_OK;
 }
@@ -769,14 +895,16 @@ extern "C" void mg_destroy(rav_mg* mg) {
     Level& L = mg->lev[l];
     for (int a = 0; a < 3; ++a) {
       cudaFree(L.xv_dev[a]);
-      cudaFree(L.k2[a]);
-      cudaFree(L.w2[a]);
-      cudaFree(L.k1[a]);
-      cudaFree(L.w1[a]);
+      cudaFree(L.xfer[a]);
     }
     cudaFree(L.rp);
     cudaFree(L.ci);
     cudaFree(L.va);
+    cudaFree(L.sperm);
+    cudaFree(L.sptr);
+    cudaFree(L.slen);
+    cudaFree(L.scol);
+    cudaFree(L.sval);
     cudaFree(L.x);
     cudaFree(L.b);
     cudaFree(L.r);

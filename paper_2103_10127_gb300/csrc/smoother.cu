@@ -37,6 +37,7 @@ struct BoxT {
   static constexpr int NR = D * NON + 1;         // owned rows
   static constexpr int RB = D == 2 ? 9 : 5;      // owned rows per thread in the RAV apply
   static constexpr int NCH = NR / RB;            // threads per subdomain in the RAV apply
+  static constexpr int NF = NON * NV + D * NV + 1;  // factored storage per subdomain
 };
 
 // Vertex tuple of subdomain p.
@@ -62,13 +63,16 @@ __device__ __forceinline__ void box_tuple(int D, int m, int* a) {
 // ---------------------------------------------------------------------------
 // Factorisation: one block per subdomain.  Writes the requested fp64 rows in
 // box coordinates, row-major: RAV rows = owned rows (NR), all rows otherwise (NC).
-template <int D, bool ALL>
+// MODE 0: owned rows; 1: all rows; 2: factored (owned rows of K^{-1}, w, 1/s).
+template <int D, int MODE>
 __global__ void __launch_bounds__(256) k_factor(Geo g, const int64_t* __restrict__ rp, const double* __restrict__ va,
                                                 int64_t first, int64_t count, double* __restrict__ out,
                                                 int* __restrict__ err) {
   using B = BoxT<D>;
   constexpr int NV = B::NV, NC = B::NC;
+  constexpr bool ALL = MODE == 1;
   constexpr int NROW = ALL ? NC : B::NR;
+  constexpr int NF = B::NF;
   constexpr int NRHS = 32;  // right-hand sides solved per batch
   extern __shared__ double sm[];
   double* K = sm;                  // NV x NV, lower triangle -> Cholesky factor
@@ -205,6 +209,24 @@ __global__ void __launch_bounds__(256) k_factor(Geo g, const int64_t* __restrict
   }
   __syncthreads();
   const double si = s_inv;
+  if (MODE == 2) {
+    // factored: rows of K^{-1} of the owned nodes, then w (node-major), then 1/s
+    double* o = out + pl * (int64_t)NF;
+    for (int q = warp; q < B::NON; q += nwarp) {
+      const int m = (2 + (q & 1)) + 5 * (2 + ((q >> 1) & 1)) + (D == 3 ? 25 * (2 + ((q >> 2) & 1)) : 0);
+      double* z = Z + q * NV;
+      for (int n = lane; n < NV; n += 32) z[n] = (n == m) ? 1.0 : 0.0;
+      __syncwarp();
+      if (valid[m]) solve_rhs(z);
+      __syncwarp();
+      for (int n = lane; n < NV; n += 32) o[q * NV + n] = valid[m] && valid[n] ? z[n] : 0.0;
+    }
+    for (int e = tid; e < NV * D; e += nt) o[B::NON * NV + e] = w[e];
+    if (tid == 0) o[NF - 1] = si;
+    __syncthreads();
+    if (tid == 0 && bad) atomicOr(err, 1);
+    return;
+  }
   double* orow = out + pl * (int64_t)NROW * NC;
   // Pressure row (last row in both layouts): (n,c') -> -w[n,c'] / s, (p,p) -> 1/s.
   for (int k = tid; k < NC; k += nt) orow[(int64_t)(NROW - 1) * NC + k] = k < NC - 1 ? -w[k] * si : si;
@@ -428,6 +450,121 @@ __global__ void __launch_bounds__(128) k_rav_apply(Geo g, const T* __restrict__ 
       x[g.n_u + p] += om * (double)y;
     }
   }
+}
+
+// ---------------------------------------------------------------------------
+// Factored RAV storage.  Rows of K^{-1} of the owned nodes: unit u = subdomain
+// * 2^d + owned node q, element (u, n) at ((u/32) * NV + n) * 32 + u%32.
+// w (node-major, NV*D) and 1/s: per subdomain, contiguous (NV*D + 1 values).
+template <int D>
+__global__ void k_pack_fact(const double* __restrict__ stage, int64_t first, int64_t count,
+                            double* __restrict__ kinv, double* __restrict__ ws) {
+  using B = BoxT<D>;
+  constexpr int NV = B::NV, NON = B::NON, NF = B::NF, NWS = D * NV + 1;
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t < count * NON) {
+    const int64_t pl = t / NON;
+    const int q = (int)(t % NON);
+    const int64_t u = (first + pl) * NON + q;
+    const double* src = stage + pl * NF + q * NV;
+    double* dst = kinv + ((u >> 5) * NV) * 32 + (u & 31);
+    for (int n = 0; n < NV; ++n) dst[n * 32] = src[n];
+  }
+  if (t < count * NWS) {
+    const int64_t pl = t / NWS;
+    const int e = (int)(t % NWS);
+    ws[(first + pl) * NWS + e] = stage[pl * NF + NON * NV + e];
+  }
+}
+
+// RAV apply with the factored inverse (Eq. 13 via the block form of L_i^{-1}):
+//   tau = (1/s) (w^T r_u - r_p),
+//   y(m,c) = sum_n K^{-1}[m,n] r(n,c) + w(m,c) tau   for the owned nodes m,
+//   y_p = -tau;   x[owned] += omega_i y.
+// 2^d threads per subdomain, one per owned node; w^T r_u is split over them
+// and summed with a width-2^d shuffle.
+template <int D>
+__global__ void __launch_bounds__(128) k_rav_apply_fact(Geo g, const double* __restrict__ kinv,
+                                                        const double* __restrict__ ws,
+                                                        const double* __restrict__ omega,
+                                                        const double* __restrict__ r, double* __restrict__ x,
+                                                        int64_t units) {
+  using B = BoxT<D>;
+  constexpr int NV = B::NV, NON = B::NON, NWS = D * NV + 1;
+  const int64_t u = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  // warps past the last 32-unit group own no storage; the others stay whole
+  // (their shuffles need every lane), idle lanes computing on subdomain 0
+  if (u >= ((units + 31) & ~(int64_t)31)) return;
+  const bool active = u < units;
+  const int64_t p = active ? u / NON : 0;
+  const int q = (int)(u & (NON - 1));
+  int v[3] = {0, 0, 0};
+  vertex_of(g, p, v);
+  const int M = (int)g.M;
+  int alo[3] = {0, 0, 0}, ahi[3] = {0, 0, 0};
+  for (int d = 0; d < D; ++d) {
+    alo[d] = 2 - 2 * v[d] > 0 ? 2 - 2 * v[d] : 0;
+    ahi[d] = 2 * g.N - 2 * v[d] + 2 < 4 ? 2 * g.N - 2 * v[d] + 2 : 4;
+  }
+  int64_t base = 0;
+  for (int d = D - 1; d >= 0; --d) base = base * M + (2 * v[d] - 2);
+  base *= D;
+  const double* kp = kinv + ((u >> 5) * NV) * 32 + (u & 31);
+  double y[D];
+#pragma unroll
+  for (int c = 0; c < D; ++c) y[c] = 0.0;
+  int n = 0;
+  for (int a2 = 0; a2 < (D == 3 ? 5 : 1); ++a2) {
+    const bool v2 = D == 2 || (a2 >= alo[2] && a2 <= ahi[2]);
+    for (int a1 = 0; a1 < 5; ++a1) {
+      const bool v1 = v2 && a1 >= alo[1] && a1 <= ahi[1];
+      const int64_t rowoff = base + (int64_t)D * M * (a1 + (int64_t)M * a2);
+#pragma unroll
+      for (int a0 = 0; a0 < 5; ++a0) {
+        const bool vv = v1 && a0 >= alo[0] && a0 <= ahi[0];
+        const double kq = kp[n * 32];
+#pragma unroll
+        for (int c = 0; c < D; ++c) y[c] += kq * (vv ? r[rowoff + D * a0 + c] : 0.0);
+        ++n;
+      }
+    }
+  }
+  // partial w^T r_u over the box nodes n = q, q + 2^d, ...
+  const double* wp = ws + p * NWS;
+  double t = 0.0;
+  for (int i = 0; i < (NV + NON - 1) / NON; ++i) {
+    const int m = q + NON * i;
+    if (m < NV) {
+      const int a0 = m % 5, a1 = (m / 5) % 5, a2 = D == 3 ? m / 25 : 0;
+      bool vv = a0 >= alo[0] && a0 <= ahi[0] && a1 >= alo[1] && a1 <= ahi[1];
+      if (D == 3) vv = vv && a2 >= alo[2] && a2 <= ahi[2];
+      if (vv) {
+        const int64_t off = base + (int64_t)D * (a0 + (int64_t)M * (a1 + (int64_t)M * a2));
+#pragma unroll
+        for (int c = 0; c < D; ++c) t += wp[m * D + c] * r[off + c];
+      }
+    }
+  }
+#pragma unroll
+  for (int o = NON / 2; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o, NON);
+  if (!active) return;
+  const double tau = wp[NWS - 1] * (t - r[g.n_u + p]);
+  const double om = omega[p];
+  int64_t J[3] = {0, 0, 0};
+  bool ok = true;
+  int mq = 0;
+  for (int d = D - 1; d >= 0; --d) {
+    const int dl = (q >> d) & 1;
+    J[d] = 2 * v[d] + dl;
+    ok &= (J[d] >= 1) & (J[d] <= 2 * g.N - 1);
+    mq = mq * 5 + 2 + dl;
+  }
+  if (ok) {
+    const int64_t dof = D * node_id(g, J);
+#pragma unroll
+    for (int c = 0; c < D; ++c) x[dof + c] += om * (y[c] + wp[mq * D + c] * tau);
+  }
+  if (q == 0) x[g.n_u + p] += om * -tau;
 }
 
 // ---------------------------------------------------------------------------
@@ -669,6 +806,69 @@ __global__ void k_export_rav(Geo g, const T* __restrict__ inv, const float* __re
     o[e] = val;
   }
 }
+// Owned rows of L_i^{-1} rebuilt from the factored storage:
+// (m,c | n,c') = delta_cc' K^{-1}[m,n] + w(m,c) w(n,c') / s,  (m,c | p) = -w(m,c) / s,
+// (p | n,c') = -w(n,c') / s,  (p | p) = 1 / s.
+template <int D>
+__global__ void k_export_fact(Geo g, const double* __restrict__ kinv, const double* __restrict__ ws, int64_t first,
+                              int64_t count, double* __restrict__ out) {
+  using B = BoxT<D>;
+  constexpr int NC = B::NC, NR = B::NR, NV = B::NV, NON = B::NON, NWS = D * NV + 1;
+  __shared__ int colmap[NC], rowmap[NR];
+  __shared__ int ncol, nrow;
+  const int64_t p = first + blockIdx.x;
+  int v[3] = {0, 0, 0};
+  vertex_of(g, p, v);
+  if (threadIdx.x == 0) {
+    int c = 0;
+    for (int k = 0; k < NC; ++k)
+      if (box_dof<D>(g, v, p, k) >= 0) colmap[c++] = k;
+    ncol = c;
+    int rr = 0;
+    for (int j = 0; j < NR; ++j) {
+      int k;
+      if (j == NR - 1) k = NC - 1;
+      else {
+        const int q = j / D;
+        const int m = (2 + (q & 1)) + 5 * (2 + ((q >> 1) & 1)) + (D == 3 ? 25 * (2 + ((q >> 2) & 1)) : 0);
+        k = m * D + j % D;
+      }
+      if (box_dof<D>(g, v, p, k) >= 0) rowmap[rr++] = j;
+    }
+    nrow = rr;
+  }
+  __syncthreads();
+  const double* wp = ws + p * NWS;
+  const double sig = wp[NWS - 1];
+  double* o = out + blockIdx.x * (int64_t)NR * NC;
+  for (int e = threadIdx.x; e < NR * NC; e += blockDim.x) {
+    const int jr = e / NC, kc = e % NC;
+    double val = 0.0;
+    if (jr < nrow && kc < ncol) {
+      const int j = rowmap[jr], k = colmap[kc];
+      const bool prow = j == NR - 1, pcol = k == NC - 1;
+      if (prow && pcol) {
+        val = sig;
+      } else if (prow) {
+        val = -wp[k] * sig;
+      } else {
+        const int q = j / D, c = j % D;
+        const int m = (2 + (q & 1)) + 5 * (2 + ((q >> 1) & 1)) + (D == 3 ? 25 * (2 + ((q >> 2) & 1)) : 0);
+        const double wm = wp[m * D + c];
+        if (pcol) {
+          val = -wm * sig;
+        } else {
+          const int n = k / D, c2 = k % D;
+          const int64_t u = p * NON + q;
+          const double kq = kinv[((u >> 5) * NV + n) * 32 + (u & 31)];
+          val = (c2 == c ? kq : 0.0) + wm * wp[k] * sig;
+        }
+      }
+    }
+    o[e] = val;
+  }
+}
+
 template <int D>
 __global__ void k_export_full(Geo g, const double* __restrict__ inv, int64_t first, int64_t count,
                               double* __restrict__ out) {
@@ -708,7 +908,7 @@ __global__ void k_f32_to_f64(const float* __restrict__ a, int64_t n, double* __r
 using namespace rav;
 
 static size_t elem_size(int prec) {
-  return prec == RAV_F64 ? 8 : prec == RAV_F32 ? 4 : prec == RAV_BF16 ? 2 : 1;
+  return (prec == RAV_F64 || prec == RAV_F64_ROWS) ? 8 : prec == RAV_F32 ? 4 : prec == RAV_BF16 ? 2 : 1;
 }
 
 template <int D>
@@ -720,12 +920,21 @@ static int setup_level(rav_smoother* sm, int l, cudaStream_t s, int* err_dev) {
   const Geo& g = L.g;
   S_.np = g.n_p;
   const bool all = sm->kind != RAV_RAV;
+  const bool fact = sm->kind == RAV_RAV && sm->prec == RAV_F64;
+  S_.factored = fact;
   const int NROW = all ? B::NC : B::NR;
+  const int64_t per = fact ? B::NF : (int64_t)NROW * B::NC;  // staging doubles per subdomain
   RAV_CUDA(cudaMalloc(&S_.omega, sizeof(double) * S_.np));
   k_fill<<<grid_for(S_.np, 256), 256, 0, s>>>(S_.omega, S_.np, sm->omega);
   if (all) {
     RAV_CUDA(cudaMalloc(&S_.inv, sizeof(double) * S_.np * B::NC * B::NC));
     if (sm->kind == RAV_AV) RAV_CUDA(cudaMalloc(&S_.corr, sizeof(double) * S_.np * B::NC));
+  } else if (fact) {
+    S_.units = S_.np * B::NON;
+    const int64_t groups = (S_.units + 31) / 32;
+    RAV_CUDA(cudaMalloc(&S_.inv, sizeof(double) * groups * 32 * B::NV));
+    RAV_CUDA(cudaMemsetAsync(S_.inv, 0, sizeof(double) * groups * 32 * B::NV, s));
+    RAV_CUDA(cudaMalloc(&S_.ws, sizeof(double) * S_.np * (D * B::NV + 1)));
   } else {
     S_.units = S_.np * B::NCH;
     const int64_t groups = (S_.units + 31) / 32;
@@ -736,22 +945,27 @@ static int setup_level(rav_smoother* sm, int l, cudaStream_t s, int* err_dev) {
   // factorise in batches; staging rows in fp64
   const int64_t batch = std::min<int64_t>(S_.np, all ? 8192 : 32768);
   double* stage = nullptr;
-  RAV_CUDA(cudaMallocAsync(&stage, sizeof(double) * batch * NROW * B::NC, s));
+  RAV_CUDA(cudaMallocAsync(&stage, sizeof(double) * batch * per, s));
   const size_t smem = sizeof(double) * (B::NV * B::NV + 2 * B::NV * D + 32 * B::NV);
-  auto kf = all ? k_factor<D, true> : k_factor<D, false>;
+  auto kf = all ? k_factor<D, 1> : (fact ? k_factor<D, 2> : k_factor<D, 0>);
   RAV_CUDA(cudaFuncSetAttribute(kf, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   const int threads = D == 2 ? 128 : 256;
   for (int64_t f = 0; f < S_.np; f += batch) {
     const int64_t cnt = std::min<int64_t>(batch, S_.np - f);
     kf<<<(unsigned)cnt, threads, smem, s>>>(g, L.rp, L.va, f, cnt, stage, err_dev);
-    if (all) {
+    if (fact) {
+      const int64_t tot = cnt * (D * B::NV + 1);
+      k_pack_fact<D><<<(unsigned)((tot + 127) / 128), 128, 0, s>>>(stage, f, cnt, (double*)S_.inv, S_.ws);
+    } else if (all) {
       const int64_t tot = cnt * B::NC * B::NC;
       k_pack_full<D><<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(stage, f, cnt, (double*)S_.inv);
     } else {
       const int64_t tot = cnt * B::NR;
       const unsigned gb = (unsigned)((tot + 127) / 128);
       switch (sm->prec) {
-        case RAV_F64: k_pack_rav<D, double><<<gb, 128, 0, s>>>(stage, f, cnt, (double*)S_.inv, S_.scale); break;
+        case RAV_F64_ROWS:
+          k_pack_rav<D, double><<<gb, 128, 0, s>>>(stage, f, cnt, (double*)S_.inv, S_.scale);
+          break;
         case RAV_F32: k_pack_rav<D, float><<<gb, 128, 0, s>>>(stage, f, cnt, (float*)S_.inv, S_.scale); break;
         case RAV_BF16:
           k_pack_rav<D, __nv_bfloat16><<<gb, 128, 0, s>>>(stage, f, cnt, (__nv_bfloat16*)S_.inv, S_.scale);
@@ -768,8 +982,8 @@ static int setup_level(rav_smoother* sm, int l, cudaStream_t s, int* err_dev) {
 extern "C" int vanka_setup(rav_mg* mg, int kind, int precision, double omega, rav_stream stream,
                            rav_smoother** out) {
   if (!mg || !out || (kind != RAV_RAV && kind != RAV_AV && kind != RAV_MV_COLOURED)) return RAV_ERR_ARG;
-  if (precision < RAV_F64 || precision > RAV_FP8) return RAV_ERR_ARG;
-  if (kind != RAV_RAV && precision != RAV_F64) return RAV_ERR_ARG;
+  if (precision < RAV_F64 || precision > RAV_F64_ROWS) return RAV_ERR_ARG;
+  if (kind != RAV_RAV && precision != RAV_F64 && precision != RAV_F64_ROWS) return RAV_ERR_ARG;
   cudaStream_t s = S(stream);
   *out = nullptr;
   rav_smoother* sm = new rav_smoother();
@@ -811,6 +1025,7 @@ extern "C" void vanka_destroy(rav_smoother* sm) {
     }
   for (int l = 0; l < kMaxLevels; ++l) {
     cudaFree(sm->lev[l].inv);
+    cudaFree(sm->lev[l].ws);
     cudaFree(sm->lev[l].scale);
     cudaFree(sm->lev[l].omega);
     cudaFree(sm->lev[l].corr);
@@ -861,20 +1076,25 @@ static int apply_impl(rav_smoother* sm, int level, const double* r, double* x, c
       k_av_gather<3><<<gg, 256, 0, s>>>(g, SL.corr, x);
     }
     note_launch(2);
+  } else if (SL.factored) {
+    const unsigned gb = (unsigned)((SL.units + 127) / 128);
+    if (D == 2) k_rav_apply_fact<2><<<gb, 128, 0, s>>>(g, (const double*)SL.inv, SL.ws, SL.omega, r, x, SL.units);
+    else k_rav_apply_fact<3><<<gb, 128, 0, s>>>(g, (const double*)SL.inv, SL.ws, SL.omega, r, x, SL.units);
+    note_launch();
   } else {
     const unsigned gb = (unsigned)((SL.units + 127) / 128);
 #define RAV_APPLY(DD, T) \
   k_rav_apply<DD, T><<<gb, 128, 0, s>>>(g, (const T*)SL.inv, SL.scale, SL.omega, r, x, SL.units)
     if (D == 2) {
       switch (sm->prec) {
-        case RAV_F64: RAV_APPLY(2, double); break;
+        case RAV_F64_ROWS: RAV_APPLY(2, double); break;
         case RAV_F32: RAV_APPLY(2, float); break;
         case RAV_BF16: RAV_APPLY(2, __nv_bfloat16); break;
         default: RAV_APPLY(2, fp8_t); break;
       }
     } else {
       switch (sm->prec) {
-        case RAV_F64: RAV_APPLY(3, double); break;
+        case RAV_F64_ROWS: RAV_APPLY(3, double); break;
         case RAV_F32: RAV_APPLY(3, float); break;
         case RAV_BF16: RAV_APPLY(3, __nv_bfloat16); break;
         default: RAV_APPLY(3, fp8_t); break;
@@ -990,18 +1210,21 @@ extern "C" int rav_get_inverse_rows(const rav_smoother* sm, int level, int64_t f
   if (sm->kind != RAV_RAV) {
     if (g.dim == 2) k_export_full<2><<<gb, 256, 0, s>>>(g, (const double*)SL.inv, first, count, out);
     else k_export_full<3><<<gb, 256, 0, s>>>(g, (const double*)SL.inv, first, count, out);
+  } else if (SL.factored) {
+    if (g.dim == 2) k_export_fact<2><<<gb, 256, 0, s>>>(g, (const double*)SL.inv, SL.ws, first, count, out);
+    else k_export_fact<3><<<gb, 256, 0, s>>>(g, (const double*)SL.inv, SL.ws, first, count, out);
   } else {
 #define RAV_EXP(DD, T) k_export_rav<DD, T><<<gb, 256, 0, s>>>(g, (const T*)SL.inv, SL.scale, first, count, out)
     if (g.dim == 2) {
       switch (sm->prec) {
-        case RAV_F64: RAV_EXP(2, double); break;
+        case RAV_F64_ROWS: RAV_EXP(2, double); break;
         case RAV_F32: RAV_EXP(2, float); break;
         case RAV_BF16: RAV_EXP(2, __nv_bfloat16); break;
         default: RAV_EXP(2, fp8_t); break;
       }
     } else {
       switch (sm->prec) {
-        case RAV_F64: RAV_EXP(3, double); break;
+        case RAV_F64_ROWS: RAV_EXP(3, double); break;
         case RAV_F32: RAV_EXP(3, float); break;
         case RAV_BF16: RAV_EXP(3, __nv_bfloat16); break;
         default: RAV_EXP(3, fp8_t); break;

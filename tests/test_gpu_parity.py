@@ -86,12 +86,13 @@ def test_patch_lists_and_owners_bit_exact(case):
 
 
 @pytest.mark.parametrize("case", CASES, ids=IDS)
-@pytest.mark.parametrize("kind", [R.RAV, R.AV])
-def test_stored_inverse_rows_match(case, kind):
+@pytest.mark.parametrize("kind,prec", [(R.RAV, R.F64), (R.RAV, R.F64_ROWS), (R.AV, R.F64)],
+                         ids=["rav-factored", "rav-rows", "av"])
+def test_stored_inverse_rows_match(case, kind, prec):
     if kind == R.AV and case["dim"] == 3 and case["N"] > 4:
         pytest.skip("full 3-D inverses checked on the 4^3 case")
     mg, orc = make_pair(**case)
-    sm = R.Smoother(mg, kind, R.F64, 0.5)
+    sm = R.Smoother(mg, kind, prec, 0.5)
     orc.setup_smoother(O.RAV if kind == R.RAV else O.AV, 0.5)
     lev = case["nlev"] - 1
     npatch = mg.counts(lev)["n_p"]
@@ -104,12 +105,14 @@ def test_stored_inverse_rows_match(case, kind):
 
 
 @pytest.mark.parametrize("case", CASES, ids=IDS)
-@pytest.mark.parametrize("kind,omega", [(R.RAV, 0.5), (R.AV, 0.1), (R.MV_COLOURED, 0.66)])
-def test_one_fp64_smoothing_step_matches(case, kind, omega):
+@pytest.mark.parametrize("kind,prec,omega", [(R.RAV, R.F64, 0.5), (R.RAV, R.F64_ROWS, 0.5), (R.AV, R.F64, 0.1),
+                                             (R.MV_COLOURED, R.F64, 0.66)],
+                         ids=["rav-factored", "rav-rows", "av", "mv"])
+def test_one_fp64_smoothing_step_matches(case, kind, prec, omega):
     if kind != R.RAV and case["dim"] == 3 and case["N"] > 4:
         pytest.skip("3-D AV/MV checked on the 4^3 case")
     mg, orc = make_pair(**case)
-    sm = R.Smoother(mg, kind, R.F64, omega)
+    sm = R.Smoother(mg, kind, prec, omega)
     okind = {R.RAV: O.RAV, R.AV: O.AV, R.MV_COLOURED: O.MV_COLOURED}[kind]
     orc.setup_smoother(okind, omega)
     rng = np.random.default_rng(3)
@@ -229,7 +232,7 @@ def test_reduced_precision_codes_and_step(case, prec):
     mg, orc = make_pair(**case)
     lev = case["nlev"] - 1
     npatch = mg.counts(lev)["n_p"]
-    s64 = R.Smoother(mg, R.RAV, R.F64, 0.5)
+    s64 = R.Smoother(mg, R.RAV, R.F64_ROWS, 0.5)  # the fp64 rows the reduced formats quantise
     sq = R.Smoother(mg, R.RAV, prec, 0.5)
     rows64 = cpu(s64.inverse_rows(lev, 0, npatch))
     rowsq = cpu(sq.inverse_rows(lev, 0, npatch))
