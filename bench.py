@@ -247,11 +247,9 @@ def run_ours(args, W):
             dist.barrier()
         torch.cuda.synchronize()
 
-    # ---- timed region (device) ----
-    lib.rav_profile_enable(sm.h, 1)
+    # ---- timed region (device): V-cycles replayed as captured CUDA graphs ----
     cnt = ctypes_i64()
     tot = ctypes_f64()
-    lib.rav_profile_read(sm.h, fine, cnt, tot)  # clear
     launches0 = lib.rav_kernel_launches()
     clk = clocks_start()
     time.sleep(0.3)
@@ -265,9 +263,37 @@ def run_ours(args, W):
     ms = e0.elapsed_time(e1)
     clocks = clocks_stop(clk, local)
     launches = lib.rav_kernel_launches() - launches0
-    lib.rav_profile_read(sm.h, fine, cnt, tot)
-    lib.rav_profile_enable(sm.h, 0)
+
+    # ---- the same steps again, kernel by kernel, with CUDA events on the launching
+    # stream around every fine-level subdomain apply (the roofline's kernel) ----
+    lib.rav_profile_enable(mg.h, 1, fine)
+    p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    p0.record(stream)
+    for _ in range(args.steps):
+        step()
+    p1.record(stream)
+    torch.cuda.synchronize()
+    ms_nograph = p0.elapsed_time(p1)
+    lib.rav_profile_read(mg.h, fine, 0, cnt, tot)
     apply_ms = tot.value / max(cnt.value, 1)
+    apply_launches = cnt.value
+
+    # ---- per-level, per-kernel-class breakdown (separate untimed pass, events on every kernel) ----
+    kb = max(5, args.steps // 10)
+    lib.rav_profile_enable(mg.h, 31, -1)
+    for _ in range(kb):
+        step()
+    torch.cuda.synchronize()
+    breakdown = {}
+    names = ["apply", "residual", "restrict", "prolong", "coarse"]
+    for lev in range(W["nlev"]):
+        row = {}
+        for k, nm in enumerate(names):
+            lib.rav_profile_read(mg.h, lev, k, cnt, tot)
+            if cnt.value:
+                row[nm] = round(1e3 * tot.value / kb, 2)
+        breakdown[f"N={mg.counts(lev)['N']}"] = row
+    lib.rav_profile_enable(mg.h, 0, -1)
     if dist is not None:
         t = torch.tensor([ms], device="cuda")
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
@@ -288,7 +314,7 @@ def run_ours(args, W):
     roof["traffic"] = traffic
     roof["kernel"] = ("k_rav_apply_fact" if W["prec"] == 0 else "k_rav_apply") + " (fine level)"
     roof["launch_ms"] = apply_ms
-    roof["launches_timed"] = cnt.value
+    roof["launches_timed"] = apply_launches
     roof["algorithmic_bytes"] = bytes_alg
     roof["algorithmic_flops"] = flops
     roof["hbm_gbs_equiv"] = bytes_alg / (apply_ms / 1e3) / 1e9
@@ -303,7 +329,9 @@ def run_ours(args, W):
                             f"({mg.counts(fine)['nnz'] * 12 / 1e9:.2f} GB) and the stored patch inverses "
                             f"({stored / 1e9:.2f} GB) > 129 MB L2",
                       "parallelism": "replicas" if ws > 1 else "single GPU"},
-           "roofline": roof, "gpu_launches": int(launches), "clocks": clocks}
+           "roofline": roof, "gpu_launches": int(launches), "clocks": clocks,
+           "ms_per_step_kernel_by_kernel": ms_nograph / args.steps,
+           "breakdown_us_per_cycle": breakdown}
 
     # ---- end to end through the public API with host buffers ----
     if not args.no_e2e:

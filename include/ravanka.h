@@ -184,9 +184,19 @@ int vanka_apply(rav_smoother* sm, int level, const double* r_dev, double* x_dev,
 
 /* One V(nu_pre, nu_post) cycle on the finest level (Sec. 2, Fig. 1): smoothing,
  * residual restriction, recursive coarse correction with x_c = 0, the coarse
- * solve on level 0, prolongation, smoothing.  x_dev is updated in place. */
+ * solve on level 0, prolongation, smoothing.  x_dev is updated in place.
+ * By default the cycle's kernels are captured into a CUDA graph on the first
+ * call for a given (sm, x_dev, b_dev, nu_pre, nu_post) and replayed on stream
+ * afterwards (the first call therefore must not happen during a capture of
+ * stream by the caller); the graph reads x_dev, b_dev and the smoother's
+ * damping at replay time.  While the timing hook records, cycles are
+ * launched kernel by kernel. */
 int vcycle(rav_mg* mg, rav_smoother* sm, double* x_dev, const double* b_dev, int nu_pre, int nu_post,
            rav_stream stream);
+
+/* Turns the graph replay of vcycle / solve on (default) or off (kernel-by-kernel
+ * launches; frees the captured graphs). */
+int rav_set_graphs(rav_mg* mg, int enable);
 
 typedef struct rav_solve_opts {
   double tol;      /* stop when ||r_k||_2 / ||r_0||_2 <= tol (Sec. 4 uses 1e-8) */
@@ -211,13 +221,16 @@ typedef struct rav_solve_info {
 int solve(rav_mg* mg, rav_smoother* sm, double* x_dev, const double* b_dev, const rav_solve_opts* opts,
           rav_solve_info* info, rav_stream stream);
 
-/* Timing hook.  While enabled, every subdomain kernel launch of the smoother
- * (vanka_apply, and the subdomain part of each smoothing step) is bracketed by
- * a pair of CUDA events recorded on its launching stream.  rav_profile_read
- * waits for the recorded events of level l and returns how many launches they
- * bracket and their summed duration in ms, then forgets them. */
-int rav_profile_enable(rav_smoother* sm, int enable);
-int rav_profile_read(rav_smoother* sm, int level, int64_t* launches, double* total_ms);
+/* Timing hook.  Kernel classes: 0 subdomain apply (also each MV colour
+ * sweep), 1 residual, 2 restriction, 3 prolongation, 4 coarse solve.  After
+ * rav_profile_enable(mg, mask, level), every launch of a class whose bit is set
+ * in mask, on the given level (-1: all levels), is bracketed by a pair of CUDA
+ * events recorded on its launching stream.  Enabling clears the totals;
+ * mask = 0 stops recording.  rav_profile_read waits for the recorded events
+ * and returns, for (level, class), the number of bracketed launches and their
+ * summed duration in ms since the last enable. */
+int rav_profile_enable(rav_mg* mg, unsigned kind_mask, int level);
+int rav_profile_read(rav_mg* mg, int level, int kind, int64_t* launches, double* total_ms);
 
 /* Number of kernels the solve path of this library (residuals, subdomain
  * applies, transfers, coarse solves, Krylov vector updates) has launched in

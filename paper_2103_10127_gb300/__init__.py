@@ -115,6 +115,10 @@ class Multigrid:
         check(_capi.load().rav_coarse_solve(self.h, _ptr(b), _ptr(x), _stream(stream)), "rav_coarse_solve")
         return x
 
+    def set_graphs(self, enable=True):
+        """Replay V-cycles as captured CUDA graphs (default) or launch kernel by kernel."""
+        check(_capi.load().rav_set_graphs(self.h, int(enable)), "rav_set_graphs")
+
     def vcycle(self, sm, x, b, nu_pre=2, nu_post=2, stream=None):
         check(_capi.load().vcycle(self.h, sm.h, _ptr(x), _ptr(b), nu_pre, nu_post, _stream(stream)), "vcycle")
         return x

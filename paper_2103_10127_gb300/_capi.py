@@ -52,9 +52,10 @@ _SIGS = {
     "vanka_smooth": (I32, [P, I32, P, P, I32, P]),
     "vanka_apply": (I32, [P, I32, P, P, P]),
     "vcycle": (I32, [P, P, P, P, I32, I32, P]),
+    "rav_set_graphs": (I32, [P, I32]),
     "solve": (I32, [P, P, P, P, ctypes.POINTER(RavSolveOpts), ctypes.POINTER(RavSolveInfo), P]),
-    "rav_profile_enable": (I32, [P, I32]),
-    "rav_profile_read": (I32, [P, I32, I64P, ctypes.POINTER(F64)]),
+    "rav_profile_enable": (I32, [P, ctypes.c_uint, I32]),
+    "rav_profile_read": (I32, [P, I32, I32, I64P, ctypes.POINTER(F64)]),
     "rav_kernel_launches": (ctypes.c_int64, []),
     "rav_strerror": (ctypes.c_char_p, [I32]),
 }

@@ -104,7 +104,39 @@ struct rav_mg {
   double* scalar_dev = nullptr;
   double* scalar_host = nullptr;  // pinned
   int part_cap = 0;
+  // timing hook (rav_profile_*): event pairs around the solve-path kernels
+  unsigned prof_mask = 0;  // bit k: record kernel class k (rav::PROF_*)
+  int prof_level = -1;     // record this level only, -1 = all
+  struct ProfRec {
+    int level, kind;
+    cudaEvent_t a, b;
+  };
+  std::vector<cudaEvent_t> ev_free;
+  std::vector<ProfRec> ev_used;
+  double prof_ms[rav::kMaxLevels][5] = {};
+  int64_t prof_cnt[rav::kMaxLevels][5] = {};
+  // captured V-cycles, replayed with cudaGraphLaunch (see vcycle in cycle.cu)
+  bool use_graphs = true;
+  cudaStream_t cap_stream = nullptr;
+  struct GraphEntry {
+    const rav_smoother* sm;
+    const double* x;
+    const double* b;
+    int nu1, nu2;
+    bool x_is_zero;
+    int64_t launches;  // kernels in one replay
+    cudaGraphExec_t exec;
+  };
+  std::vector<GraphEntry> graphs;
 };
+
+namespace rav {
+enum { PROF_APPLY = 0, PROF_RESIDUAL = 1, PROF_RESTRICT = 2, PROF_PROLONG = 3, PROF_COARSE = 4 };
+// Start/stop a recorded interval on stream s when class `kind` of `level` is
+// being recorded; *start is nullptr otherwise.  Defined in setup.cu.
+int prof_begin(rav_mg* mg, int level, int kind, cudaStream_t s, cudaEvent_t* start);
+int prof_end(rav_mg* mg, int level, int kind, cudaEvent_t start, cudaStream_t s);
+}  // namespace rav
 
 // Smoother data of one level: stored inverse rows and damping per subdomain.
 struct SmLevel {
@@ -122,10 +154,6 @@ struct rav_smoother {
   int kind = RAV_RAV, prec = RAV_F64;
   double omega = 0.5;
   SmLevel lev[rav::kMaxLevels];
-  // timing hook: event pairs around each subdomain kernel, per level
-  bool prof = false;
-  std::vector<cudaEvent_t> ev_free;
-  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_used[rav::kMaxLevels];
 };
 
 namespace rav {
@@ -211,8 +239,13 @@ int dot_impl(rav_mg* mg, const double* a, const double* b, int64_t n, double* ou
 }  // namespace rav
 
 // Smoother entry used by the cycle (defined in smoother.cu) and the V-cycle (cycle.cu).
-int rav_smooth_impl(rav_smoother* sm, int level, double* x, const double* b, int steps, cudaStream_t s);
+// x_is_zero: x is known to be 0, so the first residual is b itself (free rows)
+// and its SpMV is skipped (RAV, AV); the result is the same.
+int rav_smooth_impl(rav_smoother* sm, int level, double* x, const double* b, int steps, cudaStream_t s,
+                    bool x_is_zero = false);
 namespace rav {
 int vcycle_impl(rav_mg* mg, rav_smoother* sm, double* x, const double* b, int nu1, int nu2, bool x_is_zero,
                 cudaStream_t s);
+// Destroys the captured V-cycles that use smoother sm (all of them for nullptr).
+void drop_graphs(rav_mg* mg, const rav_smoother* sm);
 }

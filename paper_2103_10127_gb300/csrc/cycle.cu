@@ -20,24 +20,42 @@ __global__ void __launch_bounds__(256) k_residual_sell(int64_t nslots, const int
                                                        const double* __restrict__ sval,
                                                        const double* __restrict__ x, const double* __restrict__ b,
                                                        double* __restrict__ r, double* __restrict__ part) {
+  // one slice per warp, one slot per thread (no grid-stride loop: the hardware
+  // balances the slices of different lengths across the SMs)
   double acc2 = 0.0;
-  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < nslots;
-       t += (int64_t)gridDim.x * blockDim.x) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t < nslots) {
     const int64_t s = t >> 5;
     const int32_t row = sperm[t];
     const int len = slen[s];
     const int64_t base = sptr[s] + (t & 31);
-    double acc = 0.0;
+    double acc0 = 0.0, acc1 = 0.0;
     if (len > 1) {
       const int32_t* c = scol + base;
       const double* v = sval + base;
-#pragma unroll 4
-      for (int k = 0; k < len; ++k) acc += v[32 * k] * x[c[32 * k]];
+      int k = 0;
+      // eight independent gathers in flight per thread, two accumulators
+      for (; k + 8 <= len; k += 8) {
+        int ck[8];
+        double vk[8], xk[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) ck[j] = c[32 * (k + j)];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) vk[j] = v[32 * (k + j)];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) xk[j] = x[ck[j]];
+#pragma unroll
+        for (int j = 0; j < 8; j += 2) {
+          acc0 += vk[j] * xk[j];
+          acc1 += vk[j + 1] * xk[j + 1];
+        }
+      }
+      for (; k < len; ++k) acc0 += v[32 * k] * x[c[32 * k]];
     }
     if (row >= 0) {
-      const double rv = len > 1 ? b[row] - acc : 0.0;
+      const double rv = len > 1 ? b[row] - (acc0 + acc1) : 0.0;
       r[row] = rv;
-      acc2 += rv * rv;
+      acc2 = rv * rv;
     }
   }
   if (part) {
@@ -221,13 +239,16 @@ int residual_impl(rav_mg* mg, int level, const double* x, const double* b, doubl
                   cudaStream_t s) {
   const Level& L = mg->lev[level];
   const int64_t nslots = L.nslice * 32;
-  int blocks = (int)std::min<int64_t>((nslots + 255) / 256, (int64_t)mg->part_cap);
+  const int blocks = (int)((nslots + 255) / 256);
+  if (norm2_dev && blocks > mg->part_cap) return RAV_ERR_ARG;
   double* part = norm2_dev ? mg->norm_part : nullptr;
+  cudaEvent_t e0;
+  RAV_TRY(prof_begin(mg, level, PROF_RESIDUAL, s, &e0));
   k_residual_sell<<<blocks, 256, 0, s>>>(nslots, L.sperm, L.sptr, L.slen, L.scol, L.sval, x, b, r, part);
   if (norm2_dev) k_sum_parts<<<1, 256, 0, s>>>(mg->norm_part, blocks, norm2_dev, 1);
   note_launch(norm2_dev ? 2 : 1);
   RAV_CUDA(cudaGetLastError());
-  return RAV_OK;
+  return prof_end(mg, level, PROF_RESIDUAL, e0, s);
 }
 
 int dot_impl(rav_mg* mg, const double* a, const double* b, int64_t n, double* out_dev, cudaStream_t s) {
@@ -243,22 +264,26 @@ int restrict_impl(rav_mg* mg, int level, const double* rf, double* bc, cudaStrea
   const Level &F = mg->lev[level], &C = mg->lev[level - 1];
   const int64_t tot = C.g.nnode + C.g.n_p;
   const int blocks = (int)((tot + 127) / 128);
+  cudaEvent_t e0;
+  RAV_TRY(prof_begin(mg, level, PROF_RESTRICT, s, &e0));
   if (F.g.dim == 2) k_restrict_c<2><<<blocks, 128, 0, s>>>(F.g, C.g, F.tab(), rf, bc);
   else k_restrict_c<3><<<blocks, 128, 0, s>>>(F.g, C.g, F.tab(), rf, bc);
   note_launch();
   RAV_CUDA(cudaGetLastError());
-  return RAV_OK;
+  return prof_end(mg, level, PROF_RESTRICT, e0, s);
 }
 
 int prolong_impl(rav_mg* mg, int level, const double* xc, double* xf, cudaStream_t s) {
   const Level &F = mg->lev[level], &C = mg->lev[level - 1];
   const int64_t tot = F.g.nnode + F.g.n_p;
   const int blocks = (int)((tot + 127) / 128);
+  cudaEvent_t e0;
+  RAV_TRY(prof_begin(mg, level, PROF_PROLONG, s, &e0));
   if (F.g.dim == 2) k_prolong<2><<<blocks, 128, 0, s>>>(F.g, C.g, F.tab(), xc, xf);
   else k_prolong<3><<<blocks, 128, 0, s>>>(F.g, C.g, F.tab(), xc, xf);
   note_launch();
   RAV_CUDA(cudaGetLastError());
-  return RAV_OK;
+  return prof_end(mg, level, PROF_PROLONG, e0, s);
 }
 
 // x = C b (overwrite) or x += C b, with b masked to free rows.
@@ -267,11 +292,13 @@ static int coarse_apply(rav_mg* mg, const double* b, double* x, int accumulate, 
   const int64_t n = L.g.n;
   double* bm = L.b == b ? L.r : L.b;  // masked copy in whichever work vector is not the input
   if (bm == b) return RAV_ERR_ARG;
+  cudaEvent_t e0;
+  RAV_TRY(prof_begin(mg, 0, PROF_COARSE, s, &e0));
   k_mask_free<<<(int)((n + 255) / 256), 256, 0, s>>>(L.g, b, bm);
   k_coarse_gemv<<<(int)((n + 7) / 8), 256, 0, s>>>(n, mg->cinv, bm, x, accumulate);
   note_launch(2);
   RAV_CUDA(cudaGetLastError());
-  return RAV_OK;
+  return prof_end(mg, 0, PROF_COARSE, e0, s);
 }
 
 int coarse_impl(rav_mg* mg, const double* b, double* x, cudaStream_t s) { return coarse_apply(mg, b, x, 0, s); }
@@ -285,14 +312,11 @@ static int vcycle_rec(rav_mg* mg, rav_smoother* sm, int l, double* x, const doub
   if (l == 0) {
     if (x_is_zero) return coarse_apply(mg, b, x, 0, s);
     RAV_TRY(residual_impl(mg, 0, x, b, L.r, nullptr, s));
-    // masked copy of r goes to L.b; L.r is the input here
-    k_mask_free<<<(int)((L.g.n + 255) / 256), 256, 0, s>>>(L.g, L.r, L.b);
-    k_coarse_gemv<<<(int)((L.g.n + 7) / 8), 256, 0, s>>>(L.g.n, mg->cinv, L.b, x, 1);
-    note_launch(2);
-    RAV_CUDA(cudaGetLastError());
-    return RAV_OK;
+    return coarse_apply(mg, L.r, x, 1, s);  // x += C r (masked copy of r goes to L.b)
   }
-  RAV_TRY(rav_smooth_impl(sm, l, x, b, nu1, s));
+  // below the finest level x enters as 0 and b (a restricted residual) is 0 on
+  // Dirichlet rows, so the first smoothing step can take r = b
+  RAV_TRY(rav_smooth_impl(sm, l, x, b, nu1, s, x_is_zero && l < mg->nlev - 1));
   Level& C = mg->lev[l - 1];
   RAV_TRY(residual_impl(mg, l, x, b, L.r, nullptr, s));
   RAV_TRY(restrict_impl(mg, l, L.r, C.b, s));
@@ -306,6 +330,58 @@ static int vcycle_rec(rav_mg* mg, rav_smoother* sm, int l, double* x, const doub
 int vcycle_impl(rav_mg* mg, rav_smoother* sm, double* x, const double* b, int nu1, int nu2, bool x_is_zero,
                 cudaStream_t s) {
   return vcycle_rec(mg, sm, mg->nlev - 1, x, b, nu1, nu2, x_is_zero, s);
+}
+
+// One V-cycle as a CUDA graph.  The first call for a given (smoother, x, b,
+// nu1, nu2) captures the cycle's kernels on a private stream; every call
+// replays the instantiated graph on the caller's stream, which removes the
+// per-kernel launch latency that dominates the small levels.  Not used while
+// the timing hook records (its events would be baked into the graph).
+static int vcycle_graph(rav_mg* mg, rav_smoother* sm, double* x, const double* b, int nu1, int nu2, bool x_is_zero,
+                        cudaStream_t s) {
+  if (!mg->use_graphs || mg->prof_mask != 0) return vcycle_impl(mg, sm, x, b, nu1, nu2, x_is_zero, s);
+  rav_mg::GraphEntry* hit = nullptr;
+  for (auto& e : mg->graphs)
+    if (e.sm == sm && e.x == x && e.b == b && e.nu1 == nu1 && e.nu2 == nu2 && e.x_is_zero == x_is_zero) hit = &e;
+  if (!hit) {
+    // capturing runs nothing; the replay on s is ordered after s's earlier work
+    if (!mg->cap_stream) RAV_CUDA(cudaStreamCreateWithFlags(&mg->cap_stream, cudaStreamNonBlocking));
+    const int64_t l0 = rav_kernel_launches();
+    RAV_CUDA(cudaStreamBeginCapture(mg->cap_stream, cudaStreamCaptureModeThreadLocal));
+    const int rc = vcycle_impl(mg, sm, x, b, nu1, nu2, x_is_zero, mg->cap_stream);
+    cudaGraph_t graph = nullptr;
+    const cudaError_t ec = cudaStreamEndCapture(mg->cap_stream, &graph);
+    if (rc != RAV_OK || ec != cudaSuccess) {
+      if (graph) cudaGraphDestroy(graph);
+      if (ec != cudaSuccess) note_cuda_error(ec);
+      return rc != RAV_OK ? rc : RAV_ERR_CUDA;
+    }
+    cudaGraphExec_t exec = nullptr;
+    const cudaError_t ei = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    RAV_CUDA(ei);
+    if (mg->graphs.size() >= 32) {
+      cudaGraphExecDestroy(mg->graphs.front().exec);
+      mg->graphs.erase(mg->graphs.begin());
+    }
+    mg->graphs.push_back({sm, x, b, nu1, nu2, x_is_zero, rav_kernel_launches() - l0, exec});
+    hit = &mg->graphs.back();
+    note_launch((int)-hit->launches);  // counted again below, per replay
+  }
+  RAV_CUDA(cudaGraphLaunch(hit->exec, s));
+  note_launch((int)hit->launches);
+  return RAV_OK;
+}
+
+void drop_graphs(rav_mg* mg, const rav_smoother* sm) {
+  for (size_t i = 0; i < mg->graphs.size();) {
+    if (!sm || mg->graphs[i].sm == sm) {
+      cudaGraphExecDestroy(mg->graphs[i].exec);
+      mg->graphs.erase(mg->graphs.begin() + i);
+    } else {
+      ++i;
+    }
+  }
 }
 
 static int read_scalar(rav_mg* mg, const double* dev, double* host, cudaStream_t s) {
@@ -348,7 +424,14 @@ extern "C" int rav_coarse_solve(rav_mg* mg, const double* b, double* x, rav_stre
 extern "C" int vcycle(rav_mg* mg, rav_smoother* sm, double* x, const double* b, int nu1, int nu2,
                       rav_stream stream) {
   if (!mg || !sm || sm->mg != mg || !x || !b || nu1 < 0 || nu2 < 0) return RAV_ERR_ARG;
-  return vcycle_impl(mg, sm, x, b, nu1, nu2, false, S(stream));
+  return vcycle_graph(mg, sm, x, b, nu1, nu2, false, S(stream));
+}
+
+extern "C" int rav_set_graphs(rav_mg* mg, int enable) {
+  if (!mg) return RAV_ERR_ARG;
+  mg->use_graphs = enable != 0;
+  if (!mg->use_graphs) drop_graphs(mg, nullptr);
+  return RAV_OK;
 }
 
 // ---------------------------------------------------------------------------
@@ -366,7 +449,7 @@ static int solve_stationary(rav_mg* mg, rav_smoother* sm, double* x, const doubl
   int rc = RAV_ERR_NOT_CONVERGED, k = 0;
   double ratio = 1.0;
   for (k = 1; k <= o.maxit; ++k) {
-    RAV_TRY(vcycle_impl(mg, sm, x, b, o.nu_pre, o.nu_post, false, s));
+    RAV_TRY(vcycle_graph(mg, sm, x, b, o.nu_pre, o.nu_post, false, s));
     RAV_TRY(residual_impl(mg, mg->nlev - 1, x, b, L.r, mg->scalar_dev, s));
     RAV_TRY(read_scalar(mg, mg->scalar_dev, &rk, s));
     ratio = rk / r0;

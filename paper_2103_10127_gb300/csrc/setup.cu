@@ -2,9 +2,10 @@
 // CSR assembly on every level (the paper assembles on all grids, Sec. 4),
 // right-hand side, interpolation tables of the nested spaces and the explicit
 // inverse of the bordered coarse system (LU coarse solve of Sec. 2).
+#include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdio>
-#include <atomic>
 #include <cstring>
 
 #include "common.cuh"
@@ -15,6 +16,51 @@ static thread_local cudaError_t g_last_cuda = cudaSuccess;
 void note_cuda_error(cudaError_t e) { g_last_cuda = e; }
 static std::atomic<int64_t> g_launches{0};
 void note_launch(int k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
+
+static cudaEvent_t take_event(rav_mg* mg) {
+  if (mg->ev_free.empty()) {
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+    return e;
+  }
+  cudaEvent_t e = mg->ev_free.back();
+  mg->ev_free.pop_back();
+  return e;
+}
+
+int prof_begin(rav_mg* mg, int level, int kind, cudaStream_t s, cudaEvent_t* start) {
+  *start = nullptr;
+  if (!(mg->prof_mask >> kind & 1u) || (mg->prof_level >= 0 && mg->prof_level != level)) return RAV_OK;
+  cudaEvent_t e = take_event(mg);
+  if (!e) return RAV_ERR_CUDA;
+  RAV_CUDA(cudaEventRecord(e, s));
+  *start = e;
+  return RAV_OK;
+}
+
+int prof_end(rav_mg* mg, int level, int kind, cudaEvent_t start, cudaStream_t s) {
+  if (!start) return RAV_OK;
+  cudaEvent_t e = take_event(mg);
+  if (!e) return RAV_ERR_CUDA;
+  RAV_CUDA(cudaEventRecord(e, s));
+  mg->ev_used.push_back({level, kind, start, e});
+  return RAV_OK;
+}
+
+// Resolves the recorded intervals into the per-(level, class) totals.
+static int prof_collect(rav_mg* mg) {
+  for (auto& pr : mg->ev_used) {
+    RAV_CUDA(cudaEventSynchronize(pr.b));
+    float ms = 0.0f;
+    RAV_CUDA(cudaEventElapsedTime(&ms, pr.a, pr.b));
+    mg->prof_ms[pr.level][pr.kind] += ms;
+    mg->prof_cnt[pr.level][pr.kind] += 1;
+    mg->ev_free.push_back(pr.a);
+    mg->ev_free.push_back(pr.b);
+  }
+  mg->ev_used.clear();
+  return RAV_OK;
+}
 
 // ---------------------------------------------------------------------------
 // 1-D reference quantities on [0,1]: three-point Gauss rule, quadratic
@@ -879,7 +925,11 @@ extern "C" int mg_setup(const rav_problem* p, int n_levels, rav_stream stream, r
   for (int l = 1; l < n_levels; ++l)
     if ((rc = transfer_tables(mg, mg->lev[l - 1], mg->lev[l])) != RAV_OK) return fail(rc);
   if ((rc = coarse_inverse(mg, s)) != RAV_OK) return fail(rc);
+  // partial sums: one per residual block (256 rows) of the largest level, at
+  // least one per block of the grid-stride dot products
   mg->part_cap = 152 * 8;
+  for (int l = 0; l < n_levels; ++l)
+    mg->part_cap = std::max<int>(mg->part_cap, (int)((mg->lev[l].nslice * 32 + 255) / 256));
   if (cudaMalloc(&mg->norm_part, sizeof(double) * (mg->part_cap + 8)) != cudaSuccess) return fail(RAV_ERR_CUDA);
   if (cudaMalloc(&mg->scalar_dev, sizeof(double) * 64) != cudaSuccess) return fail(RAV_ERR_CUDA);
   if (cudaMallocHost(&mg->scalar_host, sizeof(double) * 64) != cudaSuccess) return fail(RAV_ERR_CUDA);
@@ -908,6 +958,13 @@ extern "C" void mg_destroy(rav_mg* mg) {
     cudaFree(L.x);
     cudaFree(L.b);
     cudaFree(L.r);
+  }
+  drop_graphs(mg, nullptr);
+  if (mg->cap_stream) cudaStreamDestroy(mg->cap_stream);
+  for (cudaEvent_t e : mg->ev_free) cudaEventDestroy(e);
+  for (auto& pr : mg->ev_used) {
+    cudaEventDestroy(pr.a);
+    cudaEventDestroy(pr.b);
   }
   cudaFree(mg->cinv);
   cudaFree(mg->blobs_dev);
@@ -973,6 +1030,27 @@ extern "C" int rav_initial_guess(rav_mg* mg, double* x, rav_stream stream) {
 }
 
 extern "C" int64_t rav_kernel_launches(void) { return g_launches.load(); }
+
+extern "C" int rav_profile_enable(rav_mg* mg, unsigned kind_mask, int level) {
+  if (!mg || level < -1 || level >= mg->nlev) return RAV_ERR_ARG;
+  RAV_TRY(prof_collect(mg));
+  mg->prof_mask = kind_mask & 31u;
+  mg->prof_level = level;
+  for (int l = 0; l < kMaxLevels; ++l)
+    for (int k = 0; k < 5; ++k) {
+      mg->prof_ms[l][k] = 0.0;
+      mg->prof_cnt[l][k] = 0;
+    }
+  return RAV_OK;
+}
+
+extern "C" int rav_profile_read(rav_mg* mg, int level, int kind, int64_t* launches, double* total_ms) {
+  if (!mg || !launches || !total_ms || level < 0 || level >= mg->nlev || kind < 0 || kind > 4) return RAV_ERR_ARG;
+  RAV_TRY(prof_collect(mg));
+  *launches = mg->prof_cnt[level][kind];
+  *total_ms = mg->prof_ms[level][kind];
+  return RAV_OK;
+}
 
 extern "C" const char* rav_strerror(int code) {
   switch (code) {

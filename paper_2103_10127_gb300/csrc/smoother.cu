@@ -1017,12 +1017,7 @@ extern "C" int vanka_setup(rav_mg* mg, int kind, int precision, double omega, ra
 extern "C" void vanka_destroy(rav_smoother* sm) {
   if (!sm) return;
   cudaDeviceSynchronize();
-  for (cudaEvent_t e : sm->ev_free) cudaEventDestroy(e);
-  for (int l = 0; l < kMaxLevels; ++l)
-    for (auto& pr : sm->ev_used[l]) {
-      cudaEventDestroy(pr.first);
-      cudaEventDestroy(pr.second);
-    }
+  if (sm->mg) drop_graphs(sm->mg, sm);
   for (int l = 0; l < kMaxLevels; ++l) {
     cudaFree(sm->lev[l].inv);
     cudaFree(sm->lev[l].ws);
@@ -1041,30 +1036,14 @@ extern "C" int rav_set_patch_omega(rav_smoother* sm, int level, const float* w, 
   return RAV_OK;
 }
 
-static cudaEvent_t take_event(rav_smoother* sm) {
-  if (sm->ev_free.empty()) {
-    cudaEvent_t e = nullptr;
-    if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
-    return e;
-  }
-  cudaEvent_t e = sm->ev_free.back();
-  sm->ev_free.pop_back();
-  return e;
-}
-
 static int apply_impl(rav_smoother* sm, int level, const double* r, double* x, cudaStream_t s) {
   rav_mg* mg = sm->mg;
   Level& L = mg->lev[level];
   SmLevel& SL = sm->lev[level];
   const Geo& g = L.g;
   const int D = g.dim;
-  cudaEvent_t e0 = nullptr, e1 = nullptr;
-  if (sm->prof) {
-    e0 = take_event(sm);
-    e1 = take_event(sm);
-    if (!e0 || !e1) return RAV_ERR_CUDA;
-    RAV_CUDA(cudaEventRecord(e0, s));
-  }
+  cudaEvent_t e0 = nullptr;
+  RAV_TRY(prof_begin(mg, level, PROF_APPLY, s, &e0));
   if (sm->kind == RAV_AV) {
     const unsigned gb = (unsigned)((g.n_p + 3) / 4);
     const int gg = (int)((g.n + 255) / 256);
@@ -1104,14 +1083,12 @@ static int apply_impl(rav_smoother* sm, int level, const double* r, double* x, c
     note_launch();
   }
   RAV_CUDA(cudaGetLastError());
-  if (sm->prof) {
-    RAV_CUDA(cudaEventRecord(e1, s));
-    sm->ev_used[level].push_back({e0, e1});
-  }
+  RAV_TRY(prof_end(mg, level, PROF_APPLY, e0, s));
   return RAV_OK;
 }
 
-int rav_smooth_impl(rav_smoother* sm, int level, double* x, const double* b, int steps, cudaStream_t s) {
+int rav_smooth_impl(rav_smoother* sm, int level, double* x, const double* b, int steps, cudaStream_t s,
+                    bool x_is_zero) {
   rav_mg* mg = sm->mg;
   Level& L = mg->lev[level];
   SmLevel& SL = sm->lev[level];
@@ -1120,6 +1097,8 @@ int rav_smooth_impl(rav_smoother* sm, int level, double* x, const double* b, int
   for (int it = 0; it < steps; ++it) {
     if (sm->kind == RAV_MV_COLOURED) {
       const int ncol = D == 2 ? 16 : 64;
+      cudaEvent_t e0;
+      RAV_TRY(prof_begin(mg, level, PROF_APPLY, s, &e0));
       for (int c = 0; c < ncol; ++c) {
         int cnt = 1;
         for (int d = 0; d < D; ++d) {
@@ -1133,6 +1112,12 @@ int rav_smooth_impl(rav_smoother* sm, int level, double* x, const double* b, int
         note_launch();
       }
       RAV_CUDA(cudaGetLastError());
+      RAV_TRY(prof_end(mg, level, PROF_APPLY, e0, s));
+      continue;
+    }
+    if (it == 0 && x_is_zero) {
+      // r = b - L 0 = b on free rows; b is 0 on Dirichlet rows of a coarse level
+      RAV_TRY(apply_impl(sm, level, b, x, s));
       continue;
     }
     RAV_TRY(residual_impl(mg, level, x, b, L.r, nullptr, s));
@@ -1236,27 +1221,3 @@ extern "C" int rav_get_inverse_rows(const rav_smoother* sm, int level, int64_t f
   return RAV_OK;
 }
 
-extern "C" int rav_profile_enable(rav_smoother* sm, int enable) {
-  if (!sm) return RAV_ERR_ARG;
-  sm->prof = enable != 0;
-  return RAV_OK;
-}
-
-extern "C" int rav_profile_read(rav_smoother* sm, int level, int64_t* launches, double* total_ms) {
-  if (!sm || !launches || !total_ms || level < 1 || level >= sm->mg->nlev) return RAV_ERR_ARG;
-  double tot = 0.0;
-  int64_t cnt = 0;
-  for (auto& pr : sm->ev_used[level]) {
-    RAV_CUDA(cudaEventSynchronize(pr.second));
-    float ms = 0.0f;
-    RAV_CUDA(cudaEventElapsedTime(&ms, pr.first, pr.second));
-    tot += ms;
-    ++cnt;
-    sm->ev_free.push_back(pr.first);
-    sm->ev_free.push_back(pr.second);
-  }
-  sm->ev_used[level].clear();
-  *launches = cnt;
-  *total_ms = tot;
-  return RAV_OK;
-}
