@@ -126,6 +126,28 @@ int rav_initial_guess(rav_mg* mg, double* x_dev, rav_stream stream);
 int rav_residual(rav_mg* mg, int level, const double* x_dev, const double* b_dev, double* r_dev,
                  double* norm_host, rav_stream stream);
 
+/* Same residual r = b - L x on level l as rav_residual, plus ||r||_2 written to
+ * the caller's device scalar norm_dev, with no memory allocation of any kind
+ * and no host synchronisation.  The paper has no counterpart: this exists for
+ * callers that cannot call cudaMalloc at the point where they need the
+ * residual (for instance while their stream is being captured into a CUDA
+ * graph, or in a loop that may only use memory reserved beforehand).
+ *  * Scratch: the norm's partial sums (one per 256 rows) go to a fixed array of
+ *    16,384 doubles (128 KiB) that the library keeps in device memory; every
+ *    GPU that loads the library holds it until the process exits.  A level
+ *    with more than 4,194,304 row slots (rows padded to slices of 32; 2-D
+ *    grids above about 680 x 680 cells, 3-D above about 55^3) is rejected with
+ *    RAV_ERR_ARG before anything is launched.
+ *  * The first call on a device looks up that array's device address (with
+ *    the device current) and caches it; make that first call before any
+ *    stream capture, and call with the device of mg current.
+ *  * All calls share the array and it keeps the last call's contents (every
+ *    call overwrites the entries it uses, nothing needs clearing first): calls
+ *    whose kernels overlap on the GPU (different streams, no ordering) race
+ *    and may return wrong norms.  r_dev and norm_dev belong to the caller. */
+int rav_residual_norm_noalloc(rav_mg* mg, int level, const double* x_dev, const double* b_dev, double* r_dev,
+                              double* norm_dev, rav_stream stream);
+
 /* Grid transfers between level l-1 (coarse) and l (fine), canonical nested
  * interpolation P of the Q2 velocity and Q1 pressure spaces (the paper builds
  * its transfers from the grid hierarchy, Sec. 2):

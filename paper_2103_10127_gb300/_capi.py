@@ -40,6 +40,7 @@ _SIGS = {
     "rav_assemble_rhs": (I32, [P, I32, P, P]),
     "rav_initial_guess": (I32, [P, P, P]),
     "rav_residual": (I32, [P, I32, P, P, P, ctypes.POINTER(F64), P]),
+    "rav_residual_norm_noalloc": (I32, [P, I32, P, P, P, P, P]),
     "rav_restrict": (I32, [P, I32, P, P, P]),
     "rav_prolong_add": (I32, [P, I32, P, P, P]),
     "rav_coarse_solve": (I32, [P, P, P, P]),

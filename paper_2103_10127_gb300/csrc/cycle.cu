@@ -1,6 +1,7 @@
 // Residual (Eq. 10), grid transfers, coarse solve, V-cycle (Sec. 2, Fig. 1)
 // and the outer iterations (stationary multigrid and FGMRES, Sec. 4).
 #include <cmath>
+#include <mutex>
 #include <vector>
 
 #include "common.cuh"
@@ -425,6 +426,53 @@ extern "C" int vcycle(rav_mg* mg, rav_smoother* sm, double* x, const double* b, 
                       rav_stream stream) {
   if (!mg || !sm || sm->mg != mg || !x || !b || nu1 < 0 || nu2 < 0) return RAV_ERR_ARG;
   return vcycle_graph(mg, sm, x, b, nu1, nu2, false, S(stream));
+}
+
+// ---------------------------------------------------------------------------
+// Residual and norm without any allocation, for callers that must not call
+// cudaMalloc (code running while a stream is captured into a CUDA graph, or
+// real-time loops that work from memory reserved up front).  The per-block
+// partial sums of the norm live in this fixed device array instead of the
+// hierarchy's work buffer.  Every GPU that loads the library holds the array
+// until the process exits.
+static constexpr int kNoAllocParts = 16384;  // partial sums: one per 256 rows
+static __device__ __align__(256) double g_noalloc_parts[kNoAllocParts];
+static constexpr int kMaxDevices = 64;
+static double* g_noalloc_addr[kMaxDevices] = {};
+static std::mutex g_noalloc_mu;
+
+// Device address of g_noalloc_parts on the current device.  In host code the
+// symbol is only a stand-in; the address is looked up once per device, with
+// that device current, and remembered.
+static int noalloc_parts_address(double** out) {
+  int dev = 0;
+  RAV_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kMaxDevices) return RAV_ERR_ARG;
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  if (!g_noalloc_addr[dev]) {
+    void* p = nullptr;
+    RAV_CUDA(cudaGetSymbolAddress(&p, g_noalloc_parts));
+    g_noalloc_addr[dev] = static_cast<double*>(p);
+  }
+  *out = g_noalloc_addr[dev];
+  return RAV_OK;
+}
+
+extern "C" int rav_residual_norm_noalloc(rav_mg* mg, int level, const double* x, const double* b, double* r,
+                                         double* norm_dev, rav_stream stream) {
+  if (!mg || !x || !b || !r || !norm_dev || level < 0 || level >= mg->nlev) return RAV_ERR_ARG;
+  const Level& L = mg->lev[level];
+  const int64_t nslots = L.nslice * 32;
+  const int64_t blocks = (nslots + 255) / 256;
+  if (blocks > kNoAllocParts) return RAV_ERR_ARG;  // level has more than 4,194,304 row slots
+  double* parts = nullptr;
+  RAV_TRY(noalloc_parts_address(&parts));
+  cudaStream_t s = S(stream);
+  k_residual_sell<<<(unsigned)blocks, 256, 0, s>>>(nslots, L.sperm, L.sptr, L.slen, L.scol, L.sval, x, b, r, parts);
+  k_sum_parts<<<1, 256, 0, s>>>(parts, (int)blocks, norm_dev, 1);
+  note_launch(2);
+  RAV_CUDA(cudaGetLastError());
+  return RAV_OK;
 }
 
 extern "C" int rav_set_graphs(rav_mg* mg, int enable) {
