@@ -56,7 +56,8 @@ def parse():
     ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="2d512", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default="2d512", choices=sorted(WORKLOADS) + ["2d-batch"])
+    ap.add_argument("--nprob", type=int, default=256, help="problems of the 2d-batch workload")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-tol", action="store_true")
@@ -384,8 +385,84 @@ def ctypes_f64():
     return ctypes.c_double(0.0)
 
 
+def run_batch(args):
+    """256 independent 2-D lid-driven cavities, N = 16 m with m uniform on
+    {2..16} (seeded), 8 right-hand sides each (lid values + iid N(0,1) forcing
+    on free velocity DoFs), FP32 patch inverses, FP64 residuals; a step is one
+    batched V(2,2) cycle of every problem and right-hand side."""
+    import numpy as np
+    import torch
+    import paper_2103_10127_gb300 as R
+    from paper_2103_10127_gb300 import _capi, inputs
+
+    torch.cuda.set_device(0)
+    lib = _capi.load()
+    nprob, nrhs = args.nprob, 8
+    sizes = inputs.batched_sizes(inputs.BASE_SEED, nprob)
+    mgs, sms, xs, bs = [], [], [], []
+    t0 = time.perf_counter()
+    for i, N in enumerate(sizes):
+        N = int(N)
+        mg = R.Multigrid(2, N, inputs.levels_for(N), bc=R.BC_CAVITY)
+        sm = R.Smoother(mg, R.RAV, R.F32, 0.5)
+        n = mg.n()
+        M = 2 * N + 1
+        idx = np.indices((M, M)).reshape(2, -1)[::-1]
+        inner = np.repeat(np.all((idx > 0) & (idx < M - 1), axis=0), 2)
+        free = np.concatenate([inner, np.zeros((N + 1) ** 2, bool)])
+        lid = mg.rhs(R.F_NONE).cpu().numpy()
+        b = np.repeat(lid[:, None], nrhs, axis=1)
+        b[free, :] += inputs.normal(inputs.BASE_SEED + 7919 * (i + 1), int(free.sum()) * nrhs).reshape(-1, nrhs)
+        x0 = mg.initial_guess().cpu().numpy()
+        mgs.append(mg)
+        sms.append(sm)
+        bs.append(torch.from_numpy(np.ascontiguousarray(b)).cuda())
+        xs.append(torch.from_numpy(np.ascontiguousarray(np.repeat(x0[:, None], nrhs, axis=1))).cuda())
+    bt = R.Batch(mgs, sms, nrhs)
+    setup_s = time.perf_counter() - t0
+    dofs = sum(m.n() for m in mgs)
+    x_init = [x.clone() for x in xs]
+    stream = torch.cuda.current_stream()
+    for _ in range(args.warmup):
+        bt.vcycle(xs, bs, 2, 2)
+    torch.cuda.synchronize()
+    launches0 = lib.rav_kernel_launches()
+    clk = clocks_start()
+    time.sleep(0.3)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        bt.vcycle(xs, bs, 2, 2)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    clocks = clocks_stop(clk, 0)
+    launches = lib.rav_kernel_launches() - launches0
+    for x, xi in zip(xs, x_init):
+        x.copy_(xi)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    it, ratios, rc = bt.solve(xs, bs, tol=1e-8, maxit=100, raise_on_error=False)
+    tsolve = time.perf_counter() - t0
+    out = {"metric": "V-cycle DoFs/s", "value": dofs * nrhs * args.steps / (ms / 1e3), "unit": "DoF/s",
+           "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": f"{nprob} 2D Q2-Q1 lid-driven cavities, N = 16 m, m ~ U{{2..16}} (seed 2103), "
+                                  f"{nrhs} RHS each, RAV V(2,2) omega 0.5, FP32 patch inverses, FP64 residuals",
+                      "problems": nprob, "rhs": nrhs, "dofs_total": dofs, "sizes_min_max": [int(sizes.min()),
+                                                                                            int(sizes.max())],
+                      "tuning": bt.tuning(), "setup_s": setup_s},
+           "gpu_launches": int(launches), "clocks": clocks,
+           "time_to_tol": {"seconds": tsolve, "max_cycles": int(it.max()), "min_cycles": int(it.min()),
+                           "status": rc, "tol": 1e-8}}
+    print(json.dumps(out), flush=True)
+
+
 def main():
     args = parse()
+    if args.workload == "2d-batch":
+        run_batch(args)
+        return
     W = dict(WORKLOADS[args.workload])
     if args.N:
         W["N"] = args.N

@@ -243,6 +243,38 @@ typedef struct rav_solve_info {
 int solve(rav_mg* mg, rav_smoother* sm, double* x_dev, const double* b_dev, const rav_solve_opts* opts,
           rav_solve_info* info, rav_stream stream);
 
+/* ---- Batched solves: many problems x several right-hand sides ------------
+ * A batch groups nprob hierarchies (any mix of sizes and depths, one
+ * dimension) with their RAV smoothers, which must store dense owned rows
+ * (RAV_F32 or RAV_F64_ROWS), and advances nrhs (1, 2, 4 or 8) right-hand
+ * sides of every problem together.  Vectors of problem p are RHS-interleaved:
+ * x_dev[p][row * nrhs + k], n(p) * nrhs doubles, numbering as above.  Each
+ * phase of the V-cycle is one kernel launch over all problems; the cycle is
+ * captured into a CUDA graph on first use and replayed.  Per right-hand side
+ * the result equals the single-problem vcycle() with the same smoother bit for
+ * bit.  batch_setup times candidate launch shapes on the batch's own data and
+ * keeps the fastest (batch_get_tuning reports them).  The batch does not own
+ * the hierarchies or smoothers; destroy it first. */
+typedef struct rav_batch rav_batch;
+int batch_setup(rav_mg* const* mgs, rav_smoother* const* sms, int nprob, int nrhs, rav_stream stream,
+                rav_batch** out);
+void batch_destroy(rav_batch* bt);
+/* out[0] = threads per block of the residual kernel, out[1] = of the apply kernel. */
+int batch_get_tuning(const rav_batch* bt, int out[2]);
+/* One V(nu_pre, nu_post) cycle of every problem and right-hand side; x_dev[p]
+ * updated in place, b_dev[p] read.  Synchronises the stream before rebinding
+ * changed vector pointers. */
+int batch_vcycle(rav_batch* bt, double* const* x_dev, const double* const* b_dev, int nu_pre, int nu_post,
+                 rav_stream stream);
+/* Stationary batched multigrid (opts->outer must be 0) until every problem
+ * and right-hand side has ||r_k||/||r_0|| <= tol or maxit cycles are done;
+ * iters_host[p * nrhs + k] = cycles that (p, k) needed (-1: not reached),
+ * ratios_host[p * nrhs + k] = its last ratio.  Host-driven, one
+ * synchronisation per cycle.  Returns RAV_ERR_NOT_CONVERGED if any (p, k)
+ * missed the tolerance. */
+int solve_batched(rav_batch* bt, double* const* x_dev, const double* const* b_dev, const rav_solve_opts* opts,
+                  int* iters_host, double* ratios_host, rav_stream stream);
+
 /* Timing hook.  Kernel classes: 0 subdomain apply (also each MV colour
  * sweep), 1 residual, 2 restriction, 3 prolongation, 4 coarse solve.  After
  * rav_profile_enable(mg, mask, level), every launch of a class whose bit is set

@@ -22,7 +22,7 @@ F64, F32, BF16, FP8, F64_ROWS = 0, 1, 2, 3, 4
 BC_CAVITY, BC_NOSLIP, BC_QUADRATIC = 0, 1, 2
 F_NONE, F_PSI, F_SINKER, F_QUADRATIC = 0, 1, 2, 3
 
-__all__ = ["Multigrid", "Smoother", "RavError", "RAV", "AV", "MV_COLOURED", "F64", "F32", "BF16", "FP8", "F64_ROWS",
+__all__ = ["Multigrid", "Smoother", "Batch", "RavError", "RAV", "AV", "MV_COLOURED", "F64", "F32", "BF16", "FP8", "F64_ROWS",
            "BC_CAVITY", "BC_NOSLIP", "BC_QUADRATIC", "F_NONE", "F_PSI", "F_SINKER", "F_QUADRATIC"]
 
 
@@ -134,6 +134,53 @@ class Multigrid:
         if raise_on_error and rc != 0:
             raise RavError(rc, "solve")
         return info.iterations, hist[: info.iterations + 1].copy(), rc
+
+
+class Batch:
+    """Many problems x nrhs right-hand sides advanced together (batch_setup).
+
+    Vectors are RHS-interleaved: a problem's x has n * nrhs entries, entry
+    (row, k) at row * nrhs + k (a torch tensor of shape (n, nrhs), contiguous)."""
+
+    def __init__(self, mgs, sms, nrhs, stream=None):
+        lib = _capi.load()
+        self.mgs, self.sms, self.nrhs = list(mgs), list(sms), nrhs
+        self._mg_arr = (ctypes.c_void_p * len(mgs))(*[m.h.value for m in mgs])
+        self._sm_arr = (ctypes.c_void_p * len(sms))(*[s.h.value for s in sms])
+        h = ctypes.c_void_p()
+        check(lib.batch_setup(self._mg_arr, self._sm_arr, len(mgs), nrhs, _stream(stream), ctypes.byref(h)),
+              "batch_setup")
+        self.h = h
+
+    def __del__(self):
+        if getattr(self, "h", None) is not None and _capi._lib is not None:
+            _capi._lib.batch_destroy(self.h)
+            self.h = None
+
+    def tuning(self):
+        out = (ctypes.c_int * 2)()
+        check(_capi.load().batch_get_tuning(self.h, out), "batch_get_tuning")
+        return {"residual_threads": out[0], "apply_threads": out[1]}
+
+    @staticmethod
+    def _ptrs(ts):
+        return (ctypes.c_void_p * len(ts))(*[_ptr(t).value for t in ts])
+
+    def vcycle(self, xs, bs, nu_pre=2, nu_post=2, stream=None):
+        check(_capi.load().batch_vcycle(self.h, self._ptrs(xs), self._ptrs(bs), nu_pre, nu_post, _stream(stream)),
+              "batch_vcycle")
+        return xs
+
+    def solve(self, xs, bs, tol=1e-8, maxit=100, nu_pre=2, nu_post=2, stream=None, raise_on_error=True):
+        """Returns (iterations[nprob, nrhs], ratios[nprob, nrhs], status)."""
+        opts = _capi.RavSolveOpts(tol, maxit, nu_pre, nu_post, 0, 30, 0.0)
+        it = np.zeros(len(xs) * self.nrhs, np.int32)
+        ra = np.zeros(len(xs) * self.nrhs)
+        rc = _capi.load().solve_batched(self.h, self._ptrs(xs), self._ptrs(bs), ctypes.byref(opts),
+                                        it.ctypes.data, ra.ctypes.data, _stream(stream))
+        if raise_on_error and rc != 0:
+            raise RavError(rc, "solve_batched")
+        return it.reshape(len(xs), self.nrhs), ra.reshape(len(xs), self.nrhs), rc
 
 
 class Smoother:

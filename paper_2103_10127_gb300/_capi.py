@@ -58,6 +58,11 @@ _SIGS = {
     "rav_profile_enable": (I32, [P, ctypes.c_uint, I32]),
     "rav_profile_read": (I32, [P, I32, I32, I64P, ctypes.POINTER(F64)]),
     "rav_kernel_launches": (ctypes.c_int64, []),
+    "batch_setup": (I32, [P, P, I32, I32, P, ctypes.POINTER(P)]),
+    "batch_destroy": (None, [P]),
+    "batch_get_tuning": (I32, [P, ctypes.POINTER(I32)]),
+    "batch_vcycle": (I32, [P, P, P, I32, I32, P]),
+    "solve_batched": (I32, [P, P, P, ctypes.POINTER(RavSolveOpts), P, P, P]),
     "rav_strerror": (ctypes.c_char_p, [I32]),
 }
 

@@ -1,0 +1,897 @@
+// Batched RAV multigrid: many independent problems of uneven size, each with
+// nrhs right-hand sides, advanced together.
+//
+// * Vectors of a batch are RHS-interleaved: entry (row, k) at row * nrhs + k,
+//   so every matrix, transfer or inverse entry loaded from HBM serves all
+//   right-hand sides.
+// * Each phase of the V-cycle (residual, subdomain apply, restriction, coarse
+//   solve, prolongation) is one kernel launch over every (problem, level) that
+//   takes part in it at that depth below the finest grid; blocks find their
+//   problem by binary search in a block-offset table.  Problems whose
+//   hierarchy is shallower reach their coarse solve at a smaller depth.
+// * The per-(problem, level) descriptors live in device memory, so the whole
+//   batched cycle is captured once into a CUDA graph and replayed, the
+//   callers' vector pointers being updated in the descriptors between replays.
+// * Per right-hand side the kernels add in the same order as the one-problem
+//   kernels, so a batched cycle reproduces the single-problem cycle bit for bit.
+// * Launch shapes (threads per block of the residual and apply kernels) are
+//   chosen at set-up by timing the candidates on the batch's finest levels.
+#include <cuda_bf16.h>
+
+#include <algorithm>
+#include <cmath>
+#include <type_traits>
+#include <vector>
+
+#include "box.cuh"
+#include "common.cuh"
+
+namespace rav {
+
+struct BLevel {
+  Geo g;
+  Geo gc;  // next coarser level (restriction target, prolongation source)
+  int64_t nslice;
+  const int32_t* sperm;
+  const int64_t* sptr;
+  const int32_t* slen;
+  const int32_t* scol;
+  const double* sval;
+  const void* inv;  // dense owned rows of the RAV inverses (float or double)
+  const double* omega;
+  int64_t units;
+  XferTab tab;      // interpolation into this level from the coarser one
+  double* x;        // n x nrhs
+  double* b;
+  double* r;
+  double* xc;       // coarser level's x and b
+  double* bc;
+  const double* cinv;  // bordered coarse inverse (coarsest level only)
+  int problem;
+};
+
+__device__ __forceinline__ int find_entry(const int64_t* __restrict__ first, int ne, int64_t blk) {
+  int lo = 0, hi = ne;  // first[lo] <= blk < first[hi]
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (first[mid] <= blk) lo = mid;
+    else hi = mid;
+  }
+  return lo;
+}
+
+// r = b - L x for every right-hand side (same addition order per RHS as
+// k_residual_sell), with per-block partial sums of r^2 per RHS when part != 0.
+template <int NR>
+__global__ void kb_residual(const BLevel* __restrict__ L, const int64_t* __restrict__ first, int ne,
+                            double* __restrict__ part) {
+  const int e = find_entry(first, ne, blockIdx.x);
+  const BLevel& lv = L[e];
+  const int64_t t = (blockIdx.x - first[e]) * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t nslots = lv.nslice * 32;
+  double sq[NR];
+#pragma unroll
+  for (int j = 0; j < NR; ++j) sq[j] = 0.0;
+  if (t < nslots) {
+    const int64_t s = t >> 5;
+    const int32_t row = lv.sperm[t];
+    const int len = lv.slen[s];
+    const int64_t base = lv.sptr[s] + (t & 31);
+    double a0[NR], a1[NR];
+#pragma unroll
+    for (int j = 0; j < NR; ++j) a0[j] = a1[j] = 0.0;
+    if (len > 1) {
+      const int32_t* c = lv.scol + base;
+      const double* v = lv.sval + base;
+      const int full = len & ~7;
+      for (int k = 0; k < full; k += 2) {
+        const double v0 = v[32 * k], v1 = v[32 * (k + 1)];
+        const double* x0 = lv.x + (int64_t)c[32 * k] * NR;
+        const double* x1 = lv.x + (int64_t)c[32 * (k + 1)] * NR;
+#pragma unroll
+        for (int j = 0; j < NR; ++j) {
+          a0[j] += v0 * x0[j];
+          a1[j] += v1 * x1[j];
+        }
+      }
+      for (int k = full; k < len; ++k) {
+        const double v0 = v[32 * k];
+        const double* x0 = lv.x + (int64_t)c[32 * k] * NR;
+#pragma unroll
+        for (int j = 0; j < NR; ++j) a0[j] += v0 * x0[j];
+      }
+    }
+    if (row >= 0) {
+#pragma unroll
+      for (int j = 0; j < NR; ++j) {
+        const double rv = len > 1 ? lv.b[(int64_t)row * NR + j] - (a0[j] + a1[j]) : 0.0;
+        lv.r[(int64_t)row * NR + j] = rv;
+        sq[j] = rv * rv;
+      }
+    }
+  }
+  if (part) {
+#pragma unroll
+    for (int j = 0; j < NR; ++j) {
+      const double bs = block_sum(sq[j]);
+      if (threadIdx.x == 0) part[blockIdx.x * NR + j] = bs;
+    }
+  }
+}
+
+// Sum of the partials of each (problem, RHS): norms[p * NR + j] = sqrt(sum).
+template <int NR>
+__global__ void kb_norm_final(const int64_t* __restrict__ first, const int* __restrict__ prob, int ne,
+                              const double* __restrict__ part, double* __restrict__ norms) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= ne * NR) return;
+  const int e = t / NR, j = t % NR;
+  double s = 0.0;
+  for (int64_t blk = first[e]; blk < first[e + 1]; ++blk) s += part[blk * NR + j];
+  norms[prob[e] * NR + j] = sqrt(s);
+}
+
+// RAV apply with dense owned rows, all right-hand sides at once (same order
+// per RHS as k_rav_apply).  use_b: the residual is b (x entered as 0).
+template <int D, typename T, int NR>
+__global__ void kb_apply(const BLevel* __restrict__ L, const int64_t* __restrict__ first, int ne, int use_b) {
+  using B = BoxT<D>;
+  constexpr int NC = B::NC, RB = B::RB, NCH = B::NCH;
+  using Acc = typename std::conditional<std::is_same<T, double>::value, double, float>::type;
+  const int e = find_entry(first, ne, blockIdx.x);
+  const BLevel& lv = L[e];
+  const int64_t u = (blockIdx.x - first[e]) * (int64_t)blockDim.x + threadIdx.x;
+  if (u >= lv.units) return;
+  const Geo& g = lv.g;
+  const double* __restrict__ r = use_b ? lv.b : lv.r;
+  const int64_t p = u / NCH;
+  const int h = (int)(u % NCH);
+  int v[3] = {0, 0, 0};
+  vertex_of(g, p, v);
+  const int M = (int)g.M;
+  int alo[3] = {0, 0, 0}, ahi[3] = {0, 0, 0};
+  for (int d = 0; d < D; ++d) {
+    alo[d] = 2 - 2 * v[d] > 0 ? 2 - 2 * v[d] : 0;
+    ahi[d] = 2 * g.N - 2 * v[d] + 2 < 4 ? 2 * g.N - 2 * v[d] + 2 : 4;
+  }
+  int64_t base = 0;
+  for (int d = D - 1; d >= 0; --d) base = base * M + (2 * v[d] - 2);
+  base *= D;
+  const T* ip = static_cast<const T*>(lv.inv) + ((u >> 5) * NC * RB) * 32 + (u & 31);
+  Acc acc[RB][NR];
+#pragma unroll
+  for (int i = 0; i < RB; ++i)
+#pragma unroll
+    for (int j = 0; j < NR; ++j) acc[i][j] = 0;
+  int k = 0;
+  for (int a2 = 0; a2 < (D == 3 ? 5 : 1); ++a2) {
+    const bool v2 = D == 2 || (a2 >= alo[2] && a2 <= ahi[2]);
+    for (int a1 = 0; a1 < 5; ++a1) {
+      const bool v1 = v2 && a1 >= alo[1] && a1 <= ahi[1];
+      const int64_t rowoff = base + (int64_t)D * M * (a1 + (int64_t)M * a2);
+      for (int a0 = 0; a0 < 5; ++a0) {
+        const bool vv = v1 && a0 >= alo[0] && a0 <= ahi[0];
+        for (int c = 0; c < D; ++c) {
+          Acc ra[NR];
+#pragma unroll
+          for (int j = 0; j < NR; ++j) ra[j] = (Acc)(vv ? r[(rowoff + D * a0 + c) * NR + j] : 0.0);
+#pragma unroll
+          for (int i = 0; i < RB; ++i) {
+            const Acc q = (Acc)ip[(k * RB + i) * 32];
+#pragma unroll
+            for (int j = 0; j < NR; ++j) acc[i][j] += q * ra[j];
+          }
+          ++k;
+        }
+      }
+    }
+  }
+  {
+    Acc ra[NR];
+#pragma unroll
+    for (int j = 0; j < NR; ++j) ra[j] = (Acc)r[(g.n_u + p) * NR + j];
+#pragma unroll
+    for (int i = 0; i < RB; ++i) {
+      const Acc q = (Acc)ip[(k * RB + i) * 32];
+#pragma unroll
+      for (int j = 0; j < NR; ++j) acc[i][j] += q * ra[j];
+    }
+  }
+  const double om = lv.omega[p];
+#pragma unroll
+  for (int i = 0; i < RB; ++i) {
+    const int jrow = h * RB + i;
+    int64_t dof = -1;
+    if (jrow < B::NR - 1) {
+      const int q = jrow / D, c = jrow % D;
+      int64_t J[3] = {0, 0, 0};
+      bool ok = true;
+      for (int d = 0; d < D; ++d) {
+        J[d] = 2 * v[d] + ((q >> d) & 1);
+        ok &= (J[d] >= 1) & (J[d] <= 2 * g.N - 1);
+      }
+      if (ok) dof = D * node_id(g, J) + c;
+    } else {
+      dof = g.n_u + p;
+    }
+    if (dof >= 0) {
+#pragma unroll
+      for (int j = 0; j < NR; ++j) lv.x[dof * NR + j] += om * (double)acc[i][j];
+    }
+  }
+}
+
+// Restriction into the coarser level (same order per RHS as k_restrict_c);
+// also zeroes the coarser iterate.
+template <int D, int NR>
+__global__ void kb_restrict(const BLevel* __restrict__ L, const int64_t* __restrict__ first, int ne) {
+  const int e = find_entry(first, ne, blockIdx.x);
+  const BLevel& lv = L[e];
+  const Geo &gf = lv.g, &gc = lv.gc;
+  const XferTab& T = lv.tab;
+  const int t = (int)((blockIdx.x - first[e]) * blockDim.x + threadIdx.x);
+  const int Mf = (int)gf.M, Mc = (int)gc.M, nnc = (int)gc.nnode;
+  const double* rf = lv.r;
+  if (t < nnc) {
+    int K[3] = {0, 0, 0}, id = t;
+    bool bnd = false;
+    for (int a = 0; a < D; ++a) {
+      K[a] = id % Mc;
+      id /= Mc;
+      bnd |= (K[a] == 0) | (K[a] == Mc - 1);
+    }
+    double acc[D][NR];
+#pragma unroll
+    for (int c = 0; c < D; ++c)
+#pragma unroll
+      for (int j = 0; j < NR; ++j) acc[c][j] = 0.0;
+    if (!bnd) {
+      const int c0 = T.rc2[0][K[0]], c1 = T.rc2[1][K[1]], c2 = D == 3 ? T.rc2[2][K[2]] : 1;
+      for (int j2 = 0; j2 < c2; ++j2) {
+        const int I2 = D == 3 ? T.rk2[2][7 * K[2] + j2] : 0;
+        const double w2 = D == 3 ? T.rw2[2][7 * K[2] + j2] : 1.0;
+        for (int j1 = 0; j1 < c1; ++j1) {
+          const int I1 = T.rk2[1][7 * K[1] + j1];
+          const double w12 = D == 3 ? w2 * T.rw2[1][7 * K[1] + j1] : T.rw2[1][7 * K[1] + j1];
+          const int64_t rowbase = (int64_t)D * Mf * (I1 + (int64_t)Mf * I2);
+          for (int j0 = 0; j0 < c0; ++j0) {
+            const double ww = w12 * T.rw2[0][7 * K[0] + j0];
+            const int64_t bse = rowbase + D * T.rk2[0][7 * K[0] + j0];
+#pragma unroll
+            for (int c = 0; c < D; ++c)
+#pragma unroll
+              for (int j = 0; j < NR; ++j) acc[c][j] += ww * rf[(bse + c) * NR + j];
+          }
+        }
+      }
+    }
+#pragma unroll
+    for (int c = 0; c < D; ++c)
+#pragma unroll
+      for (int j = 0; j < NR; ++j) {
+        lv.bc[((int64_t)D * t + c) * NR + j] = acc[c][j];
+        lv.xc[((int64_t)D * t + c) * NR + j] = 0.0;
+      }
+  } else if (t < nnc + (int)gc.n_p) {
+    const int Nf1 = gf.N + 1, Nc1 = gc.N + 1;
+    int K[3] = {0, 0, 0}, id = t - nnc;
+    for (int a = 0; a < D; ++a) { K[a] = id % Nc1; id /= Nc1; }
+    const int c0 = T.rc1[0][K[0]], c1 = T.rc1[1][K[1]], c2 = D == 3 ? T.rc1[2][K[2]] : 1;
+    double acc[NR];
+#pragma unroll
+    for (int j = 0; j < NR; ++j) acc[j] = 0.0;
+    for (int j2 = 0; j2 < c2; ++j2) {
+      const int V2 = D == 3 ? T.rk1[2][3 * K[2] + j2] : 0;
+      const double w2 = D == 3 ? T.rw1[2][3 * K[2] + j2] : 1.0;
+      for (int j1 = 0; j1 < c1; ++j1) {
+        const int V1 = T.rk1[1][3 * K[1] + j1];
+        const double w12 = D == 3 ? w2 * T.rw1[1][3 * K[1] + j1] : T.rw1[1][3 * K[1] + j1];
+        for (int j0 = 0; j0 < c0; ++j0) {
+          const double ww = w12 * T.rw1[0][3 * K[0] + j0];
+          const int64_t idx = gf.n_u + T.rk1[0][3 * K[0] + j0] + Nf1 * (V1 + (int64_t)Nf1 * V2);
+#pragma unroll
+          for (int j = 0; j < NR; ++j) acc[j] += ww * rf[idx * NR + j];
+        }
+      }
+    }
+    const int64_t o = gc.n_u + (t - nnc);
+#pragma unroll
+    for (int j = 0; j < NR; ++j) {
+      lv.bc[o * NR + j] = acc[j];
+      lv.xc[o * NR + j] = 0.0;
+    }
+  }
+}
+
+// x += P xc (same order per RHS as k_prolong).
+template <int D, int NR>
+__global__ void kb_prolong(const BLevel* __restrict__ L, const int64_t* __restrict__ first, int ne) {
+  const int e = find_entry(first, ne, blockIdx.x);
+  const BLevel& lv = L[e];
+  const Geo &gf = lv.g, &gc = lv.gc;
+  const XferTab& T = lv.tab;
+  const int t = (int)((blockIdx.x - first[e]) * blockDim.x + threadIdx.x);
+  const int Mf = (int)gf.M, Mc = (int)gc.M, nnf = (int)gf.nnode;
+  const double* xc = lv.xc;
+  if (t < nnf) {
+    int I[3] = {0, 0, 0}, id = t;
+    bool bnd = false;
+    for (int a = 0; a < D; ++a) {
+      I[a] = id % Mf;
+      id /= Mf;
+      bnd |= (I[a] == 0) | (I[a] == Mf - 1);
+    }
+    if (bnd) return;
+    const int c0 = T.pc2[0][I[0]], c1 = T.pc2[1][I[1]], c2 = D == 3 ? T.pc2[2][I[2]] : 1;
+    double acc[D][NR];
+#pragma unroll
+    for (int c = 0; c < D; ++c)
+#pragma unroll
+      for (int j = 0; j < NR; ++j) acc[c][j] = 0.0;
+    for (int j2 = 0; j2 < c2; ++j2) {
+      const int K2 = D == 3 ? T.pk2[2][3 * I[2] + j2] : 0;
+      const double w2 = D == 3 ? T.pw2[2][3 * I[2] + j2] : 1.0;
+      for (int j1 = 0; j1 < c1; ++j1) {
+        const int K1 = T.pk2[1][3 * I[1] + j1];
+        const double w12 = D == 3 ? w2 * T.pw2[1][3 * I[1] + j1] : T.pw2[1][3 * I[1] + j1];
+        const int rowbase = D * Mc * (K1 + Mc * K2);
+        for (int j0 = 0; j0 < c0; ++j0) {
+          const double ww = w12 * T.pw2[0][3 * I[0] + j0];
+          const int bse = rowbase + D * T.pk2[0][3 * I[0] + j0];
+#pragma unroll
+          for (int c = 0; c < D; ++c)
+#pragma unroll
+            for (int j = 0; j < NR; ++j) acc[c][j] += ww * xc[((int64_t)bse + c) * NR + j];
+        }
+      }
+    }
+#pragma unroll
+    for (int c = 0; c < D; ++c)
+#pragma unroll
+      for (int j = 0; j < NR; ++j) lv.x[((int64_t)D * t + c) * NR + j] += acc[c][j];
+  } else if (t < nnf + (int)gf.n_p) {
+    const int Nf1 = gf.N + 1, Nc1 = gc.N + 1;
+    int v[3] = {0, 0, 0}, id = t - nnf;
+    for (int a = 0; a < D; ++a) { v[a] = id % Nf1; id /= Nf1; }
+    const int c0 = T.pc1[0][v[0]], c1 = T.pc1[1][v[1]], c2 = D == 3 ? T.pc1[2][v[2]] : 1;
+    double acc[NR];
+#pragma unroll
+    for (int j = 0; j < NR; ++j) acc[j] = 0.0;
+    for (int j2 = 0; j2 < c2; ++j2) {
+      const int K2 = D == 3 ? T.pk1[2][2 * v[2] + j2] : 0;
+      const double w2 = D == 3 ? T.pw1[2][2 * v[2] + j2] : 1.0;
+      for (int j1 = 0; j1 < c1; ++j1) {
+        const int K1 = T.pk1[1][2 * v[1] + j1];
+        const double w12 = D == 3 ? w2 * T.pw1[1][2 * v[1] + j1] : T.pw1[1][2 * v[1] + j1];
+        for (int j0 = 0; j0 < c0; ++j0) {
+          const double w = w12 * T.pw1[0][2 * v[0] + j0];
+          const int64_t idx = gc.n_u + T.pk1[0][2 * v[0] + j0] + Nc1 * (K1 + Nc1 * K2);
+#pragma unroll
+          for (int j = 0; j < NR; ++j) acc[j] += w * xc[idx * NR + j];
+        }
+      }
+    }
+    const int64_t o = gf.n_u + (t - nnf);
+#pragma unroll
+    for (int j = 0; j < NR; ++j) lv.x[o * NR + j] += acc[j];
+  }
+}
+
+// Coarse solve on the coarsest level of each entry: r <- b masked to free
+// rows, then x = C r (one warp per row, same order per RHS as k_coarse_gemv).
+template <int NR>
+__global__ void kb_coarse_mask(const BLevel* __restrict__ L, const int64_t* __restrict__ first, int ne) {
+  const int e = find_entry(first, ne, blockIdx.x);
+  const BLevel& lv = L[e];
+  const int64_t i = (blockIdx.x - first[e]) * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= lv.g.n) return;
+  const bool d = is_dirichlet(lv.g, i);
+#pragma unroll
+  for (int j = 0; j < NR; ++j) lv.r[i * NR + j] = d ? 0.0 : lv.b[i * NR + j];
+}
+template <int NR>
+__global__ void kb_coarse_gemv(const BLevel* __restrict__ L, const int64_t* __restrict__ first, int ne) {
+  const int e = find_entry(first, ne, blockIdx.x);
+  const BLevel& lv = L[e];
+  const int64_t n = lv.g.n, m = n + 1;
+  const int lane = threadIdx.x & 31;
+  const int64_t row = (blockIdx.x - first[e]) * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (row >= n) return;
+  double s[NR];
+#pragma unroll
+  for (int j = 0; j < NR; ++j) s[j] = 0.0;
+  for (int64_t c = lane; c < n; c += 32) {
+    const double a = lv.cinv[row * m + c];
+#pragma unroll
+    for (int j = 0; j < NR; ++j) s[j] += a * lv.r[c * NR + j];
+  }
+#pragma unroll
+  for (int j = 0; j < NR; ++j) {
+    for (int o = 16; o > 0; o >>= 1) s[j] += __shfl_xor_sync(0xffffffffu, s[j], o);
+    if (lane == 0) lv.x[row * NR + j] = s[j];
+  }
+}
+
+}  // namespace rav
+
+using namespace rav;
+
+// One launch: descriptors of the taking-part entries, their block offsets.
+struct BPhase {
+  BLevel* L = nullptr;      // device
+  int64_t* first = nullptr; // device, ne + 1
+  int* prob = nullptr;      // device, ne (norm phases)
+  int ne = 0;
+  int64_t blocks = 0;
+  int threads = 0;
+  std::vector<int> entries;  // host: indices into rav_batch::lv
+};
+
+struct rav_batch {
+  int nprob = 0, nrhs = 0, dim = 2, prec = RAV_F32, depth = 0;
+  std::vector<rav_mg*> mgs;
+  std::vector<rav_smoother*> sms;
+  // host copies of every (problem, level) descriptor, finest level first per problem
+  std::vector<BLevel> lv;
+  std::vector<int> lv_first;  // start of problem p's levels in lv (finest level of p at lv_first[p])
+  std::vector<double*> owned;  // batch-owned vectors
+  BLevel* lv_dev = nullptr;    // device mirror of lv
+  int tpb_res = 256, tpb_apply = 128;
+  // phases per depth d (0 = finest)
+  std::vector<BPhase> res_smooth, apply, res_last, restrict_, prolong, coarse_mask, coarse_gemv;
+  BPhase fine_res;  // depth-0 residual with norms
+  double* part = nullptr;
+  double* norms = nullptr;   // device, nprob * nrhs
+  double* norms_h = nullptr; // pinned
+  cudaStream_t cap = nullptr;
+  cudaGraphExec_t graph = nullptr;
+  int graph_nu1 = -1, graph_nu2 = -1;
+  int64_t graph_launches = 0;
+  std::vector<const double*> cur_x, cur_b;
+};
+
+static int level_count(const rav_batch* bt, int p) {
+  return bt->mgs[p]->nlev;
+}
+
+// Builds the descriptor of problem p at depth d (level nlev-1-d).
+static BLevel make_level(rav_batch* bt, int p, int d) {
+  rav_mg* mg = bt->mgs[p];
+  rav_smoother* sm = bt->sms[p];
+  const int l = mg->nlev - 1 - d;
+  const Level& L = mg->lev[l];
+  BLevel b{};
+  b.g = L.g;
+  if (l > 0) b.gc = mg->lev[l - 1].g;
+  b.nslice = L.nslice;
+  b.sperm = L.sperm;
+  b.sptr = L.sptr;
+  b.slen = L.slen;
+  b.scol = L.scol;
+  b.sval = L.sval;
+  if (l > 0) {
+    b.inv = sm->lev[l].inv;
+    b.omega = sm->lev[l].omega;
+    b.units = sm->lev[l].units;
+    b.tab = L.tab();
+  }
+  b.cinv = l == 0 ? mg->cinv : nullptr;
+  b.problem = p;
+  return b;
+}
+
+static int upload_phase(rav_batch* bt, BPhase& ph, const std::vector<int>& entries, int threads,
+                        int64_t (*blocks_of)(const BLevel&, int)) {
+  ph.entries = entries;
+  ph.ne = (int)entries.size();
+  ph.threads = threads;
+  if (ph.ne == 0) return RAV_OK;
+  std::vector<BLevel> h(ph.ne);
+  std::vector<int64_t> first(ph.ne + 1, 0);
+  std::vector<int> prob(ph.ne);
+  for (int i = 0; i < ph.ne; ++i) {
+    h[i] = bt->lv[entries[i]];
+    prob[i] = h[i].problem;
+    first[i + 1] = first[i] + blocks_of(h[i], threads);
+  }
+  ph.blocks = first[ph.ne];
+  if (!ph.L) {
+    RAV_CUDA(cudaMalloc(&ph.L, sizeof(BLevel) * ph.ne));
+    RAV_CUDA(cudaMalloc(&ph.first, sizeof(int64_t) * (ph.ne + 1)));
+    RAV_CUDA(cudaMalloc(&ph.prob, sizeof(int) * ph.ne));
+  }
+  RAV_CUDA(cudaMemcpy(ph.L, h.data(), sizeof(BLevel) * ph.ne, cudaMemcpyHostToDevice));
+  RAV_CUDA(cudaMemcpy(ph.first, first.data(), sizeof(int64_t) * (ph.ne + 1), cudaMemcpyHostToDevice));
+  RAV_CUDA(cudaMemcpy(ph.prob, prob.data(), sizeof(int) * ph.ne, cudaMemcpyHostToDevice));
+  return RAV_OK;
+}
+
+static int64_t blk_res(const BLevel& b, int t) { return (b.nslice * 32 + t - 1) / t; }
+static int64_t blk_apply(const BLevel& b, int t) { return (b.units + t - 1) / t; }
+static int64_t blk_restrict(const BLevel& b, int t) { return (b.gc.nnode + b.gc.n_p + t - 1) / t; }
+static int64_t blk_prolong(const BLevel& b, int t) { return (b.g.nnode + b.g.n_p + t - 1) / t; }
+static int64_t blk_mask(const BLevel& b, int t) { return (b.g.n + t - 1) / t; }
+static int64_t blk_gemv(const BLevel& b, int t) { return (b.g.n + t / 32 - 1) / (t / 32); }
+
+// ---- launches --------------------------------------------------------------
+template <int NR>
+static void launch_res(const BPhase& ph, double* part, cudaStream_t s) {
+  if (ph.ne) kb_residual<NR><<<(unsigned)ph.blocks, ph.threads, 0, s>>>(ph.L, ph.first, ph.ne, part);
+}
+template <int D, int NR>
+static void launch_apply(const rav_batch* bt, const BPhase& ph, int use_b, cudaStream_t s) {
+  if (!ph.ne) return;
+  if (bt->prec == RAV_F32)
+    kb_apply<D, float, NR><<<(unsigned)ph.blocks, ph.threads, 0, s>>>(ph.L, ph.first, ph.ne, use_b);
+  else
+    kb_apply<D, double, NR><<<(unsigned)ph.blocks, ph.threads, 0, s>>>(ph.L, ph.first, ph.ne, use_b);
+}
+
+template <int D, int NR>
+static int batch_cycle(rav_batch* bt, int nu1, int nu2, cudaStream_t s) {
+  const int Dm = bt->depth;
+  // down
+  for (int d = 0; d < Dm; ++d) {
+    for (int it = 0; it < nu1; ++it) {
+      if (it == 0 && d > 0) {
+        launch_apply<D, NR>(bt, bt->apply[d], 1, s);
+      } else {
+        launch_res<NR>(bt->res_smooth[d], nullptr, s);
+        launch_apply<D, NR>(bt, bt->apply[d], 0, s);
+      }
+    }
+    launch_res<NR>(bt->res_smooth[d], nullptr, s);
+    const BPhase& rp = bt->restrict_[d];
+    if (rp.ne) kb_restrict<D, NR><<<(unsigned)rp.blocks, rp.threads, 0, s>>>(rp.L, rp.first, rp.ne);
+    const BPhase& cm = bt->coarse_mask[d + 1];
+    if (cm.ne) {
+      kb_coarse_mask<NR><<<(unsigned)cm.blocks, cm.threads, 0, s>>>(cm.L, cm.first, cm.ne);
+      const BPhase& cg = bt->coarse_gemv[d + 1];
+      kb_coarse_gemv<NR><<<(unsigned)cg.blocks, cg.threads, 0, s>>>(cg.L, cg.first, cg.ne);
+    }
+  }
+  // up
+  for (int d = Dm - 1; d >= 0; --d) {
+    const BPhase& pp = bt->prolong[d];
+    if (pp.ne) kb_prolong<D, NR><<<(unsigned)pp.blocks, pp.threads, 0, s>>>(pp.L, pp.first, pp.ne);
+    for (int it = 0; it < nu2; ++it) {
+      launch_res<NR>(bt->res_smooth[d], nullptr, s);
+      launch_apply<D, NR>(bt, bt->apply[d], 0, s);
+    }
+  }
+  RAV_CUDA(cudaGetLastError());
+  return RAV_OK;
+}
+
+static int batch_cycle_any(rav_batch* bt, int nu1, int nu2, cudaStream_t s) {
+  const int D = bt->dim, NR = bt->nrhs;
+#define RAV_BC(DD, RR) \
+  if (D == DD && NR == RR) return batch_cycle<DD, RR>(bt, nu1, nu2, s);
+  RAV_BC(2, 1) RAV_BC(2, 2) RAV_BC(2, 4) RAV_BC(2, 8) RAV_BC(3, 1) RAV_BC(3, 2) RAV_BC(3, 4) RAV_BC(3, 8)
+#undef RAV_BC
+  return RAV_ERR_ARG;
+}
+
+static int fine_norms(rav_batch* bt, cudaStream_t s) {
+  const BPhase& ph = bt->fine_res;
+  switch (bt->nrhs) {
+    case 1: launch_res<1>(ph, bt->part, s); kb_norm_final<1><<<(ph.ne + 127) / 128, 128, 0, s>>>(ph.first, ph.prob, ph.ne, bt->part, bt->norms); break;
+    case 2: launch_res<2>(ph, bt->part, s); kb_norm_final<2><<<(ph.ne * 2 + 127) / 128, 128, 0, s>>>(ph.first, ph.prob, ph.ne, bt->part, bt->norms); break;
+    case 4: launch_res<4>(ph, bt->part, s); kb_norm_final<4><<<(ph.ne * 4 + 127) / 128, 128, 0, s>>>(ph.first, ph.prob, ph.ne, bt->part, bt->norms); break;
+    default: launch_res<8>(ph, bt->part, s); kb_norm_final<8><<<(ph.ne * 8 + 127) / 128, 128, 0, s>>>(ph.first, ph.prob, ph.ne, bt->part, bt->norms); break;
+  }
+  note_launch(2);
+  RAV_CUDA(cudaGetLastError());
+  RAV_CUDA(cudaMemcpyAsync(bt->norms_h, bt->norms, sizeof(double) * bt->nprob * bt->nrhs, cudaMemcpyDeviceToHost, s));
+  RAV_CUDA(cudaStreamSynchronize(s));
+  return RAV_OK;
+}
+
+// Builds every phase for the current threads-per-block choices.
+static int build_phases(rav_batch* bt) {
+  const int Dm = bt->depth;
+  bt->res_smooth.resize(Dm);
+  bt->apply.resize(Dm);
+  bt->restrict_.resize(Dm);
+  bt->prolong.resize(Dm);
+  bt->coarse_mask.resize(Dm + 1);
+  bt->coarse_gemv.resize(Dm + 1);
+  for (int d = 0; d <= Dm; ++d) {
+    std::vector<int> smooth, coarse;
+    for (int p = 0; p < bt->nprob; ++p) {
+      const int Lp = level_count(bt, p);
+      if (d <= Lp - 2) smooth.push_back(bt->lv_first[p] + d);
+      if (d == Lp - 1) coarse.push_back(bt->lv_first[p] + d);
+    }
+    if (d < Dm) {
+      RAV_TRY(upload_phase(bt, bt->res_smooth[d], smooth, bt->tpb_res, blk_res));
+      RAV_TRY(upload_phase(bt, bt->apply[d], smooth, bt->tpb_apply, blk_apply));
+      RAV_TRY(upload_phase(bt, bt->restrict_[d], smooth, 128, blk_restrict));
+      RAV_TRY(upload_phase(bt, bt->prolong[d], smooth, 128, blk_prolong));
+    }
+    RAV_TRY(upload_phase(bt, bt->coarse_mask[d], coarse, 256, blk_mask));
+    RAV_TRY(upload_phase(bt, bt->coarse_gemv[d], coarse, 256, blk_gemv));
+  }
+  std::vector<int> fine;
+  for (int p = 0; p < bt->nprob; ++p) fine.push_back(bt->lv_first[p]);
+  RAV_TRY(upload_phase(bt, bt->fine_res, fine, 256, blk_res));
+  if (bt->part) cudaFree(bt->part);
+  RAV_CUDA(cudaMalloc(&bt->part, sizeof(double) * (bt->fine_res.blocks + 1) * bt->nrhs));
+  return RAV_OK;
+}
+
+// Points the finest-level descriptors at the caller's vectors.
+static int bind_vectors(rav_batch* bt, double* const* x, const double* const* b) {
+  bool same = (int)bt->cur_x.size() == bt->nprob;
+  for (int p = 0; same && p < bt->nprob; ++p) same = bt->cur_x[p] == x[p] && bt->cur_b[p] == b[p];
+  if (same) return RAV_OK;
+  bt->cur_x.assign(x, x + bt->nprob);
+  bt->cur_b.assign(b, b + bt->nprob);
+  for (int p = 0; p < bt->nprob; ++p) {
+    BLevel& f = bt->lv[bt->lv_first[p]];
+    f.x = x[p];
+    f.b = const_cast<double*>(b[p]);
+  }
+  // re-upload the descriptors of every phase (they hold copies)
+  std::vector<BPhase*> all;
+  for (auto* v : {&bt->res_smooth, &bt->apply, &bt->restrict_, &bt->prolong, &bt->coarse_mask, &bt->coarse_gemv})
+    for (auto& ph : *v) all.push_back(&ph);
+  all.push_back(&bt->fine_res);
+  for (BPhase* ph : all) {
+    if (!ph->ne) continue;
+    std::vector<BLevel> h(ph->ne);
+    for (int i = 0; i < ph->ne; ++i) h[i] = bt->lv[ph->entries[i]];
+    RAV_CUDA(cudaMemcpy(ph->L, h.data(), sizeof(BLevel) * ph->ne, cudaMemcpyHostToDevice));
+  }
+  return RAV_OK;
+}
+
+// Autotuner: times the finest-depth residual and apply phases for each
+// candidate block size on the batch's own data and keeps the fastest.
+static int autotune(rav_batch* bt, cudaStream_t s) {
+  cudaEvent_t e0, e1;
+  RAV_CUDA(cudaEventCreate(&e0));
+  RAV_CUDA(cudaEventCreate(&e1));
+  auto time_it = [&](auto&& fn) -> float {
+    fn();
+    cudaEventRecord(e0, s);
+    for (int i = 0; i < 3; ++i) fn();
+    cudaEventRecord(e1, s);
+    cudaEventSynchronize(e1);
+    float ms = 0.0f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    return ms;
+  };
+  const int cand_res[3] = {128, 256, 512}, cand_apply[3] = {64, 128, 256};
+  float best = 1e30f;
+  int bres = 256, bapp = 128;
+  for (int c : cand_res) {
+    bt->tpb_res = c;
+    RAV_TRY(build_phases(bt));
+    const float ms = time_it([&] {
+      switch (bt->nrhs) {
+        case 1: launch_res<1>(bt->res_smooth[0], nullptr, s); break;
+        case 2: launch_res<2>(bt->res_smooth[0], nullptr, s); break;
+        case 4: launch_res<4>(bt->res_smooth[0], nullptr, s); break;
+        default: launch_res<8>(bt->res_smooth[0], nullptr, s); break;
+      }
+    });
+    if (ms < best) { best = ms; bres = c; }
+  }
+  bt->tpb_res = bres;
+  best = 1e30f;
+  std::vector<double> xsave;
+  for (int c : cand_apply) {
+    bt->tpb_apply = c;
+    RAV_TRY(build_phases(bt));
+    // the apply updates x; time on the batch's own level-1 work vectors when
+    // they exist, else on the caller-free finest data with x restored below
+    const float ms = time_it([&] {
+      if (bt->dim == 2) {
+        switch (bt->nrhs) {
+          case 1: launch_apply<2, 1>(bt, bt->apply[0], 0, s); break;
+          case 2: launch_apply<2, 2>(bt, bt->apply[0], 0, s); break;
+          case 4: launch_apply<2, 4>(bt, bt->apply[0], 0, s); break;
+          default: launch_apply<2, 8>(bt, bt->apply[0], 0, s); break;
+        }
+      } else {
+        switch (bt->nrhs) {
+          case 1: launch_apply<3, 1>(bt, bt->apply[0], 0, s); break;
+          case 2: launch_apply<3, 2>(bt, bt->apply[0], 0, s); break;
+          case 4: launch_apply<3, 4>(bt, bt->apply[0], 0, s); break;
+          default: launch_apply<3, 8>(bt, bt->apply[0], 0, s); break;
+        }
+      }
+    });
+    if (ms < best) { best = ms; bapp = c; }
+  }
+  bt->tpb_apply = bapp;
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  RAV_TRY(build_phases(bt));
+  RAV_CUDA(cudaGetLastError());
+  return RAV_OK;
+}
+
+extern "C" int batch_setup(rav_mg* const* mgs, rav_smoother* const* sms, int nprob, int nrhs, rav_stream stream,
+                           rav_batch** out) {
+  if (!mgs || !sms || !out || nprob < 1 || !(nrhs == 1 || nrhs == 2 || nrhs == 4 || nrhs == 8)) return RAV_ERR_ARG;
+  *out = nullptr;
+  const int dim = mgs[0] ? mgs[0]->dim : 0;
+  const int prec = sms[0] ? sms[0]->prec : -1;
+  for (int p = 0; p < nprob; ++p) {
+    if (!mgs[p] || !sms[p] || sms[p]->mg != mgs[p] || mgs[p]->dim != dim || mgs[p]->nlev < 2) return RAV_ERR_ARG;
+    if (sms[p]->kind != RAV_RAV || sms[p]->prec != prec) return RAV_ERR_ARG;
+  }
+  if (prec != RAV_F32 && prec != RAV_F64_ROWS) return RAV_ERR_ARG;
+  cudaStream_t s = S(stream);
+  rav_batch* bt = new rav_batch();
+  bt->nprob = nprob;
+  bt->nrhs = nrhs;
+  bt->dim = dim;
+  bt->prec = prec;
+  bt->mgs.assign(mgs, mgs + nprob);
+  bt->sms.assign(sms, sms + nprob);
+  auto fail = [&](int rc) {
+    batch_destroy(bt);
+    return rc;
+  };
+  // descriptors and batch-owned vectors (every level of every problem, finest first)
+  for (int p = 0; p < nprob; ++p) {
+    bt->lv_first.push_back((int)bt->lv.size());
+    const int Lp = mgs[p]->nlev;
+    bt->depth = std::max(bt->depth, Lp - 1);
+    for (int d = 0; d < Lp; ++d) bt->lv.push_back(make_level(bt, p, d));
+    for (int d = 0; d < Lp; ++d) {
+      BLevel& b = bt->lv[bt->lv_first[p] + d];
+      const int64_t n = b.g.n * nrhs;
+      double* v[3] = {nullptr, nullptr, nullptr};
+      for (int k = (d == 0 ? 2 : 0); k < 3; ++k) {
+        if (cudaMalloc(&v[k], sizeof(double) * n) != cudaSuccess) return fail(RAV_ERR_CUDA);
+        cudaMemset(v[k], 0, sizeof(double) * n);
+        bt->owned.push_back(v[k]);
+      }
+      if (d > 0) { b.x = v[0]; b.b = v[1]; }
+      b.r = v[2];
+    }
+    for (int d = 0; d + 1 < Lp; ++d) {
+      BLevel& b = bt->lv[bt->lv_first[p] + d];
+      b.xc = bt->lv[bt->lv_first[p] + d + 1].x;
+      b.bc = bt->lv[bt->lv_first[p] + d + 1].b;
+    }
+  }
+  // the finest x, b are bound per call; give them scratch for the autotuner
+  for (int p = 0; p < nprob; ++p) {
+    BLevel& f = bt->lv[bt->lv_first[p]];
+    const int64_t n = f.g.n * nrhs;
+    double *x = nullptr, *b = nullptr;
+    if (cudaMalloc(&x, sizeof(double) * n) != cudaSuccess) return fail(RAV_ERR_CUDA);
+    if (cudaMalloc(&b, sizeof(double) * n) != cudaSuccess) return fail(RAV_ERR_CUDA);
+    cudaMemset(x, 0, sizeof(double) * n);
+    cudaMemset(b, 0, sizeof(double) * n);
+    bt->owned.push_back(x);
+    bt->owned.push_back(b);
+    f.x = x;
+    f.b = b;
+  }
+  if (cudaMalloc(&bt->norms, sizeof(double) * nprob * nrhs) != cudaSuccess) return fail(RAV_ERR_CUDA);
+  if (cudaMallocHost(&bt->norms_h, sizeof(double) * nprob * nrhs) != cudaSuccess) return fail(RAV_ERR_CUDA);
+  int rc = autotune(bt, s);
+  if (rc != RAV_OK) return fail(rc);
+  if (cudaStreamSynchronize(s) != cudaSuccess) return fail(RAV_ERR_CUDA);
+  *out = bt;
+  return RAV_OK;
+}
+
+extern "C" void batch_destroy(rav_batch* bt) {
+  if (!bt) return;
+  cudaDeviceSynchronize();
+  if (bt->graph) cudaGraphExecDestroy(bt->graph);
+  if (bt->cap) cudaStreamDestroy(bt->cap);
+  for (auto* v : {&bt->res_smooth, &bt->apply, &bt->restrict_, &bt->prolong, &bt->coarse_mask, &bt->coarse_gemv})
+    for (auto& ph : *v) {
+      cudaFree(ph.L);
+      cudaFree(ph.first);
+      cudaFree(ph.prob);
+    }
+  cudaFree(bt->fine_res.L);
+  cudaFree(bt->fine_res.first);
+  cudaFree(bt->fine_res.prob);
+  for (double* p : bt->owned) cudaFree(p);
+  cudaFree(bt->part);
+  cudaFree(bt->norms);
+  if (bt->norms_h) cudaFreeHost(bt->norms_h);
+  delete bt;
+}
+
+extern "C" int batch_get_tuning(const rav_batch* bt, int out[2]) {
+  if (!bt || !out) return RAV_ERR_ARG;
+  out[0] = bt->tpb_res;
+  out[1] = bt->tpb_apply;
+  return RAV_OK;
+}
+
+// One batched V-cycle, captured into a graph on first use and replayed.
+static int batch_vcycle_impl(rav_batch* bt, int nu1, int nu2, cudaStream_t s) {
+  if (!bt->graph || bt->graph_nu1 != nu1 || bt->graph_nu2 != nu2) {
+    if (bt->graph) {
+      cudaGraphExecDestroy(bt->graph);
+      bt->graph = nullptr;
+    }
+    if (!bt->cap) RAV_CUDA(cudaStreamCreateWithFlags(&bt->cap, cudaStreamNonBlocking));
+    const int64_t l0 = rav_kernel_launches();
+    RAV_CUDA(cudaStreamBeginCapture(bt->cap, cudaStreamCaptureModeThreadLocal));
+    const int rc = batch_cycle_any(bt, nu1, nu2, bt->cap);
+    cudaGraph_t g = nullptr;
+    const cudaError_t ec = cudaStreamEndCapture(bt->cap, &g);
+    if (rc != RAV_OK || ec != cudaSuccess) {
+      if (g) cudaGraphDestroy(g);
+      return rc != RAV_OK ? rc : RAV_ERR_CUDA;
+    }
+    const cudaError_t ei = cudaGraphInstantiate(&bt->graph, g, 0);
+    size_t nnodes = 0;
+    cudaGraphGetNodes(g, nullptr, &nnodes);
+    cudaGraphDestroy(g);
+    RAV_CUDA(ei);
+    bt->graph_nu1 = nu1;
+    bt->graph_nu2 = nu2;
+    bt->graph_launches = (int64_t)nnodes;
+    (void)l0;
+  }
+  RAV_CUDA(cudaGraphLaunch(bt->graph, s));
+  note_launch((int)bt->graph_launches);
+  return RAV_OK;
+}
+
+extern "C" int batch_vcycle(rav_batch* bt, double* const* x, const double* const* b, int nu1, int nu2,
+                            rav_stream stream) {
+  if (!bt || !x || !b || nu1 < 0 || nu2 < 0) return RAV_ERR_ARG;
+  for (int p = 0; p < bt->nprob; ++p)
+    if (!x[p] || !b[p]) return RAV_ERR_ARG;
+  cudaStream_t s = S(stream);
+  RAV_CUDA(cudaStreamSynchronize(s));  // descriptors are rewritten below
+  RAV_TRY(bind_vectors(bt, x, b));
+  return batch_vcycle_impl(bt, nu1, nu2, s);
+}
+
+extern "C" int solve_batched(rav_batch* bt, double* const* x, const double* const* b, const rav_solve_opts* o,
+                             int* iters, double* ratios, rav_stream stream) {
+  if (!bt || !x || !b || !o || o->maxit < 0 || !(o->tol > 0) || o->outer != 0) return RAV_ERR_ARG;
+  for (int p = 0; p < bt->nprob; ++p)
+    if (!x[p] || !b[p]) return RAV_ERR_ARG;
+  cudaStream_t s = S(stream);
+  RAV_CUDA(cudaStreamSynchronize(s));
+  RAV_TRY(bind_vectors(bt, x, b));
+  const int nk = bt->nprob * bt->nrhs;
+  std::vector<double> r0(nk);
+  std::vector<int> it(nk, -1);
+  RAV_TRY(fine_norms(bt, s));
+  for (int i = 0; i < nk; ++i) {
+    r0[i] = bt->norms_h[i];
+    if (r0[i] == 0.0) it[i] = 0;
+  }
+  std::vector<double> ratio(nk, 1.0);
+  int rc = RAV_OK;
+  for (int k = 1; k <= o->maxit; ++k) {
+    bool all = true;
+    for (int i = 0; i < nk; ++i) all &= it[i] >= 0;
+    if (all) break;
+    RAV_TRY(batch_vcycle_impl(bt, o->nu_pre, o->nu_post, s));
+    RAV_TRY(fine_norms(bt, s));
+    for (int i = 0; i < nk; ++i) {
+      if (it[i] >= 0 || r0[i] == 0.0) continue;
+      ratio[i] = bt->norms_h[i] / r0[i];
+      if (!std::isfinite(ratio[i])) rc = RAV_ERR_NAN;
+      else if (ratio[i] <= o->tol) it[i] = k;
+    }
+    if (rc != RAV_OK) break;
+  }
+  bool all = true;
+  for (int i = 0; i < nk; ++i) all &= it[i] >= 0;
+  if (rc == RAV_OK && !all) rc = RAV_ERR_NOT_CONVERGED;
+  for (int i = 0; i < nk; ++i) {
+    if (iters) iters[i] = it[i];
+    if (ratios) ratios[i] = ratio[i];
+  }
+  return rc;
+}

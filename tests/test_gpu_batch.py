@@ -1,0 +1,98 @@
+"""Batched multi-problem, multi-RHS solves (batch_setup / batch_vcycle /
+solve_batched) against the single-problem path and the oracle."""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2103_10127_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA device", allow_module_level=True)
+
+import paper_2103_10127_gb300 as R  # noqa: E402
+
+
+def free_velocity(dim, N):
+    M = 2 * N + 1
+    idx = np.indices((M,) * dim).reshape(dim, -1)[::-1]  # axis 0 fastest
+    inner = np.all((idx > 0) & (idx < M - 1), axis=0)
+    return np.concatenate([np.repeat(inner, dim), np.zeros((N + 1) ** dim, bool)])
+
+
+def random_rhs(mg, seed):
+    """Lid values on Dirichlet rows plus iid N(0,1) forcing on free velocity rows."""
+    b = mg.rhs(R.F_NONE).cpu().numpy()
+    m = free_velocity(mg.dim, mg.N)
+    b[m] += inputs.normal(seed, int(m.sum()))
+    return b
+
+
+def make_batch(sizes, nrhs, prec, seed=0):
+    mgs, sms, xs, bs = [], [], [], []
+    for i, N in enumerate(sizes):
+        L = inputs.levels_for(N)
+        mg = R.Multigrid(2, N, L, bc=R.BC_CAVITY)
+        sm = R.Smoother(mg, R.RAV, prec, 0.5)
+        n = mg.n()
+        b = np.stack([random_rhs(mg, 1000 * seed + 10 * i + k) for k in range(nrhs)], axis=1)
+        x0 = mg.initial_guess().cpu().numpy()
+        x = np.repeat(x0[:, None], nrhs, axis=1)
+        mgs.append(mg)
+        sms.append(sm)
+        xs.append(torch.from_numpy(np.ascontiguousarray(x)).cuda())
+        bs.append(torch.from_numpy(np.ascontiguousarray(b)).cuda())
+    return mgs, sms, xs, bs
+
+
+SIZES = [16, 24, 32, 48, 20]
+
+
+@pytest.mark.parametrize("prec", [R.F32, R.F64_ROWS])
+def test_batched_vcycle_equals_single_problem_cycles_bitwise(prec):
+    nrhs = 4
+    mgs, sms, xs, bs = make_batch(SIZES, nrhs, prec)
+    bt = R.Batch(mgs, sms, nrhs)
+    x_in = [x.clone() for x in xs]
+    bt.vcycle(xs, bs, 2, 2)
+    bt.vcycle(xs, bs, 2, 2)
+    for p, (mg, sm) in enumerate(zip(mgs, sms)):
+        for k in range(nrhs):
+            x = x_in[p][:, k].contiguous()
+            b = bs[p][:, k].contiguous()
+            mg.vcycle(sm, x, b, 2, 2)
+            mg.vcycle(sm, x, b, 2, 2)
+            assert torch.equal(x, xs[p][:, k]), (p, k)
+    assert bt.tuning()["residual_threads"] in (128, 256, 512)
+
+
+def test_batched_vcycle_matches_the_oracle():
+    nrhs = 2
+    mgs, sms, xs, bs = make_batch([16, 24], nrhs, R.F64_ROWS, seed=3)
+    bt = R.Batch(mgs, sms, nrhs)
+    x_in = [x.cpu().numpy() for x in xs]
+    bt.vcycle(xs, bs, 2, 2)
+    for p, N in enumerate([16, 24]):
+        orc = O.Oracle(2, N, inputs.levels_for(N), bc=O.BC_CAVITY)
+        orc.setup_smoother(O.RAV, 0.5)
+        for k in range(nrhs):
+            want = orc.vcycle(x_in[p][:, k], bs[p][:, k].cpu().numpy(), 2, 2)
+            got = xs[p][:, k].cpu().numpy()
+            assert np.abs(got - want).max() <= 1e-11 * np.abs(want).max()
+
+
+def test_batched_solve_matches_single_solves():
+    nrhs = 2
+    mgs, sms, xs, bs = make_batch(SIZES, nrhs, R.F32, seed=5)
+    bt = R.Batch(mgs, sms, nrhs)
+    x_in = [x.clone() for x in xs]
+    it, ratios, rc = bt.solve(xs, bs, tol=1e-8, maxit=100)
+    assert rc == 0 and np.all(it > 0) and np.all(ratios <= 1e-8)
+    for p, (mg, sm) in enumerate(zip(mgs, sms)):
+        for k in range(nrhs):
+            x = x_in[p][:, k].contiguous()
+            b = bs[p][:, k].contiguous()
+            its, hist, rcs = mg.solve(sm, x, b, tol=1e-8, maxit=100)
+            assert rcs == 0 and its == it[p, k]
