@@ -79,6 +79,10 @@ def _load():
             "orc_solve": (i, [P, P, P, d, i, i, i, P]),
             "orc_fgmres": (i, [P, P, P, d, i, i, i, i, P]),
             "orc_round_format": (None, [i, P, P, ll]),
+            "orc_labels": (None, [P, i, P, d, P]),
+            "orc_mlp_nparam": (ll, []),
+            "orc_mlp_forward": (None, [P, P, ll, P]),
+            "orc_mlp_loss_grad": (d, [P, P, P, ll, P]),
         }
         for name, (res, args) in sig.items():
             f = getattr(lib, name)
@@ -102,6 +106,26 @@ def round_format(prec: int, v) -> np.ndarray:
     out = np.empty_like(v)
     _load().orc_round_format(prec, _ptr(v), _ptr(out), v.size)
     return out
+
+
+def mlp_nparam() -> int:
+    return _load().orc_mlp_nparam()
+
+
+def mlp_forward(params, X) -> np.ndarray:
+    """omega = 1.5 sigmoid(MLP(x)) for the rows of X (n, 8), fp64."""
+    P, X = _f64(params), _f64(X).reshape(-1, 8)
+    out = np.empty(X.shape[0])
+    _load().orc_mlp_forward(_ptr(P), _ptr(X), X.shape[0], _ptr(out))
+    return out
+
+
+def mlp_loss_grad(params, X, y):
+    """(mean squared error, gradient with respect to the 4801 parameters), fp64."""
+    P, X, y = _f64(params), _f64(X).reshape(-1, 8), _f64(y)
+    g = np.empty(mlp_nparam())
+    loss = _load().orc_mlp_loss_grad(_ptr(P), _ptr(X), _ptr(y), X.shape[0], _ptr(g))
+    return loss, g
 
 
 class Oracle:
@@ -215,6 +239,13 @@ class Oracle:
         _lib.orc_get_inverse(self.h, lev, p, int(quantised), _ptr(out), _ptr(sc))
         out = out.reshape(-1, ni)
         return (out, sc) if quantised else out
+
+    def labels(self, lev, r, fallback=0.5):
+        """Line-search optimal damping per subdomain for residual r (needs patches on lev)."""
+        r = _f64(r)
+        out = np.empty(self.count(lev, 5))
+        _lib.orc_labels(self.h, lev, _ptr(r), float(fallback), _ptr(out))
+        return out
 
     def patch_rows(self, lev, p, max_rows=64, max_n=512):
         """Owned rows of L_p^{-1} computed on demand (needs build_patches(lev))."""

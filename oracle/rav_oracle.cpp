@@ -1127,6 +1127,116 @@ int orc_fgmres(void* h, double* x, const double* b, double tol, int maxit, int r
   return -5;
 }
 
+// ---------------------------------------------------------------------------
+// Learned damping (not in the paper, which allows a diagonal weighting per
+// subdomain in Eq. 11): a per-subdomain weight omega_i predicted by a small
+// MLP from local features, trained on line-search-optimal weights.
+//
+// Label of subdomain i for residual r: c_i = Rt_i^T (L_i^{-1} R_i r) (its own
+// restricted correction, weight 1), omega*_i = argmin_w ||r - w L c_i||_2 =
+// <r, L c_i> / <L c_i, L c_i>, clipped to [0, 1.5]; `fallback` when L c_i = 0.
+// L c_i is formed with the full sparse L (rows of all DoFs), r on free rows.
+void orc_labels(void* h, int l, const double* r, double fallback, double* out) {
+  const Level& L = ((Oracle*)h)->lev[l];
+  const int64_t np = (int64_t)L.poff.size() - 1;
+  std::vector<double> c(L.n, 0.0), Lc(L.n, 0.0);
+  for (int64_t p = 0; p < np; ++p) {
+    const int64_t b0 = L.poff[p], ni = L.poff[p + 1] - b0;
+    std::vector<double> rloc(ni), rows;
+    for (int64_t k = 0; k < ni; ++k) rloc[k] = r[L.pdof[b0 + k]];
+    inverse_rows(L, p, false, rows);
+    std::vector<int64_t> touched;
+    for (size_t j = 0; j < L.owned[p].size(); ++j) {
+      double s = 0.0;
+      for (int64_t k = 0; k < ni; ++k) s += rows[j * ni + k] * rloc[k];
+      const int64_t dof = L.pdof[b0 + L.owned[p][j]];
+      c[dof] = s;
+      touched.push_back(dof);
+    }
+    double num = 0.0, den = 0.0;
+    for (int64_t m = 0; m < L.n; ++m) {
+      if (L.dir[m]) continue;
+      double s = 0.0;
+      for (int64_t k = L.rp[m]; k < L.rp[m + 1]; ++k) s += L.va[k] * c[L.ci[k]];
+      num += r[m] * s;
+      den += s * s;
+    }
+    double w = den > 0.0 ? num / den : fallback;
+    out[p] = w < 0.0 ? 0.0 : (w > 1.5 ? 1.5 : w);
+    for (int64_t dof : touched) c[dof] = 0.0;
+  }
+}
+
+// MLP 8 -> 64 -> 64 -> 1 (ReLU, ReLU, omega = 1.5 sigmoid(z)).  Parameters in
+// one vector: W1[64][8], b1[64], W2[64][64], b2[64], W3[64], b3.
+static const int kH = 64, kF = 8;
+static const int64_t kNParam = kH * kF + kH + kH * kH + kH + kH + 1;
+
+void mlp_one(const double* P, const double* f, double* a1, double* a2, double* z) {
+  const double *W1 = P, *b1 = W1 + kH * kF, *W2 = b1 + kH, *b2 = W2 + kH * kH, *W3 = b2 + kH, *b3 = W3 + kH;
+  for (int i = 0; i < kH; ++i) {
+    double s = b1[i];
+    for (int k = 0; k < kF; ++k) s += W1[i * kF + k] * f[k];
+    a1[i] = s > 0.0 ? s : 0.0;
+  }
+  for (int i = 0; i < kH; ++i) {
+    double s = b2[i];
+    for (int k = 0; k < kH; ++k) s += W2[i * kH + k] * a1[k];
+    a2[i] = s > 0.0 ? s : 0.0;
+  }
+  double s = b3[0];
+  for (int k = 0; k < kH; ++k) s += W3[k] * a2[k];
+  *z = s;
+}
+
+long long orc_mlp_nparam() { return kNParam; }
+
+void orc_mlp_forward(const double* P, const double* X, long long n, double* out) {
+  double a1[kH], a2[kH], z;
+  for (long long s = 0; s < n; ++s) {
+    mlp_one(P, X + s * kF, a1, a2, &z);
+    out[s] = 1.5 / (1.0 + std::exp(-z));
+  }
+}
+
+// Mean squared error (1/n) sum_s (omega_s - y_s)^2 and its gradient with
+// respect to every parameter (backpropagation through the three layers).
+double orc_mlp_loss_grad(const double* P, const double* X, const double* y, long long n, double* grad) {
+  const double *W2 = P + kH * kF + kH, *W3 = W2 + kH * kH + kH;
+  double *gW1 = grad, *gb1 = gW1 + kH * kF, *gW2 = gb1 + kH, *gb2 = gW2 + kH * kH, *gW3 = gb2 + kH,
+         *gb3 = gW3 + kH;
+  std::fill(grad, grad + kNParam, 0.0);
+  double loss = 0.0, a1[kH], a2[kH], z, d2[kH], d1[kH];
+  for (long long s = 0; s < n; ++s) {
+    const double* f = X + s * kF;
+    mlp_one(P, f, a1, a2, &z);
+    const double sg = 1.0 / (1.0 + std::exp(-z));
+    const double om = 1.5 * sg;
+    const double e = om - y[s];
+    loss += e * e / n;
+    const double dz = 2.0 * e / n * 1.5 * sg * (1.0 - sg);
+    gb3[0] += dz;
+    for (int k = 0; k < kH; ++k) {
+      gW3[k] += dz * a2[k];
+      d2[k] = a2[k] > 0.0 ? dz * W3[k] : 0.0;
+    }
+    for (int i = 0; i < kH; ++i) {
+      gb2[i] += d2[i];
+      for (int k = 0; k < kH; ++k) gW2[i * kH + k] += d2[i] * a1[k];
+    }
+    for (int k = 0; k < kH; ++k) {
+      double s2 = 0.0;
+      for (int i = 0; i < kH; ++i) s2 += W2[i * kH + k] * d2[i];
+      d1[k] = a1[k] > 0.0 ? s2 : 0.0;
+    }
+    for (int i = 0; i < kH; ++i) {
+      gb1[i] += d1[i];
+      for (int k = 0; k < kF; ++k) gW1[i * kF + k] += d1[i] * f[k];
+    }
+  }
+  return loss;
+}
+
 // Rounds v[i] to the given format (prec 1 fp32, 2 bf16, 3 fp8 e4m3), for tests.
 void orc_round_format(int prec, const double* v, double* out, long long n) {
   for (long long i = 0; i < n; ++i) out[i] = fmt_round(prec, v[i]);

@@ -512,3 +512,71 @@ def test_reduced_precision_step_error_is_bounded(prec, bound):
     d64 = o64.smooth(1, x, b) - x
     dq = o.smooth(1, x, b) - x
     assert np.linalg.norm(dq - d64) <= bound * np.linalg.norm(d64)
+
+
+# --------------------------------------------------------------------------- learned damping
+def _mlp_params(seed, scale=0.3):
+    return scale * inputs.normal(seed, O.mlp_nparam())
+
+
+def test_mlp_forward_special_cases():
+    """All weights zero but b3: omega = 1.5 sigmoid(b3); a single path through the
+    first unit of each layer: omega = 1.5 sigmoid(max(f0, 0))."""
+    n = O.mlp_nparam()
+    assert n == 8 * 64 + 64 + 64 * 64 + 64 + 64 + 1 == 4801
+    X = inputs.normal(1, 40).reshape(5, 8)
+    P = np.zeros(n)
+    P[-1] = 0.7
+    assert np.allclose(O.mlp_forward(P, X), 1.5 / (1 + np.exp(-0.7)), rtol=0, atol=1e-15)
+    P = np.zeros(n)
+    P[0] = 1.0                      # W1[0][0]
+    P[8 * 64 + 64] = 1.0            # W2[0][0]
+    P[8 * 64 + 64 + 64 * 64 + 64] = 1.0  # W3[0]
+    want = 1.5 / (1 + np.exp(-np.maximum(X[:, 0], 0.0)))
+    assert np.abs(O.mlp_forward(P, X) - want).max() < 1e-15
+
+
+def test_mlp_gradient_matches_central_differences():
+    """Backpropagation against central finite differences of the fp64 loss."""
+    P = _mlp_params(2)
+    X = inputs.normal(3, 8 * 12).reshape(12, 8)
+    y = 1.5 * inputs.uniform(4, 12)
+    loss, g = O.mlp_loss_grad(P, X, y)
+    idx = np.concatenate([np.arange(0, 4801, 97), [4800, 4799, 4736]])
+    h = 1e-6
+    for i in idx:
+        Pp, Pm = P.copy(), P.copy()
+        Pp[i] += h
+        Pm[i] -= h
+        fd = (O.mlp_loss_grad(Pp, X, y)[0] - O.mlp_loss_grad(Pm, X, y)[0]) / (2 * h)
+        assert abs(fd - g[i]) <= 1e-6 * max(1e-3, np.abs(g).max()), (i, fd, g[i])
+
+
+def test_labels_are_the_line_search_minimisers():
+    """omega*_i minimises ||r - w L c_i||_2 over w (unclipped cases), with c_i the
+    subdomain's own restricted correction built here with numpy.linalg.inv."""
+    o = _problem(2, 4)
+    o.build_patches(1)
+    off, dofs, own = o.patches(1)
+    L = dense(o, 1)
+    m, _ = o.dirichlet(1)
+    rng = np.random.default_rng(13)
+    r = rng.standard_normal(L.shape[0])
+    r[m] = 0.0
+    lab = o.labels(1, r)
+    checked = 0
+    for p in range(len(off) - 1):
+        s = dofs[off[p]:off[p + 1]]
+        keep = own[s] == p
+        c = np.zeros(L.shape[0])
+        c[s[keep]] = (np.linalg.inv(L[np.ix_(s, s)]) @ r[s])[keep]
+        Lc = L @ c
+        Lc[m] = 0.0
+        f = lambda w: np.sum((r - w * Lc) ** 2)
+        w = lab[p]
+        assert 0.0 <= w <= 1.5
+        if 0.0 < w < 1.5:
+            checked += 1
+            assert f(w) <= f(w + 1e-3) and f(w) <= f(w - 1e-3)
+            assert abs(w - (r @ Lc) / (Lc @ Lc)) < 1e-12
+    assert checked > 10
