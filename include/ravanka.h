@@ -228,6 +228,10 @@ typedef struct rav_solve_opts {
                       right preconditioner                                         */
   int restart;     /* FGMRES restart length (30)                                */
   double diverge;  /* stop with RAV_ERR_DIVERGED when the ratio exceeds this     */
+  double fallback_rho; /* stationary only, > 0: after a V-cycle that reduced the
+                          residual by a factor worse than this, reset every
+                          subdomain's damping to the fixed value of vanka_setup
+                          (once) and go on; 0 disables                      */
 } rav_solve_opts;
 
 typedef struct rav_solve_info {
@@ -235,6 +239,7 @@ typedef struct rav_solve_info {
   int status;             /* RAV_OK or the error returned                       */
   double final_ratio;     /* ||r||/||r_0|| at exit                              */
   double* history_host;   /* optional, maxit+1 entries: ratio after each step  */
+  int fell_back;          /* 1 if the fallback to fixed damping happened        */
 } rav_solve_info;
 
 /* Solves L x = b from the given x (usually rav_initial_guess).  Host-driven:
@@ -242,6 +247,46 @@ typedef struct rav_solve_info {
  * read the residual norm.  info may be NULL. */
 int solve(rav_mg* mg, rav_smoother* sm, double* x_dev, const double* b_dev, const rav_solve_opts* opts,
           rav_solve_info* info, rav_stream stream);
+
+/* ---- Learned damping per subdomain ---------------------------------------
+ * The paper allows a diagonal weighting omega_i per subdomain (Eq. 11) and
+ * uses one constant.  These calls predict omega_i with an MLP 8 -> 64 -> 64 -> 1
+ * (ReLU, ReLU, omega = 1.5 sigmoid(z)) from 8 features per subdomain, and
+ * train it on line-search-optimal weights gathered from the method's own runs.
+ * Parameters: 4801 fp32 values W1[64][8], b1[64], W2[64][64], b2[64], W3[64],
+ * b3 (device).  Inference rounds the weights to fp16 and accumulates in fp32.
+ *
+ * rav_patch_features: feat_dev[n_p(l) * 8] (fp32) for level l: log10(eta_max /
+ *   eta_min) and mean log10 eta over the Gauss points of the cells around the
+ *   vertex, log10 of the largest and smallest cell aspect ratio there,
+ *   l / (levels - 1), subdomain DoFs / box positions, fraction of in-domain box
+ *   nodes on the Dirichlet boundary, log10 of the mean cell diagonal.
+ * rav_label_collection(sm, 1): clears and starts accumulating, in every RAV
+ *   smoothing step (vanka_smooth, vcycle, solve; V-cycles then run kernel by
+ *   kernel), omega*_i = clip(<r, L c_i> / <L c_i, L c_i>, 0, 1.5), where r is the
+ *   step's residual and c_i the subdomain's own restricted correction with
+ *   weight 1: the exact minimiser of ||r - w L c_i||_2.  (sm, 0) stops.
+ * rav_read_labels: label_dev[n_p(l)] = mean omega*_i (the fixed damping where
+ *   no sample was taken).
+ * rav_mlp_forward: omega_dev[n] for feature rows X_dev[n * 8].
+ * rav_mlp_loss_grad: mean squared error of omega against y_dev and its
+ *   gradient grad_dev[4801] (fp32, deterministic); work_dev must hold
+ *   ceil(n / 64) * 4802 floats.  loss_dev may be NULL.
+ * rav_adam_step: one Adam update (beta 0.9 / 0.999, eps 1e-8) of params_dev
+ *   with moments m_dev, v_dev; t = 1, 2, ... the step number.
+ * rav_set_learned_omega: features -> MLP -> omega_i on every level of sm
+ *   (replaces the damping; rav_reset_omega restores the fixed value). */
+int rav_mlp_nparam(void);
+int rav_patch_features(rav_smoother* sm, int level, float* feat_dev, rav_stream stream);
+int rav_label_collection(rav_smoother* sm, int enable);
+int rav_read_labels(rav_smoother* sm, int level, float* label_dev, rav_stream stream);
+int rav_mlp_forward(const float* params_dev, const float* X_dev, int64_t n, float* omega_dev, rav_stream stream);
+int rav_mlp_loss_grad(const float* params_dev, const float* X_dev, const float* y_dev, int64_t n, float* grad_dev,
+                      float* loss_dev, float* work_dev, int64_t work_floats, rav_stream stream);
+int rav_adam_step(float* params_dev, float* m_dev, float* v_dev, const float* grad_dev, float lr, int t,
+                  rav_stream stream);
+int rav_set_learned_omega(rav_smoother* sm, const float* params_dev, rav_stream stream);
+int rav_reset_omega(rav_smoother* sm, rav_stream stream);
 
 /* ---- Batched solves: many problems x several right-hand sides ------------
  * A batch groups nprob hierarchies (any mix of sizes and depths, one

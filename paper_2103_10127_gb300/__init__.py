@@ -124,15 +124,17 @@ class Multigrid:
         return x
 
     def solve(self, sm, x, b, tol=1e-8, maxit=100, nu_pre=2, nu_post=2, outer=0, restart=30, diverge=1e6,
-              stream=None, raise_on_error=True):
-        """Returns (iterations, history ||r_k||/||r_0||, status)."""
-        opts = _capi.RavSolveOpts(tol, maxit, nu_pre, nu_post, outer, restart, diverge)
+              fallback_rho=0.0, stream=None, raise_on_error=True, info_out=None):
+        """Returns (iterations, history ||r_k||/||r_0||, status); info_out (dict) gets 'fell_back'."""
+        opts = _capi.RavSolveOpts(tol, maxit, nu_pre, nu_post, outer, restart, diverge, fallback_rho)
         hist = np.zeros(maxit + 1)
-        info = _capi.RavSolveInfo(0, 0, 0.0, hist.ctypes.data)
+        info = _capi.RavSolveInfo(0, 0, 0.0, hist.ctypes.data, 0)
         rc = _capi.load().solve(self.h, sm.h, _ptr(x), _ptr(b), ctypes.byref(opts), ctypes.byref(info),
                                 _stream(stream))
         if raise_on_error and rc != 0:
             raise RavError(rc, "solve")
+        if info_out is not None:
+            info_out["fell_back"] = bool(info.fell_back)
         return info.iterations, hist[: info.iterations + 1].copy(), rc
 
 
@@ -173,7 +175,7 @@ class Batch:
 
     def solve(self, xs, bs, tol=1e-8, maxit=100, nu_pre=2, nu_post=2, stream=None, raise_on_error=True):
         """Returns (iterations[nprob, nrhs], ratios[nprob, nrhs], status)."""
-        opts = _capi.RavSolveOpts(tol, maxit, nu_pre, nu_post, 0, 30, 0.0)
+        opts = _capi.RavSolveOpts(tol, maxit, nu_pre, nu_post, 0, 30, 0.0, 0.0)
         it = np.zeros(len(xs) * self.nrhs, np.int32)
         ra = np.zeros(len(xs) * self.nrhs)
         rc = _capi.load().solve_batched(self.h, self._ptrs(xs), self._ptrs(bs), ctypes.byref(opts),

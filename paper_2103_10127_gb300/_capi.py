@@ -25,11 +25,12 @@ class RavProblem(ctypes.Structure):
 
 class RavSolveOpts(ctypes.Structure):
     _fields_ = [("tol", F64), ("maxit", I32), ("nu_pre", I32), ("nu_post", I32), ("outer", I32),
-                ("restart", I32), ("diverge", F64)]
+                ("restart", I32), ("diverge", F64), ("fallback_rho", F64)]
 
 
 class RavSolveInfo(ctypes.Structure):
-    _fields_ = [("iterations", I32), ("status", I32), ("final_ratio", F64), ("history_host", P)]
+    _fields_ = [("iterations", I32), ("status", I32), ("final_ratio", F64), ("history_host", P),
+                ("fell_back", I32)]
 
 
 _SIGS = {
@@ -58,6 +59,15 @@ _SIGS = {
     "rav_profile_enable": (I32, [P, ctypes.c_uint, I32]),
     "rav_profile_read": (I32, [P, I32, I32, I64P, ctypes.POINTER(F64)]),
     "rav_kernel_launches": (ctypes.c_int64, []),
+    "rav_mlp_nparam": (I32, []),
+    "rav_patch_features": (I32, [P, I32, P, P]),
+    "rav_label_collection": (I32, [P, I32]),
+    "rav_read_labels": (I32, [P, I32, P, P]),
+    "rav_mlp_forward": (I32, [P, P, ctypes.c_int64, P, P]),
+    "rav_mlp_loss_grad": (I32, [P, P, P, ctypes.c_int64, P, P, P, ctypes.c_int64, P]),
+    "rav_adam_step": (I32, [P, P, P, P, ctypes.c_float, I32, P]),
+    "rav_set_learned_omega": (I32, [P, P, P]),
+    "rav_reset_omega": (I32, [P, P]),
     "batch_setup": (I32, [P, P, I32, I32, P, ctypes.POINTER(P)]),
     "batch_destroy": (None, [P]),
     "batch_get_tuning": (I32, [P, ctypes.POINTER(I32)]),

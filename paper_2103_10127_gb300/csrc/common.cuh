@@ -147,14 +147,26 @@ struct SmLevel {
   float* scale = nullptr;    // fp8 row scales
   double* omega = nullptr;   // damping per subdomain
   double* corr = nullptr;    // AV corrections, n_p x n_box
+  // line-search label collection (learn.cu)
+  double* lsum = nullptr;    // sum of omega* per subdomain
+  int* lcnt = nullptr;       // number of samples
+  double* ones = nullptr;    // unit damping
+  double* ctmp = nullptr;    // subdomain corrections with unit damping
 };
 
 struct rav_smoother {
   rav_mg* mg = nullptr;
   int kind = RAV_RAV, prec = RAV_F64;
   double omega = 0.5;
+  bool collect = false;  // accumulate line-search labels in each smoothing step
   SmLevel lev[rav::kMaxLevels];
 };
+
+// Subdomain apply with an explicit damping array; labels; damping reset
+// (smoother.cu, learn.cu).
+int apply_with_omega(rav_smoother* sm, int level, const double* r, double* x, const double* omega, cudaStream_t s);
+int collect_labels(rav_smoother* sm, int level, const double* r, cudaStream_t s);
+int reset_omega(rav_smoother* sm, cudaStream_t s);
 
 namespace rav {
 // Process-wide count of the kernels the solve path (residual, subdomain
@@ -201,6 +213,25 @@ __device__ inline int64_t vert_id(const Geo& g, const int64_t* v) {
 }
 __device__ inline double node_coord(const Geo& g, int a, int64_t I) {
   return (I & 1) ? 0.5 * (g.xv[a][(I - 1) >> 1] + g.xv[a][(I + 1) >> 1]) : g.xv[a][I >> 1];
+}
+
+// Viscosity eta0 * 10^(max_k s_k exp(-|x - c_k|^2 / (2 rho_k^2))), eta0 without blobs.
+struct Coef {
+  double eta0;
+  int nblobs;
+  const double* blobs;  // device, nblobs * 5 (cx, cy, cz, rho, s)
+};
+__device__ inline double viscosity_at(const Coef& C, int dim, const double* x) {
+  if (C.nblobs == 0) return C.eta0;
+  double m = 0.0;
+  for (int k = 0; k < C.nblobs; ++k) {
+    const double* b = C.blobs + 5 * k;
+    double d2 = 0.0;
+    for (int a = 0; a < dim; ++a) d2 += (x[a] - b[a]) * (x[a] - b[a]);
+    const double v = b[4] * exp(-d2 / (2.0 * b[3] * b[3]));
+    m = v > m ? v : m;
+  }
+  return C.eta0 * exp(m * 2.302585092994045684);  // 10^m
 }
 
 // Block-wide sum of one double per thread (blockDim.x a multiple of 32, <= 1024).

@@ -340,7 +340,7 @@ int vcycle_impl(rav_mg* mg, rav_smoother* sm, double* x, const double* b, int nu
 // the timing hook records (its events would be baked into the graph).
 static int vcycle_graph(rav_mg* mg, rav_smoother* sm, double* x, const double* b, int nu1, int nu2, bool x_is_zero,
                         cudaStream_t s) {
-  if (!mg->use_graphs || mg->prof_mask != 0) return vcycle_impl(mg, sm, x, b, nu1, nu2, x_is_zero, s);
+  if (!mg->use_graphs || mg->prof_mask != 0 || sm->collect) return vcycle_impl(mg, sm, x, b, nu1, nu2, x_is_zero, s);
   rav_mg::GraphEntry* hit = nullptr;
   for (auto& e : mg->graphs)
     if (e.sm == sm && e.x == x && e.b == b && e.nu1 == nu1 && e.nu2 == nu2 && e.x_is_zero == x_is_zero) hit = &e;
@@ -494,8 +494,8 @@ static int solve_stationary(rav_mg* mg, rav_smoother* sm, double* x, const doubl
     if (info) { info->iterations = 0; info->final_ratio = 0.0; info->status = RAV_OK; }
     return RAV_OK;
   }
-  int rc = RAV_ERR_NOT_CONVERGED, k = 0;
-  double ratio = 1.0;
+  int rc = RAV_ERR_NOT_CONVERGED, k = 0, fell_back = 0;
+  double ratio = 1.0, prev = 1.0;
   for (k = 1; k <= o.maxit; ++k) {
     RAV_TRY(vcycle_graph(mg, sm, x, b, o.nu_pre, o.nu_post, false, s));
     RAV_TRY(residual_impl(mg, mg->nlev - 1, x, b, L.r, mg->scalar_dev, s));
@@ -505,11 +505,19 @@ static int solve_stationary(rav_mg* mg, rav_smoother* sm, double* x, const doubl
     if (!std::isfinite(ratio)) { rc = RAV_ERR_NAN; break; }
     if (ratio <= o.tol) { rc = RAV_OK; break; }
     if (o.diverge > 0 && ratio > o.diverge) { rc = RAV_ERR_DIVERGED; break; }
+    // fallback: a cycle that reduced the residual by less than fallback_rho
+    // puts every subdomain back on the fixed damping of vanka_setup
+    if (o.fallback_rho > 0 && !fell_back && ratio / prev > o.fallback_rho) {
+      RAV_TRY(reset_omega(sm, s));
+      fell_back = 1;
+    }
+    prev = ratio;
   }
   if (info) {
     info->iterations = k > o.maxit ? o.maxit : k;
     info->final_ratio = ratio;
     info->status = rc;
+    info->fell_back = fell_back;
   }
   return rc;
 }

@@ -78,25 +78,6 @@ __device__ __forceinline__ double dlag2(int a, double t) {
 }
 __device__ __forceinline__ double lag1(int b, double t) { return b == 0 ? 1.0 - t : t; }
 
-struct Coef {
-  double eta0;
-  int nblobs;
-  const double* blobs;  // device, nblobs * 5
-};
-
-__device__ double viscosity_at(const Coef& C, int dim, const double* x) {
-  if (C.nblobs == 0) return C.eta0;
-  double m = 0.0;
-  for (int k = 0; k < C.nblobs; ++k) {
-    const double* b = C.blobs + 5 * k;
-    double d2 = 0.0;
-    for (int a = 0; a < dim; ++a) d2 += (x[a] - b[a]) * (x[a] - b[a]);
-    const double v = b[4] * exp(-d2 / (2.0 * b[3] * b[3]));
-    m = v > m ? v : m;
-  }
-  return C.eta0 * exp(m * 2.302585092994045684);  // 10^m
-}
-
 __device__ void body_force(const Coef& C, int kind, int dim, const double* x, double* f) {
   for (int c = 0; c < dim; ++c) f[c] = 0.0;
   const double pi = 3.14159265358979323846;

@@ -994,6 +994,10 @@ extern "C" void vanka_destroy(rav_smoother* sm) {
     cudaFree(sm->lev[l].scale);
     cudaFree(sm->lev[l].omega);
     cudaFree(sm->lev[l].corr);
+    cudaFree(sm->lev[l].lsum);
+    cudaFree(sm->lev[l].lcnt);
+    cudaFree(sm->lev[l].ones);
+    cudaFree(sm->lev[l].ctmp);
   }
   delete sm;
 }
@@ -1006,7 +1010,7 @@ extern "C" int rav_set_patch_omega(rav_smoother* sm, int level, const float* w, 
   return RAV_OK;
 }
 
-static int apply_impl(rav_smoother* sm, int level, const double* r, double* x, cudaStream_t s) {
+int apply_with_omega(rav_smoother* sm, int level, const double* r, double* x, const double* omega, cudaStream_t s) {
   rav_mg* mg = sm->mg;
   Level& L = mg->lev[level];
   SmLevel& SL = sm->lev[level];
@@ -1018,22 +1022,22 @@ static int apply_impl(rav_smoother* sm, int level, const double* r, double* x, c
     const unsigned gb = (unsigned)((g.n_p + 3) / 4);
     const int gg = (int)((g.n + 255) / 256);
     if (D == 2) {
-      k_av_corr<2><<<gb, 128, 0, s>>>(g, (double*)SL.inv, SL.omega, r, SL.corr);
+      k_av_corr<2><<<gb, 128, 0, s>>>(g, (double*)SL.inv, omega, r, SL.corr);
       k_av_gather<2><<<gg, 256, 0, s>>>(g, SL.corr, x);
     } else {
-      k_av_corr<3><<<gb, 128, 0, s>>>(g, (double*)SL.inv, SL.omega, r, SL.corr);
+      k_av_corr<3><<<gb, 128, 0, s>>>(g, (double*)SL.inv, omega, r, SL.corr);
       k_av_gather<3><<<gg, 256, 0, s>>>(g, SL.corr, x);
     }
     note_launch(2);
   } else if (SL.factored) {
     const unsigned gb = (unsigned)((SL.units + 127) / 128);
-    if (D == 2) k_rav_apply_fact<2><<<gb, 128, 0, s>>>(g, (const double*)SL.inv, SL.ws, SL.omega, r, x, SL.units);
-    else k_rav_apply_fact<3><<<gb, 128, 0, s>>>(g, (const double*)SL.inv, SL.ws, SL.omega, r, x, SL.units);
+    if (D == 2) k_rav_apply_fact<2><<<gb, 128, 0, s>>>(g, (const double*)SL.inv, SL.ws, omega, r, x, SL.units);
+    else k_rav_apply_fact<3><<<gb, 128, 0, s>>>(g, (const double*)SL.inv, SL.ws, omega, r, x, SL.units);
     note_launch();
   } else {
     const unsigned gb = (unsigned)((SL.units + 127) / 128);
 #define RAV_APPLY(DD, T) \
-  k_rav_apply<DD, T><<<gb, 128, 0, s>>>(g, (const T*)SL.inv, SL.scale, SL.omega, r, x, SL.units)
+  k_rav_apply<DD, T><<<gb, 128, 0, s>>>(g, (const T*)SL.inv, SL.scale, omega, r, x, SL.units)
     if (D == 2) {
       switch (sm->prec) {
         case RAV_F64_ROWS: RAV_APPLY(2, double); break;
@@ -1054,6 +1058,19 @@ static int apply_impl(rav_smoother* sm, int level, const double* r, double* x, c
   }
   RAV_CUDA(cudaGetLastError());
   RAV_TRY(prof_end(mg, level, PROF_APPLY, e0, s));
+  return RAV_OK;
+}
+
+static int apply_impl(rav_smoother* sm, int level, const double* r, double* x, cudaStream_t s) {
+  if (sm->collect) RAV_TRY(collect_labels(sm, level, r, s));
+  return apply_with_omega(sm, level, r, x, sm->lev[level].omega, s);
+}
+
+int reset_omega(rav_smoother* sm, cudaStream_t s) {
+  for (int l = 1; l < sm->mg->nlev; ++l) {
+    k_fill<<<grid_for(sm->lev[l].np, 256), 256, 0, s>>>(sm->lev[l].omega, sm->lev[l].np, sm->omega);
+    RAV_CUDA(cudaGetLastError());
+  }
   return RAV_OK;
 }
 

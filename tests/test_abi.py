@@ -59,12 +59,12 @@ def test_struct_layouts_match_the_header(tmp_path):
     prog.write_text(
         '#include <stddef.h>\n#include <stdio.h>\n#include "ravanka.h"\n'
         'int main(void){printf("%zu %zu %zu %zu %zu %zu\\n", sizeof(rav_problem), offsetof(rav_problem, bc),'
-        ' sizeof(rav_solve_opts), offsetof(rav_solve_opts, diverge), sizeof(rav_solve_info),'
-        ' offsetof(rav_solve_info, history_host)); return 0;}\n')
+        ' sizeof(rav_solve_opts), offsetof(rav_solve_opts, fallback_rho), sizeof(rav_solve_info),'
+        ' offsetof(rav_solve_info, fell_back)); return 0;}\n')
     exe = tmp_path / "layout"
     subprocess.check_call(["gcc", "-std=c99", "-I", os.path.join(ROOT, "include"), str(prog), "-o", str(exe)])
     got = [int(v) for v in subprocess.check_output([str(exe)]).split()]
     want = [ctypes.sizeof(_capi.RavProblem), _capi.RavProblem.bc.offset, ctypes.sizeof(_capi.RavSolveOpts),
-            _capi.RavSolveOpts.diverge.offset, ctypes.sizeof(_capi.RavSolveInfo),
-            _capi.RavSolveInfo.history_host.offset]
+            _capi.RavSolveOpts.fallback_rho.offset, ctypes.sizeof(_capi.RavSolveInfo),
+            _capi.RavSolveInfo.fell_back.offset]
     assert got == want

@@ -1,0 +1,133 @@
+"""Learned per-subdomain damping: GPU kernels against the oracle, and what the
+trained network gains over fixed damping on a held-out problem."""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2103_10127_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA device", allow_module_level=True)
+
+import paper_2103_10127_gb300 as R  # noqa: E402
+from paper_2103_10127_gb300 import learned  # noqa: E402
+
+
+def _problem(dim, N, nlev, seed, s_max=4.0, aspect=8.0, nblobs=12):
+    coords = inputs.graded_coordinates(N, aspect, dim) if aspect > 1 else None
+    blobs = inputs.viscosity_blobs(seed, k=nblobs, s_max=s_max)
+    return dict(dim=dim, N=N, n_levels=nlev, coords=coords, blobs=blobs, bc=R.BC_NOSLIP)
+
+
+def test_mlp_gradient_matches_the_oracle():
+    P = learned.init_params(3)
+    X = torch.from_numpy(inputs.normal(4, 8 * 300).reshape(300, 8).astype(np.float32)).cuda()
+    y = torch.from_numpy((1.5 * inputs.uniform(5, 300)).astype(np.float32)).cuda()
+    loss, g = learned.loss_grad(P, X, y)
+    oloss, og = O.mlp_loss_grad(P.cpu().numpy().astype(np.float64), X.cpu().numpy(), y.cpu().numpy())
+    g = g.cpu().numpy()
+    assert abs(loss.item() - oloss) <= 1e-5 * oloss
+    assert np.linalg.norm(g - og) <= 1e-3 * np.linalg.norm(og)
+    assert np.abs(g - og).max() <= 1e-3 * np.abs(og).max()
+
+
+def test_mlp_forward_matches_the_oracle_with_fp16_weights():
+    P = learned.init_params(6)
+    X = torch.from_numpy(inputs.normal(7, 8 * 500).reshape(500, 8).astype(np.float32)).cuda()
+    got = learned.forward(P, X).cpu().numpy()
+    P16 = P.half().double().cpu().numpy()
+    want = O.mlp_forward(P16, X.cpu().numpy())
+    assert np.abs(got - want).max() <= 2e-5
+
+
+def test_labels_match_the_oracle():
+    spec = _problem(2, 12, 2, seed=8, s_max=2.0, aspect=3.0, nblobs=4)
+    mg = R.Multigrid(**spec)
+    sm = R.Smoother(mg, R.RAV, R.F64, 0.5)
+    orc = O.Oracle(2, 12, 2, coords=spec["coords"], blobs=spec["blobs"], bc=O.BC_NOSLIP)
+    orc.build_patches(1)
+    n = mg.n(1)
+    x = inputs.normal(9, n)
+    b = inputs.normal(10, n)
+    from paper_2103_10127_gb300 import _capi
+    lib = _capi.load()
+    assert lib.rav_label_collection(sm.h, 1) == 0
+    xg = torch.from_numpy(x).cuda()
+    sm.smooth(1, xg, torch.from_numpy(b).cuda(), 1)
+    y = torch.empty(mg.counts(1)["n_p"], dtype=torch.float32, device="cuda")
+    assert lib.rav_read_labels(sm.h, 1, learned._p(y), learned._s()) == 0
+    assert lib.rav_label_collection(sm.h, 0) == 0
+    r = orc.residual(1, x, b)
+    want = orc.labels(1, r)
+    assert np.abs(y.cpu().numpy() - want).max() <= 1e-6
+
+
+def test_features_follow_their_definition():
+    spec = _problem(2, 8, 2, seed=11, s_max=3.0, aspect=4.0, nblobs=3)
+    mg = R.Multigrid(**spec)
+    sm = R.Smoother(mg, R.RAV, R.F64, 0.5)
+    f = learned.features(sm, 1).cpu().numpy()
+    orc = O.Oracle(2, 8, 1, coords=spec["coords"], blobs=spec["blobs"])
+    xg, wg = np.polynomial.legendre.leggauss(3)
+    xg = 0.5 * (xg + 1)
+    c = spec["coords"]
+    N = 8
+    for p in (0, 10, 40, 80):
+        v = (p % (N + 1), p // (N + 1))
+        cells = [(i, j) for i in (v[0] - 1, v[0]) for j in (v[1] - 1, v[1]) if 0 <= i < N and 0 <= j < N]
+        etas, asp, diag = [], [], []
+        for i, j in cells:
+            hx, hy = c[0][i + 1] - c[0][i], c[1][j + 1] - c[1][j]
+            asp.append(max(hx, hy) / min(hx, hy))
+            diag.append(np.hypot(hx, hy))
+            for a in xg:
+                for bq in xg:
+                    etas.append(orc.viscosity(np.array([c[0][i] + hx * a, c[1][j] + hy * bq, 0.0])))
+        etas = np.array(etas)
+        want = [np.log10(etas.max() / etas.min()), np.log10(etas).mean(), np.log10(max(asp)), np.log10(min(asp)),
+                1.0, None, None, np.log10(np.mean(diag))]
+        for k in (0, 1, 2, 3, 4, 7):
+            assert abs(f[p, k] - want[k]) <= 1e-5 * max(1.0, abs(want[k])), (p, k)
+    assert np.all((f[:, 5] > 0) & (f[:, 5] <= 1)) and np.all((f[:, 6] >= 0) & (f[:, 6] <= 1))
+
+
+def test_trained_network_against_fixed_damping_on_a_held_out_problem():
+    """Train on line-search labels from 2-D and 3-D runs (seeds 101-104), then
+    solve a held-out 3-D problem (seed 2103, contrast up to 1e4, aspect 8) to
+    1e-8 with fixed damping and with the learned damping (fixed-damping
+    fallback armed); the oracle's residual judges the learned solution."""
+    Xs, ys = [], []
+    for seed, (dim, N, nlev) in zip((101, 102, 103, 104), ((2, 32, 3), (2, 48, 3), (3, 8, 2), (3, 12, 2))):
+        spec = _problem(dim, N, nlev, seed)
+        mg = R.Multigrid(**spec)
+        sm = R.Smoother(mg, R.RAV, R.F64, 0.5)
+        b = mg.rhs(R.F_SINKER)
+        x = mg.initial_guess()
+        X, y = learned.collect(mg, sm, x, b, cycles=3)
+        Xs.append(X)
+        ys.append(y)
+    X, y = torch.cat(Xs), torch.cat(ys)
+    P, losses = learned.train(X, y, steps=800, lr=3e-3)
+    assert losses[-1][1] < losses[0][1]
+
+    spec = _problem(3, 16, 2, seed=2103)
+    mg = R.Multigrid(**spec)
+    sm = R.Smoother(mg, R.RAV, R.F64, 0.5)
+    b = mg.rhs(R.F_SINKER)
+    x_fixed = mg.initial_guess()
+    it_fixed, h_fixed, rc1 = mg.solve(sm, x_fixed, b, tol=1e-8, maxit=200)
+    learned.install(sm, P)
+    x_learn = mg.initial_guess()
+    info = {}
+    it_learn, h_learn, rc2 = mg.solve(sm, x_learn, b, tol=1e-8, maxit=200, fallback_rho=0.9, info_out=info)
+    assert rc1 == 0 and rc2 == 0
+    print(f"cycles to 1e-8: fixed 0.5 -> {it_fixed}, learned -> {it_learn} (fallback {info['fell_back']})")
+    assert it_learn <= it_fixed + 2
+    orc = O.Oracle(3, 16, 2, coords=spec["coords"], blobs=spec["blobs"], bc=O.BC_NOSLIP)
+    bo = orc.rhs(O.F_SINKER)
+    r0 = np.linalg.norm(orc.residual(1, orc.initial_guess(), bo))
+    r = np.linalg.norm(orc.residual(1, x_learn.cpu().numpy(), bo))
+    assert r <= 2e-8 * r0
