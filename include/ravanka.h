@@ -263,9 +263,11 @@ int solve(rav_mg* mg, rav_smoother* sm, double* x_dev, const double* b_dev, cons
  *   nodes on the Dirichlet boundary, log10 of the mean cell diagonal.
  * rav_label_collection(sm, 1): clears and starts accumulating, in every RAV
  *   smoothing step (vanka_smooth, vcycle, solve; V-cycles then run kernel by
- *   kernel), omega*_i = clip(<r, L c_i> / <L c_i, L c_i>, 0, 1.5), where r is the
- *   step's residual and c_i the subdomain's own restricted correction with
- *   weight 1: the exact minimiser of ||r - w L c_i||_2.  (sm, 0) stops.
+ *   kernel), the coordinate line-search weight of each subdomain:
+ *   omega*_i = clip(omega_i + <r', L c_i> / <L c_i, L c_i>, 0, 1.5), where r is
+ *   the step's residual, c_i the subdomain's own restricted correction with
+ *   weight 1, s = sum_j omega_j c_j the whole step and r' = r - L s: the exact
+ *   minimiser over w of ||r - L (s + (w - omega_i) c_i)||_2.  (sm, 0) stops.
  * rav_read_labels: label_dev[n_p(l)] = mean omega*_i (the fixed damping where
  *   no sample was taken).
  * rav_mlp_forward: omega_dev[n] for feature rows X_dev[n * 8].

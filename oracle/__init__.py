@@ -79,7 +79,7 @@ def _load():
             "orc_solve": (i, [P, P, P, d, i, i, i, P]),
             "orc_fgmres": (i, [P, P, P, d, i, i, i, i, P]),
             "orc_round_format": (None, [i, P, P, ll]),
-            "orc_labels": (None, [P, i, P, d, P]),
+            "orc_labels": (None, [P, i, P, P, d, P]),
             "orc_mlp_nparam": (ll, []),
             "orc_mlp_forward": (None, [P, P, ll, P]),
             "orc_mlp_loss_grad": (d, [P, P, P, ll, P]),
@@ -240,11 +240,13 @@ class Oracle:
         out = out.reshape(-1, ni)
         return (out, sc) if quantised else out
 
-    def labels(self, lev, r, fallback=0.5):
-        """Line-search optimal damping per subdomain for residual r (needs patches on lev)."""
+    def labels(self, lev, r, omega=None, fallback=0.5):
+        """Coordinate line-search damping per subdomain for residual r given the
+        current weights omega (default: `fallback` everywhere); needs patches on lev."""
         r = _f64(r)
         out = np.empty(self.count(lev, 5))
-        _lib.orc_labels(self.h, lev, _ptr(r), float(fallback), _ptr(out))
+        om = None if omega is None else _f64(omega)
+        _lib.orc_labels(self.h, lev, _ptr(r), _ptr(om), float(fallback), _ptr(out))
         return out
 
     def patch_rows(self, lev, p, max_rows=64, max_n=512):

@@ -1132,38 +1132,52 @@ int orc_fgmres(void* h, double* x, const double* b, double tol, int maxit, int r
 // subdomain in Eq. 11): a per-subdomain weight omega_i predicted by a small
 // MLP from local features, trained on line-search-optimal weights.
 //
-// Label of subdomain i for residual r: c_i = Rt_i^T (L_i^{-1} R_i r) (its own
-// restricted correction, weight 1), omega*_i = argmin_w ||r - w L c_i||_2 =
-// <r, L c_i> / <L c_i, L c_i>, clipped to [0, 1.5]; `fallback` when L c_i = 0.
-// L c_i is formed with the full sparse L (rows of all DoFs), r on free rows.
-void orc_labels(void* h, int l, const double* r, double fallback, double* out) {
+// Label of subdomain i for residual r, as a coordinate line search of the
+// additive step: with c_i = Rt_i^T (L_i^{-1} R_i r) (its own restricted
+// correction at weight 1) and the whole RAV step s = sum_j omega_j c_j, the
+// weight of subdomain i alone that minimises ||r - L (s + (w - omega_i) c_i)||_2
+// is omega*_i = omega_i + <r', L c_i> / <L c_i, L c_i> with r' = r - L s,
+// clipped to [0, 1.5] (omega_i when L c_i = 0).  Norms over free rows; L c_i is
+// formed with the full sparse L.  omega: current weights (null: `fallback`).
+void orc_labels(void* h, int l, const double* r, const double* omega, double fallback, double* out) {
   const Level& L = ((Oracle*)h)->lev[l];
   const int64_t np = (int64_t)L.poff.size() - 1;
-  std::vector<double> c(L.n, 0.0), Lc(L.n, 0.0);
+  std::vector<std::vector<double>> cs(np);
+  std::vector<double> s(L.n, 0.0), rp(L.n, 0.0);
   for (int64_t p = 0; p < np; ++p) {
     const int64_t b0 = L.poff[p], ni = L.poff[p + 1] - b0;
-    std::vector<double> rloc(ni), rows;
-    for (int64_t k = 0; k < ni; ++k) rloc[k] = r[L.pdof[b0 + k]];
+    std::vector<double> rows;
     inverse_rows(L, p, false, rows);
-    std::vector<int64_t> touched;
+    cs[p].resize(L.owned[p].size());
     for (size_t j = 0; j < L.owned[p].size(); ++j) {
-      double s = 0.0;
-      for (int64_t k = 0; k < ni; ++k) s += rows[j * ni + k] * rloc[k];
-      const int64_t dof = L.pdof[b0 + L.owned[p][j]];
-      c[dof] = s;
-      touched.push_back(dof);
+      double v = 0.0;
+      for (int64_t k = 0; k < ni; ++k) v += rows[j * ni + k] * r[L.pdof[b0 + k]];
+      cs[p][j] = v;
+      s[L.pdof[b0 + L.owned[p][j]]] += (omega ? omega[p] : fallback) * v;
     }
+  }
+  for (int64_t m = 0; m < L.n; ++m) {
+    if (L.dir[m]) continue;
+    double t = 0.0;
+    for (int64_t k = L.rp[m]; k < L.rp[m + 1]; ++k) t += L.va[k] * s[L.ci[k]];
+    rp[m] = r[m] - t;
+  }
+  std::vector<double> c(L.n, 0.0);
+  for (int64_t p = 0; p < np; ++p) {
+    const int64_t b0 = L.poff[p];
+    for (size_t j = 0; j < L.owned[p].size(); ++j) c[L.pdof[b0 + L.owned[p][j]]] = cs[p][j];
     double num = 0.0, den = 0.0;
     for (int64_t m = 0; m < L.n; ++m) {
       if (L.dir[m]) continue;
-      double s = 0.0;
-      for (int64_t k = L.rp[m]; k < L.rp[m + 1]; ++k) s += L.va[k] * c[L.ci[k]];
-      num += r[m] * s;
-      den += s * s;
+      double t = 0.0;
+      for (int64_t k = L.rp[m]; k < L.rp[m + 1]; ++k) t += L.va[k] * c[L.ci[k]];
+      num += rp[m] * t;
+      den += t * t;
     }
-    double w = den > 0.0 ? num / den : fallback;
+    const double base = omega ? omega[p] : fallback;
+    double w = den > 0.0 ? base + num / den : base;
     out[p] = w < 0.0 ? 0.0 : (w > 1.5 ? 1.5 : w);
-    for (int64_t dof : touched) c[dof] = 0.0;
+    for (size_t j = 0; j < L.owned[p].size(); ++j) c[L.pdof[b0 + L.owned[p][j]]] = 0.0;
   }
 }
 

@@ -152,6 +152,8 @@ struct SmLevel {
   int* lcnt = nullptr;       // number of samples
   double* ones = nullptr;    // unit damping
   double* ctmp = nullptr;    // subdomain corrections with unit damping
+  double* stmp = nullptr;    // the whole step with the current damping
+  double* rtmp = nullptr;    // residual after that step
 };
 
 struct rav_smoother {

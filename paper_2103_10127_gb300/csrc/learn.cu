@@ -2,10 +2,12 @@
 // per subdomain; the paper itself uses one constant).
 //
 //  * features: 8 numbers per subdomain from the local grid and viscosity;
-//  * labels:   omega*_i = clip(<r, L c_i> / <L c_i, L c_i>, 0, 1.5), c_i the
-//              subdomain's own restricted correction (weight 1): the exact
-//              minimiser of ||r - w L c_i||_2, averaged over the smoothing
-//              steps in which it is collected;
+//  * labels:   omega*_i = clip(omega_i + <r', L c_i> / <L c_i, L c_i>, 0, 1.5),
+//              c_i the subdomain's own restricted correction (weight 1),
+//              r' = r - L sum_j omega_j c_j the residual after the whole
+//              step: the exact minimiser of the post-step residual norm in
+//              omega_i alone, averaged over the smoothing steps in which it
+//              is collected;
 //  * model:    MLP 8 -> 64 -> 64 -> 1 (ReLU, ReLU, 1.5 sigmoid), parameters
 //              W1[64][8], b1[64], W2[64][64], b2[64], W3[64], b3 (4801);
 //              inference with weights rounded to fp16 and fp32 accumulation,
@@ -162,10 +164,12 @@ __device__ __forceinline__ int64_t win_dof(const Geo& g, const int* v, int loc) 
   return g.n_u + vert_id(g, V);
 }
 
+// r: the residual after the whole step, r' = r - L s; label = omega_i +
+// <r', L c_i> / <L c_i, L c_i> (coordinate line search of the additive step).
 template <int D>
 __global__ void k_labels(Geo g, const int64_t* __restrict__ rp, const int32_t* __restrict__ ci,
                          const double* __restrict__ va, const double* __restrict__ r,
-                         const double* __restrict__ c, double fallback, double* __restrict__ lsum,
+                         const double* __restrict__ c, const double* __restrict__ base, double* __restrict__ lsum,
                          int* __restrict__ lcnt) {
   using Wn = Win<D>;
   constexpr int WPB = 4;
@@ -216,7 +220,7 @@ __global__ void k_labels(Geo g, const int64_t* __restrict__ rp, const int32_t* _
     den += __shfl_xor_sync(0xffffffffu, den, o);
   }
   if (lane == 0) {
-    double w = den > 0.0 ? num / den : fallback;
+    double w = den > 0.0 ? base[p] + num / den : base[p];
     w = w < 0.0 ? 0.0 : (w > 1.5 ? 1.5 : w);
     lsum[p] += w;
     lcnt[p] += 1;
@@ -425,6 +429,8 @@ extern "C" int rav_label_collection(rav_smoother* sm, int enable) {
       RAV_CUDA(cudaMalloc(&SL.lcnt, sizeof(int) * np));
       RAV_CUDA(cudaMalloc(&SL.ones, sizeof(double) * np));
       RAV_CUDA(cudaMalloc(&SL.ctmp, sizeof(double) * n));
+      RAV_CUDA(cudaMalloc(&SL.stmp, sizeof(double) * n));
+      RAV_CUDA(cudaMalloc(&SL.rtmp, sizeof(double) * n));
       std::vector<double> one(np, 1.0);
       RAV_CUDA(cudaMemcpy(SL.ones, one.data(), sizeof(double) * np, cudaMemcpyHostToDevice));
     }
@@ -435,18 +441,22 @@ extern "C" int rav_label_collection(rav_smoother* sm, int enable) {
 }
 
 // Called by the smoother, before its apply, while collection is on: c = the
-// subdomains' own corrections (weight 1) for residual r, then the labels.
+// subdomains' own corrections (weight 1) for residual r, s = the whole step
+// with the current weights, r' = r - L s, then the labels.
 int collect_labels(rav_smoother* sm, int level, const double* r, cudaStream_t s) {
   rav_mg* mg = sm->mg;
   SmLevel& SL = sm->lev[level];
-  const Level& L = mg->lev[level];
+  Level& L = mg->lev[level];
   RAV_CUDA(cudaMemsetAsync(SL.ctmp, 0, sizeof(double) * L.g.n, s));
+  RAV_CUDA(cudaMemsetAsync(SL.stmp, 0, sizeof(double) * L.g.n, s));
   RAV_TRY(apply_with_omega(sm, level, r, SL.ctmp, SL.ones, s));
+  RAV_TRY(apply_with_omega(sm, level, r, SL.stmp, SL.omega, s));
+  RAV_TRY(residual_impl(mg, level, SL.stmp, r, SL.rtmp, nullptr, s));
   const unsigned gb = (unsigned)((L.g.n_p + 3) / 4);
   if (L.g.dim == 2)
-    k_labels<2><<<gb, 128, 0, s>>>(L.g, L.rp, L.ci, L.va, r, SL.ctmp, sm->omega, SL.lsum, SL.lcnt);
+    k_labels<2><<<gb, 128, 0, s>>>(L.g, L.rp, L.ci, L.va, SL.rtmp, SL.ctmp, SL.omega, SL.lsum, SL.lcnt);
   else
-    k_labels<3><<<gb, 128, 0, s>>>(L.g, L.rp, L.ci, L.va, r, SL.ctmp, sm->omega, SL.lsum, SL.lcnt);
+    k_labels<3><<<gb, 128, 0, s>>>(L.g, L.rp, L.ci, L.va, SL.rtmp, SL.ctmp, SL.omega, SL.lsum, SL.lcnt);
   RAV_CUDA(cudaGetLastError());
   return RAV_OK;
 }

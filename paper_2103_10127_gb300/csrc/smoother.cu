@@ -998,6 +998,8 @@ extern "C" void vanka_destroy(rav_smoother* sm) {
     cudaFree(sm->lev[l].lcnt);
     cudaFree(sm->lev[l].ones);
     cudaFree(sm->lev[l].ctmp);
+    cudaFree(sm->lev[l].stmp);
+    cudaFree(sm->lev[l].rtmp);
   }
   delete sm;
 }
