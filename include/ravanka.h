@@ -276,8 +276,11 @@ int solve(rav_mg* mg, rav_smoother* sm, double* x_dev, const double* b_dev, cons
  *   ceil(n / 64) * 4802 floats.  loss_dev may be NULL.
  * rav_adam_step: one Adam update (beta 0.9 / 0.999, eps 1e-8) of params_dev
  *   with moments m_dev, v_dev; t = 1, 2, ... the step number.
- * rav_set_learned_omega: features -> MLP -> omega_i on every level of sm
- *   (replaces the damping; rav_reset_omega restores the fixed value). */
+ * rav_set_learned_omega: features -> MLP -> omega_i on every level of sm, then
+ *   omega_i <- m + shrink (omega_i - m) with m the level's mean prediction
+ *   (shrink in [0, 1]: 1 keeps the per-subdomain predictions, 0 gives one
+ *   predicted weight per level); replaces the damping, rav_reset_omega
+ *   restores the fixed value. */
 int rav_mlp_nparam(void);
 int rav_patch_features(rav_smoother* sm, int level, float* feat_dev, rav_stream stream);
 int rav_label_collection(rav_smoother* sm, int enable);
@@ -287,7 +290,7 @@ int rav_mlp_loss_grad(const float* params_dev, const float* X_dev, const float* 
                       float* loss_dev, float* work_dev, int64_t work_floats, rav_stream stream);
 int rav_adam_step(float* params_dev, float* m_dev, float* v_dev, const float* grad_dev, float lr, int t,
                   rav_stream stream);
-int rav_set_learned_omega(rav_smoother* sm, const float* params_dev, rav_stream stream);
+int rav_set_learned_omega(rav_smoother* sm, const float* params_dev, double shrink, rav_stream stream);
 int rav_reset_omega(rav_smoother* sm, rav_stream stream);
 
 /* ---- Batched solves: many problems x several right-hand sides ------------

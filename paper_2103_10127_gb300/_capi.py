@@ -66,7 +66,7 @@ _SIGS = {
     "rav_mlp_forward": (I32, [P, P, ctypes.c_int64, P, P]),
     "rav_mlp_loss_grad": (I32, [P, P, P, ctypes.c_int64, P, P, P, ctypes.c_int64, P]),
     "rav_adam_step": (I32, [P, P, P, P, ctypes.c_float, I32, P]),
-    "rav_set_learned_omega": (I32, [P, P, P]),
+    "rav_set_learned_omega": (I32, [P, P, F64, P]),
     "rav_reset_omega": (I32, [P, P]),
     "batch_setup": (I32, [P, P, I32, I32, P, ctypes.POINTER(P)]),
     "batch_destroy": (None, [P]),

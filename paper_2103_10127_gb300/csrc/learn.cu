@@ -503,8 +503,23 @@ extern "C" int rav_adam_step(float* params, float* m, float* v, const float* gra
   return RAV_OK;
 }
 
-extern "C" int rav_set_learned_omega(rav_smoother* sm, const float* params, rav_stream stream) {
-  if (!sm || !params) return RAV_ERR_ARG;
+// omega_i <- m + shrink * (omega_i - m), m the mean over the level (one block).
+__global__ void k_shrink_to_mean(double* __restrict__ w, int64_t n, double shrink) {
+  __shared__ double red[1024];
+  double s = 0.0;
+  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) s += w[i];
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+    __syncthreads();
+  }
+  const double m = red[0] / (double)n;
+  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) w[i] = m + shrink * (w[i] - m);
+}
+
+extern "C" int rav_set_learned_omega(rav_smoother* sm, const float* params, double shrink, rav_stream stream) {
+  if (!sm || !params || !(shrink >= 0.0 && shrink <= 1.0)) return RAV_ERR_ARG;
   rav_mg* mg = sm->mg;
   cudaStream_t s = S(stream);
   for (int l = 1; l < mg->nlev; ++l) {
@@ -513,6 +528,7 @@ extern "C" int rav_set_learned_omega(rav_smoother* sm, const float* params, rav_
     RAV_CUDA(cudaMallocAsync(&feat, sizeof(float) * np * kF, s));
     RAV_TRY(rav_patch_features(sm, l, feat, stream));
     k_mlp_forward<<<(unsigned)((np + 127) / 128), 128, 0, s>>>(params, feat, np, nullptr, sm->lev[l].omega);
+    if (shrink < 1.0) k_shrink_to_mean<<<1, 1024, 0, s>>>(sm->lev[l].omega, np, shrink);
     RAV_CUDA(cudaGetLastError());
     RAV_CUDA(cudaFreeAsync(feat, s));
   }

@@ -114,9 +114,10 @@ def train(X, y, steps=1500, lr=3e-3, seed=inputs.BASE_SEED, log_every=100):
     return P, losses
 
 
-def install(sm, params):
-    """omega_i of every subdomain of every level predicted by the MLP."""
-    check(_capi.load().rav_set_learned_omega(sm.h, _p(params), _s()), "rav_set_learned_omega")
+def install(sm, params, shrink=0.0):
+    """omega_i of every subdomain of every level predicted by the MLP, shrunk
+    toward the level's mean prediction by `shrink` (0: one weight per level)."""
+    check(_capi.load().rav_set_learned_omega(sm.h, _p(params), float(shrink), _s()), "rav_set_learned_omega")
 
 
 def reset(sm):
