@@ -56,7 +56,8 @@ def parse():
     ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="2d512", choices=sorted(WORKLOADS) + ["2d-batch"])
+    ap.add_argument("--workload", default="2d512",
+                    choices=sorted(WORKLOADS) + ["2d-batch", "3d-precision", "3d-learned"])
     ap.add_argument("--nprob", type=int, default=256, help="problems of the 2d-batch workload")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -458,10 +459,128 @@ def run_batch(args):
     print(json.dumps(out), flush=True)
 
 
+def run_precision(args):
+    """3-D Stokes Q2-Q1 on 32^3 (or --N), 4 levels, 20 viscosity blobs
+    (contrast up to 1e3, seed 2103), no-slip, sinker force; FGMRES(30) with one
+    RAV V(2,2) cycle as preconditioner, fp64 residual / coarse solve / LU, the
+    patch inverses stored as fp64 (factored), fp64 rows, fp32, bf16 or fp8:
+    wall time and iterations to a 1e-8 residual reduction for each."""
+    import torch
+    import paper_2103_10127_gb300 as R
+    from paper_2103_10127_gb300 import inputs
+
+    torch.cuda.set_device(0)
+    N = args.N or 32
+    nlev = args.levels or 4
+    blobs = inputs.viscosity_blobs(inputs.BASE_SEED, k=20, s_max=3.0)
+    mg = R.Multigrid(3, N, nlev, blobs=blobs, bc=R.BC_NOSLIP)
+    b = mg.rhs(R.F_SINKER)
+    n = mg.n()
+    res = {}
+    for name, prec in (("f64-factored", R.F64), ("f64-rows", R.F64_ROWS), ("f32", R.F32), ("bf16", R.BF16),
+                       ("fp8", R.FP8)):
+        t0 = time.perf_counter()
+        sm = R.Smoother(mg, R.RAV, prec, 0.5)
+        torch.cuda.synchronize()
+        setup = time.perf_counter() - t0
+        x = mg.initial_guess()
+        mg.solve(sm, x, b, tol=1e-8, maxit=1, outer=1, raise_on_error=False)  # capture graphs, warm
+        best = None
+        for _ in range(3):
+            x = mg.initial_guess()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            it, hist, rc = mg.solve(sm, x, b, tol=1e-8, maxit=200, outer=1, raise_on_error=False)
+            torch.cuda.synchronize()
+            dt = time.perf_counter() - t0
+            best = dt if best is None or dt < best else best
+        _, r_true = mg.residual(nlev - 1, x, b, norm=True)
+        _, r0 = mg.residual(nlev - 1, mg.initial_guess(), b, norm=True)
+        res[name] = {"seconds": best, "iterations": it, "status": rc, "true_ratio": r_true / r0,
+                     "setup_s": setup}
+        del sm
+    base = res["f64-factored"]["seconds"]
+    out = {"metric": "time to 1e-8 residual reduction (FGMRES(30), RAV V(2,2) preconditioner)",
+           "value": min(r["seconds"] for r in res.values()), "unit": "s", "higher_is_better": False,
+           "n_gpus": 1, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": f"3D Stokes Q2-Q1 {N}^3, {nlev} levels, 20 blobs contrast <= 1e3, sinker",
+                      "dofs": n},
+           "formats": res, "speedup_vs_f64_factored": {k: base / v["seconds"] for k, v in res.items()}}
+    print(json.dumps(out), flush=True)
+
+
+def run_learned(args):
+    """Learned damping on 3-D 40^3 (or --N), 4 levels, 20 blobs with contrast
+    up to 1e4 and z-graded cells of aspect 8 (seed 2103): the MLP is trained on
+    line-search labels from eight 2-D/3-D runs with other seeds, then FGMRES(30)
+    and stationary solves to 1e-8 with fixed damping 0.5 and with the learned
+    per-level damping."""
+    import torch
+    import paper_2103_10127_gb300 as R
+    from paper_2103_10127_gb300 import inputs, learned
+
+    torch.cuda.set_device(0)
+
+    def spec(dim, N, nlev, seed, s_max, asp):
+        return dict(dim=dim, N=N, n_levels=nlev, bc=R.BC_NOSLIP,
+                    coords=inputs.graded_coordinates(N, asp, dim) if asp > 1 else None,
+                    blobs=inputs.viscosity_blobs(seed, k=12 if seed != inputs.BASE_SEED else 20, s_max=s_max))
+
+    train_set = [(101, 2, 32, 3, 4.0, 8.0), (102, 2, 48, 3, 2.0, 1.0), (103, 3, 8, 2, 4.0, 8.0),
+                 (104, 3, 12, 2, 2.0, 1.0), (105, 3, 16, 2, 3.0, 4.0), (106, 2, 64, 4, 3.0, 4.0),
+                 (107, 3, 16, 2, 1.0, 1.0), (108, 2, 64, 4, 1.0, 2.0)]
+    t0 = time.perf_counter()
+    Xs, ys = [], []
+    for seed, dim, N, nlev, s_max, asp in train_set:
+        mg = R.Multigrid(**spec(dim, N, nlev, seed, s_max, asp))
+        sm = R.Smoother(mg, R.RAV, R.F64, 0.5)
+        X, y = learned.collect(mg, sm, mg.initial_guess(), mg.rhs(R.F_SINKER), cycles=3)
+        Xs.append(X)
+        ys.append(y)
+    collect_s = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    P, losses = learned.train(torch.cat(Xs), torch.cat(ys), steps=1500, lr=3e-3)
+    torch.cuda.synchronize()
+    train_s = time.perf_counter() - t0
+    N = args.N or 40
+    nlev = args.levels or 4
+    results = {}
+    for label, (s_max, asp) in (("contrast1e4-aspect8", (4.0, 8.0)), ("contrast1e3-aspect1", (3.0, 1.0))):
+        mg = R.Multigrid(**spec(3, N, nlev, inputs.BASE_SEED, s_max, asp))
+        sm = R.Smoother(mg, R.RAV, R.F64, 0.5)
+        b = mg.rhs(R.F_SINKER)
+        row = {}
+        for mode in ("fixed", "learned"):
+            if mode == "learned":
+                learned.install(sm, P, shrink=0.0)
+            for outer, oname in ((1, "fgmres"), (0, "stationary")):
+                x = mg.initial_guess()
+                mg.solve(sm, x, b, tol=1e-8, maxit=1, outer=outer, raise_on_error=False)
+                x = mg.initial_guess()
+                torch.cuda.synchronize()
+                t1 = time.perf_counter()
+                it, hist, rc = mg.solve(sm, x, b, tol=1e-8, maxit=200, outer=outer, raise_on_error=False)
+                torch.cuda.synchronize()
+                row[f"{mode}-{oname}"] = {"iterations": it, "status": rc, "seconds": time.perf_counter() - t1}
+        results[label] = row
+    out = {"metric": "iterations / time to 1e-8, learned vs fixed damping", "n_gpus": 1, "data": "synthetic",
+           "config": {"workload": f"3D Stokes Q2-Q1 {N}^3, {nlev} levels, 20 blobs, sinker", "train_problems": 8,
+                      "train_samples": int(sum(len(y) for y in ys)), "collect_s": collect_s, "train_s": train_s,
+                      "loss_first_last": [losses[0][1], losses[-1][1]]},
+           "results": results}
+    print(json.dumps(out), flush=True)
+
+
 def main():
     args = parse()
     if args.workload == "2d-batch":
         run_batch(args)
+        return
+    if args.workload == "3d-precision":
+        run_precision(args)
+        return
+    if args.workload == "3d-learned":
+        run_learned(args)
         return
     W = dict(WORKLOADS[args.workload])
     if args.N:
