@@ -29,6 +29,7 @@ _LIB = os.path.join(_HERE, "librav_oracle.so")
 
 RAV, AV, MV, MV_COLOURED = 0, 1, 2, 3
 F64, F32, BF16, FP8 = 0, 1, 2, 3
+F32_FACT, BF16_FACT = 5, 6  # factored storage rounded to fp32 / bf16
 BC_CAVITY, BC_NOSLIP, BC_QUADRATIC = 0, 1, 2
 F_NONE, F_PSI, F_SINKER, F_QUADRATIC = 0, 1, 2, 3
 

@@ -156,7 +156,7 @@ struct Oracle {
   Problem P;
   std::vector<Level> lev;  // lev[0] coarsest
   int kind = 0;            // 0 RAV, 1 AV, 2 MV lexicographic, 3 MV coloured
-  int prec = 0;            // 0 fp64, 1 fp32, 2 bf16, 3 fp8 e4m3 (RAV only)
+  int prec = 0;            // 0 fp64, 1 fp32, 2 bf16, 3 fp8 e4m3, 5/6 fp32/bf16 factored (RAV only)
   int err = 0;
 };
 
@@ -658,11 +658,67 @@ double fmt_scale(int prec, const double* row, int64_t n) {
   return (double)(float)(m / 448.0);
 }
 
+// Factored storage of the owned rows (prec 5: fp32, 6: bf16).  The local
+// system of Eq. 11 has the saddle-point form L_i = [A b; b^T 0] (one pressure
+// DoF, the last in sorted order), so with w = A^{-1} b and s = -b^T w
+//   L_i^{-1} = [A^{-1} + w w^T / s,  -w / s;  -w^T / s,  1 / s].
+// The owned rows of A^{-1}, w and 1/s are rounded to the format, then the owned
+// rows of L_i^{-1} are rebuilt from the rounded values by that formula in fp64.
+bool factored_rows(const Level& L, int64_t p, int fmt, std::vector<double>& out) {
+  std::vector<double> Li;
+  local_matrix(L, p, Li);
+  const int64_t ni = L.poff[p + 1] - L.poff[p], nv = ni - 1;
+  std::vector<double> T(nv * nv), w(nv);
+  for (int64_t r = 0; r < nv; ++r) {
+    w[r] = Li[r * ni + nv];
+    for (int64_t c = 0; c < nv; ++c) T[c * nv + r] = Li[r * ni + c];  // A^T
+  }
+  std::vector<int64_t> piv;
+  if (!lu_factor(T, nv, piv)) return false;
+  std::vector<double> Tt(nv * nv);  // A itself, for w = A^{-1} b
+  for (int64_t r = 0; r < nv; ++r)
+    for (int64_t c = 0; c < nv; ++c) Tt[r * nv + c] = Li[r * ni + c];
+  std::vector<int64_t> piv2;
+  if (!lu_factor(Tt, nv, piv2)) return false;
+  lu_solve(Tt, nv, piv2, w.data());
+  double s = 0.0;
+  for (int64_t r = 0; r < nv; ++r) s -= Li[nv * ni + r] * w[r];
+  if (s == 0.0) return false;
+  const double sig = fmt_round(fmt, 1.0 / s);
+  std::vector<double> rw(nv);
+  for (int64_t r = 0; r < nv; ++r) rw[r] = fmt_round(fmt, w[r]);
+  const std::vector<int>& rows = L.owned[p];
+  out.assign(rows.size() * ni, 0.0);
+  std::vector<double> z(nv);
+  for (size_t k = 0; k < rows.size(); ++k) {
+    double* o = &out[k * ni];
+    const int j = rows[k];
+    if (j == nv) {  // pressure row
+      for (int64_t c = 0; c < nv; ++c) o[c] = -rw[c] * sig;
+      o[nv] = sig;
+      continue;
+    }
+    std::fill(z.begin(), z.end(), 0.0);
+    z[j] = 1.0;
+    lu_solve(T, nv, piv, z.data());  // row j of A^{-1}
+    for (int64_t c = 0; c < nv; ++c) o[c] = fmt_round(fmt, z[c]) + rw[j] * rw[c] * sig;
+    o[nv] = -rw[j] * sig;
+  }
+  return true;
+}
+
 void quantise(Oracle& O, Level& L) {
   const int64_t np = (int64_t)L.poff.size() - 1;
   L.qinv.assign(np, {});
   L.qscale.assign(np, {});
   if (O.prec == 0) return;
+  if (O.prec >= 5) {
+    for (int64_t p = 0; p < np; ++p) {
+      factored_rows(L, p, O.prec - 4, L.qinv[p]);
+      L.qscale[p].assign(L.owned[p].size(), 1.0);
+    }
+    return;
+  }
   for (int64_t p = 0; p < np; ++p) {
     const int64_t ni = L.poff[p + 1] - L.poff[p];
     const int64_t nr = (int64_t)L.inv[p].size() / std::max<int64_t>(ni, 1);
@@ -695,9 +751,10 @@ void apply_rows(const Oracle& O, const Level& L, int64_t p, const double* rloc, 
   const std::vector<double>& R = L.inv[p];
   const int64_t nr = (int64_t)R.size() / std::max<int64_t>(ni, 1);
   for (int64_t j = 0; j < nr; ++j) {
-    if (O.prec == 0) {
+    if (O.prec == 0 || O.prec >= 5) {
+      const std::vector<double>& M = O.prec == 0 ? R : L.qinv[p];
       double s = 0.0;
-      for (int64_t k = 0; k < ni; ++k) s += R[j * ni + k] * rloc[k];
+      for (int64_t k = 0; k < ni; ++k) s += M[j * ni + k] * rloc[k];
       y[j] = s;
     } else {
       float s = 0.0f;
@@ -932,7 +989,8 @@ double orc_viscosity(void* h, const double* x) { return viscosity(((Oracle*)h)->
 
 // Builds subdomains, ownership and inverses on every level.
 // kind: 0 RAV, 1 AV, 2 MV (lexicographic), 3 MV (4^d-coloured order).
-// prec: 0 fp64, 1 fp32, 2 bf16, 3 fp8 e4m3 (stored inverse rows, fp32 accumulation).
+// prec: 0 fp64, 1 fp32, 2 bf16, 3 fp8 e4m3 (stored inverse rows, fp32 accumulation);
+// 5 fp32, 6 bf16 factored storage (rows rebuilt from rounded A^{-1}, w, 1/s; fp64 apply).
 int orc_setup_smoother(void* h, int kind, double omega, int prec) {
   Oracle& O = *(Oracle*)h;
   O.kind = kind;

@@ -514,6 +514,47 @@ def test_reduced_precision_step_error_is_bounded(prec, bound):
     assert np.linalg.norm(dq - d64) <= bound * np.linalg.norm(d64)
 
 
+@pytest.mark.parametrize("dim,N", [(2, 8), (3, 4)])
+def test_factored_storage_rebuilds_the_inverse(dim, N):
+    """Rows rebuilt from A^{-1}, w = A^{-1} b and 1/s (block inverse of the
+    saddle-point local system) equal the rows of L_i^{-1} from the LU of L_i^T
+    up to the format's rounding: a wrong sign, index or dropped rank-one term
+    would leave an O(1) error.  fp32 rounding of the stored values is exactly
+    numpy's cast, so fp32 stays near 2^-24 and bf16 near 2^-8."""
+    blobs = inputs.viscosity_blobs(3, k=6, s_max=3.0)
+    exact = O.Oracle(dim, N, 2, blobs=blobs, bc=O.BC_NOSLIP)
+    exact.setup_smoother(O.RAV, 0.5)
+    for prec, bound in ((O.F32_FACT, 2.0 ** -23), (O.BF16_FACT, 2.0 ** -7)):
+        o = O.Oracle(dim, N, 2, blobs=blobs, bc=O.BC_NOSLIP)
+        o.setup_smoother(O.RAV, 0.5, prec)
+        worst = 0.0
+        for p in range((N + 1) ** dim):
+            rows = exact.inverse(1, p)
+            q, s = o.inverse(1, p, quantised=True)
+            assert np.array_equal(s, np.ones(len(s)))
+            assert q.shape == rows.shape
+            worst = max(worst, np.abs(q - rows).max() / np.abs(rows).max())
+        assert worst <= bound, (prec, worst)
+        assert worst > 0.0  # the rounding did happen
+
+
+def test_factored_storage_step_error_is_bounded():
+    """One RAV step with fp32 / bf16 factored storage moves within the format's
+    roundoff of the fp64 step (the rows are applied in fp64)."""
+    o64 = _problem(2, 8)
+    o64.setup_smoother(O.RAV, 0.5)
+    rng = np.random.default_rng(13)
+    n = o64.sizes(1)["n"]
+    x, b = rng.standard_normal(n), rng.standard_normal(n)
+    d64 = o64.smooth(1, x, b) - x
+    for prec, bound in ((O.F32_FACT, 1e-6), (O.BF16_FACT, 2e-2)):
+        o = _problem(2, 8)
+        o.setup_smoother(O.RAV, 0.5, prec)
+        dq = o.smooth(1, x, b) - x
+        err = np.linalg.norm(dq - d64) / np.linalg.norm(d64)
+        assert 0.0 < err <= bound, (prec, err)
+
+
 # --------------------------------------------------------------------------- learned damping
 def _mlp_params(seed, scale=0.3):
     return scale * inputs.normal(seed, O.mlp_nparam())
