@@ -47,7 +47,22 @@ WORKLOADS = {
                        desc="as 2d512 with the owned rows of the patch inverses stored densely in FP64"),
     "2d512-f32": dict(dim=2, N=512, nlev=7, bc=1, forcing=1, kind=0, prec=1, omega=0.5, nu=2,
                       desc="as 2d512 with FP32-stored patch inverses (FP32 accumulation)"),
+    "3d32": dict(dim=3, N=32, nlev=4, bc=1, forcing=2, kind=0, prec=0, omega=0.5, nu=2, blobs=(20, 3.0),
+                 desc="3D Stokes Q2-Q1 32^3 unit cube, 4 levels, 20 seeded viscosity blobs (contrast <= 1e3), "
+                      "sinker forcing, no-slip, RAV V(2,2) omega 0.5, FP64 factored inverses"),
+    "3d32-bf16": dict(dim=3, N=32, nlev=4, bc=1, forcing=2, kind=0, prec=6, omega=0.5, nu=2, blobs=(20, 3.0),
+                      desc="as 3d32 with the factored inverses stored in BF16 (FP32 accumulation)"),
 }
+STORAGE = {0: "f64 factored", 1: "f32 rows", 2: "bf16 rows", 3: "fp8 rows", 4: "f64 rows", 5: "f32 factored",
+           6: "bf16 factored"}
+
+
+def make_blobs(W):
+    if "blobs" not in W:
+        return None
+    from paper_2103_10127_gb300 import inputs
+    k, s_max = W["blobs"]
+    return inputs.viscosity_blobs(inputs.BASE_SEED, k=k, s_max=s_max)
 
 
 def parse():
@@ -81,7 +96,7 @@ def patch_work(dim, N, prec, n):
     ñ_i owned rows, nodes_i velocity nodes, own_i owned velocity nodes.
       dense rows:  ñ_i n_i FMAs and stored entries per subdomain;
       factored:    d own_i nodes_i + d nodes_i + d own_i + 1 FMAs and
-                   own_i nodes_i + d nodes_i + 1 stored fp64 values.
+                   own_i nodes_i + d nodes_i + 1 stored values (fp64, fp32 or bf16).
     Vectors: r read once (8 n bytes), owned x read and written (16 ñ_i)."""
     import numpy as np
     per_n, per_o = [], []
@@ -95,9 +110,9 @@ def patch_work(dim, N, prec, n):
         nodes, own = np.einsum("i,j,k->ijk", pn, pn, pn), np.einsum("i,j,k->ijk", po, po, po)
     ni, nown = dim * nodes + 1, dim * own + 1
     vec = 8.0 * n + 16.0 * nown.sum()
-    if prec == 0:
+    if prec in (0, 5, 6):
         fma = (dim * own * nodes + dim * nodes + dim * own + 1).sum()
-        stored = 8.0 * (own * nodes + dim * nodes + 1).sum()
+        stored = {0: 8.0, 5: 4.0, 6: 2.0}[prec] * (own * nodes + dim * nodes + 1).sum()
     else:
         fma = (ni * nown).sum()
         stored = {4: 8, 1: 4, 2: 2, 3: 1}[prec] * fma
@@ -173,8 +188,8 @@ def cpu_baseline(W, cycles=1):
     `cycles` timed V-cycles on one host core."""
     import oracle as O
     import numpy as np
-    orc = O.Oracle(W["dim"], W["N"], W["nlev"], bc=W["bc"])
-    orc.setup_smoother(O.RAV, W["omega"], W["prec"] if W["prec"] in (1, 2, 3) else 0)
+    orc = O.Oracle(W["dim"], W["N"], W["nlev"], bc=W["bc"], blobs=make_blobs(W))
+    orc.setup_smoother(O.RAV, W["omega"], W["prec"] if W["prec"] in (1, 2, 3, 5, 6) else 0)
     b = orc.rhs(W["forcing"])
     x = orc.initial_guess()
     n = orc.sizes(W["nlev"] - 1)["n"]
@@ -191,8 +206,8 @@ def run_reference(args, W):
     if rank != 0:
         return
     import oracle as O
-    orc = O.Oracle(W["dim"], W["N"], W["nlev"], bc=W["bc"])
-    orc.setup_smoother(O.RAV, W["omega"], W["prec"] if W["prec"] in (1, 2, 3) else 0)
+    orc = O.Oracle(W["dim"], W["N"], W["nlev"], bc=W["bc"], blobs=make_blobs(W))
+    orc.setup_smoother(O.RAV, W["omega"], W["prec"] if W["prec"] in (1, 2, 3, 5, 6) else 0)
     b = orc.rhs(W["forcing"])
     x = orc.initial_guess()
     n = orc.sizes(W["nlev"] - 1)["n"]
@@ -228,7 +243,7 @@ def run_ours(args, W):
     lib = _capi.load()
     stream = torch.cuda.current_stream()
 
-    mg = R.Multigrid(W["dim"], W["N"], W["nlev"], bc=W["bc"])
+    mg = R.Multigrid(W["dim"], W["N"], W["nlev"], bc=W["bc"], blobs=make_blobs(W))
     sm = R.Smoother(mg, W["kind"], W["prec"], W["omega"])
     fine = W["nlev"] - 1
     n = mg.n()
@@ -304,7 +319,7 @@ def run_ours(args, W):
 
     # ---- roofline of the dominant kernel: fine-level subdomain apply ----
     flops, bytes_alg, stored = patch_work(W["dim"], W["N"], W["prec"], n)
-    if W["prec"] in (0, 4):
+    if W["prec"] in (0, 4):  # fp64 arithmetic: bound by the FP64 pipes, not HBM
         roof = {"bound": "alu", "achieved": flops / (apply_ms / 1e3) / 1e12, "peak": FP64_PEAK_TFLOPS,
                 "unit": "TFLOP/s"}
     else:
@@ -314,7 +329,7 @@ def run_ours(args, W):
     roof["frac"] = roof["achieved"] / roof["peak"]
     traffic = measured_traffic(f"rav_apply_{args.workload}")
     roof["traffic"] = traffic
-    roof["kernel"] = ("k_rav_apply_fact" if W["prec"] == 0 else "k_rav_apply") + " (fine level)"
+    roof["kernel"] = ("k_rav_apply_fact" if W["prec"] in (0, 5, 6) else "k_rav_apply") + " (fine level)"
     roof["launch_ms"] = apply_ms
     roof["launches_timed"] = apply_launches
     roof["algorithmic_bytes"] = bytes_alg
@@ -326,7 +341,7 @@ def run_ours(args, W):
            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
            "config": {"workload": W["desc"], "dofs": n, "levels": W["nlev"], "nu": [nu, nu],
                       "smoother": "RAV",
-                      "inverse_storage": ["f64 factored", "f32 rows", "bf16 rows", "fp8 rows", "f64 rows"][W["prec"]],
+                      "inverse_storage": STORAGE[W["prec"]],
                       "l2": "inputs larger than L2: each fine-level pass streams the operator "
                             f"({mg.counts(fine)['nnz'] * 12 / 1e9:.2f} GB) and the stored patch inverses "
                             f"({stored / 1e9:.2f} GB) > 129 MB L2",
@@ -364,7 +379,7 @@ def run_ours(args, W):
         out["time_to_tol"] = {"seconds": dt, "cycles": it, "tol": 1e-8, "status": rc,
                               "rho": float(hist[-1] ** (1.0 / max(it, 1)))}
 
-    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline and W["dim"] == 2:
         v, dt, nn = cpu_baseline(W)
         out["cpu_baseline"] = {"value": v, "unit": "DoF/s", "cores": 1, "kind": "oracle",
                                "sample": "1 V(2,2) cycle of the full workload on one host core after untimed "
@@ -478,7 +493,7 @@ def run_precision(args):
     n = mg.n()
     res = {}
     for name, prec in (("f64-factored", R.F64), ("f64-rows", R.F64_ROWS), ("f32", R.F32), ("bf16", R.BF16),
-                       ("fp8", R.FP8)):
+                       ("fp8", R.FP8), ("f32-factored", R.F32_FACT), ("bf16-factored", R.BF16_FACT)):
         t0 = time.perf_counter()
         sm = R.Smoother(mg, R.RAV, prec, 0.5)
         torch.cuda.synchronize()

@@ -67,9 +67,20 @@ enum rav_smoother_kind { RAV_RAV = 0, RAV_AV = 1, RAV_MV_COLOURED = 3 };
  * 1/s; see vanka_setup).  RAV_F64_ROWS: the owned rows of L_i^{-1} themselves
  * in fp64 (the storage of Sec. 4.3 as written).  RAV_F32 / RAV_BF16 / RAV_FP8:
  * the owned rows rounded to nearest-even into that format (fp8 e4m3 with an
- * fp32 scale max|row|/448 per row), applied with fp32 accumulation.  AV and MV
- * store all rows in fp64 (RAV_F64 or RAV_F64_ROWS). */
-enum rav_precision { RAV_F64 = 0, RAV_F32 = 1, RAV_BF16 = 2, RAV_FP8 = 3, RAV_F64_ROWS = 4 };
+ * fp32 scale max|row|/448 per row), applied with fp32 accumulation.
+ * RAV_F32_FACT / RAV_BF16_FACT: the factored storage of RAV_F64 with every
+ * stored value (K_i^{-1} rows, w, 1/s) rounded to nearest-even into fp32 /
+ * bf16, applied with fp32 accumulation (the correction is added to x in fp64).
+ * AV and MV store all rows in fp64 (RAV_F64 or RAV_F64_ROWS). */
+enum rav_precision {
+  RAV_F64 = 0,
+  RAV_F32 = 1,
+  RAV_BF16 = 2,
+  RAV_FP8 = 3,
+  RAV_F64_ROWS = 4,
+  RAV_F32_FACT = 5,
+  RAV_BF16_FACT = 6
+};
 
 /* Problem on the unit square (dim 2) or cube (dim 3).
  *  coords_host: dim*(N+1) finest-level vertex coordinates, axis-major, strictly
@@ -125,6 +136,17 @@ int rav_initial_guess(rav_mg* mg, double* x_dev, rav_stream stream);
  * NULL the call synchronises and stores ||r||_2 there. */
 int rav_residual(rav_mg* mg, int level, const double* x_dev, const double* b_dev, double* r_dev,
                  double* norm_host, rav_stream stream);
+
+/* Launch shape of the residual on level l (every residual of the library
+ * except rav_residual_norm_noalloc, which always uses 1): threads_per_row
+ * threads (1, 2, 4, 8, 16 or 32) share each row and add their partial sums by
+ * shuffles.  mg_setup picks the fewest that put 2^19 threads in flight.  The
+ * result differs only in the order of the fp64 additions.  Setting it waits
+ * for the device and drops the captured V-cycle graphs (recaptured on next
+ * use).  RAV_ERR_ARG for another value or level.  rav_get_residual_split
+ * returns the current value (or RAV_ERR_ARG). */
+int rav_set_residual_split(rav_mg* mg, int level, int threads_per_row);
+int rav_get_residual_split(const rav_mg* mg, int level);
 
 /* Same residual r = b - L x on level l as rav_residual, plus ||r||_2 written to
  * the caller's device scalar norm_dev, with no memory allocation of any kind

@@ -18,11 +18,12 @@ from . import _capi
 from ._capi import RavError, check
 
 RAV, AV, MV_COLOURED = 0, 1, 3
-F64, F32, BF16, FP8, F64_ROWS = 0, 1, 2, 3, 4
+F64, F32, BF16, FP8, F64_ROWS, F32_FACT, BF16_FACT = 0, 1, 2, 3, 4, 5, 6
 BC_CAVITY, BC_NOSLIP, BC_QUADRATIC = 0, 1, 2
 F_NONE, F_PSI, F_SINKER, F_QUADRATIC = 0, 1, 2, 3
 
 __all__ = ["Multigrid", "Smoother", "Batch", "RavError", "RAV", "AV", "MV_COLOURED", "F64", "F32", "BF16", "FP8", "F64_ROWS",
+           "F32_FACT", "BF16_FACT",
            "BC_CAVITY", "BC_NOSLIP", "BC_QUADRATIC", "F_NONE", "F_PSI", "F_SINKER", "F_QUADRATIC"]
 
 
@@ -114,6 +115,16 @@ class Multigrid:
         x = self.vector(0) if out is None else out
         check(_capi.load().rav_coarse_solve(self.h, _ptr(b), _ptr(x), _stream(stream)), "rav_coarse_solve")
         return x
+
+    def residual_split(self, level, threads_per_row=None):
+        """Threads per row of the residual kernel on `level`; sets it when given."""
+        lib = _capi.load()
+        if threads_per_row is not None:
+            check(lib.rav_set_residual_split(self.h, level, int(threads_per_row)), "rav_set_residual_split")
+        k = lib.rav_get_residual_split(self.h, level)
+        if k < 0:
+            raise RavError(k, "rav_get_residual_split")
+        return k
 
     def set_graphs(self, enable=True):
         """Replay V-cycles as captured CUDA graphs (default) or launch kernel by kernel."""

@@ -42,6 +42,8 @@ _SIGS = {
     "rav_initial_guess": (I32, [P, P, P]),
     "rav_residual": (I32, [P, I32, P, P, P, ctypes.POINTER(F64), P]),
     "rav_residual_norm_noalloc": (I32, [P, I32, P, P, P, P, P]),
+    "rav_set_residual_split": (I32, [P, I32, I32]),
+    "rav_get_residual_split": (I32, [P, I32]),
     "rav_restrict": (I32, [P, I32, P, P, P]),
     "rav_prolong_add": (I32, [P, I32, P, P, P]),
     "rav_coarse_solve": (I32, [P, P, P, P]),

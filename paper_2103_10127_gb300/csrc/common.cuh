@@ -74,6 +74,7 @@ struct Level {
   // sliced-ELL copy of the operator for the residual: slices of 32 rows of one
   // common length (rows grouped by length), column-major inside a slice
   int64_t nslice = 0;
+  int rsplit = 1;  // threads per row of the residual kernel (more on small levels: shorter latency chains)
   int32_t* sperm = nullptr;  // row of slot t = 32 s + lane, -1 for padding
   int64_t* sptr = nullptr;   // offset of slice s in sval/scol
   int32_t* slen = nullptr;   // row length of slice s (1 = Dirichlet identity rows)
@@ -141,10 +142,11 @@ int prof_end(rav_mg* mg, int level, int kind, cudaEvent_t start, cudaStream_t s)
 // Smoother data of one level: stored inverse rows and damping per subdomain.
 struct SmLevel {
   int64_t np = 0, units = 0;
-  bool factored = false;     // RAV fp64: rows of K^{-1} in inv, w and 1/s in ws
-  double* ws = nullptr;
+  bool factored = false;     // RAV factored (fp64 / fp32 / bf16): rows of K^{-1} in inv, w and 1/s in ws
+  void* ws = nullptr;
   void* inv = nullptr;       // RAV: packed owned rows; AV/MV: full inverses (fp64, column-major)
   float* scale = nullptr;    // fp8 row scales
+  float* r32 = nullptr;      // fp32 residual for reduced-precision storage (n entries)
   double* omega = nullptr;   // damping per subdomain
   double* corr = nullptr;    // AV corrections, n_p x n_box
   // line-search label collection (learn.cu)
@@ -166,7 +168,9 @@ struct rav_smoother {
 
 // Subdomain apply with an explicit damping array; labels; damping reset
 // (smoother.cu, learn.cu).
-int apply_with_omega(rav_smoother* sm, int level, const double* r, double* x, const double* omega, cudaStream_t s);
+// r32 (optional): r rounded to fp32; reduced-precision storage reads it (made from r when null).
+int apply_with_omega(rav_smoother* sm, int level, const double* r, double* x, const double* omega, cudaStream_t s,
+                     const float* r32 = nullptr);
 int collect_labels(rav_smoother* sm, int level, const double* r, cudaStream_t s);
 int reset_omega(rav_smoother* sm, cudaStream_t s);
 
@@ -261,8 +265,9 @@ inline int grid_for(int64_t n, int threads, int cap = 152 * 64) {
 }
 
 // Shared host routines (defined in cycle.cu).
+// r32 (optional): the residual rounded to fp32 as well, for applies that accumulate in fp32.
 int residual_impl(rav_mg* mg, int level, const double* x, const double* b, double* r, double* norm2_dev,
-                  cudaStream_t s);
+                  cudaStream_t s, float* r32 = nullptr);
 int restrict_impl(rav_mg* mg, int level, const double* rf, double* bc, cudaStream_t s);
 int prolong_impl(rav_mg* mg, int level, const double* xc, double* xf, cudaStream_t s);
 int coarse_impl(rav_mg* mg, const double* b, double* x, cudaStream_t s);

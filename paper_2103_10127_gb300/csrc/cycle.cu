@@ -20,7 +20,8 @@ __global__ void __launch_bounds__(256) k_residual_sell(int64_t nslots, const int
                                                        const int32_t* __restrict__ scol,
                                                        const double* __restrict__ sval,
                                                        const double* __restrict__ x, const double* __restrict__ b,
-                                                       double* __restrict__ r, double* __restrict__ part) {
+                                                       double* __restrict__ r, double* __restrict__ part,
+                                                       float* __restrict__ r32) {
   // one slice per warp, one slot per thread (no grid-stride loop: the hardware
   // balances the slices of different lengths across the SMs)
   double acc2 = 0.0;
@@ -56,6 +57,67 @@ __global__ void __launch_bounds__(256) k_residual_sell(int64_t nslots, const int
     if (row >= 0) {
       const double rv = len > 1 ? b[row] - (acc0 + acc1) : 0.0;
       r[row] = rv;
+      if (r32) r32[row] = (float)rv;  // round to nearest even, for fp32-accumulating applies
+      acc2 = rv * rv;
+    }
+  }
+  if (part) {
+    const double bs = block_sum(acc2);
+    if (threadIdx.x == 0) part[blockIdx.x] = bs;
+  }
+}
+
+// The same with K threads per row, for levels too small to fill the GPU with
+// one thread per row: K consecutive warps take one slice, a warp takes 32/K of
+// its rows, lane j of a row sums the slots j, j+K, ... and the K partial sums
+// meet by shuffles.  A warp touches K rows of the slice's storage, 32/K
+// consecutive values in each, so every 32-byte sector it loads is used.
+template <int K>
+__global__ void __launch_bounds__(256) k_residual_sell_split(int64_t nslots, const int32_t* __restrict__ sperm,
+                                                             const int64_t* __restrict__ sptr,
+                                                             const int32_t* __restrict__ slen,
+                                                             const int32_t* __restrict__ scol,
+                                                             const double* __restrict__ sval,
+                                                             const double* __restrict__ x,
+                                                             const double* __restrict__ b, double* __restrict__ r,
+                                                             double* __restrict__ part, float* __restrict__ r32) {
+  double acc2 = 0.0;
+  const int64_t gt = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (gt < nslots * K) {  // nslots * K is a multiple of 32: whole warps in or out
+    const int64_t w = gt >> 5;
+    const int lane = (int)(gt & 31);
+    const int64_t s = w / K;
+    const int t = (int)(w % K) * (32 / K) + lane / K;  // row within the slice
+    const int j = lane % K;
+    const int len = slen[s];
+    const int64_t base = sptr[s] + t;
+    double acc0 = 0.0, acc1 = 0.0;
+    if (len > 1) {
+      int k = j;
+      for (; k + 3 * K < len; k += 4 * K) {
+        int ck[4];
+        double vk[4], xk[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) ck[i] = scol[base + 32 * (k + i * K)];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) vk[i] = sval[base + 32 * (k + i * K)];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) xk[i] = x[ck[i]];
+        acc0 += vk[0] * xk[0];
+        acc1 += vk[1] * xk[1];
+        acc0 += vk[2] * xk[2];
+        acc1 += vk[3] * xk[3];
+      }
+      for (; k < len; k += K) acc0 += sval[base + 32 * k] * x[scol[base + 32 * k]];
+    }
+    double acc = acc0 + acc1;
+#pragma unroll
+    for (int o = K / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    const int32_t row = sperm[s * 32 + t];
+    if (j == 0 && row >= 0) {
+      const double rv = len > 1 ? b[row] - acc : 0.0;
+      r[row] = rv;
+      if (r32) r32[row] = (float)rv;
       acc2 = rv * rv;
     }
   }
@@ -237,15 +299,28 @@ __global__ void k_axpy_dev(int64_t n, const double* __restrict__ h, const double
 
 // ---------------------------------------------------------------------------
 int residual_impl(rav_mg* mg, int level, const double* x, const double* b, double* r, double* norm2_dev,
-                  cudaStream_t s) {
+                  cudaStream_t s, float* r32) {
   const Level& L = mg->lev[level];
   const int64_t nslots = L.nslice * 32;
-  const int blocks = (int)((nslots + 255) / 256);
+  const int K = L.rsplit;
+  const int blocks = (int)((nslots * K + 255) / 256);
   if (norm2_dev && blocks > mg->part_cap) return RAV_ERR_ARG;
   double* part = norm2_dev ? mg->norm_part : nullptr;
   cudaEvent_t e0;
   RAV_TRY(prof_begin(mg, level, PROF_RESIDUAL, s, &e0));
-  k_residual_sell<<<blocks, 256, 0, s>>>(nslots, L.sperm, L.sptr, L.slen, L.scol, L.sval, x, b, r, part);
+#define RAV_RES_SPLIT(KK)                                                                                         \
+  k_residual_sell_split<KK><<<blocks, 256, 0, s>>>(nslots, L.sperm, L.sptr, L.slen, L.scol, L.sval, x, b, r, part, \
+                                                   r32)
+  switch (K) {
+    case 2: RAV_RES_SPLIT(2); break;
+    case 4: RAV_RES_SPLIT(4); break;
+    case 8: RAV_RES_SPLIT(8); break;
+    case 16: RAV_RES_SPLIT(16); break;
+    case 32: RAV_RES_SPLIT(32); break;
+    default:
+      k_residual_sell<<<blocks, 256, 0, s>>>(nslots, L.sperm, L.sptr, L.slen, L.scol, L.sval, x, b, r, part, r32);
+  }
+#undef RAV_RES_SPLIT
   if (norm2_dev) k_sum_parts<<<1, 256, 0, s>>>(mg->norm_part, blocks, norm2_dev, 1);
   note_launch(norm2_dev ? 2 : 1);
   RAV_CUDA(cudaGetLastError());
@@ -468,7 +543,8 @@ extern "C" int rav_residual_norm_noalloc(rav_mg* mg, int level, const double* x,
   double* parts = nullptr;
   RAV_TRY(noalloc_parts_address(&parts));
   cudaStream_t s = S(stream);
-  k_residual_sell<<<(unsigned)blocks, 256, 0, s>>>(nslots, L.sperm, L.sptr, L.slen, L.scol, L.sval, x, b, r, parts);
+  k_residual_sell<<<(unsigned)blocks, 256, 0, s>>>(nslots, L.sperm, L.sptr, L.slen, L.scol, L.sval, x, b, r, parts,
+                                                   nullptr);
   k_sum_parts<<<1, 256, 0, s>>>(parts, (int)blocks, norm_dev, 1);
   note_launch(2);
   RAV_CUDA(cudaGetLastError());

@@ -906,11 +906,20 @@ extern "C" int mg_setup(const rav_problem* p, int n_levels, rav_stream stream, r
   for (int l = 1; l < n_levels; ++l)
     if ((rc = transfer_tables(mg, mg->lev[l - 1], mg->lev[l])) != RAV_OK) return fail(rc);
   if ((rc = coarse_inverse(mg, s)) != RAV_OK) return fail(rc);
-  // partial sums: one per residual block (256 rows) of the largest level, at
-  // least one per block of the grid-stride dot products
+  // threads per residual row: the fewest (a power of two, at most 32) that put
+  // 2^19 threads in flight, so that small levels are not one long dependent
+  // gather chain per row
+  for (int l = 0; l < n_levels; ++l) {
+    const int64_t nslots = mg->lev[l].nslice * 32;
+    int K = 1;
+    while (K < 32 && nslots * K < (int64_t(1) << 19)) K *= 2;
+    mg->lev[l].rsplit = K;
+  }
+  // partial sums: one per residual block (256 threads) of any level at any
+  // split, at least one per block of the grid-stride dot products
   mg->part_cap = 152 * 8;
   for (int l = 0; l < n_levels; ++l)
-    mg->part_cap = std::max<int>(mg->part_cap, (int)((mg->lev[l].nslice * 32 + 255) / 256));
+    mg->part_cap = std::max<int>(mg->part_cap, (int)((mg->lev[l].nslice * 32 * 32 + 255) / 256));
   if (cudaMalloc(&mg->norm_part, sizeof(double) * (mg->part_cap + 8)) != cudaSuccess) return fail(RAV_ERR_CUDA);
   if (cudaMalloc(&mg->scalar_dev, sizeof(double) * 64) != cudaSuccess) return fail(RAV_ERR_CUDA);
   if (cudaMallocHost(&mg->scalar_host, sizeof(double) * 64) != cudaSuccess) return fail(RAV_ERR_CUDA);
@@ -1008,6 +1017,21 @@ extern "C" int rav_initial_guess(rav_mg* mg, double* x, rav_stream stream) {
   else k_initial_guess<3><<<blocks, 256, 0, S(stream)>>>(g, mg->bc, x);
   RAV_CUDA(cudaGetLastError());
   return RAV_OK;
+}
+
+extern "C" int rav_set_residual_split(rav_mg* mg, int level, int threads_per_row) {
+  if (!mg || level < 0 || level >= mg->nlev) return RAV_ERR_ARG;
+  const int K = threads_per_row;
+  if (K != 1 && K != 2 && K != 4 && K != 8 && K != 16 && K != 32) return RAV_ERR_ARG;
+  cudaDeviceSynchronize();
+  drop_graphs(mg, nullptr);  // captured V-cycles hold the old launch shape
+  mg->lev[level].rsplit = K;
+  return RAV_OK;
+}
+
+extern "C" int rav_get_residual_split(const rav_mg* mg, int level) {
+  if (!mg || level < 0 || level >= mg->nlev) return RAV_ERR_ARG;
+  return mg->lev[level].rsplit;
 }
 
 extern "C" int64_t rav_kernel_launches(void) { return g_launches.load(); }

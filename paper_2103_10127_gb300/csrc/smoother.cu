@@ -340,13 +340,18 @@ __global__ void k_pack_full(const double* __restrict__ stage, int64_t first, int
 // its subdomain, forms RB owned rows of L_i^{-1} r_i and adds omega_i times
 // them to the owned DoFs of x.  Owned DoFs of different subdomains are
 // disjoint, so the writes need no atomics.
+// The residual arrives in the accumulation type: fp64 for fp64 storage, else
+// already rounded to fp32 (once per entry, not once per read).
+template <typename T>
+using AccT = typename std::conditional<std::is_same<T, double>::value, double, float>::type;
+
 template <int D, typename T>
 __global__ void __launch_bounds__(128) k_rav_apply(Geo g, const T* __restrict__ inv, const float* __restrict__ scale,
-                                                   const double* __restrict__ omega, const double* __restrict__ r,
+                                                   const double* __restrict__ omega, const AccT<T>* __restrict__ r,
                                                    double* __restrict__ x, int64_t units) {
   using B = BoxT<D>;
   constexpr int NC = B::NC, RB = B::RB, NCH = B::NCH;
-  using Acc = typename std::conditional<std::is_same<T, double>::value, double, float>::type;
+  using Acc = AccT<T>;
   __shared__ float lut[256];
   if (Fmt<T>::scaled) {
     for (int i = threadIdx.x; i < 256; i += blockDim.x) {
@@ -387,8 +392,7 @@ __global__ void __launch_bounds__(128) k_rav_apply(Geo g, const T* __restrict__ 
         const bool vv = v1 && a0 >= alo[0] && a0 <= ahi[0];
 #pragma unroll
         for (int c = 0; c < D; ++c) {
-          const double rv = vv ? r[rowoff + D * a0 + c] : 0.0;
-          const Acc ra = (Acc)rv;
+          const Acc ra = vv ? r[rowoff + D * a0 + c] : (Acc)0;
 #pragma unroll
           for (int j = 0; j < RB; ++j) acc[j] += (Acc)Fmt<T>::dec(ip[(k * RB + j) * 32], lut) * ra;
           ++k;
@@ -397,7 +401,7 @@ __global__ void __launch_bounds__(128) k_rav_apply(Geo g, const T* __restrict__ 
     }
   }
   {
-    const Acc ra = (Acc)r[g.n_u + p];
+    const Acc ra = r[g.n_u + p];
 #pragma unroll
     for (int j = 0; j < RB; ++j) acc[j] += (Acc)Fmt<T>::dec(ip[(k * RB + j) * 32], lut) * ra;
   }
@@ -426,9 +430,10 @@ __global__ void __launch_bounds__(128) k_rav_apply(Geo g, const T* __restrict__ 
 // Factored RAV storage.  Rows of K^{-1} of the owned nodes: unit u = subdomain
 // * 2^d + owned node q, element (u, n) at ((u/32) * NV + n) * 32 + u%32.
 // w (node-major, NV*D) and 1/s: per subdomain, contiguous (NV*D + 1 values).
-template <int D>
+// Stored as T (fp64, or rounded to nearest even into fp32 / bf16).
+template <int D, typename T>
 __global__ void k_pack_fact(const double* __restrict__ stage, int64_t first, int64_t count,
-                            double* __restrict__ kinv, double* __restrict__ ws) {
+                            T* __restrict__ kinv, T* __restrict__ ws) {
   using B = BoxT<D>;
   constexpr int NV = B::NV, NON = B::NON, NF = B::NF, NWS = D * NV + 1;
   const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -437,13 +442,13 @@ __global__ void k_pack_fact(const double* __restrict__ stage, int64_t first, int
     const int q = (int)(t % NON);
     const int64_t u = (first + pl) * NON + q;
     const double* src = stage + pl * NF + q * NV;
-    double* dst = kinv + ((u >> 5) * NV) * 32 + (u & 31);
-    for (int n = 0; n < NV; ++n) dst[n * 32] = src[n];
+    T* dst = kinv + ((u >> 5) * NV) * 32 + (u & 31);
+    for (int n = 0; n < NV; ++n) dst[n * 32] = Fmt<T>::enc(src[n]);
   }
   if (t < count * NWS) {
     const int64_t pl = t / NWS;
     const int e = (int)(t % NWS);
-    ws[(first + pl) * NWS + e] = stage[pl * NF + NON * NV + e];
+    ws[(first + pl) * NWS + e] = Fmt<T>::enc(stage[pl * NF + NON * NV + e]);
   }
 }
 
@@ -453,14 +458,17 @@ __global__ void k_pack_fact(const double* __restrict__ stage, int64_t first, int
 //   y_p = -tau;   x[owned] += omega_i y.
 // 2^d threads per subdomain, one per owned node; w^T r_u is split over them
 // and summed with a width-2^d shuffle.
-template <int D>
-__global__ void __launch_bounds__(128) k_rav_apply_fact(Geo g, const double* __restrict__ kinv,
-                                                        const double* __restrict__ ws,
+// Reduced storage types accumulate in fp32 and read the fp32-rounded residual;
+// fp64 storage accumulates in fp64.
+template <int D, typename T>
+__global__ void __launch_bounds__(128) k_rav_apply_fact(Geo g, const T* __restrict__ kinv,
+                                                        const T* __restrict__ ws,
                                                         const double* __restrict__ omega,
-                                                        const double* __restrict__ r, double* __restrict__ x,
+                                                        const AccT<T>* __restrict__ r, double* __restrict__ x,
                                                         int64_t units) {
   using B = BoxT<D>;
   constexpr int NV = B::NV, NON = B::NON, NWS = D * NV + 1;
+  using A = AccT<T>;
   const int64_t u = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   // warps past the last 32-unit group own no storage; the others stay whole
   // (their shuffles need every lane), idle lanes computing on subdomain 0
@@ -479,10 +487,10 @@ __global__ void __launch_bounds__(128) k_rav_apply_fact(Geo g, const double* __r
   int64_t base = 0;
   for (int d = D - 1; d >= 0; --d) base = base * M + (2 * v[d] - 2);
   base *= D;
-  const double* kp = kinv + ((u >> 5) * NV) * 32 + (u & 31);
-  double y[D];
+  const T* kp = kinv + ((u >> 5) * NV) * 32 + (u & 31);
+  A y[D];
 #pragma unroll
-  for (int c = 0; c < D; ++c) y[c] = 0.0;
+  for (int c = 0; c < D; ++c) y[c] = 0;
   int n = 0;
   for (int a2 = 0; a2 < (D == 3 ? 5 : 1); ++a2) {
     const bool v2 = D == 2 || (a2 >= alo[2] && a2 <= ahi[2]);
@@ -492,16 +500,16 @@ __global__ void __launch_bounds__(128) k_rav_apply_fact(Geo g, const double* __r
 #pragma unroll
       for (int a0 = 0; a0 < 5; ++a0) {
         const bool vv = v1 && a0 >= alo[0] && a0 <= ahi[0];
-        const double kq = kp[n * 32];
+        const A kq = (A)Fmt<T>::dec(kp[n * 32], nullptr);
 #pragma unroll
-        for (int c = 0; c < D; ++c) y[c] += kq * (vv ? r[rowoff + D * a0 + c] : 0.0);
+        for (int c = 0; c < D; ++c) y[c] += kq * (vv ? r[rowoff + D * a0 + c] : (A)0);
         ++n;
       }
     }
   }
   // partial w^T r_u over the box nodes n = q, q + 2^d, ...
-  const double* wp = ws + p * NWS;
-  double t = 0.0;
+  const T* wp = ws + p * NWS;
+  A t = 0;
   for (int i = 0; i < (NV + NON - 1) / NON; ++i) {
     const int m = q + NON * i;
     if (m < NV) {
@@ -511,14 +519,14 @@ __global__ void __launch_bounds__(128) k_rav_apply_fact(Geo g, const double* __r
       if (vv) {
         const int64_t off = base + (int64_t)D * (a0 + (int64_t)M * (a1 + (int64_t)M * a2));
 #pragma unroll
-        for (int c = 0; c < D; ++c) t += wp[m * D + c] * r[off + c];
+        for (int c = 0; c < D; ++c) t += (A)Fmt<T>::dec(wp[m * D + c], nullptr) * r[off + c];
       }
     }
   }
 #pragma unroll
   for (int o = NON / 2; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o, NON);
   if (!active) return;
-  const double tau = wp[NWS - 1] * (t - r[g.n_u + p]);
+  const A tau = (A)Fmt<T>::dec(wp[NWS - 1], nullptr) * (t - r[g.n_u + p]);
   const double om = omega[p];
   int64_t J[3] = {0, 0, 0};
   bool ok = true;
@@ -532,9 +540,9 @@ __global__ void __launch_bounds__(128) k_rav_apply_fact(Geo g, const double* __r
   if (ok) {
     const int64_t dof = D * node_id(g, J);
 #pragma unroll
-    for (int c = 0; c < D; ++c) x[dof + c] += om * (y[c] + wp[mq * D + c] * tau);
+    for (int c = 0; c < D; ++c) x[dof + c] += om * (double)(y[c] + (A)Fmt<T>::dec(wp[mq * D + c], nullptr) * tau);
   }
-  if (q == 0) x[g.n_u + p] += om * -tau;
+  if (q == 0) x[g.n_u + p] += om * (double)-tau;
 }
 
 // ---------------------------------------------------------------------------
@@ -779,8 +787,8 @@ __global__ void k_export_rav(Geo g, const T* __restrict__ inv, const float* __re
 // Owned rows of L_i^{-1} rebuilt from the factored storage:
 // (m,c | n,c') = delta_cc' K^{-1}[m,n] + w(m,c) w(n,c') / s,  (m,c | p) = -w(m,c) / s,
 // (p | n,c') = -w(n,c') / s,  (p | p) = 1 / s.
-template <int D>
-__global__ void k_export_fact(Geo g, const double* __restrict__ kinv, const double* __restrict__ ws, int64_t first,
+template <int D, typename T>
+__global__ void k_export_fact(Geo g, const T* __restrict__ kinv, const T* __restrict__ ws, int64_t first,
                               int64_t count, double* __restrict__ out) {
   using B = BoxT<D>;
   constexpr int NC = B::NC, NR = B::NR, NV = B::NV, NON = B::NON, NWS = D * NV + 1;
@@ -808,8 +816,8 @@ __global__ void k_export_fact(Geo g, const double* __restrict__ kinv, const doub
     nrow = rr;
   }
   __syncthreads();
-  const double* wp = ws + p * NWS;
-  const double sig = wp[NWS - 1];
+  const T* wp = ws + p * NWS;
+  const double sig = (double)Fmt<T>::dec(wp[NWS - 1], nullptr);
   double* o = out + blockIdx.x * (int64_t)NR * NC;
   for (int e = threadIdx.x; e < NR * NC; e += blockDim.x) {
     const int jr = e / NC, kc = e % NC;
@@ -820,18 +828,18 @@ __global__ void k_export_fact(Geo g, const double* __restrict__ kinv, const doub
       if (prow && pcol) {
         val = sig;
       } else if (prow) {
-        val = -wp[k] * sig;
+        val = -(double)Fmt<T>::dec(wp[k], nullptr) * sig;
       } else {
         const int q = j / D, c = j % D;
         const int m = (2 + (q & 1)) + 5 * (2 + ((q >> 1) & 1)) + (D == 3 ? 25 * (2 + ((q >> 2) & 1)) : 0);
-        const double wm = wp[m * D + c];
+        const double wm = (double)Fmt<T>::dec(wp[m * D + c], nullptr);
         if (pcol) {
           val = -wm * sig;
         } else {
           const int n = k / D, c2 = k % D;
           const int64_t u = p * NON + q;
-          const double kq = kinv[((u >> 5) * NV + n) * 32 + (u & 31)];
-          val = (c2 == c ? kq : 0.0) + wm * wp[k] * sig;
+          const double kq = (double)Fmt<T>::dec(kinv[((u >> 5) * NV + n) * 32 + (u & 31)], nullptr);
+          val = (c2 == c ? kq : 0.0) + wm * (double)Fmt<T>::dec(wp[k], nullptr) * sig;
         }
       }
     }
@@ -868,6 +876,10 @@ __global__ void k_fill(double* __restrict__ a, int64_t n, double v) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
     a[i] = v;
 }
+__global__ void k_f64_to_f32(const double* __restrict__ a, int64_t n, float* __restrict__ b) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n) b[i] = (float)a[i];
+}
 __global__ void k_f32_to_f64(const float* __restrict__ a, int64_t n, double* __restrict__ b) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
     b[i] = (double)a[i];
@@ -878,8 +890,17 @@ __global__ void k_f32_to_f64(const float* __restrict__ a, int64_t n, double* __r
 using namespace rav;
 
 static size_t elem_size(int prec) {
-  return (prec == RAV_F64 || prec == RAV_F64_ROWS) ? 8 : prec == RAV_F32 ? 4 : prec == RAV_BF16 ? 2 : 1;
+  switch (prec) {
+    case RAV_F64:
+    case RAV_F64_ROWS: return 8;
+    case RAV_F32:
+    case RAV_F32_FACT: return 4;
+    case RAV_BF16:
+    case RAV_BF16_FACT: return 2;
+    default: return 1;
+  }
 }
+static bool factored_prec(int prec) { return prec == RAV_F64 || prec == RAV_F32_FACT || prec == RAV_BF16_FACT; }
 
 template <int D>
 static int setup_level(rav_smoother* sm, int l, cudaStream_t s, int* err_dev) {
@@ -890,21 +911,24 @@ static int setup_level(rav_smoother* sm, int l, cudaStream_t s, int* err_dev) {
   const Geo& g = L.g;
   S_.np = g.n_p;
   const bool all = sm->kind != RAV_RAV;
-  const bool fact = sm->kind == RAV_RAV && sm->prec == RAV_F64;
+  const bool fact = sm->kind == RAV_RAV && factored_prec(sm->prec);
   S_.factored = fact;
   const int NROW = all ? B::NC : B::NR;
   const int64_t per = fact ? B::NF : (int64_t)NROW * B::NC;  // staging doubles per subdomain
   RAV_CUDA(cudaMalloc(&S_.omega, sizeof(double) * S_.np));
   k_fill<<<grid_for(S_.np, 256), 256, 0, s>>>(S_.omega, S_.np, sm->omega);
+  if (sm->kind == RAV_RAV && sm->prec != RAV_F64 && sm->prec != RAV_F64_ROWS)
+    RAV_CUDA(cudaMalloc(&S_.r32, sizeof(float) * g.n));
   if (all) {
     RAV_CUDA(cudaMalloc(&S_.inv, sizeof(double) * S_.np * B::NC * B::NC));
     if (sm->kind == RAV_AV) RAV_CUDA(cudaMalloc(&S_.corr, sizeof(double) * S_.np * B::NC));
   } else if (fact) {
     S_.units = S_.np * B::NON;
     const int64_t groups = (S_.units + 31) / 32;
-    RAV_CUDA(cudaMalloc(&S_.inv, sizeof(double) * groups * 32 * B::NV));
-    RAV_CUDA(cudaMemsetAsync(S_.inv, 0, sizeof(double) * groups * 32 * B::NV, s));
-    RAV_CUDA(cudaMalloc(&S_.ws, sizeof(double) * S_.np * (D * B::NV + 1)));
+    const size_t es = elem_size(sm->prec);
+    RAV_CUDA(cudaMalloc(&S_.inv, es * groups * 32 * B::NV));
+    RAV_CUDA(cudaMemsetAsync(S_.inv, 0, es * groups * 32 * B::NV, s));
+    RAV_CUDA(cudaMalloc(&S_.ws, es * S_.np * (D * B::NV + 1)));
   } else {
     S_.units = S_.np * B::NCH;
     const int64_t groups = (S_.units + 31) / 32;
@@ -925,7 +949,14 @@ static int setup_level(rav_smoother* sm, int l, cudaStream_t s, int* err_dev) {
     kf<<<(unsigned)cnt, threads, smem, s>>>(g, L.rp, L.va, f, cnt, stage, err_dev);
     if (fact) {
       const int64_t tot = cnt * (D * B::NV + 1);
-      k_pack_fact<D><<<(unsigned)((tot + 127) / 128), 128, 0, s>>>(stage, f, cnt, (double*)S_.inv, S_.ws);
+      const unsigned gb = (unsigned)((tot + 127) / 128);
+      if (sm->prec == RAV_F64)
+        k_pack_fact<D, double><<<gb, 128, 0, s>>>(stage, f, cnt, (double*)S_.inv, (double*)S_.ws);
+      else if (sm->prec == RAV_F32_FACT)
+        k_pack_fact<D, float><<<gb, 128, 0, s>>>(stage, f, cnt, (float*)S_.inv, (float*)S_.ws);
+      else
+        k_pack_fact<D, __nv_bfloat16>
+            <<<gb, 128, 0, s>>>(stage, f, cnt, (__nv_bfloat16*)S_.inv, (__nv_bfloat16*)S_.ws);
     } else if (all) {
       const int64_t tot = cnt * B::NC * B::NC;
       k_pack_full<D><<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(stage, f, cnt, (double*)S_.inv);
@@ -952,7 +983,7 @@ static int setup_level(rav_smoother* sm, int l, cudaStream_t s, int* err_dev) {
 extern "C" int vanka_setup(rav_mg* mg, int kind, int precision, double omega, rav_stream stream,
                            rav_smoother** out) {
   if (!mg || !out || (kind != RAV_RAV && kind != RAV_AV && kind != RAV_MV_COLOURED)) return RAV_ERR_ARG;
-  if (precision < RAV_F64 || precision > RAV_F64_ROWS) return RAV_ERR_ARG;
+  if (precision < RAV_F64 || precision > RAV_BF16_FACT) return RAV_ERR_ARG;
   if (kind != RAV_RAV && precision != RAV_F64 && precision != RAV_F64_ROWS) return RAV_ERR_ARG;
   cudaStream_t s = S(stream);
   *out = nullptr;
@@ -992,6 +1023,7 @@ extern "C" void vanka_destroy(rav_smoother* sm) {
     cudaFree(sm->lev[l].inv);
     cudaFree(sm->lev[l].ws);
     cudaFree(sm->lev[l].scale);
+    cudaFree(sm->lev[l].r32);
     cudaFree(sm->lev[l].omega);
     cudaFree(sm->lev[l].corr);
     cudaFree(sm->lev[l].lsum);
@@ -1012,12 +1044,18 @@ extern "C" int rav_set_patch_omega(rav_smoother* sm, int level, const float* w, 
   return RAV_OK;
 }
 
-int apply_with_omega(rav_smoother* sm, int level, const double* r, double* x, const double* omega, cudaStream_t s) {
+int apply_with_omega(rav_smoother* sm, int level, const double* r, double* x, const double* omega, cudaStream_t s,
+                     const float* r32) {
   rav_mg* mg = sm->mg;
   Level& L = mg->lev[level];
   SmLevel& SL = sm->lev[level];
   const Geo& g = L.g;
   const int D = g.dim;
+  if (SL.r32 && !r32) {
+    k_f64_to_f32<<<grid_for(g.n, 256), 256, 0, s>>>(r, g.n, SL.r32);
+    note_launch();
+    r32 = SL.r32;
+  }
   cudaEvent_t e0 = nullptr;
   RAV_TRY(prof_begin(mg, level, PROF_APPLY, s, &e0));
   if (sm->kind == RAV_AV) {
@@ -1033,13 +1071,30 @@ int apply_with_omega(rav_smoother* sm, int level, const double* r, double* x, co
     note_launch(2);
   } else if (SL.factored) {
     const unsigned gb = (unsigned)((SL.units + 127) / 128);
-    if (D == 2) k_rav_apply_fact<2><<<gb, 128, 0, s>>>(g, (const double*)SL.inv, SL.ws, omega, r, x, SL.units);
-    else k_rav_apply_fact<3><<<gb, 128, 0, s>>>(g, (const double*)SL.inv, SL.ws, omega, r, x, SL.units);
+#define RAV_APPLY_F(DD, T)                                                                               \
+  k_rav_apply_fact<DD, T><<<gb, 128, 0, s>>>(g, (const T*)SL.inv, (const T*)SL.ws, omega,               \
+                                             (const AccT<T>*)(std::is_same<T, double>::value ? (const void*)r \
+                                                                                             : (const void*)r32), \
+                                             x, SL.units)
+    if (sm->prec == RAV_F64) {
+      if (D == 2) RAV_APPLY_F(2, double);
+      else RAV_APPLY_F(3, double);
+    } else if (sm->prec == RAV_F32_FACT) {
+      if (D == 2) RAV_APPLY_F(2, float);
+      else RAV_APPLY_F(3, float);
+    } else {
+      if (D == 2) RAV_APPLY_F(2, __nv_bfloat16);
+      else RAV_APPLY_F(3, __nv_bfloat16);
+    }
+#undef RAV_APPLY_F
     note_launch();
   } else {
     const unsigned gb = (unsigned)((SL.units + 127) / 128);
-#define RAV_APPLY(DD, T) \
-  k_rav_apply<DD, T><<<gb, 128, 0, s>>>(g, (const T*)SL.inv, SL.scale, omega, r, x, SL.units)
+#define RAV_APPLY(DD, T)                                                                                    \
+  k_rav_apply<DD, T><<<gb, 128, 0, s>>>(g, (const T*)SL.inv, SL.scale, omega,                               \
+                                        (const AccT<T>*)(std::is_same<T, double>::value ? (const void*)r    \
+                                                                                        : (const void*)r32), \
+                                        x, SL.units)
     if (D == 2) {
       switch (sm->prec) {
         case RAV_F64_ROWS: RAV_APPLY(2, double); break;
@@ -1063,9 +1118,10 @@ int apply_with_omega(rav_smoother* sm, int level, const double* r, double* x, co
   return RAV_OK;
 }
 
-static int apply_impl(rav_smoother* sm, int level, const double* r, double* x, cudaStream_t s) {
+static int apply_impl(rav_smoother* sm, int level, const double* r, double* x, cudaStream_t s,
+                      const float* r32 = nullptr) {
   if (sm->collect) RAV_TRY(collect_labels(sm, level, r, s));
-  return apply_with_omega(sm, level, r, x, sm->lev[level].omega, s);
+  return apply_with_omega(sm, level, r, x, sm->lev[level].omega, s, r32);
 }
 
 int reset_omega(rav_smoother* sm, cudaStream_t s) {
@@ -1109,8 +1165,8 @@ int rav_smooth_impl(rav_smoother* sm, int level, double* x, const double* b, int
       RAV_TRY(apply_impl(sm, level, b, x, s));
       continue;
     }
-    RAV_TRY(residual_impl(mg, level, x, b, L.r, nullptr, s));
-    RAV_TRY(apply_impl(sm, level, L.r, x, s));
+    RAV_TRY(residual_impl(mg, level, x, b, L.r, nullptr, s, SL.r32));
+    RAV_TRY(apply_impl(sm, level, L.r, x, s, SL.r32));
     RAV_CUDA(cudaGetLastError());
   }
   return RAV_OK;
@@ -1185,8 +1241,19 @@ extern "C" int rav_get_inverse_rows(const rav_smoother* sm, int level, int64_t f
     if (g.dim == 2) k_export_full<2><<<gb, 256, 0, s>>>(g, (const double*)SL.inv, first, count, out);
     else k_export_full<3><<<gb, 256, 0, s>>>(g, (const double*)SL.inv, first, count, out);
   } else if (SL.factored) {
-    if (g.dim == 2) k_export_fact<2><<<gb, 256, 0, s>>>(g, (const double*)SL.inv, SL.ws, first, count, out);
-    else k_export_fact<3><<<gb, 256, 0, s>>>(g, (const double*)SL.inv, SL.ws, first, count, out);
+#define RAV_EXP_F(DD, T) \
+  k_export_fact<DD, T><<<gb, 256, 0, s>>>(g, (const T*)SL.inv, (const T*)SL.ws, first, count, out)
+    if (sm->prec == RAV_F64) {
+      if (g.dim == 2) RAV_EXP_F(2, double);
+      else RAV_EXP_F(3, double);
+    } else if (sm->prec == RAV_F32_FACT) {
+      if (g.dim == 2) RAV_EXP_F(2, float);
+      else RAV_EXP_F(3, float);
+    } else {
+      if (g.dim == 2) RAV_EXP_F(2, __nv_bfloat16);
+      else RAV_EXP_F(3, __nv_bfloat16);
+    }
+#undef RAV_EXP_F
   } else {
 #define RAV_EXP(DD, T) k_export_rav<DD, T><<<gb, 256, 0, s>>>(g, (const T*)SL.inv, SL.scale, first, count, out)
     if (g.dim == 2) {

@@ -49,6 +49,8 @@ def test_invalid_arguments_are_rejected_without_a_gpu():
     assert lib.vanka_setup(None, 0, 0, 0.5, None, ctypes.byref(h)) == -1
     assert lib.vcycle(None, None, None, None, 2, 2, None) == -1
     assert lib.solve(None, None, None, None, None, None, None) == -1
+    assert lib.rav_set_residual_split(None, 0, 4) == -1
+    assert lib.rav_get_residual_split(None, 0) == -1
     assert lib.rav_strerror(-3) == b"singular subdomain system"
 
 

@@ -170,6 +170,27 @@ def test_residual_transfers_and_coarse_solve_match(case):
     assert rel(got, want) <= 1e-11
 
 
+@pytest.mark.parametrize("case", [CASES[1], CASES[3]], ids=[IDS[1], IDS[3]])
+def test_residual_at_every_row_split(case):
+    """Every launch shape of the residual (1..32 threads per row) gives the
+    oracle's residual and norm.  These levels hold far fewer than 2^19 rows, so
+    the default split is the largest."""
+    mg, orc = make_pair(**case)
+    rng = np.random.default_rng(23)
+    lev = case["nlev"] - 1
+    n = mg.n(lev)
+    assert mg.residual_split(lev) == 32
+    x, b = rng.standard_normal(n), rng.standard_normal(n)
+    want = orc.residual(lev, x, b)
+    for k in (1, 2, 4, 8, 16, 32):
+        assert mg.residual_split(lev, k) == k
+        r, nrm = mg.residual(lev, gpu(x), gpu(b), norm=True)
+        assert rel(cpu(r), want) <= 1e-13, k
+        assert abs(nrm - np.linalg.norm(want)) <= 1e-13 * np.linalg.norm(want), k
+    with pytest.raises(R.RavError):
+        mg.residual_split(lev, 3)
+
+
 @pytest.mark.parametrize("case", CASES[:3], ids=IDS[:3])
 def test_vcycle_matches(case):
     mg, orc = make_pair(**case)
@@ -279,7 +300,36 @@ def test_reduced_precision_codes_and_step(case, prec):
     assert fmt_err <= {R.F32: 1e-6, R.BF16: 2e-2, R.FP8: 2e-1}[prec]
 
 
-@pytest.mark.parametrize("prec", [R.F32, R.BF16])
+@pytest.mark.parametrize("prec", [R.F32_FACT, R.BF16_FACT], ids=["f32-factored", "bf16-factored"])
+@pytest.mark.parametrize("case", [CASES[1], CASES[2]], ids=[IDS[1], IDS[2]])
+def test_factored_reduced_storage_matches_the_oracle(case, prec):
+    """Rows rebuilt from the rounded K^{-1}, w and 1/s equal the oracle's rebuild
+    (both round the same fp64 values; fp64 differences of the two factorisations
+    can move an fp32 rounding by one unit, hence the small tolerance), and one
+    step (fp32 accumulation) stays within fp32 roundoff of the oracle's step."""
+    mg, orc = make_pair(**case)
+    lev = case["nlev"] - 1
+    npatch = mg.counts(lev)["n_p"]
+    sq = R.Smoother(mg, R.RAV, prec, 0.5)
+    orc.setup_smoother(O.RAV, 0.5, {R.F32_FACT: O.F32_FACT, R.BF16_FACT: O.BF16_FACT}[prec])
+    got = cpu(sq.inverse_rows(lev, 0, npatch))
+    for p in range(npatch):
+        want, _ = orc.inverse(lev, p, quantised=True)
+        g = got[p, : want.shape[0], : want.shape[1]]
+        assert np.abs(g - want).max() <= 2.0 ** -22 * np.abs(want).max(), p
+        assert not got[p, want.shape[0]:, :].any() and not got[p, :, want.shape[1]:].any()
+    rng = np.random.default_rng(17)
+    n = mg.n(lev)
+    x, b = rng.standard_normal(n), rng.standard_normal(n)
+    xg = gpu(x)
+    sq.smooth(lev, xg, gpu(b), 1)
+    d = cpu(xg) - x
+    want = orc.smooth(lev, x, b, 1) - x
+    assert np.linalg.norm(d - want) <= 1e-5 * np.linalg.norm(want)
+
+
+@pytest.mark.parametrize("prec", [R.F32, R.BF16, R.F32_FACT, R.BF16_FACT],
+                         ids=["f32", "bf16", "f32-factored", "bf16-factored"])
 def test_reduced_precision_fgmres_reaches_fp64_tolerance(prec):
     """The fp64 outer loop absorbs the error of the stored inverses (spec form 1)."""
     mg, _ = make_pair(3, 8, 2, nblobs=10, s_max=3.0, bc=O.BC_NOSLIP)
