@@ -140,7 +140,9 @@ int rav_residual(rav_mg* mg, int level, const double* x_dev, const double* b_dev
 /* Launch shape of the residual on level l (every residual of the library
  * except rav_residual_norm_noalloc, which always uses 1): threads_per_row
  * threads (1, 2, 4, 8, 16 or 32) share each row and add their partial sums by
- * shuffles.  mg_setup picks the fewest that put 2^19 threads in flight.  The
+ * shuffles.  mg_setup times every choice on every level (5 launches each on
+ * the level's work vectors) and keeps the fewest threads within 3 % of the
+ * fastest, so the choice can differ between runs where two are that close.  The
  * result differs only in the order of the fp64 additions.  Setting it waits
  * for the device and drops the captured V-cycle graphs (recaptured on next
  * use).  RAV_ERR_ARG for another value or level.  rav_get_residual_split
@@ -197,6 +199,20 @@ int rav_coarse_solve(rav_mg* mg, const double* b_dev, double* x_dev, rav_stream 
  * RAV_ERR_SINGULAR_PATCH. */
 int vanka_setup(rav_mg* mg, int kind, int precision, double omega, rav_stream stream, rav_smoother** out);
 void vanka_destroy(rav_smoother* sm);
+
+/* Launch shape of the factored RAV apply (RAV_F64, RAV_F32_FACT,
+ * RAV_BF16_FACT) on level l: split threads per owned node (1, 2, 4 or 8 in
+ * 2-D; 1, 2 or 4 in 3-D) share the sum over the subdomain's box nodes and add
+ * their partial sums by shuffles.  vanka_setup times every choice on every
+ * level (5 applies each) and keeps the fewest threads within 3 % of the
+ * fastest.  The stored K_i^{-1} rows are grouped by 32/split
+ * subdomain nodes, so setting it regroups them on the device (synchronises
+ * the stream, allocates and frees one copy) and drops the captured V-cycle
+ * graphs of this smoother.  Results differ only in the order of additions.
+ * RAV_ERR_ARG for other values, levels or storage.  rav_get_apply_split
+ * returns the current value (or RAV_ERR_ARG). */
+int rav_set_apply_split(rav_smoother* sm, int level, int split, rav_stream stream);
+int rav_get_apply_split(const rav_smoother* sm, int level);
 
 /* Replaces the damping of level l's subdomains by w_dev[n_p(l)] (fp32, device),
  * e.g. the per-subdomain weights of a learned model. */

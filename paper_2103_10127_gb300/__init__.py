@@ -220,6 +220,16 @@ class Smoother:
         check(_capi.load().vanka_apply(self.h, level, _ptr(r), _ptr(x), _stream(stream)), "vanka_apply")
         return x
 
+    def apply_split(self, level, split=None, stream=None):
+        """Threads per owned node of the factored apply on `level`; sets it when given."""
+        lib = _capi.load()
+        if split is not None:
+            check(lib.rav_set_apply_split(self.h, level, int(split), _stream(stream)), "rav_set_apply_split")
+        k = lib.rav_get_apply_split(self.h, level)
+        if k < 0:
+            raise RavError(k, "rav_get_apply_split")
+        return k
+
     def set_omega(self, level, w, stream=None):
         w = w.to(dtype=_torch().float32).contiguous()
         check(_capi.load().rav_set_patch_omega(self.h, level, _ptr(w), _stream(stream)), "rav_set_patch_omega")

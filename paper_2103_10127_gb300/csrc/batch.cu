@@ -46,6 +46,8 @@ struct BLevel {
   double* r;
   double* xc;       // coarser level's x and b
   double* bc;
+  float* r32;       // fp32 batches: r rounded to fp32 (the apply's input), else null
+  float* bc32;      // coarser level's r32: its b rounded, written by the restriction
   const double* cinv;  // bordered coarse inverse (coarsest level only)
   int problem;
 };
@@ -106,6 +108,7 @@ __global__ void kb_residual(const BLevel* __restrict__ L, const int64_t* __restr
       for (int j = 0; j < NR; ++j) {
         const double rv = len > 1 ? lv.b[(int64_t)row * NR + j] - (a0[j] + a1[j]) : 0.0;
         lv.r[(int64_t)row * NR + j] = rv;
+        if (lv.r32) lv.r32[(int64_t)row * NR + j] = (float)rv;
         sq[j] = rv * rv;
       }
     }
@@ -143,18 +146,23 @@ __global__ void kb_apply(const BLevel* __restrict__ L, const int64_t* __restrict
   const int64_t u = (blockIdx.x - first[e]) * (int64_t)blockDim.x + threadIdx.x;
   if (u >= lv.units) return;
   const Geo& g = lv.g;
-  const double* __restrict__ r = use_b ? lv.b : lv.r;
+  // fp32 storage reads the fp32-rounded residual (r32 holds b itself after the
+  // restriction, when x entered as 0)
+  const Acc* __restrict__ r =
+      std::is_same<T, double>::value ? (const Acc*)(use_b ? lv.b : lv.r) : (const Acc*)lv.r32;
   const int64_t p = u / NCH;
   const int h = (int)(u % NCH);
   int v[3] = {0, 0, 0};
-  vertex_of(g, p, v);
+  vertex_of_t<D>(g, p, v);
   const int M = (int)g.M;
   int alo[3] = {0, 0, 0}, ahi[3] = {0, 0, 0};
+#pragma unroll
   for (int d = 0; d < D; ++d) {
     alo[d] = 2 - 2 * v[d] > 0 ? 2 - 2 * v[d] : 0;
     ahi[d] = 2 * g.N - 2 * v[d] + 2 < 4 ? 2 * g.N - 2 * v[d] + 2 : 4;
   }
   int64_t base = 0;
+#pragma unroll
   for (int d = D - 1; d >= 0; --d) base = base * M + (2 * v[d] - 2);
   base *= D;
   const T* ip = static_cast<const T*>(lv.inv) + ((u >> 5) * NC * RB) * 32 + (u & 31);
@@ -174,7 +182,7 @@ __global__ void kb_apply(const BLevel* __restrict__ L, const int64_t* __restrict
         for (int c = 0; c < D; ++c) {
           Acc ra[NR];
 #pragma unroll
-          for (int j = 0; j < NR; ++j) ra[j] = (Acc)(vv ? r[(rowoff + D * a0 + c) * NR + j] : 0.0);
+          for (int j = 0; j < NR; ++j) ra[j] = vv ? r[(rowoff + D * a0 + c) * NR + j] : (Acc)0;
 #pragma unroll
           for (int i = 0; i < RB; ++i) {
             const Acc q = (Acc)ip[(k * RB + i) * 32];
@@ -189,7 +197,7 @@ __global__ void kb_apply(const BLevel* __restrict__ L, const int64_t* __restrict
   {
     Acc ra[NR];
 #pragma unroll
-    for (int j = 0; j < NR; ++j) ra[j] = (Acc)r[(g.n_u + p) * NR + j];
+    for (int j = 0; j < NR; ++j) ra[j] = r[(g.n_u + p) * NR + j];
 #pragma unroll
     for (int i = 0; i < RB; ++i) {
       const Acc q = (Acc)ip[(k * RB + i) * 32];
@@ -206,11 +214,12 @@ __global__ void kb_apply(const BLevel* __restrict__ L, const int64_t* __restrict
       const int q = jrow / D, c = jrow % D;
       int64_t J[3] = {0, 0, 0};
       bool ok = true;
+#pragma unroll
       for (int d = 0; d < D; ++d) {
         J[d] = 2 * v[d] + ((q >> d) & 1);
         ok &= (J[d] >= 1) & (J[d] <= 2 * g.N - 1);
       }
-      if (ok) dof = D * node_id(g, J) + c;
+      if (ok) dof = D * node_id_t<D>(g, J) + c;
     } else {
       dof = g.n_u + p;
     }
@@ -270,6 +279,7 @@ __global__ void kb_restrict(const BLevel* __restrict__ L, const int64_t* __restr
 #pragma unroll
       for (int j = 0; j < NR; ++j) {
         lv.bc[((int64_t)D * t + c) * NR + j] = acc[c][j];
+        if (lv.bc32) lv.bc32[((int64_t)D * t + c) * NR + j] = (float)acc[c][j];
         lv.xc[((int64_t)D * t + c) * NR + j] = 0.0;
       }
   } else if (t < nnc + (int)gc.n_p) {
@@ -298,6 +308,7 @@ __global__ void kb_restrict(const BLevel* __restrict__ L, const int64_t* __restr
 #pragma unroll
     for (int j = 0; j < NR; ++j) {
       lv.bc[o * NR + j] = acc[j];
+      if (lv.bc32) lv.bc32[o * NR + j] = (float)acc[j];
       lv.xc[o * NR + j] = 0.0;
     }
   }
@@ -434,7 +445,7 @@ struct rav_batch {
   // host copies of every (problem, level) descriptor, finest level first per problem
   std::vector<BLevel> lv;
   std::vector<int> lv_first;  // start of problem p's levels in lv (finest level of p at lv_first[p])
-  std::vector<double*> owned;  // batch-owned vectors
+  std::vector<void*> owned;    // batch-owned vectors
   BLevel* lv_dev = nullptr;    // device mirror of lv
   int tpb_res = 256, tpb_apply = 128;
   // phases per depth d (0 = finest)
@@ -753,11 +764,20 @@ extern "C" int batch_setup(rav_mg* const* mgs, rav_smoother* const* sms, int npr
       }
       if (d > 0) { b.x = v[0]; b.b = v[1]; }
       b.r = v[2];
+      b.r32 = nullptr;
+      if (prec == RAV_F32 && d + 1 < Lp) {  // the coarsest level is solved directly
+        float* f = nullptr;
+        if (cudaMalloc(&f, sizeof(float) * n) != cudaSuccess) return fail(RAV_ERR_CUDA);
+        cudaMemset(f, 0, sizeof(float) * n);
+        bt->owned.push_back(f);
+        b.r32 = f;
+      }
     }
-    for (int d = 0; d + 1 < Lp; ++d) {
+    for (int d = 0; d < Lp; ++d) {
       BLevel& b = bt->lv[bt->lv_first[p] + d];
-      b.xc = bt->lv[bt->lv_first[p] + d + 1].x;
-      b.bc = bt->lv[bt->lv_first[p] + d + 1].b;
+      b.xc = d + 1 < Lp ? bt->lv[bt->lv_first[p] + d + 1].x : nullptr;
+      b.bc = d + 1 < Lp ? bt->lv[bt->lv_first[p] + d + 1].b : nullptr;
+      b.bc32 = d + 1 < Lp ? bt->lv[bt->lv_first[p] + d + 1].r32 : nullptr;
     }
   }
   // the finest x, b are bound per call; give them scratch for the autotuner
@@ -797,7 +817,7 @@ extern "C" void batch_destroy(rav_batch* bt) {
   cudaFree(bt->fine_res.L);
   cudaFree(bt->fine_res.first);
   cudaFree(bt->fine_res.prob);
-  for (double* p : bt->owned) cudaFree(p);
+  for (void* p : bt->owned) cudaFree(p);
   cudaFree(bt->part);
   cudaFree(bt->norms);
   if (bt->norms_h) cudaFreeHost(bt->norms_h);

@@ -27,6 +27,15 @@ struct BoxT {
 __device__ __forceinline__ void vertex_of(const Geo& g, int64_t p, int* v) {
   for (int a = 0; a < g.dim; ++a) { v[a] = (int)(p % (g.N + 1)); p /= (g.N + 1); }
 }
+// Same for a compile-time dimension, in 32-bit arithmetic (vertex counts stay
+// below 2^31), so that v stays in registers.
+template <int D>
+__device__ __forceinline__ void vertex_of_t(const Geo& g, int64_t p, int* v) {
+  unsigned q = (unsigned)p;
+  const unsigned m = (unsigned)g.N + 1;
+#pragma unroll
+  for (int a = 0; a < D; ++a) { v[a] = (int)(q % m); q /= m; }
+}
 // Box node a (per-axis offsets) of subdomain at vertex v is valid iff
 // 1 <= 2v - 2 + a <= 2N - 1 on every axis (inside, not on the boundary).
 __device__ __forceinline__ bool box_node_valid(const Geo& g, const int* v, const int* a) {

@@ -143,6 +143,7 @@ int prof_end(rav_mg* mg, int level, int kind, cudaEvent_t start, cudaStream_t s)
 struct SmLevel {
   int64_t np = 0, units = 0;
   bool factored = false;     // RAV factored (fp64 / fp32 / bf16): rows of K^{-1} in inv, w and 1/s in ws
+  int split = 1;             // factored apply: threads per owned node (storage grouped by 32/split units)
   void* ws = nullptr;
   void* inv = nullptr;       // RAV: packed owned rows; AV/MV: full inverses (fp64, column-major)
   float* scale = nullptr;    // fp8 row scales
@@ -210,6 +211,13 @@ __device__ inline bool is_dirichlet(const Geo& g, int64_t i) {
 __device__ inline int64_t node_id(const Geo& g, const int64_t* I) {
   int64_t id = 0;
   for (int a = g.dim - 1; a >= 0; --a) id = id * g.M + I[a];
+  return id;
+}
+template <int D>
+__device__ __forceinline__ int64_t node_id_t(const Geo& g, const int64_t* I) {
+  int64_t id = 0;
+#pragma unroll
+  for (int a = D - 1; a >= 0; --a) id = id * g.M + I[a];
   return id;
 }
 __device__ inline int64_t vert_id(const Geo& g, const int64_t* v) {

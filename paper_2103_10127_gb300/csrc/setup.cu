@@ -863,6 +863,40 @@ static int coarse_inverse(rav_mg* mg, cudaStream_t s) {
 
 using namespace rav;
 
+// Threads per residual row, per level: each candidate (1, 2, 4, ..., 32) is
+// timed over 5 launches on the level's work vectors (zeroed first), and the
+// fewest threads within 3 % of the fastest win.  Small levels want more
+// threads per row (short dependent gather chains), large ones fewer.
+static int tune_residual_split(rav_mg* mg, cudaStream_t s) {
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  RAV_CUDA(cudaEventCreate(&e0));
+  RAV_CUDA(cudaEventCreate(&e1));
+  int rc = RAV_OK;
+  for (int l = 0; l < mg->nlev && rc == RAV_OK; ++l) {
+    Level& L = mg->lev[l];
+    cudaMemsetAsync(L.x, 0, sizeof(double) * L.g.n, s);
+    cudaMemsetAsync(L.b, 0, sizeof(double) * L.g.n, s);
+    float t[6] = {0, 0, 0, 0, 0, 0};
+    for (int i = 0; i < 6 && rc == RAV_OK; ++i) {
+      L.rsplit = 1 << i;
+      for (int w = 0; w < 2 && rc == RAV_OK; ++w) rc = residual_impl(mg, l, L.x, L.b, L.r, nullptr, s);
+      cudaEventRecord(e0, s);
+      for (int w = 0; w < 5 && rc == RAV_OK; ++w) rc = residual_impl(mg, l, L.x, L.b, L.r, nullptr, s);
+      cudaEventRecord(e1, s);
+      if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&t[i], e0, e1) != cudaSuccess)
+        rc = RAV_ERR_CUDA;
+    }
+    float best = t[0];
+    for (int i = 1; i < 6; ++i) best = t[i] < best ? t[i] : best;
+    int pick = 0;
+    while (t[pick] > 1.03f * best) ++pick;
+    L.rsplit = 1 << pick;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  return rc;
+}
+
 extern "C" int mg_setup(const rav_problem* p, int n_levels, rav_stream stream, rav_mg** out) {
   if (!p || !out || (p->dim != 2 && p->dim != 3) || p->N < 2 || n_levels < 1 || n_levels > kMaxLevels)
     return RAV_ERR_ARG;
@@ -906,15 +940,6 @@ extern "C" int mg_setup(const rav_problem* p, int n_levels, rav_stream stream, r
   for (int l = 1; l < n_levels; ++l)
     if ((rc = transfer_tables(mg, mg->lev[l - 1], mg->lev[l])) != RAV_OK) return fail(rc);
   if ((rc = coarse_inverse(mg, s)) != RAV_OK) return fail(rc);
-  // threads per residual row: the fewest (a power of two, at most 32) that put
-  // 2^19 threads in flight, so that small levels are not one long dependent
-  // gather chain per row
-  for (int l = 0; l < n_levels; ++l) {
-    const int64_t nslots = mg->lev[l].nslice * 32;
-    int K = 1;
-    while (K < 32 && nslots * K < (int64_t(1) << 19)) K *= 2;
-    mg->lev[l].rsplit = K;
-  }
   // partial sums: one per residual block (256 threads) of any level at any
   // split, at least one per block of the grid-stride dot products
   mg->part_cap = 152 * 8;
@@ -923,6 +948,7 @@ extern "C" int mg_setup(const rav_problem* p, int n_levels, rav_stream stream, r
   if (cudaMalloc(&mg->norm_part, sizeof(double) * (mg->part_cap + 8)) != cudaSuccess) return fail(RAV_ERR_CUDA);
   if (cudaMalloc(&mg->scalar_dev, sizeof(double) * 64) != cudaSuccess) return fail(RAV_ERR_CUDA);
   if (cudaMallocHost(&mg->scalar_host, sizeof(double) * 64) != cudaSuccess) return fail(RAV_ERR_CUDA);
+  if ((rc = tune_residual_split(mg, s)) != RAV_OK) return fail(rc);
   if (cudaStreamSynchronize(s) != cudaSuccess) return fail(RAV_ERR_CUDA);
   *out = mg;
   return RAV_OK;

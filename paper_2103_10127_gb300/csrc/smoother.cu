@@ -365,7 +365,7 @@ __global__ void __launch_bounds__(128) k_rav_apply(Geo g, const T* __restrict__ 
   const int64_t p = u / NCH;
   const int h = (int)(u % NCH);
   int v[3] = {0, 0, 0};
-  vertex_of(g, p, v);
+  vertex_of_t<D>(g, p, v);
   const int M = (int)g.M;
   int alo[3] = {0, 0, 0}, ahi[3] = {0, 0, 0};
   for (int d = 0; d < 3; ++d) {
@@ -419,7 +419,7 @@ __global__ void __launch_bounds__(128) k_rav_apply(Geo g, const T* __restrict__ 
         J[d] = 2 * v[d] + ((q >> d) & 1);
         ok &= (J[d] >= 1) & (J[d] <= 2 * g.N - 1);
       }
-      if (ok) x[D * node_id(g, J) + c] += om * (double)y;
+      if (ok) x[D * node_id_t<D>(g, J) + c] += om * (double)y;
     } else {
       x[g.n_u + p] += om * (double)y;
     }
@@ -431,9 +431,11 @@ __global__ void __launch_bounds__(128) k_rav_apply(Geo g, const T* __restrict__ 
 // * 2^d + owned node q, element (u, n) at ((u/32) * NV + n) * 32 + u%32.
 // w (node-major, NV*D) and 1/s: per subdomain, contiguous (NV*D + 1 values).
 // Stored as T (fp64, or rounded to nearest even into fp32 / bf16).
+// K^{-1} rows grouped by G = 2^lg units: element (u, n) at
+// ((u / G) NV + n) G + u % G, so the G units of a warp read G consecutive values.
 template <int D, typename T>
 __global__ void k_pack_fact(const double* __restrict__ stage, int64_t first, int64_t count,
-                            T* __restrict__ kinv, T* __restrict__ ws) {
+                            T* __restrict__ kinv, T* __restrict__ ws, int lg) {
   using B = BoxT<D>;
   constexpr int NV = B::NV, NON = B::NON, NF = B::NF, NWS = D * NV + 1;
   const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -442,8 +444,9 @@ __global__ void k_pack_fact(const double* __restrict__ stage, int64_t first, int
     const int q = (int)(t % NON);
     const int64_t u = (first + pl) * NON + q;
     const double* src = stage + pl * NF + q * NV;
-    T* dst = kinv + ((u >> 5) * NV) * 32 + (u & 31);
-    for (int n = 0; n < NV; ++n) dst[n * 32] = Fmt<T>::enc(src[n]);
+    const int64_t G = int64_t(1) << lg;
+    T* dst = kinv + ((u >> lg) * NV) * G + (u & (G - 1));
+    for (int n = 0; n < NV; ++n) dst[n * G] = Fmt<T>::enc(src[n]);
   }
   if (t < count * NWS) {
     const int64_t pl = t / NWS;
@@ -452,85 +455,121 @@ __global__ void k_pack_fact(const double* __restrict__ stage, int64_t first, int
   }
 }
 
+// Moves K^{-1} rows from grouping 2^ls to grouping 2^ld (one thread per element).
+template <typename T>
+__global__ void k_regroup(const T* __restrict__ src, T* __restrict__ dst, int64_t units, int nv, int ls, int ld) {
+  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e >= units * nv) return;
+  const int64_t u = e / nv;
+  const int n = (int)(e % nv);
+  const int64_t Gs = int64_t(1) << ls, Gd = int64_t(1) << ld;
+  dst[((u >> ld) * nv + n) * Gd + (u & (Gd - 1))] = src[((u >> ls) * nv + n) * Gs + (u & (Gs - 1))];
+}
+
 // RAV apply with the factored inverse (Eq. 13 via the block form of L_i^{-1}):
 //   tau = (1/s) (w^T r_u - r_p),
 //   y(m,c) = sum_n K^{-1}[m,n] r(n,c) + w(m,c) tau   for the owned nodes m,
 //   y_p = -tau;   x[owned] += omega_i y.
-// 2^d threads per subdomain, one per owned node; w^T r_u is split over them
-// and summed with a width-2^d shuffle.
+// One unit per owned node (2^d per subdomain), S threads per unit: a warp
+// holds G = 32/S units, lane = s G + j for split s and unit j; split s sums the
+// box nodes n = s, s+S, ... and the S partial sums meet by shuffles (offsets
+// G, 2G, ...).  w^T r_u is split over all 2^d S threads of the subdomain.
+// More splits keep small levels busy; the storage grouping follows G.
 // Reduced storage types accumulate in fp32 and read the fp32-rounded residual;
 // fp64 storage accumulates in fp64.
-template <int D, typename T>
+template <int D, typename T, int S>
 __global__ void __launch_bounds__(128) k_rav_apply_fact(Geo g, const T* __restrict__ kinv,
                                                         const T* __restrict__ ws,
                                                         const double* __restrict__ omega,
                                                         const AccT<T>* __restrict__ r, double* __restrict__ x,
                                                         int64_t units) {
   using B = BoxT<D>;
-  constexpr int NV = B::NV, NON = B::NON, NWS = D * NV + 1;
+  constexpr int NV = B::NV, NON = B::NON, NWS = D * NV + 1, G = 32 / S;
+  static_assert(G % NON == 0, "a warp holds whole subdomains");
   using A = AccT<T>;
-  const int64_t u = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  // warps past the last 32-unit group own no storage; the others stay whole
-  // (their shuffles need every lane), idle lanes computing on subdomain 0
-  if (u >= ((units + 31) & ~(int64_t)31)) return;
+  const int64_t t0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int lane = (int)(t0 & 31);
+  const int sp = lane / G;
+  const int64_t u = (t0 >> 5) * G + (lane % G);
+  // warps past the last unit own no storage; the others stay whole (their
+  // shuffles need every lane), idle lanes computing on subdomain 0
+  if ((t0 >> 5) * G >= units) return;
   const bool active = u < units;
   const int64_t p = active ? u / NON : 0;
   const int q = (int)(u & (NON - 1));
   int v[3] = {0, 0, 0};
-  vertex_of(g, p, v);
+  vertex_of_t<D>(g, p, v);
   const int M = (int)g.M;
   int alo[3] = {0, 0, 0}, ahi[3] = {0, 0, 0};
+#pragma unroll
   for (int d = 0; d < D; ++d) {
     alo[d] = 2 - 2 * v[d] > 0 ? 2 - 2 * v[d] : 0;
     ahi[d] = 2 * g.N - 2 * v[d] + 2 < 4 ? 2 * g.N - 2 * v[d] + 2 : 4;
   }
   int64_t base = 0;
+#pragma unroll
   for (int d = D - 1; d >= 0; --d) base = base * M + (2 * v[d] - 2);
   base *= D;
-  const T* kp = kinv + ((u >> 5) * NV) * 32 + (u & 31);
+  const T* kp = kinv + ((u / G) * NV) * G + (u % G);
   A y[D];
 #pragma unroll
   for (int c = 0; c < D; ++c) y[c] = 0;
-  int n = 0;
-  for (int a2 = 0; a2 < (D == 3 ? 5 : 1); ++a2) {
-    const bool v2 = D == 2 || (a2 >= alo[2] && a2 <= ahi[2]);
-    for (int a1 = 0; a1 < 5; ++a1) {
-      const bool v1 = v2 && a1 >= alo[1] && a1 <= ahi[1];
-      const int64_t rowoff = base + (int64_t)D * M * (a1 + (int64_t)M * a2);
+  if (S == 1) {
+    int n = 0;
+    for (int a2 = 0; a2 < (D == 3 ? 5 : 1); ++a2) {
+      const bool v2 = D == 2 || (a2 >= alo[2] && a2 <= ahi[2]);
+      for (int a1 = 0; a1 < 5; ++a1) {
+        const bool v1 = v2 && a1 >= alo[1] && a1 <= ahi[1];
+        const int64_t rowoff = base + (int64_t)D * M * (a1 + (int64_t)M * a2);
 #pragma unroll
-      for (int a0 = 0; a0 < 5; ++a0) {
-        const bool vv = v1 && a0 >= alo[0] && a0 <= ahi[0];
-        const A kq = (A)Fmt<T>::dec(kp[n * 32], nullptr);
+        for (int a0 = 0; a0 < 5; ++a0) {
+          const bool vv = v1 && a0 >= alo[0] && a0 <= ahi[0];
+          const A kq = (A)Fmt<T>::dec(kp[n * G], nullptr);
 #pragma unroll
-        for (int c = 0; c < D; ++c) y[c] += kq * (vv ? r[rowoff + D * a0 + c] : (A)0);
-        ++n;
+          for (int c = 0; c < D; ++c) y[c] += kq * (vv ? r[rowoff + D * a0 + c] : (A)0);
+          ++n;
+        }
       }
     }
-  }
-  // partial w^T r_u over the box nodes n = q, q + 2^d, ...
-  const T* wp = ws + p * NWS;
-  A t = 0;
-  for (int i = 0; i < (NV + NON - 1) / NON; ++i) {
-    const int m = q + NON * i;
-    if (m < NV) {
-      const int a0 = m % 5, a1 = (m / 5) % 5, a2 = D == 3 ? m / 25 : 0;
+  } else {
+    for (int n = sp; n < NV; n += S) {
+      const int a0 = n % 5, a1 = (n / 5) % 5, a2 = D == 3 ? n / 25 : 0;
       bool vv = a0 >= alo[0] && a0 <= ahi[0] && a1 >= alo[1] && a1 <= ahi[1];
       if (D == 3) vv = vv && a2 >= alo[2] && a2 <= ahi[2];
-      if (vv) {
-        const int64_t off = base + (int64_t)D * (a0 + (int64_t)M * (a1 + (int64_t)M * a2));
+      const int64_t off = base + (int64_t)D * (a0 + (int64_t)M * (a1 + (int64_t)M * a2));
+      const A kq = (A)Fmt<T>::dec(kp[n * G], nullptr);
 #pragma unroll
-        for (int c = 0; c < D; ++c) t += (A)Fmt<T>::dec(wp[m * D + c], nullptr) * r[off + c];
-      }
+      for (int c = 0; c < D; ++c) y[c] += kq * (vv ? r[off + c] : (A)0);
+    }
+#pragma unroll
+    for (int o = G; o < 32; o <<= 1)
+#pragma unroll
+      for (int c = 0; c < D; ++c) y[c] += __shfl_xor_sync(0xffffffffu, y[c], o);
+  }
+  // partial w^T r_u over the box nodes n = q + 2^d s, q + 2^d s + 2^d S, ...
+  const T* wp = ws + p * NWS;
+  A t = 0;
+  for (int m = q + NON * sp; m < NV; m += NON * S) {
+    const int a0 = m % 5, a1 = (m / 5) % 5, a2 = D == 3 ? m / 25 : 0;
+    bool vv = a0 >= alo[0] && a0 <= ahi[0] && a1 >= alo[1] && a1 <= ahi[1];
+    if (D == 3) vv = vv && a2 >= alo[2] && a2 <= ahi[2];
+    if (vv) {
+      const int64_t off = base + (int64_t)D * (a0 + (int64_t)M * (a1 + (int64_t)M * a2));
+#pragma unroll
+      for (int c = 0; c < D; ++c) t += (A)Fmt<T>::dec(wp[m * D + c], nullptr) * r[off + c];
     }
   }
 #pragma unroll
-  for (int o = NON / 2; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o, NON);
-  if (!active) return;
+  for (int o = NON / 2; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+#pragma unroll
+  for (int o = G; o < 32; o <<= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+  if (!active || sp != 0) return;
   const A tau = (A)Fmt<T>::dec(wp[NWS - 1], nullptr) * (t - r[g.n_u + p]);
   const double om = omega[p];
   int64_t J[3] = {0, 0, 0};
   bool ok = true;
   int mq = 0;
+#pragma unroll
   for (int d = D - 1; d >= 0; --d) {
     const int dl = (q >> d) & 1;
     J[d] = 2 * v[d] + dl;
@@ -538,7 +577,7 @@ __global__ void __launch_bounds__(128) k_rav_apply_fact(Geo g, const T* __restri
     mq = mq * 5 + 2 + dl;
   }
   if (ok) {
-    const int64_t dof = D * node_id(g, J);
+    const int64_t dof = D * node_id_t<D>(g, J);
 #pragma unroll
     for (int c = 0; c < D; ++c) x[dof + c] += om * (double)(y[c] + (A)Fmt<T>::dec(wp[mq * D + c], nullptr) * tau);
   }
@@ -789,7 +828,7 @@ __global__ void k_export_rav(Geo g, const T* __restrict__ inv, const float* __re
 // (p | n,c') = -w(n,c') / s,  (p | p) = 1 / s.
 template <int D, typename T>
 __global__ void k_export_fact(Geo g, const T* __restrict__ kinv, const T* __restrict__ ws, int64_t first,
-                              int64_t count, double* __restrict__ out) {
+                              int64_t count, double* __restrict__ out, int lg) {
   using B = BoxT<D>;
   constexpr int NC = B::NC, NR = B::NR, NV = B::NV, NON = B::NON, NWS = D * NV + 1;
   __shared__ int colmap[NC], rowmap[NR];
@@ -838,7 +877,8 @@ __global__ void k_export_fact(Geo g, const T* __restrict__ kinv, const T* __rest
         } else {
           const int n = k / D, c2 = k % D;
           const int64_t u = p * NON + q;
-          const double kq = (double)Fmt<T>::dec(kinv[((u >> 5) * NV + n) * 32 + (u & 31)], nullptr);
+          const int64_t G = int64_t(1) << lg;
+          const double kq = (double)Fmt<T>::dec(kinv[((u >> lg) * NV + n) * G + (u & (G - 1))], nullptr);
           val = (c2 == c ? kq : 0.0) + wm * (double)Fmt<T>::dec(wp[k], nullptr) * sig;
         }
       }
@@ -900,6 +940,11 @@ static size_t elem_size(int prec) {
     default: return 1;
   }
 }
+static int ilog2(int v) {
+  int l = 0;
+  while ((1 << l) < v) ++l;
+  return l;
+}
 static bool factored_prec(int prec) { return prec == RAV_F64 || prec == RAV_F32_FACT || prec == RAV_BF16_FACT; }
 
 template <int D>
@@ -924,6 +969,7 @@ static int setup_level(rav_smoother* sm, int l, cudaStream_t s, int* err_dev) {
     if (sm->kind == RAV_AV) RAV_CUDA(cudaMalloc(&S_.corr, sizeof(double) * S_.np * B::NC));
   } else if (fact) {
     S_.units = S_.np * B::NON;
+    S_.split = 1;  // packed for one thread per owned node; vanka_setup tunes it afterwards
     const int64_t groups = (S_.units + 31) / 32;
     const size_t es = elem_size(sm->prec);
     RAV_CUDA(cudaMalloc(&S_.inv, es * groups * 32 * B::NV));
@@ -950,13 +996,14 @@ static int setup_level(rav_smoother* sm, int l, cudaStream_t s, int* err_dev) {
     if (fact) {
       const int64_t tot = cnt * (D * B::NV + 1);
       const unsigned gb = (unsigned)((tot + 127) / 128);
+      const int lg = 5 - ilog2(S_.split);
       if (sm->prec == RAV_F64)
-        k_pack_fact<D, double><<<gb, 128, 0, s>>>(stage, f, cnt, (double*)S_.inv, (double*)S_.ws);
+        k_pack_fact<D, double><<<gb, 128, 0, s>>>(stage, f, cnt, (double*)S_.inv, (double*)S_.ws, lg);
       else if (sm->prec == RAV_F32_FACT)
-        k_pack_fact<D, float><<<gb, 128, 0, s>>>(stage, f, cnt, (float*)S_.inv, (float*)S_.ws);
+        k_pack_fact<D, float><<<gb, 128, 0, s>>>(stage, f, cnt, (float*)S_.inv, (float*)S_.ws, lg);
       else
         k_pack_fact<D, __nv_bfloat16>
-            <<<gb, 128, 0, s>>>(stage, f, cnt, (__nv_bfloat16*)S_.inv, (__nv_bfloat16*)S_.ws);
+            <<<gb, 128, 0, s>>>(stage, f, cnt, (__nv_bfloat16*)S_.inv, (__nv_bfloat16*)S_.ws, lg);
     } else if (all) {
       const int64_t tot = cnt * B::NC * B::NC;
       k_pack_full<D><<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(stage, f, cnt, (double*)S_.inv);
@@ -979,6 +1026,8 @@ static int setup_level(rav_smoother* sm, int l, cudaStream_t s, int* err_dev) {
   RAV_CUDA(cudaFreeAsync(stage, s));
   return RAV_OK;
 }
+
+static int tune_apply_split(rav_smoother* sm, cudaStream_t s);
 
 extern "C" int vanka_setup(rav_mg* mg, int kind, int precision, double omega, rav_stream stream,
                            rav_smoother** out) {
@@ -1007,6 +1056,8 @@ extern "C" int vanka_setup(rav_mg* mg, int kind, int precision, double omega, ra
       rc = RAV_ERR_SINGULAR_PATCH;
   }
   cudaFree(err_dev);
+  if (rc == RAV_OK) rc = tune_apply_split(sm, s);
+  if (rc == RAV_OK && cudaStreamSynchronize(s) != cudaSuccess) rc = RAV_ERR_CUDA;
   if (rc != RAV_OK) {
     vanka_destroy(sm);
     return rc;
@@ -1036,12 +1087,108 @@ extern "C" void vanka_destroy(rav_smoother* sm) {
   delete sm;
 }
 
+static int regroup(rav_smoother* sm, int level, int split, cudaStream_t s) {
+  SmLevel& SL = sm->lev[level];
+  const int NV = sm->mg->dim == 2 ? 25 : 125;
+  if (split == SL.split) return RAV_OK;
+  const size_t es = elem_size(sm->prec);
+  const size_t bytes = es * ((SL.units + 31) / 32) * 32 * NV;
+  void* dst = nullptr;
+  RAV_CUDA(cudaMalloc(&dst, bytes));
+  RAV_CUDA(cudaMemsetAsync(dst, 0, bytes, s));
+  const int ls = 5 - ilog2(SL.split), ld = 5 - ilog2(split);
+  const unsigned gb = (unsigned)((SL.units * NV + 255) / 256);
+  if (es == 8) k_regroup<double><<<gb, 256, 0, s>>>((const double*)SL.inv, (double*)dst, SL.units, NV, ls, ld);
+  else if (es == 4) k_regroup<float><<<gb, 256, 0, s>>>((const float*)SL.inv, (float*)dst, SL.units, NV, ls, ld);
+  else k_regroup<uint16_t><<<gb, 256, 0, s>>>((const uint16_t*)SL.inv, (uint16_t*)dst, SL.units, NV, ls, ld);
+  RAV_CUDA(cudaGetLastError());
+  RAV_CUDA(cudaStreamSynchronize(s));
+  cudaFree(SL.inv);
+  SL.inv = dst;
+  SL.split = split;
+  return RAV_OK;
+}
+
+// Threads per owned node of the factored apply, per level: each candidate is
+// timed over 5 applies on the level's work vectors (zeroed first and after),
+// and the fewest threads within 3 % of the fastest win.
+static int tune_apply_split(rav_smoother* sm, cudaStream_t s) {
+  rav_mg* mg = sm->mg;
+  const int maxs = mg->dim == 2 ? 8 : 4;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  RAV_CUDA(cudaEventCreate(&e0));
+  RAV_CUDA(cudaEventCreate(&e1));
+  int rc = RAV_OK;
+  for (int l = 1; l < mg->nlev && rc == RAV_OK; ++l) {
+    SmLevel& SL = sm->lev[l];
+    Level& L = mg->lev[l];
+    if (!SL.factored) continue;
+    cudaMemsetAsync(L.r, 0, sizeof(double) * L.g.n, s);
+    if (SL.r32) cudaMemsetAsync(SL.r32, 0, sizeof(float) * L.g.n, s);
+    float t[4] = {0, 0, 0, 0};
+    int nc = 0;
+    for (int sp = 1; sp <= maxs && rc == RAV_OK; sp *= 2, ++nc) {
+      rc = regroup(sm, l, sp, s);
+      for (int w = 0; w < 2 && rc == RAV_OK; ++w) rc = apply_with_omega(sm, l, L.r, L.x, SL.omega, s, SL.r32);
+      cudaEventRecord(e0, s);
+      for (int w = 0; w < 5 && rc == RAV_OK; ++w) rc = apply_with_omega(sm, l, L.r, L.x, SL.omega, s, SL.r32);
+      cudaEventRecord(e1, s);
+      if (rc == RAV_OK &&
+          (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&t[nc], e0, e1) != cudaSuccess))
+        rc = RAV_ERR_CUDA;
+    }
+    if (rc != RAV_OK) break;
+    float best = t[0];
+    for (int i = 1; i < nc; ++i) best = t[i] < best ? t[i] : best;
+    int pick = 0;
+    while (t[pick] > 1.03f * best) ++pick;
+    rc = regroup(sm, l, 1 << pick, s);
+    cudaMemsetAsync(L.x, 0, sizeof(double) * L.g.n, s);
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  return rc;
+}
+
+extern "C" int rav_set_apply_split(rav_smoother* sm, int level, int split, rav_stream stream) {
+  if (!sm || level < 1 || level >= sm->mg->nlev) return RAV_ERR_ARG;
+  SmLevel& SL = sm->lev[level];
+  const int NON = sm->mg->dim == 2 ? 4 : 8;
+  if (!SL.factored || split < 1 || split > 32 / NON || (split & (split - 1))) return RAV_ERR_ARG;
+  if (split == SL.split) return RAV_OK;
+  cudaStream_t s = S(stream);
+  RAV_CUDA(cudaStreamSynchronize(s));
+  drop_graphs(sm->mg, sm);  // captured cycles hold the old launch shape
+  return regroup(sm, level, split, s);
+}
+
+extern "C" int rav_get_apply_split(const rav_smoother* sm, int level) {
+  if (!sm || level < 1 || level >= sm->mg->nlev) return RAV_ERR_ARG;
+  return sm->lev[level].split;
+}
+
 extern "C" int rav_set_patch_omega(rav_smoother* sm, int level, const float* w, rav_stream stream) {
   if (!sm || !w || level < 1 || level >= sm->mg->nlev) return RAV_ERR_ARG;
   const int64_t n = sm->lev[level].np;
   k_f32_to_f64<<<grid_for(n, 256), 256, 0, S(stream)>>>(w, n, sm->lev[level].omega);
   RAV_CUDA(cudaGetLastError());
   return RAV_OK;
+}
+
+template <int D, typename T>
+static void launch_fact(const SmLevel& SL, const Geo& g, unsigned gb, const double* omega, const void* r, double* x,
+                        cudaStream_t s) {
+  const T* kinv = (const T*)SL.inv;
+  const T* ws = (const T*)SL.ws;
+  const AccT<T>* rr = (const AccT<T>*)r;
+  switch (SL.split) {
+    case 1: k_rav_apply_fact<D, T, 1><<<gb, 128, 0, s>>>(g, kinv, ws, omega, rr, x, SL.units); break;
+    case 2: k_rav_apply_fact<D, T, 2><<<gb, 128, 0, s>>>(g, kinv, ws, omega, rr, x, SL.units); break;
+    case 4: k_rav_apply_fact<D, T, 4><<<gb, 128, 0, s>>>(g, kinv, ws, omega, rr, x, SL.units); break;
+    default:
+      if constexpr (D == 2) k_rav_apply_fact<D, T, 8><<<gb, 128, 0, s>>>(g, kinv, ws, omega, rr, x, SL.units);
+      break;
+  }
 }
 
 int apply_with_omega(rav_smoother* sm, int level, const double* r, double* x, const double* omega, cudaStream_t s,
@@ -1070,23 +1217,17 @@ int apply_with_omega(rav_smoother* sm, int level, const double* r, double* x, co
     }
     note_launch(2);
   } else if (SL.factored) {
-    const unsigned gb = (unsigned)((SL.units + 127) / 128);
-#define RAV_APPLY_F(DD, T)                                                                               \
-  k_rav_apply_fact<DD, T><<<gb, 128, 0, s>>>(g, (const T*)SL.inv, (const T*)SL.ws, omega,               \
-                                             (const AccT<T>*)(std::is_same<T, double>::value ? (const void*)r \
-                                                                                             : (const void*)r32), \
-                                             x, SL.units)
-    if (sm->prec == RAV_F64) {
-      if (D == 2) RAV_APPLY_F(2, double);
-      else RAV_APPLY_F(3, double);
-    } else if (sm->prec == RAV_F32_FACT) {
-      if (D == 2) RAV_APPLY_F(2, float);
-      else RAV_APPLY_F(3, float);
+    const unsigned gbs = (unsigned)((SL.units * SL.split + 127) / 128);
+    const void* rr = sm->prec == RAV_F64 ? (const void*)r : (const void*)r32;
+    if (D == 2) {
+      if (sm->prec == RAV_F64) launch_fact<2, double>(SL, g, gbs, omega, rr, x, s);
+      else if (sm->prec == RAV_F32_FACT) launch_fact<2, float>(SL, g, gbs, omega, rr, x, s);
+      else launch_fact<2, __nv_bfloat16>(SL, g, gbs, omega, rr, x, s);
     } else {
-      if (D == 2) RAV_APPLY_F(2, __nv_bfloat16);
-      else RAV_APPLY_F(3, __nv_bfloat16);
+      if (sm->prec == RAV_F64) launch_fact<3, double>(SL, g, gbs, omega, rr, x, s);
+      else if (sm->prec == RAV_F32_FACT) launch_fact<3, float>(SL, g, gbs, omega, rr, x, s);
+      else launch_fact<3, __nv_bfloat16>(SL, g, gbs, omega, rr, x, s);
     }
-#undef RAV_APPLY_F
     note_launch();
   } else {
     const unsigned gb = (unsigned)((SL.units + 127) / 128);
@@ -1241,8 +1382,9 @@ extern "C" int rav_get_inverse_rows(const rav_smoother* sm, int level, int64_t f
     if (g.dim == 2) k_export_full<2><<<gb, 256, 0, s>>>(g, (const double*)SL.inv, first, count, out);
     else k_export_full<3><<<gb, 256, 0, s>>>(g, (const double*)SL.inv, first, count, out);
   } else if (SL.factored) {
-#define RAV_EXP_F(DD, T) \
-  k_export_fact<DD, T><<<gb, 256, 0, s>>>(g, (const T*)SL.inv, (const T*)SL.ws, first, count, out)
+#define RAV_EXP_F(DD, T)                                                                              \
+  k_export_fact<DD, T><<<gb, 256, 0, s>>>(g, (const T*)SL.inv, (const T*)SL.ws, first, count, out, \
+                                          5 - ilog2(SL.split))
     if (sm->prec == RAV_F64) {
       if (g.dim == 2) RAV_EXP_F(2, double);
       else RAV_EXP_F(3, double);

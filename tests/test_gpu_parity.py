@@ -173,13 +173,12 @@ def test_residual_transfers_and_coarse_solve_match(case):
 @pytest.mark.parametrize("case", [CASES[1], CASES[3]], ids=[IDS[1], IDS[3]])
 def test_residual_at_every_row_split(case):
     """Every launch shape of the residual (1..32 threads per row) gives the
-    oracle's residual and norm.  These levels hold far fewer than 2^19 rows, so
-    the default split is the largest."""
+    oracle's residual and norm."""
     mg, orc = make_pair(**case)
     rng = np.random.default_rng(23)
     lev = case["nlev"] - 1
     n = mg.n(lev)
-    assert mg.residual_split(lev) == 32
+    assert mg.residual_split(lev) in (1, 2, 4, 8, 16, 32)
     x, b = rng.standard_normal(n), rng.standard_normal(n)
     want = orc.residual(lev, x, b)
     for k in (1, 2, 4, 8, 16, 32):
@@ -189,6 +188,39 @@ def test_residual_at_every_row_split(case):
         assert abs(nrm - np.linalg.norm(want)) <= 1e-13 * np.linalg.norm(want), k
     with pytest.raises(R.RavError):
         mg.residual_split(lev, 3)
+
+
+@pytest.mark.parametrize("prec", [R.F64, R.F32_FACT, R.BF16_FACT], ids=["f64", "f32", "bf16"])
+@pytest.mark.parametrize("case", [CASES[1], CASES[3]], ids=[IDS[1], IDS[3]])
+def test_factored_apply_at_every_split(case, prec):
+    """Every launch shape of the factored apply (1..32/2^d threads per owned
+    node, storage regrouped to match) gives the same step: the oracle's to
+    1e-12 in fp64, each other's to fp32 roundoff in the reduced formats; the
+    stored rows read back the same after regrouping."""
+    mg, orc = make_pair(**case)
+    lev = case["nlev"] - 1
+    sm = R.Smoother(mg, R.RAV, prec, 0.5)
+    assert sm.apply_split(lev) in (1, 2, 4, 8)
+    rng = np.random.default_rng(29)
+    n = mg.n(lev)
+    x, b = rng.standard_normal(n), rng.standard_normal(n)
+    if prec == R.F64:
+        orc.setup_smoother(O.RAV, 0.5)
+    else:
+        orc.setup_smoother(O.RAV, 0.5, {R.F32_FACT: O.F32_FACT, R.BF16_FACT: O.BF16_FACT}[prec])
+    want = orc.smooth(lev, x, b, 1) - x
+    npatch = mg.counts(lev)["n_p"]
+    rows0 = cpu(sm.inverse_rows(lev, 0, npatch))
+    for split in ((1, 2, 4, 8) if case["dim"] == 2 else (1, 2, 4)):
+        assert sm.apply_split(lev, split) == split
+        xg = gpu(x)
+        sm.smooth(lev, xg, gpu(b), 1)
+        got = cpu(xg) - x
+        tol = 1e-12 if prec == R.F64 else 1e-5
+        assert np.linalg.norm(got - want) <= tol * np.linalg.norm(want), split
+        assert np.array_equal(cpu(sm.inverse_rows(lev, 0, npatch)), rows0), split
+    with pytest.raises(R.RavError):
+        sm.apply_split(lev, 3)
 
 
 @pytest.mark.parametrize("case", CASES[:3], ids=IDS[:3])
