@@ -71,6 +71,8 @@ def parse():
     ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-single", action="store_true",
+                    help="2d-batch: skip timing the single-problem FP64 form on the same problems")
     ap.add_argument("--workload", default="2d512",
                     choices=sorted(WORKLOADS) + ["2d-batch", "3d-precision", "3d-learned"])
     ap.add_argument("--nprob", type=int, default=256, help="problems of the 2d-batch workload")
@@ -454,12 +456,45 @@ def run_batch(args):
     ms = e0.elapsed_time(e1)
     clocks = clocks_stop(clk, 0)
     launches = lib.rav_kernel_launches() - launches0
+    # per-depth, per-kernel-class breakdown (separate untimed pass, events around every phase)
+    kb = max(2, args.steps // 2)
+    bt.profile(True)
+    for _ in range(kb):
+        bt.vcycle(xs, bs, 2, 2)
+    torch.cuda.synchronize()
+    breakdown = {}
+    names = ["apply", "residual", "restrict", "prolong", "coarse"]
+    for d in range(int(max(inputs.levels_for(int(N)) for N in sizes))):
+        row = {}
+        for k, nm in enumerate(names):
+            c, t = bt.profile_read(d, k)
+            if c:
+                row[nm] = round(t / kb, 3)
+        if row:
+            breakdown[f"depth {d}"] = row
+    bt.profile(False)
     for x, xi in zip(xs, x_init):
         x.copy_(xi)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     it, ratios, rc = bt.solve(xs, bs, tol=1e-8, maxit=100, raise_on_error=False)
     tsolve = time.perf_counter() - t0
+    # the plain FP64 form on the same problems: one single-problem V(2,2) cycle
+    # (FP64 factored inverses, captured graph) per problem and right-hand side
+    single_ms = 0.0
+    if not args.no_single:
+        for mg in mgs:
+            sm64 = R.Smoother(mg, R.RAV, R.F64, 0.5)
+            x1, b1 = xs[0].new_zeros(mg.n()), mg.rhs(R.F_NONE)
+            mg.vcycle(sm64, x1, b1, 2, 2)
+            torch.cuda.synchronize()
+            e0.record(stream)
+            for _ in range(nrhs):
+                mg.vcycle(sm64, x1, b1, 2, 2)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            single_ms += e0.elapsed_time(e1)
+            del sm64
     out = {"metric": "V-cycle DoFs/s", "value": dofs * nrhs * args.steps / (ms / 1e3), "unit": "DoF/s",
            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
@@ -468,7 +503,11 @@ def run_batch(args):
                       "problems": nprob, "rhs": nrhs, "dofs_total": dofs, "sizes_min_max": [int(sizes.min()),
                                                                                             int(sizes.max())],
                       "tuning": bt.tuning(), "setup_s": setup_s},
-           "gpu_launches": int(launches), "clocks": clocks,
+           "gpu_launches": int(launches), "clocks": clocks, "breakdown_ms_per_cycle": breakdown,
+           "single_problem_fp64": None if args.no_single else {
+               "ms_per_cycle_all": single_ms, "value": dofs * nrhs / (single_ms / 1e3), "unit": "DoF/s",
+               "note": "one-problem, one-RHS V(2,2) cycles with FP64 factored inverses, graphs, summed over "
+                       "every problem and RHS"},
            "time_to_tol": {"seconds": tsolve, "max_cycles": int(it.max()), "min_cycles": int(it.min()),
                            "status": rc, "tol": 1e-8}}
     print(json.dumps(out), flush=True)

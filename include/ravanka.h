@@ -340,7 +340,8 @@ int rav_reset_omega(rav_smoother* sm, rav_stream stream);
  * phase of the V-cycle is one kernel launch over all problems; the cycle is
  * captured into a CUDA graph on first use and replayed.  Per right-hand side
  * the result equals the single-problem vcycle() with the same smoother bit for
- * bit.  batch_setup times candidate launch shapes on the batch's own data and
+ * bit when that hierarchy's residual uses one thread per row
+ * (rav_set_residual_split(mg, l, 1) on every level).  batch_setup times candidate launch shapes on the batch's own data and
  * keeps the fastest (batch_get_tuning reports them).  The batch does not own
  * the hierarchies or smoothers; destroy it first. */
 typedef struct rav_batch rav_batch;
@@ -349,6 +350,15 @@ int batch_setup(rav_mg* const* mgs, rav_smoother* const* sms, int nprob, int nrh
 void batch_destroy(rav_batch* bt);
 /* out[0] = threads per block of the residual kernel, out[1] = of the apply kernel. */
 int batch_get_tuning(const rav_batch* bt, int out[2]);
+/* Timing hook of the batch, with the kernel classes of rav_profile_enable.
+ * While enabled (on != 0) batch_vcycle and solve_batched launch phase by phase
+ * instead of replaying the graph, and every phase launch is bracketed by CUDA
+ * events on the launching stream.  Enabling (or disabling) waits for the
+ * device and clears the totals.  batch_profile_read waits for the recorded
+ * events and returns, for (depth below the finest grid, class), the number of
+ * bracketed phase launches and their summed duration in ms. */
+int batch_profile_enable(rav_batch* bt, int on);
+int batch_profile_read(rav_batch* bt, int depth, int kind, int64_t* launches, double* total_ms);
 /* One V(nu_pre, nu_post) cycle of every problem and right-hand side; x_dev[p]
  * updated in place, b_dev[p] read.  Synchronises the stream before rebinding
  * changed vector pointers. */

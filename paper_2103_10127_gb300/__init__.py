@@ -175,6 +175,18 @@ class Batch:
         check(_capi.load().batch_get_tuning(self.h, out), "batch_get_tuning")
         return {"residual_threads": out[0], "apply_threads": out[1]}
 
+    def profile(self, on=True):
+        """Phase-by-phase CUDA-event timing of batched cycles (batch_profile_enable)."""
+        check(_capi.load().batch_profile_enable(self.h, int(on)), "batch_profile_enable")
+
+    def profile_read(self, depth, kind):
+        """(launches, total ms) of kernel class `kind` at `depth` below the finest grid."""
+        n = ctypes.c_int64(0)
+        ms = ctypes.c_double(0.0)
+        check(_capi.load().batch_profile_read(self.h, depth, kind, ctypes.byref(n), ctypes.byref(ms)),
+              "batch_profile_read")
+        return n.value, ms.value
+
     @staticmethod
     def _ptrs(ts):
         return (ctypes.c_void_p * len(ts))(*[_ptr(t).value for t in ts])

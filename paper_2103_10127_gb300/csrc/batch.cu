@@ -134,6 +134,34 @@ __global__ void kb_norm_final(const int64_t* __restrict__ first, const int* __re
   norms[prob[e] * NR + j] = sqrt(s);
 }
 
+// NR consecutive residual values of one row (RHS-interleaved, so the row's
+// values are contiguous and 4*NR- or 8*NR-byte aligned) in as few loads as the
+// alignment allows.
+template <typename A, int NR>
+__device__ __forceinline__ void load_row(const A* __restrict__ p, A* out) {
+  if constexpr (std::is_same<A, float>::value && NR % 4 == 0) {
+#pragma unroll
+    for (int j = 0; j < NR; j += 4) {
+      const float4 v = *reinterpret_cast<const float4*>(p + j);
+      out[j] = v.x;
+      out[j + 1] = v.y;
+      out[j + 2] = v.z;
+      out[j + 3] = v.w;
+    }
+  } else if constexpr (NR % 2 == 0) {
+    using V2 = typename std::conditional<std::is_same<A, float>::value, float2, double2>::type;
+#pragma unroll
+    for (int j = 0; j < NR; j += 2) {
+      const V2 v = *reinterpret_cast<const V2*>(p + j);
+      out[j] = v.x;
+      out[j + 1] = v.y;
+    }
+  } else {
+#pragma unroll
+    for (int j = 0; j < NR; ++j) out[j] = p[j];
+  }
+}
+
 // RAV apply with dense owned rows, all right-hand sides at once (same order
 // per RHS as k_rav_apply).  use_b: the residual is b (x entered as 0).
 template <int D, typename T, int NR>
@@ -181,8 +209,12 @@ __global__ void kb_apply(const BLevel* __restrict__ L, const int64_t* __restrict
         const bool vv = v1 && a0 >= alo[0] && a0 <= ahi[0];
         for (int c = 0; c < D; ++c) {
           Acc ra[NR];
+          if (vv) {
+            load_row<Acc, NR>(r + (rowoff + D * a0 + c) * NR, ra);
+          } else {
 #pragma unroll
-          for (int j = 0; j < NR; ++j) ra[j] = vv ? r[(rowoff + D * a0 + c) * NR + j] : (Acc)0;
+            for (int j = 0; j < NR; ++j) ra[j] = 0;
+          }
 #pragma unroll
           for (int i = 0; i < RB; ++i) {
             const Acc q = (Acc)ip[(k * RB + i) * 32];
@@ -196,8 +228,7 @@ __global__ void kb_apply(const BLevel* __restrict__ L, const int64_t* __restrict
   }
   {
     Acc ra[NR];
-#pragma unroll
-    for (int j = 0; j < NR; ++j) ra[j] = r[(g.n_u + p) * NR + j];
+    load_row<Acc, NR>(r + (g.n_u + p) * NR, ra);
 #pragma unroll
     for (int i = 0; i < RB; ++i) {
       const Acc q = (Acc)ip[(k * RB + i) * 32];
@@ -459,7 +490,47 @@ struct rav_batch {
   int graph_nu1 = -1, graph_nu2 = -1;
   int64_t graph_launches = 0;
   std::vector<const double*> cur_x, cur_b;
+  // timing hook: events around every phase launch while enabled (cycles then
+  // run kernel by kernel instead of from the graph)
+  bool prof = false;
+  struct Ev {
+    int depth, kind;
+    cudaEvent_t a, b;
+  };
+  std::vector<Ev> evs;
+  size_t ev_used = 0;
+  double prof_ms[kMaxLevels][5] = {};
+  int64_t prof_cnt[kMaxLevels][5] = {};
 };
+
+static int bprof_begin(rav_batch* bt, int depth, int kind, cudaStream_t s) {
+  if (!bt->prof) return -1;
+  if (bt->ev_used == bt->evs.size()) {
+    rav_batch::Ev e{0, 0, nullptr, nullptr};
+    if (cudaEventCreate(&e.a) != cudaSuccess || cudaEventCreate(&e.b) != cudaSuccess) return -1;
+    bt->evs.push_back(e);
+  }
+  rav_batch::Ev& e = bt->evs[bt->ev_used];
+  e.depth = depth;
+  e.kind = kind;
+  cudaEventRecord(e.a, s);
+  return (int)bt->ev_used++;
+}
+static void bprof_end(rav_batch* bt, int i, cudaStream_t s) {
+  if (i >= 0) cudaEventRecord(bt->evs[i].b, s);
+}
+static int bprof_collect(rav_batch* bt) {
+  for (size_t i = 0; i < bt->ev_used; ++i) {
+    rav_batch::Ev& e = bt->evs[i];
+    float ms = 0.0f;
+    RAV_CUDA(cudaEventSynchronize(e.b));
+    RAV_CUDA(cudaEventElapsedTime(&ms, e.a, e.b));
+    bt->prof_ms[e.depth][e.kind] += ms;
+    bt->prof_cnt[e.depth][e.kind] += 1;
+  }
+  bt->ev_used = 0;
+  return RAV_OK;
+}
 
 static int level_count(const rav_batch* bt, int p) {
   return bt->mgs[p]->nlev;
@@ -541,33 +612,50 @@ static void launch_apply(const rav_batch* bt, const BPhase& ph, int use_b, cudaS
 template <int D, int NR>
 static int batch_cycle(rav_batch* bt, int nu1, int nu2, cudaStream_t s) {
   const int Dm = bt->depth;
+  int ev;
+  auto res = [&](int d) {
+    ev = bprof_begin(bt, d, PROF_RESIDUAL, s);
+    launch_res<NR>(bt->res_smooth[d], nullptr, s);
+    bprof_end(bt, ev, s);
+  };
+  auto apply = [&](int d, int use_b) {
+    ev = bprof_begin(bt, d, PROF_APPLY, s);
+    launch_apply<D, NR>(bt, bt->apply[d], use_b, s);
+    bprof_end(bt, ev, s);
+  };
   // down
   for (int d = 0; d < Dm; ++d) {
     for (int it = 0; it < nu1; ++it) {
       if (it == 0 && d > 0) {
-        launch_apply<D, NR>(bt, bt->apply[d], 1, s);
+        apply(d, 1);
       } else {
-        launch_res<NR>(bt->res_smooth[d], nullptr, s);
-        launch_apply<D, NR>(bt, bt->apply[d], 0, s);
+        res(d);
+        apply(d, 0);
       }
     }
-    launch_res<NR>(bt->res_smooth[d], nullptr, s);
+    res(d);
     const BPhase& rp = bt->restrict_[d];
+    ev = bprof_begin(bt, d, PROF_RESTRICT, s);
     if (rp.ne) kb_restrict<D, NR><<<(unsigned)rp.blocks, rp.threads, 0, s>>>(rp.L, rp.first, rp.ne);
+    bprof_end(bt, ev, s);
     const BPhase& cm = bt->coarse_mask[d + 1];
     if (cm.ne) {
+      ev = bprof_begin(bt, d + 1, PROF_COARSE, s);
       kb_coarse_mask<NR><<<(unsigned)cm.blocks, cm.threads, 0, s>>>(cm.L, cm.first, cm.ne);
       const BPhase& cg = bt->coarse_gemv[d + 1];
       kb_coarse_gemv<NR><<<(unsigned)cg.blocks, cg.threads, 0, s>>>(cg.L, cg.first, cg.ne);
+      bprof_end(bt, ev, s);
     }
   }
   // up
   for (int d = Dm - 1; d >= 0; --d) {
     const BPhase& pp = bt->prolong[d];
+    ev = bprof_begin(bt, d, PROF_PROLONG, s);
     if (pp.ne) kb_prolong<D, NR><<<(unsigned)pp.blocks, pp.threads, 0, s>>>(pp.L, pp.first, pp.ne);
+    bprof_end(bt, ev, s);
     for (int it = 0; it < nu2; ++it) {
-      launch_res<NR>(bt->res_smooth[d], nullptr, s);
-      launch_apply<D, NR>(bt, bt->apply[d], 0, s);
+      res(d);
+      apply(d, 0);
     }
   }
   RAV_CUDA(cudaGetLastError());
@@ -808,6 +896,10 @@ extern "C" void batch_destroy(rav_batch* bt) {
   cudaDeviceSynchronize();
   if (bt->graph) cudaGraphExecDestroy(bt->graph);
   if (bt->cap) cudaStreamDestroy(bt->cap);
+  for (auto& e : bt->evs) {
+    cudaEventDestroy(e.a);
+    cudaEventDestroy(e.b);
+  }
   for (auto* v : {&bt->res_smooth, &bt->apply, &bt->restrict_, &bt->prolong, &bt->coarse_mask, &bt->coarse_gemv})
     for (auto& ph : *v) {
       cudaFree(ph.L);
@@ -833,6 +925,12 @@ extern "C" int batch_get_tuning(const rav_batch* bt, int out[2]) {
 
 // One batched V-cycle, captured into a graph on first use and replayed.
 static int batch_vcycle_impl(rav_batch* bt, int nu1, int nu2, cudaStream_t s) {
+  if (bt->prof) {  // kernel by kernel, events around each phase
+    const int64_t l0 = rav_kernel_launches();
+    RAV_TRY(batch_cycle_any(bt, nu1, nu2, s));
+    (void)l0;
+    return RAV_OK;
+  }
   if (!bt->graph || bt->graph_nu1 != nu1 || bt->graph_nu2 != nu2) {
     if (bt->graph) {
       cudaGraphExecDestroy(bt->graph);
@@ -860,6 +958,28 @@ static int batch_vcycle_impl(rav_batch* bt, int nu1, int nu2, cudaStream_t s) {
   }
   RAV_CUDA(cudaGraphLaunch(bt->graph, s));
   note_launch((int)bt->graph_launches);
+  return RAV_OK;
+}
+
+extern "C" int batch_profile_enable(rav_batch* bt, int on) {
+  if (!bt) return RAV_ERR_ARG;
+  RAV_CUDA(cudaDeviceSynchronize());
+  bt->prof = on != 0;
+  bt->ev_used = 0;
+  for (int d = 0; d < kMaxLevels; ++d)
+    for (int k = 0; k < 5; ++k) {
+      bt->prof_ms[d][k] = 0.0;
+      bt->prof_cnt[d][k] = 0;
+    }
+  return RAV_OK;
+}
+
+extern "C" int batch_profile_read(rav_batch* bt, int depth, int kind, int64_t* launches, double* total_ms) {
+  if (!bt || depth < 0 || depth >= kMaxLevels || kind < 0 || kind > 4 || !launches || !total_ms)
+    return RAV_ERR_ARG;
+  RAV_TRY(bprof_collect(bt));
+  *launches = bt->prof_cnt[depth][kind];
+  *total_ms = bt->prof_ms[depth][kind];
   return RAV_OK;
 }
 
