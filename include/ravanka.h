@@ -133,7 +133,13 @@ int rav_initial_guess(rav_mg* mg, double* x_dev, rav_stream stream);
 
 /* r = b - L x on free rows, r = 0 on Dirichlet rows (the residual of Eq. 10), on
  * level l; all three vectors have that level's n entries.  If norm_host is not
- * NULL the call synchronises and stores ||r||_2 there. */
+ * NULL the call synchronises and stores ||r||_2 there.  Every residual of the
+ * library reads a sliced-ELL copy of L that leaves out entries of magnitude at
+ * most 2^-46 of the largest in their row: on these grids those are the
+ * quadrature roundoff of couplings that cancel exactly (a quarter of the
+ * stored entries, within a few ulps of zero), genuine couplings staying above
+ * 1e-7 of their row; the effect on r is below the rounding of its fp64 sums.
+ * rav_get_csr returns L as assembled, those entries included. */
 int rav_residual(rav_mg* mg, int level, const double* x_dev, const double* b_dev, double* r_dev,
                  double* norm_host, rav_stream stream);
 

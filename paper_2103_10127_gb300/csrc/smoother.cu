@@ -477,8 +477,16 @@ __global__ void k_regroup(const T* __restrict__ src, T* __restrict__ dst, int64_
 // More splits keep small levels busy; the storage grouping follows G.
 // Reduced storage types accumulate in fp32 and read the fp32-rounded residual;
 // fp64 storage accumulates in fp64.
+// Register caps (blocks of 128 per SM): 3-D reduced storage at 32 registers,
+// so that a 32^3 level's units fit in one wave; the others at what they need
+// without spilling (about 40 in 2-D, 48 in 3-D fp64).
+template <int D, typename T>
+constexpr int fact_min_blocks() {
+  return D == 3 ? (std::is_same<T, double>::value ? 10 : 16) : 12;
+}
+
 template <int D, typename T, int S>
-__global__ void __launch_bounds__(128) k_rav_apply_fact(Geo g, const T* __restrict__ kinv,
+__global__ void __launch_bounds__(128, fact_min_blocks<D, T>()) k_rav_apply_fact(Geo g, const T* __restrict__ kinv,
                                                         const T* __restrict__ ws,
                                                         const double* __restrict__ omega,
                                                         const AccT<T>* __restrict__ r, double* __restrict__ x,
