@@ -62,6 +62,34 @@ __device__ __forceinline__ int find_entry(const int64_t* __restrict__ first, int
   return lo;
 }
 
+// NR consecutive residual values of one row (RHS-interleaved, so the row's
+// values are contiguous and 4*NR- or 8*NR-byte aligned) in as few loads as the
+// alignment allows.
+template <typename A, int NR>
+__device__ __forceinline__ void load_row(const A* __restrict__ p, A* out) {
+  if constexpr (std::is_same<A, float>::value && NR % 4 == 0) {
+#pragma unroll
+    for (int j = 0; j < NR; j += 4) {
+      const float4 v = *reinterpret_cast<const float4*>(p + j);
+      out[j] = v.x;
+      out[j + 1] = v.y;
+      out[j + 2] = v.z;
+      out[j + 3] = v.w;
+    }
+  } else if constexpr (NR % 2 == 0) {
+    using V2 = typename std::conditional<std::is_same<A, float>::value, float2, double2>::type;
+#pragma unroll
+    for (int j = 0; j < NR; j += 2) {
+      const V2 v = *reinterpret_cast<const V2*>(p + j);
+      out[j] = v.x;
+      out[j + 1] = v.y;
+    }
+  } else {
+#pragma unroll
+    for (int j = 0; j < NR; ++j) out[j] = p[j];
+  }
+}
+
 // r = b - L x for every right-hand side (same addition order per RHS as
 // k_residual_sell), with per-block partial sums of r^2 per RHS when part != 0.
 template <int NR>
@@ -87,9 +115,10 @@ __global__ void kb_residual(const BLevel* __restrict__ L, const int64_t* __restr
       const double* v = lv.sval + base;
       const int full = len & ~7;
       for (int k = 0; k < full; k += 2) {
-        const double v0 = v[32 * k], v1 = v[32 * (k + 1)];
-        const double* x0 = lv.x + (int64_t)c[32 * k] * NR;
-        const double* x1 = lv.x + (int64_t)c[32 * (k + 1)] * NR;
+        const double v0 = ld_stream(v + 32 * k), v1 = ld_stream(v + 32 * (k + 1));
+        double x0[NR], x1[NR];
+        load_row<double, NR>(lv.x + (int64_t)ld_stream(c + 32 * k) * NR, x0);
+        load_row<double, NR>(lv.x + (int64_t)ld_stream(c + 32 * (k + 1)) * NR, x1);
 #pragma unroll
         for (int j = 0; j < NR; ++j) {
           a0[j] += v0 * x0[j];
@@ -97,8 +126,9 @@ __global__ void kb_residual(const BLevel* __restrict__ L, const int64_t* __restr
         }
       }
       for (int k = full; k < len; ++k) {
-        const double v0 = v[32 * k];
-        const double* x0 = lv.x + (int64_t)c[32 * k] * NR;
+        const double v0 = ld_stream(v + 32 * k);
+        double x0[NR];
+        load_row<double, NR>(lv.x + (int64_t)ld_stream(c + 32 * k) * NR, x0);
 #pragma unroll
         for (int j = 0; j < NR; ++j) a0[j] += v0 * x0[j];
       }
@@ -132,34 +162,6 @@ __global__ void kb_norm_final(const int64_t* __restrict__ first, const int* __re
   double s = 0.0;
   for (int64_t blk = first[e]; blk < first[e + 1]; ++blk) s += part[blk * NR + j];
   norms[prob[e] * NR + j] = sqrt(s);
-}
-
-// NR consecutive residual values of one row (RHS-interleaved, so the row's
-// values are contiguous and 4*NR- or 8*NR-byte aligned) in as few loads as the
-// alignment allows.
-template <typename A, int NR>
-__device__ __forceinline__ void load_row(const A* __restrict__ p, A* out) {
-  if constexpr (std::is_same<A, float>::value && NR % 4 == 0) {
-#pragma unroll
-    for (int j = 0; j < NR; j += 4) {
-      const float4 v = *reinterpret_cast<const float4*>(p + j);
-      out[j] = v.x;
-      out[j + 1] = v.y;
-      out[j + 2] = v.z;
-      out[j + 3] = v.w;
-    }
-  } else if constexpr (NR % 2 == 0) {
-    using V2 = typename std::conditional<std::is_same<A, float>::value, float2, double2>::type;
-#pragma unroll
-    for (int j = 0; j < NR; j += 2) {
-      const V2 v = *reinterpret_cast<const V2*>(p + j);
-      out[j] = v.x;
-      out[j + 1] = v.y;
-    }
-  } else {
-#pragma unroll
-    for (int j = 0; j < NR; ++j) out[j] = p[j];
-  }
 }
 
 // RAV apply with dense owned rows, all right-hand sides at once (same order

@@ -3,6 +3,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <cuda_bf16.h>
 #include <stdint.h>
 
 #include <vector>
@@ -213,6 +214,17 @@ __device__ inline int64_t node_id(const Geo& g, const int64_t* I) {
   for (int a = g.dim - 1; a >= 0; --a) id = id * g.M + I[a];
   return id;
 }
+// Loads of data streamed once per pass (operator values and columns, stored
+// inverses) with the evict-first hint, so they do not push the vectors that
+// every pass gathers from (x, r) out of L2.
+__device__ __forceinline__ double ld_stream(const double* p) { return __ldcs(p); }
+__device__ __forceinline__ float ld_stream(const float* p) { return __ldcs(p); }
+__device__ __forceinline__ int32_t ld_stream(const int32_t* p) { return __ldcs(p); }
+__device__ __forceinline__ __nv_bfloat16 ld_stream(const __nv_bfloat16* p) {
+  const unsigned short v = __ldcs(reinterpret_cast<const unsigned short*>(p));
+  return __nv_bfloat16(__nv_bfloat16_raw{v});
+}
+
 template <int D>
 __device__ __forceinline__ int64_t node_id_t(const Geo& g, const int64_t* I) {
   int64_t id = 0;

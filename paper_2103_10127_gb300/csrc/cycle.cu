@@ -41,9 +41,9 @@ __global__ void __launch_bounds__(256) k_residual_sell(int64_t nslots, const int
         int ck[8];
         double vk[8], xk[8];
 #pragma unroll
-        for (int j = 0; j < 8; ++j) ck[j] = c[32 * (k + j)];
+        for (int j = 0; j < 8; ++j) ck[j] = ld_stream(c + 32 * (k + j));
 #pragma unroll
-        for (int j = 0; j < 8; ++j) vk[j] = v[32 * (k + j)];
+        for (int j = 0; j < 8; ++j) vk[j] = ld_stream(v + 32 * (k + j));
 #pragma unroll
         for (int j = 0; j < 8; ++j) xk[j] = x[ck[j]];
 #pragma unroll
@@ -52,7 +52,7 @@ __global__ void __launch_bounds__(256) k_residual_sell(int64_t nslots, const int
           acc1 += vk[j + 1] * xk[j + 1];
         }
       }
-      for (; k < len; ++k) acc0 += v[32 * k] * x[c[32 * k]];
+      for (; k < len; ++k) acc0 += ld_stream(v + 32 * k) * x[ld_stream(c + 32 * k)];
     }
     if (row >= 0) {
       const double rv = len > 1 ? b[row] - (acc0 + acc1) : 0.0;
@@ -98,9 +98,9 @@ __global__ void __launch_bounds__(256) k_residual_sell_split(int64_t nslots, con
         int ck[4];
         double vk[4], xk[4];
 #pragma unroll
-        for (int i = 0; i < 4; ++i) ck[i] = scol[base + 32 * (k + i * K)];
+        for (int i = 0; i < 4; ++i) ck[i] = ld_stream(scol + base + 32 * (k + i * K));
 #pragma unroll
-        for (int i = 0; i < 4; ++i) vk[i] = sval[base + 32 * (k + i * K)];
+        for (int i = 0; i < 4; ++i) vk[i] = ld_stream(sval + base + 32 * (k + i * K));
 #pragma unroll
         for (int i = 0; i < 4; ++i) xk[i] = x[ck[i]];
         acc0 += vk[0] * xk[0];
@@ -108,7 +108,7 @@ __global__ void __launch_bounds__(256) k_residual_sell_split(int64_t nslots, con
         acc0 += vk[2] * xk[2];
         acc1 += vk[3] * xk[3];
       }
-      for (; k < len; k += K) acc0 += sval[base + 32 * k] * x[scol[base + 32 * k]];
+      for (; k < len; k += K) acc0 += ld_stream(sval + base + 32 * k) * x[ld_stream(scol + base + 32 * k)];
     }
     double acc = acc0 + acc1;
 #pragma unroll

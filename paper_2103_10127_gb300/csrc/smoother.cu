@@ -532,7 +532,7 @@ __global__ void __launch_bounds__(128, fact_min_blocks<D, T>()) k_rav_apply_fact
 #pragma unroll
         for (int a0 = 0; a0 < 5; ++a0) {
           const bool vv = v1 && a0 >= alo[0] && a0 <= ahi[0];
-          const A kq = (A)Fmt<T>::dec(kp[n * G], nullptr);
+          const A kq = (A)Fmt<T>::dec(ld_stream(kp + n * G), nullptr);
 #pragma unroll
           for (int c = 0; c < D; ++c) y[c] += kq * (vv ? r[rowoff + D * a0 + c] : (A)0);
           ++n;
@@ -545,7 +545,7 @@ __global__ void __launch_bounds__(128, fact_min_blocks<D, T>()) k_rav_apply_fact
       bool vv = a0 >= alo[0] && a0 <= ahi[0] && a1 >= alo[1] && a1 <= ahi[1];
       if (D == 3) vv = vv && a2 >= alo[2] && a2 <= ahi[2];
       const int64_t off = base + (int64_t)D * (a0 + (int64_t)M * (a1 + (int64_t)M * a2));
-      const A kq = (A)Fmt<T>::dec(kp[n * G], nullptr);
+      const A kq = (A)Fmt<T>::dec(ld_stream(kp + n * G), nullptr);
 #pragma unroll
       for (int c = 0; c < D; ++c) y[c] += kq * (vv ? r[off + c] : (A)0);
     }
