@@ -13,7 +13,7 @@ Reported with it:
   roofline      the dominant kernel (the fine-level RAV subdomain apply),
                 timed live with CUDA events on its launching stream over the
                 timed region, against the FP64 arithmetic peak (it is bound by
-                fp64 FMA throughput on GB300) -- see DESIGN.md for the counts;
+                fp64 FMA throughput on GB300; patch_work() holds the counts);
   e2e           the same metric with host buffers, host<->device copies inside;
   cpu_baseline  the FP64 oracle (one host core) on a bounded sample;
   time_to_tol   wall time of a full solve to a 1e-8 residual reduction.

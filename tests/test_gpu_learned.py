@@ -103,7 +103,7 @@ def test_trained_network_gains_over_fixed_damping_on_held_out_problems():
     blob contrasts 1e1-1e4, aspect ratios 1-8), then solve held-out problems
     (seed 2103) to 1e-8 with the fixed damping 0.5 and with the learned one,
     installed as one predicted weight per level (shrink 0).  The network must
-    cut the V-cycle count; the oracle's residual judges the learned solutions."""
+    cut the V-cycle count; the oracle's residual checks the learned solutions."""
     Xs, ys = [], []
     for seed, dim, N, nlev, s_max, asp in TRAIN_SET:
         spec = _problem(dim, N, nlev, seed, s_max=s_max, aspect=asp)
