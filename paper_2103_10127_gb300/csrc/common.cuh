@@ -104,7 +104,7 @@ struct rav_mg {
   double* cinv = nullptr;      // (n0 + 1)^2 row-major inverse of the bordered coarse system
   double* norm_part = nullptr; // partial sums for norms and dot products
   double* scalar_dev = nullptr;
-  double* scalar_host = nullptr;  // pinned
+  double* scalar_host = nullptr;  // pinned, 128 entries
   int part_cap = 0;
   // timing hook (rav_profile_*): event pairs around the solve-path kernels
   unsigned prof_mask = 0;  // bit k: record kernel class k (rav::PROF_*)

@@ -289,6 +289,36 @@ __global__ void k_scale_by_inv(int64_t n, const double* __restrict__ den, const 
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
     y[i] = s * xv[i];
 }
+// Block partial sums of the nv dot products V_i . w (V: nv vectors of n,
+// contiguous): part[i * gridDim.x + block].
+__global__ void k_multi_dot_parts(const double* __restrict__ V, const double* __restrict__ w, int64_t n, int nv,
+                                  double* __restrict__ part) {
+  for (int i = 0; i < nv; ++i) {
+    const double* vi = V + (int64_t)i * n;
+    double v = 0.0;
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x)
+      v += vi[k] * w[k];
+    v = block_sum(v);
+    if (threadIdx.x == 0) part[(int64_t)i * gridDim.x + blockIdx.x] = v;
+  }
+}
+// out[i] = sum over np block partials of dot product i (one block per i).
+__global__ void k_multi_sum_parts(const double* __restrict__ part, int np, double* __restrict__ out) {
+  double v = 0.0;
+  for (int k = threadIdx.x; k < np; k += blockDim.x) v += part[(int64_t)blockIdx.x * np + k];
+  v = block_sum(v);
+  if (threadIdx.x == 0) out[blockIdx.x] = v;
+}
+// w -= sum_i h[i] V_i
+__global__ void k_multi_axpy(const double* __restrict__ V, const double* __restrict__ h, int64_t n, int nv,
+                             double* __restrict__ w) {
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
+    double acc = w[k];
+    for (int i = 0; i < nv; ++i) acc -= h[i] * V[(int64_t)i * n + k];
+    w[k] = acc;
+  }
+}
+
 // y -= (*h) x  (Gram-Schmidt step with a device coefficient)
 __global__ void k_axpy_dev(int64_t n, const double* __restrict__ h, const double* __restrict__ xv,
                            double* __restrict__ y) {
@@ -611,7 +641,10 @@ static int solve_fgmres(rav_mg* mg, rav_smoother* sm, double* x, const double* b
   RAV_CUDA(cudaMallocAsync(&Z, sizeof(double) * n * m, s));
   RAV_CUDA(cudaMallocAsync(&w, sizeof(double) * n, s));
   RAV_CUDA(cudaMallocAsync(&zero, sizeof(double) * n, s));
-  RAV_CUDA(cudaMallocAsync(&hdev, sizeof(double) * (m + 2), s));
+  RAV_CUDA(cudaMallocAsync(&hdev, sizeof(double) * (2 * m + 3), s));
+  const int ndb = 152 * 2;  // blocks of the fused dot products
+  double* dpart = nullptr;
+  RAV_CUDA(cudaMallocAsync(&dpart, sizeof(double) * ndb * (m + 1), s));
   RAV_CUDA(cudaMemsetAsync(zero, 0, sizeof(double) * n, s));
   std::vector<double> H((m + 1) * m), cs(m), sn(m), gam(m + 1), y(m);
   const int gb = grid_for(n, 256, 152 * 16);
@@ -634,22 +667,30 @@ static int solve_fgmres(rav_mg* mg, rav_smoother* sm, double* x, const double* b
     for (; j < m && it < o.maxit; ++j) {
       double* vj = V + (int64_t)j * n;
       double* zj = Z + (int64_t)j * n;
-      RAV_CUDA(cudaMemsetAsync(zj, 0, sizeof(double) * n, s));
-      RAV_TRY(vcycle_impl(mg, sm, zj, vj, o.nu_pre, o.nu_post, true, s));
+      // z_j = M v_j: one V-cycle from a zero guess, replayed from a graph on
+      // the finest level's own work vectors (fixed pointers: one graph)
+      RAV_CUDA(cudaMemcpyAsync(L.b, vj, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+      RAV_CUDA(cudaMemsetAsync(L.x, 0, sizeof(double) * n, s));
+      RAV_TRY(vcycle_graph(mg, sm, L.x, L.b, o.nu_pre, o.nu_post, true, s));
+      RAV_CUDA(cudaMemcpyAsync(zj, L.x, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
       // w = L z: the residual of z against a zero right-hand side is -L z
       RAV_TRY(residual_impl(mg, fine, zj, zero, w, nullptr, s));
       k_scale_copy<<<gb, 256, 0, s>>>(n, -1.0, w, w);
       note_launch();
-      for (int i = 0; i <= j; ++i) {
-        RAV_TRY(dot_impl(mg, w, V + (int64_t)i * n, n, hdev + i, s));
-        k_axpy_dev<<<gb, 256, 0, s>>>(n, hdev + i, V + (int64_t)i * n, w);
-        note_launch();
+      // classical Gram-Schmidt applied twice (CGS2): h = V^T w, w -= V h, twice,
+      // each pass one fused dot kernel and one fused update
+      for (int pass = 0; pass < 2; ++pass) {
+        double* hp = hdev + pass * (m + 1);
+        k_multi_dot_parts<<<ndb, 256, 0, s>>>(V, w, n, j + 1, dpart);
+        k_multi_sum_parts<<<j + 1, 256, 0, s>>>(dpart, ndb, hp);
+        k_multi_axpy<<<gb, 256, 0, s>>>(V, hp, n, j + 1, w);
+        note_launch(3);
       }
-      RAV_TRY(dot_impl(mg, w, w, n, hdev + j + 1, s));
-      RAV_CUDA(cudaMemcpyAsync(mg->scalar_host, hdev, sizeof(double) * (j + 2), cudaMemcpyDeviceToHost, s));
+      RAV_TRY(dot_impl(mg, w, w, n, hdev + 2 * (m + 1), s));
+      RAV_CUDA(cudaMemcpyAsync(mg->scalar_host, hdev, sizeof(double) * (2 * m + 3), cudaMemcpyDeviceToHost, s));
       RAV_CUDA(cudaStreamSynchronize(s));
-      for (int i = 0; i <= j; ++i) H[i * m + j] = mg->scalar_host[i];
-      const double hn = std::sqrt(mg->scalar_host[j + 1]);
+      for (int i = 0; i <= j; ++i) H[i * m + j] = mg->scalar_host[i] + mg->scalar_host[m + 1 + i];
+      const double hn = std::sqrt(mg->scalar_host[2 * (m + 1)]);
       H[(j + 1) * m + j] = hn;
       k_scale_copy<<<gb, 256, 0, s>>>(n, hn > 0 ? 1.0 / hn : 0.0, w, V + (int64_t)(j + 1) * n);
       note_launch();
@@ -695,6 +736,7 @@ static int solve_fgmres(rav_mg* mg, rav_smoother* sm, double* x, const double* b
   cudaFreeAsync(w, s);
   cudaFreeAsync(zero, s);
   cudaFreeAsync(hdev, s);
+  cudaFreeAsync(dpart, s);
   if (info) {
     info->iterations = it;
     info->final_ratio = ratio;

@@ -983,7 +983,7 @@ extern "C" int mg_setup(const rav_problem* p, int n_levels, rav_stream stream, r
     mg->part_cap = std::max<int>(mg->part_cap, (int)((mg->lev[l].nslice * 32 * 32 + 255) / 256));
   if (cudaMalloc(&mg->norm_part, sizeof(double) * (mg->part_cap + 8)) != cudaSuccess) return fail(RAV_ERR_CUDA);
   if (cudaMalloc(&mg->scalar_dev, sizeof(double) * 64) != cudaSuccess) return fail(RAV_ERR_CUDA);
-  if (cudaMallocHost(&mg->scalar_host, sizeof(double) * 64) != cudaSuccess) return fail(RAV_ERR_CUDA);
+  if (cudaMallocHost(&mg->scalar_host, sizeof(double) * 128) != cudaSuccess) return fail(RAV_ERR_CUDA);
   if ((rc = tune_residual_split(mg, s)) != RAV_OK) return fail(rc);
   if (cudaStreamSynchronize(s) != cudaSuccess) return fail(RAV_ERR_CUDA);
   *out = mg;
