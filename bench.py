@@ -91,6 +91,21 @@ def dist_env():
     return ws, rank, local
 
 
+def max_over_ranks(ms, dist, device):
+    """The slowest rank's timed region (ms): every rank ran its own replica."""
+    if dist is None:
+        return ms
+    import torch
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replicas_value(ws, dofs, steps, ms):
+    """Whole-job DoFs/s: ws replicas of `dofs` DoFs, `steps` cycles each, in ms."""
+    return ws * dofs * steps / (ms / 1e3)
+
+
 # ---------------------------------------------------------------------------
 def patch_work(dim, N, prec, n):
     """Algorithmic (flops, bytes) of one fine-level subdomain apply, counting
@@ -313,11 +328,8 @@ def run_ours(args, W):
                 row[nm] = round(1e3 * tot.value / kb, 2)
         breakdown[f"N={mg.counts(lev)['N']}"] = row
     lib.rav_profile_enable(mg.h, 0, -1)
-    if dist is not None:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = ws * n * args.steps / (ms / 1e3)
+    ms = max_over_ranks(ms, dist, "cuda")
+    value = replicas_value(ws, n, args.steps, ms)
 
     # ---- roofline of the dominant kernel: fine-level subdomain apply ----
     flops, bytes_alg, stored = patch_work(W["dim"], W["N"], W["prec"], n)
