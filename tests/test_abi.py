@@ -42,6 +42,8 @@ def test_invalid_arguments_are_rejected_without_a_gpu():
     p = _capi.RavProblem(2, 16, None, 1.0, 0, None, 0)
     assert lib.mg_setup(ctypes.byref(p), 5, None, ctypes.byref(h)) == -1  # coarsest grid 1 cell
     assert lib.mg_setup(ctypes.byref(p), 17, None, ctypes.byref(h)) == -1  # too many levels
+    big = _capi.RavProblem(3, 24, None, 1.0, 0, None, 0)  # one 24^3 level: explicit coarse inverse too large
+    assert lib.mg_setup(ctypes.byref(big), 1, None, ctypes.byref(h)) == -1
     c = (ctypes.c_double * 34)(*([0.0] * 34))  # non-increasing coordinates
     p = _capi.RavProblem(2, 16, ctypes.cast(c, ctypes.c_void_p), 1.0, 0, None, 0)
     assert lib.mg_setup(ctypes.byref(p), 2, None, ctypes.byref(h)) == -1
