@@ -125,7 +125,7 @@ struct rav_mg {
     const double* x;
     const double* b;
     int nu1, nu2;
-    bool x_is_zero;
+    int entry;
     int64_t launches;  // kernels in one replay
     cudaGraphExec_t exec;
   };
@@ -297,12 +297,18 @@ int dot_impl(rav_mg* mg, const double* a, const double* b, int64_t n, double* ou
 }  // namespace rav
 
 // Smoother entry used by the cycle (defined in smoother.cu) and the V-cycle (cycle.cu).
-// x_is_zero: x is known to be 0, so the first residual is b itself (free rows)
-// and its SpMV is skipped (RAV, AV); the result is the same.
+// entry (how x and the level's residual vector stand when smoothing starts):
+//   ENTRY_GENERAL  nothing known;
+//   ENTRY_X_ZERO   x is 0, so the first residual is b itself (free rows; b is 0
+//                  on Dirichlet rows below the finest level): its SpMV is skipped;
+//   ENTRY_R_READY  the level's r (and the fp32 copy of reduced storage) already
+//                  holds b - L x, computed for a norm: its SpMV is skipped.
+// The results are the same in every case.
+enum { ENTRY_GENERAL = 0, ENTRY_X_ZERO = 1, ENTRY_R_READY = 2 };
 int rav_smooth_impl(rav_smoother* sm, int level, double* x, const double* b, int steps, cudaStream_t s,
-                    bool x_is_zero = false);
+                    int entry = ENTRY_GENERAL);
 namespace rav {
-int vcycle_impl(rav_mg* mg, rav_smoother* sm, double* x, const double* b, int nu1, int nu2, bool x_is_zero,
+int vcycle_impl(rav_mg* mg, rav_smoother* sm, double* x, const double* b, int nu1, int nu2, int entry,
                 cudaStream_t s);
 // Destroys the captured V-cycles that use smoother sm (all of them for nullptr).
 void drop_graphs(rav_mg* mg, const rav_smoother* sm);

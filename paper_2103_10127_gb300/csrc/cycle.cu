@@ -409,33 +409,36 @@ static int coarse_apply(rav_mg* mg, const double* b, double* x, int accumulate, 
 
 int coarse_impl(rav_mg* mg, const double* b, double* x, cudaStream_t s) { return coarse_apply(mg, b, x, 0, s); }
 
-// V(nu1, nu2) on level l with iterate x and right-hand side b.  When
-// x_is_zero the first residual equals b and the coarse correction simply
-// overwrites x.
+// V(nu1, nu2) on level l with iterate x and right-hand side b.  With
+// ENTRY_X_ZERO the first residual below the finest level equals b and the
+// coarse correction simply overwrites x; with ENTRY_R_READY the finest
+// level's residual vector already holds b - L x.
 static int vcycle_rec(rav_mg* mg, rav_smoother* sm, int l, double* x, const double* b, int nu1, int nu2,
-                      bool x_is_zero, cudaStream_t s) {
+                      int entry, cudaStream_t s) {
   Level& L = mg->lev[l];
   if (l == 0) {
-    if (x_is_zero) return coarse_apply(mg, b, x, 0, s);
+    if (entry == ENTRY_X_ZERO) return coarse_apply(mg, b, x, 0, s);
     RAV_TRY(residual_impl(mg, 0, x, b, L.r, nullptr, s));
     return coarse_apply(mg, L.r, x, 1, s);  // x += C r (masked copy of r goes to L.b)
   }
   // below the finest level x enters as 0 and b (a restricted residual) is 0 on
   // Dirichlet rows, so the first smoothing step can take r = b
-  RAV_TRY(rav_smooth_impl(sm, l, x, b, nu1, s, x_is_zero && l < mg->nlev - 1));
+  const int first = l < mg->nlev - 1 ? (entry == ENTRY_X_ZERO ? ENTRY_X_ZERO : ENTRY_GENERAL)
+                                     : (entry == ENTRY_R_READY ? ENTRY_R_READY : ENTRY_GENERAL);
+  RAV_TRY(rav_smooth_impl(sm, l, x, b, nu1, s, first));
   Level& C = mg->lev[l - 1];
   RAV_TRY(residual_impl(mg, l, x, b, L.r, nullptr, s));
   RAV_TRY(restrict_impl(mg, l, L.r, C.b, s));
   RAV_CUDA(cudaMemsetAsync(C.x, 0, sizeof(double) * C.g.n, s));
-  RAV_TRY(vcycle_rec(mg, sm, l - 1, C.x, C.b, nu1, nu2, true, s));
+  RAV_TRY(vcycle_rec(mg, sm, l - 1, C.x, C.b, nu1, nu2, ENTRY_X_ZERO, s));
   RAV_TRY(prolong_impl(mg, l, C.x, x, s));
   RAV_TRY(rav_smooth_impl(sm, l, x, b, nu2, s));
   return RAV_OK;
 }
 
-int vcycle_impl(rav_mg* mg, rav_smoother* sm, double* x, const double* b, int nu1, int nu2, bool x_is_zero,
+int vcycle_impl(rav_mg* mg, rav_smoother* sm, double* x, const double* b, int nu1, int nu2, int entry,
                 cudaStream_t s) {
-  return vcycle_rec(mg, sm, mg->nlev - 1, x, b, nu1, nu2, x_is_zero, s);
+  return vcycle_rec(mg, sm, mg->nlev - 1, x, b, nu1, nu2, entry, s);
 }
 
 // One V-cycle as a CUDA graph.  The first call for a given (smoother, x, b,
@@ -443,18 +446,18 @@ int vcycle_impl(rav_mg* mg, rav_smoother* sm, double* x, const double* b, int nu
 // replays the instantiated graph on the caller's stream, which removes the
 // per-kernel launch latency that dominates the small levels.  Not used while
 // the timing hook records (its events would be baked into the graph).
-static int vcycle_graph(rav_mg* mg, rav_smoother* sm, double* x, const double* b, int nu1, int nu2, bool x_is_zero,
+static int vcycle_graph(rav_mg* mg, rav_smoother* sm, double* x, const double* b, int nu1, int nu2, int entry,
                         cudaStream_t s) {
-  if (!mg->use_graphs || mg->prof_mask != 0 || sm->collect) return vcycle_impl(mg, sm, x, b, nu1, nu2, x_is_zero, s);
+  if (!mg->use_graphs || mg->prof_mask != 0 || sm->collect) return vcycle_impl(mg, sm, x, b, nu1, nu2, entry, s);
   rav_mg::GraphEntry* hit = nullptr;
   for (auto& e : mg->graphs)
-    if (e.sm == sm && e.x == x && e.b == b && e.nu1 == nu1 && e.nu2 == nu2 && e.x_is_zero == x_is_zero) hit = &e;
+    if (e.sm == sm && e.x == x && e.b == b && e.nu1 == nu1 && e.nu2 == nu2 && e.entry == entry) hit = &e;
   if (!hit) {
     // capturing runs nothing; the replay on s is ordered after s's earlier work
     if (!mg->cap_stream) RAV_CUDA(cudaStreamCreateWithFlags(&mg->cap_stream, cudaStreamNonBlocking));
     const int64_t l0 = rav_kernel_launches();
     RAV_CUDA(cudaStreamBeginCapture(mg->cap_stream, cudaStreamCaptureModeThreadLocal));
-    const int rc = vcycle_impl(mg, sm, x, b, nu1, nu2, x_is_zero, mg->cap_stream);
+    const int rc = vcycle_impl(mg, sm, x, b, nu1, nu2, entry, mg->cap_stream);
     cudaGraph_t graph = nullptr;
     const cudaError_t ec = cudaStreamEndCapture(mg->cap_stream, &graph);
     if (rc != RAV_OK || ec != cudaSuccess) {
@@ -470,7 +473,7 @@ static int vcycle_graph(rav_mg* mg, rav_smoother* sm, double* x, const double* b
       cudaGraphExecDestroy(mg->graphs.front().exec);
       mg->graphs.erase(mg->graphs.begin());
     }
-    mg->graphs.push_back({sm, x, b, nu1, nu2, x_is_zero, rav_kernel_launches() - l0, exec});
+    mg->graphs.push_back({sm, x, b, nu1, nu2, entry, rav_kernel_launches() - l0, exec});
     hit = &mg->graphs.back();
     note_launch((int)-hit->launches);  // counted again below, per replay
   }
@@ -530,7 +533,7 @@ extern "C" int rav_coarse_solve(rav_mg* mg, const double* b, double* x, rav_stre
 extern "C" int vcycle(rav_mg* mg, rav_smoother* sm, double* x, const double* b, int nu1, int nu2,
                       rav_stream stream) {
   if (!mg || !sm || sm->mg != mg || !x || !b || nu1 < 0 || nu2 < 0) return RAV_ERR_ARG;
-  return vcycle_graph(mg, sm, x, b, nu1, nu2, false, S(stream));
+  return vcycle_graph(mg, sm, x, b, nu1, nu2, ENTRY_GENERAL, S(stream));
 }
 
 // ---------------------------------------------------------------------------
@@ -592,8 +595,11 @@ extern "C" int rav_set_graphs(rav_mg* mg, int enable) {
 static int solve_stationary(rav_mg* mg, rav_smoother* sm, double* x, const double* b, const rav_solve_opts& o,
                             rav_solve_info* info, cudaStream_t s) {
   Level& L = mg->lev[mg->nlev - 1];
+  float* r32 = sm->lev[mg->nlev - 1].r32;
   double r0 = 0.0, rk = 0.0;
-  RAV_TRY(residual_impl(mg, mg->nlev - 1, x, b, L.r, mg->scalar_dev, s));
+  // every norm residual leaves b - L x in L.r (and r32), where the next
+  // cycle's first smoothing step takes it instead of recomputing it
+  RAV_TRY(residual_impl(mg, mg->nlev - 1, x, b, L.r, mg->scalar_dev, s, r32));
   RAV_TRY(read_scalar(mg, mg->scalar_dev, &r0, s));
   if (info && info->history_host) info->history_host[0] = 1.0;
   if (r0 == 0.0) {
@@ -603,8 +609,8 @@ static int solve_stationary(rav_mg* mg, rav_smoother* sm, double* x, const doubl
   int rc = RAV_ERR_NOT_CONVERGED, k = 0, fell_back = 0;
   double ratio = 1.0, prev = 1.0;
   for (k = 1; k <= o.maxit; ++k) {
-    RAV_TRY(vcycle_graph(mg, sm, x, b, o.nu_pre, o.nu_post, false, s));
-    RAV_TRY(residual_impl(mg, mg->nlev - 1, x, b, L.r, mg->scalar_dev, s));
+    RAV_TRY(vcycle_graph(mg, sm, x, b, o.nu_pre, o.nu_post, ENTRY_R_READY, s));
+    RAV_TRY(residual_impl(mg, mg->nlev - 1, x, b, L.r, mg->scalar_dev, s, r32));
     RAV_TRY(read_scalar(mg, mg->scalar_dev, &rk, s));
     ratio = rk / r0;
     if (info && info->history_host) info->history_host[k] = ratio;
@@ -671,7 +677,7 @@ static int solve_fgmres(rav_mg* mg, rav_smoother* sm, double* x, const double* b
       // the finest level's own work vectors (fixed pointers: one graph)
       RAV_CUDA(cudaMemcpyAsync(L.b, vj, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
       RAV_CUDA(cudaMemsetAsync(L.x, 0, sizeof(double) * n, s));
-      RAV_TRY(vcycle_graph(mg, sm, L.x, L.b, o.nu_pre, o.nu_post, true, s));
+      RAV_TRY(vcycle_graph(mg, sm, L.x, L.b, o.nu_pre, o.nu_post, ENTRY_X_ZERO, s));
       RAV_CUDA(cudaMemcpyAsync(zj, L.x, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
       // w = L z: the residual of z against a zero right-hand side is -L z
       RAV_TRY(residual_impl(mg, fine, zj, zero, w, nullptr, s));

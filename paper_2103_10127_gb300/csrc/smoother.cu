@@ -1282,7 +1282,7 @@ int reset_omega(rav_smoother* sm, cudaStream_t s) {
 }
 
 int rav_smooth_impl(rav_smoother* sm, int level, double* x, const double* b, int steps, cudaStream_t s,
-                    bool x_is_zero) {
+                    int entry) {
   rav_mg* mg = sm->mg;
   Level& L = mg->lev[level];
   SmLevel& SL = sm->lev[level];
@@ -1309,9 +1309,13 @@ int rav_smooth_impl(rav_smoother* sm, int level, double* x, const double* b, int
       RAV_TRY(prof_end(mg, level, PROF_APPLY, e0, s));
       continue;
     }
-    if (it == 0 && x_is_zero) {
+    if (it == 0 && entry == ENTRY_X_ZERO) {
       // r = b - L 0 = b on free rows; b is 0 on Dirichlet rows of a coarse level
       RAV_TRY(apply_impl(sm, level, b, x, s));
+      continue;
+    }
+    if (it == 0 && entry == ENTRY_R_READY) {  // r = b - L x is already in L.r (and r32)
+      RAV_TRY(apply_impl(sm, level, L.r, x, s, SL.r32));
       continue;
     }
     RAV_TRY(residual_impl(mg, level, x, b, L.r, nullptr, s, SL.r32));
