@@ -282,13 +282,6 @@ __global__ void k_scale_copy(int64_t n, double a, const double* __restrict__ xv,
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
     y[i] = a * xv[i];
 }
-// y = a * x scaled by the device scalar 1/(*den)
-__global__ void k_scale_by_inv(int64_t n, const double* __restrict__ den, const double* __restrict__ xv,
-                               double* __restrict__ y) {
-  const double s = *den > 0.0 ? 1.0 / *den : 0.0;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-    y[i] = s * xv[i];
-}
 // Block partial sums of the nv dot products V_i . w (V: nv vectors of n,
 // contiguous): part[i * gridDim.x + block].
 __global__ void k_multi_dot_parts(const double* __restrict__ V, const double* __restrict__ w, int64_t n, int nv,
@@ -319,13 +312,6 @@ __global__ void k_multi_axpy(const double* __restrict__ V, const double* __restr
   }
 }
 
-// y -= (*h) x  (Gram-Schmidt step with a device coefficient)
-__global__ void k_axpy_dev(int64_t n, const double* __restrict__ h, const double* __restrict__ xv,
-                           double* __restrict__ y) {
-  const double a = -*h;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-    y[i] += a * xv[i];
-}
 
 // ---------------------------------------------------------------------------
 int residual_impl(rav_mg* mg, int level, const double* x, const double* b, double* r, double* norm2_dev,
