@@ -263,17 +263,24 @@ __global__ void kb_apply(const BLevel* __restrict__ L, const int64_t* __restrict
   }
 }
 
-// Restriction into the coarser level (same order per RHS as k_restrict_c);
-// also zeroes the coarser iterate.
+// Restriction into the coarser level (same threads per coarse DoF and the same
+// order per RHS as k_restrict_c); also zeroes the coarser iterate.
 template <int D, int NR>
 __global__ void kb_restrict(const BLevel* __restrict__ L, const int64_t* __restrict__ first, int ne) {
   const int e = find_entry(first, ne, blockIdx.x);
   const BLevel& lv = L[e];
   const Geo &gf = lv.g, &gc = lv.gc;
   const XferTab& T = lv.tab;
-  const int t = (int)((blockIdx.x - first[e]) * blockDim.x + threadIdx.x);
+  const int tl = restrict_split(gc);
+  const int64_t gt = (blockIdx.x - first[e]) * (int64_t)blockDim.x + threadIdx.x;
+  const int t = (int)(gt / tl), sub = (int)(gt % tl);
   const int Mf = (int)gf.M, Mc = (int)gc.M, nnc = (int)gc.nnode;
   const double* rf = lv.r;
+  double acc[D][NR];
+#pragma unroll
+  for (int c = 0; c < D; ++c)
+#pragma unroll
+    for (int j = 0; j < NR; ++j) acc[c][j] = 0.0;
   if (t < nnc) {
     int K[3] = {0, 0, 0}, id = t;
     bool bnd = false;
@@ -282,31 +289,51 @@ __global__ void kb_restrict(const BLevel* __restrict__ L, const int64_t* __restr
       id /= Mc;
       bnd |= (K[a] == 0) | (K[a] == Mc - 1);
     }
-    double acc[D][NR];
-#pragma unroll
-    for (int c = 0; c < D; ++c)
-#pragma unroll
-      for (int j = 0; j < NR; ++j) acc[c][j] = 0.0;
     if (!bnd) {
       const int c0 = T.rc2[0][K[0]], c1 = T.rc2[1][K[1]], c2 = D == 3 ? T.rc2[2][K[2]] : 1;
-      for (int j2 = 0; j2 < c2; ++j2) {
+      for (int pr = sub; pr < c2 * c1; pr += tl) {
+        const int j2 = pr / c1, j1 = pr % c1;
         const int I2 = D == 3 ? T.rk2[2][7 * K[2] + j2] : 0;
         const double w2 = D == 3 ? T.rw2[2][7 * K[2] + j2] : 1.0;
-        for (int j1 = 0; j1 < c1; ++j1) {
-          const int I1 = T.rk2[1][7 * K[1] + j1];
-          const double w12 = D == 3 ? w2 * T.rw2[1][7 * K[1] + j1] : T.rw2[1][7 * K[1] + j1];
-          const int64_t rowbase = (int64_t)D * Mf * (I1 + (int64_t)Mf * I2);
-          for (int j0 = 0; j0 < c0; ++j0) {
-            const double ww = w12 * T.rw2[0][7 * K[0] + j0];
-            const int64_t bse = rowbase + D * T.rk2[0][7 * K[0] + j0];
+        const int I1 = T.rk2[1][7 * K[1] + j1];
+        const double w12 = D == 3 ? w2 * T.rw2[1][7 * K[1] + j1] : T.rw2[1][7 * K[1] + j1];
+        const int64_t rowbase = (int64_t)D * Mf * (I1 + (int64_t)Mf * I2);
+        for (int j0 = 0; j0 < c0; ++j0) {
+          const double ww = w12 * T.rw2[0][7 * K[0] + j0];
+          const int64_t bse = rowbase + D * T.rk2[0][7 * K[0] + j0];
 #pragma unroll
-            for (int c = 0; c < D; ++c)
+          for (int c = 0; c < D; ++c)
 #pragma unroll
-              for (int j = 0; j < NR; ++j) acc[c][j] += ww * rf[(bse + c) * NR + j];
-          }
+            for (int j = 0; j < NR; ++j) acc[c][j] += ww * rf[(bse + c) * NR + j];
         }
       }
     }
+  } else if (t < nnc + (int)gc.n_p) {
+    const int Nf1 = gf.N + 1, Nc1 = gc.N + 1;
+    int K[3] = {0, 0, 0}, id = t - nnc;
+    for (int a = 0; a < D; ++a) { K[a] = id % Nc1; id /= Nc1; }
+    const int c0 = T.rc1[0][K[0]], c1 = T.rc1[1][K[1]], c2 = D == 3 ? T.rc1[2][K[2]] : 1;
+    for (int pr = sub; pr < c2 * c1; pr += tl) {
+      const int j2 = pr / c1, j1 = pr % c1;
+      const int V2 = D == 3 ? T.rk1[2][3 * K[2] + j2] : 0;
+      const double w2 = D == 3 ? T.rw1[2][3 * K[2] + j2] : 1.0;
+      const int V1 = T.rk1[1][3 * K[1] + j1];
+      const double w12 = D == 3 ? w2 * T.rw1[1][3 * K[1] + j1] : T.rw1[1][3 * K[1] + j1];
+      for (int j0 = 0; j0 < c0; ++j0) {
+        const double ww = w12 * T.rw1[0][3 * K[0] + j0];
+        const int64_t idx = gf.n_u + T.rk1[0][3 * K[0] + j0] + Nf1 * (V1 + (int64_t)Nf1 * V2);
+#pragma unroll
+        for (int j = 0; j < NR; ++j) acc[0][j] += ww * rf[idx * NR + j];
+      }
+    }
+  }
+  for (int o = tl >> 1; o > 0; o >>= 1)
+#pragma unroll
+    for (int c = 0; c < D; ++c)
+#pragma unroll
+      for (int j = 0; j < NR; ++j) acc[c][j] += __shfl_xor_sync(0xffffffffu, acc[c][j], o, tl);
+  if (sub != 0) return;
+  if (t < nnc) {
 #pragma unroll
     for (int c = 0; c < D; ++c)
 #pragma unroll
@@ -316,32 +343,11 @@ __global__ void kb_restrict(const BLevel* __restrict__ L, const int64_t* __restr
         lv.xc[((int64_t)D * t + c) * NR + j] = 0.0;
       }
   } else if (t < nnc + (int)gc.n_p) {
-    const int Nf1 = gf.N + 1, Nc1 = gc.N + 1;
-    int K[3] = {0, 0, 0}, id = t - nnc;
-    for (int a = 0; a < D; ++a) { K[a] = id % Nc1; id /= Nc1; }
-    const int c0 = T.rc1[0][K[0]], c1 = T.rc1[1][K[1]], c2 = D == 3 ? T.rc1[2][K[2]] : 1;
-    double acc[NR];
-#pragma unroll
-    for (int j = 0; j < NR; ++j) acc[j] = 0.0;
-    for (int j2 = 0; j2 < c2; ++j2) {
-      const int V2 = D == 3 ? T.rk1[2][3 * K[2] + j2] : 0;
-      const double w2 = D == 3 ? T.rw1[2][3 * K[2] + j2] : 1.0;
-      for (int j1 = 0; j1 < c1; ++j1) {
-        const int V1 = T.rk1[1][3 * K[1] + j1];
-        const double w12 = D == 3 ? w2 * T.rw1[1][3 * K[1] + j1] : T.rw1[1][3 * K[1] + j1];
-        for (int j0 = 0; j0 < c0; ++j0) {
-          const double ww = w12 * T.rw1[0][3 * K[0] + j0];
-          const int64_t idx = gf.n_u + T.rk1[0][3 * K[0] + j0] + Nf1 * (V1 + (int64_t)Nf1 * V2);
-#pragma unroll
-          for (int j = 0; j < NR; ++j) acc[j] += ww * rf[idx * NR + j];
-        }
-      }
-    }
     const int64_t o = gc.n_u + (t - nnc);
 #pragma unroll
     for (int j = 0; j < NR; ++j) {
-      lv.bc[o * NR + j] = acc[j];
-      if (lv.bc32) lv.bc32[o * NR + j] = (float)acc[j];
+      lv.bc[o * NR + j] = acc[0][j];
+      if (lv.bc32) lv.bc32[o * NR + j] = (float)acc[0][j];
       lv.xc[o * NR + j] = 0.0;
     }
   }
@@ -592,7 +598,9 @@ static int upload_phase(rav_batch* bt, BPhase& ph, const std::vector<int>& entri
 
 static int64_t blk_res(const BLevel& b, int t) { return (b.nslice * 32 + t - 1) / t; }
 static int64_t blk_apply(const BLevel& b, int t) { return (b.units + t - 1) / t; }
-static int64_t blk_restrict(const BLevel& b, int t) { return (b.gc.nnode + b.gc.n_p + t - 1) / t; }
+static int64_t blk_restrict(const BLevel& b, int t) {
+  return ((b.gc.nnode + b.gc.n_p) * restrict_split(b.gc) + t - 1) / t;
+}
 static int64_t blk_prolong(const BLevel& b, int t) { return (b.g.nnode + b.g.n_p + t - 1) / t; }
 static int64_t blk_mask(const BLevel& b, int t) { return (b.g.n + t - 1) / t; }
 static int64_t blk_gemv(const BLevel& b, int t) { return (b.g.n + t / 32 - 1) / (t / 32); }

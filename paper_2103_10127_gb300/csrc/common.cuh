@@ -288,6 +288,13 @@ inline int grid_for(int64_t n, int threads, int cap = 152 * 64) {
 // r32 (optional): the residual rounded to fp32 as well, for applies that accumulate in fp32.
 int residual_impl(rav_mg* mg, int level, const double* x, const double* b, double* r, double* norm2_dev,
                   cudaStream_t s, float* r32 = nullptr);
+// Threads per coarse DoF of the restriction into the coarse level gc: 8 below
+// 2^14 coarse DoF sites, where one thread per site leaves the GPU waiting on
+// long fp64 chains, else 1 (the shuffle reduction costs fp64 work of its own);
+// the batched restriction uses the same rule.
+__host__ __device__ inline int restrict_split(const Geo& gc) {
+  return gc.nnode + gc.n_p < (int64_t(1) << 14) ? 8 : 1;
+}
 int restrict_impl(rav_mg* mg, int level, const double* rf, double* bc, cudaStream_t s);
 int prolong_impl(rav_mg* mg, int level, const double* xc, double* xf, cudaStream_t s);
 int coarse_impl(rav_mg* mg, const double* b, double* x, cudaStream_t s);

@@ -170,11 +170,14 @@ __global__ void k_prolong(Geo gf, Geo gc, XferTab T, const double* __restrict__ 
         const int K1 = T.pk2[1][3 * I[1] + j1];
         const double w12 = D == 3 ? w2 * T.pw2[1][3 * I[1] + j1] : T.pw2[1][3 * I[1] + j1];
         const int rowbase = D * Mc * (K1 + Mc * K2);
-        for (int j0 = 0; j0 < c0; ++j0) {
-          const double ww = w12 * T.pw2[0][3 * I[0] + j0];
-          const int base = rowbase + D * T.pk2[0][3 * I[0] + j0];
 #pragma unroll
-          for (int c = 0; c < D; ++c) acc[c] += ww * xc[base + c];
+        for (int j0 = 0; j0 < 3; ++j0) {
+          if (j0 < c0) {
+            const double ww = w12 * T.pw2[0][3 * I[0] + j0];
+            const int base = rowbase + D * T.pk2[0][3 * I[0] + j0];
+#pragma unroll
+            for (int c = 0; c < D; ++c) acc[c] += ww * xc[base + c];
+          }
         }
       }
     }
@@ -192,8 +195,10 @@ __global__ void k_prolong(Geo gf, Geo gc, XferTab T, const double* __restrict__ 
       for (int j1 = 0; j1 < c1; ++j1) {
         const int K1 = T.pk1[1][2 * v[1] + j1];
         const double w12 = D == 3 ? w2 * T.pw1[1][2 * v[1] + j1] : T.pw1[1][2 * v[1] + j1];
-        for (int j0 = 0; j0 < c0; ++j0)
-          acc += w12 * T.pw1[0][2 * v[0] + j0] * xc[gc.n_u + T.pk1[0][2 * v[0] + j0] + Nc1 * (K1 + Nc1 * K2)];
+#pragma unroll
+        for (int j0 = 0; j0 < 2; ++j0)
+          if (j0 < c0)
+            acc += w12 * T.pw1[0][2 * v[0] + j0] * xc[gc.n_u + T.pk1[0][2 * v[0] + j0] + Nc1 * (K1 + Nc1 * K2)];
       }
     }
     xf[gf.n_u + (t - nnf)] += acc;
@@ -202,10 +207,19 @@ __global__ void k_prolong(Geo gf, Geo gc, XferTab T, const double* __restrict__ 
 
 // bc = P^T rf: each coarse DoF gathers the fine DoFs whose interpolation
 // uses it (fine boundary nodes are not in the lists); 0 on coarse Dirichlet rows.
+// tl (1, 2, 4 or 8) consecutive threads share one coarse DoF: thread `sub`
+// takes the rows (j2, j1) numbered sub, sub + tl, ... in row-major order and
+// the tl partial sums meet by xor shuffles (tl = 1: one thread, rows in order).
+// On small levels a single thread's fp64 chain was the whole kernel's time.
 template <int D>
-__global__ void k_restrict_c(Geo gf, Geo gc, XferTab T, const double* __restrict__ rf, double* __restrict__ bc) {
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+__global__ void k_restrict_c(Geo gf, Geo gc, XferTab T, const double* __restrict__ rf, double* __restrict__ bc,
+                             int tl) {
+  const int64_t gt = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int t = (int)(gt / tl), sub = (int)(gt % tl);
   const int Mf = (int)gf.M, Mc = (int)gc.M, nnc = (int)gc.nnode;
+  double acc[D];
+#pragma unroll
+  for (int c = 0; c < D; ++c) acc[c] = 0.0;
   if (t < nnc) {
     int K[3] = {0, 0, 0}, id = t;
     bool bnd = false;
@@ -214,19 +228,19 @@ __global__ void k_restrict_c(Geo gf, Geo gc, XferTab T, const double* __restrict
       id /= Mc;
       bnd |= (K[a] == 0) | (K[a] == Mc - 1);
     }
-    double acc[D];
-#pragma unroll
-    for (int c = 0; c < D; ++c) acc[c] = 0.0;
     if (!bnd) {
       const int c0 = T.rc2[0][K[0]], c1 = T.rc2[1][K[1]], c2 = D == 3 ? T.rc2[2][K[2]] : 1;
-      for (int j2 = 0; j2 < c2; ++j2) {
+      for (int pr = sub; pr < c2 * c1; pr += tl) {
+        const int j2 = pr / c1, j1 = pr % c1;
         const int I2 = D == 3 ? T.rk2[2][7 * K[2] + j2] : 0;
         const double w2 = D == 3 ? T.rw2[2][7 * K[2] + j2] : 1.0;
-        for (int j1 = 0; j1 < c1; ++j1) {
-          const int I1 = T.rk2[1][7 * K[1] + j1];
-          const double w12 = D == 3 ? w2 * T.rw2[1][7 * K[1] + j1] : T.rw2[1][7 * K[1] + j1];
-          const int64_t rowbase = (int64_t)D * Mf * (I1 + (int64_t)Mf * I2);
-          for (int j0 = 0; j0 < c0; ++j0) {
+        const int I1 = T.rk2[1][7 * K[1] + j1];
+        const double w12 = D == 3 ? w2 * T.rw2[1][7 * K[1] + j1] : T.rw2[1][7 * K[1] + j1];
+        const int64_t rowbase = (int64_t)D * Mf * (I1 + (int64_t)Mf * I2);
+        // fixed trip count with a guard: the loads of a row are issued together
+#pragma unroll
+        for (int j0 = 0; j0 < 7; ++j0) {
+          if (j0 < c0) {
             const double ww = w12 * T.rw2[0][7 * K[0] + j0];
             const int64_t base = rowbase + D * T.rk2[0][7 * K[0] + j0];
 #pragma unroll
@@ -235,25 +249,33 @@ __global__ void k_restrict_c(Geo gf, Geo gc, XferTab T, const double* __restrict
         }
       }
     }
-#pragma unroll
-    for (int c = 0; c < D; ++c) bc[(int64_t)D * t + c] = acc[c];
   } else if (t < nnc + (int)gc.n_p) {
     const int Nf1 = gf.N + 1, Nc1 = gc.N + 1;
     int K[3] = {0, 0, 0}, id = t - nnc;
     for (int a = 0; a < D; ++a) { K[a] = id % Nc1; id /= Nc1; }
     const int c0 = T.rc1[0][K[0]], c1 = T.rc1[1][K[1]], c2 = D == 3 ? T.rc1[2][K[2]] : 1;
-    double acc = 0.0;
-    for (int j2 = 0; j2 < c2; ++j2) {
+    for (int pr = sub; pr < c2 * c1; pr += tl) {
+      const int j2 = pr / c1, j1 = pr % c1;
       const int V2 = D == 3 ? T.rk1[2][3 * K[2] + j2] : 0;
       const double w2 = D == 3 ? T.rw1[2][3 * K[2] + j2] : 1.0;
-      for (int j1 = 0; j1 < c1; ++j1) {
-        const int V1 = T.rk1[1][3 * K[1] + j1];
-        const double w12 = D == 3 ? w2 * T.rw1[1][3 * K[1] + j1] : T.rw1[1][3 * K[1] + j1];
-        for (int j0 = 0; j0 < c0; ++j0)
-          acc += w12 * T.rw1[0][3 * K[0] + j0] * rf[gf.n_u + T.rk1[0][3 * K[0] + j0] + Nf1 * (V1 + (int64_t)Nf1 * V2)];
-      }
+      const int V1 = T.rk1[1][3 * K[1] + j1];
+      const double w12 = D == 3 ? w2 * T.rw1[1][3 * K[1] + j1] : T.rw1[1][3 * K[1] + j1];
+#pragma unroll
+      for (int j0 = 0; j0 < 3; ++j0)
+        if (j0 < c0)
+          acc[0] += w12 * T.rw1[0][3 * K[0] + j0] * rf[gf.n_u + T.rk1[0][3 * K[0] + j0] + Nf1 * (V1 + (int64_t)Nf1 * V2)];
     }
-    bc[gc.n_u + (t - nnc)] = acc;
+  }
+  // every lane reaches the shuffles (groups of tl lanes are aligned in the warp)
+  for (int o = tl >> 1; o > 0; o >>= 1)
+#pragma unroll
+    for (int c = 0; c < D; ++c) acc[c] += __shfl_xor_sync(0xffffffffu, acc[c], o, tl);
+  if (sub != 0) return;
+  if (t < nnc) {
+#pragma unroll
+    for (int c = 0; c < D; ++c) bc[(int64_t)D * t + c] = acc[c];
+  } else if (t < nnc + (int)gc.n_p) {
+    bc[gc.n_u + (t - nnc)] = acc[0];
   }
 }
 
@@ -354,12 +376,13 @@ int dot_impl(rav_mg* mg, const double* a, const double* b, int64_t n, double* ou
 
 int restrict_impl(rav_mg* mg, int level, const double* rf, double* bc, cudaStream_t s) {
   const Level &F = mg->lev[level], &C = mg->lev[level - 1];
-  const int64_t tot = C.g.nnode + C.g.n_p;
+  const int tl = restrict_split(C.g);
+  const int64_t tot = (C.g.nnode + C.g.n_p) * tl;
   const int blocks = (int)((tot + 127) / 128);
   cudaEvent_t e0;
   RAV_TRY(prof_begin(mg, level, PROF_RESTRICT, s, &e0));
-  if (F.g.dim == 2) k_restrict_c<2><<<blocks, 128, 0, s>>>(F.g, C.g, F.tab(), rf, bc);
-  else k_restrict_c<3><<<blocks, 128, 0, s>>>(F.g, C.g, F.tab(), rf, bc);
+  if (F.g.dim == 2) k_restrict_c<2><<<blocks, 128, 0, s>>>(F.g, C.g, F.tab(), rf, bc, tl);
+  else k_restrict_c<3><<<blocks, 128, 0, s>>>(F.g, C.g, F.tab(), rf, bc, tl);
   note_launch();
   RAV_CUDA(cudaGetLastError());
   return prof_end(mg, level, PROF_RESTRICT, e0, s);
