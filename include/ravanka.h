@@ -198,11 +198,14 @@ int rav_coarse_solve(rav_mg* mg, const double* b_dev, double* x_dev, rav_stream 
  *   RAV: the rows of L_i^{-1} of the DoFs owned by i (Sec. 4.3), ownership =
  *        vertex floor(I/2) for a velocity DoF at Q2 node I, own vertex for p_i;
  *   AV, MV: all rows of L_i^{-1}.
- * precision selects the stored format of those rows (fp64, fp32, bf16, or fp8
- * e4m3 with an fp32 scale per row); reduced formats are applied with fp32
- * accumulation (RAV only).  omega is the damping of every subdomain (Eq. 11).
- * Synchronises the stream.  Errors: RAV_ERR_ARG, RAV_ERR_CUDA,
- * RAV_ERR_SINGULAR_PATCH. */
+ * precision is one of rav_precision: the rows themselves (RAV_F64_ROWS, or
+ * rounded into fp32 / bf16 / fp8 e4m3 with an fp32 scale per row), or the
+ * factored form of the block inverse (RAV_F64, RAV_F32_FACT, RAV_BF16_FACT);
+ * reduced formats are applied with fp32 accumulation (RAV only; AV and MV
+ * take RAV_F64 or RAV_F64_ROWS, both meaning fp64 full inverses).  omega is
+ * the damping of every subdomain (Eq. 11).  Also times the launch shapes of
+ * the factored apply (rav_set_apply_split).  Synchronises the stream.
+ * Errors: RAV_ERR_ARG, RAV_ERR_CUDA, RAV_ERR_SINGULAR_PATCH. */
 int vanka_setup(rav_mg* mg, int kind, int precision, double omega, rav_stream stream, rav_smoother** out);
 void vanka_destroy(rav_smoother* sm);
 

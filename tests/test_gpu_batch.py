@@ -98,3 +98,30 @@ def test_batched_solve_matches_single_solves():
             b = bs[p][:, k].contiguous()
             its, hist, rcs = mg.solve(sm, x, b, tol=1e-8, maxit=100)
             assert rcs == 0 and its == it[p, k]
+
+
+@pytest.mark.parametrize("prec", [R.F32, R.F64_ROWS])
+def test_batched_3d_cycles_equal_single_problem_cycles_bitwise(prec):
+    """Two 3-D problems of different depth (8^3 with 2 levels, 16^3 with 3),
+    blob viscosity, 2 right-hand sides each."""
+    nrhs = 2
+    mgs, sms, xs, bs = [], [], [], []
+    for i, (N, nlev) in enumerate([(8, 2), (16, 3)]):
+        mg = R.Multigrid(3, N, nlev, blobs=inputs.viscosity_blobs(40 + i, k=4, s_max=2.0), bc=R.BC_CAVITY)
+        sm = R.Smoother(mg, R.RAV, prec, 0.5)
+        b = np.stack([random_rhs(mg, 300 + 10 * i + k) for k in range(nrhs)], axis=1)
+        x0 = mg.initial_guess().cpu().numpy()
+        mgs.append(mg)
+        sms.append(sm)
+        xs.append(torch.from_numpy(np.ascontiguousarray(np.repeat(x0[:, None], nrhs, axis=1))).cuda())
+        bs.append(torch.from_numpy(np.ascontiguousarray(b)).cuda())
+    bt = R.Batch(mgs, sms, nrhs)
+    x_in = [x.clone() for x in xs]
+    bt.vcycle(xs, bs, 2, 2)
+    for p, (mg, sm) in enumerate(zip(mgs, sms)):
+        for lev in range(mg.nlev):
+            mg.residual_split(lev, 1)
+        for k in range(nrhs):
+            x = x_in[p][:, k].contiguous()
+            mg.vcycle(sm, x, bs[p][:, k].contiguous(), 2, 2)
+            assert torch.equal(x, xs[p][:, k]), (p, k)
