@@ -74,7 +74,7 @@ def parse():
     ap.add_argument("--no-single", action="store_true",
                     help="2d-batch: skip timing the single-problem FP64 form on the same problems")
     ap.add_argument("--workload", default="2d512",
-                    choices=sorted(WORKLOADS) + ["2d-batch", "3d-precision", "3d-learned"])
+                    choices=sorted(WORKLOADS) + ["2d-batch", "3d-precision", "3d-learned", "2d-steps"])
     ap.add_argument("--nprob", type=int, default=256, help="problems of the 2d-batch workload")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -575,6 +575,49 @@ def run_precision(args):
     print(json.dumps(out), flush=True)
 
 
+def run_steps(args):
+    """Smoothing-steps study (the paper's comparison of AV, MV and RAV over the
+    number of smoothing steps, Sec. 4.2, Fig. 7) on the 2-D 512^2 manufactured
+    Stokes problem (or --N): for nu = 1..6, a stationary V(nu, nu) solve to a
+    1e-8 residual reduction with RAV (omega 0.5, FP64 factored inverses), AV
+    (0.1) and coloured MV (0.66), all FP64; cycles, seconds and seconds per
+    cycle for each."""
+    import torch
+    import paper_2103_10127_gb300 as R
+
+    torch.cuda.set_device(0)
+    N = args.N or 512
+    nlev = args.levels or 7
+    mg = R.Multigrid(2, N, nlev, bc=R.BC_NOSLIP)
+    b = mg.rhs(R.F_PSI)
+    res = {}
+    for name, kind, omega in (("RAV", R.RAV, 0.5), ("AV", R.AV, 0.1), ("MV", R.MV_COLOURED, 0.66)):
+        sm = R.Smoother(mg, kind, R.F64, omega)
+        row = {}
+        for nu in range(1, 7):
+            x = mg.initial_guess()
+            mg.solve(sm, x, b, tol=1e-8, maxit=1, nu_pre=nu, nu_post=nu, raise_on_error=False)  # graphs, warm
+            x = mg.initial_guess()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            it, hist, rc = mg.solve(sm, x, b, tol=1e-8, maxit=300, nu_pre=nu, nu_post=nu, raise_on_error=False)
+            torch.cuda.synchronize()
+            dt = time.perf_counter() - t0
+            row[nu] = {"cycles": it, "status": rc, "seconds": dt, "ms_per_cycle": 1e3 * dt / max(it, 1),
+                       "rho": float(hist[-1] ** (1.0 / max(it, 1)))}
+        res[name] = row
+        del sm
+    best = {k: min((v for v in row.values() if v["status"] == 0), key=lambda v: v["seconds"], default=None)
+            for k, row in res.items()}
+    out = {"metric": "time to 1e-8 residual reduction per smoother and smoothing steps", "unit": "s",
+           "higher_is_better": False, "n_gpus": 1, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": f"2D Stokes Q2-Q1 {N}x{N}, {nlev} levels, manufactured psi solution, "
+                                  "stationary V(nu,nu), nu = 1..6", "dofs": mg.n()},
+           "results": res,
+           "best_seconds": {k: (v["seconds"] if v else None) for k, v in best.items()}}
+    print(json.dumps(out), flush=True)
+
+
 def run_learned(args):
     """Learned damping on 3-D 40^3 (or --N), 4 levels, 20 blobs with contrast
     up to 1e4 and z-graded cells of aspect 8 (seed 2103): the MLP is trained on
@@ -647,6 +690,9 @@ def main():
         return
     if args.workload == "3d-learned":
         run_learned(args)
+        return
+    if args.workload == "2d-steps":
+        run_steps(args)
         return
     W = dict(WORKLOADS[args.workload])
     if args.N:

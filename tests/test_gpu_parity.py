@@ -405,3 +405,19 @@ def test_full_size_512_sampled_parity():
         rows = orc.patch_rows(0, int(p))[: len(mine) * len(s)].reshape(len(mine), len(s))
         want = x[mine] + 0.5 * rows @ r[s]
         assert np.abs(got[mine] - want).max() <= 1e-12 * max(np.abs(want).max(), 1.0), p
+
+
+@pytest.mark.parametrize("nu", [1, 3])
+@pytest.mark.parametrize("kind,omega", [(R.RAV, 0.5), (R.AV, 0.1), (R.MV_COLOURED, 0.66)], ids=["rav", "av", "mv"])
+def test_smoothing_steps_study_matches_the_oracle(kind, omega, nu):
+    """The smoothing-steps comparison (Sec. 4.2) on a 16x16 cavity, 3 levels:
+    cycle counts equal and per-cycle convergence factors within 2 % for
+    V(nu, nu) with every smoother."""
+    mg, orc = make_pair(2, 16, 3)
+    sm = R.Smoother(mg, kind, R.F64, omega)
+    orc.setup_smoother({R.RAV: O.RAV, R.AV: O.AV, R.MV_COLOURED: O.MV_COLOURED}[kind], omega)
+    it, hist, rc = mg.solve(sm, mg.initial_guess(), mg.rhs(R.F_NONE), tol=1e-8, maxit=300, nu_pre=nu, nu_post=nu)
+    _, oit, ohist = orc.solve(orc.initial_guess(), orc.rhs(O.F_NONE), tol=1e-8, maxit=300, nu1=nu, nu2=nu)
+    assert rc == 0 and it == oit
+    fac, ofac = hist[1:] / hist[:-1], ohist[1:] / ohist[:-1]
+    assert np.all(np.abs(fac / ofac - 1.0) <= 0.02)
