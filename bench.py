@@ -698,7 +698,7 @@ def main():
     if args.N:
         W["N"] = args.N
         W["nlev"] = args.levels or W["nlev"]
-        W["desc"] += f" [size override: {args.N}x{args.N}, {W['nlev']} levels]"
+        W["desc"] += f" [size override: {args.N}^{W['dim']}, {W['nlev']} levels]"
     if args.impl == "reference":
         run_reference(args, W)
     else:
