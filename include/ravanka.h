@@ -291,7 +291,13 @@ typedef struct rav_solve_info {
 
 /* Solves L x = b from the given x (usually rav_initial_guess).  Host-driven:
  * synchronises once per V-cycle (stationary) or inner iteration (FGMRES) to
- * read the residual norm.  info may be NULL. */
+ * read the residual norm.  Stationary: each V-cycle replays a graph and starts
+ * from the residual just computed for the norm.  FGMRES (flexible GMRES, right
+ * preconditioned by one V-cycle from a zero guess, restarted every `restart`
+ * iterations) orthogonalises by classical Gram-Schmidt applied twice; the
+ * least-squares update runs on the host.  The residual norm, the Krylov
+ * vectors and the solution stay fp64 whatever the smoother's storage.
+ * info may be NULL. */
 int solve(rav_mg* mg, rav_smoother* sm, double* x_dev, const double* b_dev, const rav_solve_opts* opts,
           rav_solve_info* info, rav_stream stream);
 
