@@ -643,24 +643,45 @@ static int solve_stationary(rav_mg* mg, rav_smoother* sm, double* x, const doubl
   return rc;
 }
 
-// FGMRES(m), right-preconditioned by one V-cycle from a zero guess, modified
-// Gram-Schmidt with device dot products, Givens rotations on the host.
+// FGMRES(m), right-preconditioned by one V-cycle from a zero guess; classical
+// Gram-Schmidt applied twice with fused device dot products and updates,
+// Givens rotations on the host.  Work vectors: V (m+1 Krylov vectors), Z (m
+// preconditioned ones), w, a zero vector, the Hessenberg column and the dot
+// products' block partial sums (ndb per vector).
+struct FgmresWork {
+  double *V = nullptr, *Z = nullptr, *w = nullptr, *zero = nullptr, *hdev = nullptr, *dpart = nullptr;
+};
+static constexpr int kFgmresDotBlocks = 152 * 2;
+
+static int fgmres_run(rav_mg* mg, rav_smoother* sm, double* x, const double* b, const rav_solve_opts& o,
+                      rav_solve_info* info, cudaStream_t s, const FgmresWork& W);
+
 static int solve_fgmres(rav_mg* mg, rav_smoother* sm, double* x, const double* b, const rav_solve_opts& o,
                         rav_solve_info* info, cudaStream_t s) {
+  const int64_t n = mg->lev[mg->nlev - 1].g.n;
+  const int m = o.restart > 0 ? o.restart : 30;
+  FgmresWork W;
+  bool ok = cudaMallocAsync(&W.V, sizeof(double) * n * (m + 1), s) == cudaSuccess;
+  ok = ok && cudaMallocAsync(&W.Z, sizeof(double) * n * m, s) == cudaSuccess;
+  ok = ok && cudaMallocAsync(&W.w, sizeof(double) * n, s) == cudaSuccess;
+  ok = ok && cudaMallocAsync(&W.zero, sizeof(double) * n, s) == cudaSuccess;
+  ok = ok && cudaMallocAsync(&W.hdev, sizeof(double) * (2 * m + 3), s) == cudaSuccess;
+  ok = ok && cudaMallocAsync(&W.dpart, sizeof(double) * kFgmresDotBlocks * (m + 1), s) == cudaSuccess;
+  ok = ok && cudaMemsetAsync(W.zero, 0, sizeof(double) * n, s) == cudaSuccess;
+  const int rc = ok ? fgmres_run(mg, sm, x, b, o, info, s, W) : RAV_ERR_CUDA;
+  for (double* p : {W.V, W.Z, W.w, W.zero, W.hdev, W.dpart})
+    if (p) cudaFreeAsync(p, s);
+  return rc;
+}
+
+static int fgmres_run(rav_mg* mg, rav_smoother* sm, double* x, const double* b, const rav_solve_opts& o,
+                      rav_solve_info* info, cudaStream_t s, const FgmresWork& W) {
   const int fine = mg->nlev - 1;
   Level& L = mg->lev[fine];
   const int64_t n = L.g.n;
   const int m = o.restart > 0 ? o.restart : 30;
-  double *V = nullptr, *Z = nullptr, *w = nullptr, *zero = nullptr, *hdev = nullptr;
-  RAV_CUDA(cudaMallocAsync(&V, sizeof(double) * n * (m + 1), s));
-  RAV_CUDA(cudaMallocAsync(&Z, sizeof(double) * n * m, s));
-  RAV_CUDA(cudaMallocAsync(&w, sizeof(double) * n, s));
-  RAV_CUDA(cudaMallocAsync(&zero, sizeof(double) * n, s));
-  RAV_CUDA(cudaMallocAsync(&hdev, sizeof(double) * (2 * m + 3), s));
-  const int ndb = 152 * 2;  // blocks of the fused dot products
-  double* dpart = nullptr;
-  RAV_CUDA(cudaMallocAsync(&dpart, sizeof(double) * ndb * (m + 1), s));
-  RAV_CUDA(cudaMemsetAsync(zero, 0, sizeof(double) * n, s));
+  double *V = W.V, *Z = W.Z, *w = W.w, *zero = W.zero, *hdev = W.hdev, *dpart = W.dpart;
+  const int ndb = kFgmresDotBlocks;
   std::vector<double> H((m + 1) * m), cs(m), sn(m), gam(m + 1), y(m);
   const int gb = grid_for(n, 256, 152 * 16);
   double r0 = 0.0, beta = 0.0, ratio = 1.0;
@@ -746,12 +767,6 @@ static int solve_fgmres(rav_mg* mg, rav_smoother* sm, double* x, const double* b
       if (ratio <= o.tol) rc = RAV_OK;
     }
   }
-  cudaFreeAsync(V, s);
-  cudaFreeAsync(Z, s);
-  cudaFreeAsync(w, s);
-  cudaFreeAsync(zero, s);
-  cudaFreeAsync(hdev, s);
-  cudaFreeAsync(dpart, s);
   if (info) {
     info->iterations = it;
     info->final_ratio = ratio;

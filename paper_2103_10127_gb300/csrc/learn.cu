@@ -526,11 +526,15 @@ extern "C" int rav_set_learned_omega(rav_smoother* sm, const float* params, doub
     const int64_t np = sm->lev[l].np;
     float* feat = nullptr;
     RAV_CUDA(cudaMallocAsync(&feat, sizeof(float) * np * kF, s));
-    RAV_TRY(rav_patch_features(sm, l, feat, stream));
-    k_mlp_forward<<<(unsigned)((np + 127) / 128), 128, 0, s>>>(params, feat, np, nullptr, sm->lev[l].omega);
-    if (shrink < 1.0) k_shrink_to_mean<<<1, 1024, 0, s>>>(sm->lev[l].omega, np, shrink);
-    RAV_CUDA(cudaGetLastError());
-    RAV_CUDA(cudaFreeAsync(feat, s));
+    const int rc = rav_patch_features(sm, l, feat, stream);
+    if (rc == RAV_OK) {
+      k_mlp_forward<<<(unsigned)((np + 127) / 128), 128, 0, s>>>(params, feat, np, nullptr, sm->lev[l].omega);
+      if (shrink < 1.0) k_shrink_to_mean<<<1, 1024, 0, s>>>(sm->lev[l].omega, np, shrink);
+    }
+    const cudaError_t e = cudaGetLastError();
+    cudaFreeAsync(feat, s);
+    if (rc != RAV_OK) return rc;
+    RAV_CUDA(e);
   }
   return RAV_OK;
 }

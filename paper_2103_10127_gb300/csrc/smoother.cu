@@ -994,6 +994,12 @@ static int setup_level(rav_smoother* sm, int l, cudaStream_t s, int* err_dev) {
   const int64_t batch = std::min<int64_t>(S_.np, all ? 8192 : 32768);
   double* stage = nullptr;
   RAV_CUDA(cudaMallocAsync(&stage, sizeof(double) * batch * per, s));
+  // the staging buffer is released on every exit path below
+  struct StageFree {
+    double* p;
+    cudaStream_t s;
+    ~StageFree() { cudaFreeAsync(p, s); }
+  } stage_free{stage, s};
   const size_t smem = sizeof(double) * (B::NV * B::NV + 2 * B::NV * D + 32 * B::NV);
   auto kf = all ? k_factor<D, 1> : (fact ? k_factor<D, 2> : k_factor<D, 0>);
   RAV_CUDA(cudaFuncSetAttribute(kf, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
@@ -1031,7 +1037,6 @@ static int setup_level(rav_smoother* sm, int l, cudaStream_t s, int* err_dev) {
     }
     RAV_CUDA(cudaGetLastError());
   }
-  RAV_CUDA(cudaFreeAsync(stage, s));
   return RAV_OK;
 }
 
@@ -1376,8 +1381,9 @@ extern "C" int rav_get_patches(const rav_smoother* sm, int level, int32_t* off, 
   if (g.dim == 2) k_patch_list<2><<<gb, 128, 0, s>>>(g, off, dofs);
   else k_patch_list<3><<<gb, 128, 0, s>>>(g, off, dofs);
   k_owner<<<(int)((g.n + 255) / 256), 256, 0, s>>>(g, owner);
-  RAV_CUDA(cudaGetLastError());
-  RAV_CUDA(cudaFreeAsync(cnt, s));
+  const cudaError_t e = cudaGetLastError();
+  cudaFreeAsync(cnt, s);
+  RAV_CUDA(e);
   return RAV_OK;
 }
 
