@@ -390,9 +390,20 @@ __global__ void __launch_bounds__(128) k_rav_apply(Geo g, const T* __restrict__ 
 #pragma unroll
       for (int a0 = 0; a0 < 5; ++a0) {
         const bool vv = v1 && a0 >= alo[0] && a0 <= ahi[0];
+        Acc rn[D];
+        if constexpr (D == 2 && std::is_same<Acc, float>::value) {
+          // the two fp32 components of a node are one aligned 8-byte load
+          float2 rv = make_float2(0.f, 0.f);
+          if (vv) rv = *reinterpret_cast<const float2*>(r + rowoff + 2 * a0);
+          rn[0] = rv.x;
+          rn[1] = rv.y;
+        } else {
+#pragma unroll
+          for (int c = 0; c < D; ++c) rn[c] = vv ? r[rowoff + D * a0 + c] : (Acc)0;
+        }
 #pragma unroll
         for (int c = 0; c < D; ++c) {
-          const Acc ra = vv ? r[rowoff + D * a0 + c] : (Acc)0;
+          const Acc ra = rn[c];
 #pragma unroll
           for (int j = 0; j < RB; ++j) acc[j] += (Acc)Fmt<T>::dec(ip[(k * RB + j) * 32], lut) * ra;
           ++k;
@@ -533,8 +544,16 @@ __global__ void __launch_bounds__(128, fact_min_blocks<D, T>()) k_rav_apply_fact
         for (int a0 = 0; a0 < 5; ++a0) {
           const bool vv = v1 && a0 >= alo[0] && a0 <= ahi[0];
           const A kq = (A)Fmt<T>::dec(ld_stream(kp + n * G), nullptr);
+          if constexpr (D == 2 && std::is_same<A, float>::value) {
+            // the two fp32 components of a node are one aligned 8-byte load
+            float2 rv = make_float2(0.f, 0.f);
+            if (vv) rv = *reinterpret_cast<const float2*>(r + rowoff + 2 * a0);
+            y[0] += kq * rv.x;
+            y[1] += kq * rv.y;
+          } else {
 #pragma unroll
-          for (int c = 0; c < D; ++c) y[c] += kq * (vv ? r[rowoff + D * a0 + c] : (A)0);
+            for (int c = 0; c < D; ++c) y[c] += kq * (vv ? r[rowoff + D * a0 + c] : (A)0);
+          }
           ++n;
         }
       }
