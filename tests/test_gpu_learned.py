@@ -65,6 +65,30 @@ def test_labels_match_the_oracle():
     assert np.abs(y.cpu().numpy() - want).max() <= 1e-6
 
 
+def test_labels_match_the_oracle_in_3d_with_per_patch_weights():
+    """3-D graded blob problem, labels gathered at non-uniform current weights."""
+    spec = _problem(3, 6, 2, seed=12, s_max=3.0, aspect=4.0, nblobs=5)
+    mg = R.Multigrid(**spec)
+    sm = R.Smoother(mg, R.RAV, R.F64, 0.5)
+    npatch = mg.counts(1)["n_p"]
+    w = (0.2 + 0.8 * inputs.uniform(13, npatch)).astype(np.float32)
+    sm.set_omega(1, torch.from_numpy(w).cuda())
+    orc = O.Oracle(3, 6, 2, coords=spec["coords"], blobs=spec["blobs"], bc=O.BC_NOSLIP)
+    orc.build_patches(1)
+    n = mg.n(1)
+    x = inputs.normal(14, n)
+    b = inputs.normal(15, n)
+    from paper_2103_10127_gb300 import _capi
+    lib = _capi.load()
+    assert lib.rav_label_collection(sm.h, 1) == 0
+    sm.smooth(1, torch.from_numpy(x).cuda(), torch.from_numpy(b).cuda(), 1)
+    y = torch.empty(npatch, dtype=torch.float32, device="cuda")
+    assert lib.rav_read_labels(sm.h, 1, learned._p(y), learned._s()) == 0
+    assert lib.rav_label_collection(sm.h, 0) == 0
+    want = orc.labels(1, orc.residual(1, x, b), omega=w.astype(np.float64))
+    assert np.abs(y.cpu().numpy() - want).max() <= 1e-6
+
+
 def test_features_follow_their_definition():
     spec = _problem(2, 8, 2, seed=11, s_max=3.0, aspect=4.0, nblobs=3)
     mg = R.Multigrid(**spec)
