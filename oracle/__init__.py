@@ -31,6 +31,7 @@ RAV, AV, MV, MV_COLOURED = 0, 1, 2, 3
 F64, F32, BF16, FP8 = 0, 1, 2, 3
 F32_FACT, BF16_FACT = 5, 6  # factored storage rounded to fp32 / bf16
 BC_CAVITY, BC_NOSLIP, BC_QUADRATIC = 0, 1, 2
+ELEM_Q2Q1, ELEM_Q1Q1 = 0, 1  # Taylor-Hood; stabilised equal order (Eq. 8)
 F_NONE, F_PSI, F_SINKER, F_QUADRATIC = 0, 1, 2, 3
 
 
@@ -56,6 +57,7 @@ def _load():
         i, d, ll = ctypes.c_int, ctypes.c_double, ctypes.c_longlong
         sig = {
             "orc_create": (P, [i, i, i, P, d, i, P, i]),
+            "orc_create_elem": (P, [i, i, i, P, d, i, P, i, i, d]),
             "orc_destroy": (None, [P]),
             "orc_error": (i, [P]),
             "orc_count": (ll, [P, i, i]),
@@ -136,15 +138,20 @@ class Oracle:
     blobs:  optional (k, 5) array of (cx, cy, cz, rho, s) viscosity blobs,
             eta(x) = eta0 * 10**max_k s_k exp(-|x-c_k|^2 / (2 rho_k^2)).
     bc:     BC_CAVITY (lid u = e_0 on the top face), BC_NOSLIP, BC_QUADRATIC.
+    element: ELEM_Q2Q1 (Taylor-Hood, C = 0) or ELEM_Q1Q1 (equal order with the
+            pressure stabilisation C = -beta sum_e h_e^2 (grad q, grad p)_e, Eq. 8).
     """
 
-    def __init__(self, dim, N, nlev, coords=None, eta0=1.0, blobs=None, bc=BC_CAVITY):
+    def __init__(self, dim, N, nlev, coords=None, eta0=1.0, blobs=None, bc=BC_CAVITY,
+                 element=0, beta=0.0):
         lib = _load()
         self.dim, self.N, self.nlev = dim, N, nlev
+        self.element = element
         c = None if coords is None else _f64(coords).reshape(dim, N + 1)
         bl = np.zeros((0, 5)) if blobs is None else _f64(blobs).reshape(-1, 5)
         self._keep = (c, bl)
-        self.h = lib.orc_create(dim, N, nlev, _ptr(c), float(eta0), bl.shape[0], _ptr(bl), bc)
+        self.h = lib.orc_create_elem(dim, N, nlev, _ptr(c), float(eta0), bl.shape[0], _ptr(bl), bc,
+                                     int(element), float(beta))
 
     def check_coarse(self):
         """Factorises the bordered coarse system; raises if it is singular."""

@@ -6,9 +6,11 @@
 //
 // What it computes, and where it comes from (Saberi, Meschke, Vogel,
 // "A restricted additive Vanka smoother for geometric multigrid"):
-//   * Stokes saddle-point system L x = b, L = [A B; B^T 0]      (Sec. 2, Eqs. 5-7, 9)
-//       A = (eta grad v, grad u), B = -(div v, q), C = 0 for the inf-sup stable
-//       Q2-Q1 pair (Sec. 2, remark after Eq. 7).
+//   * Stokes saddle-point system L x = b, L = [A B; B^T C]      (Sec. 2, Eqs. 5-7, 9)
+//       A = (eta grad v, grad u), B = -(div v, q); C = 0 for the inf-sup stable
+//       Q2-Q1 pair (Sec. 2, remark after Eq. 7), and for the equal-order Q1-Q1
+//       pair the pressure stabilisation of Eq. 8,
+//       C = -beta sum_e h_e^2 (grad q, grad p)_e, h_e the cell diameter.
 //   * Vanka subdomains: pressure DoF p_i plus every velocity DoF of the cells
 //     around vertex i (Sec. 3, definition before Eq. 11), taken structurally.
 //   * Local systems L_i = R_i L R_i^T and their inverses (Sec. 3, Eq. 11).
@@ -65,6 +67,8 @@ struct Problem {
   double eta0 = 1.0;
   std::vector<double> blobs;  // per blob: cx, cy, cz, rho, s
   int bc = 0;                 // 0 lid-driven cavity, 1 no-slip, 2 quadratic exact solution
+  int elem = 0;               // 0 Q2-Q1 (C = 0), 1 stabilised Q1-Q1 (Eq. 8)
+  double beta = 0.0;          // stabilisation constant of Eq. 8 (Q1-Q1 only)
 };
 
 // Viscosity: eta0 * 10^(max_k s_k exp(-|x-c_k|^2 / (2 rho_k^2))), eta0 when no blobs.
@@ -127,8 +131,9 @@ double boundary_value(const Problem& P, const double* x, bool on_top, int c) {
 // ---------------------------------------------------------------------------
 struct Level {
   int dim = 2, N = 0;
+  int q = 2;                  // velocity degree: 2 (Q2-Q1) or 1 (Q1-Q1)
   std::vector<double> xv[3];  // vertex coordinates per axis, N+1 each
-  int64_t M = 0;              // Q2 nodes per axis, 2N+1
+  int64_t M = 0;              // velocity nodes per axis, q N + 1
   int64_t nnode = 0, n_u = 0, n_p = 0, n = 0;
   std::vector<uint8_t> dir;   // 1 = Dirichlet DoF
   std::vector<double> g;      // Dirichlet values (zero on coarse levels)
@@ -178,12 +183,13 @@ void vert_of(const Level& L, int64_t id, int64_t* v) {
   for (int a = 0; a < L.dim; ++a) { v[a] = id % (L.N + 1); id /= (L.N + 1); }
 }
 double node_coord(const Level& L, int a, int64_t I) {
+  if (L.q == 1) return L.xv[a][I];
   if (I % 2 == 0) return L.xv[a][I / 2];
   return 0.5 * (L.xv[a][(I - 1) / 2] + L.xv[a][(I + 1) / 2]);
 }
 bool node_on_boundary(const Level& L, const int64_t* I) {
   for (int a = 0; a < L.dim; ++a)
-    if (I[a] == 0 || I[a] == 2 * L.N) return true;
+    if (I[a] == 0 || I[a] == L.q * L.N) return true;
   return false;
 }
 
@@ -224,7 +230,8 @@ void tensor_loop(int dim, const int* cnt, F&& f) {
 struct Elem {
   int nl = 9, nv = 4;
   double K[27][27];
-  double B[3][27][8];  // B[comp][local Q2 node][local Q1 vertex] = -int psi_b d_comp phi_a
+  double B[3][27][8];  // B[comp][local velocity node][local Q1 vertex] = -int psi_b d_comp phi_a
+  double C[8][8];      // pressure block (Q1-Q1 only)
   double F[27][3];
 };
 
@@ -291,6 +298,69 @@ void element(const Oracle& O, const Level& L, const int64_t* c, int fkind, Elem&
   }
 }
 
+// Element matrices of the stabilised equal-order pair on cell c (Sec. 2, Eq. 7
+// with the pressure block of Eq. 8).  Velocity and pressure share the 2^d
+// bilinear (trilinear) vertex functions phi_a of the cell:
+//   K[a][b]    = int eta grad phi_a . grad phi_b
+//   B[c][a][b] = -int phi_b d_c phi_a
+//   C[a][b]    = -beta h_e^2 int grad phi_a . grad phi_b, h_e^2 = sum of squared cell sides
+//   F[a][c]    = int f_c phi_a
+// with the same 3^d-point Gauss rule as the Q2-Q1 element.
+void element_q1(const Oracle& O, const Level& L, const int64_t* c, int fkind, Elem& E) {
+  const int d = L.dim;
+  E.nl = d == 2 ? 4 : 8;
+  E.nv = E.nl;
+  std::memset(&E.K, 0, sizeof(E.K));
+  std::memset(&E.B, 0, sizeof(E.B));
+  std::memset(&E.C, 0, sizeof(E.C));
+  std::memset(&E.F, 0, sizeof(E.F));
+  double lo[3], h[3], diam2 = 0.0;
+  for (int a = 0; a < d; ++a) {
+    lo[a] = L.xv[a][c[a]];
+    h[a] = L.xv[a][c[a] + 1] - lo[a];
+    diam2 += h[a] * h[a];
+  }
+  const int nq = d == 2 ? 9 : 27;
+  for (int qp = 0; qp < nq; ++qp) {
+    int qt[3];
+    local_tuple(d, qp, 3, qt);
+    double xq[3] = {0, 0, 0}, W = 1.0;
+    for (int a = 0; a < d; ++a) {
+      xq[a] = lo[a] + h[a] * kGaussX[qt[a]];
+      W *= kGaussW[qt[a]] * h[a];
+    }
+    const double eta = viscosity(O.P, xq);
+    double fq[3];
+    forcing(O.P, fkind, xq, fq);
+    double phi[8], grad[8][3];
+    for (int A = 0; A < E.nl; ++A) {
+      int at[3];
+      local_tuple(d, A, 2, at);
+      double p = 1.0;
+      for (int a = 0; a < d; ++a) p *= q1(at[a], kGaussX[qt[a]]);
+      phi[A] = p;
+      for (int k = 0; k < d; ++k) {
+        double gk = (at[k] == 0 ? -1.0 : 1.0) / h[k];
+        for (int m = 0; m < d; ++m)
+          if (m != k) gk *= q1(at[m], kGaussX[qt[m]]);
+        grad[A][k] = gk;
+      }
+    }
+    for (int A = 0; A < E.nl; ++A) {
+      for (int A2 = 0; A2 < E.nl; ++A2) {
+        double s = 0.0;
+        for (int k = 0; k < d; ++k) s += grad[A][k] * grad[A2][k];
+        E.K[A][A2] += W * eta * s;
+        E.C[A][A2] += -O.P.beta * diam2 * W * s;
+      }
+      for (int cc = 0; cc < d; ++cc) {
+        for (int b = 0; b < E.nv; ++b) E.B[cc][A][b] += -W * phi[b] * grad[A][cc];
+        E.F[A][cc] += W * fq[cc] * phi[A];
+      }
+    }
+  }
+}
+
 // Position of column j in CSR row i (binary search); -1 if absent.
 int64_t find_col(const Level& L, int64_t i, int64_t j) {
   auto b = L.ci.begin() + L.rp[i], e = L.ci.begin() + L.rp[i + 1];
@@ -306,7 +376,7 @@ int64_t find_col(const Level& L, int64_t i, int64_t j) {
 //   pressure DoF = n_u + id_v.
 void init_level(const Oracle& O, Level& L) {
   const int d = L.dim;
-  L.M = 2 * L.N + 1;
+  L.M = L.q * L.N + 1;
   L.nnode = 1;
   int64_t nvert = 1;
   for (int a = 0; a < d; ++a) { L.nnode *= L.M; nvert *= (L.N + 1); }
@@ -321,7 +391,7 @@ void init_level(const Oracle& O, Level& L) {
     if (!node_on_boundary(L, I)) continue;
     double x[3] = {0, 0, 0};
     for (int a = 0; a < d; ++a) x[a] = node_coord(L, a, I[a]);
-    const bool top = I[d - 1] == 2 * L.N;
+    const bool top = I[d - 1] == L.q * L.N;
     for (int c = 0; c < d; ++c) {
       L.dir[d * id + c] = 1;
       L.g[d * id + c] = boundary_value(O.P, x, top, c);
@@ -388,6 +458,80 @@ void build_pattern(Level& L) {
   for (int64_t i = 0; i < L.n; ++i) std::copy(rows[i].begin(), rows[i].end(), L.ci.begin() + L.rp[i]);
 }
 
+// Structural sparsity of the Q1-Q1 operator (velocity nodes are the vertices):
+// a velocity row (v,c) couples to (w,c) and to p_w, and a pressure row v to
+// (w,c') for every c' and to p_w, for every vertex w of a cell containing v
+// (the p_w of a pressure row carry the stabilisation C); Dirichlet rows are
+// identity rows.
+void build_pattern_q1(Level& L) {
+  const int d = L.dim;
+  L.rp.assign(L.n + 1, 0);
+  std::vector<std::vector<int64_t>> rows(L.n);
+  for (int64_t i = 0; i < L.n; ++i) {
+    std::vector<int64_t>& cols = rows[i];
+    if (i < L.n_u && L.dir[i]) { cols.push_back(i); continue; }
+    const bool vel = i < L.n_u;
+    int64_t v[3];
+    vert_of(L, vel ? i / d : i - L.n_u, v);
+    int64_t cl[3][2];
+    int cnt[3] = {1, 1, 1};
+    for (int a = 0; a < d; ++a) cnt[a] = cells_of_vertex(v[a], L.N, cl[a]);
+    tensor_loop(d, cnt, [&](const int* k) {
+      int c2[3] = {2, 2, 2};
+      tensor_loop(d, c2, [&](const int* t) {
+        int64_t w[3];
+        for (int a = 0; a < d; ++a) w[a] = cl[a][k[a]] + t[a];
+        const int64_t id = vert_id(L, w);
+        if (vel) {
+          cols.push_back(d * id + i % d);
+        } else {
+          for (int cc = 0; cc < d; ++cc) cols.push_back(d * id + cc);
+        }
+        cols.push_back(L.n_u + id);
+      });
+    });
+    std::sort(cols.begin(), cols.end());
+    cols.erase(std::unique(cols.begin(), cols.end()), cols.end());
+  }
+  for (int64_t i = 0; i < L.n; ++i) L.rp[i + 1] = L.rp[i] + (int64_t)rows[i].size();
+  L.ci.resize(L.rp[L.n]);
+  L.va.assign(L.rp[L.n], 0.0);
+  for (int64_t i = 0; i < L.n; ++i) std::copy(rows[i].begin(), rows[i].end(), L.ci.begin() + L.rp[i]);
+}
+
+// Element-by-element assembly of the stabilised Q1-Q1 operator (Eqs. 7-8).
+void assemble_q1(const Oracle& O, Level& L) {
+  const int d = L.dim;
+  int cnt[3] = {L.N, L.N, L.N};
+  Elem E;
+  tensor_loop(d, cnt, [&](const int* ci) {
+    int64_t c[3] = {ci[0], ci[1], ci[2]};
+    element_q1(O, L, c, 0, E);
+    int64_t gn[8];
+    for (int A = 0; A < E.nl; ++A) {
+      int at[3];
+      local_tuple(d, A, 2, at);
+      int64_t w[3];
+      for (int a = 0; a < d; ++a) w[a] = c[a] + at[a];
+      gn[A] = vert_id(L, w);
+    }
+    for (int A = 0; A < E.nl; ++A) {
+      for (int cc = 0; cc < d; ++cc) {
+        const int64_t row = d * gn[A] + cc;
+        if (!L.dir[row]) {
+          for (int A2 = 0; A2 < E.nl; ++A2) L.va[find_col(L, row, d * gn[A2] + cc)] += E.K[A][A2];
+          for (int b = 0; b < E.nv; ++b) L.va[find_col(L, row, L.n_u + gn[b])] += E.B[cc][A][b];
+        }
+        for (int b = 0; b < E.nv; ++b) L.va[find_col(L, L.n_u + gn[b], row)] += E.B[cc][A][b];
+      }
+    }
+    for (int a = 0; a < E.nv; ++a)
+      for (int b = 0; b < E.nv; ++b) L.va[find_col(L, L.n_u + gn[a], L.n_u + gn[b])] += E.C[a][b];
+  });
+  for (int64_t i = 0; i < L.n_u; ++i)
+    if (L.dir[i]) L.va[find_col(L, i, i)] = 1.0;
+}
+
 // Standard element-by-element assembly of L (Eq. 7 on Q2-Q1, C = 0).
 void assemble(const Oracle& O, Level& L) {
   const int d = L.dim;
@@ -430,7 +574,8 @@ void assemble(const Oracle& O, Level& L) {
 // a fine Q2 node takes the value of the coarse piecewise-quadratic function at
 // its position (1-D Lagrange weights of the coarse cell that contains it,
 // tensorised); a fine pressure vertex takes the coarse piecewise-bilinear
-// (trilinear) value.  Rows of fine Dirichlet DoFs are empty.
+// (trilinear) value, and so does a fine Q1 velocity node.  Rows of fine
+// Dirichlet DoFs are empty.
 void build_prolongation(const Level& C, Level& F) {
   const int d = F.dim;
   F.Prp.assign(F.n + 1, 0);
@@ -455,11 +600,14 @@ void build_prolongation(const Level& C, Level& F) {
     node_of(F, id, I);
     int64_t K[3][3];
     double w[3][3];
-    for (int a = 0; a < d; ++a) q2w(a, I[a], K[a], w[a]);
+    for (int a = 0; a < d; ++a) {
+      if (F.q == 2) q2w(a, I[a], K[a], w[a]);
+      else q1w(a, I[a], K[a], w[a]);
+    }
     for (int cc = 0; cc < d; ++cc) {
       const int64_t row = d * id + cc;
       if (F.dir[row]) continue;
-      int c3[3] = {3, 3, 3};
+      int c3[3] = {F.q + 1, F.q + 1, F.q + 1};
       tensor_loop(d, c3, [&](const int* t) {
         int64_t J[3];
         double ww = 1.0;
@@ -533,12 +681,13 @@ void lu_solve(const std::vector<double>& a, int64_t n, const std::vector<int64_t
 }
 
 // ---------------------------------------------------------------------------
-// Subdomains (Sec. 3): S_i = {p_i} u {velocity DoFs of every Q2 node of every
-// cell containing vertex i} minus Dirichlet DoFs, sorted ascending.
-// Ownership (the restricted set of Eq. 13 extended to Q2): a velocity DoF at
-// node I is owned by vertex floor(I/2) (componentwise), i.e. a vertex node by
-// its own vertex and an edge/face/cell node by the lowest vertex of its
-// entity; p_i is owned by i; Dirichlet DoFs have no owner.
+// Subdomains (Sec. 3): S_i = {p_i} u {velocity DoFs of every velocity node of
+// every cell containing vertex i} minus Dirichlet DoFs, sorted ascending.
+// Ownership (the restricted set of Eq. 13): on Q1-Q1 the velocity DoFs of
+// vertex i itself (the paper's rule); extended to Q2, a velocity DoF at node I
+// is owned by vertex floor(I/2) (componentwise), i.e. a vertex node by its own
+// vertex and an edge/face/cell node by the lowest vertex of its entity; p_i is
+// owned by i; Dirichlet DoFs have no owner.
 void build_patches(Level& L) {
   const int d = L.dim;
   L.poff.assign(L.n_p + 1, 0);
@@ -547,7 +696,7 @@ void build_patches(Level& L) {
   for (int64_t id = 0; id < L.nnode; ++id) {
     int64_t I[3], v[3];
     node_of(L, id, I);
-    for (int a = 0; a < d; ++a) v[a] = I[a] / 2;
+    for (int a = 0; a < d; ++a) v[a] = I[a] / L.q;
     for (int c = 0; c < d; ++c)
       if (!L.dir[d * id + c]) L.owner[d * id + c] = vert_id(L, v);
   }
@@ -560,10 +709,10 @@ void build_patches(Level& L) {
     int cnt[3] = {1, 1, 1};
     for (int a = 0; a < d; ++a) cnt[a] = cells_of_vertex(v[a], L.N, cl[a]);
     tensor_loop(d, cnt, [&](const int* k) {
-      int c3[3] = {3, 3, 3};
+      int c3[3] = {L.q + 1, L.q + 1, L.q + 1};
       tensor_loop(d, c3, [&](const int* t) {
         int64_t J[3];
-        for (int a = 0; a < d; ++a) J[a] = 2 * cl[a][k[a]] + t[a];
+        for (int a = 0; a < d; ++a) J[a] = L.q * cl[a][k[a]] + t[a];
         for (int c = 0; c < d; ++c) {
           int64_t dof = d * node_id(L, J) + c;
           if (!L.dir[dof]) s.push_back(dof);
@@ -659,8 +808,9 @@ double fmt_scale(int prec, const double* row, int64_t n) {
 }
 
 // Factored storage of the owned rows (prec 5: fp32, 6: bf16).  The local
-// system of Eq. 11 has the saddle-point form L_i = [A b; b^T 0] (one pressure
-// DoF, the last in sorted order), so with w = A^{-1} b and s = -b^T w
+// system of Eq. 11 has the saddle-point form L_i = [A b; b^T c] (one pressure
+// DoF, the last in sorted order; c = 0 on Q2-Q1, the diagonal entry of the
+// stabilisation of Eq. 8 on Q1-Q1), so with w = A^{-1} b and s = c - b^T w
 //   L_i^{-1} = [A^{-1} + w w^T / s,  -w / s;  -w^T / s,  1 / s].
 // The owned rows of A^{-1}, w and 1/s are rounded to the format, then the owned
 // rows of L_i^{-1} are rebuilt from the rounded values by that formula in fp64.
@@ -681,7 +831,7 @@ bool factored_rows(const Level& L, int64_t p, int fmt, std::vector<double>& out)
   std::vector<int64_t> piv2;
   if (!lu_factor(Tt, nv, piv2)) return false;
   lu_solve(Tt, nv, piv2, w.data());
-  double s = 0.0;
+  double s = Li[nv * ni + nv];
   for (int64_t r = 0; r < nv; ++r) s -= Li[nv * ni + r] * w[r];
   if (s == 0.0) return false;
   const double sig = fmt_round(fmt, 1.0 / s);
@@ -889,18 +1039,22 @@ double norm2(const std::vector<double>& v) {
 extern "C" {
 
 // coords: dim*(N+1) vertex coordinates of the finest level, axis-major; NULL = uniform on [0,1].
-// blobs: nblobs*5 (cx, cy, cz, rho, s).
-void* orc_create(int dim, int N, int nlev, const double* coords, double eta0, int nblobs,
-                 const double* blobs, int bc) {
+// blobs: nblobs*5 (cx, cy, cz, rho, s).  elem: 0 Q2-Q1, 1 stabilised Q1-Q1 with
+// constant beta (Eq. 8).
+void* orc_create_elem(int dim, int N, int nlev, const double* coords, double eta0, int nblobs,
+                      const double* blobs, int bc, int elem, double beta) {
   Oracle* O = new Oracle();
   O->P.dim = dim;
   O->P.eta0 = eta0;
   O->P.bc = bc;
+  O->P.elem = elem;
+  O->P.beta = elem == 1 ? beta : 0.0;
   O->P.blobs.assign(blobs, blobs + 5 * nblobs);
   O->lev.resize(nlev);
   for (int l = nlev - 1; l >= 0; --l) {
     Level& L = O->lev[l];
     L.dim = dim;
+    L.q = elem == 1 ? 1 : 2;
     const int stride = 1 << (nlev - 1 - l);
     L.N = N / stride;
     for (int a = 0; a < dim; ++a) {
@@ -910,11 +1064,20 @@ void* orc_create(int dim, int N, int nlev, const double* coords, double eta0, in
     }
     init_level(*O, L);
     if (l != nlev - 1) std::fill(L.g.begin(), L.g.end(), 0.0);
-    build_pattern(L);
-    assemble(*O, L);
+    if (L.q == 1) {
+      build_pattern_q1(L);
+      assemble_q1(*O, L);
+    } else {
+      build_pattern(L);
+      assemble(*O, L);
+    }
   }
   for (int l = 1; l < nlev; ++l) build_prolongation(O->lev[l - 1], O->lev[l]);
   return O;
+}
+void* orc_create(int dim, int N, int nlev, const double* coords, double eta0, int nblobs,
+                 const double* blobs, int bc) {
+  return orc_create_elem(dim, N, nlev, coords, eta0, nblobs, blobs, bc, 0, 0.0);
 }
 
 void orc_destroy(void* h) { delete (Oracle*)h; }
@@ -970,12 +1133,13 @@ void orc_rhs(void* h, int fkind, double* b) {
   Elem E;
   tensor_loop(d, cnt, [&](const int* ci) {
     int64_t c[3] = {ci[0], ci[1], ci[2]};
-    element(O, L, c, fkind, E);
+    if (L.q == 1) element_q1(O, L, c, fkind, E);
+    else element(O, L, c, fkind, E);
     for (int A = 0; A < E.nl; ++A) {
       int at[3];
-      local_tuple(d, A, 3, at);
+      local_tuple(d, A, L.q + 1, at);
       int64_t J[3];
-      for (int a = 0; a < d; ++a) J[a] = 2 * c[a] + at[a];
+      for (int a = 0; a < d; ++a) J[a] = L.q * c[a] + at[a];
       const int64_t id = node_id(L, J);
       for (int cc = 0; cc < d; ++cc) b[d * id + cc] += E.F[A][cc];
     }
