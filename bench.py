@@ -52,6 +52,17 @@ WORKLOADS = {
                       "sinker forcing, no-slip, RAV V(2,2) omega 0.5, FP64 factored inverses"),
     "3d32-bf16": dict(dim=3, N=32, nlev=4, bc=1, forcing=2, kind=0, prec=6, omega=0.5, nu=2, blobs=(20, 3.0),
                       desc="as 3d32 with the factored inverses stored in BF16 (FP32 accumulation)"),
+    "2d1024-q1": dict(dim=2, N=1024, nlev=8, bc=0, forcing=0, kind=0, prec=0, omega=0.66, nu=2, elem=1,
+                      beta=0.02, desc="2D Stokes stabilised Q1-Q1 (beta 0.02) 1024x1024 lid-driven cavity, "
+                                      "8 levels, viscosity 1, RAV V(2,2) omega 0.66, FP64 factored inverses"),
+    "2d1024-q1-f32": dict(dim=2, N=1024, nlev=8, bc=0, forcing=0, kind=0, prec=5, omega=0.66, nu=2, elem=1,
+                          beta=0.02, desc="as 2d1024-q1 with the factored inverses stored in FP32 "
+                                          "(FP32 accumulation)"),
+    "3d64-q1": dict(dim=3, N=64, nlev=5, bc=1, forcing=2, kind=0, prec=0, omega=0.66, nu=2, blobs=(20, 2.0),
+                    elem=1, beta=0.02,
+                    desc="3D Stokes stabilised Q1-Q1 (beta 0.02) 64^3 unit cube, 5 levels, 20 seeded viscosity "
+                         "blobs (contrast <= 1e2), sinker forcing, no-slip, RAV V(2,2) omega 0.66, FP64 "
+                         "factored inverses"),
 }
 STORAGE = {0: "f64 factored", 1: "f32 rows", 2: "bf16 rows", 3: "fp8 rows", 4: "f64 rows", 5: "f32 factored",
            6: "bf16 factored"}
@@ -107,10 +118,12 @@ def replicas_value(ws, dofs, steps, ms):
 
 
 # ---------------------------------------------------------------------------
-def patch_work(dim, N, prec, n):
+def patch_work(dim, N, prec, n, q=2):
     """Algorithmic (flops, bytes) of one fine-level subdomain apply, counting
     only the DoFs inside each subdomain (compact sizes, Sec. 4.3): n_i DoFs,
-    ñ_i owned rows, nodes_i velocity nodes, own_i owned velocity nodes.
+    ñ_i owned rows, nodes_i velocity nodes, own_i owned velocity nodes
+    (q = 2: Q2-Q1 boxes of 5^d nodes owning up to 2^d; q = 1: Q1-Q1 boxes of
+    3^d vertices owning the centre).
       dense rows:  ñ_i n_i FMAs and stored entries per subdomain;
       factored:    d own_i nodes_i + d nodes_i + d own_i + 1 FMAs and
                    own_i nodes_i + d nodes_i + 1 stored values (fp64, fp32 or bf16).
@@ -118,8 +131,12 @@ def patch_work(dim, N, prec, n):
     import numpy as np
     per_n, per_o = [], []
     for v in range(N + 1):
-        per_n.append(sum(1 for a in range(5) if 1 <= 2 * v - 2 + a <= 2 * N - 1))
-        per_o.append(sum(1 for a in (2, 3) if 1 <= 2 * v + a - 2 <= 2 * N - 1))
+        if q == 1:
+            per_n.append(sum(1 for a in range(3) if 1 <= v - 1 + a <= N - 1))
+            per_o.append(1 if 1 <= v <= N - 1 else 0)
+        else:
+            per_n.append(sum(1 for a in range(5) if 1 <= 2 * v - 2 + a <= 2 * N - 1))
+            per_o.append(sum(1 for a in (2, 3) if 1 <= 2 * v + a - 2 <= 2 * N - 1))
     pn, po = np.array(per_n, float), np.array(per_o, float)
     if dim == 2:
         nodes, own = np.outer(pn, pn), np.outer(po, po)
@@ -205,7 +222,8 @@ def cpu_baseline(W, cycles=1):
     `cycles` timed V-cycles on one host core."""
     import oracle as O
     import numpy as np
-    orc = O.Oracle(W["dim"], W["N"], W["nlev"], bc=W["bc"], blobs=make_blobs(W))
+    orc = O.Oracle(W["dim"], W["N"], W["nlev"], bc=W["bc"], blobs=make_blobs(W), element=W.get("elem", 0),
+                   beta=W.get("beta", 0.0))
     orc.setup_smoother(O.RAV, W["omega"], W["prec"] if W["prec"] in (1, 2, 3, 5, 6) else 0)
     b = orc.rhs(W["forcing"])
     x = orc.initial_guess()
@@ -223,7 +241,8 @@ def run_reference(args, W):
     if rank != 0:
         return
     import oracle as O
-    orc = O.Oracle(W["dim"], W["N"], W["nlev"], bc=W["bc"], blobs=make_blobs(W))
+    orc = O.Oracle(W["dim"], W["N"], W["nlev"], bc=W["bc"], blobs=make_blobs(W), element=W.get("elem", 0),
+                   beta=W.get("beta", 0.0))
     orc.setup_smoother(O.RAV, W["omega"], W["prec"] if W["prec"] in (1, 2, 3, 5, 6) else 0)
     b = orc.rhs(W["forcing"])
     x = orc.initial_guess()
@@ -260,7 +279,8 @@ def run_ours(args, W):
     lib = _capi.load()
     stream = torch.cuda.current_stream()
 
-    mg = R.Multigrid(W["dim"], W["N"], W["nlev"], bc=W["bc"], blobs=make_blobs(W))
+    mg = R.Multigrid(W["dim"], W["N"], W["nlev"], bc=W["bc"], blobs=make_blobs(W), element=W.get("elem", 0),
+                     beta=W.get("beta", 0.0))
     sm = R.Smoother(mg, W["kind"], W["prec"], W["omega"])
     fine = W["nlev"] - 1
     n = mg.n()
@@ -332,7 +352,8 @@ def run_ours(args, W):
     value = replicas_value(ws, n, args.steps, ms)
 
     # ---- roofline of the dominant kernel: fine-level subdomain apply ----
-    flops, bytes_alg, stored = patch_work(W["dim"], W["N"], W["prec"], n)
+    q1 = W.get("elem", 0) == 1
+    flops, bytes_alg, stored = patch_work(W["dim"], W["N"], W["prec"], n, q=1 if q1 else 2)
     if W["prec"] in (0, 4):  # fp64 arithmetic: bound by the FP64 pipes, not HBM
         roof = {"bound": "alu", "achieved": flops / (apply_ms / 1e3) / 1e12, "peak": FP64_PEAK_TFLOPS,
                 "unit": "TFLOP/s"}
@@ -343,7 +364,8 @@ def run_ours(args, W):
     roof["frac"] = roof["achieved"] / roof["peak"]
     traffic = measured_traffic(f"rav_apply_{args.workload}")
     roof["traffic"] = traffic
-    roof["kernel"] = ("k_rav_apply_fact" if W["prec"] in (0, 5, 6) else "k_rav_apply") + " (fine level)"
+    roof["kernel"] = ("k_rav_apply_q1" if q1 else "k_rav_apply_fact" if W["prec"] in (0, 5, 6)
+                      else "k_rav_apply") + " (fine level)"
     roof["launch_ms"] = apply_ms
     roof["launches_timed"] = apply_launches
     roof["algorithmic_bytes"] = bytes_alg

@@ -3,10 +3,12 @@
  *
  * Method: Saberi, Meschke, Vogel, "A restricted additive Vanka smoother for
  * geometric multigrid".  The library solves the Stokes saddle-point system
- * L x = b, L = [A B; B^T 0] (Sec. 2, Eqs. 5-7 and 9) discretised with
- * inf-sup-stable Q2-Q1 (Taylor-Hood) elements (C = 0, Sec. 2 after Eq. 7) on
- * tensor-product box grids, by a geometric multigrid V-cycle (Sec. 2, Fig. 1)
- * whose smoother is one of
+ * L x = b, L = [A B; B^T C] (Sec. 2, Eqs. 5-7 and 9) discretised with
+ * inf-sup-stable Q2-Q1 (Taylor-Hood) elements (C = 0, Sec. 2 after Eq. 7), or
+ * with the paper's own equal-order Q1-Q1 pair and the pressure stabilisation
+ * C = -beta sum_e h_e^2 (grad q, grad p)_e of Eq. 8, on tensor-product box
+ * grids, by a geometric multigrid V-cycle (Sec. 2, Fig. 1) whose smoother is
+ * one of
  *   RAV  restricted additive Vanka, Eq. 13 (the method of the paper),
  *   AV   additive Vanka, Eq. 12,
  *   MV   multiplicative Vanka, Eq. 11, run in a 4^d-coloured patch order,
@@ -19,7 +21,9 @@
  *      velocity DoF = d*id + c (components interleaved per node),
  *      pressure vertex v in [0,N]^d, id = v0 + (N+1)(v1 + (N+1) v2),
  *      pressure DoF = n_u + id, n_u = d (2N+1)^d, n = n_u + (N+1)^d.
- *  * Every boundary Q2 node is a Dirichlet node for all components.  Its row
+ *    On Q1-Q1 the velocity nodes are the vertices: node id = vertex id,
+ *      n_u = d (N+1)^d.
+ *  * Every boundary velocity node is a Dirichlet node for all components.  Its row
  *    of L is the identity row; the residual is defined as 0 there; the
  *    Dirichlet value lives in x (no lifting).
  *  * Level 0 is the coarsest, level n_levels-1 the finest (N cells per axis);
@@ -60,6 +64,9 @@ enum {
 };
 
 enum rav_bc { RAV_BC_CAVITY = 0, RAV_BC_NOSLIP = 1, RAV_BC_QUADRATIC = 2 };
+/* Discretisation: Taylor-Hood Q2-Q1 (C = 0), or equal-order Q1-Q1 with the
+ * pressure stabilisation of Eq. 8. */
+enum rav_element { RAV_ELEM_Q2Q1 = 0, RAV_ELEM_Q1Q1 = 1 };
 enum rav_forcing { RAV_F_NONE = 0, RAV_F_PSI = 1, RAV_F_SINKER = 2, RAV_F_QUADRATIC = 3 };
 enum rav_smoother_kind { RAV_RAV = 0, RAV_AV = 1, RAV_MV_COLOURED = 3 };
 /* Storage of the RAV inverse rows.  RAV_F64: fp64, factored through the block
@@ -90,7 +97,10 @@ enum rav_precision {
  *               with blobs_host = nblobs * (cx, cy, cz, rho, s); eta0 if nblobs = 0.
  *  bc:          RAV_BC_CAVITY (u = e_0 on the face x_{d-1} = 1, edges and corners
  *               of that face included, 0 elsewhere), RAV_BC_NOSLIP (u = 0),
- *               RAV_BC_QUADRATIC (u = (y^2, x^2) in 2-D, (y^2, z^2, x^2) in 3-D). */
+ *               RAV_BC_QUADRATIC (u = (y^2, x^2) in 2-D, (y^2, z^2, x^2) in 3-D).
+ *  element:     rav_element (zero-initialised structs get Q2-Q1).
+ *  beta:        the constant of Eq. 8 (Q1-Q1 only; finite, >= 0; h_e is the
+ *               cell diameter).  Ignored for Q2-Q1. */
 typedef struct rav_problem {
   int dim;
   int N;
@@ -99,11 +109,14 @@ typedef struct rav_problem {
   int nblobs;
   const double* blobs_host;
   int bc;
+  int element;
+  double beta;
 } rav_problem;
 
-/* Builds the hierarchy: per level the Q2-Q1 operator of Eq. 7 assembled from
- * 3^d-point Gauss quadrature (the paper assembles on every grid, Sec. 4), the
- * interpolation tables of the nested Q2/Q1 spaces, and on level 0 the explicit
+/* Builds the hierarchy: per level the operator of Eq. 7 (Q2-Q1, or Q1-Q1 with
+ * the C of Eq. 8) assembled from 3^d-point Gauss quadrature (the paper
+ * assembles on every grid, Sec. 4), the interpolation tables of the nested
+ * velocity (Q2 or Q1) and Q1 pressure spaces, and on level 0 the explicit
  * inverse of the bordered system [L e_p; e_p^T 0] for the LU coarse solve of
  * Sec. 2.  Requires N divisible by 2^(n_levels-1) and a coarsest grid of at
  * least 2 cells per axis.  Synchronises the stream before returning.
@@ -179,7 +192,7 @@ int rav_residual_norm_noalloc(rav_mg* mg, int level, const double* x_dev, const 
                               double* norm_dev, rav_stream stream);
 
 /* Grid transfers between level l-1 (coarse) and l (fine), canonical nested
- * interpolation P of the Q2 velocity and Q1 pressure spaces (the paper builds
+ * interpolation P of the velocity (Q2 or Q1) and Q1 pressure spaces (the paper builds
  * its transfers from the grid hierarchy, Sec. 2):
  *   rav_restrict:   bc = P^T rf, then 0 on coarse Dirichlet rows;
  *   rav_prolong_add: xf += P xc on free fine DoFs (fine Dirichlet DoFs untouched). */
@@ -205,6 +218,13 @@ int rav_coarse_solve(rav_mg* mg, const double* b_dev, double* x_dev, rav_stream 
  * take RAV_F64 or RAV_F64_ROWS, both meaning fp64 full inverses).  omega is
  * the damping of every subdomain (Eq. 11).  Also times the launch shapes of
  * the factored apply (rav_set_apply_split).  Synchronises the stream.
+ * On a Q1-Q1 hierarchy subdomain i holds p_i and the free velocity DoFs of the
+ * 3^d vertices around vertex i and owns exactly the velocity DoFs of vertex i
+ * and p_i (the paper's restricted set, Sec. 3); only RAV with the factored
+ * storage (RAV_F64, RAV_F32_FACT, RAV_BF16_FACT) is offered there, with
+ * s = c_ii - b^T A^{-1} b (c_ii the stabilisation's diagonal entry), one
+ * thread per subdomain and no apply split; other kinds and formats return
+ * RAV_ERR_ARG.
  * Errors: RAV_ERR_ARG, RAV_ERR_CUDA, RAV_ERR_SINGULAR_PATCH. */
 int vanka_setup(rav_mg* mg, int kind, int precision, double omega, rav_stream stream, rav_smoother** out);
 void vanka_destroy(rav_smoother* sm);
@@ -218,8 +238,8 @@ void vanka_destroy(rav_smoother* sm);
  * subdomain nodes, so setting it regroups them on the device (synchronises
  * the stream, allocates and frees one copy) and drops the captured V-cycle
  * graphs of this smoother.  Results differ only in the order of additions.
- * RAV_ERR_ARG for other values, levels or storage.  rav_get_apply_split
- * returns the current value (or RAV_ERR_ARG). */
+ * RAV_ERR_ARG for other values, levels or storage (on Q1-Q1 only 1 is
+ * accepted).  rav_get_apply_split returns the current value (or RAV_ERR_ARG). */
 int rav_set_apply_split(rav_smoother* sm, int level, int split, rav_stream stream);
 int rav_get_apply_split(const rav_smoother* sm, int level);
 
@@ -237,7 +257,8 @@ int rav_get_patches(const rav_smoother* sm, int level, int32_t* offsets_dev, int
 /* Stored inverse rows of subdomains [first, first+count) of level l, expanded
  * to fp64 (scale applied) in the sorted DoF order of each subdomain, into
  * out_dev[count][rows_max][cols_max] (zero padded); rows_max/cols_max are
- * 2^d d + 1 and 5^d d + 1 for RAV, 5^d d + 1 for both otherwise. */
+ * 2^d d + 1 and 5^d d + 1 for RAV, 5^d d + 1 for both otherwise, and d + 1 and
+ * 3^d d + 1 on a Q1-Q1 hierarchy. */
 int rav_get_inverse_rows(const rav_smoother* sm, int level, int64_t first, int64_t count, double* out_dev,
                          rav_stream stream);
 

@@ -1,4 +1,4 @@
-"""GB300 restricted additive Vanka (RAV) multigrid for Q2-Q1 Stokes.
+"""GB300 restricted additive Vanka (RAV) multigrid for Q2-Q1 and stabilised Q1-Q1 Stokes.
 
 Python binding of the C ABI in include/ravanka.h.  Every numerical step runs
 in the CUDA library (libravanka.so); this module only marshals torch device
@@ -20,11 +20,12 @@ from ._capi import RavError, check
 RAV, AV, MV_COLOURED = 0, 1, 3
 F64, F32, BF16, FP8, F64_ROWS, F32_FACT, BF16_FACT = 0, 1, 2, 3, 4, 5, 6
 BC_CAVITY, BC_NOSLIP, BC_QUADRATIC = 0, 1, 2
+ELEM_Q2Q1, ELEM_Q1Q1 = 0, 1
 F_NONE, F_PSI, F_SINKER, F_QUADRATIC = 0, 1, 2, 3
 
 __all__ = ["Multigrid", "Smoother", "Batch", "RavError", "RAV", "AV", "MV_COLOURED", "F64", "F32", "BF16", "FP8", "F64_ROWS",
            "F32_FACT", "BF16_FACT",
-           "BC_CAVITY", "BC_NOSLIP", "BC_QUADRATIC", "F_NONE", "F_PSI", "F_SINKER", "F_QUADRATIC"]
+           "BC_CAVITY", "BC_NOSLIP", "BC_QUADRATIC", "ELEM_Q2Q1", "ELEM_Q1Q1", "F_NONE", "F_PSI", "F_SINKER", "F_QUADRATIC"]
 
 
 def _torch():
@@ -47,18 +48,24 @@ def _ptr(t):
 
 
 class Multigrid:
-    """Grid hierarchy and assembled operators (mg_setup)."""
+    """Grid hierarchy and assembled operators (mg_setup).
 
-    def __init__(self, dim, N, n_levels, coords=None, eta0=1.0, blobs=None, bc=BC_CAVITY, stream=None):
+    element: ELEM_Q2Q1 (Taylor-Hood) or ELEM_Q1Q1 (equal order with the
+    pressure stabilisation of Eq. 8, constant beta)."""
+
+    def __init__(self, dim, N, n_levels, coords=None, eta0=1.0, blobs=None, bc=BC_CAVITY, element=ELEM_Q2Q1,
+                 beta=0.0, stream=None):
         lib = _capi.load()
         self._coords = None if coords is None else np.ascontiguousarray(coords, np.float64).reshape(-1)
         self._blobs = np.zeros((0, 5)) if blobs is None else np.ascontiguousarray(blobs, np.float64).reshape(-1, 5)
         prob = _capi.RavProblem(dim, N, None if self._coords is None else self._coords.ctypes.data, float(eta0),
-                                self._blobs.shape[0], self._blobs.ctypes.data if self._blobs.size else None, bc)
+                                self._blobs.shape[0], self._blobs.ctypes.data if self._blobs.size else None, bc,
+                                int(element), float(beta))
         h = ctypes.c_void_p()
         check(lib.mg_setup(ctypes.byref(prob), n_levels, _stream(stream), ctypes.byref(h)), "mg_setup")
         self.h = h
         self.dim, self.N, self.nlev = dim, N, n_levels
+        self.element = element
 
     def __del__(self):
         if getattr(self, "h", None) is not None and _capi._lib is not None:
@@ -264,8 +271,11 @@ class Smoother:
 
     def inverse_rows(self, level, first, count, stream=None):
         d = self.mg.dim
-        nc = 5 ** d * d + 1
-        nr = (2 ** d * d + 1) if self.kind == RAV else nc
+        if self.mg.element == ELEM_Q1Q1:
+            nc, nr = 3 ** d * d + 1, d + 1
+        else:
+            nc = 5 ** d * d + 1
+            nr = (2 ** d * d + 1) if self.kind == RAV else nc
         out = _torch().empty((count, nr, nc), dtype=_torch().float64, device="cuda")
         check(_capi.load().rav_get_inverse_rows(self.h, level, first, count, _ptr(out), _stream(stream)),
               "rav_get_inverse_rows")

@@ -20,7 +20,7 @@ ERRORS = {
 
 class RavProblem(ctypes.Structure):
     _fields_ = [("dim", I32), ("N", I32), ("coords_host", P), ("eta0", F64), ("nblobs", I32),
-                ("blobs_host", P), ("bc", I32)]
+                ("blobs_host", P), ("bc", I32), ("element", I32), ("beta", F64)]
 
 
 class RavSolveOpts(ctypes.Structure):

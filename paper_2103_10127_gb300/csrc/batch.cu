@@ -831,6 +831,7 @@ extern "C" int batch_setup(rav_mg* const* mgs, rav_smoother* const* sms, int npr
   for (int p = 0; p < nprob; ++p) {
     if (!mgs[p] || !sms[p] || sms[p]->mg != mgs[p] || mgs[p]->dim != dim || mgs[p]->nlev < 2) return RAV_ERR_ARG;
     if (sms[p]->kind != RAV_RAV || sms[p]->prec != prec) return RAV_ERR_ARG;
+    if (mgs[p]->elem != RAV_ELEM_Q2Q1) return RAV_ERR_ARG;  // the batched kernels are Q2-Q1 only
   }
   if (prec != RAV_F32 && prec != RAV_F64_ROWS) return RAV_ERR_ARG;
   cudaStream_t s = S(stream);

@@ -36,7 +36,8 @@ constexpr int kMaxLevels = 16;
 struct Geo {
   int dim;
   int N;
-  int64_t M;      // Q2 nodes per axis, 2N + 1
+  int q;          // velocity degree: 2 (Q2-Q1) or 1 (stabilised Q1-Q1, velocity nodes = vertices)
+  int64_t M;      // velocity nodes per axis, q N + 1
   int64_t nnode;  // M^dim
   int64_t n_u, n_p, n;
   const double* xv[3];  // device vertex coordinates per axis (N + 1)
@@ -97,6 +98,8 @@ struct rav_mg {
   int dim = 2, N = 0, nlev = 0;
   double eta0 = 1.0;
   int bc = 0;
+  int elem = RAV_ELEM_Q2Q1;  // discretisation (rav_element)
+  double beta = 0.0;         // stabilisation constant of Eq. 8 (Q1-Q1)
   std::vector<double> blobs;   // host copy
   double* blobs_dev = nullptr;
   int nblobs = 0;
@@ -191,7 +194,7 @@ __host__ __device__ inline int64_t ipow(int64_t b, int e) {
   return r;
 }
 
-// Q2 node tuple of velocity DoF i (i < n_u) and its component.
+// Velocity node tuple of velocity DoF i (i < n_u) and its component.
 __device__ inline void vel_node(const Geo& g, int64_t i, int64_t* I, int& c) {
   int64_t id = i / g.dim;
   c = (int)(i - id * g.dim);
@@ -199,7 +202,7 @@ __device__ inline void vel_node(const Geo& g, int64_t i, int64_t* I, int& c) {
 }
 __device__ inline bool node_on_boundary(const Geo& g, const int64_t* I) {
   bool b = false;
-  for (int a = 0; a < g.dim; ++a) b |= (I[a] == 0) | (I[a] == 2 * g.N);
+  for (int a = 0; a < g.dim; ++a) b |= (I[a] == 0) | (I[a] == g.M - 1);
   return b;
 }
 __device__ inline bool is_dirichlet(const Geo& g, int64_t i) {
@@ -238,6 +241,7 @@ __device__ inline int64_t vert_id(const Geo& g, const int64_t* v) {
   return id;
 }
 __device__ inline double node_coord(const Geo& g, int a, int64_t I) {
+  if (g.q == 1) return g.xv[a][I];
   return (I & 1) ? 0.5 * (g.xv[a][(I - 1) >> 1] + g.xv[a][(I + 1) >> 1]) : g.xv[a][I >> 1];
 }
 

@@ -279,6 +279,94 @@ __global__ void k_restrict_c(Geo gf, Geo gc, XferTab T, const double* __restrict
   }
 }
 
+// Q1-Q1 transfers: velocity and pressure share the vertex tables (pc1/pk1/pw1
+// and their transposes rc1/rk1/rw1); one thread per vertex carries the d
+// velocity components and the pressure.  Prolongation skips fine boundary
+// (Dirichlet) velocity nodes; restriction leaves fine boundary velocity nodes
+// out of the sums and writes 0 on coarse boundary velocity rows.
+template <int D>
+__global__ void k_prolong_q1(Geo gf, Geo gc, XferTab T, const double* __restrict__ xc, double* __restrict__ xf) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (int)gf.n_p) return;
+  const int Nf1 = gf.N + 1, Nc1 = gc.N + 1;
+  int v[3] = {0, 0, 0}, id = t;
+  bool bnd = false;
+  for (int a = 0; a < D; ++a) {
+    v[a] = id % Nf1;
+    id /= Nf1;
+    bnd |= (v[a] == 0) | (v[a] == gf.N);
+  }
+  const int c0 = T.pc1[0][v[0]], c1 = T.pc1[1][v[1]], c2 = D == 3 ? T.pc1[2][v[2]] : 1;
+  double acc[D + 1];
+#pragma unroll
+  for (int c = 0; c <= D; ++c) acc[c] = 0.0;
+  for (int j2 = 0; j2 < c2; ++j2) {
+    const int K2 = D == 3 ? T.pk1[2][2 * v[2] + j2] : 0;
+    const double w2 = D == 3 ? T.pw1[2][2 * v[2] + j2] : 1.0;
+    for (int j1 = 0; j1 < c1; ++j1) {
+      const int K1 = T.pk1[1][2 * v[1] + j1];
+      const double w12 = D == 3 ? w2 * T.pw1[1][2 * v[1] + j1] : T.pw1[1][2 * v[1] + j1];
+#pragma unroll
+      for (int j0 = 0; j0 < 2; ++j0)
+        if (j0 < c0) {
+          const double ww = w12 * T.pw1[0][2 * v[0] + j0];
+          const int K = T.pk1[0][2 * v[0] + j0] + Nc1 * (K1 + Nc1 * K2);
+#pragma unroll
+          for (int c = 0; c < D; ++c) acc[c] += ww * xc[(int64_t)D * K + c];
+          acc[D] += ww * xc[gc.n_u + K];
+        }
+    }
+  }
+  if (!bnd) {
+#pragma unroll
+    for (int c = 0; c < D; ++c) xf[(int64_t)D * t + c] += acc[c];
+  }
+  xf[gf.n_u + t] += acc[D];
+}
+
+template <int D>
+__global__ void k_restrict_q1(Geo gf, Geo gc, XferTab T, const double* __restrict__ rf, double* __restrict__ bc) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (int)gc.n_p) return;
+  const int Nf1 = gf.N + 1, Nc1 = gc.N + 1;
+  int K[3] = {0, 0, 0}, id = t;
+  bool cbnd = false;
+  for (int a = 0; a < D; ++a) {
+    K[a] = id % Nc1;
+    id /= Nc1;
+    cbnd |= (K[a] == 0) | (K[a] == gc.N);
+  }
+  const int c0 = T.rc1[0][K[0]], c1 = T.rc1[1][K[1]], c2 = D == 3 ? T.rc1[2][K[2]] : 1;
+  double acc[D + 1];
+#pragma unroll
+  for (int c = 0; c <= D; ++c) acc[c] = 0.0;
+  for (int j2 = 0; j2 < c2; ++j2) {
+    const int V2 = D == 3 ? T.rk1[2][3 * K[2] + j2] : 0;
+    const double w2 = D == 3 ? T.rw1[2][3 * K[2] + j2] : 1.0;
+    const bool b2 = D == 3 && (V2 == 0 || V2 == gf.N);
+    for (int j1 = 0; j1 < c1; ++j1) {
+      const int V1 = T.rk1[1][3 * K[1] + j1];
+      const double w12 = D == 3 ? w2 * T.rw1[1][3 * K[1] + j1] : T.rw1[1][3 * K[1] + j1];
+      const bool b1 = b2 || V1 == 0 || V1 == gf.N;
+#pragma unroll
+      for (int j0 = 0; j0 < 3; ++j0)
+        if (j0 < c0) {
+          const int V0 = T.rk1[0][3 * K[0] + j0];
+          const double ww = w12 * T.rw1[0][3 * K[0] + j0];
+          const int64_t V = V0 + Nf1 * (V1 + (int64_t)Nf1 * V2);
+          if (!(b1 || V0 == 0 || V0 == gf.N)) {
+#pragma unroll
+            for (int c = 0; c < D; ++c) acc[c] += ww * rf[(int64_t)D * V + c];
+          }
+          acc[D] += ww * rf[gf.n_u + V];
+        }
+    }
+  }
+#pragma unroll
+  for (int c = 0; c < D; ++c) bc[(int64_t)D * t + c] = cbnd ? 0.0 : acc[c];
+  bc[gc.n_u + t] = acc[D];
+}
+
 // Coarse solve x = C[:, :n] (b masked to free rows): one warp per row.
 __global__ void k_mask_free(Geo g, const double* __restrict__ b, double* __restrict__ bm) {
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -376,6 +464,16 @@ int dot_impl(rav_mg* mg, const double* a, const double* b, int64_t n, double* ou
 
 int restrict_impl(rav_mg* mg, int level, const double* rf, double* bc, cudaStream_t s) {
   const Level &F = mg->lev[level], &C = mg->lev[level - 1];
+  if (F.g.q == 1) {
+    const int blocks = (int)((C.g.n_p + 127) / 128);
+    cudaEvent_t e0;
+    RAV_TRY(prof_begin(mg, level, PROF_RESTRICT, s, &e0));
+    if (F.g.dim == 2) k_restrict_q1<2><<<blocks, 128, 0, s>>>(F.g, C.g, F.tab(), rf, bc);
+    else k_restrict_q1<3><<<blocks, 128, 0, s>>>(F.g, C.g, F.tab(), rf, bc);
+    note_launch();
+    RAV_CUDA(cudaGetLastError());
+    return prof_end(mg, level, PROF_RESTRICT, e0, s);
+  }
   const int tl = restrict_split(C.g);
   const int64_t tot = (C.g.nnode + C.g.n_p) * tl;
   const int blocks = (int)((tot + 127) / 128);
@@ -390,6 +488,16 @@ int restrict_impl(rav_mg* mg, int level, const double* rf, double* bc, cudaStrea
 
 int prolong_impl(rav_mg* mg, int level, const double* xc, double* xf, cudaStream_t s) {
   const Level &F = mg->lev[level], &C = mg->lev[level - 1];
+  if (F.g.q == 1) {
+    const int blocks = (int)((F.g.n_p + 127) / 128);
+    cudaEvent_t e0;
+    RAV_TRY(prof_begin(mg, level, PROF_PROLONG, s, &e0));
+    if (F.g.dim == 2) k_prolong_q1<2><<<blocks, 128, 0, s>>>(F.g, C.g, F.tab(), xc, xf);
+    else k_prolong_q1<3><<<blocks, 128, 0, s>>>(F.g, C.g, F.tab(), xc, xf);
+    note_launch();
+    RAV_CUDA(cudaGetLastError());
+    return prof_end(mg, level, PROF_PROLONG, e0, s);
+  }
   const int64_t tot = F.g.nnode + F.g.n_p;
   const int blocks = (int)((tot + 127) / 128);
   cudaEvent_t e0;

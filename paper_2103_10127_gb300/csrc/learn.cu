@@ -404,6 +404,7 @@ extern "C" int rav_mlp_nparam(void) { return kNParam; }
 
 extern "C" int rav_patch_features(rav_smoother* sm, int level, float* feat, rav_stream stream) {
   if (!sm || !feat || level < 1 || level >= sm->mg->nlev) return RAV_ERR_ARG;
+  if (sm->mg->elem != RAV_ELEM_Q2Q1) return RAV_ERR_ARG;  // features and labels of the Q2-Q1 subdomains
   rav_mg* mg = sm->mg;
   const Geo& g = mg->lev[level].g;
   Coef C{mg->eta0, mg->nblobs, mg->blobs_dev};
@@ -416,7 +417,7 @@ extern "C" int rav_patch_features(rav_smoother* sm, int level, float* feat, rav_
 
 extern "C" int rav_label_collection(rav_smoother* sm, int enable) {
   if (!sm) return RAV_ERR_ARG;
-  if (sm->kind != RAV_RAV) return RAV_ERR_ARG;
+  if (sm->kind != RAV_RAV || sm->mg->elem != RAV_ELEM_Q2Q1) return RAV_ERR_ARG;
   rav_mg* mg = sm->mg;
   sm->collect = enable != 0;
   if (!sm->collect) return RAV_OK;

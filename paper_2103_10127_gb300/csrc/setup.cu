@@ -530,7 +530,7 @@ __global__ void k_rhs(Geo g, int bc, const double* __restrict__ Fe, double* __re
   if (node_on_boundary(g, I)) {
     double x[3] = {0, 0, 0};
     for (int a = 0; a < D; ++a) x[a] = node_coord(g, a, I[a]);
-    b[i] = boundary_value(bc, D, x, I[D - 1] == 2 * g.N, c);
+    b[i] = boundary_value(bc, D, x, I[D - 1] == g.M - 1, c);
     return;
   }
   int64_t elo[3] = {0, 0, 0}, ehi[3] = {0, 0, 0};
@@ -563,10 +563,260 @@ __global__ void k_initial_guess(Geo g, int bc, double* __restrict__ x) {
     if (node_on_boundary(g, I)) {
       double xx[3] = {0, 0, 0};
       for (int a = 0; a < D; ++a) xx[a] = node_coord(g, a, I[a]);
-      v = boundary_value(bc, D, xx, I[D - 1] == 2 * g.N, c);
+      v = boundary_value(bc, D, xx, I[D - 1] == g.M - 1, c);
     }
   }
   x[i] = v;
+}
+
+// ---------------------------------------------------------------------------
+// Stabilised Q1-Q1 (Sec. 2, Eq. 7 with the pressure block of Eq. 8).
+// Velocity and pressure share the 2^d vertex functions phi_A of a cell, local
+// vertex A = a0 + 2 a1 + 4 a2, quadrature point q = q0 + 3 q1 + 9 q2 (the
+// 3^d-point Gauss rule of the Q2-Q1 element):
+//   Ke[e][A][A2]   = sum_q W_q eta_q grad phi_A . grad phi_A2
+//   Be[e][c][A][b] = -sum_q W_q phi_b d_c phi_A     (velocity A, pressure b)
+//   Ce[e][A][A2]   = -beta h_e^2 sum_q W_q grad phi_A . grad phi_A2,
+// h_e^2 the squared cell diameter (the sum of the squared sides).
+template <int D>
+__global__ void k_q1_cell_matrices(Geo g, Coef C, double beta, double* __restrict__ Ke, double* __restrict__ Be,
+                                   double* __restrict__ Ce) {
+  constexpr int NL = 1 << D, NQ = D == 2 ? 9 : 27;
+  __shared__ double grad[NL][NQ][D];
+  __shared__ double phi[NL][NQ];
+  __shared__ double W[NQ], eW[NQ];
+  const int64_t e = blockIdx.x;
+  int64_t c[3] = {0, 0, 0};
+  {
+    int64_t t = e;
+    for (int a = 0; a < D; ++a) { c[a] = t % g.N; t /= g.N; }
+  }
+  double lo[3], h[3], diam2 = 0.0;
+  for (int a = 0; a < D; ++a) {
+    lo[a] = g.xv[a][c[a]];
+    h[a] = g.xv[a][c[a] + 1] - lo[a];
+    diam2 += h[a] * h[a];
+  }
+  const int t = threadIdx.x;
+  if (t < NQ) {
+    const int qt[3] = {t % 3, (t / 3) % 3, t / 9};
+    double x[3] = {0, 0, 0}, w = 1.0;
+    for (int a = 0; a < D; ++a) {
+      x[a] = lo[a] + h[a] * gauss_x(qt[a]);
+      w *= gauss_w(qt[a]) * h[a];
+    }
+    W[t] = w;
+    eW[t] = w * viscosity_at(C, D, x);
+  }
+  if (t < NL) {
+    const int at[3] = {t & 1, (t >> 1) & 1, t >> 2};
+    for (int q = 0; q < NQ; ++q) {
+      const int qt[3] = {q % 3, (q / 3) % 3, q / 9};
+      double v = 1.0;
+      for (int a = 0; a < D; ++a) v *= lag1(at[a], gauss_x(qt[a]));
+      phi[t][q] = v;
+      for (int k = 0; k < D; ++k) {
+        double d = (at[k] ? 1.0 : -1.0) / h[k];
+        for (int m = 0; m < D; ++m)
+          if (m != k) d *= lag1(at[m], gauss_x(qt[m]));
+        grad[t][q][k] = d;
+      }
+    }
+  }
+  __syncthreads();
+  if (t < NL) {
+    for (int A2 = 0; A2 < NL; ++A2) {
+      double sk = 0.0, sl = 0.0;
+      for (int q = 0; q < NQ; ++q) {
+        double dd = 0.0;
+        for (int k = 0; k < D; ++k) dd += grad[t][q][k] * grad[A2][q][k];
+        sk += eW[q] * dd;
+        sl += W[q] * dd;
+      }
+      Ke[(e * NL + t) * NL + A2] = sk;
+      Ce[(e * NL + t) * NL + A2] = -beta * diam2 * sl;
+    }
+    for (int cc = 0; cc < D; ++cc)
+      for (int b = 0; b < NL; ++b) {
+        double sb = 0.0;
+        for (int q = 0; q < NQ; ++q) sb += -W[q] * phi[b][q] * grad[t][q][cc];
+        Be[((e * D + cc) * NL + t) * NL + b] = sb;
+      }
+  }
+}
+
+// Element load vectors Fe[e][A][c] = sum_q W_q f_c(x_q) phi_A(x_q) (Q1-Q1).
+template <int D>
+__global__ void k_q1_cell_load(Geo g, Coef C, int kind, double* __restrict__ Fe) {
+  constexpr int NL = 1 << D, NQ = D == 2 ? 9 : 27;
+  __shared__ double fW[NQ][D];
+  const int64_t e = blockIdx.x;
+  int64_t c[3] = {0, 0, 0};
+  {
+    int64_t t = e;
+    for (int a = 0; a < D; ++a) { c[a] = t % g.N; t /= g.N; }
+  }
+  double lo[3], h[3];
+  for (int a = 0; a < D; ++a) {
+    lo[a] = g.xv[a][c[a]];
+    h[a] = g.xv[a][c[a] + 1] - lo[a];
+  }
+  const int t = threadIdx.x;
+  if (t < NQ) {
+    const int qt[3] = {t % 3, (t / 3) % 3, t / 9};
+    double x[3] = {0, 0, 0}, w = 1.0, f[3];
+    for (int a = 0; a < D; ++a) {
+      x[a] = lo[a] + h[a] * gauss_x(qt[a]);
+      w *= gauss_w(qt[a]) * h[a];
+    }
+    body_force(C, kind, D, x, f);
+    for (int cc = 0; cc < D; ++cc) fW[t][cc] = w * f[cc];
+  }
+  __syncthreads();
+  if (t < NL) {
+    const int at[3] = {t & 1, (t >> 1) & 1, t >> 2};
+    for (int cc = 0; cc < D; ++cc) {
+      double s = 0.0;
+      for (int q = 0; q < NQ; ++q) {
+        const int qt[3] = {q % 3, (q / 3) % 3, q / 9};
+        double ph = 1.0;
+        for (int a = 0; a < D; ++a) ph *= lag1(at[a], gauss_x(qt[a]));
+        s += fW[q][cc] * ph;
+      }
+      Fe[(e * NL + t) * D + cc] = s;
+    }
+  }
+}
+
+// Q1-Q1 rows.  A free velocity row (I, c) couples to (J, c) and to p_J, and a
+// pressure row v to (J, c') for every c' and to p_J, for J in [I-1, I+1] per
+// axis clipped to [0, N] (the vertices of the cells around I); a Dirichlet
+// row is the identity row.  Columns ascend: velocity J lexicographic (axis 0
+// fastest, components inside a node), then pressure J.
+__device__ __forceinline__ void q1_range(const Geo& g, int64_t I, int64_t& lo, int64_t& hi) {
+  lo = I - 1 < 0 ? 0 : I - 1;
+  hi = I + 1 > g.N ? g.N : I + 1;
+}
+// Cells (per axis) containing both vertices I and J, and the local index of I in cell e.
+__device__ __forceinline__ void q1_shared(const Geo& g, int64_t I, int64_t J, int64_t& lo, int64_t& hi) {
+  const int64_t mx = I > J ? I : J, mn = I < J ? I : J;
+  lo = mx - 1 < 0 ? 0 : mx - 1;
+  hi = mn > g.N - 1 ? g.N - 1 : mn;
+}
+
+__global__ void k_q1_row_len(Geo g, int64_t* __restrict__ len) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= g.n) return;
+  const bool vel = i < g.n_u;
+  int64_t id = vel ? i / g.dim : i - g.n_u;
+  int64_t L = 1;
+  bool bnd = false;
+  for (int a = 0; a < g.dim; ++a) {
+    const int64_t Ia = id % (g.N + 1);
+    id /= (g.N + 1);
+    bnd |= (Ia == 0) | (Ia == g.N);
+    int64_t lo, hi;
+    q1_range(g, Ia, lo, hi);
+    L *= hi - lo + 1;
+  }
+  len[i] = vel ? (bnd ? 1 : 2 * L) : (g.dim + 1) * L;
+}
+
+template <int D>
+__global__ void k_q1_assemble(Geo g, const double* __restrict__ Ke, const double* __restrict__ Be,
+                              const double* __restrict__ Ce, const int64_t* __restrict__ rp,
+                              int32_t* __restrict__ ci, double* __restrict__ va) {
+  constexpr int NL = 1 << D;
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= g.n) return;
+  int64_t pos = rp[i];
+  const bool vel = i < g.n_u;
+  const int c = vel ? (int)(i % D) : 0;
+  int64_t I[3] = {0, 0, 0};
+  {
+    int64_t id = vel ? i / D : i - g.n_u;
+    for (int a = 0; a < D; ++a) { I[a] = id % (g.N + 1); id /= (g.N + 1); }
+  }
+  if (vel) {
+    bool bnd = false;
+    for (int a = 0; a < D; ++a) bnd |= (I[a] == 0) | (I[a] == g.N);
+    if (bnd) {
+      ci[pos] = (int32_t)i;
+      va[pos] = 1.0;
+      return;
+    }
+  }
+  int64_t lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0};
+  for (int a = 0; a < D; ++a) q1_range(g, I[a], lo[a], hi[a]);
+  // block 0: velocity columns, block 1: pressure columns
+  for (int blk = 0; blk < 2; ++blk)
+    for (int64_t J2 = (D == 3 ? lo[2] : 0); J2 <= (D == 3 ? hi[2] : 0); ++J2)
+      for (int64_t J1 = lo[1]; J1 <= hi[1]; ++J1)
+        for (int64_t J0 = lo[0]; J0 <= hi[0]; ++J0) {
+          const int64_t J[3] = {J0, J1, J2};
+          int64_t elo[3] = {0, 0, 0}, ehi[3] = {0, 0, 0};
+          for (int a = 0; a < D; ++a) q1_shared(g, I[a], J[a], elo[a], ehi[a]);
+          const int ncomp = (!vel && blk == 0) ? D : 1;
+          for (int cc = 0; cc < ncomp; ++cc) {
+            double s = 0.0;
+            for (int64_t e2 = elo[2]; e2 <= ehi[2]; ++e2)
+              for (int64_t e1 = elo[1]; e1 <= ehi[1]; ++e1)
+                for (int64_t e0 = elo[0]; e0 <= ehi[0]; ++e0) {
+                  const int64_t ec[3] = {e0, e1, e2};
+                  int64_t e = 0;
+                  int A = 0, A2 = 0;
+                  for (int a = D - 1; a >= 0; --a) {
+                    e = e * g.N + ec[a];
+                    A = A * 2 + (int)(I[a] - ec[a]);
+                    A2 = A2 * 2 + (int)(J[a] - ec[a]);
+                  }
+                  if (vel && blk == 0) s += Ke[(e * NL + A) * NL + A2];
+                  else if (vel) s += Be[((e * D + c) * NL + A) * NL + A2];
+                  else if (blk == 0) s += Be[((e * D + cc) * NL + A2) * NL + A];
+                  else s += Ce[(e * NL + A) * NL + A2];
+                }
+            int64_t jid = 0;
+            for (int a = D - 1; a >= 0; --a) jid = jid * (g.N + 1) + J[a];
+            ci[pos] = (int32_t)(blk == 0 ? D * jid + (vel ? c : cc) : g.n_u + jid);
+            va[pos] = s;
+            ++pos;
+          }
+        }
+}
+
+// Q1-Q1 right-hand side: a free velocity row sums its cells' load entries
+// (ascending cell order), Dirichlet rows get g, pressure rows 0.
+template <int D>
+__global__ void k_q1_rhs(Geo g, int bc, const double* __restrict__ Fe, double* __restrict__ b) {
+  constexpr int NL = 1 << D;
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= g.n) return;
+  if (i >= g.n_u) { b[i] = 0.0; return; }
+  int64_t I[3] = {0, 0, 0};
+  int c;
+  vel_node(g, i, I, c);
+  if (node_on_boundary(g, I)) {
+    double x[3] = {0, 0, 0};
+    for (int a = 0; a < D; ++a) x[a] = node_coord(g, a, I[a]);
+    b[i] = boundary_value(bc, D, x, I[D - 1] == g.M - 1, c);
+    return;
+  }
+  int64_t elo[3] = {0, 0, 0}, ehi[3] = {0, 0, 0};
+  for (int a = 0; a < D; ++a) q1_shared(g, I[a], I[a], elo[a], ehi[a]);
+  double s = 0.0;
+  for (int64_t e2 = elo[2]; e2 <= ehi[2]; ++e2)
+    for (int64_t e1 = elo[1]; e1 <= ehi[1]; ++e1)
+      for (int64_t e0 = elo[0]; e0 <= ehi[0]; ++e0) {
+        const int64_t ec[3] = {e0, e1, e2};
+        int64_t e = 0;
+        int A = 0;
+        for (int a = D - 1; a >= 0; --a) {
+          e = e * g.N + ec[a];
+          A = A * 2 + (int)(I[a] - ec[a]);
+        }
+        s += Fe[(e * NL + A) * D + c];
+      }
+  b[i] = s;
 }
 
 // ---------------------------------------------------------------------------
@@ -666,7 +916,8 @@ __global__ void k_gj_eliminate(double* __restrict__ A, double* __restrict__ Inv,
 static int level_geometry(rav_mg* mg, Level& L, int N, const double* fine_coords, int stride) {
   L.g.dim = mg->dim;
   L.g.N = N;
-  L.g.M = 2 * (int64_t)N + 1;
+  L.g.q = mg->elem == RAV_ELEM_Q1Q1 ? 1 : 2;
+  L.g.M = L.g.q * (int64_t)N + 1;
   L.g.nnode = ipow(L.g.M, mg->dim);
   L.g.n_u = mg->dim * L.g.nnode;
   L.g.n_p = ipow(N + 1, mg->dim);
@@ -734,21 +985,29 @@ static int build_sell(Level& L, cudaStream_t s) {
 static int assemble_level(rav_mg* mg, Level& L, cudaStream_t s) {
   const Geo& g = L.g;
   const int D = g.dim;
-  const int NL = D == 2 ? 9 : 27, NV = D == 2 ? 4 : 8;
+  const bool q1 = g.q == 1;
+  const int NL = q1 ? (1 << D) : (D == 2 ? 9 : 27), NV = D == 2 ? 4 : 8;
   const int64_t ncell = ipow(g.N, D);
-  double *Ke = nullptr, *Be = nullptr;
+  double *Ke = nullptr, *Be = nullptr, *Ce = nullptr;
   RAV_CUDA(cudaMallocAsync(&Ke, sizeof(double) * ncell * NL * NL, s));
   RAV_CUDA(cudaMallocAsync(&Be, sizeof(double) * ncell * D * NL * NV, s));
+  if (q1) RAV_CUDA(cudaMallocAsync(&Ce, sizeof(double) * ncell * NL * NL, s));
   Coef C{mg->eta0, mg->nblobs, mg->blobs_dev};
-  if (D == 2) k_cell_matrices<2><<<(unsigned)ncell, 32, 0, s>>>(g, C, Ke, Be);
-  else k_cell_matrices<3><<<(unsigned)ncell, 32, 0, s>>>(g, C, Ke, Be);
+  if (q1) {
+    if (D == 2) k_q1_cell_matrices<2><<<(unsigned)ncell, 32, 0, s>>>(g, C, mg->beta, Ke, Be, Ce);
+    else k_q1_cell_matrices<3><<<(unsigned)ncell, 32, 0, s>>>(g, C, mg->beta, Ke, Be, Ce);
+  } else {
+    if (D == 2) k_cell_matrices<2><<<(unsigned)ncell, 32, 0, s>>>(g, C, Ke, Be);
+    else k_cell_matrices<3><<<(unsigned)ncell, 32, 0, s>>>(g, C, Ke, Be);
+  }
   RAV_CUDA(cudaGetLastError());
   // row lengths -> exclusive scan -> row pointer
   RAV_CUDA(cudaMalloc(&L.rp, sizeof(int64_t) * (g.n + 1)));
   const int nb = (int)((g.n + 1023) / 1024);
   int64_t* bsum = nullptr;
   RAV_CUDA(cudaMallocAsync(&bsum, sizeof(int64_t) * (nb + 1), s));
-  k_row_len<<<nb * 4, 256, 0, s>>>(g, L.rp);
+  if (q1) k_q1_row_len<<<nb * 4, 256, 0, s>>>(g, L.rp);
+  else k_row_len<<<nb * 4, 256, 0, s>>>(g, L.rp);
   k_scan_blocks<<<nb, 1024, 0, s>>>(L.rp, g.n, bsum);
   k_scan_sums<<<1, 32, 0, s>>>(bsum, nb);
   k_scan_add<<<nb, 1024, 0, s>>>(L.rp, g.n, bsum);
@@ -759,11 +1018,17 @@ static int assemble_level(rav_mg* mg, Level& L, cudaStream_t s) {
   RAV_CUDA(cudaMalloc(&L.ci, sizeof(int32_t) * L.nnz));
   RAV_CUDA(cudaMalloc(&L.va, sizeof(double) * L.nnz));
   const int blocks = (int)((g.n + 127) / 128);
-  if (D == 2) k_assemble<2><<<blocks, 128, 0, s>>>(g, Ke, Be, L.rp, L.ci, L.va);
-  else k_assemble<3><<<blocks, 128, 0, s>>>(g, Ke, Be, L.rp, L.ci, L.va);
+  if (q1) {
+    if (D == 2) k_q1_assemble<2><<<blocks, 128, 0, s>>>(g, Ke, Be, Ce, L.rp, L.ci, L.va);
+    else k_q1_assemble<3><<<blocks, 128, 0, s>>>(g, Ke, Be, Ce, L.rp, L.ci, L.va);
+  } else {
+    if (D == 2) k_assemble<2><<<blocks, 128, 0, s>>>(g, Ke, Be, L.rp, L.ci, L.va);
+    else k_assemble<3><<<blocks, 128, 0, s>>>(g, Ke, Be, L.rp, L.ci, L.va);
+  }
   RAV_CUDA(cudaGetLastError());
   RAV_CUDA(cudaFreeAsync(Ke, s));
   RAV_CUDA(cudaFreeAsync(Be, s));
+  if (Ce) RAV_CUDA(cudaFreeAsync(Ce, s));
   RAV_CUDA(cudaFreeAsync(bsum, s));
   RAV_CUDA(cudaMalloc(&L.r, sizeof(double) * g.n));
   RAV_CUDA(cudaMalloc(&L.x, sizeof(double) * g.n));
@@ -938,10 +1203,13 @@ extern "C" int mg_setup(const rav_problem* p, int n_levels, rav_stream stream, r
     return RAV_ERR_ARG;
   if (p->N % (1 << (n_levels - 1)) != 0 || p->N / (1 << (n_levels - 1)) < 2) return RAV_ERR_ARG;
   if (p->nblobs < 0 || (p->nblobs > 0 && !p->blobs_host)) return RAV_ERR_ARG;
+  if (p->element != RAV_ELEM_Q2Q1 && p->element != RAV_ELEM_Q1Q1) return RAV_ERR_ARG;
+  if (p->element == RAV_ELEM_Q1Q1 && !(p->beta >= 0.0 && p->beta < 1e300)) return RAV_ERR_ARG;
   {
     // the explicit coarse inverse is formed with one grid row per matrix row
     const int64_t N0 = p->N >> (n_levels - 1);
-    const int64_t n0 = p->dim * ipow(2 * N0 + 1, p->dim) + ipow(N0 + 1, p->dim);
+    const int64_t q = p->element == RAV_ELEM_Q1Q1 ? 1 : 2;
+    const int64_t n0 = p->dim * ipow(q * N0 + 1, p->dim) + ipow(N0 + 1, p->dim);
     if (n0 + 1 > 65535) return RAV_ERR_ARG;
   }
   if (p->coords_host) {
@@ -957,6 +1225,8 @@ extern "C" int mg_setup(const rav_problem* p, int n_levels, rav_stream stream, r
   mg->nlev = n_levels;
   mg->eta0 = p->eta0;
   mg->bc = p->bc;
+  mg->elem = p->element;
+  mg->beta = p->element == RAV_ELEM_Q1Q1 ? p->beta : 0.0;
   mg->nblobs = p->nblobs;
   int rc = RAV_OK;
   auto fail = [&](int code) {
@@ -1053,13 +1323,21 @@ extern "C" int rav_assemble_rhs(rav_mg* mg, int forcing, double* b, rav_stream s
   Level& L = mg->lev[mg->nlev - 1];
   const Geo& g = L.g;
   cudaStream_t s = S(stream);
-  const int D = g.dim, NL = D == 2 ? 9 : 27;
+  const int D = g.dim, NL = g.q == 1 ? (1 << D) : (D == 2 ? 9 : 27);
   const int64_t ncell = ipow(g.N, D);
   double* Fe = nullptr;
   RAV_CUDA(cudaMallocAsync(&Fe, sizeof(double) * ncell * NL * D, s));
   Coef C{mg->eta0, mg->nblobs, mg->blobs_dev};
   const int blocks = (int)((g.n + 255) / 256);
-  if (D == 2) {
+  if (g.q == 1) {
+    if (D == 2) {
+      k_q1_cell_load<2><<<(unsigned)ncell, 32, 0, s>>>(g, C, forcing, Fe);
+      k_q1_rhs<2><<<blocks, 256, 0, s>>>(g, mg->bc, Fe, b);
+    } else {
+      k_q1_cell_load<3><<<(unsigned)ncell, 32, 0, s>>>(g, C, forcing, Fe);
+      k_q1_rhs<3><<<blocks, 256, 0, s>>>(g, mg->bc, Fe, b);
+    }
+  } else if (D == 2) {
     k_cell_load<2><<<(unsigned)ncell, 32, 0, s>>>(g, C, forcing, Fe);
     k_rhs<2><<<blocks, 256, 0, s>>>(g, mg->bc, Fe, b);
   } else {

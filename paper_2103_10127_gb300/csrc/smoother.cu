@@ -777,7 +777,8 @@ __global__ void k_patch_list(Geo g, const int32_t* __restrict__ off, int32_t* __
     if (dof >= 0) dofs[pos++] = (int32_t)dof;
   }
 }
-// owner(velocity DoF at node I) = vertex floor(I/2); owner(p_i) = i; Dirichlet -1.
+// owner(velocity DoF at node I) = vertex floor(I/2) (Q2-Q1) or vertex I
+// (Q1-Q1); owner(p_i) = i; Dirichlet -1.
 __global__ void k_owner(Geo g, int32_t* __restrict__ owner) {
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= g.n) return;
@@ -787,7 +788,7 @@ __global__ void k_owner(Geo g, int32_t* __restrict__ owner) {
   vel_node(g, i, I, c);
   if (node_on_boundary(g, I)) { owner[i] = -1; return; }
   int64_t v[3];
-  for (int d = 0; d < g.dim; ++d) v[d] = I[d] >> 1;
+  for (int d = 0; d < g.dim; ++d) v[d] = g.q == 1 ? I[d] : I[d] >> 1;
   owner[i] = (int32_t)vert_id(g, v);
 }
 __global__ void k_scan_i32(const int32_t* __restrict__ cnt, int64_t n, int32_t* __restrict__ off) {
@@ -939,6 +940,329 @@ __global__ void k_export_full(Geo g, const double* __restrict__ inv, int64_t fir
   }
 }
 
+// ---------------------------------------------------------------------------
+// Stabilised Q1-Q1 subdomains (Sec. 3 on the paper's own element): subdomain
+// i = p_i plus the free velocity DoFs of the 3^d vertices J = v - 1 + a,
+// a in [0,3)^d (box node m = a0 + 3 a1 + 9 a2, ascending m = ascending DoF);
+// it owns the velocity DoFs of vertex v itself (m = CEN) and p_i.  The local
+// system is [K (x) I_d, b; b^T, c] with K the scalar velocity block, b the
+// pressure row's velocity entries and c its diagonal (the stabilisation of
+// Eq. 8), so with w_c = K^{-1} b_c and s = c - sum_c b_c^T w_c the owned rows
+// of L_i^{-1} follow from the centre row of K^{-1}, w and 1/s.  Stored per
+// subdomain, structure of arrays (value k of subdomain p at k np + p):
+//   k in [0, NV): row CEN of K^{-1};  [NV, NV + d NV): w (node-major);  last: 1/s.
+template <int D>
+struct Q1Box {
+  static constexpr int NV = D == 2 ? 9 : 27;  // box vertices
+  static constexpr int NC = D * NV + 1;       // box positions
+  static constexpr int NR = D + 1;            // owned rows
+  static constexpr int NF = NV * (D + 1) + 1; // stored values per subdomain
+  static constexpr int CEN = D == 2 ? 4 : 13; // the subdomain's own vertex
+};
+__device__ __forceinline__ void q1_tuple(int m, int* a) {
+  a[0] = m % 3;
+  a[1] = (m / 3) % 3;
+  a[2] = m / 9;
+}
+// Box vertex m of subdomain v is a free velocity node: 1 <= v - 1 + a <= N - 1 on every axis.
+template <int D>
+__device__ __forceinline__ bool q1_free(const Geo& g, const int* v, int m) {
+  int a[3];
+  q1_tuple(m, a);
+  bool ok = true;
+#pragma unroll
+  for (int d = 0; d < D; ++d) ok &= (v[d] - 1 + a[d] >= 1) & (v[d] - 1 + a[d] <= g.N - 1);
+  return ok;
+}
+
+// One warp per subdomain (4 per block): gather K, b and c from the CSR rows,
+// Cholesky K = L L^T, solve for K^{-1} e_CEN and K^{-1} b_c (one lane per
+// right-hand side), write the NF stored values in fp64 to out (SoA, stride np).
+template <int D>
+__global__ void __launch_bounds__(128) k_factor_q1(Geo g, const int64_t* __restrict__ rp,
+                                                   const double* __restrict__ va, int64_t np,
+                                                   double* __restrict__ out, int* __restrict__ err) {
+  using B = Q1Box<D>;
+  constexpr int NV = B::NV, NR = B::NR, NF = B::NF;
+  __shared__ double sK[4][NV * NV];
+  __shared__ double sB[4][NV * D];
+  __shared__ double sZ[4][NR * NV];
+  __shared__ int sv[4][NV];
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t p = blockIdx.x * 4ll + w;
+  if (p >= np) return;  // whole warps
+  double* K = sK[w];
+  double* b = sB[w];
+  double* Z = sZ[w];
+  int* valid = sv[w];
+  int v[3] = {0, 0, 0};
+  vertex_of_t<D>(g, p, v);
+  const int64_t N1 = g.N + 1;
+  for (int m = lane; m < NV; m += 32) valid[m] = q1_free<D>(g, v, m);
+  __syncwarp();
+  // K from the component-0 rows of the free box vertices: a free row J lists
+  // its velocity columns over [J-1, J+1] per axis (all inside the grid)
+  for (int e = lane; e < NV * NV; e += 32) {
+    const int m = e / NV, n = e % NV;
+    double val = m == n ? 1.0 : 0.0;
+    if (valid[m] && valid[n]) {
+      int am[3], an[3];
+      q1_tuple(m, am);
+      q1_tuple(n, an);
+      bool in = true;
+      int pos = 0;
+      int64_t jm = 0;
+      for (int d = D - 1; d >= 0; --d) {
+        const int dj = an[d] - am[d];
+        in &= dj >= -1 && dj <= 1;
+        pos = pos * 3 + (dj + 1);
+        jm = jm * N1 + (v[d] - 1 + am[d]);
+      }
+      val = in ? va[rp[D * jm] + pos] : 0.0;
+    }
+    K[e] = val;
+  }
+  // b from the pressure row of p: velocity columns over [v-1, v+1] clipped, D per vertex
+  const int64_t prow = g.n_u + p;
+  int lo[3] = {0, 0, 0}, ext[3] = {1, 1, 1};
+  for (int d = 0; d < D; ++d) {
+    lo[d] = v[d] - 1 < 0 ? 0 : v[d] - 1;
+    const int hi = v[d] + 1 > g.N ? g.N : v[d] + 1;
+    ext[d] = hi - lo[d] + 1;
+  }
+  for (int e = lane; e < NV * D; e += 32) {
+    const int m = e / D, c = e % D;
+    double val = 0.0;
+    if (valid[m]) {
+      int a[3];
+      q1_tuple(m, a);
+      int pos = 0;
+      for (int d = D - 1; d >= 0; --d) pos = pos * ext[d] + (v[d] - 1 + a[d] - lo[d]);
+      val = va[rp[prow] + pos * D + c];
+    }
+    b[e] = val;
+  }
+  double cdiag = 0.0;
+  if (lane == 0) {
+    int cnt = 1, pos = 0;
+    for (int d = D - 1; d >= 0; --d) {
+      cnt *= ext[d];
+      pos = pos * ext[d] + (v[d] - lo[d]);
+    }
+    cdiag = va[rp[prow] + D * cnt + pos];
+  }
+  __syncwarp();
+  double dmax = 0.0;
+  for (int m = lane; m < NV; m += 32) dmax = fmax(dmax, fabs(K[m * NV + m]));
+  for (int o = 16; o > 0; o >>= 1) dmax = fmax(dmax, __shfl_xor_sync(0xffffffffu, dmax, o));
+  int bad = 0;
+  for (int k = 0; k < NV; ++k) {
+    if (lane == 0) {
+      const double dkk = K[k * NV + k];
+      if (!(dkk > 1e-14 * dmax)) { bad = 1; K[k * NV + k] = 1.0; }
+      else K[k * NV + k] = sqrt(dkk);
+    }
+    __syncwarp();
+    const double lkk = K[k * NV + k];
+    for (int j = k + 1 + lane; j < NV; j += 32) K[j * NV + k] /= lkk;
+    __syncwarp();
+    const int rem = NV - k - 1;
+    for (int e = lane; e < rem * rem; e += 32) {
+      const int i = k + 1 + e / rem, j = k + 1 + e % rem;
+      if (j <= i) K[i * NV + j] -= K[i * NV + k] * K[j * NV + k];
+    }
+    __syncwarp();
+  }
+  if (lane < NR) {  // right-hand side lane: e_CEN, then b_0 .. b_{D-1}
+    double* z = Z + lane * NV;
+    for (int i = 0; i < NV; ++i) {
+      double acc = lane == 0 ? (i == B::CEN ? 1.0 : 0.0) : b[i * D + lane - 1];
+      for (int j = 0; j < i; ++j) acc -= K[i * NV + j] * z[j];
+      z[i] = acc / K[i * NV + i];
+    }
+    for (int i = NV - 1; i >= 0; --i) {
+      double acc = z[i];
+      for (int j = i + 1; j < NV; ++j) acc -= K[j * NV + i] * z[j];
+      z[i] = acc / K[i * NV + i];
+    }
+  }
+  __syncwarp();
+  double sinv = 0.0;
+  if (lane == 0) {
+    double sch = cdiag;
+    for (int c = 0; c < D; ++c)
+      for (int m = 0; m < NV; ++m) sch -= b[m * D + c] * Z[(1 + c) * NV + m];
+    if (!(fabs(sch) > 0.0) || !isfinite(sch)) bad = 1;
+    else sinv = 1.0 / sch;
+  }
+  sinv = __shfl_sync(0xffffffffu, sinv, 0);
+  bad = __shfl_sync(0xffffffffu, bad, 0);
+  for (int k = lane; k < NF; k += 32) {
+    double val;
+    if (k < NV) val = Z[k];
+    else if (k < NV + NV * D) {
+      const int m = (k - NV) / D, c = (k - NV) % D;
+      val = Z[(1 + c) * NV + m];
+    } else val = sinv;
+    out[k * np + p] = val;
+  }
+  if (bad && lane == 0) atomicExch(err, 1);
+}
+
+template <typename T>
+__global__ void k_q1_pack(const double* __restrict__ stage, int64_t n, T* __restrict__ out) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n) out[i] = Fmt<T>::enc(stage[i]);
+}
+
+// RAV step on Q1-Q1 (Eq. 13), one thread per subdomain: with r_u, r_p the
+// residual on the box, t = (w^T r_u - r_p) / s,
+//   x[v, c] += omega (sum_m K^{-1}[CEN, m] r_u[m, c] + w[CEN, c] t)   (v free)
+//   x[p_i]  += omega (-t).
+// Stored values in T, accumulation in fp64 (T = double, r fp64) or fp32
+// (reduced formats, r the fp32 copy); x is updated in fp64.
+template <int D, typename T>
+__global__ void __launch_bounds__(128) k_rav_apply_q1(Geo g, const T* __restrict__ st,
+                                                      const double* __restrict__ omega,
+                                                      const AccT<T>* __restrict__ r, double* __restrict__ x,
+                                                      int64_t np) {
+  using B = Q1Box<D>;
+  using A = AccT<T>;
+  constexpr int NV = B::NV, NF = B::NF;
+  const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (p >= np) return;
+  int v[3] = {0, 0, 0};
+  vertex_of_t<D>(g, p, v);
+  const int N = g.N;
+  const int64_t N1 = N + 1;
+  A y[D], wc[D];
+#pragma unroll
+  for (int c = 0; c < D; ++c) y[c] = wc[c] = 0;
+  A t = 0;
+#pragma unroll
+  for (int a2 = 0; a2 < (D == 3 ? 3 : 1); ++a2) {
+    const int J2 = D == 3 ? v[2] - 1 + a2 : 0;
+    const bool ok2 = D == 2 || (J2 >= 1 && J2 <= N - 1);
+#pragma unroll
+    for (int a1 = 0; a1 < 3; ++a1) {
+      const int J1 = v[1] - 1 + a1;
+      const bool ok1 = ok2 && J1 >= 1 && J1 <= N - 1;
+#pragma unroll
+      for (int a0 = 0; a0 < 3; ++a0) {
+        const int n = a0 + 3 * a1 + 9 * a2;
+        const int J0 = v[0] - 1 + a0;
+        const bool ok = ok1 && J0 >= 1 && J0 <= N - 1;
+        const int64_t base = (int64_t)D * (J0 + N1 * (J1 + N1 * J2));
+        A ru[D];
+        if constexpr (D == 2 && std::is_same<A, float>::value) {
+          float2 rv = make_float2(0.f, 0.f);
+          if (ok) rv = *reinterpret_cast<const float2*>(r + base);
+          ru[0] = rv.x;
+          ru[1] = rv.y;
+        } else {
+#pragma unroll
+          for (int c = 0; c < D; ++c) ru[c] = ok ? r[base + c] : (A)0;
+        }
+        const A kq = (A)Fmt<T>::dec(ld_stream(st + n * np + p), nullptr);
+#pragma unroll
+        for (int c = 0; c < D; ++c) {
+          const A wv = (A)Fmt<T>::dec(ld_stream(st + (NV + n * D + c) * np + p), nullptr);
+          y[c] += kq * ru[c];
+          t += wv * ru[c];
+          if (n == B::CEN) wc[c] = wv;
+        }
+      }
+    }
+  }
+  const A tau = (A)Fmt<T>::dec(ld_stream(st + (NF - 1) * np + p), nullptr) * (t - r[g.n_u + p]);
+  const double om = omega[p];
+  bool cfree = true;
+#pragma unroll
+  for (int d = 0; d < D; ++d) cfree &= v[d] >= 1 && v[d] <= N - 1;
+  if (cfree) {
+#pragma unroll
+    for (int c = 0; c < D; ++c) x[D * p + c] += om * (double)(y[c] + wc[c] * tau);
+  }
+  x[g.n_u + p] -= om * (double)tau;
+}
+
+// Inspection on Q1-Q1: subdomain sizes, sorted DoF lists, and the owned rows
+// of L_i^{-1} rebuilt from the stored values,
+//   (CEN,c | n,c') = delta_cc' K^{-1}[CEN,n] + w(CEN,c) w(n,c') / s,  (CEN,c | p) = -w(CEN,c) / s,
+//   (p | n,c') = -w(n,c') / s,  (p | p) = 1 / s,
+// padded to NR x NC per subdomain.
+template <int D>
+__global__ void k_q1_patch_count(Geo g, int32_t* __restrict__ cnt) {
+  const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (p >= g.n_p) return;
+  int v[3] = {0, 0, 0};
+  vertex_of_t<D>(g, p, v);
+  int c = 1;
+  for (int m = 0; m < Q1Box<D>::NV; ++m) c += q1_free<D>(g, v, m) ? D : 0;
+  cnt[p] = c;
+}
+template <int D>
+__global__ void k_q1_patch_list(Geo g, const int32_t* __restrict__ off, int32_t* __restrict__ dofs) {
+  const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (p >= g.n_p) return;
+  int v[3] = {0, 0, 0};
+  vertex_of_t<D>(g, p, v);
+  int32_t pos = off[p];
+  for (int m = 0; m < Q1Box<D>::NV; ++m) {
+    if (!q1_free<D>(g, v, m)) continue;
+    int a[3];
+    q1_tuple(m, a);
+    int64_t id = 0;
+    for (int d = D - 1; d >= 0; --d) id = id * (g.N + 1) + (v[d] - 1 + a[d]);
+    for (int c = 0; c < D; ++c) dofs[pos++] = (int32_t)(D * id + c);
+  }
+  dofs[pos] = (int32_t)(g.n_u + p);
+}
+template <int D, typename T>
+__global__ void k_export_q1(Geo g, const T* __restrict__ st, int64_t np, int64_t first, int64_t count,
+                            double* __restrict__ out) {
+  using B = Q1Box<D>;
+  constexpr int NV = B::NV, NC = B::NC, NR = B::NR, NF = B::NF;
+  __shared__ int colmap[NC], rowmap[NR];
+  __shared__ int ncol, nrow;
+  const int64_t p = first + blockIdx.x;
+  int v[3] = {0, 0, 0};
+  vertex_of_t<D>(g, p, v);
+  if (threadIdx.x == 0) {
+    int c = 0;
+    for (int m = 0; m < NV; ++m)
+      if (q1_free<D>(g, v, m))
+        for (int cc = 0; cc < D; ++cc) colmap[c++] = m * D + cc;
+    colmap[c++] = NC - 1;
+    ncol = c;
+    int rr = 0;
+    if (q1_free<D>(g, v, B::CEN))
+      for (int cc = 0; cc < D; ++cc) rowmap[rr++] = cc;
+    rowmap[rr++] = NR - 1;
+    nrow = rr;
+  }
+  __syncthreads();
+  auto val_at = [&](int k) { return (double)Fmt<T>::dec(st[k * np + p], nullptr); };
+  const double sig = val_at(NF - 1);
+  double* o = out + blockIdx.x * (int64_t)NR * NC;
+  for (int e = threadIdx.x; e < NR * NC; e += blockDim.x) {
+    const int jr = e / NC, kc = e % NC;
+    double val = 0.0;
+    if (jr < nrow && kc < ncol) {
+      const int j = rowmap[jr], k = colmap[kc];
+      const bool prow = j == NR - 1, pcol = k == NC - 1;
+      if (prow && pcol) val = sig;
+      else if (prow) val = -val_at(NV + k) * sig;
+      else {
+        const double wm = val_at(NV + B::CEN * D + j);
+        if (pcol) val = -wm * sig;
+        else val = (k % D == j ? val_at(k / D) : 0.0) + wm * val_at(NV + k) * sig;
+      }
+    }
+    o[e] = val;
+  }
+}
+
 __global__ void k_fill(double* __restrict__ a, int64_t n, double v) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
     a[i] = v;
@@ -1059,6 +1383,39 @@ static int setup_level(rav_smoother* sm, int l, cudaStream_t s, int* err_dev) {
   return RAV_OK;
 }
 
+// Q1-Q1 level: factored storage only (RAV_F64 / RAV_F32_FACT / RAV_BF16_FACT),
+// one thread per subdomain, no split.
+template <int D>
+static int setup_level_q1(rav_smoother* sm, int l, cudaStream_t s, int* err_dev) {
+  using B = Q1Box<D>;
+  const Level& L = sm->mg->lev[l];
+  SmLevel& S_ = sm->lev[l];
+  const Geo& g = L.g;
+  S_.np = g.n_p;
+  S_.units = g.n_p;
+  S_.factored = true;
+  S_.split = 1;
+  RAV_CUDA(cudaMalloc(&S_.omega, sizeof(double) * S_.np));
+  k_fill<<<grid_for(S_.np, 256), 256, 0, s>>>(S_.omega, S_.np, sm->omega);
+  const int64_t tot = S_.np * B::NF;
+  RAV_CUDA(cudaMalloc(&S_.inv, elem_size(sm->prec) * tot));
+  const unsigned gf = (unsigned)((S_.np + 3) / 4);
+  if (sm->prec == RAV_F64) {
+    k_factor_q1<D><<<gf, 128, 0, s>>>(g, L.rp, L.va, S_.np, (double*)S_.inv, err_dev);
+  } else {
+    RAV_CUDA(cudaMalloc(&S_.r32, sizeof(float) * g.n));
+    double* stage = nullptr;
+    RAV_CUDA(cudaMallocAsync(&stage, sizeof(double) * tot, s));
+    k_factor_q1<D><<<gf, 128, 0, s>>>(g, L.rp, L.va, S_.np, stage, err_dev);
+    const unsigned gp = (unsigned)((tot + 255) / 256);
+    if (sm->prec == RAV_F32_FACT) k_q1_pack<float><<<gp, 256, 0, s>>>(stage, tot, (float*)S_.inv);
+    else k_q1_pack<__nv_bfloat16><<<gp, 256, 0, s>>>(stage, tot, (__nv_bfloat16*)S_.inv);
+    cudaFreeAsync(stage, s);
+  }
+  RAV_CUDA(cudaGetLastError());
+  return RAV_OK;
+}
+
 static int tune_apply_split(rav_smoother* sm, cudaStream_t s);
 
 extern "C" int vanka_setup(rav_mg* mg, int kind, int precision, double omega, rav_stream stream,
@@ -1066,6 +1423,8 @@ extern "C" int vanka_setup(rav_mg* mg, int kind, int precision, double omega, ra
   if (!mg || !out || (kind != RAV_RAV && kind != RAV_AV && kind != RAV_MV_COLOURED)) return RAV_ERR_ARG;
   if (precision < RAV_F64 || precision > RAV_BF16_FACT) return RAV_ERR_ARG;
   if (kind != RAV_RAV && precision != RAV_F64 && precision != RAV_F64_ROWS) return RAV_ERR_ARG;
+  const bool q1 = mg->elem == RAV_ELEM_Q1Q1;
+  if (q1 && (kind != RAV_RAV || !factored_prec(precision))) return RAV_ERR_ARG;
   cudaStream_t s = S(stream);
   *out = nullptr;
   rav_smoother* sm = new rav_smoother();
@@ -1077,8 +1436,10 @@ extern "C" int vanka_setup(rav_mg* mg, int kind, int precision, double omega, ra
   int rc = RAV_OK;
   if (cudaMalloc(&err_dev, sizeof(int)) != cudaSuccess) { delete sm; return RAV_ERR_CUDA; }
   cudaMemsetAsync(err_dev, 0, sizeof(int), s);
-  for (int l = 1; l < mg->nlev && rc == RAV_OK; ++l)
-    rc = mg->dim == 2 ? setup_level<2>(sm, l, s, err_dev) : setup_level<3>(sm, l, s, err_dev);
+  for (int l = 1; l < mg->nlev && rc == RAV_OK; ++l) {
+    if (q1) rc = mg->dim == 2 ? setup_level_q1<2>(sm, l, s, err_dev) : setup_level_q1<3>(sm, l, s, err_dev);
+    else rc = mg->dim == 2 ? setup_level<2>(sm, l, s, err_dev) : setup_level<3>(sm, l, s, err_dev);
+  }
   int err = 0;
   if (rc == RAV_OK) {
     if (cudaMemcpyAsync(&err, err_dev, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
@@ -1088,7 +1449,7 @@ extern "C" int vanka_setup(rav_mg* mg, int kind, int precision, double omega, ra
       rc = RAV_ERR_SINGULAR_PATCH;
   }
   cudaFree(err_dev);
-  if (rc == RAV_OK) rc = tune_apply_split(sm, s);
+  if (rc == RAV_OK && !q1) rc = tune_apply_split(sm, s);
   if (rc == RAV_OK && cudaStreamSynchronize(s) != cudaSuccess) rc = RAV_ERR_CUDA;
   if (rc != RAV_OK) {
     vanka_destroy(sm);
@@ -1185,6 +1546,7 @@ static int tune_apply_split(rav_smoother* sm, cudaStream_t s) {
 extern "C" int rav_set_apply_split(rav_smoother* sm, int level, int split, rav_stream stream) {
   if (!sm || level < 1 || level >= sm->mg->nlev) return RAV_ERR_ARG;
   SmLevel& SL = sm->lev[level];
+  if (sm->mg->elem == RAV_ELEM_Q1Q1) return split == 1 ? RAV_OK : RAV_ERR_ARG;  // one thread per subdomain
   const int NON = sm->mg->dim == 2 ? 4 : 8;
   if (!SL.factored || split < 1 || split > 32 / NON || (split & (split - 1))) return RAV_ERR_ARG;
   if (split == SL.split) return RAV_OK;
@@ -1237,7 +1599,23 @@ int apply_with_omega(rav_smoother* sm, int level, const double* r, double* x, co
   }
   cudaEvent_t e0 = nullptr;
   RAV_TRY(prof_begin(mg, level, PROF_APPLY, s, &e0));
-  if (sm->kind == RAV_AV) {
+  if (g.q == 1) {
+    const unsigned gb = (unsigned)((SL.np + 127) / 128);
+#define RAV_APPLY_Q1(DD, T) \
+  k_rav_apply_q1<DD, T><<<gb, 128, 0, s>>>(g, (const T*)SL.inv, omega, (const AccT<T>*)rr, x, SL.np)
+    const void* rr = sm->prec == RAV_F64 ? (const void*)r : (const void*)r32;
+    if (D == 2) {
+      if (sm->prec == RAV_F64) RAV_APPLY_Q1(2, double);
+      else if (sm->prec == RAV_F32_FACT) RAV_APPLY_Q1(2, float);
+      else RAV_APPLY_Q1(2, __nv_bfloat16);
+    } else {
+      if (sm->prec == RAV_F64) RAV_APPLY_Q1(3, double);
+      else if (sm->prec == RAV_F32_FACT) RAV_APPLY_Q1(3, float);
+      else RAV_APPLY_Q1(3, __nv_bfloat16);
+    }
+#undef RAV_APPLY_Q1
+    note_launch();
+  } else if (sm->kind == RAV_AV) {
     const unsigned gb = (unsigned)((g.n_p + 3) / 4);
     const int gg = (int)((g.n + 255) / 256);
     if (D == 2) {
@@ -1363,13 +1741,15 @@ extern "C" int rav_get_patch_counts(const rav_smoother* sm, int level, int64_t o
   if (!sm || !out || level < 1 || level >= sm->mg->nlev) return RAV_ERR_ARG;
   const Geo& g = sm->mg->lev[level].g;
   // closed form: per axis the box positions inside the domain interior
+  // (Q2-Q1: nodes 2v-2 .. 2v+2; Q1-Q1: vertices v-1 .. v+1)
   int64_t tot = 0;
   std::vector<int64_t> per(g.N + 1);
+  const int nb = g.q == 1 ? 3 : 5;
   for (int v = 0; v <= g.N; ++v) {
     int c = 0;
-    for (int a = 0; a < 5; ++a) {
-      const int J = 2 * v - 2 + a;
-      c += (J >= 1 && J <= 2 * g.N - 1);
+    for (int a = 0; a < nb; ++a) {
+      const int J = g.q * v - g.q + a;
+      c += (J >= 1 && J <= (int)g.M - 2);
     }
     per[v] = c;
   }
@@ -1394,11 +1774,21 @@ extern "C" int rav_get_patches(const rav_smoother* sm, int level, int32_t* off, 
   int32_t* cnt = nullptr;
   RAV_CUDA(cudaMallocAsync(&cnt, sizeof(int32_t) * g.n_p, s));
   const int gb = (int)((g.n_p + 127) / 128);
-  if (g.dim == 2) k_patch_count<2><<<gb, 128, 0, s>>>(g, cnt);
-  else k_patch_count<3><<<gb, 128, 0, s>>>(g, cnt);
+  if (g.q == 1) {
+    if (g.dim == 2) k_q1_patch_count<2><<<gb, 128, 0, s>>>(g, cnt);
+    else k_q1_patch_count<3><<<gb, 128, 0, s>>>(g, cnt);
+  } else {
+    if (g.dim == 2) k_patch_count<2><<<gb, 128, 0, s>>>(g, cnt);
+    else k_patch_count<3><<<gb, 128, 0, s>>>(g, cnt);
+  }
   k_scan_i32<<<1, 32, 0, s>>>(cnt, g.n_p, off);
-  if (g.dim == 2) k_patch_list<2><<<gb, 128, 0, s>>>(g, off, dofs);
-  else k_patch_list<3><<<gb, 128, 0, s>>>(g, off, dofs);
+  if (g.q == 1) {
+    if (g.dim == 2) k_q1_patch_list<2><<<gb, 128, 0, s>>>(g, off, dofs);
+    else k_q1_patch_list<3><<<gb, 128, 0, s>>>(g, off, dofs);
+  } else {
+    if (g.dim == 2) k_patch_list<2><<<gb, 128, 0, s>>>(g, off, dofs);
+    else k_patch_list<3><<<gb, 128, 0, s>>>(g, off, dofs);
+  }
   k_owner<<<(int)((g.n + 255) / 256), 256, 0, s>>>(g, owner);
   const cudaError_t e = cudaGetLastError();
   cudaFreeAsync(cnt, s);
@@ -1415,7 +1805,20 @@ extern "C" int rav_get_inverse_rows(const rav_smoother* sm, int level, int64_t f
   if (count == 0) return RAV_OK;
   cudaStream_t s = S(stream);
   const unsigned gb = (unsigned)count;
-  if (sm->kind != RAV_RAV) {
+  if (g.q == 1) {
+#define RAV_EXP_Q1(DD, T) k_export_q1<DD, T><<<gb, 128, 0, s>>>(g, (const T*)SL.inv, SL.np, first, count, out)
+    if (sm->prec == RAV_F64) {
+      if (g.dim == 2) RAV_EXP_Q1(2, double);
+      else RAV_EXP_Q1(3, double);
+    } else if (sm->prec == RAV_F32_FACT) {
+      if (g.dim == 2) RAV_EXP_Q1(2, float);
+      else RAV_EXP_Q1(3, float);
+    } else {
+      if (g.dim == 2) RAV_EXP_Q1(2, __nv_bfloat16);
+      else RAV_EXP_Q1(3, __nv_bfloat16);
+    }
+#undef RAV_EXP_Q1
+  } else if (sm->kind != RAV_RAV) {
     if (g.dim == 2) k_export_full<2><<<gb, 256, 0, s>>>(g, (const double*)SL.inv, first, count, out);
     else k_export_full<3><<<gb, 256, 0, s>>>(g, (const double*)SL.inv, first, count, out);
   } else if (SL.factored) {

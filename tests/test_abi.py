@@ -36,6 +36,10 @@ def test_invalid_arguments_are_rejected_without_a_gpu():
         _capi.RavProblem(2, 1, None, 1.0, 0, None, 0),    # N < 2
         _capi.RavProblem(2, 12, None, 1.0, 0, None, 0),   # 12 not divisible by 2^3
         _capi.RavProblem(2, 16, None, 1.0, -1, None, 0),  # negative blob count
+        _capi.RavProblem(2, 16, None, 1.0, 0, None, 0, 2, 0.0),  # unknown element
+        _capi.RavProblem(2, 16, None, 1.0, 0, None, 0, 1, -0.1),  # negative beta (Q1-Q1)
+        _capi.RavProblem(2, 16, None, 1.0, 0, None, 0, 1, float("nan")),  # beta not finite
+        _capi.RavProblem(2, 16, None, 1.0, 0, None, 0, 1, float("inf")),
     ]
     for p in bad:
         assert lib.mg_setup(ctypes.byref(p), 4, None, ctypes.byref(h)) == -1
@@ -62,13 +66,15 @@ def test_struct_layouts_match_the_header(tmp_path):
     prog = tmp_path / "layout.c"
     prog.write_text(
         '#include <stddef.h>\n#include <stdio.h>\n#include "ravanka.h"\n'
-        'int main(void){printf("%zu %zu %zu %zu %zu %zu\\n", sizeof(rav_problem), offsetof(rav_problem, bc),'
+        'int main(void){printf("%zu %zu %zu %zu %zu %zu %zu %zu\\n", sizeof(rav_problem), offsetof(rav_problem, bc),'
+        ' offsetof(rav_problem, element), offsetof(rav_problem, beta),'
         ' sizeof(rav_solve_opts), offsetof(rav_solve_opts, fallback_rho), sizeof(rav_solve_info),'
         ' offsetof(rav_solve_info, fell_back)); return 0;}\n')
     exe = tmp_path / "layout"
     subprocess.check_call(["gcc", "-std=c99", "-I", os.path.join(ROOT, "include"), str(prog), "-o", str(exe)])
     got = [int(v) for v in subprocess.check_output([str(exe)]).split()]
-    want = [ctypes.sizeof(_capi.RavProblem), _capi.RavProblem.bc.offset, ctypes.sizeof(_capi.RavSolveOpts),
+    want = [ctypes.sizeof(_capi.RavProblem), _capi.RavProblem.bc.offset, _capi.RavProblem.element.offset,
+            _capi.RavProblem.beta.offset, ctypes.sizeof(_capi.RavSolveOpts),
             _capi.RavSolveOpts.fallback_rho.offset, ctypes.sizeof(_capi.RavSolveInfo),
             _capi.RavSolveInfo.fell_back.offset]
     assert got == want

@@ -1,0 +1,293 @@
+"""Parity of the CUDA path on the stabilised Q1-Q1 element (Sec. 2, Eq. 8;
+subdomains of Sec. 3 owning exactly their vertex's DoFs) with the FP64 oracle.
+
+Bars as for Q2-Q1: structure and patch/owner lists bit-exact; assembled values,
+right-hand sides and transfers to 1e-13 relative; stored rows to 1e-11; one
+FP64 smoothing step and a V-cycle to 1e-12 / 1e-11; per-cycle convergence
+factors within 2 %; factored reduced storage within fp32 roundoff of the
+oracle's step.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2103_10127_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA device", allow_module_level=True)
+
+import paper_2103_10127_gb300 as R  # noqa: E402
+
+BETA = 0.02
+OMEGA = 0.66
+
+
+def make_pair(dim, N, nlev, graded=False, nblobs=0, bc=O.BC_CAVITY, eta0=1.0, seed=21, s_max=2.0, beta=BETA):
+    coords = inputs.graded_coordinates(N, 4.0, dim) if graded else None
+    blobs = inputs.viscosity_blobs(seed, k=nblobs, s_max=s_max) if nblobs else None
+    mg = R.Multigrid(dim, N, nlev, coords=coords, eta0=eta0, blobs=blobs, bc=bc, element=R.ELEM_Q1Q1, beta=beta)
+    orc = O.Oracle(dim, N, nlev, coords=coords, eta0=eta0, blobs=blobs, bc=bc, element=O.ELEM_Q1Q1, beta=beta)
+    return mg, orc
+
+
+CASES = [
+    dict(dim=2, N=8, nlev=3),
+    dict(dim=2, N=12, nlev=2, graded=True, nblobs=6, bc=O.BC_NOSLIP),
+    dict(dim=3, N=4, nlev=2, nblobs=4),
+    dict(dim=3, N=6, nlev=2, graded=True, nblobs=5, bc=O.BC_NOSLIP),
+]
+IDS = ["2d-8-cavity", "2d-12-graded-blobs", "3d-4-blobs", "3d-6-graded-blobs"]
+
+
+def cpu(t):
+    return t.detach().cpu().numpy()
+
+
+def gpu(a):
+    return torch.from_numpy(np.ascontiguousarray(a, np.float64)).cuda()
+
+
+def rel(a, b):
+    return np.abs(a - b).max() / max(np.abs(b).max(), 1e-300)
+
+
+@pytest.mark.parametrize("case", CASES, ids=IDS)
+def test_assembled_operators_match(case):
+    mg, orc = make_pair(**case)
+    for lev in range(case["nlev"]):
+        assert mg.counts(lev)["n"] == orc.sizes(lev)["n"]
+        rp, ci, va = (cpu(t) for t in mg.csr(lev))
+        orp, oci, ova = orc.csr(lev)
+        assert np.array_equal(rp, orp)
+        assert np.array_equal(ci.astype(np.int64), oci)
+        assert np.abs(va - ova).max() <= 1e-13 * np.abs(ova).max()
+
+
+@pytest.mark.parametrize("case", CASES, ids=IDS)
+def test_rhs_and_initial_guess_match(case):
+    mg, orc = make_pair(**case)
+    forcings = [O.F_NONE, O.F_QUADRATIC] + ([O.F_PSI] if case["dim"] == 2 else [O.F_SINKER])
+    for f in forcings:
+        b = cpu(mg.rhs(f))
+        ob = orc.rhs(f)
+        assert np.abs(b - ob).max() <= 1e-13 * max(np.abs(ob).max(), 1.0), f
+    assert np.array_equal(cpu(mg.initial_guess()), orc.initial_guess())
+
+
+@pytest.mark.parametrize("case", CASES, ids=IDS)
+def test_patch_lists_and_owners_bit_exact(case):
+    mg, orc = make_pair(**case)
+    sm = R.Smoother(mg, R.RAV, R.F64, OMEGA)
+    for lev in range(1, case["nlev"]):
+        orc.build_patches(lev)
+        off, dofs, own = (cpu(t).astype(np.int64) for t in sm.patches(lev))
+        ooff, odofs, oown = orc.patches(lev)
+        assert np.array_equal(off, ooff)
+        assert np.array_equal(dofs, odofs)
+        assert np.array_equal(own, oown)
+        assert sm.patch_counts(lev) == (len(ooff) - 1, len(odofs))
+
+
+@pytest.mark.parametrize("case", CASES, ids=IDS)
+def test_stored_inverse_rows_match(case):
+    mg, orc = make_pair(**case)
+    sm = R.Smoother(mg, R.RAV, R.F64, OMEGA)
+    orc.setup_smoother(O.RAV, OMEGA)
+    lev = case["nlev"] - 1
+    npatch = mg.counts(lev)["n_p"]
+    got = cpu(sm.inverse_rows(lev, 0, npatch))
+    for p in range(npatch):
+        want = orc.inverse(lev, p)
+        g = got[p, : want.shape[0], : want.shape[1]]
+        assert np.abs(g - want).max() <= 1e-11 * np.abs(want).max(), p
+        assert not got[p, want.shape[0]:, :].any() and not got[p, :, want.shape[1]:].any()
+
+
+@pytest.mark.parametrize("case", CASES, ids=IDS)
+def test_fp64_smoothing_steps_match(case):
+    mg, orc = make_pair(**case)
+    sm = R.Smoother(mg, R.RAV, R.F64, OMEGA)
+    orc.setup_smoother(O.RAV, OMEGA)
+    rng = np.random.default_rng(3)
+    for lev in range(1, case["nlev"]):
+        n = mg.n(lev)
+        x, b = rng.standard_normal(n), rng.standard_normal(n)
+        want = orc.smooth(lev, x, b, 2)
+        xg = gpu(x)
+        sm.smooth(lev, xg, gpu(b), 2)
+        got = cpu(xg)
+        assert rel(got, want) <= 1e-12
+        assert np.linalg.norm(got - want) <= 1e-11 * np.linalg.norm(want - x)
+
+
+@pytest.mark.parametrize("case", [CASES[1], CASES[3]], ids=[IDS[1], IDS[3]])
+def test_per_patch_damping_is_applied(case):
+    mg, orc = make_pair(**case)
+    sm = R.Smoother(mg, R.RAV, R.F64, OMEGA)
+    orc.setup_smoother(O.RAV, OMEGA)
+    lev = case["nlev"] - 1
+    w = (0.2 + 0.9 * inputs.uniform(8, mg.counts(lev)["n_p"])).astype(np.float32)
+    sm.set_omega(lev, torch.from_numpy(w).cuda())
+    orc.set_omega(lev, w.astype(np.float64))
+    rng = np.random.default_rng(4)
+    n = mg.n(lev)
+    x, b = rng.standard_normal(n), rng.standard_normal(n)
+    xg = gpu(x)
+    sm.smooth(lev, xg, gpu(b), 1)
+    assert rel(cpu(xg), orc.smooth(lev, x, b, 1)) <= 1e-12
+
+
+@pytest.mark.parametrize("case", CASES, ids=IDS)
+def test_residual_transfers_and_coarse_solve_match(case):
+    mg, orc = make_pair(**case)
+    rng = np.random.default_rng(5)
+    for lev in range(case["nlev"]):
+        n = mg.n(lev)
+        x, b = rng.standard_normal(n), rng.standard_normal(n)
+        r, nrm = mg.residual(lev, gpu(x), gpu(b), norm=True)
+        want = orc.residual(lev, x, b)
+        assert rel(cpu(r), want) <= 1e-13
+        assert abs(nrm - np.linalg.norm(want)) <= 1e-13 * np.linalg.norm(want)
+        if lev > 0:
+            bc = cpu(mg.restrict(lev, gpu(want)))
+            assert rel(bc, orc.restrict(lev, want)) <= 1e-14
+            xc = rng.standard_normal(mg.n(lev - 1))
+            xf = rng.standard_normal(n)
+            got = cpu(mg.prolong_add(lev, gpu(xc), gpu(xf)))
+            assert rel(got, orc.prolong_add(lev, xc, xf)) <= 1e-14
+    b0 = rng.standard_normal(mg.n(0))
+    assert rel(cpu(mg.coarse_solve(gpu(b0))), orc.coarse_solve(b0)) <= 1e-11
+
+
+@pytest.mark.parametrize("prec", [R.F32_FACT, R.BF16_FACT], ids=["f32-factored", "bf16-factored"])
+@pytest.mark.parametrize("case", [CASES[1], CASES[2]], ids=[IDS[1], IDS[2]])
+def test_factored_reduced_storage_matches_the_oracle(case, prec):
+    """Rows rebuilt from the rounded K^{-1} centre row, w and 1/s equal the
+    oracle's rebuild (one fp32 unit of slack for fp64 differences of the two
+    factorisations), and one step with fp32 accumulation stays within fp32
+    roundoff of the oracle's step."""
+    mg, orc = make_pair(**case)
+    lev = case["nlev"] - 1
+    npatch = mg.counts(lev)["n_p"]
+    sq = R.Smoother(mg, R.RAV, prec, OMEGA)
+    orc.setup_smoother(O.RAV, OMEGA, {R.F32_FACT: O.F32_FACT, R.BF16_FACT: O.BF16_FACT}[prec])
+    got = cpu(sq.inverse_rows(lev, 0, npatch))
+    for p in range(npatch):
+        want, _ = orc.inverse(lev, p, quantised=True)
+        g = got[p, : want.shape[0], : want.shape[1]]
+        assert np.abs(g - want).max() <= 2.0 ** -22 * np.abs(want).max(), p
+    rng = np.random.default_rng(17)
+    n = mg.n(lev)
+    x, b = rng.standard_normal(n), rng.standard_normal(n)
+    xg = gpu(x)
+    sq.smooth(lev, xg, gpu(b), 1)
+    d = cpu(xg) - x
+    want = orc.smooth(lev, x, b, 1) - x
+    assert np.linalg.norm(d - want) <= 1e-5 * np.linalg.norm(want)
+
+
+@pytest.mark.parametrize("case", CASES[:3], ids=IDS[:3])
+def test_vcycle_matches(case):
+    mg, orc = make_pair(**case)
+    sm = R.Smoother(mg, R.RAV, R.F64, OMEGA)
+    orc.setup_smoother(O.RAV, OMEGA)
+    rng = np.random.default_rng(6)
+    n = mg.n()
+    x, b = rng.standard_normal(n), rng.standard_normal(n)
+    want = orc.vcycle(x, b, 2, 2)
+    xg = gpu(x)
+    mg.vcycle(sm, xg, gpu(b), 2, 2)
+    assert rel(cpu(xg), want) <= 1e-11
+
+
+def test_cavity_convergence_factors_within_two_percent():
+    """32x32 Q1-Q1 lid-driven cavity, 4 levels, RAV(0.66), V(2,2), to 1e-8."""
+    mg, orc = make_pair(2, 32, 4)
+    sm = R.Smoother(mg, R.RAV, R.F64, OMEGA)
+    orc.setup_smoother(O.RAV, OMEGA)
+    x = mg.initial_guess()
+    it, hist, rc = mg.solve(sm, x, mg.rhs(R.F_NONE), tol=1e-8, maxit=100)
+    ox, oit, ohist = orc.solve(orc.initial_guess(), orc.rhs(O.F_NONE), tol=1e-8, maxit=100)
+    assert rc == 0 and it == oit and it <= 20
+    fac, ofac = hist[1:] / hist[:-1], ohist[1:] / ohist[:-1]
+    assert np.all(np.abs(fac / ofac - 1.0) <= 0.02)
+    assert rel(cpu(x), ox) <= 1e-6
+
+
+@pytest.mark.parametrize("prec", [R.F64, R.F32_FACT, R.BF16_FACT], ids=["f64", "f32", "bf16"])
+def test_fgmres_reaches_the_fp64_tolerance(prec):
+    """3-D Q1-Q1 with viscosity blobs: FGMRES preconditioned by RAV V-cycles
+    reaches 1e-8 in fp64 with every factored storage; the fp64 run matches the
+    oracle's FGMRES history."""
+    mg, orc = make_pair(3, 8, 2, nblobs=10, s_max=2.0, bc=O.BC_NOSLIP)
+    sm = R.Smoother(mg, R.RAV, prec, OMEGA)
+    x = mg.initial_guess()
+    b = mg.rhs(R.F_SINKER)
+    it, hist, rc = mg.solve(sm, x, b, tol=1e-8, maxit=200, outer=1)
+    assert rc == 0 and hist[-1] <= 1e-8
+    _, nrm = mg.residual(1, x, b, norm=True)
+    _, nrm0 = mg.residual(1, mg.initial_guess(), b, norm=True)
+    assert nrm <= 1.01e-8 * nrm0
+    if prec == R.F64:
+        orc.setup_smoother(O.RAV, OMEGA)
+        _, oit, ohist = orc.fgmres(orc.initial_guess(), orc.rhs(O.F_SINKER), tol=1e-8, maxit=200)
+        assert abs(it - oit) <= 1
+        k = min(it, oit)
+        assert np.all(np.abs(hist[1:k] / ohist[1:k] - 1.0) <= 1e-4)
+
+
+def test_unsupported_combinations_are_rejected():
+    """Q1-Q1 offers RAV with factored storage only; the batched and learned
+    paths are Q2-Q1 only; the apply has no split."""
+    mg, _ = make_pair(2, 8, 2)
+    for kind, prec in ((R.AV, R.F64), (R.MV_COLOURED, R.F64), (R.RAV, R.F64_ROWS), (R.RAV, R.F32),
+                       (R.RAV, R.BF16), (R.RAV, R.FP8)):
+        with pytest.raises(R.RavError):
+            R.Smoother(mg, kind, prec, 0.5)
+    sm = R.Smoother(mg, R.RAV, R.F64, OMEGA)
+    assert sm.apply_split(1) == 1
+    assert sm.apply_split(1, 1) == 1
+    with pytest.raises(R.RavError):
+        sm.apply_split(1, 2)
+    from paper_2103_10127_gb300 import learned
+    with pytest.raises(R.RavError):
+        learned.features(sm, 1)
+    with pytest.raises(R.RavError):
+        R.Batch([mg], [sm], 1)
+
+
+@pytest.mark.slow
+def test_full_size_1024_sampled_parity():
+    """1024^2 Q1-Q1 (3,151,875 DoFs), the benchmark's launch configuration:
+    the whole assembled fine operator, and one RAV step at sampled subdomains
+    (boundary corners and 60 random vertices) against rows the oracle
+    factorises one by one."""
+    N, nlev = 1024, 8
+    mg = R.Multigrid(2, N, nlev, bc=R.BC_NOSLIP, element=R.ELEM_Q1Q1, beta=BETA)
+    orc = O.Oracle(2, N, 1, bc=O.BC_NOSLIP, element=O.ELEM_Q1Q1, beta=BETA)
+    rp, ci, va = (cpu(t) for t in mg.csr(nlev - 1))
+    orp, oci, ova = orc.csr(0)
+    assert np.array_equal(rp, orp) and np.array_equal(ci.astype(np.int64), oci)
+    assert np.abs(va - ova).max() <= 1e-13 * np.abs(ova).max()
+    del oci, ova
+    sm = R.Smoother(mg, R.RAV, R.F64, OMEGA)
+    rng = np.random.default_rng(8)
+    n = mg.n()
+    x, b = rng.standard_normal(n), rng.standard_normal(n)
+    xg = gpu(x)
+    sm.smooth(nlev - 1, xg, gpu(b), 1)
+    got = cpu(xg)
+    r = orc.residual(0, x, b)
+    orc.build_patches(0)
+    off, dofs, own = orc.patches(0)
+    samples = np.concatenate([[0, N, N * (N + 1), (N + 1) ** 2 - 1],
+                              (inputs.uniform(9, 60) * (N + 1) ** 2).astype(np.int64)])
+    for p in samples:
+        s = dofs[off[p]:off[p + 1]]
+        mine = s[own[s] == p]
+        rows = orc.patch_rows(0, int(p))[: len(mine) * len(s)].reshape(len(mine), len(s))
+        want = x[mine] + OMEGA * rows @ r[s]
+        assert np.abs(got[mine] - want).max() <= 1e-12 * max(np.abs(want).max(), 1.0), p
