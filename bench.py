@@ -85,7 +85,8 @@ def parse():
     ap.add_argument("--no-single", action="store_true",
                     help="2d-batch: skip timing the single-problem FP64 form on the same problems")
     ap.add_argument("--workload", default="2d512",
-                    choices=sorted(WORKLOADS) + ["2d-batch", "3d-precision", "3d-learned", "2d-steps"])
+                    choices=sorted(WORKLOADS) + ["2d-batch", "3d-precision", "3d-learned", "2d-steps",
+                                                 "2d-steps-q1"])
     ap.add_argument("--nprob", type=int, default=256, help="problems of the 2d-batch workload")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -597,23 +598,28 @@ def run_precision(args):
     print(json.dumps(out), flush=True)
 
 
-def run_steps(args):
+def run_steps(args, q1=False):
     """Smoothing-steps study (the paper's comparison of AV, MV and RAV over the
     number of smoothing steps, Sec. 4.2, Fig. 7) on the 2-D 512^2 manufactured
     Stokes problem (or --N): for nu = 1..6, a stationary V(nu, nu) solve to a
     1e-8 residual reduction with RAV (omega 0.5, FP64 factored inverses), AV
     (0.1) and coloured MV (0.66), all FP64; cycles, seconds and seconds per
-    cycle for each."""
+    cycle for each.  q1: the same on the paper's stabilised Q1-Q1 element
+    (beta 0.02) with its damping, RAV and MV 0.66, AV 0.1."""
     import torch
     import paper_2103_10127_gb300 as R
 
     torch.cuda.set_device(0)
     N = args.N or 512
     nlev = args.levels or 7
-    mg = R.Multigrid(2, N, nlev, bc=R.BC_NOSLIP)
+    if q1:
+        mg = R.Multigrid(2, N, nlev, bc=R.BC_NOSLIP, element=R.ELEM_Q1Q1, beta=0.02)
+    else:
+        mg = R.Multigrid(2, N, nlev, bc=R.BC_NOSLIP)
     b = mg.rhs(R.F_PSI)
     res = {}
-    for name, kind, omega in (("RAV", R.RAV, 0.5), ("AV", R.AV, 0.1), ("MV", R.MV_COLOURED, 0.66)):
+    for name, kind, omega in (("RAV", R.RAV, 0.66 if q1 else 0.5), ("AV", R.AV, 0.1),
+                              ("MV", R.MV_COLOURED, 0.66)):
         sm = R.Smoother(mg, kind, R.F64, omega)
         row = {}
         for nu in range(1, 7):
@@ -633,8 +639,9 @@ def run_steps(args):
             for k, row in res.items()}
     out = {"metric": "time to 1e-8 residual reduction per smoother and smoothing steps", "unit": "s",
            "higher_is_better": False, "n_gpus": 1, "dtype": "f64", "data": "synthetic",
-           "config": {"workload": f"2D Stokes Q2-Q1 {N}x{N}, {nlev} levels, manufactured psi solution, "
-                                  "stationary V(nu,nu), nu = 1..6", "dofs": mg.n()},
+           "config": {"workload": f"2D Stokes {'stabilised Q1-Q1 (beta 0.02)' if q1 else 'Q2-Q1'} {N}x{N}, "
+                                  f"{nlev} levels, manufactured psi solution, stationary V(nu,nu), nu = 1..6",
+                      "dofs": mg.n()},
            "results": res,
            "best_seconds": {k: (v["seconds"] if v else None) for k, v in best.items()}}
     print(json.dumps(out), flush=True)
@@ -713,8 +720,8 @@ def main():
     if args.workload == "3d-learned":
         run_learned(args)
         return
-    if args.workload == "2d-steps":
-        run_steps(args)
+    if args.workload in ("2d-steps", "2d-steps-q1"):
+        run_steps(args, q1=args.workload == "2d-steps-q1")
         return
     W = dict(WORKLOADS[args.workload])
     if args.N:

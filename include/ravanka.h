@@ -220,11 +220,11 @@ int rav_coarse_solve(rav_mg* mg, const double* b_dev, double* x_dev, rav_stream 
  * the factored apply (rav_set_apply_split).  Synchronises the stream.
  * On a Q1-Q1 hierarchy subdomain i holds p_i and the free velocity DoFs of the
  * 3^d vertices around vertex i and owns exactly the velocity DoFs of vertex i
- * and p_i (the paper's restricted set, Sec. 3); only RAV with the factored
- * storage (RAV_F64, RAV_F32_FACT, RAV_BF16_FACT) is offered there, with
- * s = c_ii - b^T A^{-1} b (c_ii the stabilisation's diagonal entry), one
- * thread per subdomain and no apply split; other kinds and formats return
- * RAV_ERR_ARG.
+ * and p_i (the paper's restricted set, Sec. 3); RAV takes the factored
+ * storage only (RAV_F64, RAV_F32_FACT, RAV_BF16_FACT; other formats return
+ * RAV_ERR_ARG), with s = c_ii - b^T A^{-1} b (c_ii the stabilisation's
+ * diagonal entry), one thread per subdomain and no apply split; AV and MV
+ * store the full fp64 L_i^{-1} over the 3^d d + 1 box positions.
  * Errors: RAV_ERR_ARG, RAV_ERR_CUDA, RAV_ERR_SINGULAR_PATCH. */
 int vanka_setup(rav_mg* mg, int kind, int precision, double omega, rav_stream stream, rav_smoother** out);
 void vanka_destroy(rav_smoother* sm);
@@ -257,8 +257,8 @@ int rav_get_patches(const rav_smoother* sm, int level, int32_t* offsets_dev, int
 /* Stored inverse rows of subdomains [first, first+count) of level l, expanded
  * to fp64 (scale applied) in the sorted DoF order of each subdomain, into
  * out_dev[count][rows_max][cols_max] (zero padded); rows_max/cols_max are
- * 2^d d + 1 and 5^d d + 1 for RAV, 5^d d + 1 for both otherwise, and d + 1 and
- * 3^d d + 1 on a Q1-Q1 hierarchy. */
+ * 2^d d + 1 and 5^d d + 1 for RAV, 5^d d + 1 for both otherwise; on a Q1-Q1
+ * hierarchy d + 1 and 3^d d + 1 for RAV, 3^d d + 1 for both otherwise. */
 int rav_get_inverse_rows(const rav_smoother* sm, int level, int64_t first, int64_t count, double* out_dev,
                          rav_stream stream);
 

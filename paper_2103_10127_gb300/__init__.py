@@ -272,7 +272,8 @@ class Smoother:
     def inverse_rows(self, level, first, count, stream=None):
         d = self.mg.dim
         if self.mg.element == ELEM_Q1Q1:
-            nc, nr = 3 ** d * d + 1, d + 1
+            nc = 3 ** d * d + 1
+            nr = d + 1 if self.kind == RAV else nc
         else:
             nc = 5 ** d * d + 1
             nr = (2 ** d * d + 1) if self.kind == RAV else nc

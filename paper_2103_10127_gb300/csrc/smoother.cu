@@ -975,21 +975,30 @@ __device__ __forceinline__ bool q1_free(const Geo& g, const int* v, int m) {
   return ok;
 }
 
-// One warp per subdomain (4 per block): gather K, b and c from the CSR rows,
-// Cholesky K = L L^T, solve for K^{-1} e_CEN and K^{-1} b_c (one lane per
-// right-hand side), write the NF stored values in fp64 to out (SoA, stride np).
-template <int D>
+// One warp per subdomain: gather K, b and c from the CSR rows, Cholesky
+// K = L L^T, then one lane per right-hand side.  RAV (FULL = false, 4 warps
+// per block): solve for K^{-1} e_CEN and K^{-1} b_c and write the NF stored
+// values in fp64 to out (SoA, stride np).  AV/MV (FULL = true): solve for
+// every column of K^{-1} and the w_c, and write the whole L_i^{-1} over the
+// box positions (velocity m d + c, pressure last; identity at absent
+// positions), column-major, NC x NC per subdomain.
+template <int D, bool FULL>
 __global__ void __launch_bounds__(128) k_factor_q1(Geo g, const int64_t* __restrict__ rp,
                                                    const double* __restrict__ va, int64_t np,
                                                    double* __restrict__ out, int* __restrict__ err) {
   using B = Q1Box<D>;
-  constexpr int NV = B::NV, NR = B::NR, NF = B::NF;
-  __shared__ double sK[4][NV * NV];
-  __shared__ double sB[4][NV * D];
-  __shared__ double sZ[4][NR * NV];
-  __shared__ int sv[4][NV];
+  constexpr int NV = B::NV, NF = B::NF, NC = B::NC;
+  constexpr int NE = FULL ? NV : 1;  // unit right-hand sides
+  constexpr int NRHS = NE + D;
+  constexpr int WPB = (FULL && D == 3) ? 2 : 4;
+  static_assert(NRHS <= 32, "one lane per right-hand side");
+  __shared__ double sK[WPB][NV * NV];
+  __shared__ double sB[WPB][NV * D];
+  __shared__ double sZ[WPB][NRHS * NV];
+  __shared__ int sv[WPB][NV];
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int64_t p = blockIdx.x * 4ll + w;
+  if (w >= WPB) return;
+  const int64_t p = blockIdx.x * (int64_t)WPB + w;
   if (p >= np) return;  // whole warps
   double* K = sK[w];
   double* b = sB[w];
@@ -1073,10 +1082,11 @@ __global__ void __launch_bounds__(128) k_factor_q1(Geo g, const int64_t* __restr
     }
     __syncwarp();
   }
-  if (lane < NR) {  // right-hand side lane: e_CEN, then b_0 .. b_{D-1}
+  if (lane < NRHS) {  // right-hand side lane: unit vectors (e_CEN, or all), then b_0 .. b_{D-1}
     double* z = Z + lane * NV;
+    const int eidx = FULL ? lane : B::CEN;
     for (int i = 0; i < NV; ++i) {
-      double acc = lane == 0 ? (i == B::CEN ? 1.0 : 0.0) : b[i * D + lane - 1];
+      double acc = lane < NE ? (i == eidx ? 1.0 : 0.0) : b[i * D + lane - NE];
       for (int j = 0; j < i; ++j) acc -= K[i * NV + j] * z[j];
       z[i] = acc / K[i * NV + i];
     }
@@ -1091,22 +1101,190 @@ __global__ void __launch_bounds__(128) k_factor_q1(Geo g, const int64_t* __restr
   if (lane == 0) {
     double sch = cdiag;
     for (int c = 0; c < D; ++c)
-      for (int m = 0; m < NV; ++m) sch -= b[m * D + c] * Z[(1 + c) * NV + m];
+      for (int m = 0; m < NV; ++m) sch -= b[m * D + c] * Z[(NE + c) * NV + m];
     if (!(fabs(sch) > 0.0) || !isfinite(sch)) bad = 1;
     else sinv = 1.0 / sch;
   }
   sinv = __shfl_sync(0xffffffffu, sinv, 0);
   bad = __shfl_sync(0xffffffffu, bad, 0);
-  for (int k = lane; k < NF; k += 32) {
-    double val;
-    if (k < NV) val = Z[k];
-    else if (k < NV + NV * D) {
-      const int m = (k - NV) / D, c = (k - NV) % D;
-      val = Z[(1 + c) * NV + m];
-    } else val = sinv;
-    out[k * np + p] = val;
+  if (FULL) {
+    // L^{-1}[j][k] at k NC + j: (m,c | n,c') = delta_cc' K^{-1}[m][n] + w(m,c) w(n,c') / s,
+    // (m,c | p) = -w(m,c) / s, (p | n,c') = -w(n,c') / s, (p | p) = 1 / s
+    double* o = out + p * (int64_t)NC * NC;
+    for (int e = lane; e < NC * NC; e += 32) {
+      const int k = e / NC, j = e % NC;
+      double val;
+      if (j == NC - 1 && k == NC - 1) val = sinv;
+      else if (j == NC - 1) val = -Z[(NE + k % D) * NV + k / D] * sinv;
+      else if (k == NC - 1) val = -Z[(NE + j % D) * NV + j / D] * sinv;
+      else
+        val = (j % D == k % D ? Z[(j / D) * NV + k / D] : 0.0) +
+              Z[(NE + j % D) * NV + j / D] * Z[(NE + k % D) * NV + k / D] * sinv;
+      o[e] = val;
+    }
+  } else {
+    for (int k = lane; k < NF; k += 32) {
+      double val;
+      if (k < NV) val = Z[k];
+      else if (k < NV + NV * D) {
+        const int m = (k - NV) / D, c = (k - NV) % D;
+        val = Z[(1 + c) * NV + m];
+      } else val = sinv;
+      out[k * np + p] = val;
+    }
   }
   if (bad && lane == 0) atomicExch(err, 1);
+}
+
+// Global DoF of Q1-Q1 box position k (velocity m d + c, pressure NC - 1) of the
+// subdomain at vertex v, -1 if not in it.
+template <int D>
+__device__ __forceinline__ int64_t q1_box_dof(const Geo& g, const int* v, int64_t p, int k) {
+  constexpr int NC = Q1Box<D>::NC;
+  if (k == NC - 1) return g.n_u + p;
+  const int m = k / D;
+  if (!q1_free<D>(g, v, m)) return -1;
+  int a[3];
+  q1_tuple(m, a);
+  int64_t id = 0;
+  for (int d = D - 1; d >= 0; --d) id = id * (g.N + 1) + (v[d] - 1 + a[d]);
+  return D * id + k % D;
+}
+template <int D>
+__device__ void q1_warp_full_solve(const double* __restrict__ Inv, const double* rloc, double* y) {
+  constexpr int NC = Q1Box<D>::NC;
+  const int lane = threadIdx.x & 31;
+  for (int j = lane; j < NC; j += 32) {
+    double s = 0.0;
+    for (int k = 0; k < NC; ++k) s += Inv[(int64_t)k * NC + j] * rloc[k];
+    y[j] = s;
+  }
+  __syncwarp();
+}
+
+// AV (Eq. 12) on Q1-Q1, step 1: corr[p][k] = omega_p (L_p^{-1} r_p)_k, one warp per subdomain.
+template <int D>
+__global__ void k_av_q1_corr(Geo g, const double* __restrict__ inv, const double* __restrict__ omega,
+                             const double* __restrict__ r, double* __restrict__ corr) {
+  constexpr int NC = Q1Box<D>::NC;
+  constexpr int WPB = 4;
+  __shared__ double rl[WPB][NC], yl[WPB][NC];
+  const int wi = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t p = blockIdx.x * (int64_t)WPB + wi;
+  if (p >= g.n_p) return;
+  int v[3] = {0, 0, 0};
+  vertex_of_t<D>(g, p, v);
+  for (int k = lane; k < NC; k += 32) {
+    const int64_t dof = q1_box_dof<D>(g, v, p, k);
+    rl[wi][k] = dof >= 0 ? r[dof] : 0.0;
+  }
+  __syncwarp();
+  q1_warp_full_solve<D>(inv + p * (int64_t)NC * NC, rl[wi], yl[wi]);
+  const double om = omega[p];
+  for (int k = lane; k < NC; k += 32) corr[p * NC + k] = om * yl[wi][k];
+}
+
+// AV on Q1-Q1, step 2: x[dof] += sum over the subdomains containing dof (ascending) of corr.
+template <int D>
+__global__ void k_av_q1_gather(Geo g, const double* __restrict__ corr, double* __restrict__ x) {
+  constexpr int NC = Q1Box<D>::NC;
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= g.n) return;
+  if (i >= g.n_u) {
+    x[i] += corr[(i - g.n_u) * NC + NC - 1];
+    return;
+  }
+  int64_t I[3] = {0, 0, 0};
+  int c;
+  vel_node(g, i, I, c);
+  if (node_on_boundary(g, I)) return;
+  double s = 0.0;
+  for (int v2 = (D == 3 ? (int)I[2] - 1 : 0); v2 <= (D == 3 ? (int)I[2] + 1 : 0); ++v2)
+    for (int v1 = (int)I[1] - 1; v1 <= (int)I[1] + 1; ++v1)
+      for (int v0 = (int)I[0] - 1; v0 <= (int)I[0] + 1; ++v0) {
+        const int vv[3] = {v0, v1, v2};
+        int64_t p = 0;
+        int m = 0;
+        for (int d = D - 1; d >= 0; --d) {
+          p = p * (g.N + 1) + vv[d];
+          m = m * 3 + (int)(I[d] - vv[d] + 1);
+        }
+        s += corr[p * NC + m * D + c];  // free I: every v in [I-1, I+1] is a vertex
+      }
+  x[i] += s;
+}
+
+// MV (Eq. 11 with the residual refresh of Eq. 15) on Q1-Q1 over one colour
+// class (vertices equal mod 4 on every axis): a subdomain writes vertices
+// v-1..v+1 and its refresh reads v-2..v+2, so subdomains of a class four
+// vertices apart neither overlap nor read each other's writes.
+template <int D>
+__global__ void k_mv_q1_colour(Geo g, const int64_t* __restrict__ rp, const int32_t* __restrict__ ci,
+                               const double* __restrict__ va, const double* __restrict__ inv,
+                               const double* __restrict__ omega, const double* __restrict__ b,
+                               double* __restrict__ x, int colour) {
+  constexpr int NC = Q1Box<D>::NC;
+  constexpr int WPB = 4;
+  __shared__ double rl[WPB][NC], yl[WPB][NC];
+  __shared__ int64_t dl[WPB][NC];
+  const int wi = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  int col[3] = {colour & 3, (colour >> 2) & 3, (colour >> 4) & 3};
+  int cnt[3] = {1, 1, 1};
+  int64_t tot = 1;
+  for (int d = 0; d < D; ++d) {
+    cnt[d] = col[d] <= g.N ? (g.N - col[d]) / 4 + 1 : 0;
+    tot *= cnt[d];
+  }
+  const int64_t t = blockIdx.x * (int64_t)WPB + wi;
+  if (t >= tot) return;
+  int v[3] = {0, 0, 0};
+  {
+    int64_t tt = t;
+    for (int d = 0; d < D; ++d) { v[d] = col[d] + 4 * (int)(tt % cnt[d]); tt /= cnt[d]; }
+  }
+  int64_t p = 0;
+  for (int d = D - 1; d >= 0; --d) p = p * (g.N + 1) + v[d];
+  for (int k = lane; k < NC; k += 32) {
+    const int64_t dof = q1_box_dof<D>(g, v, p, k);
+    dl[wi][k] = dof;
+    double s = 0.0;
+    if (dof >= 0) {
+      s = b[dof];
+      for (int64_t q = rp[dof]; q < rp[dof + 1]; ++q) s -= va[q] * x[ci[q]];
+    }
+    rl[wi][k] = s;
+  }
+  __syncwarp();
+  q1_warp_full_solve<D>(inv + p * (int64_t)NC * NC, rl[wi], yl[wi]);
+  const double om = omega[p];
+  for (int k = lane; k < NC; k += 32)
+    if (dl[wi][k] >= 0) x[dl[wi][k]] += om * yl[wi][k];
+}
+
+// Full inverses (AV/MV) on Q1-Q1 expanded to the compact sorted order.
+template <int D>
+__global__ void k_export_q1_full(Geo g, const double* __restrict__ inv, int64_t first, int64_t count,
+                                 double* __restrict__ out) {
+  constexpr int NC = Q1Box<D>::NC;
+  __shared__ int colmap[NC];
+  __shared__ int ncol;
+  const int64_t p = first + blockIdx.x;
+  int v[3] = {0, 0, 0};
+  vertex_of_t<D>(g, p, v);
+  if (threadIdx.x == 0) {
+    int c = 0;
+    for (int k = 0; k < NC; ++k)
+      if (q1_box_dof<D>(g, v, p, k) >= 0) colmap[c++] = k;
+    ncol = c;
+  }
+  __syncthreads();
+  double* o = out + blockIdx.x * (int64_t)NC * NC;
+  for (int e = threadIdx.x; e < NC * NC; e += blockDim.x) {
+    const int jr = e / NC, kc = e % NC;
+    double val = 0.0;
+    if (jr < ncol && kc < ncol) val = inv[p * (int64_t)NC * NC + (int64_t)colmap[kc] * NC + colmap[jr]];
+    o[e] = val;
+  }
 }
 
 template <typename T>
@@ -1383,8 +1561,9 @@ static int setup_level(rav_smoother* sm, int l, cudaStream_t s, int* err_dev) {
   return RAV_OK;
 }
 
-// Q1-Q1 level: factored storage only (RAV_F64 / RAV_F32_FACT / RAV_BF16_FACT),
-// one thread per subdomain, no split.
+// Q1-Q1 level: RAV with factored storage (RAV_F64 / RAV_F32_FACT /
+// RAV_BF16_FACT), one thread per subdomain, no split; AV and MV with the full
+// fp64 inverse per subdomain.
 template <int D>
 static int setup_level_q1(rav_smoother* sm, int l, cudaStream_t s, int* err_dev) {
   using B = Q1Box<D>;
@@ -1393,20 +1572,30 @@ static int setup_level_q1(rav_smoother* sm, int l, cudaStream_t s, int* err_dev)
   const Geo& g = L.g;
   S_.np = g.n_p;
   S_.units = g.n_p;
-  S_.factored = true;
   S_.split = 1;
   RAV_CUDA(cudaMalloc(&S_.omega, sizeof(double) * S_.np));
   k_fill<<<grid_for(S_.np, 256), 256, 0, s>>>(S_.omega, S_.np, sm->omega);
+  if (sm->kind != RAV_RAV) {
+    S_.factored = false;
+    RAV_CUDA(cudaMalloc(&S_.inv, sizeof(double) * S_.np * B::NC * B::NC));
+    if (sm->kind == RAV_AV) RAV_CUDA(cudaMalloc(&S_.corr, sizeof(double) * S_.np * B::NC));
+    constexpr int wpb = D == 3 ? 2 : 4;
+    k_factor_q1<D, true><<<(unsigned)((S_.np + wpb - 1) / wpb), 32 * wpb, 0, s>>>(g, L.rp, L.va, S_.np,
+                                                                                (double*)S_.inv, err_dev);
+    RAV_CUDA(cudaGetLastError());
+    return RAV_OK;
+  }
+  S_.factored = true;
   const int64_t tot = S_.np * B::NF;
   RAV_CUDA(cudaMalloc(&S_.inv, elem_size(sm->prec) * tot));
   const unsigned gf = (unsigned)((S_.np + 3) / 4);
   if (sm->prec == RAV_F64) {
-    k_factor_q1<D><<<gf, 128, 0, s>>>(g, L.rp, L.va, S_.np, (double*)S_.inv, err_dev);
+    k_factor_q1<D, false><<<gf, 128, 0, s>>>(g, L.rp, L.va, S_.np, (double*)S_.inv, err_dev);
   } else {
     RAV_CUDA(cudaMalloc(&S_.r32, sizeof(float) * g.n));
     double* stage = nullptr;
     RAV_CUDA(cudaMallocAsync(&stage, sizeof(double) * tot, s));
-    k_factor_q1<D><<<gf, 128, 0, s>>>(g, L.rp, L.va, S_.np, stage, err_dev);
+    k_factor_q1<D, false><<<gf, 128, 0, s>>>(g, L.rp, L.va, S_.np, stage, err_dev);
     const unsigned gp = (unsigned)((tot + 255) / 256);
     if (sm->prec == RAV_F32_FACT) k_q1_pack<float><<<gp, 256, 0, s>>>(stage, tot, (float*)S_.inv);
     else k_q1_pack<__nv_bfloat16><<<gp, 256, 0, s>>>(stage, tot, (__nv_bfloat16*)S_.inv);
@@ -1424,7 +1613,7 @@ extern "C" int vanka_setup(rav_mg* mg, int kind, int precision, double omega, ra
   if (precision < RAV_F64 || precision > RAV_BF16_FACT) return RAV_ERR_ARG;
   if (kind != RAV_RAV && precision != RAV_F64 && precision != RAV_F64_ROWS) return RAV_ERR_ARG;
   const bool q1 = mg->elem == RAV_ELEM_Q1Q1;
-  if (q1 && (kind != RAV_RAV || !factored_prec(precision))) return RAV_ERR_ARG;
+  if (q1 && kind == RAV_RAV && !factored_prec(precision)) return RAV_ERR_ARG;
   cudaStream_t s = S(stream);
   *out = nullptr;
   rav_smoother* sm = new rav_smoother();
@@ -1599,7 +1788,18 @@ int apply_with_omega(rav_smoother* sm, int level, const double* r, double* x, co
   }
   cudaEvent_t e0 = nullptr;
   RAV_TRY(prof_begin(mg, level, PROF_APPLY, s, &e0));
-  if (g.q == 1) {
+  if (g.q == 1 && sm->kind == RAV_AV) {
+    const unsigned gb = (unsigned)((g.n_p + 3) / 4);
+    const int gg = (int)((g.n + 255) / 256);
+    if (D == 2) {
+      k_av_q1_corr<2><<<gb, 128, 0, s>>>(g, (double*)SL.inv, omega, r, SL.corr);
+      k_av_q1_gather<2><<<gg, 256, 0, s>>>(g, SL.corr, x);
+    } else {
+      k_av_q1_corr<3><<<gb, 128, 0, s>>>(g, (double*)SL.inv, omega, r, SL.corr);
+      k_av_q1_gather<3><<<gg, 256, 0, s>>>(g, SL.corr, x);
+    }
+    note_launch(2);
+  } else if (g.q == 1) {
     const unsigned gb = (unsigned)((SL.np + 127) / 128);
 #define RAV_APPLY_Q1(DD, T) \
   k_rav_apply_q1<DD, T><<<gb, 128, 0, s>>>(g, (const T*)SL.inv, omega, (const AccT<T>*)rr, x, SL.np)
@@ -1703,8 +1903,14 @@ int rav_smooth_impl(rav_smoother* sm, int level, double* x, const double* b, int
         }
         if (cnt == 0) continue;
         const unsigned gb = (unsigned)((cnt + 3) / 4);
-        if (D == 2) k_mv_colour<2><<<gb, 128, 0, s>>>(g, L.rp, L.ci, L.va, (double*)SL.inv, SL.omega, b, x, c);
-        else k_mv_colour<3><<<gb, 128, 0, s>>>(g, L.rp, L.ci, L.va, (double*)SL.inv, SL.omega, b, x, c);
+        if (g.q == 1) {
+          if (D == 2) k_mv_q1_colour<2><<<gb, 128, 0, s>>>(g, L.rp, L.ci, L.va, (double*)SL.inv, SL.omega, b, x, c);
+          else k_mv_q1_colour<3><<<gb, 128, 0, s>>>(g, L.rp, L.ci, L.va, (double*)SL.inv, SL.omega, b, x, c);
+        } else if (D == 2) {
+          k_mv_colour<2><<<gb, 128, 0, s>>>(g, L.rp, L.ci, L.va, (double*)SL.inv, SL.omega, b, x, c);
+        } else {
+          k_mv_colour<3><<<gb, 128, 0, s>>>(g, L.rp, L.ci, L.va, (double*)SL.inv, SL.omega, b, x, c);
+        }
         note_launch();
       }
       RAV_CUDA(cudaGetLastError());
@@ -1805,7 +2011,10 @@ extern "C" int rav_get_inverse_rows(const rav_smoother* sm, int level, int64_t f
   if (count == 0) return RAV_OK;
   cudaStream_t s = S(stream);
   const unsigned gb = (unsigned)count;
-  if (g.q == 1) {
+  if (g.q == 1 && sm->kind != RAV_RAV) {
+    if (g.dim == 2) k_export_q1_full<2><<<gb, 256, 0, s>>>(g, (const double*)SL.inv, first, count, out);
+    else k_export_q1_full<3><<<gb, 256, 0, s>>>(g, (const double*)SL.inv, first, count, out);
+  } else if (g.q == 1) {
 #define RAV_EXP_Q1(DD, T) k_export_q1<DD, T><<<gb, 128, 0, s>>>(g, (const T*)SL.inv, SL.np, first, count, out)
     if (sm->prec == RAV_F64) {
       if (g.dim == 2) RAV_EXP_Q1(2, double);

@@ -189,6 +189,51 @@ def test_factored_reduced_storage_matches_the_oracle(case, prec):
     assert np.linalg.norm(d - want) <= 1e-5 * np.linalg.norm(want)
 
 
+@pytest.mark.parametrize("case", CASES, ids=IDS)
+@pytest.mark.parametrize("kind,omega", [(R.AV, 0.1), (R.MV_COLOURED, OMEGA)], ids=["av", "mv"])
+def test_comparator_inverses_and_steps_match(case, kind, omega):
+    """AV (Eq. 12) and coloured MV (Eqs. 11, 15) on Q1-Q1: the full stored
+    L_i^{-1} to 1e-11 and two smoothing steps to 1e-12 against the oracle (MV in
+    the same 4^d colour order)."""
+    mg, orc = make_pair(**case)
+    sm = R.Smoother(mg, kind, R.F64, omega)
+    orc.setup_smoother(O.AV if kind == R.AV else O.MV_COLOURED, omega)
+    lev = case["nlev"] - 1
+    npatch = mg.counts(lev)["n_p"]
+    got = cpu(sm.inverse_rows(lev, 0, npatch))
+    for p in range(npatch):
+        want = orc.inverse(lev, p)
+        g = got[p, : want.shape[0], : want.shape[1]]
+        assert np.abs(g - want).max() <= 1e-11 * np.abs(want).max(), p
+        assert not got[p, want.shape[0]:, :].any() and not got[p, :, want.shape[1]:].any()
+    rng = np.random.default_rng(31)
+    for lv in range(1, case["nlev"]):
+        n = mg.n(lv)
+        x, b = rng.standard_normal(n), rng.standard_normal(n)
+        want = orc.smooth(lv, x, b, 2)
+        xg = gpu(x)
+        sm.smooth(lv, xg, gpu(b), 2)
+        assert rel(cpu(xg), want) <= 1e-12
+
+
+@pytest.mark.parametrize("nu", [1, 3])
+@pytest.mark.parametrize("kind,omega", [(R.RAV, OMEGA), (R.AV, 0.1), (R.MV_COLOURED, OMEGA)],
+                         ids=["rav", "av", "mv"])
+def test_smoothing_steps_study_matches_the_oracle(kind, omega, nu):
+    """The smoothing-steps comparison (Sec. 4.2) on the paper's element: a 16^2
+    Q1-Q1 cavity, 3 levels, V(nu, nu) to 1e-8 with every smoother: equal cycle
+    counts and per-cycle factors within 2 % of the oracle."""
+    mg, orc = make_pair(2, 16, 3)
+    sm = R.Smoother(mg, kind, R.F64, omega)
+    orc.setup_smoother({R.RAV: O.RAV, R.AV: O.AV, R.MV_COLOURED: O.MV_COLOURED}[kind], omega)
+    it, hist, rc = mg.solve(sm, mg.initial_guess(), mg.rhs(R.F_NONE), tol=1e-8, maxit=300, nu_pre=nu,
+                            nu_post=nu)
+    _, oit, ohist = orc.solve(orc.initial_guess(), orc.rhs(O.F_NONE), tol=1e-8, maxit=300, nu1=nu, nu2=nu)
+    assert rc == 0 and it == oit
+    fac, ofac = hist[1:] / hist[:-1], ohist[1:] / ohist[:-1]
+    assert np.all(np.abs(fac / ofac - 1.0) <= 0.02)
+
+
 @pytest.mark.parametrize("case", CASES[:3], ids=IDS[:3])
 def test_vcycle_matches(case):
     mg, orc = make_pair(**case)
@@ -240,10 +285,10 @@ def test_fgmres_reaches_the_fp64_tolerance(prec):
 
 
 def test_unsupported_combinations_are_rejected():
-    """Q1-Q1 offers RAV with factored storage only; the batched and learned
-    paths are Q2-Q1 only; the apply has no split."""
+    """Q1-Q1 RAV takes the factored storage only, AV/MV fp64 only; the batched
+    and learned paths are Q2-Q1 only; the apply has no split."""
     mg, _ = make_pair(2, 8, 2)
-    for kind, prec in ((R.AV, R.F64), (R.MV_COLOURED, R.F64), (R.RAV, R.F64_ROWS), (R.RAV, R.F32),
+    for kind, prec in ((R.AV, R.F32), (R.MV_COLOURED, R.BF16_FACT), (R.RAV, R.F64_ROWS), (R.RAV, R.F32),
                        (R.RAV, R.BF16), (R.RAV, R.FP8)):
         with pytest.raises(R.RavError):
             R.Smoother(mg, kind, prec, 0.5)
