@@ -73,15 +73,19 @@ __global__ void k_features(Geo g, Coef C, int level, int nlev, float* __restrict
           ++nq;
         }
       }
+  // box nodes J = q v - q + a, a in [0, 2q] per axis (5^d on Q2-Q1, 3^d on Q1-Q1)
+  const int ext = 2 * g.q + 1, last = (int)g.M - 1;
+  int nbox = 1;
+  for (int d = 0; d < D; ++d) nbox *= ext;
   int nin = 0, nbnd = 0, nvalid = 0;
-  for (int m = 0; m < BoxT<D>::NV; ++m) {
-    int a[3];
-    box_tuple(D, m, a);
+  for (int m = 0; m < nbox; ++m) {
     bool in = true, bnd = false;
+    int mm = m;
     for (int d = 0; d < D; ++d) {
-      const int J = 2 * v[d] - 2 + a[d];
-      in &= (J >= 0) & (J <= 2 * g.N);
-      bnd |= (J == 0) | (J == 2 * g.N);
+      const int J = g.q * v[d] - g.q + mm % ext;
+      mm /= ext;
+      in &= (J >= 0) & (J <= last);
+      bnd |= (J == 0) | (J == last);
     }
     nin += in;
     nbnd += in && bnd;
@@ -93,7 +97,7 @@ __global__ void k_features(Geo g, Coef C, int level, int nlev, float* __restrict
   f[2] = (float)log10(amax);
   f[3] = (float)log10(amin);
   f[4] = nlev > 1 ? (float)level / (float)(nlev - 1) : 0.0f;
-  f[5] = (float)(D * nvalid + 1) / (float)BoxT<D>::NC;
+  f[5] = (float)(D * nvalid + 1) / (float)(D * nbox + 1);
   f[6] = nin ? (float)nbnd / (float)nin : 0.0f;
   f[7] = (float)log10(diag / ncell);
 }
@@ -101,18 +105,22 @@ __global__ void k_features(Geo g, Coef C, int level, int nlev, float* __restrict
 // ---------------------------------------------------------------------------
 // Line-search labels.  One warp per subdomain: L c_i on the free rows equals
 // sum_j c_j (row j of L) over the owned DoFs j (L is symmetric on the free
-// DoFs), accumulated in shared memory on the local window of nodes
-// [2v-2, 2v+3]^d (all components) and vertices [v-1, v+2]^d.
+// DoFs), accumulated in shared memory on the local window the owned rows
+// reach: Q2-Q1 nodes [2v-2, 2v+3]^d (all components) and vertices
+// [v-1, v+2]^d; Q1-Q1 vertices [v-1, v+1]^d for velocity and pressure.
 template <int D>
 struct Win {
-  static constexpr int W = 6, WV = 4;
+  static constexpr int W = 6, WV = 4;  // the Q2-Q1 extents, which bound the Q1-Q1 ones
   static constexpr int NNODE = D == 2 ? 36 : 216, NVERT = D == 2 ? 16 : 64;
   static constexpr int NLOC = D * NNODE + NVERT;
 };
+__device__ __forceinline__ int win_w(const Geo& g) { return g.q == 2 ? 6 : 3; }
+__device__ __forceinline__ int win_wv(const Geo& g) { return g.q == 2 ? 4 : 3; }
 
 template <int D>
 __device__ __forceinline__ int win_index(const Geo& g, const int* v, int64_t m) {
   using Wn = Win<D>;
+  const int W = win_w(g), WV = win_wv(g);
   if (m < g.n_u) {
     int64_t id = m / D;
     const int c = (int)(m - id * D);
@@ -120,10 +128,10 @@ __device__ __forceinline__ int win_index(const Geo& g, const int* v, int64_t m) 
     for (int a = 0; a < D; ++a) {
       const int J = (int)(id % g.M);
       id /= g.M;
-      const int o = J - (2 * v[a] - 2);
-      if (o < 0 || o >= Wn::W) return -1;
+      const int o = J - (g.q * v[a] - g.q);
+      if (o < 0 || o >= W) return -1;
       loc += o * mul;
-      mul *= Wn::W;
+      mul *= W;
     }
     return loc * D + c;
   }
@@ -133,9 +141,9 @@ __device__ __forceinline__ int win_index(const Geo& g, const int* v, int64_t m) 
     const int V = (int)(id % (g.N + 1));
     id /= (g.N + 1);
     const int o = V - (v[a] - 1);
-    if (o < 0 || o >= Wn::WV) return -1;
+    if (o < 0 || o >= WV) return -1;
     loc += o * mul;
-    mul *= Wn::WV;
+    mul *= WV;
   }
   return D * Wn::NNODE + loc;
 }
@@ -143,22 +151,23 @@ __device__ __forceinline__ int win_index(const Geo& g, const int* v, int64_t m) 
 template <int D>
 __device__ __forceinline__ int64_t win_dof(const Geo& g, const int* v, int loc) {
   using Wn = Win<D>;
+  const int W = win_w(g), WV = win_wv(g);
   if (loc < D * Wn::NNODE) {
     const int c = loc % D;
     int n = loc / D;
     int64_t J[3] = {0, 0, 0};
     for (int a = 0; a < D; ++a) {
-      J[a] = 2 * v[a] - 2 + n % Wn::W;
-      n /= Wn::W;
-      if (J[a] < 0 || J[a] > 2 * g.N) return -1;
+      J[a] = g.q * v[a] - g.q + n % W;
+      n /= W;
+      if (J[a] < 0 || J[a] > g.M - 1) return -1;
     }
     return D * node_id(g, J) + c;
   }
   int n = loc - D * Wn::NNODE;
   int64_t V[3] = {0, 0, 0};
   for (int a = 0; a < D; ++a) {
-    V[a] = v[a] - 1 + n % Wn::WV;
-    n /= Wn::WV;
+    V[a] = v[a] - 1 + n % WV;
+    n /= WV;
     if (V[a] < 0 || V[a] > g.N) return -1;
   }
   return g.n_u + vert_id(g, V);
@@ -181,18 +190,20 @@ __global__ void k_labels(Geo g, const int64_t* __restrict__ rp, const int32_t* _
   vertex_of(g, p, v);
   for (int k = lane; k < Wn::NLOC; k += 32) buf[wi][k] = 0.0;
   __syncwarp();
-  // owned DoFs: nodes 2v + delta (interior), all components, and p_v
-  for (int j = 0; j < BoxT<D>::NR; ++j) {
+  // owned DoFs: nodes 2v + delta (Q2-Q1) or vertex v itself (Q1-Q1), interior
+  // ones only, all components, and p_v
+  const int nr = (g.q == 2 ? (1 << D) : 1) * D + 1;
+  for (int j = 0; j < nr; ++j) {
     int64_t dof;
-    if (j == BoxT<D>::NR - 1) {
+    if (j == nr - 1) {
       dof = g.n_u + p;
     } else {
       const int q = j / D;
       int64_t J[3] = {0, 0, 0};
       bool ok = true;
       for (int d = 0; d < D; ++d) {
-        J[d] = 2 * v[d] + ((q >> d) & 1);
-        ok &= (J[d] >= 1) & (J[d] <= 2 * g.N - 1);
+        J[d] = g.q == 2 ? 2 * v[d] + ((q >> d) & 1) : v[d];
+        ok &= (J[d] >= 1) & (J[d] <= g.M - 2);
       }
       if (!ok) continue;
       dof = D * node_id(g, J) + j % D;
@@ -404,7 +415,6 @@ extern "C" int rav_mlp_nparam(void) { return kNParam; }
 
 extern "C" int rav_patch_features(rav_smoother* sm, int level, float* feat, rav_stream stream) {
   if (!sm || !feat || level < 1 || level >= sm->mg->nlev) return RAV_ERR_ARG;
-  if (sm->mg->elem != RAV_ELEM_Q2Q1) return RAV_ERR_ARG;  // features and labels of the Q2-Q1 subdomains
   rav_mg* mg = sm->mg;
   const Geo& g = mg->lev[level].g;
   Coef C{mg->eta0, mg->nblobs, mg->blobs_dev};
@@ -417,7 +427,7 @@ extern "C" int rav_patch_features(rav_smoother* sm, int level, float* feat, rav_
 
 extern "C" int rav_label_collection(rav_smoother* sm, int enable) {
   if (!sm) return RAV_ERR_ARG;
-  if (sm->kind != RAV_RAV || sm->mg->elem != RAV_ELEM_Q2Q1) return RAV_ERR_ARG;
+  if (sm->kind != RAV_RAV) return RAV_ERR_ARG;
   rav_mg* mg = sm->mg;
   sm->collect = enable != 0;
   if (!sm->collect) return RAV_OK;

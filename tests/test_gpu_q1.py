@@ -286,7 +286,7 @@ def test_fgmres_reaches_the_fp64_tolerance(prec):
 
 def test_unsupported_combinations_are_rejected():
     """Q1-Q1 RAV takes the factored storage only, AV/MV fp64 only; the batched
-    and learned paths are Q2-Q1 only; the apply has no split."""
+    path is Q2-Q1 only; the apply has no split."""
     mg, _ = make_pair(2, 8, 2)
     for kind, prec in ((R.AV, R.F32), (R.MV_COLOURED, R.BF16_FACT), (R.RAV, R.F64_ROWS), (R.RAV, R.F32),
                        (R.RAV, R.BF16), (R.RAV, R.FP8)):
@@ -297,11 +297,60 @@ def test_unsupported_combinations_are_rejected():
     assert sm.apply_split(1, 1) == 1
     with pytest.raises(R.RavError):
         sm.apply_split(1, 2)
-    from paper_2103_10127_gb300 import learned
-    with pytest.raises(R.RavError):
-        learned.features(sm, 1)
     with pytest.raises(R.RavError):
         R.Batch([mg], [sm], 1)
+
+
+@pytest.mark.parametrize("dim,N,per_patch", [(2, 12, False), (3, 6, True)])
+def test_learned_damping_labels_match_the_oracle(dim, N, per_patch):
+    """Line-search labels of the learned damping on Q1-Q1 subdomains (graded
+    blob problems; in 3-D gathered at non-uniform current weights) equal the
+    oracle's coordinate minimisers."""
+    from paper_2103_10127_gb300 import _capi, learned
+    mg, orc = make_pair(dim, N, 2, graded=True, nblobs=5, bc=O.BC_NOSLIP, s_max=2.0, seed=12)
+    sm = R.Smoother(mg, R.RAV, R.F64, OMEGA)
+    npatch = mg.counts(1)["n_p"]
+    w = None
+    if per_patch:
+        w = (0.2 + 0.8 * inputs.uniform(13, npatch)).astype(np.float32)
+        sm.set_omega(1, torch.from_numpy(w).cuda())
+    orc.build_patches(1)
+    n = mg.n(1)
+    x, b = inputs.normal(14, n), inputs.normal(15, n)
+    lib = _capi.load()
+    assert lib.rav_label_collection(sm.h, 1) == 0
+    sm.smooth(1, torch.from_numpy(x).cuda(), torch.from_numpy(b).cuda(), 1)
+    y = torch.empty(npatch, dtype=torch.float32, device="cuda")
+    assert lib.rav_read_labels(sm.h, 1, learned._p(y), learned._s()) == 0
+    assert lib.rav_label_collection(sm.h, 0) == 0
+    om = np.full(npatch, OMEGA) if w is None else w.astype(np.float64)
+    want = orc.labels(1, orc.residual(1, x, b), omega=om)
+    assert np.abs(y.cpu().numpy() - want).max() <= 1e-6
+
+
+def test_learned_damping_features_on_q1_subdomains():
+    """The cell-based features (viscosity, aspect, level, diagonal) equal those
+    of the Q2-Q1 hierarchy on the same grid (the same cells surround a vertex);
+    the size feature is n_i / (3^d d + 1) from the subdomain lists and the
+    Dirichlet feature the boundary share of the in-domain box vertices."""
+    from paper_2103_10127_gb300 import learned
+    N = 8
+    coords = inputs.graded_coordinates(N, 4.0, 2)
+    blobs = inputs.viscosity_blobs(11, k=3, s_max=3.0)
+    mg1 = R.Multigrid(2, N, 2, coords=coords, blobs=blobs, bc=R.BC_NOSLIP, element=R.ELEM_Q1Q1, beta=BETA)
+    mg2 = R.Multigrid(2, N, 2, coords=coords, blobs=blobs, bc=R.BC_NOSLIP)
+    s1, s2 = R.Smoother(mg1, R.RAV, R.F64, OMEGA), R.Smoother(mg2, R.RAV, R.F64, 0.5)
+    f1, f2 = learned.features(s1, 1).cpu().numpy(), learned.features(s2, 1).cpu().numpy()
+    keep = [0, 1, 2, 3, 4, 7]
+    assert np.array_equal(f1[:, keep], f2[:, keep])
+    off, _, _ = (cpu(t) for t in s1.patches(1))
+    assert np.allclose(f1[:, 5], np.diff(off) / (2 * 9 + 1), rtol=1e-6)
+    for p in range((N + 1) ** 2):
+        v = (p % (N + 1), p // (N + 1))
+        box = [(v[0] - 1 + a, v[1] - 1 + c) for a in range(3) for c in range(3)]
+        inside = [(i, j) for i, j in box if 0 <= i <= N and 0 <= j <= N]
+        bnd = [(i, j) for i, j in inside if i in (0, N) or j in (0, N)]
+        assert abs(f1[p, 6] - len(bnd) / len(inside)) <= 1e-6, p
 
 
 @pytest.mark.slow
