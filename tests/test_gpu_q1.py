@@ -385,3 +385,67 @@ def test_full_size_1024_sampled_parity():
         rows = orc.patch_rows(0, int(p))[: len(mine) * len(s)].reshape(len(mine), len(s))
         want = x[mine] + OMEGA * rows @ r[s]
         assert np.abs(got[mine] - want).max() <= 1e-12 * max(np.abs(want).max(), 1.0), p
+
+
+# --------------------------------------------------------------------------- edge cases
+@pytest.mark.parametrize("dim,N", [(2, 4), (3, 2)])
+def test_single_level_cycle_is_the_exact_coarse_solve(dim, N):
+    """One Q1-Q1 level: the V-cycle is the bordered LU solve (residual at
+    roundoff after one cycle, equal to the oracle's coarse solve)."""
+    mg, orc = make_pair(dim, N, 1, bc=O.BC_QUADRATIC)
+    sm = R.Smoother(mg, R.RAV, R.F64, OMEGA)
+    b = mg.rhs(R.F_QUADRATIC)
+    x = mg.initial_guess()
+    mg.vcycle(sm, x, b, 2, 2)
+    _, r = mg.residual(0, x, b, norm=True)
+    _, r0 = mg.residual(0, mg.initial_guess(), b, norm=True)
+    assert r <= 1e-11 * r0
+    ob, ox = orc.rhs(O.F_QUADRATIC), orc.initial_guess()
+    want = ox + orc.coarse_solve(orc.residual(0, ox, ob))
+    nu = mg.counts(0)["n_u"]
+    assert np.abs(cpu(x)[:nu] - want[:nu]).max() <= 1e-10 * max(1.0, np.abs(want[:nu]).max())
+    it, _, rc = mg.solve(sm, mg.initial_guess(), b, tol=1e-8, maxit=5)
+    assert rc == 0 and it == 1
+
+
+def test_zero_problem_needs_no_iteration():
+    mg, _ = make_pair(2, 8, 2, bc=O.BC_NOSLIP)
+    sm = R.Smoother(mg, R.RAV, R.F64, OMEGA)
+    x = mg.initial_guess()
+    for outer in (0, 1):
+        it, _, rc = mg.solve(sm, x, mg.rhs(R.F_NONE), tol=1e-8, maxit=10, outer=outer)
+        assert rc == 0 and it == 0
+    assert not cpu(x).any()
+
+
+@pytest.mark.parametrize("kind,prec", [(R.RAV, R.F64), (R.RAV, R.F32_FACT), (R.RAV, R.BF16_FACT), (R.AV, R.F64),
+                                       (R.MV_COLOURED, R.F64)], ids=["rav", "rav-f32", "rav-bf16", "av", "mv"])
+def test_zero_damping_zero_steps_and_zero_residual_leave_x_unchanged(kind, prec):
+    mg, _ = make_pair(2, 8, 2, bc=O.BC_CAVITY)
+    rng = np.random.default_rng(1)
+    n = mg.n()
+    x0, b = rng.standard_normal(n), rng.standard_normal(n)
+    x = gpu(x0)
+    R.Smoother(mg, kind, prec, 0.0).smooth(1, x, gpu(b), 3)
+    assert np.array_equal(cpu(x), x0)
+    sm = R.Smoother(mg, kind, prec, OMEGA)
+    sm.smooth(1, x, gpu(b), 0)
+    assert np.array_equal(cpu(x), x0)
+    if kind != R.MV_COLOURED:  # MV has no apply of a given residual
+        sm.apply(1, torch.zeros(n, dtype=torch.float64, device="cuda"), x)
+        assert np.array_equal(cpu(x), x0)
+
+
+@pytest.mark.parametrize("dim,N,nlev", [(2, 4, 2), (3, 4, 2), (2, 6, 2)])
+def test_smallest_hierarchies_match_the_oracle(dim, N, nlev):
+    """Coarsest Q1-Q1 grids of 2 or 3 cells per axis (one or four free vertices)."""
+    mg, orc = make_pair(dim, N, nlev, graded=True, bc=O.BC_NOSLIP)
+    sm = R.Smoother(mg, R.RAV, R.F64, OMEGA)
+    orc.setup_smoother(O.RAV, OMEGA)
+    rng = np.random.default_rng(3)
+    n = mg.n()
+    x, b = rng.standard_normal(n), rng.standard_normal(n)
+    want = orc.vcycle(x, b, 2, 2)
+    xg = gpu(x)
+    mg.vcycle(sm, xg, gpu(b), 2, 2)
+    assert rel(cpu(xg), want) <= 1e-11
