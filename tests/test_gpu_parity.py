@@ -421,3 +421,53 @@ def test_smoothing_steps_study_matches_the_oracle(kind, omega, nu):
     assert rc == 0 and it == oit
     fac, ofac = hist[1:] / hist[:-1], ohist[1:] / ohist[:-1]
     assert np.all(np.abs(fac / ofac - 1.0) <= 0.02)
+
+
+@pytest.mark.slow
+def test_full_size_32cube_sampled_parity():
+    """3-D 32^3 Q2-Q1 with the 20 seeded viscosity blobs (859,812 DoFs), the
+    3-D benchmark's launch configuration: row pointer in full and sampled rows
+    of the fine operator bit-exact in structure and to 1e-13 in value; one RAV
+    step with FP64 factored storage at sampled subdomains (boundary corners and
+    40 random vertices) to 1e-12 against rows the oracle factorises one by one,
+    and the BF16 factored step there within the format's error."""
+    N, nlev = 32, 4
+    blobs = inputs.viscosity_blobs(inputs.BASE_SEED, k=20, s_max=3.0)
+    mg = R.Multigrid(3, N, nlev, blobs=blobs, bc=R.BC_NOSLIP)
+    orc = O.Oracle(3, N, 1, blobs=blobs, bc=O.BC_NOSLIP)
+    rp, ci, va = (cpu(t) for t in mg.csr(nlev - 1))
+    orp, oci, ova = orc.csr(0)
+    assert np.array_equal(rp, orp)
+    rows = (inputs.uniform(41, 500) * (len(rp) - 1)).astype(np.int64)
+    scale = np.abs(ova).max()
+    for i in rows:
+        a, b_ = rp[i], rp[i + 1]
+        assert np.array_equal(ci[a:b_].astype(np.int64), oci[a:b_]), i
+        assert np.abs(va[a:b_] - ova[a:b_]).max() <= 1e-13 * scale, i
+    del ci, va, oci, ova
+    rng = np.random.default_rng(42)
+    n = mg.n()
+    x, b = rng.standard_normal(n), rng.standard_normal(n)
+    r = orc.residual(0, x, b)
+    orc.build_patches(0)
+    off, dofs, own = orc.patches(0)
+    samples = np.concatenate([[0, N, (N + 1) ** 2 - 1, (N + 1) ** 3 - 1],
+                              (inputs.uniform(43, 40) * (N + 1) ** 3).astype(np.int64)])
+    steps = {}
+    for prec in (R.F64, R.BF16_FACT):
+        sm = R.Smoother(mg, R.RAV, prec, 0.5)
+        xg = gpu(x)
+        sm.smooth(nlev - 1, xg, gpu(b), 1)
+        steps[prec] = cpu(xg) - x
+        del sm
+    wants, bf16 = [], []
+    for p in samples:
+        s = dofs[off[p]:off[p + 1]]
+        mine = s[own[s] == p]
+        Li = orc.patch_rows(0, int(p), max_rows=32, max_n=400)[: len(mine) * len(s)].reshape(len(mine), len(s))
+        want = 0.5 * Li @ r[s]
+        assert np.abs(steps[R.F64][mine] - want).max() <= 1e-12 * max(np.abs(want).max(), 1e-300), p
+        wants.append(want)
+        bf16.append(steps[R.BF16_FACT][mine])
+    wants, bf16 = np.concatenate(wants), np.concatenate(bf16)
+    assert 0.0 < np.linalg.norm(bf16 - wants) <= 2e-2 * np.linalg.norm(wants)

@@ -449,3 +449,37 @@ def test_smallest_hierarchies_match_the_oracle(dim, N, nlev):
     xg = gpu(x)
     mg.vcycle(sm, xg, gpu(b), 2, 2)
     assert rel(cpu(xg), want) <= 1e-11
+
+
+@pytest.mark.slow
+def test_full_size_64cube_sampled_parity():
+    """3-D 64^3 Q1-Q1 with 20 seeded blobs (1,098,500 DoFs), the 3-D Q1-Q1
+    benchmark's launch configuration: the fine operator in full, and one RAV
+    step at sampled subdomains against rows the oracle factorises one by one."""
+    N, nlev = 64, 5
+    blobs = inputs.viscosity_blobs(inputs.BASE_SEED, k=20, s_max=2.0)
+    mg = R.Multigrid(3, N, nlev, blobs=blobs, bc=R.BC_NOSLIP, element=R.ELEM_Q1Q1, beta=BETA)
+    orc = O.Oracle(3, N, 1, blobs=blobs, bc=O.BC_NOSLIP, element=O.ELEM_Q1Q1, beta=BETA)
+    rp, ci, va = (cpu(t) for t in mg.csr(nlev - 1))
+    orp, oci, ova = orc.csr(0)
+    assert np.array_equal(rp, orp) and np.array_equal(ci.astype(np.int64), oci)
+    assert np.abs(va - ova).max() <= 1e-13 * np.abs(ova).max()
+    del ci, va, oci, ova
+    sm = R.Smoother(mg, R.RAV, R.F64, OMEGA)
+    rng = np.random.default_rng(44)
+    n = mg.n()
+    x, b = rng.standard_normal(n), rng.standard_normal(n)
+    xg = gpu(x)
+    sm.smooth(nlev - 1, xg, gpu(b), 1)
+    got = cpu(xg)
+    r = orc.residual(0, x, b)
+    orc.build_patches(0)
+    off, dofs, own = orc.patches(0)
+    samples = np.concatenate([[0, N, (N + 1) ** 2 - 1, (N + 1) ** 3 - 1],
+                              (inputs.uniform(45, 60) * (N + 1) ** 3).astype(np.int64)])
+    for p in samples:
+        s = dofs[off[p]:off[p + 1]]
+        mine = s[own[s] == p]
+        rows = orc.patch_rows(0, int(p))[: len(mine) * len(s)].reshape(len(mine), len(s))
+        want = x[mine] + OMEGA * rows @ r[s]
+        assert np.abs(got[mine] - want).max() <= 1e-12 * max(np.abs(want).max(), 1.0), p
