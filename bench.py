@@ -555,7 +555,7 @@ def run_precision(args, q1=False):
     patch inverses stored as fp64 (factored), fp64 rows, fp32, bf16 or fp8:
     wall time and iterations to a 1e-8 residual reduction for each.  q1: the
     stabilised Q1-Q1 element (beta 0.02) on 64^3, 5 levels, contrast up to 1e2,
-    RAV omega 0.66, with the factored fp64 / fp32 / bf16 storage it offers."""
+    RAV omega 0.66, with the same storage formats."""
     import torch
     import paper_2103_10127_gb300 as R
     from paper_2103_10127_gb300 import inputs
@@ -566,7 +566,8 @@ def run_precision(args, q1=False):
     blobs = inputs.viscosity_blobs(inputs.BASE_SEED, k=20, s_max=2.0 if q1 else 3.0)
     if q1:
         mg = R.Multigrid(3, N, nlev, blobs=blobs, bc=R.BC_NOSLIP, element=R.ELEM_Q1Q1, beta=0.02)
-        formats = (("f64-factored", R.F64), ("f32-factored", R.F32_FACT), ("bf16-factored", R.BF16_FACT))
+        formats = (("f64-factored", R.F64), ("f64-rows", R.F64_ROWS), ("f32", R.F32), ("bf16", R.BF16),
+                   ("fp8", R.FP8), ("f32-factored", R.F32_FACT), ("bf16-factored", R.BF16_FACT))
     else:
         mg = R.Multigrid(3, N, nlev, blobs=blobs, bc=R.BC_NOSLIP)
         formats = (("f64-factored", R.F64), ("f64-rows", R.F64_ROWS), ("f32", R.F32), ("bf16", R.BF16),

@@ -220,11 +220,11 @@ int rav_coarse_solve(rav_mg* mg, const double* b_dev, double* x_dev, rav_stream 
  * the factored apply (rav_set_apply_split).  Synchronises the stream.
  * On a Q1-Q1 hierarchy subdomain i holds p_i and the free velocity DoFs of the
  * 3^d vertices around vertex i and owns exactly the velocity DoFs of vertex i
- * and p_i (the paper's restricted set, Sec. 3); RAV takes the factored
- * storage only (RAV_F64, RAV_F32_FACT, RAV_BF16_FACT; other formats return
- * RAV_ERR_ARG), with s = c_ii - b^T A^{-1} b (c_ii the stabilisation's
- * diagonal entry), one thread per subdomain and no apply split; AV and MV
- * store the full fp64 L_i^{-1} over the 3^d d + 1 box positions.
+ * and p_i (the paper's restricted set, Sec. 3); RAV takes every storage
+ * (factored with s = c_ii - b^T A^{-1} b, c_ii the stabilisation's diagonal
+ * entry, or the d + 1 owned rows over the 3^d d + 1 box positions), one thread
+ * per subdomain and no apply split; AV and MV store the full fp64 L_i^{-1}
+ * over the box positions.
  * Errors: RAV_ERR_ARG, RAV_ERR_CUDA, RAV_ERR_SINGULAR_PATCH. */
 int vanka_setup(rav_mg* mg, int kind, int precision, double omega, rav_stream stream, rav_smoother** out);
 void vanka_destroy(rav_smoother* sm);

@@ -280,6 +280,11 @@ struct Fmt<__nv_bfloat16> {
 struct fp8_t {
   uint8_t bits;
 };
+__device__ __forceinline__ fp8_t ld_stream(const fp8_t* p) {
+  fp8_t r;
+  r.bits = __ldcs(reinterpret_cast<const unsigned char*>(p));
+  return r;
+}
 template <>
 struct Fmt<fp8_t> {
   static __device__ fp8_t enc(double v) {
@@ -1293,6 +1298,162 @@ __global__ void k_q1_pack(const double* __restrict__ stage, int64_t n, T* __rest
   if (i < n) out[i] = Fmt<T>::enc(stage[i]);
 }
 
+// Owned row j of L_i^{-1} at box position k (velocity m d + c, pressure NC - 1)
+// from the factored values of subdomain p (stage: SoA, NF x np, fp64):
+//   row c < d (vertex i's component c): delta_{c, k%d} K^{-1}[CEN, k/d] + w(CEN,c) w(k) / s,
+//                                       -w(CEN,c) / s at the pressure;
+//   row d (p_i): -w(k) / s, 1 / s at the pressure.
+template <int D>
+__device__ __forceinline__ double q1_row_entry(const double* __restrict__ stage, int64_t np, int64_t p, int j,
+                                               int k) {
+  using B = Q1Box<D>;
+  constexpr int NV = B::NV, NC = B::NC, NF = B::NF;
+  const double sig = stage[(int64_t)(NF - 1) * np + p];
+  if (j == D) return k == NC - 1 ? sig : -stage[(int64_t)(NV + k) * np + p] * sig;
+  const double wj = stage[(int64_t)(NV + B::CEN * D + j) * np + p];
+  if (k == NC - 1) return -wj * sig;
+  return (k % D == j ? stage[(int64_t)(k / D) * np + p] : 0.0) + wj * stage[(int64_t)(NV + k) * np + p] * sig;
+}
+
+// Q1-Q1 dense-row storage (the owned rows of Sec. 4.3): the d + 1 owned rows
+// over the NC box positions rounded into T (fp8 with an fp32 scale
+// max|row| / 448 per row); element (j, k) of subdomain p at (j NC + k) np + p,
+// the scale of row j at j np + p.  One thread per (row, subdomain).
+template <int D, typename T>
+__global__ void k_q1_rows(const double* __restrict__ stage, int64_t np, T* __restrict__ out,
+                          float* __restrict__ scale) {
+  using B = Q1Box<D>;
+  constexpr int NC = B::NC, NR = B::NR;
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= np * NR) return;
+  const int j = (int)(t / np);
+  const int64_t p = t - j * np;
+  double sc = 1.0;
+  if (Fmt<T>::scaled) {
+    double m = 0.0;
+    for (int k = 0; k < NC; ++k) m = fmax(m, fabs(q1_row_entry<D>(stage, np, p, j, k)));
+    sc = m == 0.0 ? 1.0 : (double)(float)(m / 448.0);
+    scale[(int64_t)j * np + p] = (float)sc;
+  }
+  for (int k = 0; k < NC; ++k)
+    out[((int64_t)j * NC + k) * np + p] = Fmt<T>::enc(q1_row_entry<D>(stage, np, p, j, k) / sc);
+}
+
+// RAV step on Q1-Q1 with dense rows, one thread per subdomain: y_j = sum_k
+// row_j[k] r[k] over the box (fp64, or fp32 on the fp32 residual for reduced
+// formats, times the row scale), x[owned j] += omega y_j.
+template <int D, typename T>
+__global__ void __launch_bounds__(128) k_rav_apply_q1_rows(Geo g, const T* __restrict__ st,
+                                                           const float* __restrict__ scale,
+                                                           const double* __restrict__ omega,
+                                                           const AccT<T>* __restrict__ r, double* __restrict__ x,
+                                                           int64_t np) {
+  using B = Q1Box<D>;
+  using A = AccT<T>;
+  constexpr int NC = B::NC, NR = B::NR;
+  __shared__ float lut[256];
+  if (Fmt<T>::scaled) {
+    for (int i = threadIdx.x; i < 256; i += blockDim.x) {
+      __half_raw h = __nv_cvt_fp8_to_halfraw((__nv_fp8_storage_t)i, __NV_E4M3);
+      lut[i] = __half2float(__half(h));
+    }
+    __syncthreads();
+  }
+  const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (p >= np) return;
+  int v[3] = {0, 0, 0};
+  vertex_of_t<D>(g, p, v);
+  const int N = g.N;
+  const int64_t N1 = N + 1;
+  A y[NR];
+#pragma unroll
+  for (int j = 0; j < NR; ++j) y[j] = 0;
+#pragma unroll
+  for (int a2 = 0; a2 < (D == 3 ? 3 : 1); ++a2) {
+    const int J2 = D == 3 ? v[2] - 1 + a2 : 0;
+    const bool ok2 = D == 2 || (J2 >= 1 && J2 <= N - 1);
+#pragma unroll
+    for (int a1 = 0; a1 < 3; ++a1) {
+      const int J1 = v[1] - 1 + a1;
+      const bool ok1 = ok2 && J1 >= 1 && J1 <= N - 1;
+#pragma unroll
+      for (int a0 = 0; a0 < 3; ++a0) {
+        const int n = a0 + 3 * a1 + 9 * a2;
+        const int J0 = v[0] - 1 + a0;
+        const bool ok = ok1 && J0 >= 1 && J0 <= N - 1;
+        const int64_t base = (int64_t)D * (J0 + N1 * (J1 + N1 * J2));
+#pragma unroll
+        for (int c = 0; c < D; ++c) {
+          const A rv = ok ? r[base + c] : (A)0;
+#pragma unroll
+          for (int j = 0; j < NR; ++j)
+            y[j] += (A)Fmt<T>::dec(ld_stream(st + ((int64_t)j * NC + n * D + c) * np + p), lut) * rv;
+        }
+      }
+    }
+  }
+  const A rp = r[g.n_u + p];
+#pragma unroll
+  for (int j = 0; j < NR; ++j) {
+    y[j] += (A)Fmt<T>::dec(ld_stream(st + ((int64_t)j * NC + NC - 1) * np + p), lut) * rp;
+    if (Fmt<T>::scaled) y[j] *= (A)scale[(int64_t)j * np + p];
+  }
+  const double om = omega[p];
+  bool cfree = true;
+#pragma unroll
+  for (int d = 0; d < D; ++d) cfree &= v[d] >= 1 && v[d] <= N - 1;
+  if (cfree) {
+#pragma unroll
+    for (int c = 0; c < D; ++c) x[D * p + c] += om * (double)y[c];
+  }
+  x[g.n_u + p] += om * (double)y[D];
+}
+
+// Dense Q1-Q1 rows expanded (scale applied) to the compact sorted order.
+template <int D, typename T>
+__global__ void k_export_q1_rows(Geo g, const T* __restrict__ st, const float* __restrict__ scale, int64_t np,
+                                 int64_t first, int64_t count, double* __restrict__ out) {
+  using B = Q1Box<D>;
+  constexpr int NC = B::NC, NR = B::NR;
+  __shared__ float lut[256];
+  __shared__ int colmap[NC], rowmap[NR];
+  __shared__ int ncol, nrow;
+  if (Fmt<T>::scaled) {
+    for (int i = threadIdx.x; i < 256; i += blockDim.x) {
+      __half_raw h = __nv_cvt_fp8_to_halfraw((__nv_fp8_storage_t)i, __NV_E4M3);
+      lut[i] = __half2float(__half(h));
+    }
+  }
+  const int64_t p = first + blockIdx.x;
+  int v[3] = {0, 0, 0};
+  vertex_of_t<D>(g, p, v);
+  if (threadIdx.x == 0) {
+    int c = 0;
+    for (int m = 0; m < B::NV; ++m)
+      if (q1_free<D>(g, v, m))
+        for (int cc = 0; cc < D; ++cc) colmap[c++] = m * D + cc;
+    colmap[c++] = NC - 1;
+    ncol = c;
+    int rr = 0;
+    if (q1_free<D>(g, v, B::CEN))
+      for (int cc = 0; cc < D; ++cc) rowmap[rr++] = cc;
+    rowmap[rr++] = NR - 1;
+    nrow = rr;
+  }
+  __syncthreads();
+  double* o = out + blockIdx.x * (int64_t)NR * NC;
+  for (int e = threadIdx.x; e < NR * NC; e += blockDim.x) {
+    const int jr = e / NC, kc = e % NC;
+    double val = 0.0;
+    if (jr < nrow && kc < ncol) {
+      const int j = rowmap[jr], k = colmap[kc];
+      val = (double)Fmt<T>::dec(st[((int64_t)j * NC + k) * np + p], lut);
+      if (Fmt<T>::scaled) val *= (double)scale[(int64_t)j * np + p];
+    }
+    o[e] = val;
+  }
+}
+
 // RAV step on Q1-Q1 (Eq. 13), one thread per subdomain: with r_u, r_p the
 // residual on the box, t = (w^T r_u - r_p) / s,
 //   x[v, c] += omega (sum_m K^{-1}[CEN, m] r_u[m, c] + w[CEN, c] t)   (v free)
@@ -1562,8 +1723,9 @@ static int setup_level(rav_smoother* sm, int l, cudaStream_t s, int* err_dev) {
 }
 
 // Q1-Q1 level: RAV with factored storage (RAV_F64 / RAV_F32_FACT /
-// RAV_BF16_FACT), one thread per subdomain, no split; AV and MV with the full
-// fp64 inverse per subdomain.
+// RAV_BF16_FACT) or the owned rows (RAV_F64_ROWS / RAV_F32 / RAV_BF16 /
+// RAV_FP8), one thread per subdomain, no split; AV and MV with the full fp64
+// inverse per subdomain.
 template <int D>
 static int setup_level_q1(rav_smoother* sm, int l, cudaStream_t s, int* err_dev) {
   using B = Q1Box<D>;
@@ -1582,6 +1744,28 @@ static int setup_level_q1(rav_smoother* sm, int l, cudaStream_t s, int* err_dev)
     constexpr int wpb = D == 3 ? 2 : 4;
     k_factor_q1<D, true><<<(unsigned)((S_.np + wpb - 1) / wpb), 32 * wpb, 0, s>>>(g, L.rp, L.va, S_.np,
                                                                                 (double*)S_.inv, err_dev);
+    RAV_CUDA(cudaGetLastError());
+    return RAV_OK;
+  }
+  if (!factored_prec(sm->prec)) {
+    S_.factored = false;
+    const int64_t nrow = S_.np * B::NR;
+    RAV_CUDA(cudaMalloc(&S_.inv, elem_size(sm->prec) * nrow * B::NC));
+    if (sm->prec == RAV_FP8) RAV_CUDA(cudaMalloc(&S_.scale, sizeof(float) * nrow));
+    if (sm->prec != RAV_F64_ROWS) RAV_CUDA(cudaMalloc(&S_.r32, sizeof(float) * g.n));
+    double* stage = nullptr;
+    RAV_CUDA(cudaMallocAsync(&stage, sizeof(double) * S_.np * B::NF, s));
+    k_factor_q1<D, false><<<(unsigned)((S_.np + 3) / 4), 128, 0, s>>>(g, L.rp, L.va, S_.np, stage, err_dev);
+    const unsigned gr = (unsigned)((nrow + 127) / 128);
+    switch (sm->prec) {
+      case RAV_F64_ROWS: k_q1_rows<D, double><<<gr, 128, 0, s>>>(stage, S_.np, (double*)S_.inv, S_.scale); break;
+      case RAV_F32: k_q1_rows<D, float><<<gr, 128, 0, s>>>(stage, S_.np, (float*)S_.inv, S_.scale); break;
+      case RAV_BF16:
+        k_q1_rows<D, __nv_bfloat16><<<gr, 128, 0, s>>>(stage, S_.np, (__nv_bfloat16*)S_.inv, S_.scale);
+        break;
+      default: k_q1_rows<D, fp8_t><<<gr, 128, 0, s>>>(stage, S_.np, (fp8_t*)S_.inv, S_.scale); break;
+    }
+    cudaFreeAsync(stage, s);
     RAV_CUDA(cudaGetLastError());
     return RAV_OK;
   }
@@ -1613,7 +1797,6 @@ extern "C" int vanka_setup(rav_mg* mg, int kind, int precision, double omega, ra
   if (precision < RAV_F64 || precision > RAV_BF16_FACT) return RAV_ERR_ARG;
   if (kind != RAV_RAV && precision != RAV_F64 && precision != RAV_F64_ROWS) return RAV_ERR_ARG;
   const bool q1 = mg->elem == RAV_ELEM_Q1Q1;
-  if (q1 && kind == RAV_RAV && !factored_prec(precision)) return RAV_ERR_ARG;
   cudaStream_t s = S(stream);
   *out = nullptr;
   rav_smoother* sm = new rav_smoother();
@@ -1799,6 +1982,27 @@ int apply_with_omega(rav_smoother* sm, int level, const double* r, double* x, co
       k_av_q1_gather<3><<<gg, 256, 0, s>>>(g, SL.corr, x);
     }
     note_launch(2);
+  } else if (g.q == 1 && !SL.factored) {
+    const unsigned gb = (unsigned)((SL.np + 127) / 128);
+    const void* rr = sm->prec == RAV_F64_ROWS ? (const void*)r : (const void*)r32;
+#define RAV_APPLY_Q1R(DD, T)                                                                              \
+  k_rav_apply_q1_rows<DD, T><<<gb, 128, 0, s>>>(g, (const T*)SL.inv, SL.scale, omega, (const AccT<T>*)rr, x, \
+                                                SL.np)
+#define RAV_APPLY_Q1R_D(DD)                                  \
+  switch (sm->prec) {                                        \
+    case RAV_F64_ROWS: RAV_APPLY_Q1R(DD, double); break;     \
+    case RAV_F32: RAV_APPLY_Q1R(DD, float); break;           \
+    case RAV_BF16: RAV_APPLY_Q1R(DD, __nv_bfloat16); break;  \
+    default: RAV_APPLY_Q1R(DD, fp8_t); break;                \
+  }
+    if (D == 2) {
+      RAV_APPLY_Q1R_D(2)
+    } else {
+      RAV_APPLY_Q1R_D(3)
+    }
+#undef RAV_APPLY_Q1R_D
+#undef RAV_APPLY_Q1R
+    note_launch();
   } else if (g.q == 1) {
     const unsigned gb = (unsigned)((SL.np + 127) / 128);
 #define RAV_APPLY_Q1(DD, T) \
@@ -2014,6 +2218,23 @@ extern "C" int rav_get_inverse_rows(const rav_smoother* sm, int level, int64_t f
   if (g.q == 1 && sm->kind != RAV_RAV) {
     if (g.dim == 2) k_export_q1_full<2><<<gb, 256, 0, s>>>(g, (const double*)SL.inv, first, count, out);
     else k_export_q1_full<3><<<gb, 256, 0, s>>>(g, (const double*)SL.inv, first, count, out);
+  } else if (g.q == 1 && !SL.factored) {
+#define RAV_EXP_Q1R(DD, T) \
+  k_export_q1_rows<DD, T><<<gb, 128, 0, s>>>(g, (const T*)SL.inv, SL.scale, SL.np, first, count, out)
+#define RAV_EXP_Q1R_D(DD)                                  \
+  switch (sm->prec) {                                      \
+    case RAV_F64_ROWS: RAV_EXP_Q1R(DD, double); break;     \
+    case RAV_F32: RAV_EXP_Q1R(DD, float); break;           \
+    case RAV_BF16: RAV_EXP_Q1R(DD, __nv_bfloat16); break;  \
+    default: RAV_EXP_Q1R(DD, fp8_t); break;                \
+  }
+    if (g.dim == 2) {
+      RAV_EXP_Q1R_D(2)
+    } else {
+      RAV_EXP_Q1R_D(3)
+    }
+#undef RAV_EXP_Q1R_D
+#undef RAV_EXP_Q1R
   } else if (g.q == 1) {
 #define RAV_EXP_Q1(DD, T) k_export_q1<DD, T><<<gb, 128, 0, s>>>(g, (const T*)SL.inv, SL.np, first, count, out)
     if (sm->prec == RAV_F64) {

@@ -234,6 +234,64 @@ def test_smoothing_steps_study_matches_the_oracle(kind, omega, nu):
     assert np.all(np.abs(fac / ofac - 1.0) <= 0.02)
 
 
+@pytest.mark.parametrize("case", CASES, ids=IDS)
+def test_dense_fp64_rows_match(case):
+    """The paper's storage (Sec. 4.3), the owned rows of L_i^{-1} in fp64: the
+    stored rows to 1e-11 and one step to 1e-12 against the oracle."""
+    mg, orc = make_pair(**case)
+    sm = R.Smoother(mg, R.RAV, R.F64_ROWS, OMEGA)
+    orc.setup_smoother(O.RAV, OMEGA)
+    lev = case["nlev"] - 1
+    npatch = mg.counts(lev)["n_p"]
+    got = cpu(sm.inverse_rows(lev, 0, npatch))
+    for p in range(npatch):
+        want = orc.inverse(lev, p)
+        g = got[p, : want.shape[0], : want.shape[1]]
+        assert np.abs(g - want).max() <= 1e-11 * np.abs(want).max(), p
+    rng = np.random.default_rng(19)
+    n = mg.n(lev)
+    x, b = rng.standard_normal(n), rng.standard_normal(n)
+    xg = gpu(x)
+    sm.smooth(lev, xg, gpu(b), 1)
+    assert rel(cpu(xg), orc.smooth(lev, x, b, 1)) <= 1e-12
+
+
+@pytest.mark.parametrize("prec", [R.F32, R.BF16, R.FP8])
+@pytest.mark.parametrize("case", [CASES[1], CASES[2]], ids=[IDS[1], IDS[2]])
+def test_reduced_precision_row_codes_and_step(case, prec):
+    """Reduced-precision rows: the codes equal the oracle's rounding of the same
+    fp64 rows (bit-exact, fp8 with its fp32 row scale), and one step (fp32
+    accumulation) is within the format's error of the fp64 step and close to
+    the oracle's emulation of the same format."""
+    mg, orc = make_pair(**case)
+    lev = case["nlev"] - 1
+    npatch = mg.counts(lev)["n_p"]
+    s64 = R.Smoother(mg, R.RAV, R.F64_ROWS, OMEGA)
+    sq = R.Smoother(mg, R.RAV, prec, OMEGA)
+    rows64 = cpu(s64.inverse_rows(lev, 0, npatch))
+    rowsq = cpu(sq.inverse_rows(lev, 0, npatch))
+    if prec == R.FP8:
+        m = np.abs(rows64).max(axis=2, keepdims=True)
+        sc = np.where(m == 0, 1.0, (m / 448.0).astype(np.float32).astype(np.float64))
+    else:
+        sc = np.ones_like(rows64[..., :1])
+    assert np.array_equal(rowsq, O.round_format(prec, rows64 / sc) * sc)
+    orc.setup_smoother(O.RAV, OMEGA, prec)
+    rng = np.random.default_rng(7)
+    n = mg.n(lev)
+    x, b = rng.standard_normal(n), rng.standard_normal(n)
+    xg = gpu(x)
+    sq.smooth(lev, xg, gpu(b), 1)
+    got = cpu(xg) - x
+    want_q = orc.smooth(lev, x, b, 1) - x
+    x64 = gpu(x)
+    s64.smooth(lev, x64, gpu(b), 1)
+    d64 = cpu(x64) - x
+    fmt_err = np.linalg.norm(want_q - d64) / np.linalg.norm(d64)
+    assert np.linalg.norm(got - want_q) <= 1e-5 * np.linalg.norm(d64) + 0.05 * fmt_err * np.linalg.norm(d64)
+    assert fmt_err <= {R.F32: 1e-6, R.BF16: 2e-2, R.FP8: 2e-1}[prec]
+
+
 @pytest.mark.parametrize("case", CASES[:3], ids=IDS[:3])
 def test_vcycle_matches(case):
     mg, orc = make_pair(**case)
@@ -262,7 +320,8 @@ def test_cavity_convergence_factors_within_two_percent():
     assert rel(cpu(x), ox) <= 1e-6
 
 
-@pytest.mark.parametrize("prec", [R.F64, R.F32_FACT, R.BF16_FACT], ids=["f64", "f32", "bf16"])
+@pytest.mark.parametrize("prec", [R.F64, R.F32_FACT, R.BF16_FACT, R.F64_ROWS, R.F32, R.BF16, R.FP8],
+                         ids=["f64", "f32", "bf16", "f64-rows", "f32-rows", "bf16-rows", "fp8-rows"])
 def test_fgmres_reaches_the_fp64_tolerance(prec):
     """3-D Q1-Q1 with viscosity blobs: FGMRES preconditioned by RAV V-cycles
     reaches 1e-8 in fp64 with every factored storage; the fp64 run matches the
@@ -285,11 +344,10 @@ def test_fgmres_reaches_the_fp64_tolerance(prec):
 
 
 def test_unsupported_combinations_are_rejected():
-    """Q1-Q1 RAV takes the factored storage only, AV/MV fp64 only; the batched
-    path is Q2-Q1 only; the apply has no split."""
+    """Q1-Q1 AV/MV take fp64 only; the batched path is Q2-Q1 only; the apply
+    has no split."""
     mg, _ = make_pair(2, 8, 2)
-    for kind, prec in ((R.AV, R.F32), (R.MV_COLOURED, R.BF16_FACT), (R.RAV, R.F64_ROWS), (R.RAV, R.F32),
-                       (R.RAV, R.BF16), (R.RAV, R.FP8)):
+    for kind, prec in ((R.AV, R.F32), (R.MV_COLOURED, R.BF16_FACT), (R.AV, R.FP8)):
         with pytest.raises(R.RavError):
             R.Smoother(mg, kind, prec, 0.5)
     sm = R.Smoother(mg, R.RAV, R.F64, OMEGA)
