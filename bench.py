@@ -85,8 +85,8 @@ def parse():
     ap.add_argument("--no-single", action="store_true",
                     help="2d-batch: skip timing the single-problem FP64 form on the same problems")
     ap.add_argument("--workload", default="2d512",
-                    choices=sorted(WORKLOADS) + ["2d-batch", "3d-precision", "3d-precision-q1", "3d-learned",
-                                                 "2d-steps", "2d-steps-q1"])
+                    choices=sorted(WORKLOADS) + ["2d-batch", "2d-batch-q1", "3d-precision", "3d-precision-q1",
+                                                 "3d-learned", "2d-steps", "2d-steps-q1"])
     ap.add_argument("--nprob", type=int, default=256, help="problems of the 2d-batch workload")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -438,11 +438,12 @@ def ctypes_f64():
     return ctypes.c_double(0.0)
 
 
-def run_batch(args):
+def run_batch(args, q1=False):
     """256 independent 2-D lid-driven cavities, N = 16 m with m uniform on
     {2..16} (seeded), 8 right-hand sides each (lid values + iid N(0,1) forcing
     on free velocity DoFs), FP32 patch inverses, FP64 residuals; a step is one
-    batched V(2,2) cycle of every problem and right-hand side."""
+    batched V(2,2) cycle of every problem and right-hand side.  q1: the same
+    problems on the stabilised Q1-Q1 element (beta 0.02, RAV omega 0.66)."""
     import numpy as np
     import torch
     import paper_2103_10127_gb300 as R
@@ -454,12 +455,16 @@ def run_batch(args):
     sizes = inputs.batched_sizes(inputs.BASE_SEED, nprob)
     mgs, sms, xs, bs = [], [], [], []
     t0 = time.perf_counter()
+    omega = 0.66 if q1 else 0.5
     for i, N in enumerate(sizes):
         N = int(N)
-        mg = R.Multigrid(2, N, inputs.levels_for(N), bc=R.BC_CAVITY)
-        sm = R.Smoother(mg, R.RAV, R.F32, 0.5)
+        if q1:
+            mg = R.Multigrid(2, N, inputs.levels_for(N), bc=R.BC_CAVITY, element=R.ELEM_Q1Q1, beta=0.02)
+        else:
+            mg = R.Multigrid(2, N, inputs.levels_for(N), bc=R.BC_CAVITY)
+        sm = R.Smoother(mg, R.RAV, R.F32, omega)
         n = mg.n()
-        M = 2 * N + 1
+        M = (1 if q1 else 2) * N + 1
         idx = np.indices((M, M)).reshape(2, -1)[::-1]
         inner = np.repeat(np.all((idx > 0) & (idx < M - 1), axis=0), 2)
         free = np.concatenate([inner, np.zeros((N + 1) ** 2, bool)])
@@ -519,7 +524,7 @@ def run_batch(args):
     single_ms = 0.0
     if not args.no_single:
         for mg in mgs:
-            sm64 = R.Smoother(mg, R.RAV, R.F64, 0.5)
+            sm64 = R.Smoother(mg, R.RAV, R.F64, omega)
             x1, b1 = xs[0].new_zeros(mg.n()), mg.rhs(R.F_NONE)
             mg.vcycle(sm64, x1, b1, 2, 2)
             torch.cuda.synchronize()
@@ -533,8 +538,9 @@ def run_batch(args):
     out = {"metric": "V-cycle DoFs/s", "value": dofs * nrhs * args.steps / (ms / 1e3), "unit": "DoF/s",
            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-           "config": {"workload": f"{nprob} 2D Q2-Q1 lid-driven cavities, N = 16 m, m ~ U{{2..16}} (seed 2103), "
-                                  f"{nrhs} RHS each, RAV V(2,2) omega 0.5, FP32 patch inverses, FP64 residuals",
+           "config": {"workload": f"{nprob} 2D {'stabilised Q1-Q1 (beta 0.02)' if q1 else 'Q2-Q1'} lid-driven "
+                                  f"cavities, N = 16 m, m ~ U{{2..16}} (seed 2103), {nrhs} RHS each, RAV V(2,2) "
+                                  f"omega {omega}, FP32 patch inverses, FP64 residuals",
                       "problems": nprob, "rhs": nrhs, "dofs_total": dofs, "sizes_min_max": [int(sizes.min()),
                                                                                             int(sizes.max())],
                       "tuning": bt.tuning(), "setup_s": setup_s},
@@ -720,8 +726,8 @@ def run_learned(args):
 
 def main():
     args = parse()
-    if args.workload == "2d-batch":
-        run_batch(args)
+    if args.workload in ("2d-batch", "2d-batch-q1"):
+        run_batch(args, q1=args.workload == "2d-batch-q1")
         return
     if args.workload in ("3d-precision", "3d-precision-q1"):
         run_precision(args, q1=args.workload == "3d-precision-q1")

@@ -369,7 +369,7 @@ int rav_reset_omega(rav_smoother* sm, rav_stream stream);
 
 /* ---- Batched solves: many problems x several right-hand sides ------------
  * A batch groups nprob hierarchies (any mix of sizes and depths, one
- * dimension) with their RAV smoothers, which must store dense owned rows
+ * dimension, one element: Q2-Q1 or Q1-Q1) with their RAV smoothers, which must store dense owned rows
  * (RAV_F32 or RAV_F64_ROWS), and advances nrhs (1, 2, 4 or 8) right-hand
  * sides of every problem together.  Vectors of problem p are RHS-interleaved:
  * x_dev[p][row * nrhs + k], n(p) * nrhs doubles, numbering as above.  Each

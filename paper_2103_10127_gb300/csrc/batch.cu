@@ -427,6 +427,209 @@ __global__ void kb_prolong(const BLevel* __restrict__ L, const int64_t* __restri
   }
 }
 
+// ---- stabilised Q1-Q1 (one thread per subdomain / vertex) --------------------
+// RAV apply with the dense owned rows of a Q1-Q1 subdomain (structure of
+// arrays, element (j, k) of subdomain p at (j NC + k) np + p; same order per
+// RHS as k_rav_apply_q1_rows).  use_b: the residual is b (x entered as 0).
+template <int D, typename T, int NR>
+__global__ void kb_apply_q1(const BLevel* __restrict__ L, const int64_t* __restrict__ first, int ne, int use_b) {
+  constexpr int NV = D == 2 ? 9 : 27, NC = D * NV + 1, NROW = D + 1;
+  using Acc = typename std::conditional<std::is_same<T, double>::value, double, float>::type;
+  const int e = find_entry(first, ne, blockIdx.x);
+  const BLevel& lv = L[e];
+  const int64_t p = (blockIdx.x - first[e]) * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t np = lv.units;
+  if (p >= np) return;
+  const Geo& g = lv.g;
+  const Acc* __restrict__ r =
+      std::is_same<T, double>::value ? (const Acc*)(use_b ? lv.b : lv.r) : (const Acc*)lv.r32;
+  const T* __restrict__ st = static_cast<const T*>(lv.inv);
+  int v[3] = {0, 0, 0};
+  vertex_of_t<D>(g, p, v);
+  const int N = g.N;
+  const int64_t N1 = N + 1;
+  Acc acc[NROW][NR];
+#pragma unroll
+  for (int i = 0; i < NROW; ++i)
+#pragma unroll
+    for (int j = 0; j < NR; ++j) acc[i][j] = 0;
+  for (int a2 = 0; a2 < (D == 3 ? 3 : 1); ++a2) {
+    const int J2 = D == 3 ? v[2] - 1 + a2 : 0;
+    const bool ok2 = D == 2 || (J2 >= 1 && J2 <= N - 1);
+    for (int a1 = 0; a1 < 3; ++a1) {
+      const int J1 = v[1] - 1 + a1;
+      const bool ok1 = ok2 && J1 >= 1 && J1 <= N - 1;
+#pragma unroll
+      for (int a0 = 0; a0 < 3; ++a0) {
+        const int n = a0 + 3 * a1 + 9 * a2;
+        const int J0 = v[0] - 1 + a0;
+        const bool ok = ok1 && J0 >= 1 && J0 <= N - 1;
+        const int64_t base = (int64_t)D * (J0 + N1 * (J1 + N1 * J2));
+#pragma unroll
+        for (int c = 0; c < D; ++c) {
+          Acc ra[NR];
+          if (ok) {
+            load_row<Acc, NR>(r + (base + c) * NR, ra);
+          } else {
+#pragma unroll
+            for (int j = 0; j < NR; ++j) ra[j] = 0;
+          }
+#pragma unroll
+          for (int i = 0; i < NROW; ++i) {
+            const Acc q = (Acc)ld_stream(st + ((int64_t)i * NC + n * D + c) * np + p);
+#pragma unroll
+            for (int j = 0; j < NR; ++j) acc[i][j] += q * ra[j];
+          }
+        }
+      }
+    }
+  }
+  {
+    Acc ra[NR];
+    load_row<Acc, NR>(r + (g.n_u + p) * NR, ra);
+#pragma unroll
+    for (int i = 0; i < NROW; ++i) {
+      const Acc q = (Acc)ld_stream(st + ((int64_t)i * NC + NC - 1) * np + p);
+#pragma unroll
+      for (int j = 0; j < NR; ++j) acc[i][j] += q * ra[j];
+    }
+  }
+  const double om = lv.omega[p];
+  bool cfree = true;
+#pragma unroll
+  for (int d = 0; d < D; ++d) cfree &= v[d] >= 1 && v[d] <= N - 1;
+  if (cfree) {
+#pragma unroll
+    for (int c = 0; c < D; ++c)
+#pragma unroll
+      for (int j = 0; j < NR; ++j) lv.x[((int64_t)D * p + c) * NR + j] += om * (double)acc[c][j];
+  }
+#pragma unroll
+  for (int j = 0; j < NR; ++j) lv.x[(g.n_u + p) * NR + j] += om * (double)acc[D][j];
+}
+
+// Q1-Q1 restriction (same order per RHS as k_restrict_q1); zeroes the coarser iterate.
+template <int D, int NR>
+__global__ void kb_restrict_q1(const BLevel* __restrict__ L, const int64_t* __restrict__ first, int ne) {
+  const int e = find_entry(first, ne, blockIdx.x);
+  const BLevel& lv = L[e];
+  const Geo &gf = lv.g, &gc = lv.gc;
+  const XferTab& T = lv.tab;
+  const int t = (int)((blockIdx.x - first[e]) * blockDim.x + threadIdx.x);
+  if (t >= (int)gc.n_p) return;
+  const int Nf1 = gf.N + 1, Nc1 = gc.N + 1;
+  const double* rf = lv.r;
+  int K[3] = {0, 0, 0}, id = t;
+  bool cbnd = false;
+  for (int a = 0; a < D; ++a) {
+    K[a] = id % Nc1;
+    id /= Nc1;
+    cbnd |= (K[a] == 0) | (K[a] == gc.N);
+  }
+  const int c0 = T.rc1[0][K[0]], c1 = T.rc1[1][K[1]], c2 = D == 3 ? T.rc1[2][K[2]] : 1;
+  double acc[D + 1][NR];
+#pragma unroll
+  for (int c = 0; c <= D; ++c)
+#pragma unroll
+    for (int j = 0; j < NR; ++j) acc[c][j] = 0.0;
+  for (int j2 = 0; j2 < c2; ++j2) {
+    const int V2 = D == 3 ? T.rk1[2][3 * K[2] + j2] : 0;
+    const double w2 = D == 3 ? T.rw1[2][3 * K[2] + j2] : 1.0;
+    const bool b2 = D == 3 && (V2 == 0 || V2 == gf.N);
+    for (int j1 = 0; j1 < c1; ++j1) {
+      const int V1 = T.rk1[1][3 * K[1] + j1];
+      const double w12 = D == 3 ? w2 * T.rw1[1][3 * K[1] + j1] : T.rw1[1][3 * K[1] + j1];
+      const bool b1 = b2 || V1 == 0 || V1 == gf.N;
+#pragma unroll
+      for (int j0 = 0; j0 < 3; ++j0)
+        if (j0 < c0) {
+          const int V0 = T.rk1[0][3 * K[0] + j0];
+          const double ww = w12 * T.rw1[0][3 * K[0] + j0];
+          const int64_t V = V0 + Nf1 * (V1 + (int64_t)Nf1 * V2);
+          if (!(b1 || V0 == 0 || V0 == gf.N)) {
+#pragma unroll
+            for (int c = 0; c < D; ++c)
+#pragma unroll
+              for (int j = 0; j < NR; ++j) acc[c][j] += ww * rf[((int64_t)D * V + c) * NR + j];
+          }
+#pragma unroll
+          for (int j = 0; j < NR; ++j) acc[D][j] += ww * rf[(gf.n_u + V) * NR + j];
+        }
+    }
+  }
+#pragma unroll
+  for (int c = 0; c < D; ++c)
+#pragma unroll
+    for (int j = 0; j < NR; ++j) {
+      const double val = cbnd ? 0.0 : acc[c][j];
+      const int64_t o = ((int64_t)D * t + c) * NR + j;
+      lv.bc[o] = val;
+      if (lv.bc32) lv.bc32[o] = (float)val;
+      lv.xc[o] = 0.0;
+    }
+#pragma unroll
+  for (int j = 0; j < NR; ++j) {
+    const int64_t o = (gc.n_u + t) * NR + j;
+    lv.bc[o] = acc[D][j];
+    if (lv.bc32) lv.bc32[o] = (float)acc[D][j];
+    lv.xc[o] = 0.0;
+  }
+}
+
+// Q1-Q1 prolongation x += P xc (same order per RHS as k_prolong_q1).
+template <int D, int NR>
+__global__ void kb_prolong_q1(const BLevel* __restrict__ L, const int64_t* __restrict__ first, int ne) {
+  const int e = find_entry(first, ne, blockIdx.x);
+  const BLevel& lv = L[e];
+  const Geo &gf = lv.g, &gc = lv.gc;
+  const XferTab& T = lv.tab;
+  const int t = (int)((blockIdx.x - first[e]) * blockDim.x + threadIdx.x);
+  if (t >= (int)gf.n_p) return;
+  const int Nf1 = gf.N + 1, Nc1 = gc.N + 1;
+  const double* xc = lv.xc;
+  int v[3] = {0, 0, 0}, id = t;
+  bool bnd = false;
+  for (int a = 0; a < D; ++a) {
+    v[a] = id % Nf1;
+    id /= Nf1;
+    bnd |= (v[a] == 0) | (v[a] == gf.N);
+  }
+  const int c0 = T.pc1[0][v[0]], c1 = T.pc1[1][v[1]], c2 = D == 3 ? T.pc1[2][v[2]] : 1;
+  double acc[D + 1][NR];
+#pragma unroll
+  for (int c = 0; c <= D; ++c)
+#pragma unroll
+    for (int j = 0; j < NR; ++j) acc[c][j] = 0.0;
+  for (int j2 = 0; j2 < c2; ++j2) {
+    const int K2 = D == 3 ? T.pk1[2][2 * v[2] + j2] : 0;
+    const double w2 = D == 3 ? T.pw1[2][2 * v[2] + j2] : 1.0;
+    for (int j1 = 0; j1 < c1; ++j1) {
+      const int K1 = T.pk1[1][2 * v[1] + j1];
+      const double w12 = D == 3 ? w2 * T.pw1[1][2 * v[1] + j1] : T.pw1[1][2 * v[1] + j1];
+#pragma unroll
+      for (int j0 = 0; j0 < 2; ++j0)
+        if (j0 < c0) {
+          const double ww = w12 * T.pw1[0][2 * v[0] + j0];
+          const int K = T.pk1[0][2 * v[0] + j0] + Nc1 * (K1 + Nc1 * K2);
+#pragma unroll
+          for (int c = 0; c < D; ++c)
+#pragma unroll
+            for (int j = 0; j < NR; ++j) acc[c][j] += ww * xc[((int64_t)D * K + c) * NR + j];
+#pragma unroll
+          for (int j = 0; j < NR; ++j) acc[D][j] += ww * xc[(gc.n_u + K) * NR + j];
+        }
+    }
+  }
+  if (!bnd) {
+#pragma unroll
+    for (int c = 0; c < D; ++c)
+#pragma unroll
+      for (int j = 0; j < NR; ++j) lv.x[((int64_t)D * t + c) * NR + j] += acc[c][j];
+  }
+#pragma unroll
+  for (int j = 0; j < NR; ++j) lv.x[(gf.n_u + t) * NR + j] += acc[D][j];
+}
+
 // Coarse solve on the coarsest level of each entry: r <- b masked to free
 // rows, then x = C r (one warp per row, same order per RHS as k_coarse_gemv).
 template <int NR>
@@ -479,6 +682,7 @@ struct BPhase {
 
 struct rav_batch {
   int nprob = 0, nrhs = 0, dim = 2, prec = RAV_F32, depth = 0;
+  int elem = RAV_ELEM_Q2Q1;  // every problem of a batch has the same element
   std::vector<rav_mg*> mgs;
   std::vector<rav_smoother*> sms;
   // host copies of every (problem, level) descriptor, finest level first per problem
@@ -599,9 +803,12 @@ static int upload_phase(rav_batch* bt, BPhase& ph, const std::vector<int>& entri
 static int64_t blk_res(const BLevel& b, int t) { return (b.nslice * 32 + t - 1) / t; }
 static int64_t blk_apply(const BLevel& b, int t) { return (b.units + t - 1) / t; }
 static int64_t blk_restrict(const BLevel& b, int t) {
+  if (b.g.q == 1) return (b.gc.n_p + t - 1) / t;
   return ((b.gc.nnode + b.gc.n_p) * restrict_split(b.gc) + t - 1) / t;
 }
-static int64_t blk_prolong(const BLevel& b, int t) { return (b.g.nnode + b.g.n_p + t - 1) / t; }
+static int64_t blk_prolong(const BLevel& b, int t) {
+  return ((b.g.q == 1 ? 0 : b.g.nnode) + b.g.n_p + t - 1) / t;
+}
 static int64_t blk_mask(const BLevel& b, int t) { return (b.g.n + t - 1) / t; }
 static int64_t blk_gemv(const BLevel& b, int t) { return (b.g.n + t / 32 - 1) / (t / 32); }
 
@@ -613,10 +820,16 @@ static void launch_res(const BPhase& ph, double* part, cudaStream_t s) {
 template <int D, int NR>
 static void launch_apply(const rav_batch* bt, const BPhase& ph, int use_b, cudaStream_t s) {
   if (!ph.ne) return;
-  if (bt->prec == RAV_F32)
+  if (bt->elem == RAV_ELEM_Q1Q1) {
+    if (bt->prec == RAV_F32)
+      kb_apply_q1<D, float, NR><<<(unsigned)ph.blocks, ph.threads, 0, s>>>(ph.L, ph.first, ph.ne, use_b);
+    else
+      kb_apply_q1<D, double, NR><<<(unsigned)ph.blocks, ph.threads, 0, s>>>(ph.L, ph.first, ph.ne, use_b);
+  } else if (bt->prec == RAV_F32) {
     kb_apply<D, float, NR><<<(unsigned)ph.blocks, ph.threads, 0, s>>>(ph.L, ph.first, ph.ne, use_b);
-  else
+  } else {
     kb_apply<D, double, NR><<<(unsigned)ph.blocks, ph.threads, 0, s>>>(ph.L, ph.first, ph.ne, use_b);
+  }
 }
 
 template <int D, int NR>
@@ -646,7 +859,10 @@ static int batch_cycle(rav_batch* bt, int nu1, int nu2, cudaStream_t s) {
     res(d);
     const BPhase& rp = bt->restrict_[d];
     ev = bprof_begin(bt, d, PROF_RESTRICT, s);
-    if (rp.ne) kb_restrict<D, NR><<<(unsigned)rp.blocks, rp.threads, 0, s>>>(rp.L, rp.first, rp.ne);
+    if (rp.ne && bt->elem == RAV_ELEM_Q1Q1)
+      kb_restrict_q1<D, NR><<<(unsigned)rp.blocks, rp.threads, 0, s>>>(rp.L, rp.first, rp.ne);
+    else if (rp.ne)
+      kb_restrict<D, NR><<<(unsigned)rp.blocks, rp.threads, 0, s>>>(rp.L, rp.first, rp.ne);
     bprof_end(bt, ev, s);
     const BPhase& cm = bt->coarse_mask[d + 1];
     if (cm.ne) {
@@ -661,7 +877,10 @@ static int batch_cycle(rav_batch* bt, int nu1, int nu2, cudaStream_t s) {
   for (int d = Dm - 1; d >= 0; --d) {
     const BPhase& pp = bt->prolong[d];
     ev = bprof_begin(bt, d, PROF_PROLONG, s);
-    if (pp.ne) kb_prolong<D, NR><<<(unsigned)pp.blocks, pp.threads, 0, s>>>(pp.L, pp.first, pp.ne);
+    if (pp.ne && bt->elem == RAV_ELEM_Q1Q1)
+      kb_prolong_q1<D, NR><<<(unsigned)pp.blocks, pp.threads, 0, s>>>(pp.L, pp.first, pp.ne);
+    else if (pp.ne)
+      kb_prolong<D, NR><<<(unsigned)pp.blocks, pp.threads, 0, s>>>(pp.L, pp.first, pp.ne);
     bprof_end(bt, ev, s);
     for (int it = 0; it < nu2; ++it) {
       res(d);
@@ -831,7 +1050,7 @@ extern "C" int batch_setup(rav_mg* const* mgs, rav_smoother* const* sms, int npr
   for (int p = 0; p < nprob; ++p) {
     if (!mgs[p] || !sms[p] || sms[p]->mg != mgs[p] || mgs[p]->dim != dim || mgs[p]->nlev < 2) return RAV_ERR_ARG;
     if (sms[p]->kind != RAV_RAV || sms[p]->prec != prec) return RAV_ERR_ARG;
-    if (mgs[p]->elem != RAV_ELEM_Q2Q1) return RAV_ERR_ARG;  // the batched kernels are Q2-Q1 only
+    if (mgs[p]->elem != mgs[0]->elem) return RAV_ERR_ARG;  // one element per batch
   }
   if (prec != RAV_F32 && prec != RAV_F64_ROWS) return RAV_ERR_ARG;
   cudaStream_t s = S(stream);
@@ -840,6 +1059,7 @@ extern "C" int batch_setup(rav_mg* const* mgs, rav_smoother* const* sms, int npr
   bt->nrhs = nrhs;
   bt->dim = dim;
   bt->prec = prec;
+  bt->elem = mgs[0]->elem;
   bt->mgs.assign(mgs, mgs + nprob);
   bt->sms.assign(sms, sms + nprob);
   auto fail = [&](int rc) {

@@ -344,8 +344,8 @@ def test_fgmres_reaches_the_fp64_tolerance(prec):
 
 
 def test_unsupported_combinations_are_rejected():
-    """Q1-Q1 AV/MV take fp64 only; the batched path is Q2-Q1 only; the apply
-    has no split."""
+    """Q1-Q1 AV/MV take fp64 only; a batch holds one element and dense-row
+    storage; the apply has no split."""
     mg, _ = make_pair(2, 8, 2)
     for kind, prec in ((R.AV, R.F32), (R.MV_COLOURED, R.BF16_FACT), (R.AV, R.FP8)):
         with pytest.raises(R.RavError):
@@ -356,7 +356,10 @@ def test_unsupported_combinations_are_rejected():
     with pytest.raises(R.RavError):
         sm.apply_split(1, 2)
     with pytest.raises(R.RavError):
-        R.Batch([mg], [sm], 1)
+        R.Batch([mg], [sm], 1)  # factored storage: the batch takes dense rows
+    mg2 = R.Multigrid(2, 8, 2, bc=R.BC_CAVITY)
+    with pytest.raises(R.RavError):
+        R.Batch([mg, mg2], [R.Smoother(mg, R.RAV, R.F32, OMEGA), R.Smoother(mg2, R.RAV, R.F32, 0.5)], 1)
 
 
 @pytest.mark.parametrize("dim,N,per_patch", [(2, 12, False), (3, 6, True)])
@@ -541,3 +544,86 @@ def test_full_size_64cube_sampled_parity():
         rows = orc.patch_rows(0, int(p))[: len(mine) * len(s)].reshape(len(mine), len(s))
         want = x[mine] + OMEGA * rows @ r[s]
         assert np.abs(got[mine] - want).max() <= 1e-12 * max(np.abs(want).max(), 1.0), p
+
+
+# --------------------------------------------------------------------------- batched
+def _free_velocity_q1(dim, N):
+    idx = np.indices((N + 1,) * dim).reshape(dim, -1)[::-1]  # axis 0 fastest
+    inner = np.all((idx > 0) & (idx < N), axis=0)
+    return np.concatenate([np.repeat(inner, dim), np.zeros((N + 1) ** dim, bool)])
+
+
+def _q1_batch(specs, nrhs, prec, seed):
+    """specs: (dim, N, levels, blobs); lid values plus iid N(0,1) forcing on
+    the free velocity rows per right-hand side."""
+    mgs, sms, xs, bs = [], [], [], []
+    for i, (dim, N, nlev, blobs) in enumerate(specs):
+        mg = R.Multigrid(dim, N, nlev, blobs=blobs, bc=R.BC_CAVITY, element=R.ELEM_Q1Q1, beta=BETA)
+        sm = R.Smoother(mg, R.RAV, prec, OMEGA)
+        m = _free_velocity_q1(dim, N)
+        b0 = mg.rhs(R.F_NONE).cpu().numpy()
+        cols = []
+        for k in range(nrhs):
+            bk = b0.copy()
+            bk[m] += inputs.normal(1000 * seed + 10 * i + k, int(m.sum()))
+            cols.append(bk)
+        x0 = mg.initial_guess().cpu().numpy()
+        mgs.append(mg)
+        sms.append(sm)
+        xs.append(torch.from_numpy(np.ascontiguousarray(np.repeat(x0[:, None], nrhs, axis=1))).cuda())
+        bs.append(torch.from_numpy(np.ascontiguousarray(np.stack(cols, axis=1))).cuda())
+    return mgs, sms, xs, bs
+
+
+@pytest.mark.parametrize("prec", [R.F32, R.F64_ROWS], ids=["f32-rows", "f64-rows"])
+@pytest.mark.parametrize("dim", [2, 3])
+def test_batched_q1_cycles_equal_single_problem_cycles_bitwise(dim, prec):
+    """Uneven Q1-Q1 problems (2-D 16^2..32^2 of 3-4 levels; 3-D 8^3 and 16^3 with
+    blobs) advanced together: two batched V(2,2) cycles equal, bit for bit, two
+    single-problem cycles of every right-hand side."""
+    if dim == 2:
+        specs = [(2, N, inputs.levels_for(N), None) for N in (16, 24, 32, 20)]
+        nrhs = 4
+    else:
+        specs = [(3, 8, 2, inputs.viscosity_blobs(40, k=4, s_max=2.0)),
+                 (3, 16, 3, inputs.viscosity_blobs(41, k=4, s_max=2.0))]
+        nrhs = 2
+    mgs, sms, xs, bs = _q1_batch(specs, nrhs, prec, seed=dim)
+    bt = R.Batch(mgs, sms, nrhs)
+    x_in = [x.clone() for x in xs]
+    bt.vcycle(xs, bs, 2, 2)
+    bt.vcycle(xs, bs, 2, 2)
+    for p, (mg, sm) in enumerate(zip(mgs, sms)):
+        for lev in range(mg.nlev):  # the batched residual sums a row in one thread, as split 1 does
+            mg.residual_split(lev, 1)
+        for k in range(nrhs):
+            x = x_in[p][:, k].contiguous()
+            b = bs[p][:, k].contiguous()
+            mg.vcycle(sm, x, b, 2, 2)
+            mg.vcycle(sm, x, b, 2, 2)
+            assert torch.equal(x, xs[p][:, k]), (p, k)
+
+
+def test_batched_q1_cycle_matches_the_oracle_and_solves():
+    """One batched Q1-Q1 V-cycle (fp64 rows) against the oracle's, and a batched
+    solve (fp32 rows) reaching 1e-8 in the cycles of the single solves."""
+    specs = [(2, 16, 3, None), (2, 24, 2, None)]
+    mgs, sms, xs, bs = _q1_batch(specs, 2, R.F64_ROWS, seed=3)
+    bt = R.Batch(mgs, sms, 2)
+    x_in = [x.cpu().numpy() for x in xs]
+    bt.vcycle(xs, bs, 2, 2)
+    for p, (_, N, nlev, _) in enumerate(specs):
+        orc = O.Oracle(2, N, nlev, bc=O.BC_CAVITY, element=O.ELEM_Q1Q1, beta=BETA)
+        orc.setup_smoother(O.RAV, OMEGA)
+        for k in range(2):
+            want = orc.vcycle(x_in[p][:, k], bs[p][:, k].cpu().numpy(), 2, 2)
+            assert rel(xs[p][:, k].cpu().numpy(), want) <= 1e-11
+    mgs, sms, xs, bs = _q1_batch(specs + [(2, 32, 4, None)], 2, R.F32, seed=5)
+    bt = R.Batch(mgs, sms, 2)
+    x_in = [x.clone() for x in xs]
+    it, ratios, rc = bt.solve(xs, bs, tol=1e-8, maxit=100)
+    assert rc == 0 and np.all(it > 0) and np.all(ratios <= 1e-8)
+    for p, (mg, sm) in enumerate(zip(mgs, sms)):
+        for k in range(2):
+            its, _, rcs = mg.solve(sm, x_in[p][:, k].contiguous(), bs[p][:, k].contiguous(), tol=1e-8, maxit=100)
+            assert rcs == 0 and its == it[p, k]
