@@ -91,6 +91,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-tol", action="store_true")
+    ap.add_argument("--fused", action="store_true",
+                    help="Q1-Q1 RAV fp64 workloads: one fused residual + subdomain-apply kernel per smoothing step")
     ap.add_argument("--N", type=int, default=None, help="override the grid size (profiling runs)")
     ap.add_argument("--levels", type=int, default=None)
     return ap.parse_args()
@@ -283,6 +285,8 @@ def run_ours(args, W):
     mg = R.Multigrid(W["dim"], W["N"], W["nlev"], bc=W["bc"], blobs=make_blobs(W), element=W.get("elem", 0),
                      beta=W.get("beta", 0.0))
     sm = R.Smoother(mg, W["kind"], W["prec"], W["omega"])
+    if args.fused:
+        sm.fused(True)
     fine = W["nlev"] - 1
     n = mg.n()
     b = mg.rhs(W["forcing"])
@@ -355,6 +359,8 @@ def run_ours(args, W):
     # ---- roofline of the dominant kernel: fine-level subdomain apply ----
     q1 = W.get("elem", 0) == 1
     flops, bytes_alg, stored = patch_work(W["dim"], W["N"], W["prec"], n, q=1 if q1 else 2)
+    if args.fused:  # the fused kernel also forms the residual: one FMA per assembled entry
+        flops += 2.0 * mg.counts(fine)["nnz"]
     if W["prec"] in (0, 4):  # fp64 arithmetic: bound by the FP64 pipes, not HBM
         roof = {"bound": "alu", "achieved": flops / (apply_ms / 1e3) / 1e12, "peak": FP64_PEAK_TFLOPS,
                 "unit": "TFLOP/s"}
@@ -365,8 +371,10 @@ def run_ours(args, W):
     roof["frac"] = roof["achieved"] / roof["peak"]
     traffic = measured_traffic(f"rav_apply_{args.workload}")
     roof["traffic"] = traffic
-    roof["kernel"] = ("k_rav_apply_q1" if q1 else "k_rav_apply_fact" if W["prec"] in (0, 5, 6)
-                      else "k_rav_apply") + " (fine level)"
+    roof["kernel"] = ("k_fused_q1" if args.fused else "k_rav_apply_q1" if q1 else
+                      "k_rav_apply_fact" if W["prec"] in (0, 5, 6) else "k_rav_apply") + " (fine level)"
+    if args.fused:
+        roof["traffic"] = None
     roof["launch_ms"] = apply_ms
     roof["launches_timed"] = apply_launches
     roof["algorithmic_bytes"] = bytes_alg
@@ -377,7 +385,7 @@ def run_ours(args, W):
            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
            "config": {"workload": W["desc"], "dofs": n, "levels": W["nlev"], "nu": [nu, nu],
-                      "smoother": "RAV",
+                      "smoother": "RAV" + (", fused residual + apply per step" if args.fused else ""),
                       "inverse_storage": STORAGE[W["prec"]],
                       "l2": "inputs larger than L2: each fine-level pass streams the operator "
                             f"({mg.counts(fine)['nnz'] * 12 / 1e9:.2f} GB) and the stored patch inverses "

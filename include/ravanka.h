@@ -243,6 +243,17 @@ void vanka_destroy(rav_smoother* sm);
 int rav_set_apply_split(rav_smoother* sm, int level, int split, rav_stream stream);
 int rav_get_apply_split(const rav_smoother* sm, int level);
 
+/* Fused smoothing (Q1-Q1, RAV, RAV_F64 only; RAV_ERR_ARG otherwise): with
+ * enable != 0 every smoothing step of this smoother runs as one kernel that
+ * computes the residual of Eq. 10 on each tile's subdomain boxes (tiles of
+ * 16 x 16 or 8 x 8 x 4 vertices plus a one-vertex halo, kept in shared
+ * memory) and applies the subdomain corrections of Eq. 13, reading one
+ * iterate buffer and writing another (the library allocates the second one per
+ * level); 0 returns to the residual + apply kernels.  Results agree with the
+ * two-kernel path to rounding (the fused residual sums the assembled rows).
+ * Synchronises the device and drops this smoother's captured cycles. */
+int rav_set_fused_smoothing(rav_smoother* sm, int enable);
+
 /* Replaces the damping of level l's subdomains by w_dev[n_p(l)] (fp32, device),
  * e.g. the per-subdomain weights of a learned model. */
 int rav_set_patch_omega(rav_smoother* sm, int level, const float* w_dev, rav_stream stream);

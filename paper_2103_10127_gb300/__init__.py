@@ -249,6 +249,10 @@ class Smoother:
             raise RavError(k, "rav_get_apply_split")
         return k
 
+    def fused(self, enable=True):
+        """Q1-Q1 RAV fp64: run each smoothing step as one fused residual + apply kernel."""
+        check(_capi.load().rav_set_fused_smoothing(self.h, int(bool(enable))), "rav_set_fused_smoothing")
+
     def set_omega(self, level, w, stream=None):
         w = w.to(dtype=_torch().float32).contiguous()
         check(_capi.load().rav_set_patch_omega(self.h, level, _ptr(w), _stream(stream)), "rav_set_patch_omega")

@@ -52,6 +52,7 @@ _SIGS = {
     "rav_set_patch_omega": (I32, [P, I32, P, P]),
     "rav_set_apply_split": (I32, [P, I32, I32, P]),
     "rav_get_apply_split": (I32, [P, I32]),
+    "rav_set_fused_smoothing": (I32, [P, I32]),
     "rav_get_patch_counts": (I32, [P, I32, I64P]),
     "rav_get_patches": (I32, [P, I32, P, P, P, P]),
     "rav_get_inverse_rows": (I32, [P, I32, ctypes.c_int64, ctypes.c_int64, P, P]),

@@ -78,6 +78,7 @@ struct Level {
   int64_t nslice = 0;
   int rsplit = 1;  // threads per row of the residual kernel (more on small levels: shorter latency chains)
   int32_t* sperm = nullptr;  // row of slot t = 32 s + lane, -1 for padding
+  int32_t* sslot = nullptr;  // slot of row i (the inverse of sperm; Q1-Q1 hierarchies only, for fused smoothing)
   int64_t* sptr = nullptr;   // offset of slice s in sval/scol
   int32_t* slen = nullptr;   // row length of slice s (1 = Dirichlet identity rows)
   int32_t* scol = nullptr;
@@ -161,6 +162,7 @@ struct SmLevel {
   double* ctmp = nullptr;    // subdomain corrections with unit damping
   double* stmp = nullptr;    // the whole step with the current damping
   double* rtmp = nullptr;    // residual after that step
+  double* xalt = nullptr;    // fused smoothing: the second iterate buffer (n entries)
 };
 
 struct rav_smoother {
@@ -168,6 +170,7 @@ struct rav_smoother {
   int kind = RAV_RAV, prec = RAV_F64;
   double omega = 0.5;
   bool collect = false;  // accumulate line-search labels in each smoothing step
+  bool fused = false;    // Q1-Q1 RAV fp64: residual and subdomain apply in one kernel per step
   SmLevel lev[rav::kMaxLevels];
 };
 
@@ -318,6 +321,9 @@ int dot_impl(rav_mg* mg, const double* a, const double* b, int64_t n, double* ou
 enum { ENTRY_GENERAL = 0, ENTRY_X_ZERO = 1, ENTRY_R_READY = 2 };
 int rav_smooth_impl(rav_smoother* sm, int level, double* x, const double* b, int steps, cudaStream_t s,
                     int entry = ENTRY_GENERAL);
+// The fused form of `steps` RAV steps (fused.cu): one kernel per step computes
+// the residual on each tile's subdomain boxes and applies the subdomains.
+int fused_smooth_impl(rav_smoother* sm, int level, double* x, const double* b, int steps, cudaStream_t s);
 namespace rav {
 int vcycle_impl(rav_mg* mg, rav_smoother* sm, double* x, const double* b, int nu1, int nu2, int entry,
                 cudaStream_t s);

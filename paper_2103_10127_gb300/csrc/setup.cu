@@ -976,6 +976,13 @@ static int build_sell(Level& L, cudaStream_t s) {
   RAV_CUDA(cudaMemcpy(L.sperm, perm.data(), sizeof(int32_t) * perm.size(), cudaMemcpyHostToDevice));
   RAV_CUDA(cudaMemcpy(L.sptr, sptr.data(), sizeof(int64_t) * sptr.size(), cudaMemcpyHostToDevice));
   RAV_CUDA(cudaMemcpy(L.slen, slen.data(), sizeof(int32_t) * slen.size(), cudaMemcpyHostToDevice));
+  if (L.g.q == 1) {  // row -> slot, for the fused smoothing step's residual
+    std::vector<int32_t> slot(n, -1);
+    for (size_t t = 0; t < perm.size(); ++t)
+      if (perm[t] >= 0) slot[perm[t]] = (int32_t)t;
+    RAV_CUDA(cudaMalloc(&L.sslot, sizeof(int32_t) * n));
+    RAV_CUDA(cudaMemcpy(L.sslot, slot.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice));
+  }
   k_sell_fill<<<(int)((L.nslice * 32 + 255) / 256), 256, 0, s>>>(L.nslice, L.sperm, L.sptr, L.slen, L.rp, L.ci,
                                                                   L.va, L.scol, L.sval);
   RAV_CUDA(cudaGetLastError());
@@ -1273,6 +1280,7 @@ extern "C" void mg_destroy(rav_mg* mg) {
     cudaFree(L.ci);
     cudaFree(L.va);
     cudaFree(L.sperm);
+    cudaFree(L.sslot);
     cudaFree(L.sptr);
     cudaFree(L.slen);
     cudaFree(L.scol);

@@ -1848,6 +1848,7 @@ extern "C" void vanka_destroy(rav_smoother* sm) {
     cudaFree(sm->lev[l].ctmp);
     cudaFree(sm->lev[l].stmp);
     cudaFree(sm->lev[l].rtmp);
+    cudaFree(sm->lev[l].xalt);
   }
   delete sm;
 }
@@ -2094,6 +2095,7 @@ int rav_smooth_impl(rav_smoother* sm, int level, double* x, const double* b, int
   SmLevel& SL = sm->lev[level];
   const Geo& g = L.g;
   const int D = g.dim;
+  if (sm->fused && !sm->collect) return fused_smooth_impl(sm, level, x, b, steps, s);
   for (int it = 0; it < steps; ++it) {
     if (sm->kind == RAV_MV_COLOURED) {
       const int ncol = D == 2 ? 16 : 64;

@@ -627,3 +627,54 @@ def test_batched_q1_cycle_matches_the_oracle_and_solves():
         for k in range(2):
             its, _, rcs = mg.solve(sm, x_in[p][:, k].contiguous(), bs[p][:, k].contiguous(), tol=1e-8, maxit=100)
             assert rcs == 0 and its == it[p, k]
+
+
+# --------------------------------------------------------------------------- fused smoothing
+@pytest.mark.parametrize("case", CASES, ids=IDS)
+def test_fused_smoothing_matches_two_kernel_steps_and_the_oracle(case):
+    """The fused residual + apply step (one kernel per step, tile halos) gives
+    the two-kernel steps to rounding and the oracle's steps to 1e-12, for an
+    odd and an even number of steps; a V-cycle with it matches the oracle's."""
+    mg, orc = make_pair(**case)
+    sm = R.Smoother(mg, R.RAV, R.F64, OMEGA)
+    orc.setup_smoother(O.RAV, OMEGA)
+    rng = np.random.default_rng(37)
+    lev = case["nlev"] - 1
+    n = mg.n(lev)
+    x, b = rng.standard_normal(n), rng.standard_normal(n)
+    ref = {}
+    for steps in (1, 2, 3):
+        xg = gpu(x)
+        sm.smooth(lev, xg, gpu(b), steps)
+        ref[steps] = cpu(xg)
+    sm.fused(True)
+    for steps in (1, 2, 3):
+        xg = gpu(x)
+        sm.smooth(lev, xg, gpu(b), steps)
+        got = cpu(xg)
+        assert rel(got, ref[steps]) <= 1e-13, steps
+        assert rel(got, orc.smooth(lev, x, b, steps)) <= 1e-12, steps
+    if case["nlev"] > 2:
+        xn = rng.standard_normal(mg.n())
+        bn = rng.standard_normal(mg.n())
+        xg = gpu(xn)
+        mg.vcycle(sm, xg, gpu(bn), 2, 2)
+        assert rel(cpu(xg), orc.vcycle(xn, bn, 2, 2)) <= 1e-11
+    sm.fused(False)
+
+
+def test_fused_smoothing_solves_like_the_two_kernel_path():
+    mg, orc = make_pair(2, 32, 4)
+    sm = R.Smoother(mg, R.RAV, R.F64, OMEGA)
+    b = mg.rhs(R.F_NONE)
+    it0, h0, rc0 = mg.solve(sm, mg.initial_guess(), b, tol=1e-8, maxit=100)
+    sm.fused(True)
+    it1, h1, rc1 = mg.solve(sm, mg.initial_guess(), b, tol=1e-8, maxit=100)
+    assert rc0 == rc1 == 0 and it0 == it1
+    assert np.all(np.abs(h1[1:] / h0[1:] - 1.0) <= 1e-6)
+    for kind, prec in ((R.RAV, R.F32_FACT), (R.RAV, R.F64_ROWS), (R.AV, R.F64)):
+        with pytest.raises(R.RavError):
+            R.Smoother(mg, kind, prec, 0.5).fused(True)
+    q2 = R.Multigrid(2, 8, 2, bc=R.BC_CAVITY)
+    with pytest.raises(R.RavError):
+        R.Smoother(q2, R.RAV, R.F64, 0.5).fused(True)
