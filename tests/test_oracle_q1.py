@@ -306,3 +306,82 @@ def test_rav_multigrid_converges_on_the_cavity():
         du = np.abs(y[:nu] - ref[:nu]).max()
         dp = np.abs((y[nu:] - y[nu:].mean()) - (ref[nu:] - ref[nu:].mean())).max()
         assert du < 1e-6 and dp < 1e-5
+
+
+@pytest.mark.parametrize("dim,N", [(2, 4), (3, 3)])
+def test_av_step_equals_assembled_operator(dim, N):
+    """x + S_AV (b - L x), S_AV = sum_i R_i^T w L_i^{-1} R_i (Eq. 12), on the
+    stabilised Q1-Q1 subdomains."""
+    blobs = inputs.viscosity_blobs(17, k=3, s_max=1.0)
+    o = q1_oracle(dim, N, nlev=2, blobs=blobs)
+    o.setup_smoother(O.AV, 0.1)
+    off, dofs, own = o.patches(1)
+    L = dense(o, 1)
+    m, _ = o.dirichlet(1)
+    S = rav_matrix(L, off, dofs, own, 0.1, restricted=False)
+    rng = np.random.default_rng(2)
+    x, b = rng.standard_normal(L.shape[0]), rng.standard_normal(L.shape[0])
+    want = x + S @ free_residual(L, x, b, m)
+    got = o.smooth(1, x, b)
+    assert np.abs(got - want).max() <= 1e-12 * np.abs(want).max()
+
+
+@pytest.mark.parametrize("kind", [O.MV, O.MV_COLOURED])
+def test_mv_step_is_the_product_of_subdomain_corrections(kind):
+    """Multiplicative Vanka on Q1-Q1: the error propagates as
+    prod_i (I - w R_i^T L_i^{-1} R_i L) in the sweep order (lexicographic, or
+    coloured by (v mod 4) with colours ascending)."""
+    dim, N = 2, 4
+    o = q1_oracle(dim, N, nlev=2, blobs=inputs.viscosity_blobs(18, k=3, s_max=1.0))
+    o.setup_smoother(kind, 0.66)
+    off, dofs, own = o.patches(1)
+    L = dense(o, 1)
+    m, _ = o.dirichlet(1)
+    n = L.shape[0]
+    order = np.arange(len(off) - 1)
+    if kind == O.MV_COLOURED:
+        v = vertex_index(dim, N)
+        order = np.argsort((v[:, 0] % 4) + 4 * (v[:, 1] % 4), kind="stable")
+    E = np.eye(n)
+    for p in order:
+        s = dofs[off[p]:off[p + 1]]
+        Pi = np.zeros((n, n))
+        Pi[np.ix_(s, np.arange(n))] = np.linalg.solve(L[np.ix_(s, s)], L[s, :])
+        E = (np.eye(n) - 0.66 * Pi) @ E
+    rng = np.random.default_rng(3)
+    xs = rng.standard_normal(n)
+    b = L @ xs
+    b[m] = xs[m]
+    e0 = rng.standard_normal(n)
+    e0[m] = 0.0
+    got = o.smooth(1, xs + e0, b) - xs
+    assert np.abs(got - E @ e0).max() <= 1e-11 * np.abs(e0).max()
+
+
+def test_single_global_subdomain_solves_exactly():
+    """One subdomain holding every free DoF but one pressure (which fixes the
+    constant-pressure kernel of the all-Dirichlet problem), owning all of them,
+    with unit damping: one RAV step solves L x = b on those DoFs exactly."""
+    N = 4
+    o = q1_oracle(2, N, nlev=2)
+    o.setup_smoother(O.RAV, 1.0)
+    L = dense(o, 1)
+    m, g = o.dirichlet(1)
+    n = L.shape[0]
+    nu = o.sizes(1)["n_u"]
+    free = np.nonzero(~m)[0]
+    keep = free[free != nu]  # pin p_0
+    off = np.array([0, len(keep)], np.int64)
+    owner = np.full(n, -1, np.int64)
+    owner[keep] = 0
+    o.set_patches(1, off, keep.astype(np.int64), owner, 1.0)
+    rng = np.random.default_rng(9)
+    xs = rng.standard_normal(n)
+    xs[m] = g[m]
+    xs[nu] = 0.0
+    b = L @ xs
+    b[m] = g[m]
+    x0 = np.zeros(n)
+    x0[m] = g[m]
+    got = o.smooth(1, x0, b)
+    assert np.abs(got - xs).max() <= 1e-10 * np.abs(xs).max()
