@@ -363,7 +363,7 @@ def test_factored_reduced_storage_matches_the_oracle(case, prec):
 @pytest.mark.parametrize("prec", [R.F32, R.BF16, R.F32_FACT, R.BF16_FACT],
                          ids=["f32", "bf16", "f32-factored", "bf16-factored"])
 def test_reduced_precision_fgmres_reaches_fp64_tolerance(prec):
-    """The fp64 outer loop absorbs the error of the stored inverses (spec form 1)."""
+    """The fp64 outer loop absorbs the error of the stored inverses (reduced-precision inverses inside FP64 FGMRES)."""
     mg, _ = make_pair(3, 8, 2, nblobs=10, s_max=3.0, bc=O.BC_NOSLIP)
     sm = R.Smoother(mg, R.RAV, prec, 0.5)
     x = mg.initial_guess()
