@@ -125,3 +125,43 @@ def test_batched_3d_cycles_equal_single_problem_cycles_bitwise(prec):
             x = x_in[p][:, k].contiguous()
             mg.vcycle(sm, x, bs[p][:, k].contiguous(), 2, 2)
             assert torch.equal(x, xs[p][:, k]), (p, k)
+
+
+@pytest.mark.slow
+def test_full_size_batch_sampled_bitwise():
+    """The batched benchmark's configuration: 256 cavities of N = 16 m,
+    m ~ U{2..16} (seed 2103), 8 right-hand sides each, FP32 inverses.  One
+    batched V(2,2) cycle; the smallest, the largest and two seeded problems are
+    checked right-hand side by right-hand side, bit for bit, against
+    single-problem cycles."""
+    sizes = inputs.batched_sizes(inputs.BASE_SEED, 256)
+    nrhs = 8
+    mgs, sms, xs, bs = [], [], [], []
+    for i, N in enumerate(sizes):
+        N = int(N)
+        mg = R.Multigrid(2, N, inputs.levels_for(N), bc=R.BC_CAVITY)
+        sm = R.Smoother(mg, R.RAV, R.F32, 0.5)
+        m = free_velocity(2, N)
+        b0 = mg.rhs(R.F_NONE).cpu().numpy()
+        b = np.repeat(b0[:, None], nrhs, axis=1)
+        b[m, :] += inputs.normal(inputs.BASE_SEED + 7919 * (i + 1), int(m.sum()) * nrhs).reshape(-1, nrhs)
+        x0 = mg.initial_guess().cpu().numpy()
+        mgs.append(mg)
+        sms.append(sm)
+        xs.append(torch.from_numpy(np.ascontiguousarray(np.repeat(x0[:, None], nrhs, axis=1))).cuda())
+        bs.append(torch.from_numpy(np.ascontiguousarray(b)).cuda())
+    bt = R.Batch(mgs, sms, nrhs)
+    x_in = {}
+    picks = sorted({int(np.argmin(sizes)), int(np.argmax(sizes))} |
+                   set((inputs.uniform(77, 2) * len(sizes)).astype(int).tolist()))
+    for p in picks:
+        x_in[p] = xs[p].clone()
+    bt.vcycle(xs, bs, 2, 2)
+    for p in picks:
+        mg, sm = mgs[p], sms[p]
+        for lev in range(mg.nlev):
+            mg.residual_split(lev, 1)
+        for k in range(nrhs):
+            x = x_in[p][:, k].contiguous()
+            mg.vcycle(sm, x, bs[p][:, k].contiguous(), 2, 2)
+            assert torch.equal(x, xs[p][:, k]), (p, k)

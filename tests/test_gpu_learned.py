@@ -170,3 +170,47 @@ def test_fallback_restores_fixed_damping():
     info = {}
     it, hist, rc = mg.solve(sm, mg.initial_guess(), b, tol=1e-8, maxit=200, fallback_rho=1.0, info_out=info)
     assert rc == 0 and info["fell_back"]
+
+
+@pytest.mark.slow
+def test_full_size_40cube_features_follow_their_definition():
+    """The learned-damping benchmark's configuration (3-D 40^3, 4 levels, 20
+    blobs of contrast up to 1e4, z-graded cells of aspect 8, seed 2103): the
+    features of sampled fine-level subdomains equal their definition computed
+    with numpy (viscosity at the 3^3 Gauss points of the cells around the
+    vertex, cell aspects and diagonals, level, size and Dirichlet shares)."""
+    N, nlev = 40, 4
+    coords = inputs.graded_coordinates(N, 8.0, 3)
+    blobs = inputs.viscosity_blobs(inputs.BASE_SEED, k=20, s_max=4.0)
+    mg = R.Multigrid(3, N, nlev, coords=coords, blobs=blobs, bc=R.BC_NOSLIP)
+    sm = R.Smoother(mg, R.RAV, R.F64, 0.5)
+    f = learned.features(sm, nlev - 1).cpu().numpy()
+    orc = O.Oracle(3, 4, 1, blobs=blobs)  # viscosity only
+    xg, _ = np.polynomial.legendre.leggauss(3)
+    xg = 0.5 * (xg + 1)
+    N1 = N + 1
+    samples = [0, N, N1 * N1 - 1, N1 ** 3 - 1] + (inputs.uniform(78, 12) * N1 ** 3).astype(int).tolist()
+    for p in samples:
+        v = (p % N1, (p // N1) % N1, p // (N1 * N1))
+        cells = [(i, j, k) for i in (v[0] - 1, v[0]) for j in (v[1] - 1, v[1]) for k in (v[2] - 1, v[2])
+                 if 0 <= i < N and 0 <= j < N and 0 <= k < N]
+        etas, asp, diag = [], [], []
+        for i, j, k in cells:
+            h = [coords[0][i + 1] - coords[0][i], coords[1][j + 1] - coords[1][j], coords[2][k + 1] - coords[2][k]]
+            asp.append(max(h) / min(h))
+            diag.append(np.sqrt(sum(t * t for t in h)))
+            for a in xg:
+                for bq in xg:
+                    for cq in xg:
+                        etas.append(orc.viscosity(np.array([coords[0][i] + h[0] * a, coords[1][j] + h[1] * bq,
+                                                            coords[2][k] + h[2] * cq])))
+        etas = np.array(etas)
+        box = [(2 * v[0] - 2 + a, 2 * v[1] - 2 + b2, 2 * v[2] - 2 + c) for a in range(5) for b2 in range(5)
+               for c in range(5)]
+        inside = [t for t in box if all(0 <= q <= 2 * N for q in t)]
+        bnd = [t for t in inside if any(q in (0, 2 * N) for q in t)]
+        nvalid = len(inside) - len(bnd)
+        want = [np.log10(etas.max() / etas.min()), np.log10(etas).mean(), np.log10(max(asp)), np.log10(min(asp)),
+                1.0, (3 * nvalid + 1) / (3 * 125 + 1), len(bnd) / len(inside), np.log10(np.mean(diag))]
+        for q in range(8):
+            assert abs(f[p, q] - want[q]) <= 1e-5 * max(1.0, abs(want[q])), (p, q, f[p, q], want[q])
