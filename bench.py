@@ -86,7 +86,7 @@ def parse():
                     help="2d-batch: skip timing the single-problem FP64 form on the same problems")
     ap.add_argument("--workload", default="2d512",
                     choices=sorted(WORKLOADS) + ["2d-batch", "2d-batch-q1", "3d-precision", "3d-precision-q1",
-                                                 "3d-learned", "2d-steps", "2d-steps-q1"])
+                                                 "3d-learned", "3d-learned-q1", "2d-steps", "2d-steps-q1"])
     ap.add_argument("--nprob", type=int, default=256, help="problems of the 2d-batch workload")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -670,22 +670,32 @@ def run_steps(args, q1=False):
     print(json.dumps(out), flush=True)
 
 
-def run_learned(args):
+def run_learned(args, q1=False):
     """Learned damping on 3-D 40^3 (or --N), 4 levels, 20 blobs with contrast
     up to 1e4 and z-graded cells of aspect 8 (seed 2103): the MLP is trained on
     line-search labels from eight 2-D/3-D runs with other seeds, then FGMRES(30)
     and stationary solves to 1e-8 with fixed damping 0.5 and with the learned
-    per-level damping."""
+    per-level damping.  q1: the same on the stabilised Q1-Q1 element (beta
+    0.02, fixed damping 0.66) with contrasts capped at 1e2 (beta does not
+    scale with the viscosity) and cell aspects at 2 (at aspect 4 the fixed
+    smoother already needs tens of FGMRES iterations on small grids)."""
     import torch
     import paper_2103_10127_gb300 as R
     from paper_2103_10127_gb300 import inputs, learned
 
     torch.cuda.set_device(0)
+    omega = 0.66 if q1 else 0.5
 
     def spec(dim, N, nlev, seed, s_max, asp):
-        return dict(dim=dim, N=N, n_levels=nlev, bc=R.BC_NOSLIP,
-                    coords=inputs.graded_coordinates(N, asp, dim) if asp > 1 else None,
-                    blobs=inputs.viscosity_blobs(seed, k=12 if seed != inputs.BASE_SEED else 20, s_max=s_max))
+        if q1:
+            asp = min(asp, 2.0)
+        d = dict(dim=dim, N=N, n_levels=nlev, bc=R.BC_NOSLIP,
+                 coords=inputs.graded_coordinates(N, asp, dim) if asp > 1 else None,
+                 blobs=inputs.viscosity_blobs(seed, k=12 if seed != inputs.BASE_SEED else 20,
+                                              s_max=min(s_max, 2.0) if q1 else s_max))
+        if q1:
+            d.update(element=R.ELEM_Q1Q1, beta=0.02)
+        return d
 
     train_set = [(101, 2, 32, 3, 4.0, 8.0), (102, 2, 48, 3, 2.0, 1.0), (103, 3, 8, 2, 4.0, 8.0),
                  (104, 3, 12, 2, 2.0, 1.0), (105, 3, 16, 2, 3.0, 4.0), (106, 2, 64, 4, 3.0, 4.0),
@@ -694,7 +704,7 @@ def run_learned(args):
     Xs, ys = [], []
     for seed, dim, N, nlev, s_max, asp in train_set:
         mg = R.Multigrid(**spec(dim, N, nlev, seed, s_max, asp))
-        sm = R.Smoother(mg, R.RAV, R.F64, 0.5)
+        sm = R.Smoother(mg, R.RAV, R.F64, omega)
         X, y = learned.collect(mg, sm, mg.initial_guess(), mg.rhs(R.F_SINKER), cycles=3)
         Xs.append(X)
         ys.append(y)
@@ -706,9 +716,11 @@ def run_learned(args):
     N = args.N or 40
     nlev = args.levels or 4
     results = {}
-    for label, (s_max, asp) in (("contrast1e4-aspect8", (4.0, 8.0)), ("contrast1e3-aspect1", (3.0, 1.0))):
+    cases = ((("contrast1e2-aspect2", (2.0, 2.0)), ("contrast1e2-aspect1", (2.0, 1.0))) if q1 else
+             (("contrast1e4-aspect8", (4.0, 8.0)), ("contrast1e3-aspect1", (3.0, 1.0))))
+    for label, (s_max, asp) in cases:
         mg = R.Multigrid(**spec(3, N, nlev, inputs.BASE_SEED, s_max, asp))
-        sm = R.Smoother(mg, R.RAV, R.F64, 0.5)
+        sm = R.Smoother(mg, R.RAV, R.F64, omega)
         b = mg.rhs(R.F_SINKER)
         row = {}
         for mode in ("fixed", "learned"):
@@ -725,7 +737,8 @@ def run_learned(args):
                 row[f"{mode}-{oname}"] = {"iterations": it, "status": rc, "seconds": time.perf_counter() - t1}
         results[label] = row
     out = {"metric": "iterations / time to 1e-8, learned vs fixed damping", "n_gpus": 1, "data": "synthetic",
-           "config": {"workload": f"3D Stokes Q2-Q1 {N}^3, {nlev} levels, 20 blobs, sinker", "train_problems": 8,
+           "config": {"workload": f"3D Stokes {'stabilised Q1-Q1 (beta 0.02)' if q1 else 'Q2-Q1'} {N}^3, {nlev} "
+                                  "levels, 20 blobs, sinker", "train_problems": 8,
                       "train_samples": int(sum(len(y) for y in ys)), "collect_s": collect_s, "train_s": train_s,
                       "loss_first_last": [losses[0][1], losses[-1][1]]},
            "results": results}
@@ -740,8 +753,8 @@ def main():
     if args.workload in ("3d-precision", "3d-precision-q1"):
         run_precision(args, q1=args.workload == "3d-precision-q1")
         return
-    if args.workload == "3d-learned":
-        run_learned(args)
+    if args.workload in ("3d-learned", "3d-learned-q1"):
+        run_learned(args, q1=args.workload == "3d-learned-q1")
         return
     if args.workload in ("2d-steps", "2d-steps-q1"):
         run_steps(args, q1=args.workload == "2d-steps-q1")
