@@ -47,6 +47,10 @@ WORKLOADS = {
                        desc="as 2d512 with the owned rows of the patch inverses stored densely in FP64"),
     "2d512-f32": dict(dim=2, N=512, nlev=7, bc=1, forcing=1, kind=0, prec=1, omega=0.5, nu=2,
                       desc="as 2d512 with FP32-stored patch inverses (FP32 accumulation)"),
+    "2d512-f32fact": dict(dim=2, N=512, nlev=7, bc=1, forcing=1, kind=0, prec=5, omega=0.5, nu=2,
+                          desc="as 2d512 with the factored inverses stored in FP32 (FP32 accumulation)"),
+    "2d512-bf16fact": dict(dim=2, N=512, nlev=7, bc=1, forcing=1, kind=0, prec=6, omega=0.5, nu=2,
+                           desc="as 2d512 with the factored inverses stored in BF16 (FP32 accumulation)"),
     "3d32": dict(dim=3, N=32, nlev=4, bc=1, forcing=2, kind=0, prec=0, omega=0.5, nu=2, blobs=(20, 3.0),
                  desc="3D Stokes Q2-Q1 32^3 unit cube, 4 levels, 20 seeded viscosity blobs (contrast <= 1e3), "
                       "sinker forcing, no-slip, RAV V(2,2) omega 0.5, FP64 factored inverses"),
