@@ -385,3 +385,15 @@ def test_single_global_subdomain_solves_exactly():
     x0[m] = g[m]
     got = o.smooth(1, x0, b)
     assert np.abs(got - xs).max() <= 1e-10 * np.abs(xs).max()
+
+
+def test_dof_count_equals_the_papers_table():
+    """The paper's Table 1 row Omega_h^1 (64 elements, 243 DoFs) is a uniform
+    8x8 Q1-Q1 grid counted with every DoF: the oracle's Q1-Q1 hierarchy on it
+    has exactly 243 DoFs (162 velocity + 81 pressure)."""
+    from test_oracle import read_golden
+    g = read_golden("dof_counts.txt")
+    o = q1_oracle(2, 8)
+    s = o.sizes(0)
+    assert 8 * 8 == g["table1_omega1_elements"]
+    assert s["n"] == g["table1_omega1_q1q1_dofs"] and s["n_u"] == 162 and s["n_p"] == 81
