@@ -400,23 +400,51 @@ def run_ours(args, W):
            "breakdown_us_per_cycle": breakdown}
 
     # ---- end to end through the public API with host buffers ----
+    # Every step uploads its x and b from pinned host memory, runs one V-cycle
+    # and reads its x back.  Steps are pipelined over two device buffer pairs:
+    # the upload of step k+1 (one stream) and the read-back of step k-1
+    # (another) overlap the V-cycle of step k (a third), ordered by events.
     if not args.no_e2e:
         xh = x0.cpu().pin_memory()
         bh = b.cpu().pin_memory()
-        xo = torch.empty_like(xh).pin_memory()
-        xd, bd = torch.empty_like(x), torch.empty_like(b)
+        xo = [torch.empty_like(xh).pin_memory() for _ in range(2)]
+        xd = [torch.empty_like(x) for _ in range(2)]
+        bd = [torch.empty_like(b) for _ in range(2)]
+        s_up, s_comp, s_down = torch.cuda.Stream(), torch.cuda.Stream(), torch.cuda.Stream()
+        up_done = [torch.cuda.Event() for _ in range(2)]
+        comp_done = [torch.cuda.Event() for _ in range(2)]
+        down_done = [torch.cuda.Event() for _ in range(2)]
+        for j in range(2):  # capture each buffer pair's cycle before timing
+            xd[j].copy_(xh)
+            bd[j].copy_(bh)
+            with torch.cuda.stream(s_comp):
+                mg.vcycle(sm, xd[j], bd[j], nu, nu)
+        torch.cuda.synchronize()
         K = max(10, args.steps // 10)
         barrier()
         t0 = time.perf_counter()
-        for _ in range(K):
-            xd.copy_(xh, non_blocking=True)
-            bd.copy_(bh, non_blocking=True)
-            mg.vcycle(sm, xd, bd, nu, nu)
-            xo.copy_(xd, non_blocking=True)
+        for k in range(K):
+            j = k % 2
+            if k >= 2:
+                s_up.wait_event(down_done[j])  # step k-2 has left buffer j
+            with torch.cuda.stream(s_up):
+                xd[j].copy_(xh, non_blocking=True)
+                bd[j].copy_(bh, non_blocking=True)
+                up_done[j].record(s_up)
+            s_comp.wait_event(up_done[j])
+            with torch.cuda.stream(s_comp):
+                mg.vcycle(sm, xd[j], bd[j], nu, nu)
+                comp_done[j].record(s_comp)
+            s_down.wait_event(comp_done[j])
+            with torch.cuda.stream(s_down):
+                xo[j].copy_(xd[j], non_blocking=True)
+                down_done[j].record(s_down)
         torch.cuda.synchronize()
         dt = time.perf_counter() - t0
         out["e2e"] = {"value": ws * n * K / dt, "unit": "DoF/s", "h2d_bytes_per_step": 2 * n * 8,
-                      "d2h_bytes_per_step": n * 8, "steps": K}
+                      "d2h_bytes_per_step": n * 8, "steps": K,
+                      "pipelined": "uploads and read-backs of neighbouring steps overlap each V-cycle "
+                                   "(three streams, two device buffer pairs)"}
 
     # ---- time to a 1e-8 residual reduction (host-driven stationary solve) ----
     if not args.no_tol:
