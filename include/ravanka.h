@@ -183,7 +183,9 @@ int rav_get_residual_split(const rav_mg* mg, int level);
  *    RAV_ERR_ARG before anything is launched.
  *  * The first call on a device looks up that array's device address (with
  *    the device current) and caches it; make that first call before any
- *    stream capture, and call with the device of mg current.
+ *    stream capture.  Call with the device of mg (the one current at
+ *    mg_setup) current: any other current device gives RAV_ERR_ARG before
+ *    anything is launched.
  *  * All calls share the array and it keeps the last call's contents (every
  *    call overwrites the entries it uses, nothing needs clearing first): calls
  *    whose kernels overlap on the GPU (different streams, no ordering) race
@@ -329,7 +331,9 @@ typedef struct rav_solve_info {
  * iterations) orthogonalises by classical Gram-Schmidt applied twice; the
  * least-squares update runs on the host.  The residual norm, the Krylov
  * vectors and the solution stay fp64 whatever the smoother's storage.
- * info may be NULL. */
+ * info may be NULL; otherwise it is filled on every return, failures included
+ * (status = the returned code; iterations, final_ratio and history up to the
+ * iteration reached; fell_back = 0 unless the stationary fallback happened). */
 int solve(rav_mg* mg, rav_smoother* sm, double* x_dev, const double* b_dev, const rav_solve_opts* opts,
           rav_solve_info* info, rav_stream stream);
 

@@ -97,6 +97,7 @@ struct Level {
 
 struct rav_mg {
   int dim = 2, N = 0, nlev = 0;
+  int device = 0;  // CUDA device current at mg_setup (the hierarchy's memory lives there)
   double eta0 = 1.0;
   int bc = 0;
   int elem = RAV_ELEM_Q2Q1;  // discretisation (rav_element)

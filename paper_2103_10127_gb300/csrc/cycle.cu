@@ -666,13 +666,14 @@ static constexpr int kMaxDevices = 64;
 static double* g_noalloc_addr[kMaxDevices] = {};
 static std::mutex g_noalloc_mu;
 
-// Device address of g_noalloc_parts on the current device.  In host code the
-// symbol is only a stand-in; the address is looked up once per device, with
-// that device current, and remembered.
-static int noalloc_parts_address(double** out) {
+// Device address of g_noalloc_parts on the current device, which must be the
+// device the hierarchy was built on (its pointers are only valid there).  In
+// host code the symbol is only a stand-in; the address is looked up once per
+// device, with that device current, and remembered.
+static int noalloc_parts_address(const rav_mg* mg, double** out) {
   int dev = 0;
   RAV_CUDA(cudaGetDevice(&dev));
-  if (dev < 0 || dev >= kMaxDevices) return RAV_ERR_ARG;
+  if (dev != mg->device || dev < 0 || dev >= kMaxDevices) return RAV_ERR_ARG;
   std::lock_guard<std::mutex> lock(g_noalloc_mu);
   if (!g_noalloc_addr[dev]) {
     void* p = nullptr;
@@ -691,7 +692,7 @@ extern "C" int rav_residual_norm_noalloc(rav_mg* mg, int level, const double* x,
   const int64_t blocks = (nslots + 255) / 256;
   if (blocks > kNoAllocParts) return RAV_ERR_ARG;  // level has more than 4,194,304 row slots
   double* parts = nullptr;
-  RAV_TRY(noalloc_parts_address(&parts));
+  RAV_TRY(noalloc_parts_address(mg, &parts));
   cudaStream_t s = S(stream);
   k_residual_sell<<<(unsigned)blocks, 256, 0, s>>>(nslots, L.sperm, L.sptr, L.slen, L.scol, L.sval, x, b, r, parts,
                                                    nullptr);
@@ -885,10 +886,18 @@ static int fgmres_run(rav_mg* mg, rav_smoother* sm, double* x, const double* b, 
 
 extern "C" int solve(rav_mg* mg, rav_smoother* sm, double* x, const double* b, const rav_solve_opts* opts,
                      rav_solve_info* info, rav_stream stream) {
-  if (!mg || !sm || sm->mg != mg || !x || !b || !opts || opts->maxit < 0 || !(opts->tol > 0)) return RAV_ERR_ARG;
-  if (opts->outer == 1) {
-    if (opts->restart > 62) return RAV_ERR_ARG;
-    return solve_fgmres(mg, sm, x, b, *opts, info, S(stream));
+  // info is filled on every exit, failures included: the outer loops set
+  // what they reached, and a failure before that leaves these defaults
+  if (info) {
+    info->iterations = 0;
+    info->status = RAV_ERR_ARG;
+    info->final_ratio = 1.0;
+    info->fell_back = 0;
   }
-  return solve_stationary(mg, sm, x, b, *opts, info, S(stream));
+  int rc = RAV_ERR_ARG;
+  if (!mg || !sm || sm->mg != mg || !x || !b || !opts || opts->maxit < 0 || !(opts->tol > 0)) rc = RAV_ERR_ARG;
+  else if (opts->outer == 1) rc = opts->restart > 62 ? RAV_ERR_ARG : solve_fgmres(mg, sm, x, b, *opts, info, S(stream));
+  else rc = solve_stationary(mg, sm, x, b, *opts, info, S(stream));
+  if (info) info->status = rc;
+  return rc;
 }

@@ -1230,6 +1230,10 @@ extern "C" int mg_setup(const rav_problem* p, int n_levels, rav_stream stream, r
   mg->dim = p->dim;
   mg->N = p->N;
   mg->nlev = n_levels;
+  if (cudaGetDevice(&mg->device) != cudaSuccess) {
+    delete mg;
+    return RAV_ERR_CUDA;
+  }
   mg->eta0 = p->eta0;
   mg->bc = p->bc;
   mg->elem = p->element;
