@@ -36,11 +36,13 @@ F_NONE, F_PSI, F_SINKER, F_QUADRATIC = 0, 1, 2, 3
 
 
 def build(force: bool = False) -> str:
-    """Compile the oracle shared library next to its source."""
+    """Compile the oracle shared library next to its source (with OpenMP for
+    the independent subdomain loops when the compiler has it, else serial)."""
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
         tmp = _LIB + f".tmp{os.getpid()}"
-        subprocess.check_call(["g++", "-O2", "-ffp-contract=off", "-std=c++17", "-shared", "-fPIC",
-                               _SRC, "-o", tmp])
+        base = ["g++", "-O2", "-ffp-contract=off", "-std=c++17", "-shared", "-fPIC", _SRC, "-o", tmp]
+        if subprocess.call(base[:1] + ["-fopenmp"] + base[1:], stderr=subprocess.DEVNULL) != 0:
+            subprocess.check_call(base)
         os.replace(tmp, _LIB)
     return _LIB
 
@@ -86,6 +88,7 @@ def _load():
             "orc_mlp_nparam": (ll, []),
             "orc_mlp_forward": (None, [P, P, ll, P]),
             "orc_mlp_loss_grad": (d, [P, P, P, ll, P]),
+            "orc_set_threads": (i, [i]),
         }
         for name, (res, args) in sig.items():
             f = getattr(lib, name)
@@ -93,6 +96,13 @@ def _load():
             f.argtypes = args
         _lib = lib
     return _lib
+
+
+def set_threads(n: int) -> int:
+    """Threads of the oracle's loops over independent subdomains (local
+    inverses, RAV corrections); the results do not depend on it.  Returns the
+    number in effect (1 without OpenMP)."""
+    return _load().orc_set_threads(int(n))
 
 
 def _ptr(a):

@@ -38,6 +38,12 @@
 
 namespace {
 
+// Threads for the loops over independent subdomains (local inverses and the
+// RAV/AV corrections, whose per-subdomain arithmetic does not depend on the
+// order); 1 unless orc_set_threads says otherwise.  Every other loop runs
+// serially.  Without OpenMP the pragmas are ignored and everything is serial.
+int g_threads = 1;
+
 // ---------------------------------------------------------------------------
 // 1-D building blocks on the reference interval [0,1].
 // Three-point Gauss-Legendre rule (exact to degree 5).
@@ -863,6 +869,7 @@ void quantise(Oracle& O, Level& L) {
   L.qscale.assign(np, {});
   if (O.prec == 0) return;
   if (O.prec >= 5) {
+#pragma omp parallel for schedule(dynamic, 16) num_threads(g_threads)
     for (int64_t p = 0; p < np; ++p) {
       factored_rows(L, p, O.prec - 4, L.qinv[p]);
       L.qscale[p].assign(L.owned[p].size(), 1.0);
@@ -921,6 +928,11 @@ void smooth(Oracle& O, Level& L, double* x, const double* b) {
   if (O.kind == 0 || O.kind == 1) {
     residual(L, x, b, r.data());
     std::vector<double> xn(x, x + L.n);
+    // The subdomain corrections all use the same residual r.  RAV (Eq. 13)
+    // writes only owned DoFs, which belong to one subdomain each, so its
+    // subdomains are independent; AV (Eq. 12) adds overlapping corrections to
+    // shared DoFs and stays in ascending subdomain order.
+#pragma omp parallel for schedule(dynamic, 64) num_threads(O.kind == 0 ? g_threads : 1) private(rloc, y)
     for (int64_t p = 0; p < np; ++p) {
       const int64_t b0 = L.poff[p], ni = L.poff[p + 1] - b0;
       rloc.resize(ni);
@@ -1148,6 +1160,18 @@ void orc_rhs(void* h, int fkind, double* b) {
     if (L.dir[i]) b[i] = L.g[i];
 }
 
+// Threads of the subdomain loops (>= 1); returns the number in effect, which
+// is 1 when the library was built without OpenMP.
+int orc_set_threads(int n) {
+#ifdef _OPENMP
+  g_threads = n < 1 ? 1 : n;
+#else
+  (void)n;
+  g_threads = 1;
+#endif
+  return g_threads;
+}
+
 // Viscosity at a point (so tests can check the coefficient field).
 double orc_viscosity(void* h, const double* x) { return viscosity(((Oracle*)h)->P, x); }
 
@@ -1166,8 +1190,11 @@ int orc_setup_smoother(void* h, int kind, double omega, int prec) {
     const int64_t np = (int64_t)L.poff.size() - 1;
     L.inv.assign(np, {});
     L.omega.assign(np, omega);
+    int bad = 0;
+#pragma omp parallel for schedule(dynamic, 16) num_threads(g_threads) reduction(|: bad)
     for (int64_t p = 0; p < np; ++p)
-      if (!inverse_rows(L, p, kind != 0, L.inv[p])) return -3;
+      if (!inverse_rows(L, p, kind != 0, L.inv[p])) bad = 1;
+    if (bad) return -3;
     quantise(O, L);
   }
   return 0;
@@ -1192,8 +1219,11 @@ int orc_set_patches(void* h, int l, long long np, const int64_t* off, const int6
   fill_owned(L);
   L.inv.assign(np, {});
   L.omega.assign(np, omega);
+  int bad = 0;
+#pragma omp parallel for schedule(dynamic, 16) num_threads(g_threads) reduction(|: bad)
   for (long long p = 0; p < np; ++p)
-    if (!inverse_rows(L, p, O.kind != 0, L.inv[p])) return -3;
+    if (!inverse_rows(L, p, O.kind != 0, L.inv[p])) bad = 1;
+  if (bad) return -3;
   quantise(O, L);
   return 0;
 }

@@ -471,3 +471,60 @@ def test_full_size_32cube_sampled_parity():
         bf16.append(steps[R.BF16_FACT][mine])
     wants, bf16 = np.concatenate(wants), np.concatenate(bf16)
     assert 0.0 < np.linalg.norm(bf16 - wants) <= 2e-2 * np.linalg.norm(wants)
+
+
+@pytest.mark.slow
+def test_full_size_512_convergence_factors_within_two_percent():
+    """The benchmark workload itself: 512^2 Q2-Q1, 7 levels, the manufactured
+    psi problem, stationary RAV(0.5) V(2,2) multigrid to a 1e-8 residual
+    reduction (Sec. 4's stopping rule) in the launch configuration the bench
+    times (graph replay, tuned launch shapes).  The cycle count equals the
+    oracle's and every per-cycle reduction factor ||r_k||/||r_{k-1}|| and the
+    mean factor are within 2 % of the oracle's."""
+    N, nlev = 512, 7
+    mg = R.Multigrid(2, N, nlev, bc=R.BC_NOSLIP)
+    sm = R.Smoother(mg, R.RAV, R.F64, 0.5)
+    x = mg.initial_guess()
+    it, hist, rc = mg.solve(sm, x, mg.rhs(R.F_PSI), tol=1e-8, maxit=40)
+    xg = cpu(x)
+    del sm, mg
+    orc = O.Oracle(2, N, nlev, bc=O.BC_NOSLIP)
+    orc.setup_smoother(O.RAV, 0.5)
+    ox, oit, ohist = orc.solve(orc.initial_guess(), orc.rhs(O.F_PSI), tol=1e-8, maxit=40)
+    assert rc == 0 and oit > 0 and it == oit
+    fac, ofac = hist[1:] / hist[:-1], ohist[1:] / ohist[:-1]
+    assert np.all(np.abs(fac / ofac - 1.0) <= 0.02), np.abs(fac / ofac - 1.0).max()
+    assert abs((hist[-1] / ohist[-1]) ** (1.0 / it) - 1.0) <= 0.02
+    # the iterates agree to well within what the 1e-8 reduction leaves
+    assert rel(xg, ox) <= 1e-6
+
+
+@pytest.mark.slow
+def test_3d_blob_fgmres_iterations_match():
+    """A reduced stand-in of the 3-D blob workload: 16^3 Q2-Q1, 3 levels, the
+    20 seeded viscosity blobs (contrast <= 1e3), sinker forcing, no-slip,
+    FGMRES(30) right-preconditioned by one RAV(0.5) V(2,2) cycle, to 1e-8.
+    FP64 factored storage: the same iteration count as the oracle's FGMRES and
+    every per-iteration factor within 2 %; FP32 and BF16 factored storage
+    (fp32 accumulation) reach the same fp64 tolerance in at most one more
+    iteration than the FP64 oracle."""
+    N, nlev = 16, 3
+    blobs = inputs.viscosity_blobs(inputs.BASE_SEED, k=20, s_max=3.0)
+    mg = R.Multigrid(3, N, nlev, blobs=blobs, bc=R.BC_NOSLIP)
+    b = mg.rhs(R.F_SINKER)
+    runs = {}
+    for prec in (R.F64, R.F32_FACT, R.BF16_FACT):
+        sm = R.Smoother(mg, R.RAV, prec, 0.5)
+        runs[prec] = mg.solve(sm, mg.initial_guess(), b, tol=1e-8, maxit=100, outer=1)
+        del sm
+    del mg
+    orc = O.Oracle(3, N, nlev, blobs=blobs, bc=O.BC_NOSLIP)
+    orc.setup_smoother(O.RAV, 0.5)
+    _, oit, ohist = orc.fgmres(orc.initial_guess(), orc.rhs(O.F_SINKER), tol=1e-8, maxit=100)
+    it, hist, rc = runs[R.F64]
+    assert rc == 0 and oit > 0 and it == oit
+    fac, ofac = hist[1:] / hist[:-1], ohist[1:] / ohist[:-1]
+    assert np.all(np.abs(fac / ofac - 1.0) <= 0.02), np.abs(fac / ofac - 1.0).max()
+    for prec in (R.F32_FACT, R.BF16_FACT):
+        it_p, hist_p, rc_p = runs[prec]
+        assert rc_p == 0 and hist_p[-1] <= 1e-8 and it_p <= oit + 1, (prec, it_p, oit)

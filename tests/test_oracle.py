@@ -631,3 +631,30 @@ def test_labels_are_coordinate_line_search_minimisers():
         else:
             assert f(1.5) <= f(1.5 - 1e-3)
     assert checked >= 5
+
+
+@pytest.mark.parametrize("kind,prec", [(O.RAV, O.F64), (O.RAV, O.F32_FACT), (O.AV, O.F64)])
+def test_thread_count_does_not_change_the_oracle(kind, prec):
+    """The oracle's subdomain loops (local inverses, RAV corrections) may run
+    on several threads; each subdomain's arithmetic is the same and RAV writes
+    disjoint owned DoFs, so set-up, steps and V-cycles are bit-identical for
+    any thread count."""
+    rng = np.random.default_rng(3)
+    coords = inputs.graded_coordinates(12, 3.0, 2)
+    blobs = inputs.viscosity_blobs(17, k=5, s_max=2.0)
+    outs = []
+    try:
+        for threads in (1, 4):
+            O.set_threads(threads)
+            orc = O.Oracle(2, 12, 2, coords=coords, blobs=blobs, bc=O.BC_NOSLIP)
+            orc.setup_smoother(kind, 0.5 if kind == O.RAV else 0.1, prec)
+            n = orc.sizes(1)["n"]
+            x, b = rng.standard_normal(n), rng.standard_normal(n)
+            outs.append((orc.smooth(1, x, b, 2), orc.vcycle(x, b, 2, 2),
+                         orc.inverse(1, 5), orc.inverse(1, 40, quantised=prec != O.F64)))
+            rng = np.random.default_rng(3)
+    finally:
+        O.set_threads(1)
+    for a, b in zip(*outs):
+        a, b = (a[0], b[0]) if isinstance(a, tuple) else (a, b)
+        assert np.array_equal(a, b)
