@@ -15,8 +15,15 @@ Reported with it:
                 timed region, against the FP64 arithmetic peak (it is bound by
                 fp64 FMA throughput on GB300; patch_work() holds the counts);
   e2e           the same metric with host buffers, host<->device copies inside;
-  cpu_baseline  the FP64 oracle (one host core) on a bounded sample;
-  time_to_tol   wall time of a full solve to a 1e-8 residual reduction.
+  cpu_baseline  the FP64 oracle on a bounded sample, on one host core and on
+                every host core (its subdomain loops in parallel);
+  time_to_tol   wall time of a full solve to a 1e-8 residual reduction;
+  forms_to_tol  (default workload) time to 1e-8 of the reduced-precision and
+                batched forms against the plain FP64 GPU form on the same
+                problems: 512^2 stationary and 32^3 FGMRES(30) with FP64 /
+                FP32 / BF16 factored inverses, and the 256-cavity x 8-RHS batch
+                with FP32 and FP64 rows on the batched path, each group with
+                its own clock record (forms_vs_fp64()).
 
 --impl reference times the oracle itself as the reference arm.
 """
@@ -95,6 +102,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-tol", action="store_true")
+    ap.add_argument("--no-forms", action="store_true",
+                    help="default workload: skip the reduced-precision / batched vs FP64 time-to-tolerance runs")
     ap.add_argument("--fused", action="store_true",
                     help="Q1-Q1 RAV fp64 workloads: one fused residual + subdomain-apply kernel per smoothing step")
     ap.add_argument("--N", type=int, default=None, help="override the grid size (profiling runs)")
@@ -223,37 +232,64 @@ def measured_traffic(kernel_key):
         return None
 
 
+def workload_config(W, n, nnz, stored, ws, fused=False):
+    """The `config` object of a default-style line, the same for both arms."""
+    return {"workload": W["desc"], "dofs": n, "levels": W["nlev"], "nu": [W["nu"], W["nu"]],
+            "smoother": "RAV" + (", fused residual + apply per step" if fused else ""),
+            "inverse_storage": STORAGE[W["prec"]],
+            "l2": "inputs larger than L2: each fine-level pass streams the operator "
+                  f"({nnz * 12 / 1e9:.2f} GB) and the stored patch inverses "
+                  f"({stored / 1e9:.2f} GB) > 129 MB L2",
+            "parallelism": "replicas" if ws > 1 else "single GPU"}
+
+
 # ---------------------------------------------------------------------------
-def cpu_baseline(W, cycles=1):
-    """The oracle, as it stands, on the same workload: untimed set-up, then
-    `cycles` timed V-cycles on one host core."""
+def oracle_for(W):
+    """The oracle on the workload, set up (untimed) with every host core."""
     import oracle as O
-    import numpy as np
+    O.set_threads(os.cpu_count() or 1)
     orc = O.Oracle(W["dim"], W["N"], W["nlev"], bc=W["bc"], blobs=make_blobs(W), element=W.get("elem", 0),
                    beta=W.get("beta", 0.0))
     orc.setup_smoother(O.RAV, W["omega"], W["prec"] if W["prec"] in (1, 2, 3, 5, 6) else 0)
+    return O, orc
+
+
+def cpu_baseline(W, cycles=1):
+    """The oracle, as it stands, on the same workload: untimed set-up, then
+    `cycles` timed V-cycles on one host core (the paper's setting) and the
+    same on every host core (its independent subdomain loops in parallel,
+    everything else serial).  Returns (DoF/s one core, s, DoF/s all cores, s,
+    cores, n)."""
+    O, orc = oracle_for(W)
     b = orc.rhs(W["forcing"])
-    x = orc.initial_guess()
+    x0 = orc.initial_guess()
     n = orc.sizes(W["nlev"] - 1)["n"]
-    t0 = time.perf_counter()
-    for _ in range(cycles):
-        x = orc.vcycle(x, b, W["nu"], W["nu"])
-    dt = time.perf_counter() - t0
+    res = []
+    for threads in (1, os.cpu_count() or 1):
+        used = O.set_threads(threads)
+        x = x0
+        t0 = time.perf_counter()
+        for _ in range(cycles):
+            x = orc.vcycle(x, b, W["nu"], W["nu"])
+        dt = time.perf_counter() - t0
+        res.append((n * cycles / dt, dt, used))
+    O.set_threads(1)
     del orc
-    return n * cycles / dt, dt, n
+    return res[0][0], res[0][1], res[1][0], res[1][1], res[1][2], n
 
 
 def run_reference(args, W):
+    """The reference arm: the oracle itself on the same workload, one host core
+    for the timed cycles (the paper's setting), set-up untimed."""
     ws, rank, _ = dist_env()
     if rank != 0:
         return
-    import oracle as O
-    orc = O.Oracle(W["dim"], W["N"], W["nlev"], bc=W["bc"], blobs=make_blobs(W), element=W.get("elem", 0),
-                   beta=W.get("beta", 0.0))
-    orc.setup_smoother(O.RAV, W["omega"], W["prec"] if W["prec"] in (1, 2, 3, 5, 6) else 0)
+    O, orc = oracle_for(W)
+    O.set_threads(1)
     b = orc.rhs(W["forcing"])
     x = orc.initial_guess()
-    n = orc.sizes(W["nlev"] - 1)["n"]
+    sz = orc.sizes(W["nlev"] - 1)
+    n = sz["n"]
     for _ in range(args.warmup):
         x = orc.vcycle(x, b, W["nu"], W["nu"])
     t0 = time.perf_counter()
@@ -261,10 +297,11 @@ def run_reference(args, W):
         x = orc.vcycle(x, b, W["nu"], W["nu"])
     dt = time.perf_counter() - t0
     v = n * args.steps / dt
+    _, _, stored = patch_work(W["dim"], W["N"], W["prec"], n, q=1 if W.get("elem", 0) == 1 else 2)
     out = {"impl": "reference", "metric": "V-cycle DoFs/s", "value": v, "unit": "DoF/s", "n_gpus": args.gpus,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-           "config": {"workload": W["desc"], "dofs": n, "levels": W["nlev"]},
+           "config": workload_config(W, n, sz["nnz"], stored, args.gpus),
            "cpu_baseline": {"value": v, "unit": "DoF/s", "cores": 1, "kind": "oracle",
                             "sample": f"{args.steps} V(2,2) cycles of the full workload after untimed set-up"},
            "e2e": {"value": v, "unit": "DoF/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -388,13 +425,7 @@ def run_ours(args, W):
     out = {"metric": "V-cycle DoFs/s", "value": value, "unit": "DoF/s", "n_gpus": ws, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-           "config": {"workload": W["desc"], "dofs": n, "levels": W["nlev"], "nu": [nu, nu],
-                      "smoother": "RAV" + (", fused residual + apply per step" if args.fused else ""),
-                      "inverse_storage": STORAGE[W["prec"]],
-                      "l2": "inputs larger than L2: each fine-level pass streams the operator "
-                            f"({mg.counts(fine)['nnz'] * 12 / 1e9:.2f} GB) and the stored patch inverses "
-                            f"({stored / 1e9:.2f} GB) > 129 MB L2",
-                      "parallelism": "replicas" if ws > 1 else "single GPU"},
+           "config": workload_config(W, n, mg.counts(fine)["nnz"], stored, ws, args.fused),
            "roofline": roof, "gpu_launches": int(launches), "clocks": clocks,
            "ms_per_step_kernel_by_kernel": ms_nograph / args.steps,
            "breakdown_us_per_cycle": breakdown}
@@ -456,11 +487,18 @@ def run_ours(args, W):
         out["time_to_tol"] = {"seconds": dt, "cycles": it, "tol": 1e-8, "status": rc,
                               "rho": float(hist[-1] ** (1.0 / max(it, 1)))}
 
+    # ---- reduced-precision and batched forms against plain FP64, to 1e-8 ----
+    if rank == 0 and ws == 1 and not args.no_forms and args.workload == "2d512" and not args.N:
+        out["forms_to_tol"] = forms_vs_fp64()
+
     if rank == 0 and ws == 1 and not args.no_cpu_baseline and W["dim"] == 2:
-        v, dt, nn = cpu_baseline(W)
+        v, dt, va, dta, cores, nn = cpu_baseline(W)
         out["cpu_baseline"] = {"value": v, "unit": "DoF/s", "cores": 1, "kind": "oracle",
                                "sample": "1 V(2,2) cycle of the full workload on one host core after untimed "
-                                         f"set-up ({dt:.2f} s)"}
+                                         f"set-up ({dt:.2f} s)",
+                               "all_cores": {"value": va, "unit": "DoF/s", "cores": cores, "kind": "oracle",
+                                             "sample": f"the same cycle with the subdomain loops on {cores} "
+                                                       f"threads, the rest serial ({dta:.2f} s)"}}
     if dist is not None:
         dist.barrier()
         dist.destroy_process_group()
@@ -478,32 +516,24 @@ def ctypes_f64():
     return ctypes.c_double(0.0)
 
 
-def run_batch(args, q1=False):
-    """256 independent 2-D lid-driven cavities, N = 16 m with m uniform on
-    {2..16} (seeded), 8 right-hand sides each (lid values + iid N(0,1) forcing
-    on free velocity DoFs), FP32 patch inverses, FP64 residuals; a step is one
-    batched V(2,2) cycle of every problem and right-hand side.  q1: the same
-    problems on the stabilised Q1-Q1 element (beta 0.02, RAV omega 0.66)."""
+def batch_problems(nprob, nrhs, q1=False):
+    """The batched workload's hierarchies and vectors: nprob 2-D lid-driven
+    cavities, N = 16 m with m uniform on {2..16} (seed 2103), nrhs right-hand
+    sides each (lid values + iid N(0,1) forcing on free velocity DoFs),
+    RHS-interleaved.  q1: the stabilised Q1-Q1 element (beta 0.02)."""
     import numpy as np
     import torch
     import paper_2103_10127_gb300 as R
-    from paper_2103_10127_gb300 import _capi, inputs
+    from paper_2103_10127_gb300 import inputs
 
-    torch.cuda.set_device(0)
-    lib = _capi.load()
-    nprob, nrhs = args.nprob, 8
     sizes = inputs.batched_sizes(inputs.BASE_SEED, nprob)
-    mgs, sms, xs, bs = [], [], [], []
-    t0 = time.perf_counter()
-    omega = 0.66 if q1 else 0.5
+    mgs, xs, bs = [], [], []
     for i, N in enumerate(sizes):
         N = int(N)
         if q1:
             mg = R.Multigrid(2, N, inputs.levels_for(N), bc=R.BC_CAVITY, element=R.ELEM_Q1Q1, beta=0.02)
         else:
             mg = R.Multigrid(2, N, inputs.levels_for(N), bc=R.BC_CAVITY)
-        sm = R.Smoother(mg, R.RAV, R.F32, omega)
-        n = mg.n()
         M = (1 if q1 else 2) * N + 1
         idx = np.indices((M, M)).reshape(2, -1)[::-1]
         inner = np.repeat(np.all((idx > 0) & (idx < M - 1), axis=0), 2)
@@ -513,9 +543,53 @@ def run_batch(args, q1=False):
         b[free, :] += inputs.normal(inputs.BASE_SEED + 7919 * (i + 1), int(free.sum()) * nrhs).reshape(-1, nrhs)
         x0 = mg.initial_guess().cpu().numpy()
         mgs.append(mg)
-        sms.append(sm)
         bs.append(torch.from_numpy(np.ascontiguousarray(b)).cuda())
         xs.append(torch.from_numpy(np.ascontiguousarray(np.repeat(x0[:, None], nrhs, axis=1))).cuda())
+    return sizes, mgs, xs, bs
+
+
+def single_problem_fp64_ms(mgs, nrhs, omega):
+    """The plain FP64 form on the batch's problems: one single-problem V(2,2)
+    cycle (FP64 factored inverses, captured graph) per problem and right-hand
+    side, CUDA-event timed and summed (ms)."""
+    import torch
+    import paper_2103_10127_gb300 as R
+
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    total = 0.0
+    for mg in mgs:
+        sm64 = R.Smoother(mg, R.RAV, R.F64, omega)
+        x1, b1 = mg.vector(), mg.rhs(R.F_NONE)
+        mg.vcycle(sm64, x1, b1, 2, 2)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(nrhs):
+            mg.vcycle(sm64, x1, b1, 2, 2)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        total += e0.elapsed_time(e1)
+        del sm64
+    return total
+
+
+def run_batch(args, q1=False):
+    """256 independent 2-D lid-driven cavities, N = 16 m with m uniform on
+    {2..16} (seeded), 8 right-hand sides each (lid values + iid N(0,1) forcing
+    on free velocity DoFs), FP32 patch inverses, FP64 residuals; a step is one
+    batched V(2,2) cycle of every problem and right-hand side.  q1: the same
+    problems on the stabilised Q1-Q1 element (beta 0.02, RAV omega 0.66)."""
+    import torch
+    import paper_2103_10127_gb300 as R
+    from paper_2103_10127_gb300 import _capi, inputs
+
+    torch.cuda.set_device(0)
+    lib = _capi.load()
+    nprob, nrhs = args.nprob, 8
+    t0 = time.perf_counter()
+    omega = 0.66 if q1 else 0.5
+    sizes, mgs, xs, bs = batch_problems(nprob, nrhs, q1)
+    sms = [R.Smoother(mg, R.RAV, R.F32, omega) for mg in mgs]
     bt = R.Batch(mgs, sms, nrhs)
     setup_s = time.perf_counter() - t0
     dofs = sum(m.n() for m in mgs)
@@ -559,22 +633,7 @@ def run_batch(args, q1=False):
     t0 = time.perf_counter()
     it, ratios, rc = bt.solve(xs, bs, tol=1e-8, maxit=100, raise_on_error=False)
     tsolve = time.perf_counter() - t0
-    # the plain FP64 form on the same problems: one single-problem V(2,2) cycle
-    # (FP64 factored inverses, captured graph) per problem and right-hand side
-    single_ms = 0.0
-    if not args.no_single:
-        for mg in mgs:
-            sm64 = R.Smoother(mg, R.RAV, R.F64, omega)
-            x1, b1 = xs[0].new_zeros(mg.n()), mg.rhs(R.F_NONE)
-            mg.vcycle(sm64, x1, b1, 2, 2)
-            torch.cuda.synchronize()
-            e0.record(stream)
-            for _ in range(nrhs):
-                mg.vcycle(sm64, x1, b1, 2, 2)
-            e1.record(stream)
-            torch.cuda.synchronize()
-            single_ms += e0.elapsed_time(e1)
-            del sm64
+    single_ms = 0.0 if args.no_single else single_problem_fp64_ms(mgs, nrhs, omega)
     out = {"metric": "V-cycle DoFs/s", "value": dofs * nrhs * args.steps / (ms / 1e3), "unit": "DoF/s",
            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
@@ -592,6 +651,108 @@ def run_batch(args, q1=False):
            "time_to_tol": {"seconds": tsolve, "max_cycles": int(it.max()), "min_cycles": int(it.min()),
                            "status": rc, "tol": 1e-8}}
     print(json.dumps(out), flush=True)
+
+
+def timed_solve(mg, sm, b, outer, reps=3, maxit=200):
+    """Best wall time of `reps` solves to a 1e-8 residual reduction from the
+    initial guess (stationary V(2,2) multigrid, or FGMRES(30) preconditioned by
+    one V(2,2) cycle), after one warm call that captures the cycle graphs."""
+    import torch
+    x = mg.initial_guess()
+    mg.solve(sm, x, b, tol=1e-8, maxit=1, outer=outer, raise_on_error=False)
+    best = None
+    for _ in range(reps):
+        x = mg.initial_guess()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        it, hist, rc = mg.solve(sm, x, b, tol=1e-8, maxit=maxit, outer=outer, raise_on_error=False)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        best = dt if best is None or dt < best else best
+    return {"seconds": best, "iterations": int(it), "status": int(rc), "final_ratio": float(hist[-1])}
+
+
+def forms_vs_fp64(nprob=256, nrhs=8):
+    """Time to a 1e-8 residual reduction of the reduced-precision and batched
+    forms against the plain FP64 GPU form, on the same problems, each group
+    with its own clock record:
+      2d512:  the 512^2 manufactured problem, stationary RAV(0.5) V(2,2), FP64
+              vs FP32 vs BF16 factored inverses (fp32 accumulation);
+      3d32:   the 32^3 blob problem (contrast <= 1e3, sinker), FGMRES(30) with
+              one V(2,2) cycle, FP64 vs FP32 vs BF16 factored inverses;
+      batch:  the 256 cavities x 8 right-hand sides on the batched path with
+              FP32 rows against the same batched path with FP64 rows (the
+              batching gain and the precision gain apart), and the sum of the
+              single-problem FP64 cycles over every problem and RHS."""
+    import torch
+    import paper_2103_10127_gb300 as R
+    from paper_2103_10127_gb300 import inputs
+
+    formats = (("f64-factored", R.F64), ("f32-factored", R.F32_FACT), ("bf16-factored", R.BF16_FACT))
+    out = {}
+    for key, dim, N, nlev, outer in (("2d512_stationary", 2, 512, 7, 0), ("3d32_fgmres30", 3, 32, 4, 1)):
+        if dim == 2:
+            mg = R.Multigrid(2, N, nlev, bc=R.BC_NOSLIP)
+            b = mg.rhs(R.F_PSI)
+        else:
+            mg = R.Multigrid(3, N, nlev, blobs=inputs.viscosity_blobs(inputs.BASE_SEED, k=20, s_max=3.0),
+                             bc=R.BC_NOSLIP)
+            b = mg.rhs(R.F_SINKER)
+        row = {"dofs": mg.n()}
+        clk = clocks_start()
+        for name, prec in formats:
+            sm = R.Smoother(mg, R.RAV, prec, 0.5)
+            row[name] = timed_solve(mg, sm, b, outer)
+            del sm
+        row["clocks"] = clocks_stop(clk, torch.cuda.current_device())
+        base = row["f64-factored"]["seconds"]
+        row["speedup_vs_f64"] = {nm: base / row[nm]["seconds"] for nm, _ in formats}
+        out[key] = row
+        del mg
+    # the batch: the same problems and right-hand sides on the batched path, FP32 and FP64 rows
+    t0 = time.perf_counter()
+    sizes, mgs, xs, bs = batch_problems(nprob, nrhs)
+    x_init = [x.clone() for x in xs]
+    row = {"problems": nprob, "rhs": nrhs, "dofs_total": int(sum(m.n() for m in mgs))}
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    clk = clocks_start()
+    for name, prec in (("batched-f32-rows", R.F32), ("batched-f64-rows", R.F64_ROWS)):
+        sms = [R.Smoother(mg, R.RAV, prec, 0.5) for mg in mgs]
+        bt = R.Batch(mgs, sms, nrhs)
+        for _ in range(2):
+            bt.vcycle(xs, bs, 2, 2)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(3):
+            bt.vcycle(xs, bs, 2, 2)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        cyc = e0.elapsed_time(e1) / 3
+        for x, xi in zip(xs, x_init):
+            x.copy_(xi)
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        it, _, rc = bt.solve(xs, bs, tol=1e-8, maxit=100, raise_on_error=False)
+        torch.cuda.synchronize()
+        row[name] = {"ms_per_cycle": cyc, "seconds_to_tol": time.perf_counter() - t1, "status": int(rc),
+                     "cycles_min_max": [int(it.min()), int(it.max())]}
+        for x, xi in zip(xs, x_init):
+            x.copy_(xi)
+        del bt, sms
+    row["single-problem-f64-factored"] = {"ms_per_cycle_all": single_problem_fp64_ms(mgs, nrhs, 0.5),
+                                          "note": "one V(2,2) cycle per problem and RHS, summed"}
+    row["clocks"] = clocks_stop(clk, torch.cuda.current_device())
+    row["setup_and_run_s"] = time.perf_counter() - t0
+    f32, f64 = row["batched-f32-rows"], row["batched-f64-rows"]
+    row["speedup"] = {"precision (batched f64 / batched f32, time to tol)": f64["seconds_to_tol"] /
+                      f32["seconds_to_tol"],
+                      "batching (single-problem f64 / batched f64, per cycle)":
+                      row["single-problem-f64-factored"]["ms_per_cycle_all"] / f64["ms_per_cycle"],
+                      "both (single-problem f64 / batched f32, per cycle)":
+                      row["single-problem-f64-factored"]["ms_per_cycle_all"] / f32["ms_per_cycle"]}
+    out["batch_256x8"] = row
+    return out
 
 
 def run_precision(args, q1=False):
