@@ -30,6 +30,7 @@ Reported with it:
 from __future__ import annotations
 
 import argparse
+import ctypes
 import hashlib
 import json
 import os
@@ -105,7 +106,11 @@ def parse():
     ap.add_argument("--no-forms", action="store_true",
                     help="default workload: skip the reduced-precision / batched vs FP64 time-to-tolerance runs")
     ap.add_argument("--fused", action="store_true",
-                    help="Q1-Q1 RAV fp64 workloads: one fused residual + subdomain-apply kernel per smoothing step")
+                    help="RAV workloads with factored storage (Q1-Q1: fp64): one fused residual + "
+                         "subdomain-apply kernel per smoothing step")
+    ap.add_argument("--apply-staged", type=int, default=None,
+                    help="reduced factored storage: force the staged apply with this many threads per subdomain "
+                         "on the finest level (0: the grouped kernel; default: the set-up tuner's choice)")
     ap.add_argument("--N", type=int, default=None, help="override the grid size (profiling runs)")
     ap.add_argument("--levels", type=int, default=None)
     return ap.parse_args()
@@ -329,6 +334,8 @@ def run_ours(args, W):
     if args.fused:
         sm.fused(True)
     fine = W["nlev"] - 1
+    if args.apply_staged is not None:
+        sm.apply_staged(fine, args.apply_staged)
     n = mg.n()
     b = mg.rhs(W["forcing"])
     x0 = mg.initial_guess()
@@ -404,16 +411,26 @@ def run_ours(args, W):
         flops += 2.0 * mg.counts(fine)["nnz"]
     if W["prec"] in (0, 4):  # fp64 arithmetic: bound by the FP64 pipes, not HBM
         roof = {"bound": "alu", "achieved": flops / (apply_ms / 1e3) / 1e12, "peak": FP64_PEAK_TFLOPS,
-                "unit": "TFLOP/s"}
+                "unit": "TFLOP/s",
+                "peak_note": "derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz"}
+        meas = ctypes_f64()
+        if lib.rav_fp64_fma_rate(ctypes.byref(meas), stream.cuda_stream) == 0:
+            roof["peak_measured"] = meas.value
+            roof["frac_of_measured"] = roof["achieved"] / meas.value
+            roof["peak_measured_note"] = ("rav_fp64_fma_rate: 8 independent FP64 FMA chains per thread, "
+                                          "8 x 256 threads per SM, CUDA events")
     else:
-        peak = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"] if os.path.exists(
-            os.path.join(ROOT, "MEASURED_PEAKS.json")) else 6800.0
-        roof = {"bound": "hbm", "achieved": bytes_alg / (apply_ms / 1e3) / 1e9, "peak": peak, "unit": "GB/s"}
+        mp = os.path.join(ROOT, "MEASURED_PEAKS.json")
+        peak = json.load(open(mp))["hbm_gbs"] if os.path.exists(mp) else 6800.0
+        roof = {"bound": "hbm", "achieved": bytes_alg / (apply_ms / 1e3) / 1e9, "peak": peak, "unit": "GB/s",
+                "peak_note": "of measured (MEASURED_PEAKS.json hbm_gbs)" if os.path.exists(mp) else
+                "of fallback (6.8 TB/s, one earlier GB300 copy measurement)"}
     roof["frac"] = roof["achieved"] / roof["peak"]
     traffic = measured_traffic(f"rav_apply_{args.workload}")
     roof["traffic"] = traffic
-    roof["kernel"] = ("k_fused_q1" if args.fused else "k_rav_apply_q1" if q1 else
-                      "k_rav_apply_fact" if W["prec"] in (0, 5, 6) else "k_rav_apply") + " (fine level)"
+    roof["kernel"] = (("k_fused_q1" if q1 else "k_fused_q2") if args.fused else "k_rav_apply_q1" if q1 else
+                      ("k_rav_apply_staged" if W["prec"] in (5, 6) and sm.apply_staged(fine) else "k_rav_apply_fact")
+                      if W["prec"] in (0, 5, 6) else "k_rav_apply") + " (fine level)"
     if args.fused:
         roof["traffic"] = None
     roof["launch_ms"] = apply_ms
@@ -633,6 +650,42 @@ def run_batch(args, q1=False):
     t0 = time.perf_counter()
     it, ratios, rc = bt.solve(xs, bs, tol=1e-8, maxit=100, raise_on_error=False)
     tsolve = time.perf_counter() - t0
+    # the same batch with the interior subdomains of uniform levels on the tensor cores
+    tensor = None
+    if not q1:
+        nlev_tc = bt.tensor_apply(True)
+        for x, xi in zip(xs, x_init):
+            x.copy_(xi)
+        for _ in range(2):
+            bt.vcycle(xs, bs, 2, 2)
+        torch.cuda.synchronize()
+        clk_tc = clocks_start()
+        e0.record(stream)
+        for _ in range(args.steps):
+            bt.vcycle(xs, bs, 2, 2)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms_tc = e0.elapsed_time(e1)
+        bt.profile(True)
+        for _ in range(kb):
+            bt.vcycle(xs, bs, 2, 2)
+        torch.cuda.synchronize()
+        bd_tc = {}
+        for d in range(int(max(inputs.levels_for(int(N)) for N in sizes))):
+            c, tm = bt.profile_read(d, 0)
+            if c:
+                bd_tc[f"depth {d}"] = round(tm / kb, 3)
+        bt.profile(False)
+        for x, xi in zip(xs, x_init):
+            x.copy_(xi)
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        it_tc, _, rc_tc = bt.solve(xs, bs, tol=1e-8, maxit=100, raise_on_error=False)
+        tsolve_tc = time.perf_counter() - t1
+        tensor = {"levels_using_it": nlev_tc, "ms_per_cycle": ms_tc / args.steps,
+                  "apply_ms_per_cycle_by_depth": bd_tc, "clocks": clocks_stop(clk_tc, 0),
+                  "time_to_tol": {"seconds": tsolve_tc, "max_cycles": int(it_tc.max()), "status": rc_tc}}
+        bt.tensor_apply(False)
     single_ms = 0.0 if args.no_single else single_problem_fp64_ms(mgs, nrhs, omega)
     out = {"metric": "V-cycle DoFs/s", "value": dofs * nrhs * args.steps / (ms / 1e3), "unit": "DoF/s",
            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
@@ -649,7 +702,8 @@ def run_batch(args, q1=False):
                "note": "one-problem, one-RHS V(2,2) cycles with FP64 factored inverses, graphs, summed over "
                        "every problem and RHS"},
            "time_to_tol": {"seconds": tsolve, "max_cycles": int(it.max()), "min_cycles": int(it.min()),
-                           "status": rc, "tol": 1e-8}}
+                           "status": rc, "tol": 1e-8},
+           "tensor_core_shared_inverse_apply": tensor}
     print(json.dumps(out), flush=True)
 
 
@@ -717,9 +771,12 @@ def forms_vs_fp64(nprob=256, nrhs=8):
     stream = torch.cuda.current_stream()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     clk = clocks_start()
-    for name, prec in (("batched-f32-rows", R.F32), ("batched-f64-rows", R.F64_ROWS)):
+    for name, prec in (("batched-f32-rows", R.F32), ("batched-f32-rows-tensor-core", R.F32),
+                       ("batched-f64-rows", R.F64_ROWS)):
         sms = [R.Smoother(mg, R.RAV, prec, 0.5) for mg in mgs]
         bt = R.Batch(mgs, sms, nrhs)
+        if name.endswith("tensor-core"):
+            bt.tensor_apply(True)
         for _ in range(2):
             bt.vcycle(xs, bs, 2, 2)
         torch.cuda.synchronize()
@@ -745,6 +802,7 @@ def forms_vs_fp64(nprob=256, nrhs=8):
     row["clocks"] = clocks_stop(clk, torch.cuda.current_device())
     row["setup_and_run_s"] = time.perf_counter() - t0
     f32, f64 = row["batched-f32-rows"], row["batched-f64-rows"]
+    row["tensor_core_vs_cuda_core"] = f32["ms_per_cycle"] / row["batched-f32-rows-tensor-core"]["ms_per_cycle"]
     row["speedup"] = {"precision (batched f64 / batched f32, time to tol)": f64["seconds_to_tol"] /
                       f32["seconds_to_tol"],
                       "batching (single-problem f64 / batched f64, per cycle)":
@@ -916,9 +974,25 @@ def run_learned(args, q1=False):
         sm = R.Smoother(mg, R.RAV, R.F64, omega)
         b = mg.rhs(R.F_SINKER)
         row = {}
-        for mode in ("fixed", "learned"):
+        # baseline: the best fixed damping of a sweep (FGMRES(30) iterations and seconds)
+        sweep = {}
+        for om in (0.3, 0.4, 0.5, 0.6, 0.7, 0.8, 0.9):
+            sw = R.Smoother(mg, R.RAV, R.F64, om)
+            x = mg.initial_guess()
+            mg.solve(sw, x, b, tol=1e-8, maxit=1, outer=1, raise_on_error=False)
+            x = mg.initial_guess()
+            torch.cuda.synchronize()
+            t1 = time.perf_counter()
+            it, hist, rc = mg.solve(sw, x, b, tol=1e-8, maxit=200, outer=1, raise_on_error=False)
+            torch.cuda.synchronize()
+            sweep[str(om)] = {"iterations": it, "status": rc, "seconds": time.perf_counter() - t1}
+            del sw
+        row["fixed-sweep-fgmres"] = sweep
+        for mode in ("fixed", "learned", "learned-per-subdomain"):
             if mode == "learned":
                 learned.install(sm, P, shrink=0.0)
+            elif mode == "learned-per-subdomain":
+                learned.install(sm, P, shrink=1.0)
             for outer, oname in ((1, "fgmres"), (0, "stationary")):
                 x = mg.initial_guess()
                 mg.solve(sm, x, b, tol=1e-8, maxit=1, outer=outer, raise_on_error=False)

@@ -245,15 +245,39 @@ void vanka_destroy(rav_smoother* sm);
 int rav_set_apply_split(rav_smoother* sm, int level, int split, rav_stream stream);
 int rav_get_apply_split(const rav_smoother* sm, int level);
 
-/* Fused smoothing (Q1-Q1, RAV, RAV_F64 only; RAV_ERR_ARG otherwise): with
- * enable != 0 every smoothing step of this smoother runs as one kernel that
- * computes the residual of Eq. 10 on each tile's subdomain boxes (tiles of
- * 16 x 16 or 8 x 8 x 4 vertices plus a one-vertex halo, kept in shared
- * memory) and applies the subdomain corrections of Eq. 13, reading one
- * iterate buffer and writing another (the library allocates the second one per
- * level); 0 returns to the residual + apply kernels.  Results agree with the
- * two-kernel path to rounding (the fused residual sums the assembled rows).
- * Synchronises the device and drops this smoother's captured cycles. */
+/* Staged apply of the reduced factored storage (RAV_F32_FACT, RAV_BF16_FACT;
+ * Q2-Q1) on level l: the same Eq. 13 step computed by thread blocks that
+ * each copy the fp32 residual of their tile of subdomain boxes (tiles of
+ * vertices, chosen per level) into shared memory once, then stream the stored
+ * values of their subdomains in per-thread chunks (the 2^d owned rows of
+ * K_i^{-1} and w at one box node) with threads_per_subdomain threads per
+ * subdomain (1 or 2 in 2-D, 2 or 4 in 3-D; partial sums meet by shuffles).
+ * 0 returns to the grouped kernel of rav_set_apply_split.  The chunks are a
+ * second copy of the stored values, built from the grouped storage (same
+ * rounded values) when set; vanka_setup times both kernels on every level and
+ * keeps the staged one where it is 3 % faster.  Setting it synchronises the
+ * stream and drops this smoother's captured cycles.  Results differ from the
+ * grouped kernel only in the order of the fp32 additions.  RAV_ERR_ARG for
+ * other values or storage (0 is accepted everywhere).  rav_get_apply_staged
+ * returns the current value (or RAV_ERR_ARG). */
+int rav_set_apply_staged(rav_smoother* sm, int level, int threads_per_subdomain, rav_stream stream);
+int rav_get_apply_staged(const rav_smoother* sm, int level);
+
+/* Fused smoothing (RAV only; on Q1-Q1 with RAV_F64 storage, on Q2-Q1 with
+ * the factored storages RAV_F64, RAV_F32_FACT, RAV_BF16_FACT; RAV_ERR_ARG
+ * otherwise): with enable != 0 every smoothing step of this smoother runs as
+ * one kernel that computes the residual of Eq. 10 on each tile's subdomain
+ * boxes (Q1-Q1: tiles of 16 x 16 or 8 x 8 x 4 vertices plus a one-vertex
+ * halo; Q2-Q1: tiles of 16 x 16 or 8 x 8 x 4 vertices, their boxes reaching
+ * two Q2 nodes past the tile, kept in shared memory in the accumulation type
+ * of the storage) and applies the subdomain corrections of Eq. 13, reading
+ * one iterate buffer and writing another (the library allocates the second
+ * one per level); 0 returns to the residual + apply kernels.  On Q2-Q1 the
+ * stored rows are regrouped for one thread per owned node (as
+ * rav_set_apply_split(sm, l, 1)).  Results agree with the two-kernel path to
+ * rounding (the fused residual sums the rows in the order of the residual
+ * kernel with one thread per row).  Synchronises the device and drops this
+ * smoother's captured cycles. */
 int rav_set_fused_smoothing(rav_smoother* sm, int enable);
 
 /* Replaces the damping of level l's subdomains by w_dev[n_p(l)] (fp32, device),
@@ -401,6 +425,28 @@ int batch_setup(rav_mg* const* mgs, rav_smoother* const* sms, int nprob, int nrh
 void batch_destroy(rav_batch* bt);
 /* out[0] = threads per block of the residual kernel, out[1] = of the apply kernel. */
 int batch_get_tuning(const rav_batch* bt, int out[2]);
+/* Shared-inverse apply on the tensor cores (2-D Q2-Q1 batches with RAV_F32
+ * rows and 8 right-hand sides; RAV_ERR_ARG otherwise).  On a uniform grid
+ * with constant viscosity every interior subdomain of a level (vertex 2 .. N-2
+ * on each axis) has the same local system, hence the same owned rows of
+ * L_i^{-1} (Eq. 13).  With enable != 0 the call checks each (problem, level)
+ * of the batch: where every interior subdomain's stored rows equal those of
+ * the subdomain at vertex (2, 2) to within two units in the last place of
+ * their largest entry, that level's interior subdomains are applied as one
+ * small GEMM per 16 subdomains x 8 right-hand sides on the tensor cores
+ * (tcgen05.mma kind::tf32, the fp32 operands split into tf32 high and low
+ * parts, three products, fp32 accumulation: about 2^-20 relative error per
+ * product), reading one copy of the rows instead of one per subdomain; the
+ * boundary subdomains, and every subdomain of the other levels, stay on the
+ * fp32 CUDA-core apply.  Synchronises the stream; drops the captured cycle.
+ * Results differ from the CUDA-core apply by the rounding of the split
+ * operands and the order of additions.  A tensor-core wait that gives up is
+ * reported by solve_batched as RAV_ERR_TIMEOUT.  enable = 0 returns to the
+ * CUDA-core apply.  batch_tensor_apply_levels returns how many (problem,
+ * level) pairs use it (or RAV_ERR_ARG). */
+int batch_set_tensor_apply(rav_batch* bt, int enable, rav_stream stream);
+int batch_tensor_apply_levels(const rav_batch* bt);
+
 /* Timing hook of the batch, with the kernel classes of rav_profile_enable.
  * While enabled (on != 0) batch_vcycle and solve_batched launch phase by phase
  * instead of replaying the graph, and every phase launch is bracketed by CUDA
@@ -439,6 +485,13 @@ int rav_profile_read(rav_mg* mg, int level, int kind, int64_t* launches, double*
  * applies, transfers, coarse solves, Krylov vector updates) has launched in
  * this process so far; set-up kernels are not counted. */
 int64_t rav_kernel_launches(void);
+
+/* Measured FP64 fused multiply-add throughput of the current device in
+ * TFLOP/s (2 flops per FMA), the denominator of the fp64-bound kernels'
+ * rooflines: 10 timed launches (CUDA events on stream) of a kernel that runs 8
+ * independent FMA chains of 4,096 steps in each of 256 threads x 8 blocks per
+ * SM.  Synchronises the stream.  The paper has no counterpart. */
+int rav_fp64_fma_rate(double* tflops_host, rav_stream stream);
 
 const char* rav_strerror(int code);
 

@@ -89,6 +89,7 @@ def _load():
             "orc_mlp_forward": (None, [P, P, ll, P]),
             "orc_mlp_loss_grad": (d, [P, P, P, ll, P]),
             "orc_set_threads": (i, [i]),
+            "orc_patch_features": (None, [P, i, P]),
         }
         for name, (res, args) in sig.items():
             f = getattr(lib, name)
@@ -257,6 +258,12 @@ class Oracle:
         _lib.orc_get_inverse(self.h, lev, p, int(quantised), _ptr(out), _ptr(sc))
         out = out.reshape(-1, ni)
         return (out, sc) if quantised else out
+
+    def patch_features(self, lev):
+        """The 8 learned-damping features of every subdomain of level lev, (n_p, 8)."""
+        out = np.zeros((self.count(lev, 1), 8))
+        _lib.orc_patch_features(self.h, lev, _ptr(out))
+        return out
 
     def labels(self, lev, r, omega=None, fallback=0.5):
         """Coordinate line-search damping per subdomain for residual r given the

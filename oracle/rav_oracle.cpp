@@ -1391,6 +1391,83 @@ int orc_fgmres(void* h, double* x, const double* b, double tol, int maxit, int r
 // is omega*_i = omega_i + <r', L c_i> / <L c_i, L c_i> with r' = r - L s,
 // clipped to [0, 1.5] (omega_i when L c_i = 0).  Norms over free rows; L c_i is
 // formed with the full sparse L.  omega: current weights (null: `fallback`).
+// Features of the learned per-subdomain damping (not in the paper; they
+// describe what the local system of subdomain i sees), 8 per subdomain p of
+// level l, written to out[8 p + k]:
+//   0  log10(eta_max / eta_min) over the 3^d Gauss points of the cells around vertex p
+//   1  mean of log10 eta over those points
+//   2  log10 of the largest cell aspect ratio (longest over shortest side) there
+//   3  log10 of the smallest one
+//   4  l / (levels - 1)  (0 for a single level)
+//   5  (d * free box nodes + 1) / (d * box nodes + 1): the subdomain's size
+//      over the box's (box nodes: 5^d on Q2-Q1, 3^d on Q1-Q1; free = inside
+//      the domain and not on its boundary)
+//   6  boundary box nodes / box nodes inside the domain
+//   7  log10 of the mean cell diagonal around vertex p
+void orc_patch_features(void* h, int l, double* out) {
+  const Oracle& O = *(const Oracle*)h;
+  const Level& L = O.lev[l];
+  const int d = L.dim, nlev = (int)O.lev.size();
+  for (int64_t p = 0; p < L.n_p; ++p) {
+    int64_t v[3] = {0, 0, 0};
+    vert_of(L, p, v);
+    double emin = 1e300, emax = 0.0, lsum = 0.0, amax = 0.0, amin = 1e300, diag = 0.0;
+    int nq = 0, ncell = 0;
+    int64_t cl[3][2];
+    int cnt[3] = {1, 1, 1};
+    for (int a = 0; a < d; ++a) cnt[a] = cells_of_vertex(v[a], L.N, cl[a]);
+    tensor_loop(d, cnt, [&](const int* k) {
+      double lo[3] = {0, 0, 0}, hh[3] = {0, 0, 0}, hmax = 0.0, hmin = 1e300, d2 = 0.0;
+      for (int a = 0; a < d; ++a) {
+        lo[a] = L.xv[a][cl[a][k[a]]];
+        hh[a] = L.xv[a][cl[a][k[a]] + 1] - lo[a];
+        hmax = std::max(hmax, hh[a]);
+        hmin = std::min(hmin, hh[a]);
+        d2 += hh[a] * hh[a];
+      }
+      amax = std::max(amax, hmax / hmin);
+      amin = std::min(amin, hmax / hmin);
+      diag += std::sqrt(d2);
+      ++ncell;
+      int g3[3] = {3, 3, 3};
+      tensor_loop(d, g3, [&](const int* t) {
+        double x[3] = {0, 0, 0};
+        for (int a = 0; a < d; ++a) x[a] = lo[a] + hh[a] * kGaussX[t[a]];
+        const double eta = viscosity(O.P, x);
+        emin = std::min(emin, eta);
+        emax = std::max(emax, eta);
+        lsum += std::log10(eta);
+        ++nq;
+      });
+    });
+    // box nodes J = q v - q + a, a = 0 .. 2q per axis
+    int ext[3] = {1, 1, 1};
+    for (int a = 0; a < d; ++a) ext[a] = 2 * L.q + 1;
+    int nbox = 0, nin = 0, nbnd = 0, nfree = 0;
+    tensor_loop(d, ext, [&](const int* a) {
+      bool in = true, bnd = false;
+      for (int ax = 0; ax < d; ++ax) {
+        const int64_t J = L.q * v[ax] - L.q + a[ax];
+        in = in && J >= 0 && J <= L.M - 1;
+        bnd = bnd || J == 0 || J == L.M - 1;
+      }
+      ++nbox;
+      nin += in;
+      nbnd += in && bnd;
+      nfree += in && !bnd;
+    });
+    double* f = out + 8 * p;
+    f[0] = std::log10(emax / emin);
+    f[1] = lsum / nq;
+    f[2] = std::log10(amax);
+    f[3] = std::log10(amin);
+    f[4] = nlev > 1 ? (double)l / (double)(nlev - 1) : 0.0;
+    f[5] = (double)(d * nfree + 1) / (double)(d * nbox + 1);
+    f[6] = nin ? (double)nbnd / (double)nin : 0.0;
+    f[7] = std::log10(diag / ncell);
+  }
+}
+
 void orc_labels(void* h, int l, const double* r, const double* omega, double fallback, double* out) {
   const Level& L = ((Oracle*)h)->lev[l];
   const int64_t np = (int64_t)L.poff.size() - 1;

@@ -182,6 +182,16 @@ class Batch:
         check(_capi.load().batch_get_tuning(self.h, out), "batch_get_tuning")
         return {"residual_threads": out[0], "apply_threads": out[1]}
 
+    def tensor_apply(self, enable=True, stream=None):
+        """Shared-inverse apply of interior subdomains on the tensor cores
+        (batch_set_tensor_apply); returns how many (problem, level) pairs use it."""
+        lib = _capi.load()
+        check(lib.batch_set_tensor_apply(self.h, int(bool(enable)), _stream(stream)), "batch_set_tensor_apply")
+        n = lib.batch_tensor_apply_levels(self.h)
+        if n < 0:
+            raise RavError(n, "batch_tensor_apply_levels")
+        return n
+
     def profile(self, on=True):
         """Phase-by-phase CUDA-event timing of batched cycles (batch_profile_enable)."""
         check(_capi.load().batch_profile_enable(self.h, int(on)), "batch_profile_enable")
@@ -247,6 +257,18 @@ class Smoother:
         k = lib.rav_get_apply_split(self.h, level)
         if k < 0:
             raise RavError(k, "rav_get_apply_split")
+        return k
+
+    def apply_staged(self, level, threads_per_subdomain=None, stream=None):
+        """Threads per subdomain of the staged reduced-precision apply on
+        `level` (0: the grouped kernel); sets it when given."""
+        lib = _capi.load()
+        if threads_per_subdomain is not None:
+            check(lib.rav_set_apply_staged(self.h, level, int(threads_per_subdomain), _stream(stream)),
+                  "rav_set_apply_staged")
+        k = lib.rav_get_apply_staged(self.h, level)
+        if k < 0:
+            raise RavError(k, "rav_get_apply_staged")
         return k
 
     def fused(self, enable=True):

@@ -52,6 +52,11 @@ _SIGS = {
     "rav_set_patch_omega": (I32, [P, I32, P, P]),
     "rav_set_apply_split": (I32, [P, I32, I32, P]),
     "rav_get_apply_split": (I32, [P, I32]),
+    "rav_set_apply_staged": (I32, [P, I32, I32, P]),
+    "batch_set_tensor_apply": (I32, [P, I32, P]),
+    "rav_fp64_fma_rate": (I32, [ctypes.POINTER(F64), P]),
+    "batch_tensor_apply_levels": (I32, [P]),
+    "rav_get_apply_staged": (I32, [P, I32]),
     "rav_set_fused_smoothing": (I32, [P, I32]),
     "rav_get_patch_counts": (I32, [P, I32, I64P]),
     "rav_get_patches": (I32, [P, I32, P, P, P, P]),

@@ -25,6 +25,7 @@
 
 #include "box.cuh"
 #include "common.cuh"
+#include "tcgen05.cuh"
 
 namespace rav {
 
@@ -50,6 +51,11 @@ struct BLevel {
   float* bc32;      // coarser level's r32: its b rounded, written by the restriction
   const double* cinv;  // bordered coarse inverse (coarsest level only)
   int problem;
+  // 2-D Q2-Q1, fp32 rows, 8 RHS: the owned rows shared by every interior
+  // subdomain of this level (vertices 2 .. N-2 per axis), split into tf32 high
+  // and low parts in the tensor-core operand layout (2 x 4096 bytes), or null
+  // when the level's interior subdomains do not share them
+  const float* gtc;
 };
 
 __device__ __forceinline__ int find_entry(const int64_t* __restrict__ first, int ne, int64_t blk) {
@@ -184,6 +190,8 @@ __global__ void kb_apply(const BLevel* __restrict__ L, const int64_t* __restrict
   const int h = (int)(u % NCH);
   int v[3] = {0, 0, 0};
   vertex_of_t<D>(g, p, v);
+  // interior subdomains of a level with shared rows go through kb_apply_tc
+  if (D == 2 && lv.gtc && v[0] >= 2 && v[0] <= g.N - 2 && v[1] >= 2 && v[1] <= g.N - 2) return;
   const int M = (int)g.M;
   int alo[3] = {0, 0, 0}, ahi[3] = {0, 0, 0};
 #pragma unroll
@@ -261,6 +269,249 @@ __global__ void kb_apply(const BLevel* __restrict__ L, const int64_t* __restrict
       for (int j = 0; j < NR; ++j) lv.x[dof * NR + j] += om * (double)acc[i][j];
     }
   }
+}
+
+// ---- shared-inverse apply on the tensor cores ----------------------------------
+// On a uniform grid with constant viscosity every interior subdomain of a level
+// (vertices 2 .. N-2 per axis: the whole 5 x 5 node box free) has the same local
+// system L_i, so the same owned rows G = (L_i^{-1})_{owned,:} (9 x 51 in 2-D,
+// Eq. 13 with the restricted rows of Sec. 4.3).  For 16 such subdomains and the
+// 8 right-hand sides of each, the restricted local solves are one small GEMM
+//   Y[(16 x 8) x 9] = Rloc[(16 x 8) x 51] G^T,
+// rows = (subdomain, right-hand side), Rloc row = the gathered residual box
+// (Sec. 3's restriction R_i).  It runs as tcgen05.mma kind::tf32, M = 128,
+// N = 16 (9 used), K = 64 (51 used), fp32 accumulation in tensor memory, in
+// three passes hi*hi + hi*lo + lo*hi of operands split into tf32 parts
+// (x = hi + lo, hi = x with the low 13 mantissa bits cleared), which keeps
+// each product's relative error near 2^-20 instead of tf32's 2^-11.
+// Per tile: the 256 threads of a block store Rloc, gathered from the fp32
+// residual into registers while the previous tile's MMAs ran, into shared
+// memory (core matrices of 8 rows x 16 bytes, K-major, no swizzle; one row
+// group = one subdomain's 8 right-hand sides; a 16-byte pad between groups
+// spreads the stores over all banks), one thread issues the 24 MMAs and
+// commits them to an mbarrier, the threads load the next tile's rows, then
+// read the 128 x 16 accumulator from tensor memory (two warps per lane
+// quarter, five owned rows each) and add omega_i y to the owned DoFs of x
+// (restricted scatter, disjoint per subdomain, no atomics).  Waits on the
+// mbarrier are bounded: a wait that gives up sets *err and the block stops
+// after a second bounded wait for its MMAs, freeing its tensor memory.
+// Boundary subdomains of the same level stay on kb_apply.
+constexpr int kTcP = 16;                       // subdomains per tile (x 8 RHS = M = 128)
+constexpr int kTcSboA = 16 * 128 + 16;         // bytes between row groups of Rloc
+constexpr int kTcABytes = kTcP * kTcSboA;      // 33,024
+constexpr int kTcBBytes = 2 * 16 * 128;        // 16 x 64 tf32, row groups 2048 bytes apart
+constexpr int kTcSmem = 2 * kTcABytes + 2 * kTcBBytes + 16;
+constexpr long kTcWaitProbes = 1L << 22;
+
+__device__ __forceinline__ float tf32_hi(float v) { return __uint_as_float(__float_as_uint(v) & 0xffffe000u); }
+
+__device__ __forceinline__ bool tc_wait(uint64_t* bar, uint32_t parity) {
+  for (long i = 0; i < kTcWaitProbes; ++i)
+    if (tc::mbar_try_wait(bar, parity)) return true;
+  return false;
+}
+
+// Residual rows of one tile gathered into registers: thread task i (of 4)
+// covers subdomain pl = 8 (w & 1) + lane / 4 and box position
+// kk = 4 (w / 2) + lane % 4, w = warp + 8 i; 8 right-hand sides each.
+struct TcGather {
+  float4 v[4][2];
+};
+__device__ __forceinline__ void tc_gather_load(const BLevel& lv, int64_t t0, int warp, int lane, TcGather& gr) {
+  const Geo& g = lv.g;
+  const int ni = g.N - 3;
+  const int64_t nint = (int64_t)ni * ni;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int w = warp + 8 * i;
+    const int pl = 8 * (w & 1) + (lane >> 2);
+    const int kk = 4 * (w >> 1) + (lane & 3);
+    const int64_t idx = t0 + pl;
+    gr.v[i][0] = gr.v[i][1] = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (idx < nint && kk <= 50) {
+      const int vx = 2 + (int)(idx % ni), vy = 2 + (int)(idx / ni);
+      int64_t row;
+      if (kk == 50) {
+        row = g.n_u + vx + (int64_t)(g.N + 1) * vy;
+      } else {
+        const int a = kk >> 1;
+        row = 2 * ((2 * vx - 2 + a % 5) + g.M * (2 * vy - 2 + a / 5)) + (kk & 1);
+      }
+      const float4* src = reinterpret_cast<const float4*>(lv.r32 + row * 8);
+      gr.v[i][0] = src[0];
+      gr.v[i][1] = src[1];
+    }
+  }
+}
+__device__ __forceinline__ void tc_gather_store(const TcGather& gr, int warp, int lane, uint8_t* a_hi, uint8_t* a_lo) {
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int w = warp + 8 * i;
+    const int pl = 8 * (w & 1) + (lane >> 2);
+    const int kk = 4 * (w >> 1) + (lane & 3);
+    const int off = pl * kTcSboA + (kk >> 2) * 128 + (kk & 3) * 4;
+    const float v[8] = {gr.v[i][0].x, gr.v[i][0].y, gr.v[i][0].z, gr.v[i][0].w,
+                        gr.v[i][1].x, gr.v[i][1].y, gr.v[i][1].z, gr.v[i][1].w};
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const float hi = tf32_hi(v[j]);
+      *reinterpret_cast<float*>(a_hi + off + 16 * j) = hi;
+      *reinterpret_cast<float*>(a_lo + off + 16 * j) = v[j] - hi;
+    }
+  }
+}
+
+// 8 warps: all gather; thread 0 issues the MMAs; warps w and w + 4 read the
+// same accumulator rows (lane quarter w % 4) and write owned rows 0-4 and 5-8.
+// The next tile's residual rows are loaded into registers while the MMAs of
+// the current one run.
+__global__ void __launch_bounds__(256) kb_apply_tc(const BLevel* __restrict__ L, const int64_t* __restrict__ first,
+                                                   int ne, int* __restrict__ err) {
+  extern __shared__ __align__(128) uint8_t tsm[];
+  uint8_t* a_hi = tsm;
+  uint8_t* a_lo = tsm + kTcABytes;
+  uint8_t* b_hi = tsm + 2 * kTcABytes;
+  uint8_t* b_lo = b_hi + kTcBBytes;
+  uint64_t* bar = reinterpret_cast<uint64_t*>(b_lo + kTcBBytes);
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(bar + 1);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  if (warp == 0) tc::tmem_alloc(tslot, 32);
+  if (tid == 0) {
+    tc::mbar_init(bar, 1);
+    tc::mbar_init_fence();
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t tmem = *tslot;
+  // contiguous tile range per block (neighbouring tiles share residual rows in L2)
+  const int64_t ntiles = first[ne];
+  const int64_t per = (ntiles + gridDim.x - 1) / gridDim.x;
+  const int64_t t_begin = blockIdx.x * per, t_end = t_begin + per < ntiles ? t_begin + per : ntiles;
+  const uint32_t idesc = tc::idesc_tf32(128, 16);
+  uint32_t phase = 0;
+  int cur = -1;
+  bool failed = false;
+  TcGather gr;
+  int e = t_begin < t_end ? find_entry(first, ne, t_begin) : 0;
+  if (t_begin < t_end) tc_gather_load(L[e], (t_begin - first[e]) * kTcP, warp, lane, gr);
+  for (int64_t tile = t_begin; tile < t_end; ++tile) {
+    const BLevel& lv = L[e];
+    const Geo& g = lv.g;
+    if (e != cur) {  // this level's shared rows, both tf32 parts
+      const uint4* src = reinterpret_cast<const uint4*>(lv.gtc);
+      uint4* dst = reinterpret_cast<uint4*>(b_hi);
+      for (int i = tid; i < 2 * kTcBBytes / 16; i += 256) dst[i] = src[i];
+      cur = e;
+    }
+    const int ni = g.N - 3;  // interior vertices per axis
+    const int64_t nint = (int64_t)ni * ni;
+    const int64_t t0 = (tile - first[e]) * kTcP;
+    tc_gather_store(gr, warp, lane, a_hi, a_lo);
+    tc::fence_async_smem();
+    __syncthreads();
+    if (tid == 0) {
+      tc::fence_after_sync();
+      const uint32_t ah = tc::smem_addr(a_hi), al = tc::smem_addr(a_lo);
+      const uint32_t bh = tc::smem_addr(b_hi), bl = tc::smem_addr(b_lo);
+#pragma unroll
+      for (int k = 0; k < 8; ++k) {  // K = 8 tf32 per MMA: two 16-byte core-matrix columns
+        const uint64_t dah = tc::smem_desc(ah + 256 * k, 128, kTcSboA);
+        const uint64_t dal = tc::smem_desc(al + 256 * k, 128, kTcSboA);
+        const uint64_t dbh = tc::smem_desc(bh + 256 * k, 128, 2048);
+        const uint64_t dbl = tc::smem_desc(bl + 256 * k, 128, 2048);
+        tc::mma_tf32(tmem, dah, dbh, idesc, k > 0 ? 1u : 0u);
+        tc::mma_tf32(tmem, dah, dbl, idesc, 1u);
+        tc::mma_tf32(tmem, dal, dbh, idesc, 1u);
+      }
+      tc::mma_commit(bar);
+    }
+    // the next tile's residual rows, while the tensor cores work
+    const int e_next = tile + 1 < t_end ? find_entry(first, ne, tile + 1) : e;
+    if (tile + 1 < t_end) tc_gather_load(L[e_next], (tile + 1 - first[e_next]) * kTcP, warp, lane, gr);
+    const bool done = tc_wait(bar, phase);
+    failed = __syncthreads_or(!done) != 0;
+    if (failed) break;
+    phase ^= 1u;
+    tc::fence_after_sync();
+    float y[16];
+    tc::tmem_ld16(tmem + ((uint32_t)((warp & 3) * 32) << 16), y);
+    const int m = (warp & 3) * 32 + lane;  // accumulator row: subdomain m / 8, right-hand side m % 8
+    const int64_t idx = t0 + (m >> 3);
+    const int rhs = m & 7;
+    if (idx < nint) {
+      const int vx = 2 + (int)(idx % ni), vy = 2 + (int)(idx / ni);
+      const int64_t p = vx + (int64_t)(g.N + 1) * vy;
+      const double om = lv.omega[p];
+      const int j0 = warp < 4 ? 0 : 5, j1 = warp < 4 ? 5 : 9;
+      double* xp[5];
+      double xv[5];
+#pragma unroll
+      for (int jj = 0; jj < 5; ++jj) {  // owned row j: node 2v + (q & 1, q >> 1), q = j / 2, component j % 2
+        const int j = j0 + jj;
+        xp[jj] = nullptr;
+        if (j < j1) {
+          const int q = j >> 1;
+          const int64_t dof =
+              j == 8 ? g.n_u + p : 2 * ((2 * vx + (q & 1)) + g.M * (2 * vy + (q >> 1))) + (j & 1);
+          xp[jj] = lv.x + dof * 8 + rhs;
+          xv[jj] = *xp[jj];
+        }
+      }
+#pragma unroll
+      for (int jj = 0; jj < 5; ++jj)
+        if (xp[jj]) *xp[jj] = xv[jj] + om * (double)y[j0 + jj];
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    e = e_next;
+  }
+  if (failed) {
+    if (tid == 0) atomicExch(err, 1);
+    tc_wait(bar, phase);  // the MMAs of the abandoned tile, bounded again
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  if (warp == 0) {
+    tc::fence_after_sync();
+    tc::tmem_dealloc(tmem, 32);
+  }
+}
+
+// Checks whether every interior subdomain's stored fp32 rows (2-D, one unit
+// per subdomain: element (u, j, k) at ((u / 32) NC + k) RB + j) 32 + u % 32)
+// equal those of the subdomain at vertex (2, 2) within tol; *bad = 1 if not.
+__global__ void kb_shared_check(Geo g, const float* __restrict__ inv, float tol, int* __restrict__ bad) {
+  using B = BoxT<2>;
+  constexpr int NC = B::NC, RB = B::RB;
+  const int ni = g.N - 3;
+  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e >= (int64_t)ni * ni * RB * NC) return;
+  const int64_t idx = e / (RB * NC);
+  const int j = (int)((e / NC) % RB), k = (int)(e % NC);
+  const int64_t u = (2 + idx % ni) + (int64_t)(g.N + 1) * (2 + idx / ni);
+  const int64_t u0 = 2 + (int64_t)(g.N + 1) * 2;
+  const float a = inv[((u >> 5) * NC + k) * RB * 32 + j * 32 + (u & 31)];
+  const float r = inv[((u0 >> 5) * NC + k) * RB * 32 + j * 32 + (u0 & 31)];
+  if (!(fabsf(a - r) <= tol)) atomicExch(bad, 1);
+}
+
+// Shared rows of the subdomain at vertex (2, 2) as the B operand: element
+// (n, k) (owned row n < 9, box position k < 51; zero elsewhere) of the 16 x 64
+// matrix at (n / 8) 2048 + (k / 4) 128 + (n % 8) 16 + (k % 4) 4 bytes, tf32
+// high part in the first 4096 bytes, low part in the next.
+__global__ void kb_shared_build(Geo g, const float* __restrict__ inv, float* __restrict__ out) {
+  using B = BoxT<2>;
+  constexpr int NC = B::NC, RB = B::RB;
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= 16 * 64) return;
+  const int n = e / 64, k = e % 64;
+  const int64_t u0 = 2 + (int64_t)(g.N + 1) * 2;
+  const float v = (n < RB && k < NC) ? inv[((u0 >> 5) * NC + k) * RB * 32 + n * 32 + (u0 & 31)] : 0.f;
+  const float hi = tf32_hi(v);
+  const int off = ((n >> 3) * 2048 + (k >> 2) * 128 + (n & 7) * 16 + (k & 3) * 4) / 4;
+  out[off] = hi;
+  out[1024 + off] = v - hi;
 }
 
 // Restriction into the coarser level (same threads per coarse DoF and the same
@@ -674,7 +925,7 @@ struct BPhase {
   BLevel* L = nullptr;      // device
   int64_t* first = nullptr; // device, ne + 1
   int* prob = nullptr;      // device, ne (norm phases)
-  int ne = 0;
+  int ne = 0, cap = 0;  // entries, allocated descriptor slots
   int64_t blocks = 0;
   int threads = 0;
   std::vector<int> entries;  // host: indices into rav_batch::lv
@@ -693,6 +944,12 @@ struct rav_batch {
   int tpb_res = 256, tpb_apply = 128;
   // phases per depth d (0 = finest)
   std::vector<BPhase> res_smooth, apply, res_last, restrict_, prolong, coarse_mask, coarse_gemv;
+  // shared-inverse tensor-core apply (kb_apply_tc): per depth, the entries
+  // whose interior subdomains share their rows; blocks = tiles of 16
+  bool use_tc = false;
+  std::vector<BPhase> tc_apply;
+  std::vector<float*> gtc_bufs;  // per lv entry, null where not shared
+  int* tc_err = nullptr;         // set by a tensor-core block whose wait gave up
   BPhase fine_res;  // depth-0 residual with norms
   double* part = nullptr;
   double* norms = nullptr;   // device, nprob * nrhs
@@ -789,10 +1046,17 @@ static int upload_phase(rav_batch* bt, BPhase& ph, const std::vector<int>& entri
     first[i + 1] = first[i] + blocks_of(h[i], threads);
   }
   ph.blocks = first[ph.ne];
-  if (!ph.L) {
+  if (ph.ne > ph.cap) {
+    cudaFree(ph.L);
+    cudaFree(ph.first);
+    cudaFree(ph.prob);
+    ph.L = nullptr;
+    ph.first = nullptr;
+    ph.prob = nullptr;
     RAV_CUDA(cudaMalloc(&ph.L, sizeof(BLevel) * ph.ne));
     RAV_CUDA(cudaMalloc(&ph.first, sizeof(int64_t) * (ph.ne + 1)));
     RAV_CUDA(cudaMalloc(&ph.prob, sizeof(int) * ph.ne));
+    ph.cap = ph.ne;
   }
   RAV_CUDA(cudaMemcpy(ph.L, h.data(), sizeof(BLevel) * ph.ne, cudaMemcpyHostToDevice));
   RAV_CUDA(cudaMemcpy(ph.first, first.data(), sizeof(int64_t) * (ph.ne + 1), cudaMemcpyHostToDevice));
@@ -810,6 +1074,10 @@ static int64_t blk_prolong(const BLevel& b, int t) {
   return ((b.g.q == 1 ? 0 : b.g.nnode) + b.g.n_p + t - 1) / t;
 }
 static int64_t blk_mask(const BLevel& b, int t) { return (b.g.n + t - 1) / t; }
+static int64_t blk_tc(const BLevel& b, int) {
+  const int64_t ni = b.g.N - 3;
+  return (ni * ni + kTcP - 1) / kTcP;
+}
 static int64_t blk_gemv(const BLevel& b, int t) { return (b.g.n + t / 32 - 1) / (t / 32); }
 
 // ---- launches --------------------------------------------------------------
@@ -844,6 +1112,11 @@ static int batch_cycle(rav_batch* bt, int nu1, int nu2, cudaStream_t s) {
   auto apply = [&](int d, int use_b) {
     ev = bprof_begin(bt, d, PROF_APPLY, s);
     launch_apply<D, NR>(bt, bt->apply[d], use_b, s);
+    if (bt->use_tc && d < (int)bt->tc_apply.size() && bt->tc_apply[d].ne) {
+      const BPhase& tp = bt->tc_apply[d];
+      const unsigned grid = (unsigned)std::min<int64_t>(tp.blocks, 152 * 2);
+      kb_apply_tc<<<grid, 256, kTcSmem, s>>>(tp.L, tp.first, tp.ne, bt->tc_err);
+    }
     bprof_end(bt, ev, s);
   };
   // down
@@ -911,7 +1184,10 @@ static int fine_norms(rav_batch* bt, cudaStream_t s) {
   note_launch(2);
   RAV_CUDA(cudaGetLastError());
   RAV_CUDA(cudaMemcpyAsync(bt->norms_h, bt->norms, sizeof(double) * bt->nprob * bt->nrhs, cudaMemcpyDeviceToHost, s));
+  if (bt->use_tc)  // the tensor-core apply's bounded waits report here
+    RAV_CUDA(cudaMemcpyAsync(bt->norms_h + bt->nprob * bt->nrhs, bt->tc_err, sizeof(int), cudaMemcpyDeviceToHost, s));
   RAV_CUDA(cudaStreamSynchronize(s));
+  if (bt->use_tc && *reinterpret_cast<const int*>(bt->norms_h + bt->nprob * bt->nrhs)) return RAV_ERR_TIMEOUT;
   return RAV_OK;
 }
 
@@ -940,6 +1216,13 @@ static int build_phases(rav_batch* bt) {
     RAV_TRY(upload_phase(bt, bt->coarse_mask[d], coarse, 256, blk_mask));
     RAV_TRY(upload_phase(bt, bt->coarse_gemv[d], coarse, 256, blk_gemv));
   }
+  bt->tc_apply.resize(Dm);
+  for (int d = 0; d < Dm; ++d) {
+    std::vector<int> shared;
+    for (int p = 0; p < bt->nprob; ++p)
+      if (d <= level_count(bt, p) - 2 && bt->lv[bt->lv_first[p] + d].gtc) shared.push_back(bt->lv_first[p] + d);
+    RAV_TRY(upload_phase(bt, bt->tc_apply[d], shared, 256, blk_tc));
+  }
   std::vector<int> fine;
   for (int p = 0; p < bt->nprob; ++p) fine.push_back(bt->lv_first[p]);
   RAV_TRY(upload_phase(bt, bt->fine_res, fine, 256, blk_res));
@@ -962,7 +1245,8 @@ static int bind_vectors(rav_batch* bt, double* const* x, const double* const* b)
   }
   // re-upload the descriptors of every phase (they hold copies)
   std::vector<BPhase*> all;
-  for (auto* v : {&bt->res_smooth, &bt->apply, &bt->restrict_, &bt->prolong, &bt->coarse_mask, &bt->coarse_gemv})
+  for (auto* v : {&bt->res_smooth, &bt->apply, &bt->restrict_, &bt->prolong, &bt->coarse_mask, &bt->coarse_gemv,
+                  &bt->tc_apply})
     for (auto& ph : *v) all.push_back(&ph);
   all.push_back(&bt->fine_res);
   for (BPhase* ph : all) {
@@ -1114,7 +1398,8 @@ extern "C" int batch_setup(rav_mg* const* mgs, rav_smoother* const* sms, int npr
     f.b = b;
   }
   if (cudaMalloc(&bt->norms, sizeof(double) * nprob * nrhs) != cudaSuccess) return fail(RAV_ERR_CUDA);
-  if (cudaMallocHost(&bt->norms_h, sizeof(double) * nprob * nrhs) != cudaSuccess) return fail(RAV_ERR_CUDA);
+  // one spare slot: the tensor-core apply's error flag is read back beside the norms
+  if (cudaMallocHost(&bt->norms_h, sizeof(double) * (nprob * nrhs + 1)) != cudaSuccess) return fail(RAV_ERR_CUDA);
   int rc = autotune(bt, s);
   if (rc != RAV_OK) return fail(rc);
   if (cudaStreamSynchronize(s) != cudaSuccess) return fail(RAV_ERR_CUDA);
@@ -1131,12 +1416,15 @@ extern "C" void batch_destroy(rav_batch* bt) {
     cudaEventDestroy(e.a);
     cudaEventDestroy(e.b);
   }
-  for (auto* v : {&bt->res_smooth, &bt->apply, &bt->restrict_, &bt->prolong, &bt->coarse_mask, &bt->coarse_gemv})
+  for (auto* v : {&bt->res_smooth, &bt->apply, &bt->restrict_, &bt->prolong, &bt->coarse_mask, &bt->coarse_gemv,
+                  &bt->tc_apply})
     for (auto& ph : *v) {
       cudaFree(ph.L);
       cudaFree(ph.first);
       cudaFree(ph.prob);
     }
+  for (float* g : bt->gtc_bufs) cudaFree(g);
+  cudaFree(bt->tc_err);
   cudaFree(bt->fine_res.L);
   cudaFree(bt->fine_res.first);
   cudaFree(bt->fine_res.prob);
@@ -1265,4 +1553,74 @@ extern "C" int solve_batched(rav_batch* bt, double* const* x, const double* cons
     if (ratios) ratios[i] = ratio[i];
   }
   return rc;
+}
+
+extern "C" int batch_set_tensor_apply(rav_batch* bt, int enable, rav_stream stream) {
+  if (!bt) return RAV_ERR_ARG;
+  if (!enable) {
+    if (!bt->use_tc) return RAV_OK;
+    RAV_CUDA(cudaDeviceSynchronize());
+    bt->use_tc = false;
+    for (BLevel& b : bt->lv) b.gtc = nullptr;
+  } else {
+    if (bt->dim != 2 || bt->elem != RAV_ELEM_Q2Q1 || bt->prec != RAV_F32 || bt->nrhs != 8) return RAV_ERR_ARG;
+    if (bt->use_tc) return RAV_OK;
+    cudaStream_t s = S(stream);
+    RAV_CUDA(cudaStreamSynchronize(s));
+    if (!bt->tc_err) RAV_CUDA(cudaMalloc(&bt->tc_err, sizeof(int)));
+    RAV_CUDA(cudaMemset(bt->tc_err, 0, sizeof(int)));
+    RAV_CUDA(cudaFuncSetAttribute(kb_apply_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmem));
+    bt->gtc_bufs.resize(bt->lv.size(), nullptr);
+    int* bad = nullptr;
+    RAV_CUDA(cudaMalloc(&bad, sizeof(int)));
+    std::vector<float> h(2048);
+    for (size_t i = 0; i < bt->lv.size(); ++i) {
+      BLevel& b = bt->lv[i];
+      b.gtc = nullptr;
+      if (!b.inv || b.g.N < 4) continue;  // coarsest levels, grids without an interior subdomain
+      float*& buf = bt->gtc_bufs[i];
+      if (!buf && cudaMalloc(&buf, sizeof(float) * 2048) != cudaSuccess) {
+        cudaFree(bad);
+        return RAV_ERR_CUDA;
+      }
+      kb_shared_build<<<8, 128, 0, s>>>(b.g, (const float*)b.inv, buf);
+      if (cudaMemcpyAsync(h.data(), buf, sizeof(float) * 2048, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+          cudaStreamSynchronize(s) != cudaSuccess) {
+        cudaFree(bad);
+        return RAV_ERR_CUDA;
+      }
+      float amax = 0.f;
+      for (int k = 0; k < 1024; ++k) amax = std::max(amax, std::fabs(h[k] + h[1024 + k]));
+      // stored fp32 rows equal to within two units in the last place of the largest
+      const float tol = std::ldexp(amax, -22);
+      const int64_t ni = b.g.N - 3, tot = ni * ni * 9 * 51;
+      cudaMemsetAsync(bad, 0, sizeof(int), s);
+      kb_shared_check<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(b.g, (const float*)b.inv, tol, bad);
+      int hb = 1;
+      if (cudaMemcpyAsync(&hb, bad, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+          cudaStreamSynchronize(s) != cudaSuccess) {
+        cudaFree(bad);
+        return RAV_ERR_CUDA;
+      }
+      if (!hb) b.gtc = buf;
+    }
+    cudaFree(bad);
+    bt->use_tc = true;
+  }
+  if (bt->graph) {  // the captured cycle holds the previous apply kernels
+    cudaGraphExecDestroy(bt->graph);
+    bt->graph = nullptr;
+  }
+  bt->cur_x.clear();  // descriptors are re-uploaded at the next bind
+  RAV_TRY(build_phases(bt));
+  RAV_CUDA(cudaGetLastError());
+  return RAV_OK;
+}
+
+extern "C" int batch_tensor_apply_levels(const rav_batch* bt) {
+  if (!bt) return RAV_ERR_ARG;
+  int n = 0;
+  if (bt->use_tc)
+    for (const BLevel& b : bt->lv) n += b.gtc != nullptr;
+  return n;
 }

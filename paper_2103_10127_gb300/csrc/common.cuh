@@ -78,7 +78,7 @@ struct Level {
   int64_t nslice = 0;
   int rsplit = 1;  // threads per row of the residual kernel (more on small levels: shorter latency chains)
   int32_t* sperm = nullptr;  // row of slot t = 32 s + lane, -1 for padding
-  int32_t* sslot = nullptr;  // slot of row i (the inverse of sperm; Q1-Q1 hierarchies only, for fused smoothing)
+  int32_t* sslot = nullptr;  // slot of row i (the inverse of sperm), for the fused smoothing step
   int64_t* sptr = nullptr;   // offset of slice s in sval/scol
   int32_t* slen = nullptr;   // row length of slice s (1 = Dirichlet identity rows)
   int32_t* scol = nullptr;
@@ -145,6 +145,18 @@ int prof_begin(rav_mg* mg, int level, int kind, cudaStream_t s, cudaEvent_t* sta
 int prof_end(rav_mg* mg, int level, int kind, cudaEvent_t start, cudaStream_t s);
 }  // namespace rav
 
+namespace rav {
+// Tiling of the staged reduced-precision apply (staged.cu): tiles of
+// tx x ty x tz vertices, ntx x nty x ntz of them, wpt warps per tile, staged
+// Q2-node block sx x sy x sz (2t + 3 per axis; sz = 1 in 2-D).
+struct StagedGeo {
+  int tx, ty, tz;
+  int ntx, nty, ntz;
+  int wpt;
+  int sx, sy, sz;
+};
+}  // namespace rav
+
 // Smoother data of one level: stored inverse rows and damping per subdomain.
 struct SmLevel {
   int64_t np = 0, units = 0;
@@ -164,6 +176,13 @@ struct SmLevel {
   double* stmp = nullptr;    // the whole step with the current damping
   double* rtmp = nullptr;    // residual after that step
   double* xalt = nullptr;    // fused smoothing: the second iterate buffer (n entries)
+  // staged apply of reduced factored storage (staged.cu): threads per
+  // subdomain (0 = not used), tiling and the chunks it streams
+  int staged = 0;
+  rav::StagedGeo sgeo{};
+  void* skq = nullptr;
+  void* swq = nullptr;
+  float* ssinv = nullptr;
 };
 
 struct rav_smoother {
@@ -181,6 +200,12 @@ struct rav_smoother {
 int apply_with_omega(rav_smoother* sm, int level, const double* r, double* x, const double* omega, cudaStream_t s,
                      const float* r32 = nullptr);
 int collect_labels(rav_smoother* sm, int level, const double* r, cudaStream_t s);
+// Staged apply (staged.cu): build its chunks for S threads per subdomain (0
+// frees them), launch it, release it.
+int staged_build(rav_smoother* sm, int level, int S, cudaStream_t s);
+void staged_launch(const rav_smoother* sm, int level, const double* omega, const float* r32, double* x,
+                   cudaStream_t s);
+void staged_free(SmLevel& SL);
 int reset_omega(rav_smoother* sm, cudaStream_t s);
 
 namespace rav {

@@ -976,7 +976,7 @@ static int build_sell(Level& L, cudaStream_t s) {
   RAV_CUDA(cudaMemcpy(L.sperm, perm.data(), sizeof(int32_t) * perm.size(), cudaMemcpyHostToDevice));
   RAV_CUDA(cudaMemcpy(L.sptr, sptr.data(), sizeof(int64_t) * sptr.size(), cudaMemcpyHostToDevice));
   RAV_CUDA(cudaMemcpy(L.slen, slen.data(), sizeof(int32_t) * slen.size(), cudaMemcpyHostToDevice));
-  if (L.g.q == 1) {  // row -> slot, for the fused smoothing step's residual
+  {  // row -> slot, for the fused smoothing step's residual
     std::vector<int32_t> slot(n, -1);
     for (size_t t = 0; t < perm.size(); ++t)
       if (perm[t] >= 0) slot[perm[t]] = (int32_t)t;
@@ -1387,6 +1387,53 @@ extern "C" int rav_get_residual_split(const rav_mg* mg, int level) {
 }
 
 extern "C" int64_t rav_kernel_launches(void) { return g_launches.load(); }
+
+namespace rav {
+// FP64 fused multiply-add throughput: 8 independent chains per thread, every
+// SM full; the chain values stay bounded (x <- x * a + c with |a| < 1).
+__global__ void __launch_bounds__(256) k_fp64_fma_probe(int iters, double a, double c, double* out) {
+  double v[8];
+#pragma unroll
+  for (int k = 0; k < 8; ++k) v[k] = (threadIdx.x + k) * 1e-3;
+  for (int i = 0; i < iters; ++i)
+#pragma unroll
+    for (int k = 0; k < 8; ++k) v[k] = fma(v[k], a, c);
+  double sum = 0.0;
+#pragma unroll
+  for (int k = 0; k < 8; ++k) sum += v[k];
+  if (sum == 12345.678) out[0] = sum;  // keeps the chains live; never true for these inputs
+}
+}  // namespace rav
+
+extern "C" int rav_fp64_fma_rate(double* tflops_host, rav_stream stream) {
+  if (!tflops_host) return RAV_ERR_ARG;
+  cudaStream_t s = S(stream);
+  int dev = 0, nsm = 0;
+  RAV_CUDA(cudaGetDevice(&dev));
+  RAV_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+  double* sink = nullptr;
+  RAV_CUDA(cudaMallocAsync(&sink, sizeof(double), s));
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  int rc = RAV_OK;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) rc = RAV_ERR_CUDA;
+  const int iters = 4096, blocks = nsm * 8, threads = 256;
+  float ms = 0.f;
+  if (rc == RAV_OK) {
+    k_fp64_fma_probe<<<blocks, threads, 0, s>>>(iters, 0.999999, 1e-6, sink);  // warm-up
+    cudaEventRecord(e0, s);
+    for (int r = 0; r < 10; ++r) k_fp64_fma_probe<<<blocks, threads, 0, s>>>(iters, 0.999999, 1e-6, sink);
+    cudaEventRecord(e1, s);
+    if (cudaGetLastError() != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+        cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess || ms <= 0.f)
+      rc = RAV_ERR_CUDA;
+  }
+  if (rc == RAV_OK) *tflops_host = 2.0 * 8.0 * iters * (double)blocks * threads * 10 / (ms * 1e-3) / 1e12;
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  cudaFreeAsync(sink, s);
+  if (rc == RAV_OK && cudaStreamSynchronize(s) != cudaSuccess) rc = RAV_ERR_CUDA;
+  return rc;
+}
 
 extern "C" int rav_profile_enable(rav_mg* mg, unsigned kind_mask, int level) {
   if (!mg || level < -1 || level >= mg->nlev) return RAV_ERR_ARG;

@@ -165,3 +165,74 @@ def test_full_size_batch_sampled_bitwise():
             x = x_in[p][:, k].contiguous()
             mg.vcycle(sm, x, bs[p][:, k].contiguous(), 2, 2)
             assert torch.equal(x, xs[p][:, k]), (p, k)
+
+
+def test_tensor_core_shared_inverse_apply_matches_the_cuda_core_apply():
+    """Uniform constant-viscosity cavities: every interior subdomain of a level
+    shares its owned rows, so the batch applies them as one tcgen05 GEMM per 16
+    subdomains x 8 right-hand sides (tf32 split into high and low parts, fp32
+    accumulation).  One batched cycle equals the fp32 CUDA-core cycle to fp32
+    roundoff of the step, a solve takes the same cycles per system, and
+    switching it off restores the CUDA-core result bit for bit."""
+    nrhs = 8
+    sizes = [16, 32, 48, 64, 24]
+    mgs, sms, xs, bs = make_batch(sizes, nrhs, R.F32, seed=5)
+    bt = R.Batch(mgs, sms, nrhs)
+    x_in = [x.clone() for x in xs]
+    bt.vcycle(xs, bs, 2, 2)
+    ref = [x.clone() for x in xs]
+    nlev = sum(m.nlev - 1 for m in mgs)  # levels with subdomains; N >= 4 everywhere here
+    assert bt.tensor_apply(True) == nlev
+    for x, xi in zip(xs, x_in):
+        x.copy_(xi)
+    bt.vcycle(xs, bs, 2, 2)
+    for p in range(len(sizes)):
+        step_ref = (ref[p] - x_in[p]).cpu().numpy()
+        step_tc = (xs[p] - x_in[p]).cpu().numpy()
+        for k in range(nrhs):
+            d = np.linalg.norm(step_tc[:, k] - step_ref[:, k])
+            assert d <= 1e-5 * np.linalg.norm(step_ref[:, k]), (p, k, d)
+    for x, xi in zip(xs, x_in):
+        x.copy_(xi)
+    it_tc, ra_tc, rc = bt.solve(xs, bs, tol=1e-8, maxit=60)
+    assert rc == 0 and np.all(ra_tc <= 1e-8)
+    assert bt.tensor_apply(False) == 0
+    for x, xi in zip(xs, x_in):
+        x.copy_(xi)
+    bt.vcycle(xs, bs, 2, 2)
+    for p in range(len(sizes)):
+        assert torch.equal(xs[p], ref[p]), p
+    for x, xi in zip(xs, x_in):
+        x.copy_(xi)
+    it_cc, _, rc = bt.solve(xs, bs, tol=1e-8, maxit=60)
+    assert rc == 0 and np.array_equal(it_tc, it_cc)
+
+
+def test_tensor_core_apply_only_where_rows_are_shared():
+    """Blob viscosity breaks the translation invariance of the local systems:
+    those levels keep the CUDA-core apply (and give its result bit for bit),
+    while a uniform problem in the same batch uses the tensor cores; the
+    uniform problem's step still matches the CUDA-core step."""
+    nrhs = 8
+    mg_u = R.Multigrid(2, 32, 3, bc=R.BC_CAVITY)
+    mg_b = R.Multigrid(2, 32, 3, bc=R.BC_CAVITY, blobs=inputs.viscosity_blobs(9, k=4, s_max=1.0))
+    mgs = [mg_u, mg_b]
+    sms = [R.Smoother(m, R.RAV, R.F32, 0.5) for m in mgs]
+    xs, bs = [], []
+    for i, m in enumerate(mgs):
+        b = np.stack([random_rhs(m, 77 + 10 * i + k) for k in range(nrhs)], axis=1)
+        xs.append(torch.from_numpy(np.repeat(m.initial_guess().cpu().numpy()[:, None], nrhs, axis=1).copy()).cuda())
+        bs.append(torch.from_numpy(np.ascontiguousarray(b)).cuda())
+    bt = R.Batch(mgs, sms, nrhs)
+    x_in = [x.clone() for x in xs]
+    bt.vcycle(xs, bs, 2, 2)
+    ref = [x.clone() for x in xs]
+    assert bt.tensor_apply(True) == mg_u.nlev - 1
+    for x, xi in zip(xs, x_in):
+        x.copy_(xi)
+    bt.vcycle(xs, bs, 2, 2)
+    assert torch.equal(xs[1], ref[1])
+    d = (xs[0] - ref[0]).norm() / (ref[0] - x_in[0]).norm()
+    assert 0.0 < d.item() <= 1e-5
+    with pytest.raises(R.RavError):
+        R.Batch(mgs, sms, 4).tensor_apply(True)  # 8 right-hand sides only

@@ -211,6 +211,7 @@ def test_factored_apply_at_every_split(case, prec):
     want = orc.smooth(lev, x, b, 1) - x
     npatch = mg.counts(lev)["n_p"]
     rows0 = cpu(sm.inverse_rows(lev, 0, npatch))
+    sm.apply_staged(lev, 0)  # the grouped kernel, whose launch shape the split sets
     for split in ((1, 2, 4, 8) if case["dim"] == 2 else (1, 2, 4)):
         assert sm.apply_split(lev, split) == split
         xg = gpu(x)
@@ -221,6 +222,46 @@ def test_factored_apply_at_every_split(case, prec):
         assert np.array_equal(cpu(sm.inverse_rows(lev, 0, npatch)), rows0), split
     with pytest.raises(R.RavError):
         sm.apply_split(lev, 3)
+
+
+@pytest.mark.parametrize("prec", [R.F32_FACT, R.BF16_FACT], ids=["f32", "bf16"])
+@pytest.mark.parametrize("case", [CASES[0], CASES[1], CASES[2], CASES[3]], ids=IDS)
+def test_staged_apply_matches_grouped_and_oracle(case, prec):
+    """The staged apply (residual tiles in shared memory, streamed chunks) on
+    every level and with every thread count per subdomain: one step with
+    per-subdomain damping equals the grouped kernel's to fp32 roundoff and the
+    oracle's reduced-storage step within the same bound; 0 restores the
+    grouped kernel bit for bit."""
+    mg, orc = make_pair(**case)
+    sm = R.Smoother(mg, R.RAV, prec, 0.5)
+    orc.setup_smoother(O.RAV, 0.5, {R.F32_FACT: O.F32_FACT, R.BF16_FACT: O.BF16_FACT}[prec])
+    rng = np.random.default_rng(31)
+    for lev in range(1, case["nlev"]):
+        n, npatch = mg.n(lev), mg.counts(lev)["n_p"]
+        w = 0.3 + 0.4 * rng.random(npatch)
+        sm.set_omega(lev, torch.from_numpy(w).cuda())
+        orc.set_omega(lev, w.astype(np.float32).astype(np.float64))
+        x, b = rng.standard_normal(n), rng.standard_normal(n)
+        want = orc.smooth(lev, x, b, 1) - x
+        sm.apply_staged(lev, 0)
+        xg = gpu(x)
+        sm.smooth(lev, xg, gpu(b), 1)
+        grouped = cpu(xg) - x
+        for S in ((1, 2) if case["dim"] == 2 else (2, 4)):
+            assert sm.apply_staged(lev, S) == S
+            xg = gpu(x)
+            sm.smooth(lev, xg, gpu(b), 1)
+            got = cpu(xg) - x
+            assert np.linalg.norm(got - grouped) <= 1e-5 * np.linalg.norm(grouped), (lev, S)
+            assert np.linalg.norm(got - want) <= 1e-5 * np.linalg.norm(want), (lev, S)
+            # owned DoFs only: Dirichlet DoFs are never written
+            assert np.array_equal(got[grouped == 0.0], grouped[grouped == 0.0]), (lev, S)
+        assert sm.apply_staged(lev, 0) == 0
+        xg = gpu(x)
+        sm.smooth(lev, xg, gpu(b), 1)
+        assert np.array_equal(cpu(xg) - x, grouped)
+    with pytest.raises(R.RavError):
+        sm.apply_staged(case["nlev"] - 1, 3)
 
 
 @pytest.mark.parametrize("case", CASES[:3], ids=IDS[:3])
@@ -405,6 +446,19 @@ def test_full_size_512_sampled_parity():
         rows = orc.patch_rows(0, int(p))[: len(mine) * len(s)].reshape(len(mine), len(s))
         want = x[mine] + 0.5 * rows @ r[s]
         assert np.abs(got[mine] - want).max() <= 1e-12 * max(np.abs(want).max(), 1.0), p
+    del sm
+    # reduced factored storage at this size: the staged kernel (1 thread per
+    # subdomain) and the grouped one agree over the whole level
+    for prec in (R.F32_FACT, R.BF16_FACT):
+        sq = R.Smoother(mg, R.RAV, prec, 0.5)
+        out = []
+        for S in (1, 0):
+            sq.apply_staged(nlev - 1, S)
+            xg = gpu(x)
+            sq.smooth(nlev - 1, xg, gpu(b), 1)
+            out.append(cpu(xg) - x)
+        assert np.linalg.norm(out[0] - out[1]) <= 1e-5 * np.linalg.norm(out[1]), prec
+        del sq
 
 
 @pytest.mark.parametrize("nu", [1, 3])
@@ -471,6 +525,16 @@ def test_full_size_32cube_sampled_parity():
         bf16.append(steps[R.BF16_FACT][mine])
     wants, bf16 = np.concatenate(wants), np.concatenate(bf16)
     assert 0.0 < np.linalg.norm(bf16 - wants) <= 2e-2 * np.linalg.norm(wants)
+    # the BF16 step of the staged kernel (4 threads per subdomain) and of the
+    # grouped one agree over the whole level to fp32 roundoff
+    sm = R.Smoother(mg, R.RAV, R.BF16_FACT, 0.5)
+    out = []
+    for S in (4, 0):
+        sm.apply_staged(nlev - 1, S)
+        xg = gpu(x)
+        sm.smooth(nlev - 1, xg, gpu(b), 1)
+        out.append(cpu(xg) - x)
+    assert np.linalg.norm(out[0] - out[1]) <= 1e-5 * np.linalg.norm(out[1])
 
 
 @pytest.mark.slow
@@ -528,3 +592,52 @@ def test_3d_blob_fgmres_iterations_match():
     for prec in (R.F32_FACT, R.BF16_FACT):
         it_p, hist_p, rc_p = runs[prec]
         assert rc_p == 0 and hist_p[-1] <= 1e-8 and it_p <= oit + 1, (prec, it_p, oit)
+
+
+@pytest.mark.parametrize("prec", [R.F64, R.F32_FACT, R.BF16_FACT], ids=["f64", "f32", "bf16"])
+@pytest.mark.parametrize("case", CASES, ids=IDS)
+def test_fused_q2_smoothing_equals_the_two_kernel_steps(case, prec):
+    """The fused Q2-Q1 smoothing step (residual of the tile's boxes with a
+    two-node halo in shared memory + factored apply, x double-buffered) on
+    every level: three steps equal the residual + apply kernels (one thread
+    per row and per owned node, the orders the fused kernel keeps) to
+    rounding, and the FP64 form equals the oracle's steps to 1e-12; a V-cycle
+    and a solve with fused steps take the same course as without."""
+    mg, orc = make_pair(**case)
+    for lev in range(case["nlev"]):
+        mg.residual_split(lev, 1)
+    sm = R.Smoother(mg, R.RAV, prec, 0.5)
+    for lev in range(1, case["nlev"]):
+        sm.apply_staged(lev, 0)
+        sm.apply_split(lev, 1)
+    if prec == R.F64:
+        orc.setup_smoother(O.RAV, 0.5)
+    rng = np.random.default_rng(61)
+    tol = 1e-13 if prec == R.F64 else 2e-6
+    for lev in range(1, case["nlev"]):
+        n = mg.n(lev)
+        x, b = rng.standard_normal(n), rng.standard_normal(n)
+        sm.fused(False)
+        xg = gpu(x)
+        sm.smooth(lev, xg, gpu(b), 3)
+        ref = cpu(xg)
+        sm.fused(True)
+        xg = gpu(x)
+        sm.smooth(lev, xg, gpu(b), 3)
+        got = cpu(xg)
+        assert np.abs(got - ref).max() <= tol * np.abs(ref - x).max(), lev
+        if prec == R.F64:
+            want = orc.smooth(lev, x, b, 3)
+            assert np.abs(got - want).max() <= 1e-12 * np.abs(want - x).max(), lev
+    # whole cycles and a solve
+    b = mg.rhs(R.F_NONE)
+    runs = []
+    for fused in (False, True):
+        sm.fused(fused)
+        x = mg.initial_guess()
+        mg.vcycle(sm, x, b, 2, 2)
+        it, hist, rc = mg.solve(sm, mg.initial_guess(), b, tol=1e-8, maxit=60)
+        runs.append((cpu(x), it, hist, rc))
+    assert np.abs(runs[0][0] - runs[1][0]).max() <= 1e-6 * np.abs(runs[0][0]).max()
+    assert runs[0][3] == runs[1][3] == 0 and runs[0][1] == runs[1][1]
+    sm.fused(False)

@@ -675,6 +675,7 @@ def test_fused_smoothing_solves_like_the_two_kernel_path():
     for kind, prec in ((R.RAV, R.F32_FACT), (R.RAV, R.F64_ROWS), (R.AV, R.F64)):
         with pytest.raises(R.RavError):
             R.Smoother(mg, kind, prec, 0.5).fused(True)
-    q2 = R.Multigrid(2, 8, 2, bc=R.BC_CAVITY)
-    with pytest.raises(R.RavError):
-        R.Smoother(q2, R.RAV, R.F64, 0.5).fused(True)
+    q2 = R.Multigrid(2, 8, 2, bc=R.BC_CAVITY)  # Q2-Q1: the factored storages only
+    for kind, prec in ((R.RAV, R.F64_ROWS), (R.RAV, R.F32), (R.AV, R.F64)):
+        with pytest.raises(R.RavError):
+            R.Smoother(q2, kind, prec, 0.5).fused(True)

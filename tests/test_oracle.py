@@ -658,3 +658,72 @@ def test_thread_count_does_not_change_the_oracle(kind, prec):
     for a, b in zip(*outs):
         a, b = (a[0], b[0]) if isinstance(a, tuple) else (a, b)
         assert np.array_equal(a, b)
+
+
+@pytest.mark.parametrize("dim,N,elem", [(2, 8, O.ELEM_Q2Q1), (3, 4, O.ELEM_Q2Q1), (2, 8, O.ELEM_Q1Q1)])
+def test_patch_features_closed_forms_on_a_uniform_grid(dim, N, elem):
+    """Constant viscosity eta0 on a uniform grid: no contrast, mean log10 eta0,
+    aspect 1, level share, log10 of the cell diagonal h sqrt(d); the size and
+    boundary shares of interior, corner and edge subdomains counted by hand
+    from the box (5^d nodes on Q2-Q1, 3^d on Q1-Q1)."""
+    orc = O.Oracle(dim, N, 2, eta0=2.5, bc=O.BC_NOSLIP, element=elem, beta=0.02)
+    q = 1 if elem == O.ELEM_Q1Q1 else 2
+    ext = 2 * q + 1
+    for lev in (0, 1):
+        Nl = N // 2 ** (1 - lev)
+        f = orc.patch_features(lev)
+        assert f.shape == ((Nl + 1) ** dim, 8)
+        assert np.allclose(f[:, 0], 0.0, atol=1e-14)
+        assert np.allclose(f[:, 1], np.log10(2.5), atol=1e-14)
+        assert np.allclose(f[:, 2:4], 0.0, atol=1e-14)
+        assert np.allclose(f[:, 4], lev)
+        assert np.allclose(f[:, 7], np.log10(np.sqrt(dim) / Nl), atol=1e-14)
+        M = q * Nl + 1
+
+        def shares(v):
+            axes = [[q * vv - q + a for a in range(ext)] for vv in v]
+            inside = [J for J in np.array(np.meshgrid(*axes)).reshape(dim, -1).T if np.all((J >= 0) & (J < M))]
+            bnd = [J for J in inside if np.any((J == 0) | (J == M - 1))]
+            free = len(inside) - len(bnd)
+            return (dim * free + 1) / (dim * ext ** dim + 1), len(bnd) / len(inside)
+
+        for v in [(0,) * dim, (Nl // 2,) * dim, (1,) + (Nl // 2,) * (dim - 1), (Nl,) * dim]:
+            p = sum(vv * (Nl + 1) ** a for a, vv in enumerate(v))
+            want5, want6 = shares(v)
+            assert abs(f[p, 5] - want5) < 1e-15 and abs(f[p, 6] - want6) < 1e-15, v
+        if Nl >= 4:  # a vertex whose whole box is free
+            inner = (Nl // 2,) * dim
+            p = sum(vv * (Nl + 1) ** a for a, vv in enumerate(inner))
+            assert f[p, 5] == 1.0 and f[p, 6] == 0.0
+
+
+def test_patch_features_on_graded_cells_and_blobs():
+    """Graded coordinates: the largest and smallest aspect ratios of the cells
+    around a vertex are their side ratios; blob viscosity: the contrast is
+    positive and grows with the blob strength, vanishes for strength 0, and
+    the mean of log10 eta lies between log10 of the extremes."""
+    N = 8
+    coords = inputs.graded_coordinates(N, 4.0, 2)
+    orc = O.Oracle(2, N, 1, coords=coords, bc=O.BC_NOSLIP)
+    f = orc.patch_features(0)
+    for v in [(0, 0), (3, 5), (8, 8), (4, 0)]:
+        ratios = []
+        for i in (v[0] - 1, v[0]):
+            for j in (v[1] - 1, v[1]):
+                if 0 <= i < N and 0 <= j < N:
+                    hx, hy = coords[0][i + 1] - coords[0][i], coords[1][j + 1] - coords[1][j]
+                    ratios.append(max(hx, hy) / min(hx, hy))
+        p = v[0] + (N + 1) * v[1]
+        assert abs(f[p, 2] - np.log10(max(ratios))) < 1e-13 and abs(f[p, 3] - np.log10(min(ratios))) < 1e-13
+    blob = np.array([[0.5, 0.5, 0.0, 0.15, 0.0]])
+    prev = None
+    for s_ in (0.0, 1.0, 2.0):
+        blob[0, 4] = s_
+        fb = O.Oracle(2, N, 1, blobs=blob, bc=O.BC_NOSLIP).patch_features(0)
+        p = 4 + (N + 1) * 4  # the vertex under the blob centre
+        if s_ == 0.0:
+            assert np.allclose(fb[:, 0], 0.0) and np.allclose(fb[:, 1], 0.0)
+        else:
+            assert fb[p, 0] > 0.0 and fb[p, 0] > prev
+            assert 0.0 <= fb[p, 1] <= s_
+        prev = fb[p, 0]
