@@ -111,6 +111,9 @@ def parse():
     ap.add_argument("--apply-staged", type=int, default=None,
                     help="reduced factored storage: force the staged apply with this many threads per subdomain "
                          "on the finest level (0: the grouped kernel; default: the set-up tuner's choice)")
+    ap.add_argument("--residual-blocked", type=int, default=None, choices=[0, 1],
+                    help="Q2-Q1: force the node-blocked (1) or the row-wise (0) residual on every level "
+                         "(default: the set-up tuner's choice per level)")
     ap.add_argument("--N", type=int, default=None, help="override the grid size (profiling runs)")
     ap.add_argument("--levels", type=int, default=None)
     return ap.parse_args()
@@ -216,10 +219,10 @@ def clocks_stop(handle, gpu_index):
             "samples": len(sm), "reasons": sorted(reasons)}
 
 
-def measured_traffic(kernel_key):
+def measured_traffic(kernel_key, source="smoother.cu"):
     """dram bytes per launch from the committed ncu summary, if it was taken on
-    the current kernel source (else None)."""
-    src = os.path.join(ROOT, "paper_2103_10127_gb300", "csrc", "smoother.cu")
+    the current kernel source file (else None)."""
+    src = os.path.join(ROOT, "paper_2103_10127_gb300", "csrc", source)
     digest = hashlib.sha1(open(src, "rb").read()).hexdigest()[:12]
     path = os.path.join(ROOT, "profiles", f"{kernel_key}.txt")
     if not os.path.exists(path):
@@ -336,6 +339,9 @@ def run_ours(args, W):
     fine = W["nlev"] - 1
     if args.apply_staged is not None:
         sm.apply_staged(fine, args.apply_staged)
+    if args.residual_blocked is not None:
+        for lev in range(W["nlev"]):
+            mg.residual_blocked(lev, args.residual_blocked)
     n = mg.n()
     b = mg.rhs(W["forcing"])
     x0 = mg.initial_guess()
@@ -362,10 +368,12 @@ def run_ours(args, W):
     time.sleep(0.3)
     barrier()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.nvtx.range_push("timed")  # lets a profiler select the timed steps (ncu --nvtx-include timed/)
     e0.record(stream)
     for _ in range(args.steps):
         step()
     e1.record(stream)
+    torch.cuda.nvtx.range_pop()
     barrier()
     ms = e0.elapsed_time(e1)
     clocks = clocks_stop(clk, local)
@@ -426,10 +434,12 @@ def run_ours(args, W):
                 "peak_note": "of measured (MEASURED_PEAKS.json hbm_gbs)" if os.path.exists(mp) else
                 "of fallback (6.8 TB/s, one earlier GB300 copy measurement)"}
     roof["frac"] = roof["achieved"] / roof["peak"]
-    traffic = measured_traffic(f"rav_apply_{args.workload}")
+    staged = W["prec"] in (5, 6) and not q1 and sm.apply_staged(fine) > 0
+    traffic = measured_traffic(f"rav_apply_staged_{args.workload}", "staged.cu") if staged else \
+        measured_traffic(f"rav_apply_{args.workload}")
     roof["traffic"] = traffic
     roof["kernel"] = (("k_fused_q1" if q1 else "k_fused_q2") if args.fused else "k_rav_apply_q1" if q1 else
-                      ("k_rav_apply_staged" if W["prec"] in (5, 6) and sm.apply_staged(fine) else "k_rav_apply_fact")
+                      ("k_rav_apply_staged" if staged else "k_rav_apply_fact")
                       if W["prec"] in (0, 5, 6) else "k_rav_apply") + " (fine level)"
     if args.fused:
         roof["traffic"] = None
@@ -445,7 +455,12 @@ def run_ours(args, W):
            "config": workload_config(W, n, mg.counts(fine)["nnz"], stored, ws, args.fused),
            "roofline": roof, "gpu_launches": int(launches), "clocks": clocks,
            "ms_per_step_kernel_by_kernel": ms_nograph / args.steps,
-           "breakdown_us_per_cycle": breakdown}
+           "breakdown_us_per_cycle": breakdown,
+           "launch_shapes": {f"N={mg.counts(lev)['N']}": {
+               "residual": "node-blocked" if mg.residual_blocked(lev) else f"rows, {mg.residual_split(lev)} thr/row",
+               **({"apply": (f"staged, {sm.apply_staged(lev)} thr/subdomain" if sm.apply_staged(lev)
+                             else f"grouped, split {sm.apply_split(lev)}")} if lev > 0 and W["prec"] in (0, 5, 6)
+                  and not q1 else {})} for lev in range(W["nlev"])}}
 
     # ---- end to end through the public API with host buffers ----
     # Every step uploads its x and b from pinned host memory, runs one V-cycle

@@ -169,6 +169,22 @@ int rav_residual(rav_mg* mg, int level, const double* x_dev, const double* b_dev
 int rav_set_residual_split(rav_mg* mg, int level, int threads_per_row);
 int rav_get_residual_split(const rav_mg* mg, int level);
 
+/* Node-blocked residual on level l (Q2-Q1 hierarchies): the gradient form of
+ * Eq. 7 gives the d velocity rows of a node the same velocity columns and
+ * values (A = I_d (x) K), so one thread per velocity node reads each stored K
+ * entry once for the d components (x as a d-vector) and each pressure column
+ * once with the node's d entries of B; pressure rows keep a row-wise copy of
+ * their own.  Same fp64 products as the row-wise residual, about 40 % (2-D)
+ * or 60 % (3-D) fewer stored bytes; results differ in the order of the
+ * additions.  mg_setup times it against the row-wise kernel on every level and
+ * keeps it where 3 % faster (only then does it hold its memory).  Used when x
+ * is 16-byte aligned (the row-wise kernel serves other x).  enable = 0 frees it.
+ * Synchronises the stream and drops the captured V-cycle graphs.  RAV_ERR_ARG
+ * on Q1-Q1 levels or when a level's component rows differ.
+ * rav_get_residual_blocked returns 1 or 0 (or RAV_ERR_ARG). */
+int rav_set_residual_blocked(rav_mg* mg, int level, int enable, rav_stream stream);
+int rav_get_residual_blocked(const rav_mg* mg, int level);
+
 /* Same residual r = b - L x on level l as rav_residual, plus ||r||_2 written to
  * the caller's device scalar norm_dev, with no memory allocation of any kind
  * and no host synchronisation.  The paper has no counterpart: this exists for
@@ -254,8 +270,11 @@ int rav_get_apply_split(const rav_smoother* sm, int level);
  * subdomain (1 or 2 in 2-D, 2 or 4 in 3-D; partial sums meet by shuffles).
  * 0 returns to the grouped kernel of rav_set_apply_split.  The chunks are a
  * second copy of the stored values, built from the grouped storage (same
- * rounded values) when set; vanka_setup times both kernels on every level and
- * keeps the staged one where it is 3 % faster.  Setting it synchronises the
+ * rounded values) when set, for the tiling ranked first for that thread count
+ * (fewest idle thread slots, best use of the last wave, least halo);
+ * vanka_setup times the grouped kernel and the staged one with the three
+ * best-ranked tilings of each thread count on every level and keeps the
+ * staged one where it is 3 % faster.  Setting it synchronises the
  * stream and drops this smoother's captured cycles.  Results differ from the
  * grouped kernel only in the order of the fp32 additions.  RAV_ERR_ARG for
  * other values or storage (0 is accepted everywhere).  rav_get_apply_staged

@@ -133,6 +133,17 @@ class Multigrid:
             raise RavError(k, "rav_get_residual_split")
         return k
 
+    def residual_blocked(self, level, enable=None, stream=None):
+        """Node-blocked residual on `level` (Q2-Q1); sets it when given, returns 0/1."""
+        lib = _capi.load()
+        if enable is not None:
+            check(lib.rav_set_residual_blocked(self.h, level, int(bool(enable)), _stream(stream)),
+                  "rav_set_residual_blocked")
+        k = lib.rav_get_residual_blocked(self.h, level)
+        if k < 0:
+            raise RavError(k, "rav_get_residual_blocked")
+        return k
+
     def set_graphs(self, enable=True):
         """Replay V-cycles as captured CUDA graphs (default) or launch kernel by kernel."""
         check(_capi.load().rav_set_graphs(self.h, int(enable)), "rav_set_graphs")

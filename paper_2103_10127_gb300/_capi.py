@@ -44,6 +44,8 @@ _SIGS = {
     "rav_residual_norm_noalloc": (I32, [P, I32, P, P, P, P, P]),
     "rav_set_residual_split": (I32, [P, I32, I32]),
     "rav_get_residual_split": (I32, [P, I32]),
+    "rav_set_residual_blocked": (I32, [P, I32, I32, P]),
+    "rav_get_residual_blocked": (I32, [P, I32]),
     "rav_restrict": (I32, [P, I32, P, P, P]),
     "rav_prolong_add": (I32, [P, I32, P, P, P]),
     "rav_coarse_solve": (I32, [P, P, P, P]),

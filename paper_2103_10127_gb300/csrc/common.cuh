@@ -83,6 +83,23 @@ struct Level {
   int32_t* slen = nullptr;   // row length of slice s (1 = Dirichlet identity rows)
   int32_t* scol = nullptr;
   double* sval = nullptr;
+  // node-blocked residual (blocked.cu, Q2-Q1): velocity nodes in slices of 32
+  // by (K, B) entry counts, pressure rows in a sliced-ELL copy of their own;
+  // rblock: the residual uses it (chosen per level at set-up)
+  bool rblock = false;
+  int64_t nbslice = 0, npslice = 0;
+  int32_t* bperm = nullptr;
+  int64_t* bcptr = nullptr;
+  int64_t* bvptr = nullptr;
+  int32_t* bkl = nullptr;
+  int32_t* bbl = nullptr;
+  int32_t* bcol = nullptr;
+  double* bval = nullptr;
+  int32_t* psperm = nullptr;
+  int64_t* psptr = nullptr;
+  int32_t* pslen = nullptr;
+  int32_t* pscol = nullptr;
+  double* psval = nullptr;
   double* x = nullptr;     // level work vectors (coarse levels' iterate and rhs)
   double* b = nullptr;
   double* r = nullptr;     // residual
@@ -202,10 +219,23 @@ int apply_with_omega(rav_smoother* sm, int level, const double* r, double* x, co
 int collect_labels(rav_smoother* sm, int level, const double* r, cudaStream_t s);
 // Staged apply (staged.cu): build its chunks for S threads per subdomain (0
 // frees them), launch it, release it.
-int staged_build(rav_smoother* sm, int level, int S, cudaStream_t s);
+int staged_build(rav_smoother* sm, int level, int S, cudaStream_t s, int cand = 0);
 void staged_launch(const rav_smoother* sm, int level, const double* omega, const float* r32, double* x,
                    cudaStream_t s);
 void staged_free(SmLevel& SL);
+// Node-blocked residual (blocked.cu): build (leaves nbslice 0 where the level
+// does not qualify), free, partial-sum blocks of one launch, launch.
+namespace rav {
+int blocked_build(Level& L, cudaStream_t s);
+void blocked_free(Level& L);
+int64_t blocked_blocks(const Level& L);
+void blocked_launch(const Level& L, const double* x, const double* b, double* r, double* part, float* r32,
+                    cudaStream_t s);
+// The row-wise residual kernel on a sliced-ELL copy (cycle.cu).
+void launch_residual_rows(int64_t nslots, const int32_t* sperm, const int64_t* sptr, const int32_t* slen,
+                          const int32_t* scol, const double* sval, const double* x, const double* b, double* r,
+                          double* part, float* r32, cudaStream_t s);
+}  // namespace rav
 int reset_omega(rav_smoother* sm, cudaStream_t s);
 
 namespace rav {

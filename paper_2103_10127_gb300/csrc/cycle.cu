@@ -427,6 +427,18 @@ __global__ void k_multi_axpy(const double* __restrict__ V, const double* __restr
 int residual_impl(rav_mg* mg, int level, const double* x, const double* b, double* r, double* norm2_dev,
                   cudaStream_t s, float* r32) {
   const Level& L = mg->lev[level];
+  if (L.rblock && ((uintptr_t)x & 15) == 0) {  // node-blocked velocity rows (x read as 16-byte pairs) + pressure rows
+    const int64_t blocks = blocked_blocks(L);
+    if (norm2_dev && blocks > mg->part_cap) return RAV_ERR_ARG;
+    double* part = norm2_dev ? mg->norm_part : nullptr;
+    cudaEvent_t e0;
+    RAV_TRY(prof_begin(mg, level, PROF_RESIDUAL, s, &e0));
+    blocked_launch(L, x, b, r, part, r32, s);
+    if (norm2_dev) k_sum_parts<<<1, 256, 0, s>>>(mg->norm_part, (int)blocks, norm2_dev, 1);
+    note_launch(norm2_dev ? 3 : 2);
+    RAV_CUDA(cudaGetLastError());
+    return prof_end(mg, level, PROF_RESIDUAL, e0, s);
+  }
   const int64_t nslots = L.nslice * 32;
   const int K = L.rsplit;
   const int blocks = (int)((nslots * K + 255) / 256);
@@ -451,6 +463,13 @@ int residual_impl(rav_mg* mg, int level, const double* x, const double* b, doubl
   note_launch(norm2_dev ? 2 : 1);
   RAV_CUDA(cudaGetLastError());
   return prof_end(mg, level, PROF_RESIDUAL, e0, s);
+}
+
+void launch_residual_rows(int64_t nslots, const int32_t* sperm, const int64_t* sptr, const int32_t* slen,
+                          const int32_t* scol, const double* sval, const double* x, const double* b, double* r,
+                          double* part, float* r32, cudaStream_t s) {
+  k_residual_sell<<<(unsigned)((nslots + 255) / 256), 256, 0, s>>>(nslots, sperm, sptr, slen, scol, sval, x, b, r,
+                                                                   part, r32);
 }
 
 int dot_impl(rav_mg* mg, const double* a, const double* b, int64_t n, double* out_dev, cudaStream_t s) {

@@ -1199,6 +1199,19 @@ static int tune_residual_split(rav_mg* mg, cudaStream_t s) {
     int pick = 0;
     while (t[pick] > 1.03f * best) ++pick;
     L.rsplit = 1 << pick;
+    // Q2-Q1: the node-blocked form replaces the row-wise one where it is 3 % faster
+    if (rc == RAV_OK && L.g.q == 2) rc = blocked_build(L, s);
+    if (rc == RAV_OK && L.nbslice) {
+      float tb = 0.f;
+      L.rblock = true;
+      for (int w = 0; w < 2 && rc == RAV_OK; ++w) rc = residual_impl(mg, l, L.x, L.b, L.r, nullptr, s);
+      cudaEventRecord(e0, s);
+      for (int w = 0; w < 5 && rc == RAV_OK; ++w) rc = residual_impl(mg, l, L.x, L.b, L.r, nullptr, s);
+      cudaEventRecord(e1, s);
+      if (rc == RAV_OK && (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&tb, e0, e1) != cudaSuccess))
+        rc = RAV_ERR_CUDA;
+      if (rc == RAV_OK && !(tb < 0.97f * best)) blocked_free(L);  // keeps the memory only where used
+    }
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
@@ -1283,6 +1296,7 @@ extern "C" void mg_destroy(rav_mg* mg) {
     cudaFree(L.rp);
     cudaFree(L.ci);
     cudaFree(L.va);
+    blocked_free(L);
     cudaFree(L.sperm);
     cudaFree(L.sslot);
     cudaFree(L.sptr);
@@ -1379,6 +1393,33 @@ extern "C" int rav_set_residual_split(rav_mg* mg, int level, int threads_per_row
   drop_graphs(mg, nullptr);  // captured V-cycles hold the old launch shape
   mg->lev[level].rsplit = K;
   return RAV_OK;
+}
+
+extern "C" int rav_set_residual_blocked(rav_mg* mg, int level, int enable, rav_stream stream) {
+  if (!mg || level < 0 || level >= mg->nlev) return RAV_ERR_ARG;
+  Level& L = mg->lev[level];
+  if (!enable) {
+    if (!L.rblock) return RAV_OK;
+    RAV_CUDA(cudaDeviceSynchronize());
+    drop_graphs(mg, nullptr);  // captured cycles hold the node-blocked kernels
+    blocked_free(L);
+    return RAV_OK;
+  }
+  if (L.g.q != 2) return RAV_ERR_ARG;
+  if (L.rblock) return RAV_OK;
+  cudaStream_t s = S(stream);
+  RAV_CUDA(cudaStreamSynchronize(s));
+  RAV_TRY(blocked_build(L, s));
+  if (!L.nbslice) return RAV_ERR_ARG;  // the component rows do not share their velocity block
+  RAV_CUDA(cudaStreamSynchronize(s));
+  drop_graphs(mg, nullptr);
+  L.rblock = true;
+  return RAV_OK;
+}
+
+extern "C" int rav_get_residual_blocked(const rav_mg* mg, int level) {
+  if (!mg || level < 0 || level >= mg->nlev) return RAV_ERR_ARG;
+  return mg->lev[level].rblock ? 1 : 0;
 }
 
 extern "C" int rav_get_residual_split(const rav_mg* mg, int level) {

@@ -1855,24 +1855,29 @@ static int tune_apply_split(rav_smoother* sm, cudaStream_t s) {
     // reduced storage: the staged kernel (shared-memory residual tiles,
     // streamed chunks) replaces the grouped one where it is 3 % faster
     if (rc == RAV_OK && sm->prec != RAV_F64) {
-      const int cand[2] = {mg->dim == 2 ? 1 : 2, mg->dim == 2 ? 2 : 4};
+      const int splits[2] = {mg->dim == 2 ? 1 : 2, mg->dim == 2 ? 2 : 4};
       float tb = 0.97f * best;
-      int sbest = 0;
-      for (int ci = 0; ci < 2 && rc == RAV_OK; ++ci) {
-        rc = staged_build(sm, l, cand[ci], s);
-        for (int w = 0; w < 2 && rc == RAV_OK; ++w) rc = apply_with_omega(sm, l, L.r, L.x, SL.omega, s, SL.r32);
-        cudaEventRecord(e0, s);
-        for (int w = 0; w < 5 && rc == RAV_OK; ++w) rc = apply_with_omega(sm, l, L.r, L.x, SL.omega, s, SL.r32);
-        cudaEventRecord(e1, s);
-        float ts = 0.f;
-        if (rc == RAV_OK && (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ts, e0, e1) != cudaSuccess))
-          rc = RAV_ERR_CUDA;
-        if (rc == RAV_OK && ts < tb) {
-          tb = ts;
-          sbest = cand[ci];
+      int sbest = 0, cbest = 0;
+      for (int ci = 0; ci < 2 && rc == RAV_OK; ++ci)
+        for (int tc = 0; tc < 3 && rc == RAV_OK; ++tc) {  // the three best tilings
+          const int rb = staged_build(sm, l, splits[ci], s, tc);
+          if (rb == RAV_ERR_ARG) break;  // no further candidate
+          rc = rb;
+          for (int w = 0; w < 2 && rc == RAV_OK; ++w) rc = apply_with_omega(sm, l, L.r, L.x, SL.omega, s, SL.r32);
+          cudaEventRecord(e0, s);
+          for (int w = 0; w < 5 && rc == RAV_OK; ++w) rc = apply_with_omega(sm, l, L.r, L.x, SL.omega, s, SL.r32);
+          cudaEventRecord(e1, s);
+          float ts = 0.f;
+          if (rc == RAV_OK &&
+              (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ts, e0, e1) != cudaSuccess))
+            rc = RAV_ERR_CUDA;
+          if (rc == RAV_OK && ts < tb) {
+            tb = ts;
+            sbest = splits[ci];
+            cbest = tc;
+          }
         }
-      }
-      if (rc == RAV_OK && sbest != SL.staged) rc = staged_build(sm, l, sbest, s);
+      if (rc == RAV_OK) rc = staged_build(sm, l, sbest, s, cbest);
     }
     cudaMemsetAsync(L.x, 0, sizeof(double) * L.g.n, s);
   }

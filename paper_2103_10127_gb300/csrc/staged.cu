@@ -157,26 +157,46 @@ __device__ __forceinline__ void sm_chunk(const T* p, float* out) {
 }
 
 // Shared-memory plan of a block of nthr threads: the K^{-1} chunk ring (slot q
-// of thread i at (q nthr + i) CK bytes), the w chunk ring, the staged residual
-// nodes, the box-node offset table.
+// of thread i at (q nthr + i) CK bytes), the w chunk ring, the epilogue slots
+// (per thread the x values and w chunks of the owned nodes it writes, fetched
+// at the start), the staged residual nodes, the box-node offset table.
 template <int D, typename T, int S>
 struct StagedPlan {
   static constexpr int NV = StagedBox<D>::NV, NON = StagedBox<D>::NON, WC = StagedBox<D>::WC;
   static constexpr int NJ = (NV + S - 1) / S;
   static constexpr int CK = NON * (int)sizeof(T), CW = WC * (int)sizeof(T);
+  static constexpr int OWN = (NON + S - 1) / S;              // owned nodes written per thread
+  static constexpr int OFFX = (CW + 7) / 8 * 8;               // per owned node: its w chunk, then
+  static constexpr int BLK = (OFFX + 8 * D + 15) / 16 * 16;   // its d fp64 x values (16-byte blocks)
+  static constexpr int EPI = OWN * BLK;
   __host__ __device__ static size_t ring_k(int nthr) { return (size_t)kStRing * nthr * CK; }
   __host__ __device__ static size_t ring(int nthr) { return (size_t)kStRing * nthr * (CK + CW); }
+  __host__ __device__ static size_t epi_off(int nthr) { return ring(nthr); }
+  __host__ __device__ static size_t nodes_off(int nthr) { return epi_off(nthr) + (size_t)EPI * nthr; }
   __host__ __device__ static size_t offs_off(const StagedGeo& sg) {
-    return ring(sg.wpt * 32) + (size_t)sg.sx * sg.sy * sg.sz * (D == 3 ? 16 : 8);
+    return nodes_off(sg.wpt * 32) + (size_t)sg.sx * sg.sy * sg.sz * (D == 3 ? 16 : 8);
   }
   __host__ __device__ static size_t bytes(const StagedGeo& sg) { return offs_off(sg) + sizeof(int) * NJ * S; }
 };
 
+// cp.async of 4 bytes, zero-filled when !valid (then src is not read).
+__device__ __forceinline__ void st_copy4z(void* dst, const void* src, bool valid) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(st_smem(dst)), "l"(src), "r"(valid ? 4 : 0)
+               : "memory");
+}
+
+// Blocks per SM the register budget must allow: 4 of 256 threads (64
+// registers); 3-D fp32 chunks run in blocks of 128 threads and get more.
+template <int D, typename T>
+constexpr int staged_min_blocks() {
+  return (D == 3 && sizeof(T) == 4) ? 3 : 4;
+}
+
 template <int D, typename T, int S>
-__global__ void __launch_bounds__(256, 4) k_rav_apply_staged(Geo g, StagedGeo sg, const T* __restrict__ kq,
-                                                         const T* __restrict__ wq, const float* __restrict__ sinv,
-                                                         const double* __restrict__ omega,
-                                                         const float* __restrict__ r32, double* __restrict__ x) {
+__global__ void __launch_bounds__(256, staged_min_blocks<D, T>()) k_rav_apply_staged(Geo g, StagedGeo sg, const T* __restrict__ kq,
+                                                            const T* __restrict__ wq, const float* __restrict__ sinv,
+                                                            const double* __restrict__ omega,
+                                                            const float* __restrict__ r32, double* __restrict__ x) {
   using P = StagedPlan<D, T, S>;
   using RV = typename NodeT<D>::type;
   constexpr int NV = P::NV, NON = P::NON, WC = P::WC, NJ = P::NJ, CK = P::CK, CW = P::CW;
@@ -185,7 +205,8 @@ __global__ void __launch_bounds__(256, 4) k_rav_apply_staged(Geo g, StagedGeo sg
   const int tid = threadIdx.x;
   uint8_t* ringk = sraw;
   uint8_t* ringw = sraw + P::ring_k(nthr);
-  RV* tile = reinterpret_cast<RV*>(sraw + P::ring(nthr));
+  uint8_t* epi = sraw + P::epi_off(nthr) + (size_t)tid * P::EPI;
+  RV* tile = reinterpret_cast<RV*>(sraw + P::nodes_off(nthr));
   int* offs = reinterpret_cast<int*>(sraw + P::offs_off(sg));
   const int nst = sg.sx * sg.sy * (D == 3 ? sg.sz : 1);
   const int t = blockIdx.x;
@@ -197,8 +218,55 @@ __global__ void __launch_bounds__(256, 4) k_rav_apply_staged(Geo g, StagedGeo sg
   const int v[3] = {v0x + lx, v0y + ly, v0z + lz};
   // threads of slots outside the grid (or past the tile) only help staging r
   const bool active = l < TS && v[0] <= g.N && v[1] <= g.N && (D == 2 || v[2] <= g.N);
-  // this thread's chunk at node step j: ((t NJ + j) W + warp) 32 + lane, W warps per block
   const size_t cstride = (size_t)nthr;  // chunks per node step of the block
+  // group 0: the tile's residual boxes (every thread a share, zero outside the
+  // domain; r is zero on Dirichlet rows already) and this thread's epilogue data
+  const int64_t M = g.M;
+  for (int i = tid; i < nst; i += blockDim.x) {
+    const int i0 = i % sg.sx, i1 = (i / sg.sx) % sg.sy, i2 = D == 3 ? i / (sg.sx * sg.sy) : 0;
+    const int64_t J0 = 2 * v0x - 2 + i0, J1 = 2 * v0y - 2 + i1, J2 = D == 3 ? 2 * v0z - 2 + i2 : 0;
+    bool in = J0 >= 0 && J0 < M && J1 >= 0 && J1 < M;
+    if (D == 3) in = in && J2 >= 0 && J2 < M;
+    const float* src = r32 + (in ? (J0 + M * (J1 + M * J2)) * D : 0);
+    float* dst = reinterpret_cast<float*>(tile + i);
+#pragma unroll
+    for (int c = 0; c < D; ++c) st_copy4z(dst + c, src + c, in);
+    if (D == 3) dst[3] = 0.f;
+  }
+  // owned node q (bit d = offset on axis d) is written by split q % S: its first
+  // velocity DoF (-1: a Dirichlet node) and its box position mq
+  auto owned = [&](int q, int& mq) -> int64_t {
+    int64_t J[3] = {0, 0, 0};
+    bool ok = true;
+    mq = 0;
+#pragma unroll
+    for (int d = D - 1; d >= 0; --d) {
+      const int dl = (q >> d) & 1;
+      J[d] = 2 * v[d] + dl;
+      ok &= (J[d] >= 1) & (J[d] <= 2 * g.N - 1);
+      mq = mq * 5 + 2 + dl;
+    }
+    return ok ? D * node_id_t<D>(g, J) : -1;
+  };
+  if (active) {
+#pragma unroll
+    for (int k = 0; k < P::OWN; ++k) {
+      const int q = s + S * k;
+      if (q >= NON) continue;
+      int mq;
+      const int64_t dof = owned(q, mq);
+      if (dof < 0) continue;
+      double* ex = reinterpret_cast<double*>(epi + k * P::BLK + P::OFFX);
+#pragma unroll
+      for (int c = 0; c < D; ++c) st_copy<8>(ex + c, x + dof + c);
+      // w at the owned node's box position: its chunk, streamed by split mq % S at step mq / S
+      const int kk = l * S + mq % S;
+      const size_t ci = ((size_t)t * NJ + mq / S) * cstride + kk;
+      st_copy<CW>(epi + k * P::BLK, wq + ci * WC);
+    }
+  }
+  st_commit();
+  // groups 1 .. RING: the first node steps of this thread's chunk stream
   const T* kme = kq + ((size_t)t * NJ * cstride + tid) * NON;
   const T* wme = wq + ((size_t)t * NJ * cstride + tid) * WC;
   auto issue = [&](int j) {
@@ -206,34 +274,10 @@ __global__ void __launch_bounds__(256, 4) k_rav_apply_staged(Geo g, StagedGeo sg
     st_copy<CK>(ringk + ((size_t)q * nthr + tid) * CK, kme + (size_t)j * cstride * NON);
     st_copy<CW>(ringw + ((size_t)q * nthr + tid) * CW, wme + (size_t)j * cstride * WC);
   };
-  if (active) {
 #pragma unroll
-    for (int j = 0; j < kStRing; ++j) {
-      if (j < NJ) issue(j);
-      st_commit();
-    }
-  }
-  // meanwhile: stage r over the tile's boxes (node (i0, i1, i2) of the block is Q2 node 2 v0 - 2 + i)
-  const int64_t M = g.M;
-  for (int i = tid; i < nst; i += blockDim.x) {
-    const int i0 = i % sg.sx, i1 = (i / sg.sx) % sg.sy, i2 = D == 3 ? i / (sg.sx * sg.sy) : 0;
-    const int64_t J0 = 2 * v0x - 2 + i0, J1 = 2 * v0y - 2 + i1, J2 = D == 3 ? 2 * v0z - 2 + i2 : 0;
-    bool in = J0 >= 0 && J0 < M && J1 >= 0 && J1 < M;
-    if (D == 3) in = in && J2 >= 0 && J2 < M;
-    RV rv;
-    if constexpr (D == 2) {
-      rv = make_float2(0.f, 0.f);
-      if (in) rv = *reinterpret_cast<const float2*>(r32 + (J0 + M * J1) * 2);
-    } else {
-      rv = make_float4(0.f, 0.f, 0.f, 0.f);
-      if (in) {
-        const float* src = r32 + (J0 + M * (J1 + M * J2)) * 3;
-        rv.x = src[0];
-        rv.y = src[1];
-        rv.z = src[2];
-      }
-    }
-    tile[i] = rv;
+  for (int j = 0; j < kStRing; ++j) {
+    if (active && j < NJ) issue(j);
+    st_commit();
   }
   for (int n = tid; n < NJ * S; n += blockDim.x) {
     int off = 0;  // padded node: any staged node (its stored values are zero)
@@ -243,6 +287,7 @@ __global__ void __launch_bounds__(256, 4) k_rav_apply_staged(Geo g, StagedGeo sg
     }
     offs[n] = off;
   }
+  st_wait<kStRing>();  // group 0 has landed
   __syncthreads();
   if (!active) return;
   const int base = ((D == 3 ? 2 * lz * sg.sy : 0) + 2 * ly) * sg.sx + 2 * lx;
@@ -286,29 +331,26 @@ __global__ void __launch_bounds__(256, 4) k_rav_apply_staged(Geo g, StagedGeo sg
   const int64_t p = v[0] + (int64_t)(g.N + 1) * (v[1] + (int64_t)(g.N + 1) * v[2]);
   const float tau = sinv[(int64_t)t * TS + l] * (tw - r32[g.n_u + p]);
   const double om = omega[p];
-  // owned node q (bit d of q = offset on axis d) is written by split q % S;
-  // w at its box position is read back from its chunk (just streamed, in L2)
 #pragma unroll
-  for (int q = 0; q < NON; ++q) {
-    if (q % S != s) continue;
-    int64_t J[3] = {0, 0, 0};
-    bool ok = true;
-    int mq = 0;
-#pragma unroll
-    for (int d = D - 1; d >= 0; --d) {
-      const int dl = (q >> d) & 1;
-      J[d] = 2 * v[d] + dl;
-      ok &= (J[d] >= 1) & (J[d] <= 2 * g.N - 1);
-      mq = mq * 5 + 2 + dl;
-    }
-    if (!ok) continue;
-    const int kk = l * S + mq % S;
-    const size_t ci = ((size_t)t * NJ + mq / S) * cstride + kk;
+  for (int k = 0; k < P::OWN; ++k) {
+    const int q = s + S * k;
+    if (q >= NON) continue;
+    int mq;
+    const int64_t dof = owned(q, mq);
+    if (dof < 0) continue;
+    const double* ex = reinterpret_cast<const double*>(epi + k * P::BLK + P::OFFX);
     float wm[WC];
-    ld_chunk<T, WC>(wq + ci * WC, wm);
-    const int64_t dof = D * node_id_t<D>(g, J);
+    sm_chunk<T, WC>(reinterpret_cast<const T*>(epi + k * P::BLK), wm);
+    float yq[D];
 #pragma unroll
-    for (int c = 0; c < D; ++c) x[dof + c] += om * (double)(y[q][c] + wm[c] * tau);
+    for (int c = 0; c < D; ++c) yq[c] = y[0][c];
+#pragma unroll
+    for (int qq = 1; qq < NON; ++qq)
+      if (qq == q)
+#pragma unroll
+        for (int c = 0; c < D; ++c) yq[c] = y[qq][c];
+#pragma unroll
+    for (int c = 0; c < D; ++c) x[dof + c] = ex[c] + om * (double)(yq[c] + wm[c] * tau);
   }
   if (s == 0) x[g.n_u + p] += om * (double)-tau;
 }
@@ -350,15 +392,21 @@ __global__ void k_restage(Geo g, StagedGeo sg, const T* __restrict__ kinv, const
 
 using namespace rav;
 
-// Tile of vertices for a level of N cells per axis and S threads per
+// Tiles of vertices for a level of N cells per axis and S threads per
 // subdomain: 64 to max_threads threads per block and at most 100 KiB of shared
-// memory (ring of streamed chunks: ring_per_warp bytes per warp, plus the
-// staged residual nodes), as few idle thread slots as possible (tiles past the
-// grid's last vertex), then as little halo.
-StagedGeo staged_tiles(int D, int N, int S, size_t ring_per_warp, int max_threads) {
+// memory (ring of streamed chunks and epilogue slots: ring_per_warp bytes per
+// warp, plus the staged residual nodes).  Candidates are ranked by idle thread
+// slots (tiles past the grid's last vertex) and the use of the last wave, with
+// a penalty for halo (staged nodes per owned node); cand picks the cand-th best
+// of distinct block counts (the set-up tuner times the first few).  tx == 0:
+// no candidate.
+StagedGeo staged_tiles(int D, int N, int S, size_t ring_per_warp, int max_threads, int cand) {
   const int mv = N + 1;
-  StagedGeo best{};
-  double best_score = 1e300;
+  struct Cand {
+    double score;
+    StagedGeo sg;
+  };
+  std::vector<Cand> all;
   const int zmax = D == 3 ? std::min(mv, 16) : 1;
   for (int tx = 1; tx <= std::min(mv, 64); ++tx)
     for (int ty = 1; ty <= std::min(mv, 32); ++ty)
@@ -379,13 +427,19 @@ StagedGeo staged_tiles(int D, int N, int S, size_t ring_per_warp, int max_thread
         const int per_sm = std::max(1, std::min({(int)(228 * 1024 / (smem + 1024)), 2048 / (wpt * 32), 32}));
         const double slots_gpu = 152.0 * per_sm;
         const double wave_use = tiles / (std::ceil(tiles / slots_gpu) * slots_gpu);
-        const double score = slots / used * (1.0 + 0.05 * halo) / wave_use;
-        if (score < best_score) {
-          best_score = score;
-          best = StagedGeo{tx, ty, tz, ntx, nty, ntz, wpt, 2 * tx + 3, 2 * ty + 3, D == 3 ? 2 * tz + 3 : 1};
-        }
+        const double score = slots / used * (1.0 + 0.15 * halo) / wave_use;
+        all.push_back({score, StagedGeo{tx, ty, tz, ntx, nty, ntz, wpt, 2 * tx + 3, 2 * ty + 3,
+                                        D == 3 ? 2 * tz + 3 : 1}});
       }
-  return best;
+  std::sort(all.begin(), all.end(), [](const Cand& a, const Cand& b) { return a.score < b.score; });
+  std::vector<int64_t> seen;
+  for (const Cand& c : all) {
+    const int64_t key = (int64_t)c.sg.ntx * c.sg.nty * c.sg.ntz * 4096 + c.sg.wpt;
+    if (std::find(seen.begin(), seen.end(), key) != seen.end()) continue;
+    if ((int)seen.size() == cand) return c.sg;
+    seen.push_back(key);
+  }
+  return StagedGeo{};
 }
 
 // Frees the staged chunks of a level (its grouped storage stays).
@@ -399,13 +453,14 @@ void staged_free(SmLevel& SL) {
 }
 
 template <int D, typename T, int S>
-static int restage_t(const Geo& g, SmLevel& SL, cudaStream_t s) {
+static int restage_t(const Geo& g, SmLevel& SL, int cand, cudaStream_t s) {
   using P = StagedPlan<D, T, S>;
   using SB = StagedBox<D>;
   constexpr int NJ = P::NJ;
   // 3-D fp32 chunks are twice as large: smaller blocks keep two per SM
   const int max_thr = (D == 3 && sizeof(T) == 4) ? 128 : 256;
-  const StagedGeo sg = staged_tiles(D, g.N, S, (size_t)kStRing * 32 * (P::CK + P::CW), max_thr);
+  const StagedGeo sg =
+      staged_tiles(D, g.N, S, (size_t)kStRing * 32 * (P::CK + P::CW) + 32 * P::EPI, max_thr, cand);
   if (sg.tx == 0) return RAV_ERR_ARG;
   const int64_t tiles = (int64_t)sg.ntx * sg.nty * sg.ntz;
   const int64_t chunks = tiles * sg.wpt * NJ * 32;
@@ -433,9 +488,10 @@ static int restage_t(const Geo& g, SmLevel& SL, cudaStream_t s) {
 }
 
 // (Re)builds the staged chunks of a reduced factored Q2-Q1 level for S threads
-// per subdomain (2-D: 1 or 2; 3-D: 2 or 4); S = 0 frees them (the grouped
-// kernel is used again).
-int staged_build(rav_smoother* sm, int level, int S, cudaStream_t s) {
+// per subdomain (2-D: 1 or 2; 3-D: 2 or 4) and the cand-th tiling candidate;
+// S = 0 frees them (the grouped kernel is used again).  RAV_ERR_ARG when
+// there is no such candidate.
+int staged_build(rav_smoother* sm, int level, int S, cudaStream_t s, int cand) {
   SmLevel& SL = sm->lev[level];
   const Geo& g = sm->mg->lev[level].g;
   if (S == 0) {
@@ -444,11 +500,11 @@ int staged_build(rav_smoother* sm, int level, int S, cudaStream_t s) {
   }
   const bool bf = sm->prec == RAV_BF16_FACT;
   if (g.dim == 2) {
-    if (S == 1) return bf ? restage_t<2, __nv_bfloat16, 1>(g, SL, s) : restage_t<2, float, 1>(g, SL, s);
-    if (S == 2) return bf ? restage_t<2, __nv_bfloat16, 2>(g, SL, s) : restage_t<2, float, 2>(g, SL, s);
+    if (S == 1) return bf ? restage_t<2, __nv_bfloat16, 1>(g, SL, cand, s) : restage_t<2, float, 1>(g, SL, cand, s);
+    if (S == 2) return bf ? restage_t<2, __nv_bfloat16, 2>(g, SL, cand, s) : restage_t<2, float, 2>(g, SL, cand, s);
   } else {
-    if (S == 2) return bf ? restage_t<3, __nv_bfloat16, 2>(g, SL, s) : restage_t<3, float, 2>(g, SL, s);
-    if (S == 4) return bf ? restage_t<3, __nv_bfloat16, 4>(g, SL, s) : restage_t<3, float, 4>(g, SL, s);
+    if (S == 2) return bf ? restage_t<3, __nv_bfloat16, 2>(g, SL, cand, s) : restage_t<3, float, 2>(g, SL, cand, s);
+    if (S == 4) return bf ? restage_t<3, __nv_bfloat16, 4>(g, SL, cand, s) : restage_t<3, float, 4>(g, SL, cand, s);
   }
   return RAV_ERR_ARG;
 }
