@@ -267,14 +267,17 @@ int rav_get_apply_split(const rav_smoother* sm, int level);
  * vertices, chosen per level) into shared memory once, then stream the stored
  * values of their subdomains in per-thread chunks (the 2^d owned rows of
  * K_i^{-1} and w at one box node) with threads_per_subdomain threads per
- * subdomain (1 or 2 in 2-D, 2 or 4 in 3-D; partial sums meet by shuffles).
- * 0 returns to the grouped kernel of rav_set_apply_split.  The chunks are a
+ * subdomain: 1 (tiles of fixed shape, 16 x 24 vertices in 2-D with each
+ * thread taking three subdomains in turn, 3 x 3 x 3 in 3-D; box offsets known
+ * at compile time, the stream kept in flight in registers), 2 (2-D and 3-D)
+ * or 4 (3-D), the partial sums of several threads meeting by shuffles.  0
+ * returns to the grouped kernel of rav_set_apply_split.  The chunks are a
  * second copy of the stored values, built from the grouped storage (same
- * rounded values) when set, for the tiling ranked first for that thread count
- * (fewest idle thread slots, best use of the last wave, least halo);
- * vanka_setup times the grouped kernel and the staged one with the three
- * best-ranked tilings of each thread count on every level and keeps the
- * staged one where it is 3 % faster.  Setting it synchronises the
+ * rounded values) when set, for 2 and 4 with the tiling ranked first for that
+ * thread count (fewest idle thread slots, best use of the last wave, least
+ * halo); vanka_setup times the grouped kernel and the staged one (1 thread;
+ * the three best-ranked tilings of 2 and 4 threads) on every level and keeps
+ * the staged one where it is 3 % faster.  Setting it synchronises the
  * stream and drops this smoother's captured cycles.  Results differ from the
  * grouped kernel only in the order of the fp32 additions.  RAV_ERR_ARG for
  * other values or storage (0 is accepted everywhere).  rav_get_apply_staged

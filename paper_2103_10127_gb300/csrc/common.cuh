@@ -193,8 +193,8 @@ struct SmLevel {
   double* stmp = nullptr;    // the whole step with the current damping
   double* rtmp = nullptr;    // residual after that step
   double* xalt = nullptr;    // fused smoothing: the second iterate buffer (n entries)
-  // staged apply of reduced factored storage (staged.cu): threads per
-  // subdomain (0 = not used), tiling and the chunks it streams
+  // staged apply of reduced factored storage (staged.cu, stream.cu): threads
+  // per subdomain (0 = not used), tiling and the chunks it streams
   int staged = 0;
   rav::StagedGeo sgeo{};
   void* skq = nullptr;
@@ -223,6 +223,10 @@ int staged_build(rav_smoother* sm, int level, int S, cudaStream_t s, int cand = 
 void staged_launch(const rav_smoother* sm, int level, const double* omega, const float* r32, double* x,
                    cudaStream_t s);
 void staged_free(SmLevel& SL);
+// Streamed apply, one thread per subdomain (stream.cu): the S = 1 case of the above.
+int stream_build(rav_smoother* sm, int level, cudaStream_t s);
+void stream_launch(const rav_smoother* sm, int level, const double* omega, const float* r32, double* x,
+                   cudaStream_t s);
 // Node-blocked residual (blocked.cu): build (leaves nbslice 0 where the level
 // does not qualify), free, partial-sum blocks of one launch, launch.
 namespace rav {

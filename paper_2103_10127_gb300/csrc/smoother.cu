@@ -1855,10 +1855,11 @@ static int tune_apply_split(rav_smoother* sm, cudaStream_t s) {
     // reduced storage: the staged kernel (shared-memory residual tiles,
     // streamed chunks) replaces the grouped one where it is 3 % faster
     if (rc == RAV_OK && sm->prec != RAV_F64) {
-      const int splits[2] = {mg->dim == 2 ? 1 : 2, mg->dim == 2 ? 2 : 4};
+      const int splits[3] = {1, 2, 4};
+      const int nsplit = mg->dim == 2 ? 2 : 3;
       float tb = 0.97f * best;
       int sbest = 0, cbest = 0;
-      for (int ci = 0; ci < 2 && rc == RAV_OK; ++ci)
+      for (int ci = 0; ci < nsplit && rc == RAV_OK; ++ci)
         for (int tc = 0; tc < 3 && rc == RAV_OK; ++tc) {  // the three best tilings
           const int rb = staged_build(sm, l, splits[ci], s, tc);
           if (rb == RAV_ERR_ARG) break;  // no further candidate
@@ -1910,7 +1911,7 @@ extern "C" int rav_set_apply_staged(rav_smoother* sm, int level, int threads_per
   SmLevel& SL = sm->lev[level];
   const int nt = threads_per_subdomain;
   if (sm->mg->elem != RAV_ELEM_Q2Q1 || !SL.factored || sm->prec == RAV_F64) return nt == 0 ? RAV_OK : RAV_ERR_ARG;
-  const bool ok = nt == 0 || (sm->mg->dim == 2 ? (nt == 1 || nt == 2) : (nt == 2 || nt == 4));
+  const bool ok = nt == 0 || nt == 1 || nt == 2 || (sm->mg->dim == 3 && nt == 4);
   if (!ok) return RAV_ERR_ARG;
   if (nt == SL.staged) return RAV_OK;
   cudaStream_t s = S(stream);

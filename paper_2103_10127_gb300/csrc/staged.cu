@@ -39,6 +39,7 @@
 
 #include "box.cuh"
 #include "common.cuh"
+#include "cpasync.cuh"
 #include "fmt.cuh"
 
 namespace rav {
@@ -50,111 +51,11 @@ struct StagedBox {
   static constexpr int WC = D == 3 ? 4 : 2; // w values per chunk (3-D: 3 and a zero)
 };
 
-// NVAL consecutive stored values of type T (one chunk) widened to fp32; the
-// chunk is NVAL * sizeof(T) bytes, aligned to that size (4 to 32 bytes), and is
-// read once per pass, hence the evict-first loads.
-template <typename T, int NVAL>
-__device__ __forceinline__ void ld_chunk(const T* __restrict__ p, float* out) {
-  constexpr int BYTES = NVAL * (int)sizeof(T);
-  constexpr int NW = BYTES / 4;
-  unsigned w[NW];
-  if constexpr (BYTES == 4) {
-    w[0] = __ldcs(reinterpret_cast<const unsigned*>(p));
-  } else if constexpr (BYTES == 8) {
-    const uint2 v = __ldcs(reinterpret_cast<const uint2*>(p));
-    w[0] = v.x;
-    w[1] = v.y;
-  } else {
-#pragma unroll
-    for (int i = 0; i < NW; i += 4) {
-      const uint4 v = __ldcs(reinterpret_cast<const uint4*>(p) + i / 4);
-      w[i] = v.x;
-      w[i + 1] = v.y;
-      w[i + 2] = v.z;
-      w[i + 3] = v.w;
-    }
-  }
-  if constexpr (std::is_same<T, float>::value) {
-#pragma unroll
-    for (int i = 0; i < NW; ++i) out[i] = __uint_as_float(w[i]);
-  } else {  // bf16 pairs: the lower address is the low half of the word
-#pragma unroll
-    for (int i = 0; i < NW; ++i) {
-      out[2 * i] = __uint_as_float(w[i] << 16);
-      out[2 * i + 1] = __uint_as_float(w[i] & 0xffff0000u);
-    }
-  }
-}
-
-template <int D>
-struct NodeT;
-template <>
-struct NodeT<2> {
-  using type = float2;
-};
-template <>
-struct NodeT<3> {
-  using type = float4;
-};
-
 // Streaming of the chunks: every thread keeps kStRing node steps of its own
 // chunks in flight with cp.async (global -> shared, no registers held), in a
 // per-thread ring of shared-memory slots, and waits only for its own oldest
 // copy group before using it.
 constexpr int kStRing = 4;
-
-__device__ __forceinline__ uint32_t st_smem(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
-// Asynchronous copy of BYTES (4, 8 or a multiple of 16) from global to shared memory.
-template <int BYTES>
-__device__ __forceinline__ void st_copy(void* dst, const void* src) {
-  if constexpr (BYTES % 16 == 0) {
-#pragma unroll
-    for (int i = 0; i < BYTES; i += 16)
-      asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(st_smem((char*)dst + i)),
-                   "l"((const char*)src + i)
-                   : "memory");
-  } else {
-    asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" ::"r"(st_smem(dst)), "l"(src), "n"(BYTES) : "memory");
-  }
-}
-__device__ __forceinline__ void st_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void st_wait() {
-  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
-}
-
-// NVAL stored values of a chunk already in shared memory, widened to fp32.
-template <typename T, int NVAL>
-__device__ __forceinline__ void sm_chunk(const T* p, float* out) {
-  constexpr int NW = NVAL * (int)sizeof(T) / 4;
-  unsigned w[NW];
-  if constexpr (NW == 1) {
-    w[0] = *reinterpret_cast<const unsigned*>(p);
-  } else if constexpr (NW == 2) {
-    const uint2 v = *reinterpret_cast<const uint2*>(p);
-    w[0] = v.x;
-    w[1] = v.y;
-  } else {
-#pragma unroll
-    for (int i = 0; i < NW; i += 4) {
-      const uint4 v = reinterpret_cast<const uint4*>(p)[i / 4];
-      w[i] = v.x;
-      w[i + 1] = v.y;
-      w[i + 2] = v.z;
-      w[i + 3] = v.w;
-    }
-  }
-  if constexpr (std::is_same<T, float>::value) {
-#pragma unroll
-    for (int i = 0; i < NW; ++i) out[i] = __uint_as_float(w[i]);
-  } else {
-#pragma unroll
-    for (int i = 0; i < NW; ++i) {
-      out[2 * i] = __uint_as_float(w[i] << 16);
-      out[2 * i + 1] = __uint_as_float(w[i] & 0xffff0000u);
-    }
-  }
-}
 
 // Shared-memory plan of a block of nthr threads: the K^{-1} chunk ring (slot q
 // of thread i at (q nthr + i) CK bytes), the w chunk ring, the epilogue slots
@@ -178,12 +79,6 @@ struct StagedPlan {
   }
   __host__ __device__ static size_t bytes(const StagedGeo& sg) { return offs_off(sg) + sizeof(int) * NJ * S; }
 };
-
-// cp.async of 4 bytes, zero-filled when !valid (then src is not read).
-__device__ __forceinline__ void st_copy4z(void* dst, const void* src, bool valid) {
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(st_smem(dst)), "l"(src), "r"(valid ? 4 : 0)
-               : "memory");
-}
 
 // Blocks per SM the register budget must allow: 4 of 256 threads (64
 // registers); 3-D fp32 chunks run in blocks of 128 threads and get more.
@@ -488,9 +383,10 @@ static int restage_t(const Geo& g, SmLevel& SL, int cand, cudaStream_t s) {
 }
 
 // (Re)builds the staged chunks of a reduced factored Q2-Q1 level for S threads
-// per subdomain (2-D: 1 or 2; 3-D: 2 or 4) and the cand-th tiling candidate;
-// S = 0 frees them (the grouped kernel is used again).  RAV_ERR_ARG when
-// there is no such candidate.
+// per subdomain and the cand-th tiling candidate: S = 1 the streamed kernel of
+// stream.cu (one tiling), 2-D S = 2, 3-D S = 2 or 4 the kernel above; S = 0
+// frees them (the grouped kernel is used again).  RAV_ERR_ARG when there is no
+// such candidate.
 int staged_build(rav_smoother* sm, int level, int S, cudaStream_t s, int cand) {
   SmLevel& SL = sm->lev[level];
   const Geo& g = sm->mg->lev[level].g;
@@ -498,9 +394,9 @@ int staged_build(rav_smoother* sm, int level, int S, cudaStream_t s, int cand) {
     staged_free(SL);
     return RAV_OK;
   }
+  if (S == 1) return cand == 0 ? stream_build(sm, level, s) : RAV_ERR_ARG;
   const bool bf = sm->prec == RAV_BF16_FACT;
   if (g.dim == 2) {
-    if (S == 1) return bf ? restage_t<2, __nv_bfloat16, 1>(g, SL, cand, s) : restage_t<2, float, 1>(g, SL, cand, s);
     if (S == 2) return bf ? restage_t<2, __nv_bfloat16, 2>(g, SL, cand, s) : restage_t<2, float, 2>(g, SL, cand, s);
   } else {
     if (S == 2) return bf ? restage_t<3, __nv_bfloat16, 2>(g, SL, cand, s) : restage_t<3, float, 2>(g, SL, cand, s);
@@ -523,15 +419,14 @@ void staged_launch(const rav_smoother* sm, int level, const double* omega, const
                    cudaStream_t s) {
   const SmLevel& SL = sm->lev[level];
   const Geo& g = sm->mg->lev[level].g;
+  if (SL.staged == 1) {
+    stream_launch(sm, level, omega, r32, x, s);
+    return;
+  }
   const bool bf = sm->prec == RAV_BF16_FACT;
   if (g.dim == 2) {
-    if (SL.staged == 1) {
-      if (bf) launch_staged_t<2, __nv_bfloat16, 1>(g, SL, omega, r32, x, s);
-      else launch_staged_t<2, float, 1>(g, SL, omega, r32, x, s);
-    } else {
-      if (bf) launch_staged_t<2, __nv_bfloat16, 2>(g, SL, omega, r32, x, s);
-      else launch_staged_t<2, float, 2>(g, SL, omega, r32, x, s);
-    }
+    if (bf) launch_staged_t<2, __nv_bfloat16, 2>(g, SL, omega, r32, x, s);
+    else launch_staged_t<2, float, 2>(g, SL, omega, r32, x, s);
   } else {
     if (SL.staged == 2) {
       if (bf) launch_staged_t<3, __nv_bfloat16, 2>(g, SL, omega, r32, x, s);
