@@ -515,6 +515,17 @@ int64_t rav_kernel_launches(void);
  * SM.  Synchronises the stream.  The paper has no counterpart. */
 int rav_fp64_fma_rate(double* tflops_host, rav_stream stream);
 
+/* Measured rate in GB/s of a plain read of `bytes` bytes (rounded down to 16)
+ * on the current device: a coalesced grid-stride kernel of 16-byte
+ * evict-first loads, 8 x 256 threads per SM, after an L2 flush (a write of
+ * twice the L2 size), the mean of 10 timed launches (CUDA events on stream)
+ * after a warm-up.  A memory-bound kernel that moves `bytes` can be set
+ * against it: at tens to hundreds of MB the rate of such a short read stays
+ * well below the large-copy bandwidth (launch, ramp-up and tail).  Allocates
+ * and frees bytes + 2 x L2 of device memory; synchronises the stream.
+ * RAV_ERR_ARG for bytes outside [16, 64 GiB].  The paper has no counterpart. */
+int rav_hbm_read_rate(int64_t bytes, double* gbs_host, rav_stream stream);
+
 const char* rav_strerror(int code);
 
 #ifdef __cplusplus

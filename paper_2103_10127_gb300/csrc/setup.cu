@@ -1476,6 +1476,63 @@ extern "C" int rav_fp64_fma_rate(double* tflops_host, rav_stream stream) {
   return rc;
 }
 
+namespace rav {
+// Plain read of n16 16-byte words (evict-first, grid-stride, coalesced); the
+// checksum keeps the loads live.
+__global__ void __launch_bounds__(256) k_read_probe(const uint4* __restrict__ a, int64_t n16, unsigned* out) {
+  unsigned acc = 0;
+  const int64_t st = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n16; i += st) {
+    const uint4 v = __ldcs(a + i);
+    acc += v.x ^ v.y ^ v.z ^ v.w;
+  }
+  if (acc == 0x9e3779b9u) out[0] = acc;  // never true for the zero-filled buffer
+}
+__global__ void __launch_bounds__(256) k_l2_flush(uint4* f, int64_t n16) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n16; i += (int64_t)gridDim.x * blockDim.x)
+    f[i] = make_uint4((unsigned)i, 0u, 0u, 0u);
+}
+}  // namespace rav
+
+extern "C" int rav_hbm_read_rate(int64_t bytes, double* gbs_host, rav_stream stream) {
+  if (!gbs_host || bytes < 16 || bytes > (int64_t(64) << 30)) return RAV_ERR_ARG;
+  cudaStream_t s = S(stream);
+  int dev = 0, nsm = 0, l2 = 0;
+  RAV_CUDA(cudaGetDevice(&dev));
+  RAV_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+  RAV_CUDA(cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, dev));
+  const int64_t n16 = bytes / 16, nfl = 2 * (int64_t)std::max(l2, 1 << 20) / 16;
+  uint4 *buf = nullptr, *fl = nullptr;
+  unsigned* sink = nullptr;
+  int rc = RAV_OK;
+  if (cudaMalloc(&buf, n16 * 16) != cudaSuccess || cudaMalloc(&fl, nfl * 16) != cudaSuccess ||
+      cudaMalloc(&sink, sizeof(unsigned)) != cudaSuccess)
+    rc = RAV_ERR_CUDA;
+  if (rc == RAV_OK && cudaMemsetAsync(buf, 0, n16 * 16, s) != cudaSuccess) rc = RAV_ERR_CUDA;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (rc == RAV_OK && (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess))
+    rc = RAV_ERR_CUDA;
+  double tot = 0.0;
+  for (int r = 0; r < 11 && rc == RAV_OK; ++r) {  // the first run is a warm-up
+    k_l2_flush<<<nsm * 4, 256, 0, s>>>(fl, nfl);
+    cudaEventRecord(e0, s);
+    k_read_probe<<<nsm * 8, 256, 0, s>>>(buf, n16, sink);
+    cudaEventRecord(e1, s);
+    float ms = 0.f;
+    if (cudaGetLastError() != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+        cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess || ms <= 0.f)
+      rc = RAV_ERR_CUDA;
+    if (r > 0) tot += ms;
+  }
+  if (rc == RAV_OK) *gbs_host = (double)n16 * 16.0 / (tot / 10 * 1e-3) / 1e9;
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  cudaFree(buf);
+  cudaFree(fl);
+  cudaFree(sink);
+  return rc;
+}
+
 extern "C" int rav_profile_enable(rav_mg* mg, unsigned kind_mask, int level) {
   if (!mg || level < -1 || level >= mg->nlev) return RAV_ERR_ARG;
   RAV_TRY(prof_collect(mg));

@@ -57,6 +57,9 @@ def test_invalid_arguments_are_rejected_without_a_gpu():
     assert lib.solve(None, None, None, None, None, None, None) == -1
     assert lib.rav_set_residual_split(None, 0, 4) == -1
     assert lib.rav_get_residual_split(None, 0) == -1
+    rate = ctypes.c_double()
+    assert lib.rav_hbm_read_rate(8, ctypes.byref(rate), None) == -1  # fewer than 16 bytes
+    assert lib.rav_hbm_read_rate(1 << 20, None, None) == -1
     assert lib.rav_strerror(-3) == b"singular subdomain system"
 
 

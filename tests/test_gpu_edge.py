@@ -1,5 +1,7 @@
 """Edge cases of the CUDA path through the C ABI: the degenerate hierarchies,
 weights and inputs the method admits, against the oracle or exact answers."""
+import ctypes
+
 import numpy as np
 import pytest
 
@@ -12,7 +14,7 @@ if not torch.cuda.is_available():
     pytest.skip("needs a CUDA device", allow_module_level=True)
 
 import paper_2103_10127_gb300 as R  # noqa: E402
-from paper_2103_10127_gb300 import inputs  # noqa: E402
+from paper_2103_10127_gb300 import _capi, inputs  # noqa: E402
 
 
 def cpu(t):
@@ -109,3 +111,18 @@ def test_invalid_calls_are_rejected_without_side_effects():
         with pytest.raises(R.RavError):
             bad()
     assert np.array_equal(cpu(x), x0)
+
+
+def test_measured_read_rate_is_a_bandwidth():
+    """rav_hbm_read_rate (the size-matched context of the memory-bound
+    rooflines): a positive finite GB/s below any HBM3e figure, and a read of
+    256 MB runs at least as fast per byte as one of 1 MB (launch and ramp-up
+    weigh less)."""
+    lib = _capi.load()
+    rates = []
+    for nbytes in (1 << 20, 256 << 20):
+        r = ctypes.c_double()
+        assert lib.rav_hbm_read_rate(nbytes, ctypes.byref(r), None) == 0
+        assert 10.0 < r.value < 20000.0
+        rates.append(r.value)
+    assert rates[1] >= rates[0]
