@@ -264,6 +264,39 @@ def test_staged_apply_matches_grouped_and_oracle(case, prec):
         sm.apply_staged(case["nlev"] - 1, 3)
 
 
+@pytest.mark.parametrize("prec", [R.F32_FACT, R.BF16_FACT], ids=["f32", "bf16"])
+@pytest.mark.parametrize("case", [dict(dim=2, N=40, nlev=2, graded=True, nblobs=6, bc=O.BC_NOSLIP),
+                                  dict(dim=3, N=10, nlev=2, nblobs=5)], ids=["2d-40-graded-blobs", "3d-10-blobs"])
+def test_streamed_apply_across_tiles_and_ragged_edges(case, prec):
+    """The one-thread-per-subdomain streamed apply on a level of several of its
+    fixed tiles (2-D 41^2 vertices: 3 x 2 tiles of 16 x 24, ragged in both
+    axes, three slabs each; 3-D 11^3: 4 tiles of 3^3 per axis, the last one
+    holding a single vertex layer): one step with per-subdomain damping equals
+    the grouped kernel's to fp32 roundoff and the oracle's reduced-storage step
+    within the same bound, and leaves the Dirichlet DoFs untouched."""
+    mg, orc = make_pair(**case)
+    lev = case["nlev"] - 1
+    sm = R.Smoother(mg, R.RAV, prec, 0.5)
+    orc.setup_smoother(O.RAV, 0.5, {R.F32_FACT: O.F32_FACT, R.BF16_FACT: O.BF16_FACT}[prec])
+    rng = np.random.default_rng(37)
+    n, npatch = mg.n(lev), mg.counts(lev)["n_p"]
+    w = 0.3 + 0.4 * rng.random(npatch)
+    sm.set_omega(lev, torch.from_numpy(w).cuda())
+    orc.set_omega(lev, w.astype(np.float32).astype(np.float64))
+    x, b = rng.standard_normal(n), rng.standard_normal(n)
+    want = orc.smooth(lev, x, b, 1) - x
+    out = []
+    for S in (0, 1):
+        assert sm.apply_staged(lev, S) == S
+        xg = gpu(x)
+        sm.smooth(lev, xg, gpu(b), 1)
+        out.append(cpu(xg) - x)
+    grouped, got = out
+    assert np.linalg.norm(got - grouped) <= 1e-5 * np.linalg.norm(grouped)
+    assert np.linalg.norm(got - want) <= 1e-5 * np.linalg.norm(want)
+    assert np.array_equal(got[grouped == 0.0], grouped[grouped == 0.0])
+
+
 @pytest.mark.parametrize("case", CASES[:3], ids=IDS[:3])
 def test_vcycle_matches(case):
     mg, orc = make_pair(**case)
