@@ -27,14 +27,14 @@
 //   K^{-1}[q, n], q = 0 .. 2^d - 1, and in a second array the d values
 //   w(n, c) (zero padded to WC), n = s + S j (zero chunks past the last box
 //   node), so the threads of a block read one contiguous run per step.  Each
-//   thread keeps kStRing steps of its chunks in flight with cp.async into a
-//   ring of shared-memory slots and waits only for its own oldest copy.  1/s
-//   per subdomain slot.  The chunks are rebuilt from the grouped factored
+//   thread keeps kStRing steps of its chunks in flight in registers.  1/s per
+//   subdomain slot.  The chunks are rebuilt from the grouped factored
 //   storage (k_restage), so they hold exactly the same rounded values.
 #include <cuda_bf16.h>
 
 #include <algorithm>
 #include <cmath>
+#include <functional>
 #include <type_traits>
 
 #include "box.cuh"
@@ -52,15 +52,13 @@ struct StagedBox {
 };
 
 // Streaming of the chunks: every thread keeps kStRing node steps of its own
-// chunks in flight with cp.async (global -> shared, no registers held), in a
-// per-thread ring of shared-memory slots, and waits only for its own oldest
-// copy group before using it.
+// chunks in flight in registers (evict-first loads; the loop is unrolled by
+// kStRing so that every slot is known at compile time).
 constexpr int kStRing = 4;
 
-// Shared-memory plan of a block of nthr threads: the K^{-1} chunk ring (slot q
-// of thread i at (q nthr + i) CK bytes), the w chunk ring, the epilogue slots
-// (per thread the x values and w chunks of the owned nodes it writes, fetched
-// at the start), the staged residual nodes, the box-node offset table.
+// Shared-memory plan of a block of nthr threads: the epilogue slots (per
+// thread the x values and w chunks of the owned nodes it writes, fetched at
+// the start), the staged residual nodes, the box-node offset table.
 template <int D, typename T, int S>
 struct StagedPlan {
   static constexpr int NV = StagedBox<D>::NV, NON = StagedBox<D>::NON, WC = StagedBox<D>::WC;
@@ -70,9 +68,7 @@ struct StagedPlan {
   static constexpr int OFFX = (CW + 7) / 8 * 8;               // per owned node: its w chunk, then
   static constexpr int BLK = (OFFX + 8 * D + 15) / 16 * 16;   // its d fp64 x values (16-byte blocks)
   static constexpr int EPI = OWN * BLK;
-  __host__ __device__ static size_t ring_k(int nthr) { return (size_t)kStRing * nthr * CK; }
-  __host__ __device__ static size_t ring(int nthr) { return (size_t)kStRing * nthr * (CK + CW); }
-  __host__ __device__ static size_t epi_off(int nthr) { return ring(nthr); }
+  __host__ __device__ static size_t epi_off(int) { return 0; }
   __host__ __device__ static size_t nodes_off(int nthr) { return epi_off(nthr) + (size_t)EPI * nthr; }
   __host__ __device__ static size_t offs_off(const StagedGeo& sg) {
     return nodes_off(sg.wpt * 32) + (size_t)sg.sx * sg.sy * sg.sz * (D == 3 ? 16 : 8);
@@ -80,15 +76,20 @@ struct StagedPlan {
   __host__ __device__ static size_t bytes(const StagedGeo& sg) { return offs_off(sg) + sizeof(int) * NJ * S; }
 };
 
-// Blocks per SM the register budget must allow: 4 of 256 threads (64
-// registers); 3-D fp32 chunks run in blocks of 128 threads and get more.
+// Launch bounds: 3 blocks of 256 threads per SM (85 registers: the
+// accumulators and kStRing chunks in flight); 3-D fp32 chunks are twice as
+// large and run in blocks of at most 128 threads, 4 per SM (128 registers).
+template <int D, typename T>
+constexpr int staged_max_threads() {
+  return (D == 3 && sizeof(T) == 4) ? 128 : 256;
+}
 template <int D, typename T>
 constexpr int staged_min_blocks() {
-  return (D == 3 && sizeof(T) == 4) ? 3 : 4;
+  return (D == 3 && sizeof(T) == 4) ? 4 : 3;
 }
 
 template <int D, typename T, int S>
-__global__ void __launch_bounds__(256, staged_min_blocks<D, T>()) k_rav_apply_staged(Geo g, StagedGeo sg, const T* __restrict__ kq,
+__global__ void __launch_bounds__(staged_max_threads<D, T>(), staged_min_blocks<D, T>()) k_rav_apply_staged(Geo g, StagedGeo sg, const T* __restrict__ kq,
                                                             const T* __restrict__ wq, const float* __restrict__ sinv,
                                                             const double* __restrict__ omega,
                                                             const float* __restrict__ r32, double* __restrict__ x) {
@@ -98,8 +99,6 @@ __global__ void __launch_bounds__(256, staged_min_blocks<D, T>()) k_rav_apply_st
   extern __shared__ __align__(128) uint8_t sraw[];
   const int nthr = sg.wpt * 32;
   const int tid = threadIdx.x;
-  uint8_t* ringk = sraw;
-  uint8_t* ringw = sraw + P::ring_k(nthr);
   uint8_t* epi = sraw + P::epi_off(nthr) + (size_t)tid * P::EPI;
   RV* tile = reinterpret_cast<RV*>(sraw + P::nodes_off(nthr));
   int* offs = reinterpret_cast<int*>(sraw + P::offs_off(sg));
@@ -161,18 +160,23 @@ __global__ void __launch_bounds__(256, staged_min_blocks<D, T>()) k_rav_apply_st
     }
   }
   st_commit();
-  // groups 1 .. RING: the first node steps of this thread's chunk stream
+  // the first node steps of this thread's chunk stream, in flight while the tile lands
   const T* kme = kq + ((size_t)t * NJ * cstride + tid) * NON;
   const T* wme = wq + ((size_t)t * NJ * cstride + tid) * WC;
-  auto issue = [&](int j) {
-    const int q = j % kStRing;
-    st_copy<CK>(ringk + ((size_t)q * nthr + tid) * CK, kme + (size_t)j * cstride * NON);
-    st_copy<CW>(ringw + ((size_t)q * nthr + tid) * CW, wme + (size_t)j * cstride * WC);
-  };
+  constexpr int R = kStRing;
+  RawChunk<CK> kb[R];
+  RawChunk<CW> wb[R];
 #pragma unroll
-  for (int j = 0; j < kStRing; ++j) {
-    if (active && j < NJ) issue(j);
-    st_commit();
+  for (int j = 0; j < R; ++j) {
+    if (active && j < NJ) {
+      kb[j] = ld_raw<CK>(kme + (size_t)j * cstride * NON);
+      wb[j] = ld_raw<CW>(wme + (size_t)j * cstride * WC);
+    } else {
+#pragma unroll
+      for (int i = 0; i < CK / 4; ++i) kb[j].w[i] = 0u;
+#pragma unroll
+      for (int i = 0; i < CW / 4; ++i) wb[j].w[i] = 0u;
+    }
   }
   for (int n = tid; n < NJ * S; n += blockDim.x) {
     int off = 0;  // padded node: any staged node (its stored values are zero)
@@ -182,7 +186,7 @@ __global__ void __launch_bounds__(256, staged_min_blocks<D, T>()) k_rav_apply_st
     }
     offs[n] = off;
   }
-  st_wait<kStRing>();  // group 0 has landed
+  st_wait<0>();  // group 0 has landed
   __syncthreads();
   if (!active) return;
   const int base = ((D == 3 ? 2 * lz * sg.sy : 0) + 2 * ly) * sg.sx + 2 * lx;
@@ -191,27 +195,33 @@ __global__ void __launch_bounds__(256, staged_min_blocks<D, T>()) k_rav_apply_st
   for (int q = 0; q < NON; ++q)
 #pragma unroll
     for (int c = 0; c < D; ++c) y[q][c] = 0.f;
-#pragma unroll 2
-  for (int j = 0; j < NJ; ++j) {
-    st_wait<kStRing - 1>();  // the group of step j has landed
-    const int q = j % kStRing;
-    float kf[NON], wf[WC];
-    sm_chunk<T, NON>(reinterpret_cast<const T*>(ringk + ((size_t)q * nthr + tid) * CK), kf);
-    sm_chunk<T, WC>(reinterpret_cast<const T*>(ringw + ((size_t)q * nthr + tid) * CW), wf);
-    const RV rv = tile[base + offs[s + S * j]];
-    float rc[D];
-    rc[0] = rv.x;
-    rc[1] = rv.y;
-    if constexpr (D == 3) rc[2] = reinterpret_cast<const float4&>(rv).z;
+#pragma unroll 1
+  for (int j0 = 0; j0 < NJ; j0 += R) {
 #pragma unroll
-    for (int qq = 0; qq < NON; ++qq)
+    for (int q = 0; q < R; ++q) {  // slot q holds step j = j0 + q
+      const int j = j0 + q;
+      if (j < NJ) {
+        float kf[NON], wf[WC];
+        widen_words<T, CK / 4>(kb[q].w, kf);
+        widen_words<T, CW / 4>(wb[q].w, wf);
+        const RV rv = tile[base + offs[s + S * j]];
+        float rc[D];
+        rc[0] = rv.x;
+        rc[1] = rv.y;
+        if constexpr (D == 3) rc[2] = reinterpret_cast<const float4&>(rv).z;
 #pragma unroll
-      for (int c = 0; c < D; ++c) y[qq][c] = fmaf(kf[qq], rc[c], y[qq][c]);
+        for (int qq = 0; qq < NON; ++qq)
 #pragma unroll
-    for (int c = 0; c < D; ++c) tw = fmaf(wf[c], rc[c], tw);
-    // the slot is read (its values are in the FMAs above): refill it with step j + ring
-    if (j + kStRing < NJ) issue(j + kStRing);
-    st_commit();
+          for (int c = 0; c < D; ++c) y[qq][c] = fmaf(kf[qq], rc[c], y[qq][c]);
+#pragma unroll
+        for (int c = 0; c < D; ++c) tw = fmaf(wf[c], rc[c], tw);
+        // the slot is read (its values are in the FMAs above): refill it with step j + R
+        if (j + R < NJ) {
+          kb[q] = ld_raw<CK>(kme + (size_t)(j + R) * cstride * NON);
+          wb[q] = ld_raw<CW>(wme + (size_t)(j + R) * cstride * WC);
+        }
+      }
+    }
   }
   const int lane = tid & 31;
   const unsigned gmask = S == 32 ? 0xffffffffu : (((1u << S) - 1u) << (lane & ~(S - 1)));
@@ -289,13 +299,15 @@ using namespace rav;
 
 // Tiles of vertices for a level of N cells per axis and S threads per
 // subdomain: 64 to max_threads threads per block and at most 100 KiB of shared
-// memory (ring of streamed chunks and epilogue slots: ring_per_warp bytes per
-// warp, plus the staged residual nodes).  Candidates are ranked by idle thread
-// slots (tiles past the grid's last vertex) and the use of the last wave, with
-// a penalty for halo (staged nodes per owned node); cand picks the cand-th best
-// of distinct block counts (the set-up tuner times the first few).  tx == 0:
-// no candidate.
-StagedGeo staged_tiles(int D, int N, int S, size_t ring_per_warp, int max_threads, int cand) {
+// memory (epilogue slots: epi_per_warp bytes per warp, plus the staged residual
+// nodes).  Candidates are ranked by idle thread slots (tiles past the grid's
+// last vertex) and the use of the last wave, with a penalty for halo (staged
+// nodes per owned node); per_sm_of(threads, shared bytes) gives a candidate's
+// resident blocks per SM (the kernel's registers, shared memory and threads),
+// nsm the SM count.  cand picks the cand-th best of distinct block counts (the
+// set-up tuner times the first few).  tx == 0: no candidate.
+StagedGeo staged_tiles(int D, int N, int S, size_t epi_per_warp, int max_threads, int cand,
+                       const std::function<int(int, size_t)>& per_sm_of, int nsm) {
   const int mv = N + 1;
   struct Cand {
     double score;
@@ -314,13 +326,12 @@ StagedGeo staged_tiles(int D, int N, int S, size_t ring_per_warp, int max_thread
         const double slots = tiles * wpt * 32;
         const double used = (D == 3 ? (double)mv * mv * mv : (double)mv * mv) * S;
         const double nodes = (2.0 * tx + 3) * (2.0 * ty + 3) * (D == 3 ? 2.0 * tz + 3 : 1.0);
-        const double smem = nodes * (D == 3 ? 16 : 8) + (double)ring_per_warp * wpt;
+        const double smem = nodes * (D == 3 ? 16 : 8) + (double)epi_per_warp * wpt;
         if (smem > 100 * 1024) continue;
         const double halo = nodes / (ts * (D == 3 ? 8.0 : 4.0));
-        // blocks per SM (shared memory with 1 KiB reserved per block, threads,
-        // 64 registers per thread) and the share of the last wave's slots used
-        const int per_sm = std::max(1, std::min({(int)(228 * 1024 / (smem + 1024)), 2048 / (wpt * 32), 32}));
-        const double slots_gpu = 152.0 * per_sm;
+        // resident blocks per SM and the share of the last wave's slots used
+        const int per_sm = std::max(1, per_sm_of(wpt * 32, (size_t)smem + 512));
+        const double slots_gpu = (double)nsm * per_sm;
         const double wave_use = tiles / (std::ceil(tiles / slots_gpu) * slots_gpu);
         const double score = slots / used * (1.0 + 0.15 * halo) / wave_use;
         all.push_back({score, StagedGeo{tx, ty, tz, ntx, nty, ntz, wpt, 2 * tx + 3, 2 * ty + 3,
@@ -352,10 +363,21 @@ static int restage_t(const Geo& g, SmLevel& SL, int cand, cudaStream_t s) {
   using P = StagedPlan<D, T, S>;
   using SB = StagedBox<D>;
   constexpr int NJ = P::NJ;
-  // 3-D fp32 chunks are twice as large: smaller blocks keep two per SM
-  const int max_thr = (D == 3 && sizeof(T) == 4) ? 128 : 256;
-  const StagedGeo sg =
-      staged_tiles(D, g.N, S, (size_t)kStRing * 32 * (P::CK + P::CW) + 32 * P::EPI, max_thr, cand);
+  const int max_thr = staged_max_threads<D, T>();
+  // the attribute is per kernel instance, shared by every level: allow the
+  // largest plan staged_tiles admits (100 KiB and the small tables after it)
+  RAV_CUDA(cudaFuncSetAttribute(k_rav_apply_staged<D, T, S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                104 * 1024));
+  int dev = 0, nsm = 0;
+  RAV_CUDA(cudaGetDevice(&dev));
+  RAV_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+  auto per_sm_of = [](int thr, size_t smem) {
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_rav_apply_staged<D, T, S>, thr, smem) != cudaSuccess)
+      return 1;
+    return nb;
+  };
+  const StagedGeo sg = staged_tiles(D, g.N, S, (size_t)32 * P::EPI, max_thr, cand, per_sm_of, nsm);
   if (sg.tx == 0) return RAV_ERR_ARG;
   const int64_t tiles = (int64_t)sg.ntx * sg.nty * sg.ntz;
   const int64_t chunks = tiles * sg.wpt * NJ * 32;
@@ -372,10 +394,6 @@ static int restage_t(const Geo& g, SmLevel& SL, int cand, cudaStream_t s) {
   k_restage<D, T, S><<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(g, sg, (const T*)SL.inv, (const T*)SL.ws, lg,
                                                                   (T*)SL.skq, (T*)SL.swq, SL.ssinv);
   RAV_CUDA(cudaGetLastError());
-  // the attribute is per kernel instance, shared by every level: allow the
-  // largest plan staged_tiles admits (100 KiB and the small tables after it)
-  RAV_CUDA(cudaFuncSetAttribute(k_rav_apply_staged<D, T, S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                104 * 1024));
   if (P::bytes(sg) > 104 * 1024) return RAV_ERR_ARG;
   SL.sgeo = sg;
   SL.staged = S;

@@ -57,33 +57,6 @@ struct StreamTile<3> {
 
 constexpr int kSmRing = 5;  // node steps in flight per thread (divides the 25 nodes of a plane)
 
-// BYTES of one chunk as 32-bit words, read once (evict-first).
-template <int BYTES>
-struct RawChunk {
-  unsigned w[BYTES / 4];
-};
-template <int BYTES>
-__device__ __forceinline__ RawChunk<BYTES> ld_raw(const void* p) {
-  RawChunk<BYTES> r;
-  if constexpr (BYTES == 4) {
-    r.w[0] = __ldcs(reinterpret_cast<const unsigned*>(p));
-  } else if constexpr (BYTES == 8) {
-    const uint2 v = __ldcs(reinterpret_cast<const uint2*>(p));
-    r.w[0] = v.x;
-    r.w[1] = v.y;
-  } else {
-#pragma unroll
-    for (int i = 0; i < BYTES / 16; ++i) {
-      const uint4 v = __ldcs(reinterpret_cast<const uint4*>(p) + i);
-      r.w[4 * i] = v.x;
-      r.w[4 * i + 1] = v.y;
-      r.w[4 * i + 2] = v.z;
-      r.w[4 * i + 3] = v.w;
-    }
-  }
-  return r;
-}
-
 template <int D, typename T>
 struct StreamPlan {
   using ST = StreamTile<D>;
