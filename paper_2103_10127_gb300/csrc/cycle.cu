@@ -160,6 +160,14 @@ __global__ void k_prolong(Geo gf, Geo gc, XferTab T, const double* __restrict__ 
     }
     if (bnd) return;
     const int c0 = T.pc2[0][I[0]], c1 = T.pc2[1][I[1]], c2 = D == 3 ? T.pc2[2][I[2]] : 1;
+    // axis-0 entries are the same for every row: loaded once
+    int k0[3];
+    double w0[3];
+#pragma unroll
+    for (int j0 = 0; j0 < 3; ++j0) {
+      k0[j0] = j0 < c0 ? D * T.pk2[0][3 * I[0] + j0] : 0;
+      w0[j0] = j0 < c0 ? T.pw2[0][3 * I[0] + j0] : 0.0;
+    }
     double acc[D];
 #pragma unroll
     for (int c = 0; c < D; ++c) acc[c] = 0.0;
@@ -173,8 +181,8 @@ __global__ void k_prolong(Geo gf, Geo gc, XferTab T, const double* __restrict__ 
 #pragma unroll
         for (int j0 = 0; j0 < 3; ++j0) {
           if (j0 < c0) {
-            const double ww = w12 * T.pw2[0][3 * I[0] + j0];
-            const int base = rowbase + D * T.pk2[0][3 * I[0] + j0];
+            const double ww = w12 * w0[j0];
+            const int base = rowbase + k0[j0];
 #pragma unroll
             for (int c = 0; c < D; ++c) acc[c] += ww * xc[base + c];
           }
@@ -230,6 +238,14 @@ __global__ void k_restrict_c(Geo gf, Geo gc, XferTab T, const double* __restrict
     }
     if (!bnd) {
       const int c0 = T.rc2[0][K[0]], c1 = T.rc2[1][K[1]], c2 = D == 3 ? T.rc2[2][K[2]] : 1;
+      // axis-0 entries are the same for every row: loaded once
+      int k0[7];
+      double w0[7];
+#pragma unroll
+      for (int j0 = 0; j0 < 7; ++j0) {
+        k0[j0] = j0 < c0 ? D * T.rk2[0][7 * K[0] + j0] : 0;
+        w0[j0] = j0 < c0 ? T.rw2[0][7 * K[0] + j0] : 0.0;
+      }
       for (int pr = sub; pr < c2 * c1; pr += tl) {
         const int j2 = pr / c1, j1 = pr % c1;
         const int I2 = D == 3 ? T.rk2[2][7 * K[2] + j2] : 0;
@@ -241,8 +257,8 @@ __global__ void k_restrict_c(Geo gf, Geo gc, XferTab T, const double* __restrict
 #pragma unroll
         for (int j0 = 0; j0 < 7; ++j0) {
           if (j0 < c0) {
-            const double ww = w12 * T.rw2[0][7 * K[0] + j0];
-            const int64_t base = rowbase + D * T.rk2[0][7 * K[0] + j0];
+            const double ww = w12 * w0[j0];
+            const int64_t base = rowbase + k0[j0];
 #pragma unroll
             for (int c = 0; c < D; ++c) acc[c] += ww * rf[base + c];
           }
