@@ -185,6 +185,23 @@ int rav_get_residual_split(const rav_mg* mg, int level);
 int rav_set_residual_blocked(rav_mg* mg, int level, int enable, rav_stream stream);
 int rav_get_residual_blocked(const rav_mg* mg, int level);
 
+/* FP32 residuals on the levels between the coarsest and the finest that hold
+ * at least min_dofs DoFs (enable = 1; 0 returns to fp64 everywhere; smaller
+ * levels are latency-bound and keep fp64): r = b - L x (Eq. 10) there with the operator values
+ * rounded to fp32, x rounded to fp32 before each residual (one conversion
+ * kernel), products summed in fp32 and r = b - sum formed in fp64.  The finest
+ * level's residual, which measures convergence and feeds the outer loop, and
+ * the coarse solve stay fp64.  On the levels in between r then
+ * carries fp32 rounding (about 2^-24 of sum_k |a_k x_k| per row), which the
+ * coarse-grid correction tolerates like the reduced-precision subdomain
+ * inverses.  Allocates an fp32 copy of each such level's operator and of its
+ * x, synchronises the stream and drops the captured cycles of every smoother
+ * of mg.  RAV_ERR_ARG for other values or a negative min_dofs.
+ * rav_get_coarse_residual_f32 returns
+ * 1 when it is on, 0 when off.  The paper has no counterpart. */
+int rav_set_coarse_residual_f32(rav_mg* mg, int enable, int64_t min_dofs, rav_stream stream);
+int rav_get_coarse_residual_f32(const rav_mg* mg);
+
 /* Same residual r = b - L x on level l as rav_residual, plus ||r||_2 written to
  * the caller's device scalar norm_dev, with no memory allocation of any kind
  * and no host synchronisation.  The paper has no counterpart: this exists for

@@ -133,6 +133,19 @@ class Multigrid:
             raise RavError(k, "rav_get_residual_split")
         return k
 
+    def coarse_residual_f32(self, enable=None, min_dofs=0, stream=None):
+        """FP32 residuals on the levels between the coarsest and the finest with
+        at least min_dofs DoFs (rav_set_coarse_residual_f32); sets it when
+        given, returns 0/1."""
+        lib = _capi.load()
+        if enable is not None:
+            check(lib.rav_set_coarse_residual_f32(self.h, int(bool(enable)), int(min_dofs), _stream(stream)),
+                  "rav_set_coarse_residual_f32")
+        k = lib.rav_get_coarse_residual_f32(self.h)
+        if k < 0:
+            raise RavError(k, "rav_get_coarse_residual_f32")
+        return k
+
     def residual_blocked(self, level, enable=None, stream=None):
         """Node-blocked residual on `level` (Q2-Q1); sets it when given, returns 0/1."""
         lib = _capi.load()

@@ -58,6 +58,8 @@ _SIGS = {
     "batch_set_tensor_apply": (I32, [P, I32, P]),
     "rav_fp64_fma_rate": (I32, [ctypes.POINTER(F64), P]),
     "rav_hbm_read_rate": (I32, [ctypes.c_int64, ctypes.POINTER(F64), P]),
+    "rav_set_coarse_residual_f32": (I32, [P, I32, ctypes.c_int64, P]),
+    "rav_get_coarse_residual_f32": (I32, [P]),
     "batch_tensor_apply_levels": (I32, [P]),
     "rav_get_apply_staged": (I32, [P, I32]),
     "rav_set_fused_smoothing": (I32, [P, I32]),

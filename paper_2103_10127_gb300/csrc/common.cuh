@@ -83,6 +83,11 @@ struct Level {
   int32_t* slen = nullptr;   // row length of slice s (1 = Dirichlet identity rows)
   int32_t* scol = nullptr;
   double* sval = nullptr;
+  // fp32 residual on levels between the coarsest and the finest
+  // (rav_set_coarse_residual_f32): sval rounded to fp32 in the same slots, and
+  // a work copy of x in fp32
+  float* sval32 = nullptr;
+  float* x32 = nullptr;
   // node-blocked residual (blocked.cu, Q2-Q1): velocity nodes in slices of 32
   // by (K, B) entry counts, pressure rows in a sliced-ELL copy of their own;
   // rblock: the residual uses it (chosen per level at set-up)
@@ -141,6 +146,7 @@ struct rav_mg {
   int64_t prof_cnt[rav::kMaxLevels][5] = {};
   // captured V-cycles, replayed with cudaGraphLaunch (see vcycle in cycle.cu)
   bool use_graphs = true;
+  bool coarse_f32 = false;  // fp32 residuals on the levels between the coarsest and the finest
   cudaStream_t cap_stream = nullptr;
   struct GraphEntry {
     const rav_smoother* sm;

@@ -14,12 +14,16 @@ namespace rav {
 // slice runs the same trip count, so each fp64 FMA instruction is fully used
 // (on GB300 an fp64 warp instruction occupies the pipe whatever its active
 // lanes).  Slices of length 1 hold the Dirichlet identity rows: r = 0.
+// V = double: the fp64 residual.  V = float (levels between the coarsest and
+// the finest when rav_set_coarse_residual_f32 is on): fp32 operator values and
+// an fp32 copy of x, products summed in fp32, r = b - sum formed in fp64.
+template <typename V>
 __global__ void __launch_bounds__(256) k_residual_sell(int64_t nslots, const int32_t* __restrict__ sperm,
                                                        const int64_t* __restrict__ sptr,
                                                        const int32_t* __restrict__ slen,
                                                        const int32_t* __restrict__ scol,
-                                                       const double* __restrict__ sval,
-                                                       const double* __restrict__ x, const double* __restrict__ b,
+                                                       const V* __restrict__ sval,
+                                                       const V* __restrict__ x, const double* __restrict__ b,
                                                        double* __restrict__ r, double* __restrict__ part,
                                                        float* __restrict__ r32) {
   // one slice per warp, one slot per thread (no grid-stride loop: the hardware
@@ -31,15 +35,15 @@ __global__ void __launch_bounds__(256) k_residual_sell(int64_t nslots, const int
     const int32_t row = sperm[t];
     const int len = slen[s];
     const int64_t base = sptr[s] + (t & 31);
-    double acc0 = 0.0, acc1 = 0.0;
+    V acc0 = 0, acc1 = 0;
     if (len > 1) {
       const int32_t* c = scol + base;
-      const double* v = sval + base;
+      const V* v = sval + base;
       int k = 0;
       // eight independent gathers in flight per thread, two accumulators
       for (; k + 8 <= len; k += 8) {
         int ck[8];
-        double vk[8], xk[8];
+        V vk[8], xk[8];
 #pragma unroll
         for (int j = 0; j < 8; ++j) ck[j] = ld_stream(c + 32 * (k + j));
 #pragma unroll
@@ -55,7 +59,7 @@ __global__ void __launch_bounds__(256) k_residual_sell(int64_t nslots, const int
       for (; k < len; ++k) acc0 += ld_stream(v + 32 * k) * x[ld_stream(c + 32 * k)];
     }
     if (row >= 0) {
-      const double rv = len > 1 ? b[row] - (acc0 + acc1) : 0.0;
+      const double rv = len > 1 ? b[row] - (double)(acc0 + acc1) : 0.0;
       r[row] = rv;
       if (r32) r32[row] = (float)rv;  // round to nearest even, for fp32-accumulating applies
       acc2 = rv * rv;
@@ -72,13 +76,13 @@ __global__ void __launch_bounds__(256) k_residual_sell(int64_t nslots, const int
 // its rows, lane j of a row sums the slots j, j+K, ... and the K partial sums
 // meet by shuffles.  A warp touches K rows of the slice's storage, 32/K
 // consecutive values in each, so every 32-byte sector it loads is used.
-template <int K>
+template <int K, typename V>
 __global__ void __launch_bounds__(256) k_residual_sell_split(int64_t nslots, const int32_t* __restrict__ sperm,
                                                              const int64_t* __restrict__ sptr,
                                                              const int32_t* __restrict__ slen,
                                                              const int32_t* __restrict__ scol,
-                                                             const double* __restrict__ sval,
-                                                             const double* __restrict__ x,
+                                                             const V* __restrict__ sval,
+                                                             const V* __restrict__ x,
                                                              const double* __restrict__ b, double* __restrict__ r,
                                                              double* __restrict__ part, float* __restrict__ r32) {
   double acc2 = 0.0;
@@ -91,12 +95,12 @@ __global__ void __launch_bounds__(256) k_residual_sell_split(int64_t nslots, con
     const int j = lane % K;
     const int len = slen[s];
     const int64_t base = sptr[s] + t;
-    double acc0 = 0.0, acc1 = 0.0;
+    V acc0 = 0, acc1 = 0;
     if (len > 1) {
       int k = j;
       for (; k + 3 * K < len; k += 4 * K) {
         int ck[4];
-        double vk[4], xk[4];
+        V vk[4], xk[4];
 #pragma unroll
         for (int i = 0; i < 4; ++i) ck[i] = ld_stream(scol + base + 32 * (k + i * K));
 #pragma unroll
@@ -110,12 +114,12 @@ __global__ void __launch_bounds__(256) k_residual_sell_split(int64_t nslots, con
       }
       for (; k < len; k += K) acc0 += ld_stream(sval + base + 32 * k) * x[ld_stream(scol + base + 32 * k)];
     }
-    double acc = acc0 + acc1;
+    V acc = acc0 + acc1;
 #pragma unroll
     for (int o = K / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
     const int32_t row = sperm[s * 32 + t];
     if (j == 0 && row >= 0) {
-      const double rv = len > 1 ? b[row] - acc : 0.0;
+      const double rv = len > 1 ? b[row] - (double)acc : 0.0;
       r[row] = rv;
       if (r32) r32[row] = (float)rv;
       acc2 = rv * rv;
@@ -439,11 +443,19 @@ __global__ void k_multi_axpy(const double* __restrict__ V, const double* __restr
 }
 
 
+// x rounded to fp32 (to nearest even), the input of the fp32 coarse-level residual.
+__global__ void k_x_to_f32(const double* __restrict__ x, int64_t n, float* __restrict__ x32) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n) x32[i] = (float)x[i];
+}
+
 // ---------------------------------------------------------------------------
 int residual_impl(rav_mg* mg, int level, const double* x, const double* b, double* r, double* norm2_dev,
                   cudaStream_t s, float* r32) {
   const Level& L = mg->lev[level];
-  if (L.rblock && ((uintptr_t)x & 15) == 0) {  // node-blocked velocity rows (x read as 16-byte pairs) + pressure rows
+  // fp32 operator and x on the levels between the coarsest and the finest
+  const bool f32 = mg->coarse_f32 && L.sval32 && level > 0 && level < mg->nlev - 1;
+  if (L.rblock && !f32 && ((uintptr_t)x & 15) == 0) {  // node-blocked velocity rows (x read as 16-byte pairs) + pressure rows
     const int64_t blocks = blocked_blocks(L);
     if (norm2_dev && blocks > mg->part_cap) return RAV_ERR_ARG;
     double* part = norm2_dev ? mg->norm_part : nullptr;
@@ -462,9 +474,19 @@ int residual_impl(rav_mg* mg, int level, const double* x, const double* b, doubl
   double* part = norm2_dev ? mg->norm_part : nullptr;
   cudaEvent_t e0;
   RAV_TRY(prof_begin(mg, level, PROF_RESIDUAL, s, &e0));
-#define RAV_RES_SPLIT(KK)                                                                                         \
-  k_residual_sell_split<KK><<<blocks, 256, 0, s>>>(nslots, L.sperm, L.sptr, L.slen, L.scol, L.sval, x, b, r, part, \
-                                                   r32)
+  if (f32) {
+    k_x_to_f32<<<(unsigned)((L.g.n + 255) / 256), 256, 0, s>>>(x, L.g.n, L.x32);
+    note_launch();
+  }
+#define RAV_RES_SPLIT(KK)                                                                                          \
+  {                                                                                                                \
+    if (f32)                                                                                                       \
+      k_residual_sell_split<KK, float><<<blocks, 256, 0, s>>>(nslots, L.sperm, L.sptr, L.slen, L.scol, L.sval32,   \
+                                                              L.x32, b, r, part, r32);                             \
+    else                                                                                                           \
+      k_residual_sell_split<KK, double><<<blocks, 256, 0, s>>>(nslots, L.sperm, L.sptr, L.slen, L.scol, L.sval, x, \
+                                                               b, r, part, r32);                                   \
+  }
   switch (K) {
     case 2: RAV_RES_SPLIT(2); break;
     case 4: RAV_RES_SPLIT(4); break;
@@ -472,7 +494,12 @@ int residual_impl(rav_mg* mg, int level, const double* x, const double* b, doubl
     case 16: RAV_RES_SPLIT(16); break;
     case 32: RAV_RES_SPLIT(32); break;
     default:
-      k_residual_sell<<<blocks, 256, 0, s>>>(nslots, L.sperm, L.sptr, L.slen, L.scol, L.sval, x, b, r, part, r32);
+      if (f32)
+        k_residual_sell<float><<<blocks, 256, 0, s>>>(nslots, L.sperm, L.sptr, L.slen, L.scol, L.sval32, L.x32, b, r,
+                                                      part, r32);
+      else
+        k_residual_sell<double><<<blocks, 256, 0, s>>>(nslots, L.sperm, L.sptr, L.slen, L.scol, L.sval, x, b, r,
+                                                       part, r32);
   }
 #undef RAV_RES_SPLIT
   if (norm2_dev) k_sum_parts<<<1, 256, 0, s>>>(mg->norm_part, blocks, norm2_dev, 1);
@@ -484,7 +511,7 @@ int residual_impl(rav_mg* mg, int level, const double* x, const double* b, doubl
 void launch_residual_rows(int64_t nslots, const int32_t* sperm, const int64_t* sptr, const int32_t* slen,
                           const int32_t* scol, const double* sval, const double* x, const double* b, double* r,
                           double* part, float* r32, cudaStream_t s) {
-  k_residual_sell<<<(unsigned)((nslots + 255) / 256), 256, 0, s>>>(nslots, sperm, sptr, slen, scol, sval, x, b, r,
+  k_residual_sell<double><<<(unsigned)((nslots + 255) / 256), 256, 0, s>>>(nslots, sperm, sptr, slen, scol, sval, x, b, r,
                                                                    part, r32);
 }
 
@@ -729,7 +756,7 @@ extern "C" int rav_residual_norm_noalloc(rav_mg* mg, int level, const double* x,
   double* parts = nullptr;
   RAV_TRY(noalloc_parts_address(mg, &parts));
   cudaStream_t s = S(stream);
-  k_residual_sell<<<(unsigned)blocks, 256, 0, s>>>(nslots, L.sperm, L.sptr, L.slen, L.scol, L.sval, x, b, r, parts,
+  k_residual_sell<double><<<(unsigned)blocks, 256, 0, s>>>(nslots, L.sperm, L.sptr, L.slen, L.scol, L.sval, x, b, r, parts,
                                                    nullptr);
   k_sum_parts<<<1, 256, 0, s>>>(parts, (int)blocks, norm_dev, 1);
   note_launch(2);

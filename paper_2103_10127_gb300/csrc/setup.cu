@@ -1296,6 +1296,8 @@ extern "C" void mg_destroy(rav_mg* mg) {
     cudaFree(L.rp);
     cudaFree(L.ci);
     cudaFree(L.va);
+    cudaFree(L.sval32);
+    cudaFree(L.x32);
     blocked_free(L);
     cudaFree(L.sperm);
     cudaFree(L.sslot);
@@ -1415,6 +1417,55 @@ extern "C" int rav_set_residual_blocked(rav_mg* mg, int level, int enable, rav_s
   drop_graphs(mg, nullptr);
   L.rblock = true;
   return RAV_OK;
+}
+
+namespace rav {
+__global__ void k_vals_to_f32(const double* __restrict__ v, int64_t n, float* __restrict__ v32) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n) v32[i] = (float)v[i];
+}
+}  // namespace rav
+
+static void coarse_f32_free(rav_mg* mg) {
+  for (int l = 0; l < mg->nlev; ++l) {
+    Level& L = mg->lev[l];
+    cudaFree(L.sval32);
+    cudaFree(L.x32);
+    L.sval32 = nullptr;
+    L.x32 = nullptr;
+  }
+  mg->coarse_f32 = false;
+}
+
+extern "C" int rav_set_coarse_residual_f32(rav_mg* mg, int enable, int64_t min_dofs, rav_stream stream) {
+  if (!mg || (enable != 0 && enable != 1) || min_dofs < 0) return RAV_ERR_ARG;
+  if (!enable && !mg->coarse_f32) return RAV_OK;
+  cudaStream_t s = S(stream);
+  RAV_CUDA(cudaStreamSynchronize(s));
+  drop_graphs(mg, nullptr);  // captured cycles hold the other residual kernels
+  coarse_f32_free(mg);
+  if (!enable) return RAV_OK;
+  for (int l = 1; l + 1 < mg->nlev; ++l) {
+    Level& L = mg->lev[l];
+    if (L.g.n < min_dofs) continue;  // small levels: latency-bound, the conversion launch would not pay
+    int64_t nval = 0;  // stored slots of the sliced-ELL copy
+    RAV_CUDA(cudaMemcpy(&nval, L.sptr + L.nslice, sizeof(int64_t), cudaMemcpyDeviceToHost));
+    if (cudaMalloc(&L.sval32, sizeof(float) * std::max<int64_t>(nval, 1)) != cudaSuccess ||
+        cudaMalloc(&L.x32, sizeof(float) * L.g.n) != cudaSuccess) {
+      coarse_f32_free(mg);
+      return RAV_ERR_CUDA;
+    }
+    if (nval) k_vals_to_f32<<<(unsigned)((nval + 255) / 256), 256, 0, s>>>(L.sval, nval, L.sval32);
+  }
+  RAV_CUDA(cudaGetLastError());
+  RAV_CUDA(cudaStreamSynchronize(s));
+  mg->coarse_f32 = true;
+  return RAV_OK;
+}
+
+extern "C" int rav_get_coarse_residual_f32(const rav_mg* mg) {
+  if (!mg) return RAV_ERR_ARG;
+  return mg->coarse_f32 ? 1 : 0;
 }
 
 extern "C" int rav_get_residual_blocked(const rav_mg* mg, int level) {

@@ -764,3 +764,58 @@ def test_rav_multigrid_convergence_is_mesh_independent():
         del sm, mg
     assert max(its) - min(its) <= 2, its
     assert max(rhos) < 0.3, rhos
+
+
+@pytest.mark.parametrize("case", [dict(dim=2, N=16, nlev=4, graded=True, nblobs=6, bc=O.BC_NOSLIP),
+                                  dict(dim=3, N=8, nlev=3, nblobs=5)], ids=["2d-16-graded-blobs", "3d-8-blobs"])
+def test_coarse_residual_f32_between_the_coarsest_and_the_finest(case):
+    """rav_set_coarse_residual_f32: on the levels between the coarsest and the
+    finest the residual (fp32 operator and x, fp32 sums, r = b - sum in fp64)
+    equals the oracle's to fp32 rounding of the row sums; the finest and the
+    coarsest level keep the fp64 residual bit for bit; off restores it."""
+    mg, orc = make_pair(**case)
+    rng = np.random.default_rng(47)
+    L = case["nlev"]
+    xs = [rng.standard_normal(mg.n(l)) for l in range(L)]
+    bs = [rng.standard_normal(mg.n(l)) for l in range(L)]
+    ref = [cpu(mg.residual(l, gpu(xs[l]), gpu(bs[l]))) for l in range(L)]
+    assert mg.coarse_residual_f32(True) == 1
+    for l in range(L):
+        got = cpu(mg.residual(l, gpu(xs[l]), gpu(bs[l])))
+        if 0 < l < L - 1:
+            want = orc.residual(l, xs[l], bs[l])
+            assert 0.0 < rel(got, want) <= 2e-6, l
+        else:
+            assert np.array_equal(got, ref[l]), l
+    assert mg.coarse_residual_f32(False) == 0
+    for l in range(L):
+        assert np.array_equal(cpu(mg.residual(l, gpu(xs[l]), gpu(bs[l]))), ref[l]), l
+    # levels below min_dofs keep the fp64 residual
+    assert mg.coarse_residual_f32(True, min_dofs=10**9) == 1
+    for l in range(L):
+        assert np.array_equal(cpu(mg.residual(l, gpu(xs[l]), gpu(bs[l]))), ref[l]), l
+    mg.coarse_residual_f32(False)
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_coarse_residual_f32_keeps_the_convergence(dim):
+    """With BF16 factored inverses, fp32 residuals on the intermediate levels
+    take the same stationary cycles (2-D 64^2, 4 levels) or FGMRES iterations
+    within one (3-D 16^3 blobs, 3 levels) to 1e-8 as fp64 residuals there."""
+    if dim == 2:
+        mg = R.Multigrid(2, 64, 4, bc=R.BC_NOSLIP)
+        b, outer = mg.rhs(R.F_PSI), 0
+    else:
+        mg = R.Multigrid(3, 16, 3, blobs=inputs.viscosity_blobs(inputs.BASE_SEED, k=20, s_max=3.0),
+                         bc=R.BC_NOSLIP)
+        b, outer = mg.rhs(R.F_SINKER), 1
+    sm = R.Smoother(mg, R.RAV, R.BF16_FACT, 0.5)
+    its = []
+    for on in (False, True):
+        mg.coarse_residual_f32(on)
+        x = mg.initial_guess()
+        it, hist, rc = mg.solve(sm, x, b, tol=1e-8, maxit=100, outer=outer)
+        assert rc == 0 and hist[-1] <= 1e-8
+        its.append(it)
+    mg.coarse_residual_f32(False)
+    assert (its[0] == its[1]) if dim == 2 else abs(its[0] - its[1]) <= 1, its
