@@ -486,6 +486,19 @@ int batch_get_tuning(const rav_batch* bt, int out[2]);
 int batch_set_tensor_apply(rav_batch* bt, int enable, rav_stream stream);
 int batch_tensor_apply_levels(const rav_batch* bt);
 
+/* FP32 residuals on the depths below the finest of a batch (enable = 1; 0
+ * returns to fp64): there r = b - L x (Eq. 10) for every right-hand side uses
+ * the operator values and x rounded to fp32 (x converted before each
+ * residual), products summed in fp32 and r = b - sum formed in fp64; the
+ * finest depth's residual, which measures convergence, and the coarse solves
+ * stay fp64.  The single-problem counterpart is rav_set_coarse_residual_f32.
+ * Allocates fp32 copies of those levels' operators and x, synchronises the
+ * stream and drops the captured cycle.  RAV_ERR_ARG for other values.
+ * batch_coarse_residual_f32 returns 1 when it is on, 0 when off.  The paper
+ * has no counterpart. */
+int batch_set_coarse_residual_f32(rav_batch* bt, int enable, rav_stream stream);
+int batch_coarse_residual_f32(const rav_batch* bt);
+
 /* Timing hook of the batch, with the kernel classes of rav_profile_enable.
  * While enabled (on != 0) batch_vcycle and solve_batched launch phase by phase
  * instead of replaying the graph, and every phase launch is bracketed by CUDA

@@ -56,6 +56,11 @@ struct BLevel {
   // and low parts in the tensor-core operand layout (2 x 4096 bytes), or null
   // when the level's interior subdomains do not share them
   const float* gtc;
+  // fp32 residual on depths below the finest (batch_set_coarse_residual_f32):
+  // the operator values in fp32 (slot order of sval) and a work copy of x in
+  // fp32 (n x nrhs); null where the level keeps the fp64 residual
+  const float* sval32;
+  float* x32;
 };
 
 __device__ __forceinline__ int find_entry(const int64_t* __restrict__ first, int ne, int64_t blk) {
@@ -94,6 +99,24 @@ __device__ __forceinline__ void load_row(const A* __restrict__ p, A* out) {
 #pragma unroll
     for (int j = 0; j < NR; ++j) out[j] = p[j];
   }
+}
+
+// x of every row of each entry rounded to fp32 (the residual phase's block
+// layout: one thread per row slot, and every row has a slot).
+template <int NR>
+__global__ void kb_x_to_f32(const BLevel* __restrict__ L, const int64_t* __restrict__ first, int ne) {
+  const int e = find_entry(first, ne, blockIdx.x);
+  const BLevel& lv = L[e];
+  const int64_t t = (blockIdx.x - first[e]) * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= lv.g.n) return;
+#pragma unroll
+  for (int j = 0; j < NR; ++j) lv.x32[t * NR + j] = (float)lv.x[t * NR + j];
+}
+
+// The operator values of one level rounded to fp32 (set-up).
+__global__ void kb_vals_to_f32(const double* __restrict__ v, int64_t n, float* __restrict__ v32) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n) v32[i] = (float)v[i];
 }
 
 // r = b - L x for every right-hand side (same addition order per RHS as
@@ -154,6 +177,55 @@ __global__ void kb_residual(const BLevel* __restrict__ L, const int64_t* __restr
     for (int j = 0; j < NR; ++j) {
       const double bs = block_sum(sq[j]);
       if (threadIdx.x == 0) part[blockIdx.x * NR + j] = bs;
+    }
+  }
+}
+
+// The same residual on a depth below the finest with fp32 operator values and
+// x (batch_set_coarse_residual_f32): products summed in fp32 in the same
+// order, r = b - sum formed in fp64.
+template <int NR>
+__global__ void kb_residual_f32(const BLevel* __restrict__ L, const int64_t* __restrict__ first, int ne) {
+  const int e = find_entry(first, ne, blockIdx.x);
+  const BLevel& lv = L[e];
+  const int64_t t = (blockIdx.x - first[e]) * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= lv.nslice * 32) return;
+  const int64_t s = t >> 5;
+  const int32_t row = lv.sperm[t];
+  const int len = lv.slen[s];
+  const int64_t base = lv.sptr[s] + (t & 31);
+  float a0[NR], a1[NR];
+#pragma unroll
+  for (int j = 0; j < NR; ++j) a0[j] = a1[j] = 0.f;
+  if (len > 1) {
+    const int32_t* c = lv.scol + base;
+    const float* v = lv.sval32 + base;
+    const int full = len & ~7;
+    for (int k = 0; k < full; k += 2) {
+      const float v0 = ld_stream(v + 32 * k), v1 = ld_stream(v + 32 * (k + 1));
+      float x0[NR], x1[NR];
+      load_row<float, NR>(lv.x32 + (int64_t)ld_stream(c + 32 * k) * NR, x0);
+      load_row<float, NR>(lv.x32 + (int64_t)ld_stream(c + 32 * (k + 1)) * NR, x1);
+#pragma unroll
+      for (int j = 0; j < NR; ++j) {
+        a0[j] += v0 * x0[j];
+        a1[j] += v1 * x1[j];
+      }
+    }
+    for (int k = full; k < len; ++k) {
+      const float v0 = ld_stream(v + 32 * k);
+      float x0[NR];
+      load_row<float, NR>(lv.x32 + (int64_t)ld_stream(c + 32 * k) * NR, x0);
+#pragma unroll
+      for (int j = 0; j < NR; ++j) a0[j] += v0 * x0[j];
+    }
+  }
+  if (row >= 0) {
+#pragma unroll
+    for (int j = 0; j < NR; ++j) {
+      const double rv = len > 1 ? lv.b[(int64_t)row * NR + j] - (double)(a0[j] + a1[j]) : 0.0;
+      lv.r[(int64_t)row * NR + j] = rv;
+      if (lv.r32) lv.r32[(int64_t)row * NR + j] = (float)rv;
     }
   }
 }
@@ -947,6 +1019,9 @@ struct rav_batch {
   // shared-inverse tensor-core apply (kb_apply_tc): per depth, the entries
   // whose interior subdomains share their rows; blocks = tiles of 16
   bool use_tc = false;
+  // fp32 residuals below the finest depth (batch_set_coarse_residual_f32)
+  bool coarse_f32 = false;
+  std::vector<void*> c32_bufs;
   std::vector<BPhase> tc_apply;
   std::vector<float*> gtc_bufs;  // per lv entry, null where not shared
   int* tc_err = nullptr;         // set by a tensor-core block whose wait gave up
@@ -1082,8 +1157,14 @@ static int64_t blk_gemv(const BLevel& b, int t) { return (b.g.n + t / 32 - 1) / 
 
 // ---- launches --------------------------------------------------------------
 template <int NR>
-static void launch_res(const BPhase& ph, double* part, cudaStream_t s) {
-  if (ph.ne) kb_residual<NR><<<(unsigned)ph.blocks, ph.threads, 0, s>>>(ph.L, ph.first, ph.ne, part);
+static void launch_res(const BPhase& ph, double* part, cudaStream_t s, bool f32 = false) {
+  if (!ph.ne) return;
+  if (f32) {  // no norm partials on these depths
+    kb_x_to_f32<NR><<<(unsigned)ph.blocks, ph.threads, 0, s>>>(ph.L, ph.first, ph.ne);
+    kb_residual_f32<NR><<<(unsigned)ph.blocks, ph.threads, 0, s>>>(ph.L, ph.first, ph.ne);
+  } else {
+    kb_residual<NR><<<(unsigned)ph.blocks, ph.threads, 0, s>>>(ph.L, ph.first, ph.ne, part);
+  }
 }
 template <int D, int NR>
 static void launch_apply(const rav_batch* bt, const BPhase& ph, int use_b, cudaStream_t s) {
@@ -1106,7 +1187,7 @@ static int batch_cycle(rav_batch* bt, int nu1, int nu2, cudaStream_t s) {
   int ev;
   auto res = [&](int d) {
     ev = bprof_begin(bt, d, PROF_RESIDUAL, s);
-    launch_res<NR>(bt->res_smooth[d], nullptr, s);
+    launch_res<NR>(bt->res_smooth[d], nullptr, s, bt->coarse_f32 && d > 0);
     bprof_end(bt, ev, s);
   };
   auto apply = [&](int d, int use_b) {
@@ -1412,6 +1493,7 @@ extern "C" void batch_destroy(rav_batch* bt) {
   cudaDeviceSynchronize();
   if (bt->graph) cudaGraphExecDestroy(bt->graph);
   if (bt->cap) cudaStreamDestroy(bt->cap);
+  for (void* q : bt->c32_bufs) cudaFree(q);
   for (auto& e : bt->evs) {
     cudaEventDestroy(e.a);
     cudaEventDestroy(e.b);
@@ -1615,6 +1697,53 @@ extern "C" int batch_set_tensor_apply(rav_batch* bt, int enable, rav_stream stre
   RAV_TRY(build_phases(bt));
   RAV_CUDA(cudaGetLastError());
   return RAV_OK;
+}
+
+extern "C" int batch_set_coarse_residual_f32(rav_batch* bt, int enable, rav_stream stream) {
+  if (!bt || (enable != 0 && enable != 1)) return RAV_ERR_ARG;
+  if ((enable != 0) == bt->coarse_f32) return RAV_OK;
+  cudaStream_t s = S(stream);
+  RAV_CUDA(cudaStreamSynchronize(s));
+  for (void* q : bt->c32_bufs) cudaFree(q);
+  bt->c32_bufs.clear();
+  for (BLevel& b : bt->lv) {
+    b.sval32 = nullptr;
+    b.x32 = nullptr;
+  }
+  bt->coarse_f32 = false;
+  if (enable) {
+    for (int p = 0; p < bt->nprob; ++p) {
+      const int Lp = bt->mgs[p]->nlev;
+      for (int d = 1; d <= Lp - 2; ++d) {  // depths below the finest that run residuals
+        BLevel& b = bt->lv[bt->lv_first[p] + d];
+        int64_t nval = 0;  // stored slots of the level's sliced-ELL copy
+        RAV_CUDA(cudaMemcpy(&nval, b.sptr + b.nslice, sizeof(int64_t), cudaMemcpyDeviceToHost));
+        float *v32 = nullptr, *x32 = nullptr;
+        if (cudaMalloc(&v32, sizeof(float) * std::max<int64_t>(nval, 1)) != cudaSuccess) return RAV_ERR_CUDA;
+        bt->c32_bufs.push_back(v32);
+        if (cudaMalloc(&x32, sizeof(float) * b.g.n * bt->nrhs) != cudaSuccess) return RAV_ERR_CUDA;
+        bt->c32_bufs.push_back(x32);
+        if (nval) kb_vals_to_f32<<<(unsigned)((nval + 255) / 256), 256, 0, s>>>(b.sval, nval, v32);
+        b.sval32 = v32;
+        b.x32 = x32;
+      }
+    }
+    RAV_CUDA(cudaGetLastError());
+    bt->coarse_f32 = true;
+  }
+  if (bt->graph) {  // the captured cycle holds the previous residual kernels
+    cudaGraphExecDestroy(bt->graph);
+    bt->graph = nullptr;
+  }
+  bt->cur_x.clear();  // descriptors are re-uploaded at the next bind
+  RAV_TRY(build_phases(bt));
+  RAV_CUDA(cudaStreamSynchronize(s));
+  return RAV_OK;
+}
+
+extern "C" int batch_coarse_residual_f32(const rav_batch* bt) {
+  if (!bt) return RAV_ERR_ARG;
+  return bt->coarse_f32 ? 1 : 0;
 }
 
 extern "C" int batch_tensor_apply_levels(const rav_batch* bt) {

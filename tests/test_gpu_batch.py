@@ -236,3 +236,45 @@ def test_tensor_core_apply_only_where_rows_are_shared():
     assert 0.0 < d.item() <= 1e-5
     with pytest.raises(R.RavError):
         R.Batch(mgs, sms, 4).tensor_apply(True)  # 8 right-hand sides only
+
+
+@pytest.mark.parametrize("nrhs", [1, 2, 8])
+def test_coarse_residual_f32_batched_cycle(nrhs):
+    """batch_set_coarse_residual_f32: with fp64 rows (the apply reads r in
+    fp64) one batched V-cycle with fp32 residuals below the finest depth
+    differs from the fp64-residual cycle only by their fp32 rounding; switching
+    back restores the fp64 cycle bit for bit."""
+    mgs, sms, xs, bs = make_batch(SIZES, nrhs, R.F64_ROWS, seed=7)
+    bt = R.Batch(mgs, sms, nrhs)
+    x_in = [x.clone() for x in xs]
+    ref = [x.clone() for x in x_in]
+    bt.vcycle(ref, bs, 2, 2)
+    assert bt.coarse_residual_f32(True)
+    got = [x.clone() for x in x_in]
+    bt.vcycle(got, bs, 2, 2)
+    for p in range(len(SIZES)):
+        d = (got[p] - x_in[p]).cpu().numpy()
+        w = (ref[p] - x_in[p]).cpu().numpy()
+        assert np.linalg.norm(d - w) <= 1e-5 * np.linalg.norm(w), p
+    assert not bt.coarse_residual_f32(False)
+    again = [x.clone() for x in x_in]
+    bt.vcycle(again, bs, 2, 2)
+    for p in range(len(SIZES)):
+        assert torch.equal(again[p], ref[p]), p
+
+
+@pytest.mark.parametrize("nrhs", [2, 8])
+def test_coarse_residual_f32_batched_solve_takes_the_same_cycles(nrhs):
+    """FP32 rows with fp32 residuals below the finest depth reach 1e-8 in the
+    same number of cycles per system as with fp64 residuals there."""
+    mgs, sms, xs, bs = make_batch(SIZES, nrhs, R.F32, seed=9)
+    out = []
+    for on in (False, True):
+        bt = R.Batch(mgs, sms, nrhs)
+        bt.coarse_residual_f32(on)
+        x = [t.clone() for t in xs]
+        it, ratios, rc = bt.solve(x, bs, tol=1e-8, maxit=100)
+        assert rc == 0 and np.all(ratios <= 1e-8)
+        out.append(it)
+        del bt
+    assert np.array_equal(out[0], out[1])
