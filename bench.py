@@ -767,10 +767,11 @@ def forms_vs_fp64(nprob=256, nrhs=8):
     import paper_2103_10127_gb300 as R
     from paper_2103_10127_gb300 import inputs
 
-    # the last form adds fp32 residuals on the levels between the coarsest and
-    # the finest (rav_set_coarse_residual_f32); the finest residual stays fp64
+    # the last form adds fp32 coarse-grid work: residuals on the levels between
+    # the coarsest and the finest (rav_set_coarse_residual_f32) and the grid
+    # transfers (rav_set_transfers_f32); the finest residual stays fp64
     formats = (("f64-factored", R.F64, False), ("f32-factored", R.F32_FACT, False),
-               ("bf16-factored", R.BF16_FACT, False), ("bf16-factored+f32-coarse-residuals", R.BF16_FACT, True))
+               ("bf16-factored", R.BF16_FACT, False), ("bf16-factored+f32-coarse-grid", R.BF16_FACT, True))
     out = {}
     for key, dim, N, nlev, outer in (("2d512_stationary", 2, 512, 7, 0), ("3d32_fgmres30", 3, 32, 4, 1)):
         if dim == 2:
@@ -785,8 +786,10 @@ def forms_vs_fp64(nprob=256, nrhs=8):
         for name, prec, coarse32 in formats:
             sm = R.Smoother(mg, R.RAV, prec, 0.5)
             mg.coarse_residual_f32(coarse32)
+            mg.transfers_f32(coarse32)
             row[name] = timed_solve(mg, sm, b, outer)
             mg.coarse_residual_f32(False)
+            mg.transfers_f32(False)
             del sm
         row["clocks"] = clocks_stop(clk, torch.cuda.current_device())
         base = row["f64-factored"]["seconds"]

@@ -202,6 +202,20 @@ int rav_get_residual_blocked(const rav_mg* mg, int level);
 int rav_set_coarse_residual_f32(rav_mg* mg, int enable, int64_t min_dofs, rav_stream stream);
 int rav_get_coarse_residual_f32(const rav_mg* mg);
 
+/* FP32 grid transfers in the V-cycle (Q2-Q1; enable = 1; 0 returns to fp64):
+ * the restriction of each level's residual (rounded to fp32 by the residual
+ * kernel) and the prolongation of each coarse correction (x rounded to fp32
+ * by one conversion kernel) use the interpolation weights in fp32 and fp32
+ * sums; b of the coarser level and the update of x are fp64 (Sec. 2's
+ * transfers, computed to fp32 rounding, about 2^-24 of the sum of |terms| per
+ * entry).  rav_restrict and rav_prolong_add stay fp64.  Allocates fp32 copies
+ * of the weight tables and one fp32 vector per level, synchronises the stream
+ * and drops the captured cycles of every smoother of mg.  RAV_ERR_ARG for
+ * other values or a Q1-Q1 hierarchy.  rav_get_transfers_f32 returns 1 when it
+ * is on, 0 when off.  The paper has no counterpart. */
+int rav_set_transfers_f32(rav_mg* mg, int enable, rav_stream stream);
+int rav_get_transfers_f32(const rav_mg* mg);
+
 /* Same residual r = b - L x on level l as rav_residual, plus ||r||_2 written to
  * the caller's device scalar norm_dev, with no memory allocation of any kind
  * and no host synchronisation.  The paper has no counterpart: this exists for

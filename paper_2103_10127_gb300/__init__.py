@@ -146,6 +146,17 @@ class Multigrid:
             raise RavError(k, "rav_get_coarse_residual_f32")
         return k
 
+    def transfers_f32(self, enable=None, stream=None):
+        """FP32 restriction and prolongation in the V-cycle (rav_set_transfers_f32);
+        sets it when given, returns 0/1."""
+        lib = _capi.load()
+        if enable is not None:
+            check(lib.rav_set_transfers_f32(self.h, int(bool(enable)), _stream(stream)), "rav_set_transfers_f32")
+        k = lib.rav_get_transfers_f32(self.h)
+        if k < 0:
+            raise RavError(k, "rav_get_transfers_f32")
+        return k
+
     def residual_blocked(self, level, enable=None, stream=None):
         """Node-blocked residual on `level` (Q2-Q1); sets it when given, returns 0/1."""
         lib = _capi.load()

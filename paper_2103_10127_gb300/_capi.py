@@ -60,6 +60,8 @@ _SIGS = {
     "rav_hbm_read_rate": (I32, [ctypes.c_int64, ctypes.POINTER(F64), P]),
     "rav_set_coarse_residual_f32": (I32, [P, I32, ctypes.c_int64, P]),
     "rav_get_coarse_residual_f32": (I32, [P]),
+    "rav_set_transfers_f32": (I32, [P, I32, P]),
+    "rav_get_transfers_f32": (I32, [P]),
     "batch_tensor_apply_levels": (I32, [P]),
     "batch_set_coarse_residual_f32": (I32, [P, I32, P]),
     "batch_coarse_residual_f32": (I32, [P]),

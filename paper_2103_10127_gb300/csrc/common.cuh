@@ -50,20 +50,22 @@ struct Geo {
 // rc2[K] fine nodes rk2[7K+j] with weights rw2[7K+j], fine boundary nodes left
 // out (up to 7 per axis on graded grids); coarse vertex K gathers rc1[K] fine
 // vertices (rk1, rw1, stride 3).
-struct XferTab {
+template <typename W>
+struct XferTabT {
   const int* pc2[3];
   const int* pk2[3];
-  const double* pw2[3];
+  const W* pw2[3];
   const int* pc1[3];
   const int* pk1[3];
-  const double* pw1[3];
+  const W* pw1[3];
   const int* rc2[3];
   const int* rk2[3];
-  const double* rw2[3];
+  const W* rw2[3];
   const int* rc1[3];
   const int* rk1[3];
-  const double* rw1[3];
+  const W* rw1[3];
 };
+using XferTab = XferTabT<double>;
 
 struct Level {
   Geo g;
@@ -113,6 +115,14 @@ struct Level {
   void* xfer[3] = {nullptr, nullptr, nullptr};
   XferTab tabs{};
   XferTab tab() const { return tabs; }
+  // fp32 transfers (rav_set_transfers_f32): the weights of tabs in fp32 (one
+  // allocation per axis, the index arrays shared with tabs), the fp32 residual
+  // restricted from this level and the fp32 copy of the coarser level's x
+  // prolongated into it
+  void* xfer32[3] = {nullptr, nullptr, nullptr};
+  XferTabT<float> tabs32{};
+  float* rf32 = nullptr;
+  float* xc32 = nullptr;
 };
 
 }  // namespace rav
@@ -147,6 +157,7 @@ struct rav_mg {
   // captured V-cycles, replayed with cudaGraphLaunch (see vcycle in cycle.cu)
   bool use_graphs = true;
   bool coarse_f32 = false;  // fp32 residuals on the levels between the coarsest and the finest
+  bool xfer_f32 = false;    // fp32 restriction and prolongation in the V-cycle (Q2-Q1)
   cudaStream_t cap_stream = nullptr;
   struct GraphEntry {
     const rav_smoother* sm;

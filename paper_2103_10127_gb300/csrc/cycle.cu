@@ -150,8 +150,10 @@ __global__ void k_dot_parts(const double* __restrict__ a, const double* __restri
 // ---------------------------------------------------------------------------
 // Transfers with the per-axis tables (see common.cuh, XferTab): a tensor
 // product of per-axis lists of nonzero weights, 32-bit indices.
-template <int D>
-__global__ void k_prolong(Geo gf, Geo gc, XferTab T, const double* __restrict__ xc, double* __restrict__ xf) {
+// W = double: fp64; W = float (rav_set_transfers_f32): fp32 weights and coarse
+// values, sums in fp32, added to xf in fp64.
+template <int D, typename W>
+__global__ void k_prolong(Geo gf, Geo gc, XferTabT<W> T, const W* __restrict__ xc, double* __restrict__ xf) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   const int Mf = (int)gf.M, Mc = (int)gc.M, nnf = (int)gf.nnode;
   if (t < nnf) {
@@ -166,26 +168,26 @@ __global__ void k_prolong(Geo gf, Geo gc, XferTab T, const double* __restrict__ 
     const int c0 = T.pc2[0][I[0]], c1 = T.pc2[1][I[1]], c2 = D == 3 ? T.pc2[2][I[2]] : 1;
     // axis-0 entries are the same for every row: loaded once
     int k0[3];
-    double w0[3];
+    W w0[3];
 #pragma unroll
     for (int j0 = 0; j0 < 3; ++j0) {
       k0[j0] = j0 < c0 ? D * T.pk2[0][3 * I[0] + j0] : 0;
-      w0[j0] = j0 < c0 ? T.pw2[0][3 * I[0] + j0] : 0.0;
+      w0[j0] = j0 < c0 ? T.pw2[0][3 * I[0] + j0] : W(0);
     }
-    double acc[D];
+    W acc[D];
 #pragma unroll
-    for (int c = 0; c < D; ++c) acc[c] = 0.0;
+    for (int c = 0; c < D; ++c) acc[c] = 0;
     for (int j2 = 0; j2 < c2; ++j2) {
       const int K2 = D == 3 ? T.pk2[2][3 * I[2] + j2] : 0;
-      const double w2 = D == 3 ? T.pw2[2][3 * I[2] + j2] : 1.0;
+      const W w2 = D == 3 ? T.pw2[2][3 * I[2] + j2] : W(1);
       for (int j1 = 0; j1 < c1; ++j1) {
         const int K1 = T.pk2[1][3 * I[1] + j1];
-        const double w12 = D == 3 ? w2 * T.pw2[1][3 * I[1] + j1] : T.pw2[1][3 * I[1] + j1];
+        const W w12 = D == 3 ? w2 * T.pw2[1][3 * I[1] + j1] : T.pw2[1][3 * I[1] + j1];
         const int rowbase = D * Mc * (K1 + Mc * K2);
 #pragma unroll
         for (int j0 = 0; j0 < 3; ++j0) {
           if (j0 < c0) {
-            const double ww = w12 * w0[j0];
+            const W ww = w12 * w0[j0];
             const int base = rowbase + k0[j0];
 #pragma unroll
             for (int c = 0; c < D; ++c) acc[c] += ww * xc[base + c];
@@ -194,26 +196,26 @@ __global__ void k_prolong(Geo gf, Geo gc, XferTab T, const double* __restrict__ 
       }
     }
 #pragma unroll
-    for (int c = 0; c < D; ++c) xf[(int64_t)D * t + c] += acc[c];
+    for (int c = 0; c < D; ++c) xf[(int64_t)D * t + c] += (double)acc[c];
   } else if (t < nnf + (int)gf.n_p) {
     const int Nf1 = gf.N + 1, Nc1 = gc.N + 1;
     int v[3] = {0, 0, 0}, id = t - nnf;
     for (int a = 0; a < D; ++a) { v[a] = id % Nf1; id /= Nf1; }
     const int c0 = T.pc1[0][v[0]], c1 = T.pc1[1][v[1]], c2 = D == 3 ? T.pc1[2][v[2]] : 1;
-    double acc = 0.0;
+    W acc = 0;
     for (int j2 = 0; j2 < c2; ++j2) {
       const int K2 = D == 3 ? T.pk1[2][2 * v[2] + j2] : 0;
-      const double w2 = D == 3 ? T.pw1[2][2 * v[2] + j2] : 1.0;
+      const W w2 = D == 3 ? T.pw1[2][2 * v[2] + j2] : W(1);
       for (int j1 = 0; j1 < c1; ++j1) {
         const int K1 = T.pk1[1][2 * v[1] + j1];
-        const double w12 = D == 3 ? w2 * T.pw1[1][2 * v[1] + j1] : T.pw1[1][2 * v[1] + j1];
+        const W w12 = D == 3 ? w2 * T.pw1[1][2 * v[1] + j1] : T.pw1[1][2 * v[1] + j1];
 #pragma unroll
         for (int j0 = 0; j0 < 2; ++j0)
           if (j0 < c0)
             acc += w12 * T.pw1[0][2 * v[0] + j0] * xc[gc.n_u + T.pk1[0][2 * v[0] + j0] + Nc1 * (K1 + Nc1 * K2)];
       }
     }
-    xf[gf.n_u + (t - nnf)] += acc;
+    xf[gf.n_u + (t - nnf)] += (double)acc;
   }
 }
 
@@ -223,15 +225,17 @@ __global__ void k_prolong(Geo gf, Geo gc, XferTab T, const double* __restrict__ 
 // takes the rows (j2, j1) numbered sub, sub + tl, ... in row-major order and
 // the tl partial sums meet by xor shuffles (tl = 1: one thread, rows in order).
 // On small levels a single thread's fp64 chain was the whole kernel's time.
-template <int D>
-__global__ void k_restrict_c(Geo gf, Geo gc, XferTab T, const double* __restrict__ rf, double* __restrict__ bc,
+// W = double: fp64; W = float (rav_set_transfers_f32): fp32 weights and fine
+// residual, sums in fp32, bc written in fp64.
+template <int D, typename W>
+__global__ void k_restrict_c(Geo gf, Geo gc, XferTabT<W> T, const W* __restrict__ rf, double* __restrict__ bc,
                              int tl) {
   const int64_t gt = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const int t = (int)(gt / tl), sub = (int)(gt % tl);
   const int Mf = (int)gf.M, Mc = (int)gc.M, nnc = (int)gc.nnode;
-  double acc[D];
+  W acc[D];
 #pragma unroll
-  for (int c = 0; c < D; ++c) acc[c] = 0.0;
+  for (int c = 0; c < D; ++c) acc[c] = 0;
   if (t < nnc) {
     int K[3] = {0, 0, 0}, id = t;
     bool bnd = false;
@@ -244,24 +248,24 @@ __global__ void k_restrict_c(Geo gf, Geo gc, XferTab T, const double* __restrict
       const int c0 = T.rc2[0][K[0]], c1 = T.rc2[1][K[1]], c2 = D == 3 ? T.rc2[2][K[2]] : 1;
       // axis-0 entries are the same for every row: loaded once
       int k0[7];
-      double w0[7];
+      W w0[7];
 #pragma unroll
       for (int j0 = 0; j0 < 7; ++j0) {
         k0[j0] = j0 < c0 ? D * T.rk2[0][7 * K[0] + j0] : 0;
-        w0[j0] = j0 < c0 ? T.rw2[0][7 * K[0] + j0] : 0.0;
+        w0[j0] = j0 < c0 ? T.rw2[0][7 * K[0] + j0] : W(0);
       }
       for (int pr = sub; pr < c2 * c1; pr += tl) {
         const int j2 = pr / c1, j1 = pr % c1;
         const int I2 = D == 3 ? T.rk2[2][7 * K[2] + j2] : 0;
-        const double w2 = D == 3 ? T.rw2[2][7 * K[2] + j2] : 1.0;
+        const W w2 = D == 3 ? T.rw2[2][7 * K[2] + j2] : W(1);
         const int I1 = T.rk2[1][7 * K[1] + j1];
-        const double w12 = D == 3 ? w2 * T.rw2[1][7 * K[1] + j1] : T.rw2[1][7 * K[1] + j1];
+        const W w12 = D == 3 ? w2 * T.rw2[1][7 * K[1] + j1] : T.rw2[1][7 * K[1] + j1];
         const int64_t rowbase = (int64_t)D * Mf * (I1 + (int64_t)Mf * I2);
         // fixed trip count with a guard: the loads of a row are issued together
 #pragma unroll
         for (int j0 = 0; j0 < 7; ++j0) {
           if (j0 < c0) {
-            const double ww = w12 * w0[j0];
+            const W ww = w12 * w0[j0];
             const int64_t base = rowbase + k0[j0];
 #pragma unroll
             for (int c = 0; c < D; ++c) acc[c] += ww * rf[base + c];
@@ -277,9 +281,9 @@ __global__ void k_restrict_c(Geo gf, Geo gc, XferTab T, const double* __restrict
     for (int pr = sub; pr < c2 * c1; pr += tl) {
       const int j2 = pr / c1, j1 = pr % c1;
       const int V2 = D == 3 ? T.rk1[2][3 * K[2] + j2] : 0;
-      const double w2 = D == 3 ? T.rw1[2][3 * K[2] + j2] : 1.0;
+      const W w2 = D == 3 ? T.rw1[2][3 * K[2] + j2] : W(1);
       const int V1 = T.rk1[1][3 * K[1] + j1];
-      const double w12 = D == 3 ? w2 * T.rw1[1][3 * K[1] + j1] : T.rw1[1][3 * K[1] + j1];
+      const W w12 = D == 3 ? w2 * T.rw1[1][3 * K[1] + j1] : T.rw1[1][3 * K[1] + j1];
 #pragma unroll
       for (int j0 = 0; j0 < 3; ++j0)
         if (j0 < c0)
@@ -293,9 +297,9 @@ __global__ void k_restrict_c(Geo gf, Geo gc, XferTab T, const double* __restrict
   if (sub != 0) return;
   if (t < nnc) {
 #pragma unroll
-    for (int c = 0; c < D; ++c) bc[(int64_t)D * t + c] = acc[c];
+    for (int c = 0; c < D; ++c) bc[(int64_t)D * t + c] = (double)acc[c];
   } else if (t < nnc + (int)gc.n_p) {
-    bc[gc.n_u + (t - nnc)] = acc[0];
+    bc[gc.n_u + (t - nnc)] = (double)acc[0];
   }
 }
 
@@ -541,8 +545,8 @@ int restrict_impl(rav_mg* mg, int level, const double* rf, double* bc, cudaStrea
   const int blocks = (int)((tot + 127) / 128);
   cudaEvent_t e0;
   RAV_TRY(prof_begin(mg, level, PROF_RESTRICT, s, &e0));
-  if (F.g.dim == 2) k_restrict_c<2><<<blocks, 128, 0, s>>>(F.g, C.g, F.tab(), rf, bc, tl);
-  else k_restrict_c<3><<<blocks, 128, 0, s>>>(F.g, C.g, F.tab(), rf, bc, tl);
+  if (F.g.dim == 2) k_restrict_c<2, double><<<blocks, 128, 0, s>>>(F.g, C.g, F.tab(), rf, bc, tl);
+  else k_restrict_c<3, double><<<blocks, 128, 0, s>>>(F.g, C.g, F.tab(), rf, bc, tl);
   note_launch();
   RAV_CUDA(cudaGetLastError());
   return prof_end(mg, level, PROF_RESTRICT, e0, s);
@@ -564,9 +568,40 @@ int prolong_impl(rav_mg* mg, int level, const double* xc, double* xf, cudaStream
   const int blocks = (int)((tot + 127) / 128);
   cudaEvent_t e0;
   RAV_TRY(prof_begin(mg, level, PROF_PROLONG, s, &e0));
-  if (F.g.dim == 2) k_prolong<2><<<blocks, 128, 0, s>>>(F.g, C.g, F.tab(), xc, xf);
-  else k_prolong<3><<<blocks, 128, 0, s>>>(F.g, C.g, F.tab(), xc, xf);
+  if (F.g.dim == 2) k_prolong<2, double><<<blocks, 128, 0, s>>>(F.g, C.g, F.tab(), xc, xf);
+  else k_prolong<3, double><<<blocks, 128, 0, s>>>(F.g, C.g, F.tab(), xc, xf);
   note_launch();
+  RAV_CUDA(cudaGetLastError());
+  return prof_end(mg, level, PROF_PROLONG, e0, s);
+}
+
+// FP32 transfers of the V-cycle (rav_set_transfers_f32, Q2-Q1): the
+// restriction of the fine residual already rounded to fp32 (rf32, written by
+// the residual kernel), and the prolongation of the coarse x rounded to fp32
+// (one conversion kernel); fp32 weights and sums, fp64 outputs.
+static int restrict_f32(rav_mg* mg, int level, const float* rf32, double* bc, cudaStream_t s) {
+  const Level &F = mg->lev[level], &C = mg->lev[level - 1];
+  const int tl = restrict_split(C.g);
+  const int64_t tot = (C.g.nnode + C.g.n_p) * tl;
+  const int blocks = (int)((tot + 127) / 128);
+  cudaEvent_t e0;
+  RAV_TRY(prof_begin(mg, level, PROF_RESTRICT, s, &e0));
+  if (F.g.dim == 2) k_restrict_c<2, float><<<blocks, 128, 0, s>>>(F.g, C.g, F.tabs32, rf32, bc, tl);
+  else k_restrict_c<3, float><<<blocks, 128, 0, s>>>(F.g, C.g, F.tabs32, rf32, bc, tl);
+  note_launch();
+  RAV_CUDA(cudaGetLastError());
+  return prof_end(mg, level, PROF_RESTRICT, e0, s);
+}
+static int prolong_f32(rav_mg* mg, int level, const double* xc, double* xf, cudaStream_t s) {
+  const Level &F = mg->lev[level], &C = mg->lev[level - 1];
+  const int64_t tot = F.g.nnode + F.g.n_p;
+  const int blocks = (int)((tot + 127) / 128);
+  cudaEvent_t e0;
+  RAV_TRY(prof_begin(mg, level, PROF_PROLONG, s, &e0));
+  k_x_to_f32<<<(unsigned)((C.g.n + 255) / 256), 256, 0, s>>>(xc, C.g.n, F.xc32);
+  if (F.g.dim == 2) k_prolong<2, float><<<blocks, 128, 0, s>>>(F.g, C.g, F.tabs32, F.xc32, xf);
+  else k_prolong<3, float><<<blocks, 128, 0, s>>>(F.g, C.g, F.tabs32, F.xc32, xf);
+  note_launch(2);
   RAV_CUDA(cudaGetLastError());
   return prof_end(mg, level, PROF_PROLONG, e0, s);
 }
@@ -606,11 +641,12 @@ static int vcycle_rec(rav_mg* mg, rav_smoother* sm, int l, double* x, const doub
                                      : (entry == ENTRY_R_READY ? ENTRY_R_READY : ENTRY_GENERAL);
   RAV_TRY(rav_smooth_impl(sm, l, x, b, nu1, s, first));
   Level& C = mg->lev[l - 1];
-  RAV_TRY(residual_impl(mg, l, x, b, L.r, nullptr, s));
-  RAV_TRY(restrict_impl(mg, l, L.r, C.b, s));
+  const bool xf32 = mg->xfer_f32 && L.rf32;  // fp32 transfers between l and l-1
+  RAV_TRY(residual_impl(mg, l, x, b, L.r, nullptr, s, xf32 ? L.rf32 : nullptr));
+  RAV_TRY(xf32 ? restrict_f32(mg, l, L.rf32, C.b, s) : restrict_impl(mg, l, L.r, C.b, s));
   RAV_CUDA(cudaMemsetAsync(C.x, 0, sizeof(double) * C.g.n, s));
   RAV_TRY(vcycle_rec(mg, sm, l - 1, C.x, C.b, nu1, nu2, ENTRY_X_ZERO, s));
-  RAV_TRY(prolong_impl(mg, l, C.x, x, s));
+  RAV_TRY(xf32 ? prolong_f32(mg, l, C.x, x, s) : prolong_impl(mg, l, C.x, x, s));
   RAV_TRY(rav_smooth_impl(sm, l, x, b, nu2, s));
   return RAV_OK;
 }

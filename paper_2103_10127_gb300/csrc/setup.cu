@@ -1298,6 +1298,9 @@ extern "C" void mg_destroy(rav_mg* mg) {
     cudaFree(L.va);
     cudaFree(L.sval32);
     cudaFree(L.x32);
+    for (int a = 0; a < 3; ++a) cudaFree(L.xfer32[a]);
+    cudaFree(L.rf32);
+    cudaFree(L.xc32);
     blocked_free(L);
     cudaFree(L.sperm);
     cudaFree(L.sslot);
@@ -1461,6 +1464,77 @@ extern "C" int rav_set_coarse_residual_f32(rav_mg* mg, int enable, int64_t min_d
   RAV_CUDA(cudaStreamSynchronize(s));
   mg->coarse_f32 = true;
   return RAV_OK;
+}
+
+static void xfer_f32_free(rav_mg* mg) {
+  for (int l = 0; l < mg->nlev; ++l) {
+    Level& L = mg->lev[l];
+    for (int a = 0; a < 3; ++a) {
+      cudaFree(L.xfer32[a]);
+      L.xfer32[a] = nullptr;
+    }
+    L.tabs32 = XferTabT<float>{};
+    cudaFree(L.rf32);
+    cudaFree(L.xc32);
+    L.rf32 = nullptr;
+    L.xc32 = nullptr;
+  }
+  mg->xfer_f32 = false;
+}
+
+extern "C" int rav_set_transfers_f32(rav_mg* mg, int enable, rav_stream stream) {
+  if (!mg || (enable != 0 && enable != 1)) return RAV_ERR_ARG;
+  if (enable && mg->elem != RAV_ELEM_Q2Q1) return RAV_ERR_ARG;
+  if ((enable != 0) == mg->xfer_f32) return RAV_OK;
+  cudaStream_t s = S(stream);
+  RAV_CUDA(cudaStreamSynchronize(s));
+  drop_graphs(mg, nullptr);  // captured cycles hold the other transfer kernels
+  xfer_f32_free(mg);
+  if (!enable) return RAV_OK;
+  auto fail = [&](int rc) {
+    xfer_f32_free(mg);
+    return rc;
+  };
+  for (int l = 1; l < mg->nlev; ++l) {
+    Level& F = mg->lev[l];
+    const Level& C = mg->lev[l - 1];
+    for (int a = 0; a < mg->dim; ++a) {
+      const int64_t mf = 2 * (int64_t)F.g.N + 1, mc = 2 * (int64_t)C.g.N + 1;
+      const int64_t n2 = 3 * mf, n1 = 2 * ((int64_t)F.g.N + 1), r2 = 7 * mc, r1 = 3 * ((int64_t)C.g.N + 1);
+      float* w = nullptr;
+      if (cudaMalloc(&w, sizeof(float) * (n2 + n1 + r2 + r1)) != cudaSuccess) return fail(RAV_ERR_CUDA);
+      F.xfer32[a] = w;
+      k_vals_to_f32<<<(unsigned)((n2 + 255) / 256), 256, 0, s>>>(F.tabs.pw2[a], n2, w);
+      k_vals_to_f32<<<(unsigned)((n1 + 255) / 256), 256, 0, s>>>(F.tabs.pw1[a], n1, w + n2);
+      k_vals_to_f32<<<(unsigned)((r2 + 255) / 256), 256, 0, s>>>(F.tabs.rw2[a], r2, w + n2 + n1);
+      k_vals_to_f32<<<(unsigned)((r1 + 255) / 256), 256, 0, s>>>(F.tabs.rw1[a], r1, w + n2 + n1 + r2);
+      XferTabT<float>& T = F.tabs32;
+      T.pc2[a] = F.tabs.pc2[a];
+      T.pk2[a] = F.tabs.pk2[a];
+      T.pc1[a] = F.tabs.pc1[a];
+      T.pk1[a] = F.tabs.pk1[a];
+      T.rc2[a] = F.tabs.rc2[a];
+      T.rk2[a] = F.tabs.rk2[a];
+      T.rc1[a] = F.tabs.rc1[a];
+      T.rk1[a] = F.tabs.rk1[a];
+      T.pw2[a] = w;
+      T.pw1[a] = w + n2;
+      T.rw2[a] = w + n2 + n1;
+      T.rw1[a] = w + n2 + n1 + r2;
+    }
+    if (cudaMalloc(&F.rf32, sizeof(float) * F.g.n) != cudaSuccess ||
+        cudaMalloc(&F.xc32, sizeof(float) * C.g.n) != cudaSuccess)
+      return fail(RAV_ERR_CUDA);
+  }
+  RAV_CUDA(cudaGetLastError());
+  RAV_CUDA(cudaStreamSynchronize(s));
+  mg->xfer_f32 = true;
+  return RAV_OK;
+}
+
+extern "C" int rav_get_transfers_f32(const rav_mg* mg) {
+  if (!mg) return RAV_ERR_ARG;
+  return mg->xfer_f32 ? 1 : 0;
 }
 
 extern "C" int rav_get_coarse_residual_f32(const rav_mg* mg) {

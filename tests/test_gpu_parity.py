@@ -819,3 +819,57 @@ def test_coarse_residual_f32_keeps_the_convergence(dim):
         its.append(it)
     mg.coarse_residual_f32(False)
     assert (its[0] == its[1]) if dim == 2 else abs(its[0] - its[1]) <= 1, its
+
+
+@pytest.mark.parametrize("case", [dict(dim=2, N=16, nlev=4, graded=True, nblobs=6, bc=O.BC_NOSLIP),
+                                  dict(dim=3, N=8, nlev=3, nblobs=5)], ids=["2d-16-graded-blobs", "3d-8-blobs"])
+def test_transfers_f32_vcycle(case):
+    """rav_set_transfers_f32: a V-cycle with fp32 restriction and prolongation
+    differs from the fp64 cycle only by their fp32 rounding; off restores the
+    fp64 cycle bit for bit; Q1-Q1 hierarchies refuse it."""
+    mg, orc = make_pair(**case)
+    sm = R.Smoother(mg, R.RAV, R.F64, 0.5)
+    rng = np.random.default_rng(53)
+    n = mg.n()
+    x0, b = rng.standard_normal(n), rng.standard_normal(n)
+    ref = gpu(x0)
+    mg.vcycle(sm, ref, gpu(b), 2, 2)
+    assert mg.transfers_f32(True) == 1
+    got = gpu(x0)
+    mg.vcycle(sm, got, gpu(b), 2, 2)
+    d, w = cpu(got) - x0, cpu(ref) - x0
+    assert 0.0 < np.linalg.norm(d - w) <= 1e-5 * np.linalg.norm(w)
+    assert mg.transfers_f32(False) == 0
+    again = gpu(x0)
+    mg.vcycle(sm, again, gpu(b), 2, 2)
+    assert torch.equal(again, ref)
+    q1 = R.Multigrid(case["dim"], 8, 2, bc=R.BC_CAVITY, element=R.ELEM_Q1Q1, beta=0.02)
+    with pytest.raises(R.RavError):
+        q1.transfers_f32(True)
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_f32_coarse_grid_work_keeps_the_convergence(dim):
+    """BF16 factored inverses with fp32 intermediate-level residuals and fp32
+    transfers take the same stationary cycles (2-D 64^2, 4 levels) or FGMRES
+    iterations within one (3-D 16^3 blobs, 3 levels) to 1e-8 as with fp64
+    residuals and transfers."""
+    if dim == 2:
+        mg = R.Multigrid(2, 64, 4, bc=R.BC_NOSLIP)
+        b, outer = mg.rhs(R.F_PSI), 0
+    else:
+        mg = R.Multigrid(3, 16, 3, blobs=inputs.viscosity_blobs(inputs.BASE_SEED, k=20, s_max=3.0),
+                         bc=R.BC_NOSLIP)
+        b, outer = mg.rhs(R.F_SINKER), 1
+    sm = R.Smoother(mg, R.RAV, R.BF16_FACT, 0.5)
+    its = []
+    for on in (False, True):
+        mg.coarse_residual_f32(on)
+        mg.transfers_f32(on)
+        x = mg.initial_guess()
+        it, hist, rc = mg.solve(sm, x, b, tol=1e-8, maxit=100, outer=outer)
+        assert rc == 0 and hist[-1] <= 1e-8
+        its.append(it)
+    mg.coarse_residual_f32(False)
+    mg.transfers_f32(False)
+    assert (its[0] == its[1]) if dim == 2 else abs(its[0] - its[1]) <= 1, its
