@@ -805,15 +805,19 @@ def forms_vs_fp64(nprob=256, nrhs=8):
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     clk = clocks_start()
     # "f32-coarse-residuals": fp32 residuals below the finest depth
-    # (batch_set_coarse_residual_f32); the other rows keep fp64 residuals
+    # (batch_set_coarse_residual_f32); "f32-coarse-grid": those and fp32
+    # transfers (batch_set_transfers_f32); the other rows keep fp64 ones
     for name, prec in (("batched-f32-rows", R.F32), ("batched-f32-rows-tensor-core", R.F32),
-                       ("batched-f32-rows-f32-coarse-residuals", R.F32), ("batched-f64-rows", R.F64_ROWS)):
+                       ("batched-f32-rows-f32-coarse-residuals", R.F32),
+                       ("batched-f32-rows-f32-coarse-grid", R.F32), ("batched-f64-rows", R.F64_ROWS)):
         sms = [R.Smoother(mg, R.RAV, prec, 0.5) for mg in mgs]
         bt = R.Batch(mgs, sms, nrhs)
         if name.endswith("tensor-core"):
             bt.tensor_apply(True)
-        if name.endswith("f32-coarse-residuals"):
+        if name.endswith("f32-coarse-residuals") or name.endswith("f32-coarse-grid"):
             bt.coarse_residual_f32(True)
+        if name.endswith("f32-coarse-grid"):
+            bt.transfers_f32(True)
         for _ in range(2):
             bt.vcycle(xs, bs, 2, 2)
         torch.cuda.synchronize()
@@ -848,7 +852,11 @@ def forms_vs_fp64(nprob=256, nrhs=8):
                       row["single-problem-f64-factored"]["ms_per_cycle_all"] / f32["ms_per_cycle"],
                       "both, fp32 residuals below the finest depth (single-problem f64 / batched f32, per cycle)":
                       row["single-problem-f64-factored"]["ms_per_cycle_all"] /
-                      row["batched-f32-rows-f32-coarse-residuals"]["ms_per_cycle"]}
+                      row["batched-f32-rows-f32-coarse-residuals"]["ms_per_cycle"],
+                      "both, fp32 residuals below the finest depth and fp32 transfers "
+                      "(single-problem f64 / batched f32, per cycle)":
+                      row["single-problem-f64-factored"]["ms_per_cycle_all"] /
+                      row["batched-f32-rows-f32-coarse-grid"]["ms_per_cycle"]}
     out["batch_256x8"] = row
     return out
 

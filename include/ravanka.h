@@ -513,6 +513,18 @@ int batch_tensor_apply_levels(const rav_batch* bt);
 int batch_set_coarse_residual_f32(rav_batch* bt, int enable, rav_stream stream);
 int batch_coarse_residual_f32(const rav_batch* bt);
 
+/* FP32 grid transfers of a batch (FP32 rows, Q2-Q1; enable = 1; 0 returns to
+ * fp64): the restriction reads the residual's fp32 copy (the one the apply
+ * reads), the prolongation an fp32 copy of the coarse x (one conversion
+ * kernel per transfer); fp32 weights and sums, b of the coarser level and
+ * the update of x in fp64.  The single-problem counterpart is
+ * rav_set_transfers_f32.  Allocates fp32 weight tables and coarse x copies,
+ * synchronises the stream and drops the captured cycle.  RAV_ERR_ARG for
+ * other values or another storage or element.  batch_transfers_f32 returns 1
+ * when it is on, 0 when off.  The paper has no counterpart. */
+int batch_set_transfers_f32(rav_batch* bt, int enable, rav_stream stream);
+int batch_transfers_f32(const rav_batch* bt);
+
 /* Timing hook of the batch, with the kernel classes of rav_profile_enable.
  * While enabled (on != 0) batch_vcycle and solve_batched launch phase by phase
  * instead of replaying the graph, and every phase launch is bracketed by CUDA

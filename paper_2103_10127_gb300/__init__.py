@@ -238,6 +238,15 @@ class Batch:
             raise RavError(k, "batch_coarse_residual_f32")
         return bool(k)
 
+    def transfers_f32(self, enable=True, stream=None):
+        """FP32 restriction and prolongation (batch_set_transfers_f32); returns whether it is on."""
+        lib = _capi.load()
+        check(lib.batch_set_transfers_f32(self.h, int(bool(enable)), _stream(stream)), "batch_set_transfers_f32")
+        k = lib.batch_transfers_f32(self.h)
+        if k < 0:
+            raise RavError(k, "batch_transfers_f32")
+        return bool(k)
+
     def profile(self, on=True):
         """Phase-by-phase CUDA-event timing of batched cycles (batch_profile_enable)."""
         check(_capi.load().batch_profile_enable(self.h, int(on)), "batch_profile_enable")

@@ -65,6 +65,8 @@ _SIGS = {
     "batch_tensor_apply_levels": (I32, [P]),
     "batch_set_coarse_residual_f32": (I32, [P, I32, P]),
     "batch_coarse_residual_f32": (I32, [P]),
+    "batch_set_transfers_f32": (I32, [P, I32, P]),
+    "batch_transfers_f32": (I32, [P]),
     "rav_get_apply_staged": (I32, [P, I32]),
     "rav_set_fused_smoothing": (I32, [P, I32]),
     "rav_get_patch_counts": (I32, [P, I32, I64P]),

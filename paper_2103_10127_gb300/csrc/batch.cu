@@ -61,6 +61,10 @@ struct BLevel {
   // fp32 (n x nrhs); null where the level keeps the fp64 residual
   const float* sval32;
   float* x32;
+  // fp32 transfers (batch_set_transfers_f32): the weights of tab in fp32 and
+  // the fp32 copy of the coarser level's x prolongated into this level
+  XferTabT<float> tab32;
+  float* xc32;
 };
 
 __device__ __forceinline__ int find_entry(const int64_t* __restrict__ first, int ne, int64_t blk) {
@@ -586,24 +590,46 @@ __global__ void kb_shared_build(Geo g, const float* __restrict__ inv, float* __r
   out[1024 + off] = v - hi;
 }
 
+// Transfer tables and inputs in the transfers' arithmetic type.
+template <typename W>
+__device__ __forceinline__ const XferTabT<W>& xfer_tab(const BLevel& lv);
+template <>
+__device__ __forceinline__ const XferTabT<double>& xfer_tab<double>(const BLevel& lv) { return lv.tab; }
+template <>
+__device__ __forceinline__ const XferTabT<float>& xfer_tab<float>(const BLevel& lv) { return lv.tab32; }
+template <typename W>
+__device__ __forceinline__ const W* restrict_in(const BLevel& lv);
+template <>
+__device__ __forceinline__ const double* restrict_in<double>(const BLevel& lv) { return lv.r; }
+template <>
+__device__ __forceinline__ const float* restrict_in<float>(const BLevel& lv) { return lv.r32; }
+template <typename W>
+__device__ __forceinline__ const W* prolong_in(const BLevel& lv);
+template <>
+__device__ __forceinline__ const double* prolong_in<double>(const BLevel& lv) { return lv.xc; }
+template <>
+__device__ __forceinline__ const float* prolong_in<float>(const BLevel& lv) { return lv.xc32; }
+
 // Restriction into the coarser level (same threads per coarse DoF and the same
-// order per RHS as k_restrict_c); also zeroes the coarser iterate.
-template <int D, int NR>
+// order per RHS as k_restrict_c); also zeroes the coarser iterate.  W = double:
+// fp64; W = float (batch_set_transfers_f32): the fp32 residual copy r32, fp32
+// weights and sums, bc written in fp64.
+template <int D, int NR, typename W>
 __global__ void kb_restrict(const BLevel* __restrict__ L, const int64_t* __restrict__ first, int ne) {
   const int e = find_entry(first, ne, blockIdx.x);
   const BLevel& lv = L[e];
   const Geo &gf = lv.g, &gc = lv.gc;
-  const XferTab& T = lv.tab;
+  const XferTabT<W>& T = xfer_tab<W>(lv);
   const int tl = restrict_split(gc);
   const int64_t gt = (blockIdx.x - first[e]) * (int64_t)blockDim.x + threadIdx.x;
   const int t = (int)(gt / tl), sub = (int)(gt % tl);
   const int Mf = (int)gf.M, Mc = (int)gc.M, nnc = (int)gc.nnode;
-  const double* rf = lv.r;
-  double acc[D][NR];
+  const W* rf = restrict_in<W>(lv);
+  W acc[D][NR];
 #pragma unroll
   for (int c = 0; c < D; ++c)
 #pragma unroll
-    for (int j = 0; j < NR; ++j) acc[c][j] = 0.0;
+    for (int j = 0; j < NR; ++j) acc[c][j] = 0;
   if (t < nnc) {
     int K[3] = {0, 0, 0}, id = t;
     bool bnd = false;
@@ -617,12 +643,12 @@ __global__ void kb_restrict(const BLevel* __restrict__ L, const int64_t* __restr
       for (int pr = sub; pr < c2 * c1; pr += tl) {
         const int j2 = pr / c1, j1 = pr % c1;
         const int I2 = D == 3 ? T.rk2[2][7 * K[2] + j2] : 0;
-        const double w2 = D == 3 ? T.rw2[2][7 * K[2] + j2] : 1.0;
+        const W w2 = D == 3 ? T.rw2[2][7 * K[2] + j2] : W(1);
         const int I1 = T.rk2[1][7 * K[1] + j1];
-        const double w12 = D == 3 ? w2 * T.rw2[1][7 * K[1] + j1] : T.rw2[1][7 * K[1] + j1];
+        const W w12 = D == 3 ? w2 * T.rw2[1][7 * K[1] + j1] : T.rw2[1][7 * K[1] + j1];
         const int64_t rowbase = (int64_t)D * Mf * (I1 + (int64_t)Mf * I2);
         for (int j0 = 0; j0 < c0; ++j0) {
-          const double ww = w12 * T.rw2[0][7 * K[0] + j0];
+          const W ww = w12 * T.rw2[0][7 * K[0] + j0];
           const int64_t bse = rowbase + D * T.rk2[0][7 * K[0] + j0];
 #pragma unroll
           for (int c = 0; c < D; ++c)
@@ -639,11 +665,11 @@ __global__ void kb_restrict(const BLevel* __restrict__ L, const int64_t* __restr
     for (int pr = sub; pr < c2 * c1; pr += tl) {
       const int j2 = pr / c1, j1 = pr % c1;
       const int V2 = D == 3 ? T.rk1[2][3 * K[2] + j2] : 0;
-      const double w2 = D == 3 ? T.rw1[2][3 * K[2] + j2] : 1.0;
+      const W w2 = D == 3 ? T.rw1[2][3 * K[2] + j2] : W(1);
       const int V1 = T.rk1[1][3 * K[1] + j1];
-      const double w12 = D == 3 ? w2 * T.rw1[1][3 * K[1] + j1] : T.rw1[1][3 * K[1] + j1];
+      const W w12 = D == 3 ? w2 * T.rw1[1][3 * K[1] + j1] : T.rw1[1][3 * K[1] + j1];
       for (int j0 = 0; j0 < c0; ++j0) {
-        const double ww = w12 * T.rw1[0][3 * K[0] + j0];
+        const W ww = w12 * T.rw1[0][3 * K[0] + j0];
         const int64_t idx = gf.n_u + T.rk1[0][3 * K[0] + j0] + Nf1 * (V1 + (int64_t)Nf1 * V2);
 #pragma unroll
         for (int j = 0; j < NR; ++j) acc[0][j] += ww * rf[idx * NR + j];
@@ -661,7 +687,7 @@ __global__ void kb_restrict(const BLevel* __restrict__ L, const int64_t* __restr
     for (int c = 0; c < D; ++c)
 #pragma unroll
       for (int j = 0; j < NR; ++j) {
-        lv.bc[((int64_t)D * t + c) * NR + j] = acc[c][j];
+        lv.bc[((int64_t)D * t + c) * NR + j] = (double)acc[c][j];
         if (lv.bc32) lv.bc32[((int64_t)D * t + c) * NR + j] = (float)acc[c][j];
         lv.xc[((int64_t)D * t + c) * NR + j] = 0.0;
       }
@@ -669,23 +695,35 @@ __global__ void kb_restrict(const BLevel* __restrict__ L, const int64_t* __restr
     const int64_t o = gc.n_u + (t - nnc);
 #pragma unroll
     for (int j = 0; j < NR; ++j) {
-      lv.bc[o * NR + j] = acc[0][j];
+      lv.bc[o * NR + j] = (double)acc[0][j];
       if (lv.bc32) lv.bc32[o * NR + j] = (float)acc[0][j];
       lv.xc[o * NR + j] = 0.0;
     }
   }
 }
 
-// x += P xc (same order per RHS as k_prolong).
-template <int D, int NR>
+// The coarser level's x rounded to fp32 before an fp32 prolongation (the
+// prolongation phase's blocks, every coarse row reached by a block-stride loop).
+template <int NR>
+__global__ void kb_xc_to_f32(const BLevel* __restrict__ L, const int64_t* __restrict__ first, int ne) {
+  const int e = find_entry(first, ne, blockIdx.x);
+  const BLevel& lv = L[e];
+  const int64_t nt = (first[e + 1] - first[e]) * (int64_t)blockDim.x;
+  for (int64_t i = (blockIdx.x - first[e]) * (int64_t)blockDim.x + threadIdx.x; i < lv.gc.n * NR; i += nt)
+    lv.xc32[i] = (float)lv.xc[i];
+}
+
+// x += P xc (same order per RHS as k_prolong).  W = float: the fp32 copy of xc,
+// fp32 weights and sums, added to x in fp64.
+template <int D, int NR, typename W>
 __global__ void kb_prolong(const BLevel* __restrict__ L, const int64_t* __restrict__ first, int ne) {
   const int e = find_entry(first, ne, blockIdx.x);
   const BLevel& lv = L[e];
   const Geo &gf = lv.g, &gc = lv.gc;
-  const XferTab& T = lv.tab;
+  const XferTabT<W>& T = xfer_tab<W>(lv);
   const int t = (int)((blockIdx.x - first[e]) * blockDim.x + threadIdx.x);
   const int Mf = (int)gf.M, Mc = (int)gc.M, nnf = (int)gf.nnode;
-  const double* xc = lv.xc;
+  const W* xc = prolong_in<W>(lv);
   if (t < nnf) {
     int I[3] = {0, 0, 0}, id = t;
     bool bnd = false;
@@ -696,20 +734,20 @@ __global__ void kb_prolong(const BLevel* __restrict__ L, const int64_t* __restri
     }
     if (bnd) return;
     const int c0 = T.pc2[0][I[0]], c1 = T.pc2[1][I[1]], c2 = D == 3 ? T.pc2[2][I[2]] : 1;
-    double acc[D][NR];
+    W acc[D][NR];
 #pragma unroll
     for (int c = 0; c < D; ++c)
 #pragma unroll
-      for (int j = 0; j < NR; ++j) acc[c][j] = 0.0;
+      for (int j = 0; j < NR; ++j) acc[c][j] = 0;
     for (int j2 = 0; j2 < c2; ++j2) {
       const int K2 = D == 3 ? T.pk2[2][3 * I[2] + j2] : 0;
-      const double w2 = D == 3 ? T.pw2[2][3 * I[2] + j2] : 1.0;
+      const W w2 = D == 3 ? T.pw2[2][3 * I[2] + j2] : W(1);
       for (int j1 = 0; j1 < c1; ++j1) {
         const int K1 = T.pk2[1][3 * I[1] + j1];
-        const double w12 = D == 3 ? w2 * T.pw2[1][3 * I[1] + j1] : T.pw2[1][3 * I[1] + j1];
+        const W w12 = D == 3 ? w2 * T.pw2[1][3 * I[1] + j1] : T.pw2[1][3 * I[1] + j1];
         const int rowbase = D * Mc * (K1 + Mc * K2);
         for (int j0 = 0; j0 < c0; ++j0) {
-          const double ww = w12 * T.pw2[0][3 * I[0] + j0];
+          const W ww = w12 * T.pw2[0][3 * I[0] + j0];
           const int bse = rowbase + D * T.pk2[0][3 * I[0] + j0];
 #pragma unroll
           for (int c = 0; c < D; ++c)
@@ -721,23 +759,23 @@ __global__ void kb_prolong(const BLevel* __restrict__ L, const int64_t* __restri
 #pragma unroll
     for (int c = 0; c < D; ++c)
 #pragma unroll
-      for (int j = 0; j < NR; ++j) lv.x[((int64_t)D * t + c) * NR + j] += acc[c][j];
+      for (int j = 0; j < NR; ++j) lv.x[((int64_t)D * t + c) * NR + j] += (double)acc[c][j];
   } else if (t < nnf + (int)gf.n_p) {
     const int Nf1 = gf.N + 1, Nc1 = gc.N + 1;
     int v[3] = {0, 0, 0}, id = t - nnf;
     for (int a = 0; a < D; ++a) { v[a] = id % Nf1; id /= Nf1; }
     const int c0 = T.pc1[0][v[0]], c1 = T.pc1[1][v[1]], c2 = D == 3 ? T.pc1[2][v[2]] : 1;
-    double acc[NR];
+    W acc[NR];
 #pragma unroll
-    for (int j = 0; j < NR; ++j) acc[j] = 0.0;
+    for (int j = 0; j < NR; ++j) acc[j] = 0;
     for (int j2 = 0; j2 < c2; ++j2) {
       const int K2 = D == 3 ? T.pk1[2][2 * v[2] + j2] : 0;
-      const double w2 = D == 3 ? T.pw1[2][2 * v[2] + j2] : 1.0;
+      const W w2 = D == 3 ? T.pw1[2][2 * v[2] + j2] : W(1);
       for (int j1 = 0; j1 < c1; ++j1) {
         const int K1 = T.pk1[1][2 * v[1] + j1];
-        const double w12 = D == 3 ? w2 * T.pw1[1][2 * v[1] + j1] : T.pw1[1][2 * v[1] + j1];
+        const W w12 = D == 3 ? w2 * T.pw1[1][2 * v[1] + j1] : T.pw1[1][2 * v[1] + j1];
         for (int j0 = 0; j0 < c0; ++j0) {
-          const double w = w12 * T.pw1[0][2 * v[0] + j0];
+          const W w = w12 * T.pw1[0][2 * v[0] + j0];
           const int64_t idx = gc.n_u + T.pk1[0][2 * v[0] + j0] + Nc1 * (K1 + Nc1 * K2);
 #pragma unroll
           for (int j = 0; j < NR; ++j) acc[j] += w * xc[idx * NR + j];
@@ -746,7 +784,7 @@ __global__ void kb_prolong(const BLevel* __restrict__ L, const int64_t* __restri
     }
     const int64_t o = gf.n_u + (t - nnf);
 #pragma unroll
-    for (int j = 0; j < NR; ++j) lv.x[o * NR + j] += acc[j];
+    for (int j = 0; j < NR; ++j) lv.x[o * NR + j] += (double)acc[j];
   }
 }
 
@@ -1022,6 +1060,9 @@ struct rav_batch {
   // fp32 residuals below the finest depth (batch_set_coarse_residual_f32)
   bool coarse_f32 = false;
   std::vector<void*> c32_bufs;
+  // fp32 transfers (batch_set_transfers_f32) and their buffers
+  bool xfer_f32 = false;
+  std::vector<void*> x32_bufs;
   std::vector<BPhase> tc_apply;
   std::vector<float*> gtc_bufs;  // per lv entry, null where not shared
   int* tc_err = nullptr;         // set by a tensor-core block whose wait gave up
@@ -1215,8 +1256,10 @@ static int batch_cycle(rav_batch* bt, int nu1, int nu2, cudaStream_t s) {
     ev = bprof_begin(bt, d, PROF_RESTRICT, s);
     if (rp.ne && bt->elem == RAV_ELEM_Q1Q1)
       kb_restrict_q1<D, NR><<<(unsigned)rp.blocks, rp.threads, 0, s>>>(rp.L, rp.first, rp.ne);
+    else if (rp.ne && bt->xfer_f32)
+      kb_restrict<D, NR, float><<<(unsigned)rp.blocks, rp.threads, 0, s>>>(rp.L, rp.first, rp.ne);
     else if (rp.ne)
-      kb_restrict<D, NR><<<(unsigned)rp.blocks, rp.threads, 0, s>>>(rp.L, rp.first, rp.ne);
+      kb_restrict<D, NR, double><<<(unsigned)rp.blocks, rp.threads, 0, s>>>(rp.L, rp.first, rp.ne);
     bprof_end(bt, ev, s);
     const BPhase& cm = bt->coarse_mask[d + 1];
     if (cm.ne) {
@@ -1231,10 +1274,14 @@ static int batch_cycle(rav_batch* bt, int nu1, int nu2, cudaStream_t s) {
   for (int d = Dm - 1; d >= 0; --d) {
     const BPhase& pp = bt->prolong[d];
     ev = bprof_begin(bt, d, PROF_PROLONG, s);
-    if (pp.ne && bt->elem == RAV_ELEM_Q1Q1)
+    if (pp.ne && bt->elem == RAV_ELEM_Q1Q1) {
       kb_prolong_q1<D, NR><<<(unsigned)pp.blocks, pp.threads, 0, s>>>(pp.L, pp.first, pp.ne);
-    else if (pp.ne)
-      kb_prolong<D, NR><<<(unsigned)pp.blocks, pp.threads, 0, s>>>(pp.L, pp.first, pp.ne);
+    } else if (pp.ne && bt->xfer_f32) {
+      kb_xc_to_f32<NR><<<(unsigned)pp.blocks, pp.threads, 0, s>>>(pp.L, pp.first, pp.ne);
+      kb_prolong<D, NR, float><<<(unsigned)pp.blocks, pp.threads, 0, s>>>(pp.L, pp.first, pp.ne);
+    } else if (pp.ne) {
+      kb_prolong<D, NR, double><<<(unsigned)pp.blocks, pp.threads, 0, s>>>(pp.L, pp.first, pp.ne);
+    }
     bprof_end(bt, ev, s);
     for (int it = 0; it < nu2; ++it) {
       res(d);
@@ -1494,6 +1541,7 @@ extern "C" void batch_destroy(rav_batch* bt) {
   if (bt->graph) cudaGraphExecDestroy(bt->graph);
   if (bt->cap) cudaStreamDestroy(bt->cap);
   for (void* q : bt->c32_bufs) cudaFree(q);
+  for (void* q : bt->x32_bufs) cudaFree(q);
   for (auto& e : bt->evs) {
     cudaEventDestroy(e.a);
     cudaEventDestroy(e.b);
@@ -1739,6 +1787,72 @@ extern "C" int batch_set_coarse_residual_f32(rav_batch* bt, int enable, rav_stre
   RAV_TRY(build_phases(bt));
   RAV_CUDA(cudaStreamSynchronize(s));
   return RAV_OK;
+}
+
+extern "C" int batch_set_transfers_f32(rav_batch* bt, int enable, rav_stream stream) {
+  if (!bt || (enable != 0 && enable != 1)) return RAV_ERR_ARG;
+  if (enable && (bt->prec != RAV_F32 || bt->elem != RAV_ELEM_Q2Q1)) return RAV_ERR_ARG;
+  if ((enable != 0) == bt->xfer_f32) return RAV_OK;
+  cudaStream_t s = S(stream);
+  RAV_CUDA(cudaStreamSynchronize(s));
+  for (void* q : bt->x32_bufs) cudaFree(q);
+  bt->x32_bufs.clear();
+  for (BLevel& b : bt->lv) {
+    b.tab32 = XferTabT<float>{};
+    b.xc32 = nullptr;
+  }
+  bt->xfer_f32 = false;
+  if (enable) {
+    for (int p = 0; p < bt->nprob; ++p) {
+      const int Lp = bt->mgs[p]->nlev;
+      for (int d = 0; d + 1 < Lp; ++d) {  // levels with a coarser one
+        BLevel& b = bt->lv[bt->lv_first[p] + d];
+        const int64_t mf = 2 * (int64_t)b.g.N + 1, mc = 2 * (int64_t)b.gc.N + 1;
+        const int64_t n2 = 3 * mf, n1 = 2 * ((int64_t)b.g.N + 1), r2 = 7 * mc, r1 = 3 * ((int64_t)b.gc.N + 1);
+        for (int a = 0; a < bt->dim; ++a) {
+          float* w = nullptr;
+          if (cudaMalloc(&w, sizeof(float) * (n2 + n1 + r2 + r1)) != cudaSuccess) return RAV_ERR_CUDA;
+          bt->x32_bufs.push_back(w);
+          kb_vals_to_f32<<<(unsigned)((n2 + 255) / 256), 256, 0, s>>>(b.tab.pw2[a], n2, w);
+          kb_vals_to_f32<<<(unsigned)((n1 + 255) / 256), 256, 0, s>>>(b.tab.pw1[a], n1, w + n2);
+          kb_vals_to_f32<<<(unsigned)((r2 + 255) / 256), 256, 0, s>>>(b.tab.rw2[a], r2, w + n2 + n1);
+          kb_vals_to_f32<<<(unsigned)((r1 + 255) / 256), 256, 0, s>>>(b.tab.rw1[a], r1, w + n2 + n1 + r2);
+          XferTabT<float>& T = b.tab32;
+          T.pc2[a] = b.tab.pc2[a];
+          T.pk2[a] = b.tab.pk2[a];
+          T.pc1[a] = b.tab.pc1[a];
+          T.pk1[a] = b.tab.pk1[a];
+          T.rc2[a] = b.tab.rc2[a];
+          T.rk2[a] = b.tab.rk2[a];
+          T.rc1[a] = b.tab.rc1[a];
+          T.rk1[a] = b.tab.rk1[a];
+          T.pw2[a] = w;
+          T.pw1[a] = w + n2;
+          T.rw2[a] = w + n2 + n1;
+          T.rw1[a] = w + n2 + n1 + r2;
+        }
+        float* xc32 = nullptr;
+        if (cudaMalloc(&xc32, sizeof(float) * b.gc.n * bt->nrhs) != cudaSuccess) return RAV_ERR_CUDA;
+        bt->x32_bufs.push_back(xc32);
+        b.xc32 = xc32;
+      }
+    }
+    RAV_CUDA(cudaGetLastError());
+    bt->xfer_f32 = true;
+  }
+  if (bt->graph) {  // the captured cycle holds the previous transfer kernels
+    cudaGraphExecDestroy(bt->graph);
+    bt->graph = nullptr;
+  }
+  bt->cur_x.clear();  // descriptors are re-uploaded at the next bind
+  RAV_TRY(build_phases(bt));
+  RAV_CUDA(cudaStreamSynchronize(s));
+  return RAV_OK;
+}
+
+extern "C" int batch_transfers_f32(const rav_batch* bt) {
+  if (!bt) return RAV_ERR_ARG;
+  return bt->xfer_f32 ? 1 : 0;
 }
 
 extern "C" int batch_coarse_residual_f32(const rav_batch* bt) {

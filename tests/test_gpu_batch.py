@@ -278,3 +278,66 @@ def test_coarse_residual_f32_batched_solve_takes_the_same_cycles(nrhs):
         out.append(it)
         del bt
     assert np.array_equal(out[0], out[1])
+
+
+@pytest.mark.parametrize("nrhs", [1, 8])
+def test_transfers_f32_batched_cycle_equals_single_problem_cycles(nrhs):
+    """batch_set_transfers_f32: one batched V-cycle with fp32 restriction and
+    prolongation differs from the fp64-transfer cycle only by their fp32
+    rounding, gives each right-hand side's single-problem cycle with
+    rav_set_transfers_f32 bit for bit (same sums in the same order), and off
+    restores the fp64 cycle bit for bit."""
+    sizes = SIZES[:3]
+    mgs, sms, xs, bs = make_batch(sizes, nrhs, R.F32, seed=11)
+    bt = R.Batch(mgs, sms, nrhs)
+    x_in = [x.clone() for x in xs]
+    ref = [x.clone() for x in x_in]
+    bt.vcycle(ref, bs, 2, 2)
+    assert bt.transfers_f32(True)
+    got = [x.clone() for x in x_in]
+    bt.vcycle(got, bs, 2, 2)
+    for p in range(len(sizes)):
+        d = (got[p] - x_in[p]).cpu().numpy()
+        w = (ref[p] - x_in[p]).cpu().numpy()
+        assert 0.0 < np.linalg.norm(d - w) <= 1e-5 * np.linalg.norm(w), p
+    for p, (mg, sm) in enumerate(zip(mgs, sms)):
+        for lev in range(mg.nlev):
+            mg.residual_split(lev, 1)
+        assert mg.transfers_f32(True) == 1
+        for k in range(nrhs):
+            x = x_in[p][:, k].clone()  # a copy also when the column is contiguous (nrhs = 1)
+            mg.vcycle(sm, x, bs[p][:, k].contiguous(), 2, 2)
+            assert torch.equal(x, got[p][:, k]), (p, k)
+        mg.transfers_f32(False)
+    assert not bt.transfers_f32(False)
+    again = [x.clone() for x in x_in]
+    bt.vcycle(again, bs, 2, 2)
+    for p in range(len(sizes)):
+        assert torch.equal(again[p], ref[p]), p
+
+
+def test_transfers_f32_batched_refuses_fp64_rows():
+    """The fp32 restriction reads the fp32 residual copy that only fp32 rows keep."""
+    mgs, sms, xs, bs = make_batch(SIZES[:2], 2, R.F64_ROWS, seed=3)
+    bt = R.Batch(mgs, sms, 2)
+    with pytest.raises(R.RavError):
+        bt.transfers_f32(True)
+    assert not bt.transfers_f32(False)
+
+
+@pytest.mark.parametrize("nrhs", [2, 8])
+def test_f32_coarse_grid_work_batched_solve_takes_the_same_cycles(nrhs):
+    """FP32 rows with fp32 residuals below the finest depth and fp32 transfers
+    reach 1e-8 in the same number of cycles per system as with fp64 ones."""
+    mgs, sms, xs, bs = make_batch(SIZES, nrhs, R.F32, seed=13)
+    out = []
+    for on in (False, True):
+        bt = R.Batch(mgs, sms, nrhs)
+        bt.coarse_residual_f32(on)
+        bt.transfers_f32(on)
+        x = [t.clone() for t in xs]
+        it, ratios, rc = bt.solve(x, bs, tol=1e-8, maxit=100)
+        assert rc == 0 and np.all(ratios <= 1e-8)
+        out.append(it)
+        del bt
+    assert np.array_equal(out[0], out[1])
