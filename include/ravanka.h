@@ -478,6 +478,21 @@ int batch_setup(rav_mg* const* mgs, rav_smoother* const* sms, int nprob, int nrh
 void batch_destroy(rav_batch* bt);
 /* out[0] = threads per block of the residual kernel, out[1] = of the apply kernel. */
 int batch_get_tuning(const rav_batch* bt, int out[2]);
+/* The RAV apply of 2-D Q2-Q1 batches with FP32 rows and 8 right-hand sides
+ * can run tiled: a block of 32 x ty vertices stages the FP32 residual of its
+ * subdomain boxes (Sec. 3's restriction) in shared memory with coalesced
+ * copies and adds the velocity corrections (Eq. 13) to x by contiguous rows of
+ * owned nodes, with the same sums in the same order as the untiled kernel (bit
+ * for bit the same results).  batch_setup chooses per depth between untiled,
+ * ty = 2 and ty = 4 by timing each on the batch's own data.
+ * batch_set_apply_tile: ty = 2 or 4 tiles every depth, 0 none, -1 restores
+ * batch_setup's choice; synchronises the stream and drops the captured cycle;
+ * RAV_ERR_ARG for other values, or for 2 or 4 on any other batch.
+ * batch_get_apply_tile returns the ty in use at depth (0 = finest; 0 =
+ * untiled), RAV_ERR_ARG outside 0 .. depths - 1.  The paper has no
+ * counterpart. */
+int batch_set_apply_tile(rav_batch* bt, int ty, rav_stream stream);
+int batch_get_apply_tile(const rav_batch* bt, int depth);
 /* Shared-inverse apply on the tensor cores (2-D Q2-Q1 batches with RAV_F32
  * rows and 8 right-hand sides; RAV_ERR_ARG otherwise).  On a uniform grid
  * with constant viscosity every interior subdomain of a level (vertex 2 .. N-2

@@ -25,6 +25,7 @@
 
 #include "box.cuh"
 #include "common.cuh"
+#include "cpasync.cuh"
 #include "tcgen05.cuh"
 
 namespace rav {
@@ -344,6 +345,145 @@ __global__ void kb_apply(const BLevel* __restrict__ L, const int64_t* __restrict
 #pragma unroll
       for (int j = 0; j < NR; ++j) lv.x[dof * NR + j] += om * (double)acc[i][j];
     }
+  }
+}
+
+// ---- tiled apply: 2-D Q2-Q1, fp32 rows, 8 right-hand sides ------------------
+// kb_apply's thread per subdomain gathers each box node's 8-wide residual row
+// and updates its owned rows of x where the lanes of a warp sit two nodes
+// apart: every load or store of a warp touches 32 cache lines, and those L1
+// wavefronts, not HBM, set its time.  Here a block takes 32 x TY vertices (one
+// warp per row of vertices, so the interleaved stored rows stay one warp-wide
+// load).  The fp32 residual of the block's boxes, (2*32+3) x (2*TY+3) nodes x
+// 2 components x 8 RHS, is copied once into shared memory by coalesced 16-byte
+// cp.async (zero outside the grid, where kb_apply reads zero); each thread
+// forms kb_apply's sums in kb_apply's order from there; the velocity
+// corrections go back through the same buffer and are added to x by rows of
+// owned nodes (contiguous 16-byte pieces), the pressure correction directly.
+// Results equal kb_apply's bit for bit.
+constexpr int kTileX = 32;  // vertices per block row (one warp)
+
+// Byte offset of 16-byte chunk q (0..3: component q/2, RHS 4(q%2)..4(q%2)+3)
+// of node ln in a tile buffer: two 64-byte nodes per 128-byte line, the chunk
+// slot XOR-ed with the line index, so that the 8 lanes of a quarter-warp
+// (consecutive vertices: nodes two apart, consecutive lines) take 8 distinct
+// slots, i.e. all 32 banks.
+__device__ __forceinline__ int tile_off(int ln, int q) {
+  const int line = ln >> 1;
+  return line * 128 + (((((ln & 1) << 2) | q) ^ (line & 7)) << 4);
+}
+template <int TY>
+struct TileShape {
+  static constexpr int SX = 2 * kTileX + 3, SY = 2 * TY + 3;  // staged box nodes per axis
+  static constexpr int OX = 2 * kTileX, OY = 2 * TY;          // owned nodes per axis
+  static constexpr int BYTES = (SX * SY + 1) / 2 * 128;       // >= OX * OY / 2 * 128
+};
+
+template <int TY>
+__global__ void __launch_bounds__(kTileX * TY, 16 / TY)
+    kb_apply_tile(const BLevel* __restrict__ L, const int64_t* __restrict__ first, int ne) {
+  using B = BoxT<2>;
+  using S = TileShape<TY>;
+  constexpr int NC = B::NC, RB = B::RB, NR = 8, NT = kTileX * TY;
+  static_assert(B::NCH == 1 && RB == 9, "one thread per subdomain, 9 owned rows");
+  __shared__ __align__(128) unsigned char sm[S::BYTES];
+  const int e = find_entry(first, ne, blockIdx.x);
+  const BLevel& lv = L[e];
+  const Geo& g = lv.g;
+  const int N = g.N, V = N + 1, M = 2 * N + 1;
+  const int ntx = (V + kTileX - 1) / kTileX;
+  const int lb = (int)(blockIdx.x - first[e]);
+  const int vx0 = (lb % ntx) * kTileX, vy0 = (lb / ntx) * TY;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  const float* __restrict__ r = lv.r32;
+  // 1. the residual of the block's boxes: nodes 2*v0 - 2 + (0 .. S-1) per axis
+  const int gx0 = 2 * vx0 - 2, gy0 = 2 * vy0 - 2;
+  for (int idx = threadIdx.x; idx < S::SX * S::SY * 4; idx += NT) {
+    const int ln = idx >> 2, q = idx & 3;
+    const int gx = gx0 + ln % S::SX, gy = gy0 + ln / S::SX;
+    const bool ok = gx >= 0 && gx < M && gy >= 0 && gy < M;
+    st_copy16z(sm + tile_off(ln, q), ok ? r + ((int64_t)gy * M + gx) * 16 + 4 * q : r, ok);
+  }
+  st_commit();
+  st_wait<0>();
+  __syncthreads();
+  // 2. kb_apply's sums (tensor-core levels leave their interior subdomains to kb_apply_tc)
+  const int vx = vx0 + tx, vy = vy0 + ty;
+  const bool run = vx <= N && vy <= N && !(lv.gtc && vx >= 2 && vx <= N - 2 && vy >= 2 && vy <= N - 2);
+  const int64_t p = (int64_t)vy * V + vx;
+  float acc[RB][NR];
+#pragma unroll
+  for (int i = 0; i < RB; ++i)
+#pragma unroll
+    for (int j = 0; j < NR; ++j) acc[i][j] = 0.f;
+  if (run) {
+    const float* ip = static_cast<const float*>(lv.inv) + ((p >> 5) * NC * RB) * 32 + (p & 31);
+    int k = 0;
+    for (int a1 = 0; a1 < 5; ++a1) {
+      for (int a0 = 0; a0 < 5; ++a0) {
+        const int ln = (2 * ty + a1) * S::SX + 2 * tx + a0;
+#pragma unroll
+        for (int c = 0; c < 2; ++c) {
+          const float4 lo = *reinterpret_cast<const float4*>(sm + tile_off(ln, 2 * c));
+          const float4 hi = *reinterpret_cast<const float4*>(sm + tile_off(ln, 2 * c + 1));
+          const float ra[NR] = {lo.x, lo.y, lo.z, lo.w, hi.x, hi.y, hi.z, hi.w};
+#pragma unroll
+          for (int i = 0; i < RB; ++i) {
+            const float q = ip[(k * RB + i) * 32];
+#pragma unroll
+            for (int j = 0; j < NR; ++j) acc[i][j] += q * ra[j];
+          }
+          ++k;
+        }
+      }
+    }
+    float ra[NR];
+    load_row<float, NR>(r + (g.n_u + p) * NR, ra);
+#pragma unroll
+    for (int i = 0; i < RB; ++i) {
+      const float q = ip[(k * RB + i) * 32];
+#pragma unroll
+      for (int j = 0; j < NR; ++j) acc[i][j] += q * ra[j];
+    }
+  }
+  __syncthreads();  // the staged residual is no longer read
+  // 3. owned row i < 8: node 2v + (q & 1, q >> 1), q = i / 2, component i % 2
+  if (run) {
+#pragma unroll
+    for (int i = 0; i < RB - 1; ++i) {
+      const int q = i >> 1, c = i & 1;
+      const int on = (2 * ty + (q >> 1)) * S::OX + 2 * tx + (q & 1);
+      *reinterpret_cast<float4*>(sm + tile_off(on, 2 * c)) = make_float4(acc[i][0], acc[i][1], acc[i][2], acc[i][3]);
+      *reinterpret_cast<float4*>(sm + tile_off(on, 2 * c + 1)) =
+          make_float4(acc[i][4], acc[i][5], acc[i][6], acc[i][7]);
+    }
+    const double om = lv.omega[p];
+    double2* xp = reinterpret_cast<double2*>(lv.x + (g.n_u + p) * NR);
+#pragma unroll
+    for (int h = 0; h < NR / 2; ++h) {
+      double2 xv = xp[h];
+      xv.x += om * (double)acc[RB - 1][2 * h];
+      xv.y += om * (double)acc[RB - 1][2 * h + 1];
+      xp[h] = xv;
+    }
+  }
+  __syncthreads();
+  // x of the owned nodes, 16 bytes (two RHS of one component) per step: node
+  // J = 2 v0 + (on % OX, on / OX), pair w -> component w / 4, RHS 2(w % 4), +1;
+  // interior nodes only, owner vertex J / 2 (skipped where kb_apply_tc owns it)
+  for (int idx = threadIdx.x; idx < S::OX * S::OY * 8; idx += NT) {
+    const int on = idx >> 3, w = idx & 7;
+    const int Jx = 2 * vx0 + on % S::OX, Jy = 2 * vy0 + on / S::OX;
+    if (Jx < 1 || Jx > 2 * N - 1 || Jy < 1 || Jy > 2 * N - 1) continue;
+    const int ox = Jx >> 1, oy = Jy >> 1;
+    if (lv.gtc && ox >= 2 && ox <= N - 2 && oy >= 2 && oy <= N - 2) continue;
+    const double om = lv.omega[(int64_t)oy * V + ox];
+    const float2 a = *reinterpret_cast<const float2*>(sm + tile_off(on, w >> 1) + 8 * (w & 1));
+    double2* xp = reinterpret_cast<double2*>(lv.x + ((int64_t)Jy * M + Jx) * 16) + w;
+    double2 xv = *xp;
+    xv.x += om * (double)a.x;
+    xv.y += om * (double)a.y;
+    *xp = xv;
   }
 }
 
@@ -1064,6 +1204,11 @@ struct rav_batch {
   bool xfer_f32 = false;
   std::vector<void*> x32_bufs;
   std::vector<BPhase> tc_apply;
+  // tiled apply (kb_apply_tile, 2-D Q2-Q1, fp32 rows, 8 RHS): per depth the
+  // rows of vertices per block (2 or 4), 0 where kb_apply runs; the set-up
+  // tuner's choice is kept in tile_auto (batch_set_apply_tile(-1) restores it)
+  std::vector<int> tile_ty, tile_auto;
+  std::vector<BPhase> apply_tile;
   std::vector<float*> gtc_bufs;  // per lv entry, null where not shared
   int* tc_err = nullptr;         // set by a tensor-core block whose wait gave up
   BPhase fine_res;  // depth-0 residual with norms
@@ -1195,6 +1340,13 @@ static int64_t blk_tc(const BLevel& b, int) {
   return (ni * ni + kTcP - 1) / kTcP;
 }
 static int64_t blk_gemv(const BLevel& b, int t) { return (b.g.n + t / 32 - 1) / (t / 32); }
+static int64_t blk_tile(const BLevel& b, int t) {
+  const int64_t v = b.g.N + 1, ty = t / kTileX;
+  return (v + kTileX - 1) / kTileX * ((v + ty - 1) / ty);
+}
+static bool tile_ok(const rav_batch* bt) {
+  return bt->dim == 2 && bt->nrhs == 8 && bt->prec == RAV_F32 && bt->elem == RAV_ELEM_Q2Q1;
+}
 
 // ---- launches --------------------------------------------------------------
 template <int NR>
@@ -1222,6 +1374,12 @@ static void launch_apply(const rav_batch* bt, const BPhase& ph, int use_b, cudaS
   }
 }
 
+static void launch_tile(const BPhase& ph, int ty, cudaStream_t s) {
+  if (!ph.ne) return;
+  if (ty == 2) kb_apply_tile<2><<<(unsigned)ph.blocks, ph.threads, 0, s>>>(ph.L, ph.first, ph.ne);
+  else kb_apply_tile<4><<<(unsigned)ph.blocks, ph.threads, 0, s>>>(ph.L, ph.first, ph.ne);
+}
+
 template <int D, int NR>
 static int batch_cycle(rav_batch* bt, int nu1, int nu2, cudaStream_t s) {
   const int Dm = bt->depth;
@@ -1233,7 +1391,10 @@ static int batch_cycle(rav_batch* bt, int nu1, int nu2, cudaStream_t s) {
   };
   auto apply = [&](int d, int use_b) {
     ev = bprof_begin(bt, d, PROF_APPLY, s);
-    launch_apply<D, NR>(bt, bt->apply[d], use_b, s);
+    if (d < (int)bt->tile_ty.size() && bt->tile_ty[d])  // fp32 rows: reads r32 either way
+      launch_tile(bt->apply_tile[d], bt->tile_ty[d], s);
+    else
+      launch_apply<D, NR>(bt, bt->apply[d], use_b, s);
     if (bt->use_tc && d < (int)bt->tc_apply.size() && bt->tc_apply[d].ne) {
       const BPhase& tp = bt->tc_apply[d];
       const unsigned grid = (unsigned)std::min<int64_t>(tp.blocks, 152 * 2);
@@ -1344,6 +1505,12 @@ static int build_phases(rav_batch* bt) {
     RAV_TRY(upload_phase(bt, bt->coarse_mask[d], coarse, 256, blk_mask));
     RAV_TRY(upload_phase(bt, bt->coarse_gemv[d], coarse, 256, blk_gemv));
   }
+  bt->apply_tile.resize(Dm);
+  for (int d = 0; d < Dm; ++d) {
+    const int ty = d < (int)bt->tile_ty.size() ? bt->tile_ty[d] : 0;
+    RAV_TRY(upload_phase(bt, bt->apply_tile[d], ty ? bt->apply[d].entries : std::vector<int>{},
+                         kTileX * (ty ? ty : 2), blk_tile));
+  }
   bt->tc_apply.resize(Dm);
   for (int d = 0; d < Dm; ++d) {
     std::vector<int> shared;
@@ -1374,7 +1541,7 @@ static int bind_vectors(rav_batch* bt, double* const* x, const double* const* b)
   // re-upload the descriptors of every phase (they hold copies)
   std::vector<BPhase*> all;
   for (auto* v : {&bt->res_smooth, &bt->apply, &bt->restrict_, &bt->prolong, &bt->coarse_mask, &bt->coarse_gemv,
-                  &bt->tc_apply})
+                  &bt->tc_apply, &bt->apply_tile})
     for (auto& ph : *v) all.push_back(&ph);
   all.push_back(&bt->fine_res);
   for (BPhase* ph : all) {
@@ -1446,6 +1613,30 @@ static int autotune(rav_batch* bt, cudaStream_t s) {
     if (ms < best) { best = ms; bapp = c; }
   }
   bt->tpb_apply = bapp;
+  // per depth: kb_apply or the tiled apply with 2 or 4 rows of vertices per
+  // block (one warp per row wastes lanes where a level has few vertices)
+  bt->tile_ty.assign(bt->depth, 0);
+  if (tile_ok(bt)) {
+    RAV_TRY(build_phases(bt));
+    for (int d = 0; d < bt->depth; ++d) {
+      if (!bt->apply[d].ne) continue;
+      float bd = time_it([&] { launch_apply<2, 8>(bt, bt->apply[d], 0, s); });
+      for (int ty : {2, 4}) {
+        BPhase tmp;
+        int rc = upload_phase(bt, tmp, bt->apply[d].entries, kTileX * ty, blk_tile);
+        const float ms = rc == RAV_OK ? time_it([&] { launch_tile(tmp, ty, s); }) : 1e30f;
+        cudaFree(tmp.L);
+        cudaFree(tmp.first);
+        cudaFree(tmp.prob);
+        RAV_TRY(rc);
+        if (ms < bd) {
+          bd = ms;
+          bt->tile_ty[d] = ty;
+        }
+      }
+    }
+  }
+  bt->tile_auto = bt->tile_ty;
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   RAV_TRY(build_phases(bt));
@@ -1547,7 +1738,7 @@ extern "C" void batch_destroy(rav_batch* bt) {
     cudaEventDestroy(e.b);
   }
   for (auto* v : {&bt->res_smooth, &bt->apply, &bt->restrict_, &bt->prolong, &bt->coarse_mask, &bt->coarse_gemv,
-                  &bt->tc_apply})
+                  &bt->tc_apply, &bt->apply_tile})
     for (auto& ph : *v) {
       cudaFree(ph.L);
       cudaFree(ph.first);
@@ -1563,6 +1754,28 @@ extern "C" void batch_destroy(rav_batch* bt) {
   cudaFree(bt->norms);
   if (bt->norms_h) cudaFreeHost(bt->norms_h);
   delete bt;
+}
+
+extern "C" int batch_set_apply_tile(rav_batch* bt, int ty, rav_stream stream) {
+  if (!bt || !(ty == -1 || ty == 0 || ty == 2 || ty == 4)) return RAV_ERR_ARG;
+  if (ty > 0 && !tile_ok(bt)) return RAV_ERR_ARG;
+  cudaStream_t s = S(stream);
+  RAV_CUDA(cudaStreamSynchronize(s));
+  if (ty < 0) bt->tile_ty = bt->tile_auto;
+  else bt->tile_ty.assign(bt->depth, ty);
+  if (bt->graph) {  // the captured cycle holds the previous apply kernels
+    cudaGraphExecDestroy(bt->graph);
+    bt->graph = nullptr;
+  }
+  bt->cur_x.clear();  // descriptors are re-uploaded at the next bind
+  RAV_TRY(build_phases(bt));
+  RAV_CUDA(cudaStreamSynchronize(s));
+  return RAV_OK;
+}
+
+extern "C" int batch_get_apply_tile(const rav_batch* bt, int depth) {
+  if (!bt || depth < 0 || depth >= bt->depth) return RAV_ERR_ARG;
+  return depth < (int)bt->tile_ty.size() ? bt->tile_ty[depth] : 0;
 }
 
 extern "C" int batch_get_tuning(const rav_batch* bt, int out[2]) {

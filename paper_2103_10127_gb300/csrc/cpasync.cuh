@@ -26,13 +26,17 @@ __device__ __forceinline__ void st_copy(void* dst, const void* src) {
     asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" ::"r"(st_smem(dst)), "l"(src), "n"(BYTES) : "memory");
   }
 }
-// cp.async of 4 or 8 bytes, zero-filled when !valid (src is not read then).
+// cp.async of 4, 8 or 16 bytes, zero-filled when !valid (src is not read then).
 __device__ __forceinline__ void st_copy4z(void* dst, const void* src, bool valid) {
   asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(st_smem(dst)), "l"(src), "r"(valid ? 4 : 0)
                : "memory");
 }
 __device__ __forceinline__ void st_copy8z(void* dst, const void* src, bool valid) {
   asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(st_smem(dst)), "l"(src), "r"(valid ? 8 : 0)
+               : "memory");
+}
+__device__ __forceinline__ void st_copy16z(void* dst, const void* src, bool valid) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(st_smem(dst)), "l"(src), "r"(valid ? 16 : 0)
                : "memory");
 }
 __device__ __forceinline__ void st_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
