@@ -720,7 +720,7 @@ def run_batch(args, q1=False):
                                   f"omega {omega}, FP32 patch inverses, FP64 residuals",
                       "problems": nprob, "rhs": nrhs, "dofs_total": dofs, "sizes_min_max": [int(sizes.min()),
                                                                                             int(sizes.max())],
-                      "tuning": bt.tuning(), "setup_s": setup_s},
+                      "tuning": dict(bt.tuning(), apply_tile_by_depth=bt.apply_tile()), "setup_s": setup_s},
            "gpu_launches": int(launches), "clocks": clocks, "breakdown_ms_per_cycle": breakdown,
            "single_problem_fp64": None if args.no_single else {
                "ms_per_cycle_all": single_ms, "value": dofs * nrhs / (single_ms / 1e3), "unit": "DoF/s",

@@ -483,16 +483,19 @@ int batch_get_tuning(const rav_batch* bt, int out[2]);
  * subdomain boxes (Sec. 3's restriction) in shared memory with coalesced
  * copies and adds the velocity corrections (Eq. 13) to x by contiguous rows of
  * owned nodes, with the same sums in the same order as the untiled kernel (bit
- * for bit the same results).  batch_setup chooses per depth between untiled,
- * ty = 2 and ty = 4 by timing each on the batch's own data.
- * batch_set_apply_tile: ty = 2 or 4 tiles every depth, 0 none, -1 restores
- * batch_setup's choice; synchronises the stream and drops the captured cycle;
- * RAV_ERR_ARG for other values, or for 2 or 4 on any other batch.
- * batch_get_apply_tile returns the ty in use at depth (0 = finest; 0 =
- * untiled), RAV_ERR_ARG outside 0 .. depths - 1.  The paper has no
- * counterpart. */
-int batch_set_apply_tile(rav_batch* bt, int ty, rav_stream stream);
-int batch_get_apply_tile(const rav_batch* bt, int depth);
+ * for bit the same results); split = 2 gives each row of vertices two warps,
+ * owned rows 0-3 and 4-8 of the same subdomains.  batch_setup chooses per
+ * depth between untiled and ty in {2, 4} x split in {1, 2} by timing each on
+ * the batch's own data.
+ * batch_set_apply_tile: ty = 2 or 4 tiles every depth with the given split, 0
+ * none, -1 restores batch_setup's choice (split 1 or 2 is still required);
+ * synchronises the stream and drops the captured cycle; RAV_ERR_ARG for other
+ * values, or for ty 2 or 4 on any other batch.
+ * batch_get_apply_tile: out[0] = ty in use at depth (0 = finest; 0 =
+ * untiled), out[1] = split (1 when untiled); RAV_ERR_ARG outside 0 .. depths
+ * - 1.  The paper has no counterpart. */
+int batch_set_apply_tile(rav_batch* bt, int ty, int split, rav_stream stream);
+int batch_get_apply_tile(const rav_batch* bt, int depth, int out[2]);
 /* Shared-inverse apply on the tensor cores (2-D Q2-Q1 batches with RAV_F32
  * rows and 8 right-hand sides; RAV_ERR_ARG otherwise).  On a uniform grid
  * with constant viscosity every interior subdomain of a level (vertex 2 .. N-2

@@ -217,19 +217,18 @@ class Batch:
         check(_capi.load().batch_get_tuning(self.h, out), "batch_get_tuning")
         return {"residual_threads": out[0], "apply_threads": out[1]}
 
-    def apply_tile(self, ty=None, stream=None):
-        """Tiled apply rows of vertices per block at each depth (0 = untiled);
-        ty = 2, 4, 0 or -1 (the set-up tuner's choice) first sets every depth
-        (batch_set_apply_tile)."""
+    def apply_tile(self, ty=None, split=1, stream=None):
+        """(rows of vertices per block, warps per row) of the tiled apply at
+        each depth, (0, 1) where untiled; ty = 2, 4, 0 or -1 (the set-up
+        tuner's choice) first sets every depth (batch_set_apply_tile)."""
         lib = _capi.load()
         if ty is not None:
-            check(lib.batch_set_apply_tile(self.h, int(ty), _stream(stream)), "batch_set_apply_tile")
+            check(lib.batch_set_apply_tile(self.h, int(ty), int(split), _stream(stream)), "batch_set_apply_tile")
         out = []
+        v = (ctypes.c_int * 2)()
         for d in range(max(m.nlev for m in self.mgs) - 1):
-            k = lib.batch_get_apply_tile(self.h, d)
-            if k < 0:
-                raise RavError(k, "batch_get_apply_tile")
-            out.append(k)
+            check(lib.batch_get_apply_tile(self.h, d, v), "batch_get_apply_tile")
+            out.append((v[0], v[1]))
         return out
 
     def tensor_apply(self, enable=True, stream=None):

@@ -92,8 +92,8 @@ _SIGS = {
     "batch_setup": (I32, [P, P, I32, I32, P, ctypes.POINTER(P)]),
     "batch_destroy": (None, [P]),
     "batch_get_tuning": (I32, [P, ctypes.POINTER(I32)]),
-    "batch_set_apply_tile": (I32, [P, I32, P]),
-    "batch_get_apply_tile": (I32, [P, I32]),
+    "batch_set_apply_tile": (I32, [P, I32, I32, P]),
+    "batch_get_apply_tile": (I32, [P, I32, ctypes.POINTER(I32)]),
     "batch_profile_enable": (I32, [P, I32]),
     "batch_profile_read": (I32, [P, I32, I32, I64P, ctypes.POINTER(F64)]),
     "batch_vcycle": (I32, [P, P, P, I32, I32, P]),

@@ -379,12 +379,79 @@ struct TileShape {
   static constexpr int BYTES = (SX * SY + 1) / 2 * 128;       // >= OX * OY / 2 * 128
 };
 
-template <int TY>
-__global__ void __launch_bounds__(kTileX * TY, 16 / TY)
+// Sums of owned rows I0 .. I1-1 of the subdomain at (tx, ty) of the block
+// (kb_apply's order: box positions k = 2 (a0 + 5 a1) + c, pressure last).
+template <int I0, int I1, int RMAX>
+__device__ __forceinline__ void tile_rows(const unsigned char* sm, int sx, const float* __restrict__ ip,
+                                          const float* __restrict__ rp, int tx, int ty, float (&acc)[RMAX][8]) {
+  constexpr int RB = BoxT<2>::RB;
+  int k = 0;
+  for (int a1 = 0; a1 < 5; ++a1) {
+    for (int a0 = 0; a0 < 5; ++a0) {
+      const int ln = (2 * ty + a1) * sx + 2 * tx + a0;
+#pragma unroll
+      for (int c = 0; c < 2; ++c) {
+        const float4 lo = *reinterpret_cast<const float4*>(sm + tile_off(ln, 2 * c));
+        const float4 hi = *reinterpret_cast<const float4*>(sm + tile_off(ln, 2 * c + 1));
+        const float ra[8] = {lo.x, lo.y, lo.z, lo.w, hi.x, hi.y, hi.z, hi.w};
+#pragma unroll
+        for (int i = I0; i < I1; ++i) {
+          const float q = ip[(k * RB + i) * 32];
+#pragma unroll
+          for (int j = 0; j < 8; ++j) acc[i - I0][j] += q * ra[j];
+        }
+        ++k;
+      }
+    }
+  }
+  float ra[8];
+  load_row<float, 8>(rp, ra);
+#pragma unroll
+  for (int i = I0; i < I1; ++i) {
+    const float q = ip[(k * RB + i) * 32];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) acc[i - I0][j] += q * ra[j];
+  }
+}
+
+// Owned rows I0 .. I1-1 out: row i < 8 (node 2v + (q & 1, q >> 1), q = i / 2,
+// component i % 2) into the block's correction buffer, row 8 (the pressure)
+// straight into x.
+template <int I0, int I1, int RMAX>
+__device__ __forceinline__ void tile_store(unsigned char* sm, int ox, int tx, int ty, double om,
+                                           double* __restrict__ xp, const float (&acc)[RMAX][8]) {
+#pragma unroll
+  for (int i = I0; i < I1; ++i) {
+    if (i < 8) {
+      const int q = i >> 1, c = i & 1;
+      const int on = (2 * ty + (q >> 1)) * ox + 2 * tx + (q & 1);
+      const float* a = acc[i - I0];
+      *reinterpret_cast<float4*>(sm + tile_off(on, 2 * c)) = make_float4(a[0], a[1], a[2], a[3]);
+      *reinterpret_cast<float4*>(sm + tile_off(on, 2 * c + 1)) = make_float4(a[4], a[5], a[6], a[7]);
+    } else {
+      double2* x2 = reinterpret_cast<double2*>(xp);
+#pragma unroll
+      for (int h = 0; h < 4; ++h) {
+        double2 xv = x2[h];
+        xv.x += om * (double)acc[i - I0][2 * h];
+        xv.y += om * (double)acc[i - I0][2 * h + 1];
+        x2[h] = xv;
+      }
+    }
+  }
+}
+
+// SPLIT = 1: one thread per subdomain, all 9 owned rows (72 accumulators).
+// SPLIT = 2: two warps per row of vertices, rows 0-3 and rows 4-8 of the same
+// subdomains (at most 40 accumulators, twice the warps per SM); each reads the
+// whole staged box and its own rows of the stored inverse.
+template <int TY, int SPLIT>
+__global__ void __launch_bounds__(kTileX * TY * SPLIT, SPLIT == 1 ? 16 / TY : (TY == 2 ? 5 : 2))
     kb_apply_tile(const BLevel* __restrict__ L, const int64_t* __restrict__ first, int ne) {
   using B = BoxT<2>;
   using S = TileShape<TY>;
-  constexpr int NC = B::NC, RB = B::RB, NR = 8, NT = kTileX * TY;
+  constexpr int NC = B::NC, RB = B::RB, NR = 8, NT = kTileX * TY * SPLIT;
+  constexpr int RMAX = SPLIT == 1 ? RB : 5, IH = SPLIT == 1 ? RB : 4;  // rows of the first warp: 0 .. IH-1
   static_assert(B::NCH == 1 && RB == 9, "one thread per subdomain, 9 owned rows");
   __shared__ __align__(128) unsigned char sm[S::BYTES];
   const int e = find_entry(first, ne, blockIdx.x);
@@ -394,7 +461,7 @@ __global__ void __launch_bounds__(kTileX * TY, 16 / TY)
   const int ntx = (V + kTileX - 1) / kTileX;
   const int lb = (int)(blockIdx.x - first[e]);
   const int vx0 = (lb % ntx) * kTileX, vy0 = (lb / ntx) * TY;
-  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  const int w = threadIdx.x >> 5, tx = threadIdx.x & 31, ty = w / SPLIT, h = w % SPLIT;
   const float* __restrict__ r = lv.r32;
   // 1. the residual of the block's boxes: nodes 2*v0 - 2 + (0 .. S-1) per axis
   const int gx0 = 2 * vx0 - 2, gy0 = 2 * vy0 - 2;
@@ -411,79 +478,41 @@ __global__ void __launch_bounds__(kTileX * TY, 16 / TY)
   const int vx = vx0 + tx, vy = vy0 + ty;
   const bool run = vx <= N && vy <= N && !(lv.gtc && vx >= 2 && vx <= N - 2 && vy >= 2 && vy <= N - 2);
   const int64_t p = (int64_t)vy * V + vx;
-  float acc[RB][NR];
+  float acc[RMAX][NR];
 #pragma unroll
-  for (int i = 0; i < RB; ++i)
+  for (int i = 0; i < RMAX; ++i)
 #pragma unroll
     for (int j = 0; j < NR; ++j) acc[i][j] = 0.f;
+  const float* ip = static_cast<const float*>(lv.inv) + ((p >> 5) * NC * RB) * 32 + (p & 31);
+  const float* rp = r + (g.n_u + p) * NR;
   if (run) {
-    const float* ip = static_cast<const float*>(lv.inv) + ((p >> 5) * NC * RB) * 32 + (p & 31);
-    int k = 0;
-    for (int a1 = 0; a1 < 5; ++a1) {
-      for (int a0 = 0; a0 < 5; ++a0) {
-        const int ln = (2 * ty + a1) * S::SX + 2 * tx + a0;
-#pragma unroll
-        for (int c = 0; c < 2; ++c) {
-          const float4 lo = *reinterpret_cast<const float4*>(sm + tile_off(ln, 2 * c));
-          const float4 hi = *reinterpret_cast<const float4*>(sm + tile_off(ln, 2 * c + 1));
-          const float ra[NR] = {lo.x, lo.y, lo.z, lo.w, hi.x, hi.y, hi.z, hi.w};
-#pragma unroll
-          for (int i = 0; i < RB; ++i) {
-            const float q = ip[(k * RB + i) * 32];
-#pragma unroll
-            for (int j = 0; j < NR; ++j) acc[i][j] += q * ra[j];
-          }
-          ++k;
-        }
-      }
-    }
-    float ra[NR];
-    load_row<float, NR>(r + (g.n_u + p) * NR, ra);
-#pragma unroll
-    for (int i = 0; i < RB; ++i) {
-      const float q = ip[(k * RB + i) * 32];
-#pragma unroll
-      for (int j = 0; j < NR; ++j) acc[i][j] += q * ra[j];
-    }
+    if (h == 0) tile_rows<0, IH, RMAX>(sm, S::SX, ip, rp, tx, ty, acc);
+    else tile_rows<4, RB, RMAX>(sm, S::SX, ip, rp, tx, ty, acc);
   }
   __syncthreads();  // the staged residual is no longer read
-  // 3. owned row i < 8: node 2v + (q & 1, q >> 1), q = i / 2, component i % 2
   if (run) {
-#pragma unroll
-    for (int i = 0; i < RB - 1; ++i) {
-      const int q = i >> 1, c = i & 1;
-      const int on = (2 * ty + (q >> 1)) * S::OX + 2 * tx + (q & 1);
-      *reinterpret_cast<float4*>(sm + tile_off(on, 2 * c)) = make_float4(acc[i][0], acc[i][1], acc[i][2], acc[i][3]);
-      *reinterpret_cast<float4*>(sm + tile_off(on, 2 * c + 1)) =
-          make_float4(acc[i][4], acc[i][5], acc[i][6], acc[i][7]);
-    }
     const double om = lv.omega[p];
-    double2* xp = reinterpret_cast<double2*>(lv.x + (g.n_u + p) * NR);
-#pragma unroll
-    for (int h = 0; h < NR / 2; ++h) {
-      double2 xv = xp[h];
-      xv.x += om * (double)acc[RB - 1][2 * h];
-      xv.y += om * (double)acc[RB - 1][2 * h + 1];
-      xp[h] = xv;
-    }
+    double* xp = lv.x + (g.n_u + p) * NR;
+    if (h == 0) tile_store<0, IH, RMAX>(sm, S::OX, tx, ty, om, xp, acc);
+    else tile_store<4, RB, RMAX>(sm, S::OX, tx, ty, om, xp, acc);
   }
   __syncthreads();
   // x of the owned nodes, 16 bytes (two RHS of one component) per step: node
   // J = 2 v0 + (on % OX, on / OX), pair w -> component w / 4, RHS 2(w % 4), +1;
   // interior nodes only, owner vertex J / 2 (skipped where kb_apply_tc owns it)
   for (int idx = threadIdx.x; idx < S::OX * S::OY * 8; idx += NT) {
-    const int on = idx >> 3, w = idx & 7;
+    const int on = idx >> 3, pw = idx & 7;
     const int Jx = 2 * vx0 + on % S::OX, Jy = 2 * vy0 + on / S::OX;
     if (Jx < 1 || Jx > 2 * N - 1 || Jy < 1 || Jy > 2 * N - 1) continue;
     const int ox = Jx >> 1, oy = Jy >> 1;
     if (lv.gtc && ox >= 2 && ox <= N - 2 && oy >= 2 && oy <= N - 2) continue;
     const double om = lv.omega[(int64_t)oy * V + ox];
-    const float2 a = *reinterpret_cast<const float2*>(sm + tile_off(on, w >> 1) + 8 * (w & 1));
-    double2* xp = reinterpret_cast<double2*>(lv.x + ((int64_t)Jy * M + Jx) * 16) + w;
-    double2 xv = *xp;
+    const float2 a = *reinterpret_cast<const float2*>(sm + tile_off(on, pw >> 1) + 8 * (pw & 1));
+    double2* xq = reinterpret_cast<double2*>(lv.x + ((int64_t)Jy * M + Jx) * 16) + pw;
+    double2 xv = *xq;
     xv.x += om * (double)a.x;
     xv.y += om * (double)a.y;
-    *xp = xv;
+    *xq = xv;
   }
 }
 
@@ -1205,9 +1234,10 @@ struct rav_batch {
   std::vector<void*> x32_bufs;
   std::vector<BPhase> tc_apply;
   // tiled apply (kb_apply_tile, 2-D Q2-Q1, fp32 rows, 8 RHS): per depth the
-  // rows of vertices per block (2 or 4), 0 where kb_apply runs; the set-up
-  // tuner's choice is kept in tile_auto (batch_set_apply_tile(-1) restores it)
-  std::vector<int> tile_ty, tile_auto;
+  // rows of vertices per block (2 or 4), 0 where kb_apply runs, and the warps
+  // per row of vertices (1 or 2); the set-up tuner's choice is kept in
+  // tile_auto / split_auto (batch_set_apply_tile(-1, ...) restores it)
+  std::vector<int> tile_ty, tile_auto, tile_split, split_auto;
   std::vector<BPhase> apply_tile;
   std::vector<float*> gtc_bufs;  // per lv entry, null where not shared
   int* tc_err = nullptr;         // set by a tensor-core block whose wait gave up
@@ -1340,8 +1370,9 @@ static int64_t blk_tc(const BLevel& b, int) {
   return (ni * ni + kTcP - 1) / kTcP;
 }
 static int64_t blk_gemv(const BLevel& b, int t) { return (b.g.n + t / 32 - 1) / (t / 32); }
+template <int SPLIT>  // threads t = 32 x TY x SPLIT
 static int64_t blk_tile(const BLevel& b, int t) {
-  const int64_t v = b.g.N + 1, ty = t / kTileX;
+  const int64_t v = b.g.N + 1, ty = t / (kTileX * SPLIT);
   return (v + kTileX - 1) / kTileX * ((v + ty - 1) / ty);
 }
 static bool tile_ok(const rav_batch* bt) {
@@ -1374,10 +1405,13 @@ static void launch_apply(const rav_batch* bt, const BPhase& ph, int use_b, cudaS
   }
 }
 
-static void launch_tile(const BPhase& ph, int ty, cudaStream_t s) {
+static void launch_tile(const BPhase& ph, int ty, int split, cudaStream_t s) {
   if (!ph.ne) return;
-  if (ty == 2) kb_apply_tile<2><<<(unsigned)ph.blocks, ph.threads, 0, s>>>(ph.L, ph.first, ph.ne);
-  else kb_apply_tile<4><<<(unsigned)ph.blocks, ph.threads, 0, s>>>(ph.L, ph.first, ph.ne);
+  const unsigned nb = (unsigned)ph.blocks;
+  if (ty == 2 && split == 1) kb_apply_tile<2, 1><<<nb, ph.threads, 0, s>>>(ph.L, ph.first, ph.ne);
+  else if (ty == 4 && split == 1) kb_apply_tile<4, 1><<<nb, ph.threads, 0, s>>>(ph.L, ph.first, ph.ne);
+  else if (ty == 2) kb_apply_tile<2, 2><<<nb, ph.threads, 0, s>>>(ph.L, ph.first, ph.ne);
+  else kb_apply_tile<4, 2><<<nb, ph.threads, 0, s>>>(ph.L, ph.first, ph.ne);
 }
 
 template <int D, int NR>
@@ -1392,7 +1426,7 @@ static int batch_cycle(rav_batch* bt, int nu1, int nu2, cudaStream_t s) {
   auto apply = [&](int d, int use_b) {
     ev = bprof_begin(bt, d, PROF_APPLY, s);
     if (d < (int)bt->tile_ty.size() && bt->tile_ty[d])  // fp32 rows: reads r32 either way
-      launch_tile(bt->apply_tile[d], bt->tile_ty[d], s);
+      launch_tile(bt->apply_tile[d], bt->tile_ty[d], bt->tile_split[d], s);
     else
       launch_apply<D, NR>(bt, bt->apply[d], use_b, s);
     if (bt->use_tc && d < (int)bt->tc_apply.size() && bt->tc_apply[d].ne) {
@@ -1508,8 +1542,9 @@ static int build_phases(rav_batch* bt) {
   bt->apply_tile.resize(Dm);
   for (int d = 0; d < Dm; ++d) {
     const int ty = d < (int)bt->tile_ty.size() ? bt->tile_ty[d] : 0;
+    const int sp = ty ? bt->tile_split[d] : 1;
     RAV_TRY(upload_phase(bt, bt->apply_tile[d], ty ? bt->apply[d].entries : std::vector<int>{},
-                         kTileX * (ty ? ty : 2), blk_tile));
+                         kTileX * (ty ? ty : 2) * sp, sp == 2 ? blk_tile<2> : blk_tile<1>));
   }
   bt->tc_apply.resize(Dm);
   for (int d = 0; d < Dm; ++d) {
@@ -1616,27 +1651,31 @@ static int autotune(rav_batch* bt, cudaStream_t s) {
   // per depth: kb_apply or the tiled apply with 2 or 4 rows of vertices per
   // block (one warp per row wastes lanes where a level has few vertices)
   bt->tile_ty.assign(bt->depth, 0);
+  bt->tile_split.assign(bt->depth, 1);
   if (tile_ok(bt)) {
     RAV_TRY(build_phases(bt));
     for (int d = 0; d < bt->depth; ++d) {
       if (!bt->apply[d].ne) continue;
       float bd = time_it([&] { launch_apply<2, 8>(bt, bt->apply[d], 0, s); });
-      for (int ty : {2, 4}) {
-        BPhase tmp;
-        int rc = upload_phase(bt, tmp, bt->apply[d].entries, kTileX * ty, blk_tile);
-        const float ms = rc == RAV_OK ? time_it([&] { launch_tile(tmp, ty, s); }) : 1e30f;
-        cudaFree(tmp.L);
-        cudaFree(tmp.first);
-        cudaFree(tmp.prob);
-        RAV_TRY(rc);
-        if (ms < bd) {
-          bd = ms;
-          bt->tile_ty[d] = ty;
+      for (int sp : {1, 2})
+        for (int ty : {2, 4}) {
+          BPhase tmp;
+          int rc = upload_phase(bt, tmp, bt->apply[d].entries, kTileX * ty * sp, sp == 2 ? blk_tile<2> : blk_tile<1>);
+          const float ms = rc == RAV_OK ? time_it([&] { launch_tile(tmp, ty, sp, s); }) : 1e30f;
+          cudaFree(tmp.L);
+          cudaFree(tmp.first);
+          cudaFree(tmp.prob);
+          RAV_TRY(rc);
+          if (ms < bd) {
+            bd = ms;
+            bt->tile_ty[d] = ty;
+            bt->tile_split[d] = sp;
+          }
         }
-      }
     }
   }
   bt->tile_auto = bt->tile_ty;
+  bt->split_auto = bt->tile_split;
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   RAV_TRY(build_phases(bt));
@@ -1756,13 +1795,18 @@ extern "C" void batch_destroy(rav_batch* bt) {
   delete bt;
 }
 
-extern "C" int batch_set_apply_tile(rav_batch* bt, int ty, rav_stream stream) {
-  if (!bt || !(ty == -1 || ty == 0 || ty == 2 || ty == 4)) return RAV_ERR_ARG;
+extern "C" int batch_set_apply_tile(rav_batch* bt, int ty, int split, rav_stream stream) {
+  if (!bt || !(ty == -1 || ty == 0 || ty == 2 || ty == 4) || !(split == 1 || split == 2)) return RAV_ERR_ARG;
   if (ty > 0 && !tile_ok(bt)) return RAV_ERR_ARG;
   cudaStream_t s = S(stream);
   RAV_CUDA(cudaStreamSynchronize(s));
-  if (ty < 0) bt->tile_ty = bt->tile_auto;
-  else bt->tile_ty.assign(bt->depth, ty);
+  if (ty < 0) {
+    bt->tile_ty = bt->tile_auto;
+    bt->tile_split = bt->split_auto;
+  } else {
+    bt->tile_ty.assign(bt->depth, ty);
+    bt->tile_split.assign(bt->depth, split);
+  }
   if (bt->graph) {  // the captured cycle holds the previous apply kernels
     cudaGraphExecDestroy(bt->graph);
     bt->graph = nullptr;
@@ -1773,9 +1817,12 @@ extern "C" int batch_set_apply_tile(rav_batch* bt, int ty, rav_stream stream) {
   return RAV_OK;
 }
 
-extern "C" int batch_get_apply_tile(const rav_batch* bt, int depth) {
-  if (!bt || depth < 0 || depth >= bt->depth) return RAV_ERR_ARG;
-  return depth < (int)bt->tile_ty.size() ? bt->tile_ty[depth] : 0;
+extern "C" int batch_get_apply_tile(const rav_batch* bt, int depth, int out[2]) {
+  if (!bt || !out || depth < 0 || depth >= bt->depth) return RAV_ERR_ARG;
+  const bool t = depth < (int)bt->tile_ty.size() && bt->tile_ty[depth];
+  out[0] = t ? bt->tile_ty[depth] : 0;
+  out[1] = t ? bt->tile_split[depth] : 1;
+  return RAV_OK;
 }
 
 extern "C" int batch_get_tuning(const rav_batch* bt, int out[2]) {

@@ -346,46 +346,46 @@ def test_f32_coarse_grid_work_batched_solve_takes_the_same_cycles(nrhs):
 @pytest.mark.parametrize("tc", [False, True])
 def test_tiled_apply_equals_untiled_bitwise(tc):
     """batch_set_apply_tile: the tiled apply (32 x 2 or 32 x 4 vertices per
-    block, several blocks per row and ragged edges on these sizes) gives the
-    untiled kernel's cycle bit for bit, also where the tensor-core apply owns
-    the interior subdomains."""
+    block, one warp or two per row of vertices; several blocks per row and
+    ragged edges on these sizes) gives the untiled kernel's cycle bit for bit,
+    also where the tensor-core apply owns the interior subdomains."""
     nrhs = 8
     mgs, sms, xs, bs = make_batch(SIZES, nrhs, R.F32, seed=17)
     bt = R.Batch(mgs, sms, nrhs)
     auto = bt.apply_tile()
-    assert all(t in (0, 2, 4) for t in auto)
+    assert all(t in ((0, 1), (2, 1), (4, 1), (2, 2), (4, 2)) for t in auto)
     if tc:
         assert bt.tensor_apply(True) > 0
     x_in = [x.clone() for x in xs]
-    assert bt.apply_tile(0) == [0] * len(auto)
+    assert bt.apply_tile(0) == [(0, 1)] * len(auto)
     ref = [x.clone() for x in x_in]
     bt.vcycle(ref, bs, 2, 2)
     bt.vcycle(ref, bs, 2, 2)
-    for ty in (2, 4):
-        assert bt.apply_tile(ty) == [ty] * len(auto)
+    for ty, split in ((2, 1), (4, 1), (2, 2), (4, 2)):
+        assert bt.apply_tile(ty, split) == [(ty, split)] * len(auto)
         got = [x.clone() for x in x_in]
         bt.vcycle(got, bs, 2, 2)
         bt.vcycle(got, bs, 2, 2)
         for p in range(len(SIZES)):
-            assert torch.equal(got[p], ref[p]), (ty, p)
+            assert torch.equal(got[p], ref[p]), (ty, split, p)
     assert bt.apply_tile(-1) == auto
 
 
 def test_tiled_apply_arguments():
     """Tiles only for 2-D Q2-Q1 batches with fp32 rows and 8 right-hand sides;
-    ty in {-1, 0, 2, 4}."""
+    ty in {-1, 0, 2, 4}, split in {1, 2}."""
     mgs, sms, xs, bs = make_batch(SIZES[:2], 8, R.F32, seed=19)
     bt = R.Batch(mgs, sms, 8)
-    for ty in (1, 3, 8, -2):
+    for ty, split in ((1, 1), (3, 1), (8, 1), (-2, 1), (2, 0), (2, 3), (4, 4)):
         with pytest.raises(R.RavError):
-            bt.apply_tile(ty)
+            bt.apply_tile(ty, split)
     mgs4, sms4, _, _ = make_batch(SIZES[:2], 4, R.F32, seed=19)
     bt4 = R.Batch(mgs4, sms4, 4)
-    assert bt4.apply_tile() == [0] * (max(m.nlev for m in mgs4) - 1)
+    assert bt4.apply_tile() == [(0, 1)] * (max(m.nlev for m in mgs4) - 1)
     with pytest.raises(R.RavError):
         bt4.apply_tile(2)
     mgs64, sms64, _, _ = make_batch(SIZES[:2], 8, R.F64_ROWS, seed=19)
     bt64 = R.Batch(mgs64, sms64, 8)
     with pytest.raises(R.RavError):
         bt64.apply_tile(4)
-    assert bt64.apply_tile(0) == [0] * (max(m.nlev for m in mgs64) - 1)
+    assert bt64.apply_tile(0) == [(0, 1)] * (max(m.nlev for m in mgs64) - 1)
