@@ -60,6 +60,18 @@ def test_invalid_arguments_are_rejected_without_a_gpu():
     rate = ctypes.c_double()
     assert lib.rav_hbm_read_rate(8, ctypes.byref(rate), None) == -1  # fewer than 16 bytes
     assert lib.rav_hbm_read_rate(1 << 20, None, None) == -1
+    # the reduced-precision coarse-grid forms and the batched tile choice
+    assert lib.rav_set_coarse_residual_f32(None, 1, 0, None) == -1
+    assert lib.rav_get_coarse_residual_f32(None) == -1
+    assert lib.rav_set_transfers_f32(None, 1, None) == -1
+    assert lib.rav_get_transfers_f32(None) == -1
+    assert lib.batch_set_coarse_residual_f32(None, 1, None) == -1
+    assert lib.batch_coarse_residual_f32(None) == -1
+    assert lib.batch_set_transfers_f32(None, 1, None) == -1
+    assert lib.batch_transfers_f32(None) == -1
+    assert lib.batch_set_apply_tile(None, 2, 2, None) == -1
+    tile = (ctypes.c_int * 2)()
+    assert lib.batch_get_apply_tile(None, 0, tile) == -1
     assert lib.rav_strerror(-3) == b"singular subdomain system"
 
 
