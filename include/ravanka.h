@@ -464,7 +464,9 @@ int rav_reset_omega(rav_smoother* sm, rav_stream stream);
  * dimension, one element: Q2-Q1 or Q1-Q1) with their RAV smoothers, which must store dense owned rows
  * (RAV_F32 or RAV_F64_ROWS), and advances nrhs (1, 2, 4 or 8) right-hand
  * sides of every problem together.  Vectors of problem p are RHS-interleaved:
- * x_dev[p][row * nrhs + k], n(p) * nrhs doubles, numbering as above.  Each
+ * x_dev[p][row * nrhs + k], n(p) * nrhs doubles, numbering as above; with
+ * nrhs >= 2 they must be 16-byte aligned (rows are read two doubles at a
+ * time), else batch_vcycle and solve_batched return RAV_ERR_ARG.  Each
  * phase of the V-cycle is one kernel launch over all problems; the cycle is
  * captured into a CUDA graph on first use and replayed.  Per right-hand side
  * the result equals the single-problem vcycle() with the same smoother bit for

@@ -19,6 +19,7 @@
 #include <cuda_bf16.h>
 
 #include <algorithm>
+#include <cstdint>
 #include <cmath>
 #include <type_traits>
 #include <vector>
@@ -1892,11 +1893,17 @@ extern "C" int batch_profile_read(rav_batch* bt, int depth, int kind, int64_t* l
   return RAV_OK;
 }
 
+// The kernels read a row's nrhs values of x and b two doubles at a time when
+// nrhs >= 2, so those vectors must start on a 16-byte boundary.
+static bool bvec_ok(const rav_batch* bt, const void* v) {
+  return v && (bt->nrhs == 1 || (reinterpret_cast<uintptr_t>(v) & 15) == 0);
+}
+
 extern "C" int batch_vcycle(rav_batch* bt, double* const* x, const double* const* b, int nu1, int nu2,
                             rav_stream stream) {
   if (!bt || !x || !b || nu1 < 0 || nu2 < 0) return RAV_ERR_ARG;
   for (int p = 0; p < bt->nprob; ++p)
-    if (!x[p] || !b[p]) return RAV_ERR_ARG;
+    if (!bvec_ok(bt, x[p]) || !bvec_ok(bt, b[p])) return RAV_ERR_ARG;
   cudaStream_t s = S(stream);
   RAV_CUDA(cudaStreamSynchronize(s));  // descriptors are rewritten below
   RAV_TRY(bind_vectors(bt, x, b));
@@ -1907,7 +1914,7 @@ extern "C" int solve_batched(rav_batch* bt, double* const* x, const double* cons
                              int* iters, double* ratios, rav_stream stream) {
   if (!bt || !x || !b || !o || o->maxit < 0 || !(o->tol > 0) || o->outer != 0) return RAV_ERR_ARG;
   for (int p = 0; p < bt->nprob; ++p)
-    if (!x[p] || !b[p]) return RAV_ERR_ARG;
+    if (!bvec_ok(bt, x[p]) || !bvec_ok(bt, b[p])) return RAV_ERR_ARG;
   cudaStream_t s = S(stream);
   RAV_CUDA(cudaStreamSynchronize(s));
   RAV_TRY(bind_vectors(bt, x, b));

@@ -389,3 +389,21 @@ def test_tiled_apply_arguments():
     with pytest.raises(R.RavError):
         bt64.apply_tile(4)
     assert bt64.apply_tile(0) == [(0, 1)] * (max(m.nlev for m in mgs64) - 1)
+
+
+def test_misaligned_vectors_are_rejected():
+    """With nrhs >= 2 the batched kernels read rows of x and b two doubles at a
+    time: batch_vcycle and solve_batched refuse vectors that do not start on a
+    16-byte boundary (RAV_ERR_ARG, before any launch); aligned ones still run."""
+    mgs, sms, xs, bs = make_batch(SIZES[:2], 2, R.F32, seed=23)
+    bt = R.Batch(mgs, sms, 2)
+    buf = torch.zeros(xs[0].numel() + 1, dtype=torch.float64, device="cuda")
+    shifted = buf[1:].view(xs[0].shape)
+    assert shifted.data_ptr() % 16 == 8
+    with pytest.raises(R.RavError):
+        bt.vcycle([shifted, xs[1]], bs, 2, 2)
+    with pytest.raises(R.RavError):
+        bt.solve(xs, [shifted, bs[1]], tol=1e-8, maxit=3)
+    x_in = [x.clone() for x in xs]
+    bt.vcycle(xs, bs, 2, 2)
+    assert all(not torch.equal(x, xi) for x, xi in zip(xs, x_in))
