@@ -353,16 +353,16 @@ __global__ void kb_apply(const BLevel* __restrict__ L, const int64_t* __restrict
 // kb_apply's thread per subdomain gathers each box node's 8-wide residual row
 // and updates its owned rows of x where the lanes of a warp sit two nodes
 // apart: every load or store of a warp touches 32 cache lines, and those L1
-// wavefronts, not HBM, set its time.  Here a block takes 32 x TY vertices (one
-// warp per row of vertices, so the interleaved stored rows stay one warp-wide
-// load).  The fp32 residual of the block's boxes, (2*32+3) x (2*TY+3) nodes x
+// wavefronts, not HBM, set its time.  Here a block takes 32 x TY vertices (a
+// warp spans one row of 32 vertices, so the interleaved stored rows stay one
+// warp-wide load; SPLIT warps per row share its owned rows).  The fp32 residual of the block's boxes, (2*32+3) x (2*TY+3) nodes x
 // 2 components x 8 RHS, is copied once into shared memory by coalesced 16-byte
 // cp.async (zero outside the grid, where kb_apply reads zero); each thread
 // forms kb_apply's sums in kb_apply's order from there; the velocity
 // corrections go back through the same buffer and are added to x by rows of
 // owned nodes (contiguous 16-byte pieces), the pressure correction directly.
 // Results equal kb_apply's bit for bit.
-constexpr int kTileX = 32;  // vertices per block row (one warp)
+constexpr int kTileX = 32;  // vertices per block row (the lanes of a warp)
 
 // Byte offset of 16-byte chunk q (0..3: component q/2, RHS 4(q%2)..4(q%2)+3)
 // of node ln in a tile buffer: two 64-byte nodes per 128-byte line, the chunk
